@@ -1,0 +1,300 @@
+/*
+ * fw_oracle.c -- plain CPU oracle for the per-step transition sampling of
+ * dynamic random walks (FlexiWalker, arXiv 2512.00705).
+ *
+ * TEST INFRASTRUCTURE ONLY.  The test-suite, the package smoke check and the
+ * benchmark's CPU-baseline leg are the only users.  The GPU library neither
+ * links nor calls this file, and the two share no code, header, table or
+ * constant: the only common ground is the seeded input generator that feeds
+ * both.  Nothing here is tuned for speed; every function follows a
+ * definition from the paper, cited at the function.
+ *
+ * Compile with -ffp-contract=off: every FP32 product and sum below is one
+ * IEEE-754 single-precision operation, rounded to nearest, in source order.
+ *
+ * Definitions followed:
+ *   Eq. (prob), Sec. 2.1      w~(v,u) = w(v,u) * h(v,u);  p(u) = w~(v,u) / sum_t w~(v,t)
+ *   Eq. (node2vec), Sec. 2.1  w = 1/a if dist(v',u)=0, 1 if dist(v',u)=1, 1/b if dist(v',u)=2
+ *                             (the paper's a, b are node2vec's p, q)
+ *   MetaPath, Sec. 2.1        w in {0,1}: 1 iff the edge label equals the schema entry of the step
+ *   ITS, Sec. 2.2             one uniform, cumulative weights, first index whose cumulative
+ *                             weight exceeds the scaled uniform
+ *   Sec. 3.3 (bound), Sec. 4.1 Eq. (runtime), Eq. (sum_estimation), Sec. 4.2 (sum helper):
+ *                             B = max(w) * h_MAX[v]; sum-hat = h_SUM[v] * mean of the
+ *                             distinct return values of w; eRJS iff r * B < sum-hat
+ *   Philox4x32-10             Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+ *                             as 1, 2, 3", SC'11.
+ *
+ * Readings where the paper is silent (each also listed in the design notes):
+ *   - Hop 0 of node2vec has no previous node (vprev < 0): w = 1 for every
+ *     neighbour.
+ *   - dist(v',u) = 1 means u is in the out-adjacency of v' (graphs are symmetrised).
+ *   - A walk of length L makes L hops; its row holds L+1 entries starting with
+ *     the start node.  A walker whose current node has zero total transition
+ *     weight (no neighbours, or no neighbour with a matching label) stops and
+ *     the rest of its row is -1.
+ *   - The metapath label required at hop j is schema[j mod S].
+ *   - Exact-mode uniform: Philox4x32-10 with key = (seed low 32, seed high 32)
+ *     and counter = (walker id, hop index, 0, 0); u = (x0 >> 8) * 2^-24.
+ *   - Exact-mode pick: W_k = W_{k-1} + w~_k in FP32 in neighbour order,
+ *     t = u * W_{d-1} in FP32, pick the smallest k with t < W_k; if rounding
+ *     leaves none, pick the last k with w~_k > 0.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+enum { OR_WEIGHTED = 0, OR_NODE2VEC = 1, OR_METAPATH = 2 };
+enum { OR_MODE_RJS = 1, OR_MODE_RVS = 2 };
+
+/* ---------------------------------------------------------------------------
+ * Philox4x32-10 (Salmon et al., SC'11): a 10-round Feistel-like bijection on
+ * a 128-bit counter under a 64-bit key.  Round: two 32x32->64 multiplies by
+ * the published constants, the high halves are XORed with the other two
+ * counter words and the key; the key is bumped by the published Weyl
+ * constants between rounds.
+ * ------------------------------------------------------------------------- */
+void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+  uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Exact-mode uniform for (seed, walker, hop): u in [0,1) on a 2^-24 grid. */
+float or_exact_uniform(uint64_t seed, uint32_t walker, uint32_t hop) {
+  uint32_t ctr[4] = {walker, hop, 0u, 0u};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t x[4];
+  or_philox4x32_10(ctr, key, x);
+  return (float)(x[0] >> 8) * 0x1.0p-24f;
+}
+
+/* The FP32 node2vec constants 1/p and 1/q: the reciprocal is taken in double
+ * from the FP32 parameter and rounded once to FP32. */
+float or_recip(float p) { return (float)(1.0 / (double)p); }
+
+/* Is u an out-neighbour of x?  Rows are sorted ascending (checked by the
+ * caller's input validation); bsearch is the C library's binary search. */
+static int cmp_i32(const void *a, const void *b) {
+  int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+  return (x > y) - (x < y);
+}
+static int is_neighbour(const int32_t *offsets, const int32_t *cols, int32_t x, int32_t u) {
+  int64_t s = offsets[x], e = offsets[x + 1];
+  if (e <= s) return 0;
+  return bsearch(&u, cols + s, (size_t)(e - s), sizeof(int32_t), cmp_i32) != NULL;
+}
+
+/*
+ * Transition weights w~_k (FP32) of the d neighbours of v at hop `step`,
+ * Eq. (prob) with w from Eq. (node2vec) or the MetaPath rule (Sec. 2.1).
+ * h == NULL means h = 1 (the unweighted variants of Sec. 5.1).
+ * vprev < 0 means there is no previous node (hop 0).
+ * Returns d, or -1 on bad arguments.  wt may be NULL (degree query).
+ */
+int64_t or_transition_weights(const int32_t *offsets, const int32_t *cols, const float *h,
+                              const uint8_t *labels, int32_t n, int32_t v, int32_t vprev,
+                              int32_t step, int32_t algo, float p, float q,
+                              const uint8_t *schema, int32_t schema_len, float *wt) {
+  if (!offsets || !cols || v < 0 || v >= n || vprev >= n || step < 0) return -1;
+  if (algo == OR_NODE2VEC && !(p > 0 && q > 0 && isfinite(p) && isfinite(q))) return -1;
+  if (algo == OR_METAPATH && (!labels || !schema || schema_len < 1)) return -1;
+  if (algo != OR_WEIGHTED && algo != OR_NODE2VEC && algo != OR_METAPATH) return -1;
+  const int64_t s = offsets[v], d = (int64_t)offsets[v + 1] - s;
+  if (!wt) return d;
+  const float inv_p = or_recip(p), inv_q = or_recip(q);
+  for (int64_t k = 0; k < d; ++k) {
+    const int32_t u = cols[s + k];
+    const float hk = h ? h[s + k] : 1.0f;
+    float w;
+    if (algo == OR_WEIGHTED) {
+      w = 1.0f;
+    } else if (algo == OR_NODE2VEC) {
+      if (vprev < 0) w = 1.0f;                                       /* reading: no v'     */
+      else if (u == vprev) w = inv_p;                                /* dist(v',u) = 0     */
+      else if (is_neighbour(offsets, cols, vprev, u)) w = 1.0f;      /* dist(v',u) = 1     */
+      else w = inv_q;                                                /* dist(v',u) = 2     */
+    } else {
+      w = (labels[s + k] == schema[step % schema_len]) ? 1.0f : 0.0f;
+    }
+    wt[k] = w * hk; /* one FP32 multiply */
+  }
+  return d;
+}
+
+/* Exact transition probabilities (fp64), Eq. (prob).  All zero when the total
+ * weight is zero (a dead end).  Returns d or -1. */
+int64_t or_transition_probs(const int32_t *offsets, const int32_t *cols, const float *h,
+                            const uint8_t *labels, int32_t n, int32_t v, int32_t vprev,
+                            int32_t step, int32_t algo, float p, float q, const uint8_t *schema,
+                            int32_t schema_len, double *probs) {
+  int64_t d = or_transition_weights(offsets, cols, h, labels, n, v, vprev, step, algo, p, q,
+                                    schema, schema_len, NULL);
+  if (d < 0 || !probs) return d;
+  float *wt = (float *)malloc((size_t)(d > 0 ? d : 1) * sizeof(float));
+  if (!wt) return -1;
+  or_transition_weights(offsets, cols, h, labels, n, v, vprev, step, algo, p, q, schema,
+                        schema_len, wt);
+  double total = 0.0;
+  for (int64_t k = 0; k < d; ++k) total += (double)wt[k];
+  for (int64_t k = 0; k < d; ++k) probs[k] = total > 0.0 ? (double)wt[k] / total : 0.0;
+  free(wt);
+  return d;
+}
+
+/* Inverse-transform pick (Sec. 2.2, ITS) over FP32 weights with one uniform
+ * u in [0,1).  Returns the chosen index, or -1 when the total is zero. */
+int64_t or_icdf_pick(const float *wt, int64_t d, float u) {
+  float total = 0.0f;
+  for (int64_t k = 0; k < d; ++k) total = total + wt[k];
+  if (!(total > 0.0f)) return -1;
+  const float t = u * total;
+  float run = 0.0f;
+  for (int64_t k = 0; k < d; ++k) {
+    run = run + wt[k];
+    if (t < run) return k;
+  }
+  for (int64_t k = d - 1; k >= 0; --k)
+    if (wt[k] > 0.0f) return k;
+  return -1;
+}
+
+/*
+ * Full walks in exact mode.  out is row-major [W][L+1]; row i starts with
+ * starts[i].  The walker id used by the random stream is walker_base + i.
+ * Returns the number of hops taken (entries other than the start and -1),
+ * or -1 on bad arguments.
+ */
+int64_t or_walk(const int32_t *offsets, const int32_t *cols, const float *h,
+                const uint8_t *labels, int32_t n, const int32_t *starts, int32_t num_walkers,
+                int32_t len, int32_t algo, float p, float q, const uint8_t *schema,
+                int32_t schema_len, uint64_t seed, uint32_t walker_base, int32_t *out,
+                int32_t nthreads) {
+  if (!offsets || !cols || !starts || !out || num_walkers < 0 || len < 0 || n < 0) return -1;
+  for (int32_t i = 0; i < num_walkers; ++i)
+    if (starts[i] < 0 || starts[i] >= n) return -1;
+  if (algo == OR_NODE2VEC && !(p > 0 && q > 0 && isfinite(p) && isfinite(q))) return -1;
+  if (algo == OR_METAPATH && (!labels || !schema || schema_len < 1)) return -1;
+  int32_t maxd = 0;
+  for (int32_t v = 0; v < n; ++v)
+    if (offsets[v + 1] - offsets[v] > maxd) maxd = offsets[v + 1] - offsets[v];
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+  int64_t hops = 0;
+  int failed = 0;
+#pragma omp parallel reduction(+ : hops)
+  {
+    float *wt = (float *)malloc((size_t)(maxd > 0 ? maxd : 1) * sizeof(float));
+    if (!wt) {
+#pragma omp atomic write
+      failed = 1;
+    }
+#pragma omp for schedule(dynamic, 64)
+    for (int32_t i = 0; i < num_walkers; ++i) {
+      if (!wt) continue;
+      int32_t *row = out + (int64_t)i * (len + 1);
+      int32_t cur = starts[i], prev = -1;
+      row[0] = cur;
+      int32_t j = 0;
+      for (; j < len; ++j) {
+        int64_t d = or_transition_weights(offsets, cols, h, labels, n, cur, prev, j, algo, p, q,
+                                          schema, schema_len, wt);
+        float u = or_exact_uniform(seed, walker_base + (uint32_t)i, (uint32_t)j);
+        int64_t k = or_icdf_pick(wt, d, u);
+        if (k < 0) break;
+        int32_t nxt = cols[offsets[cur] + k];
+        row[j + 1] = nxt;
+        prev = cur;
+        cur = nxt;
+        hops++;
+      }
+      for (int32_t r = j + 1; r <= len; ++r) row[r] = -1;
+    }
+    free(wt);
+  }
+  return failed ? -1 : hops;
+}
+
+/* Per-node reductions of the property weights (Sec. 4.2, preprocess()):
+ * h_MAX[v] = max_k h (FP32, exact), h_SUM[v] = sum_k h in fp64.  h == NULL
+ * means h = 1.  Nodes without neighbours get 0 for both. */
+int or_node_stats(const int32_t *offsets, const float *h, int32_t n, float *hmax, double *hsum) {
+  if (!offsets || n < 0 || !hmax || !hsum) return -1;
+  for (int32_t v = 0; v < n; ++v) {
+    float m = 0.0f;
+    double s = 0.0;
+    for (int64_t i = offsets[v]; i < offsets[v + 1]; ++i) {
+      float x = h ? h[i] : 1.0f;
+      if (x > m) m = x;
+      s += (double)x;
+    }
+    hmax[v] = m;
+    hsum[v] = s;
+  }
+  return 0;
+}
+
+/*
+ * The per-step plan of the runtime (Sec. 3.3 bound, Sec. 4.1 cost model,
+ * Sec. 4.2 helper functions), for one walker at v (has_prev = 0 when there
+ * is no previous node, i.e. on hop 0):
+ *   B       = max(w) * h_MAX[v]        (FP32 product; max(w) of the algorithm)
+ *   sum_hat = h_SUM[v] * mean_w        (FP32 product; mean of the distinct return
+ *                                       expressions of get_weight, Eq. (sum_estimation))
+ *   mode    = eRJS iff r * B < sum_hat (FP32), else eRVS   (Eq. (runtime))
+ * Distinct return expressions: node2vec {h/a, h, h/b} (3; without v': {h}),
+ * metapath {h, 0} (2), weighted {h} (1).  The means are taken in double and
+ * rounded once to FP32.  With h = 1 (unweighted) h_MAX = 1 and h_SUM = d(v),
+ * which is the paper's PER_KERNEL rule (mean times degree).
+ */
+int or_step_plan(float hmax, float hsum, int32_t has_prev, int32_t algo, float p, float q, float r,
+                 float *bound, float *sum_hat) {
+  float wmax, wmean;
+  if (algo == OR_NODE2VEC) {
+    if (!(p > 0 && q > 0)) return -1;
+    const float ip = or_recip(p), iq = or_recip(q);
+    if (!has_prev) {
+      wmax = 1.0f;
+      wmean = 1.0f;
+    } else {
+      wmax = ip > 1.0f ? ip : 1.0f;
+      if (iq > wmax) wmax = iq;
+      wmean = (float)(((double)ip + 1.0 + (double)iq) / 3.0);
+    }
+  } else if (algo == OR_METAPATH) {
+    wmax = 1.0f;
+    wmean = 0.5f;
+  } else if (algo == OR_WEIGHTED) {
+    wmax = 1.0f;
+    wmean = 1.0f;
+  } else {
+    return -1;
+  }
+  const float B = wmax * hmax;
+  const float S = hsum * wmean;
+  if (bound) *bound = B;
+  if (sum_hat) *sum_hat = S;
+  return (r * B < S) ? OR_MODE_RJS : OR_MODE_RVS;
+}

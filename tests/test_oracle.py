@@ -1,0 +1,362 @@
+"""Pins for the CPU oracle: each test checks the oracle against something other
+than itself -- published values, closed forms, brute-force enumeration,
+library routines, or invariants (FlexiWalker, arXiv 2512.00705)."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+from paper_2512_00705_gb300 import synth
+from conftest import read_golden
+
+
+# --------------------------------------------------------------- Philox KATs
+def test_philox_known_answers():
+    """Published Random123 known-answer vectors for Philox4x32-10."""
+    rows = read_golden("philox4x32_10_kat.txt")
+    assert len(rows) == 3
+    for r in rows:
+        vals = [int(x, 16) for x in r]
+        ctr, key, want = vals[0:4], vals[4:6], tuple(vals[6:10])
+        assert oracle.philox4x32_10(ctr, key) == want
+
+
+def test_exact_uniform_range_and_uniformity():
+    us = np.array([oracle.exact_uniform(42, w, s) for w in range(2000) for s in range(5)])
+    assert us.min() >= 0.0 and us.max() < 1.0
+    # on the 2^-24 grid
+    assert np.all(us * 2**24 == np.floor(us * 2**24))
+    # uniform (Kolmogorov-Smirnov against U[0,1))
+    assert stats.kstest(us, "uniform").pvalue > 1e-3
+
+
+# ------------------------------------------------------- worked example, Fig 2
+def _star(weights):
+    d = len(weights)
+    edges = [(0, i + 1) for i in range(d)]
+    return synth.from_edges(d + 1, edges, h=weights)
+
+
+def test_worked_example_probabilities():
+    rows = read_golden("worked_example_fig2.txt")
+    w = [float(r[1]) for r in rows]
+    want = [float(r[2]) for r in rows]
+    g = _star(w)
+    got = oracle.transition_probs(g, 0, -1, 0, "weighted")
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-15)
+
+
+def test_icdf_pick_frequencies_match_probabilities():
+    """Inverse transform: over a fine grid of u the share mapped to k equals
+    p_k up to the grid step, and the map is monotone (Sec. 2.2, ITS)."""
+    rows = read_golden("worked_example_fig2.txt")
+    w = np.array([float(r[1]) for r in rows], dtype=np.float32)
+    want = np.array([float(r[2]) for r in rows])
+    grid = (np.arange(0, 2**14) * 2**10).astype(np.float64) * 2.0**-24
+    picks = np.array([oracle.icdf_pick(w, float(u)) for u in grid])
+    assert np.all(np.diff(picks) >= 0)
+    share = np.bincount(picks, minlength=4) / len(grid)
+    np.testing.assert_allclose(share, want, atol=2.0 / len(grid))
+    # zero weights are never picked; all-zero gives a dead end
+    w2 = np.array([0, 1, 0, 2, 0], dtype=np.float32)
+    picks2 = {oracle.icdf_pick(w2, float(u)) for u in grid[::7]}
+    assert picks2 == {1, 3}
+    assert oracle.icdf_pick(np.zeros(3, np.float32), 0.5) == -1
+
+
+# -------------------------------------------------- node2vec closed forms, Eq 2
+def _cycle(n):
+    return synth.from_edges(n, [(i, (i + 1) % n) for i in range(n)])
+
+
+def _complete(n):
+    return synth.from_edges(n, [(i, j) for i in range(n) for j in range(i + 1, n)])
+
+
+@pytest.mark.parametrize("p,q", [(2.0, 0.5), (0.25, 4.0), (1.0, 1.0), (3.0, 0.7)])
+def test_node2vec_closed_forms(p, q):
+    ip, iq = 1.0 / p, 1.0 / q
+    # cycle C_6, at v=2 coming from v'=1: neighbours {1 (return), 3 (distance 2)}
+    g = _cycle(6)
+    pr = oracle.transition_probs(g, 2, 1, 1, "node2vec", p, q)
+    nb = list(g.cols[g.offsets[2]:g.offsets[3]])
+    assert nb == [1, 3]
+    np.testing.assert_allclose(pr[0], ip / (ip + iq), rtol=1e-6)
+    # triangle, at v=1 from v'=0: neighbours {0 (return), 2 (adjacent to v')}
+    g = _cycle(3)
+    pr = oracle.transition_probs(g, 1, 0, 1, "node2vec", p, q)
+    np.testing.assert_allclose(pr[0], ip / (ip + 1.0), rtol=1e-6)
+    # K_5, at v=3 from v'=0: return has 1/p, the three others weight 1
+    g = _complete(5)
+    pr = oracle.transition_probs(g, 3, 0, 1, "node2vec", p, q)
+    nb = list(g.cols[g.offsets[3]:g.offsets[4]])
+    assert nb[0] == 0
+    np.testing.assert_allclose(pr[0], ip / (ip + 3.0), rtol=1e-6)
+    np.testing.assert_allclose(pr[1:], 1.0 / (ip + 3.0), rtol=1e-6)
+    # without a previous node (hop 0): first-order walk
+    pr = oracle.transition_probs(g, 3, -1, 0, "node2vec", p, q)
+    np.testing.assert_allclose(pr, 0.25, rtol=1e-12)
+
+
+def test_node2vec_weighted_closed_form():
+    """Path a-b-c-d plus chord b-d: at c from b, neighbours b (return, h=2),
+    d (adjacent to b, h=3); p=2, q=0.5 -> weights 2*0.5=1, 3*1=3."""
+    g = synth.from_edges(4, [(0, 1), (1, 2), (2, 3), (1, 3)], h=[1.0, 2.0, 3.0, 5.0])
+    pr = oracle.transition_probs(g, 2, 1, 1, "node2vec", 2.0, 0.5)
+    np.testing.assert_allclose(pr, [0.25, 0.75], rtol=1e-7)
+    # at b from a: neighbours a (return, h=1 -> 0.5), c (dist 2 from a, h=2 -> 4), d (dist 2, h=5 -> 10)
+    pr = oracle.transition_probs(g, 1, 0, 1, "node2vec", 2.0, 0.5)
+    np.testing.assert_allclose(pr, np.array([0.5, 4.0, 10.0]) / 14.5, rtol=1e-7)
+
+
+def test_known_bound_unweighted_node2vec():
+    """Sec. 3.3: unweighted node2vec with a=1, b=0.5 has maximum weight 2."""
+    (a, b, h, mx), = [[float(x) for x in r] for r in read_golden("node2vec_known_bound.txt")]
+    mode, B, _ = oracle.step_plan(h, 10.0, True, "node2vec", a, b, 4.0)
+    assert B == mx
+    g = _complete(6)  # every non-return neighbour adjacent to v'
+    wt = oracle.transition_weights(g, 2, 0, 1, "node2vec", a, b)
+    assert wt.max() <= B
+    g = _cycle(8)     # every non-return neighbour at distance 2: weight 1/b = 2 reaches the bound
+    wt = oracle.transition_weights(g, 2, 1, 1, "node2vec", a, b)
+    assert wt.max() == B
+
+
+# ------------------------------------------------------------------ metapath
+def test_metapath_filter():
+    g = synth.from_edges(5, [(0, 1), (0, 2), (0, 3), (0, 4)], h=[1.0, 2.0, 3.0, 4.0], labels=[0, 1, 1, 2])
+    schema = [1, 2, 0]
+    np.testing.assert_allclose(oracle.transition_probs(g, 0, -1, 0, "metapath", schema=schema), [0, 0.4, 0.6, 0])
+    np.testing.assert_allclose(oracle.transition_probs(g, 0, 3, 1, "metapath", schema=schema), [0, 0, 0, 1])
+    np.testing.assert_allclose(oracle.transition_probs(g, 0, 3, 2, "metapath", schema=schema), [1, 0, 0, 0])
+    # cyclic schema: hop 3 uses schema[0]
+    np.testing.assert_allclose(oracle.transition_probs(g, 0, 3, 3, "metapath", schema=schema), [0, 0.4, 0.6, 0])
+    # schema label absent -> dead end (all zero)
+    assert oracle.transition_probs(g, 0, -1, 0, "metapath", schema=[3]).sum() == 0
+
+
+# ------------------------------------------------------- brute force, 8 nodes
+def _bf_weight(adj, h, lab, v, u, vprev, hop, algo, p, q, schema):
+    """Eq. (prob) / Eq. (node2vec) / MetaPath written out on adjacency sets."""
+    hv = h[(v, u)]
+    if algo == "weighted":
+        return hv
+    if algo == "node2vec":
+        if vprev is None:
+            return hv
+        if u == vprev:
+            return hv / p
+        if u in adj[vprev]:
+            return hv
+        return hv / q
+    return hv if lab[(v, u)] == schema[hop % len(schema)] else 0.0
+
+
+def _bf_paths(g, start, length, algo, p, q, schema):
+    n = g.n
+    adj = [set(g.cols[g.offsets[i]:g.offsets[i + 1]].tolist()) for i in range(n)]
+    h, lab = {}, {}
+    for v in range(n):
+        for k in range(g.offsets[v], g.offsets[v + 1]):
+            u = int(g.cols[k])
+            h[(v, u)] = float(g.h[k]) if g.h is not None else 1.0
+            lab[(v, u)] = int(g.labels[k]) if g.labels is not None else 0
+    out = {}
+
+    def rec(path, prob):
+        hop = len(path) - 1
+        if hop == length:
+            out[tuple(path)] = out.get(tuple(path), 0.0) + prob
+            return
+        v = path[-1]
+        vprev = path[-2] if len(path) > 1 else None
+        ws = {u: _bf_weight(adj, h, lab, v, u, vprev, hop, algo, p, q, schema) for u in sorted(adj[v])}
+        tot = sum(ws.values())
+        if tot <= 0:
+            padded = tuple(path) + (-1,) * (length - hop)
+            out[padded] = out.get(padded, 0.0) + prob
+            return
+        for u, w in ws.items():
+            if w > 0:
+                rec(path + [u], prob * w / tot)
+
+    rec([start], 1.0)
+    return out
+
+
+CASES = [("weighted", 1.0, 1.0, None), ("node2vec", 2.0, 0.5, None), ("node2vec", 0.25, 4.0, None),
+         ("node2vec", 3.0, 0.7, None), ("metapath", 1.0, 1.0, [0, 1, 2])]
+
+
+@pytest.mark.parametrize("algo,p,q,schema", CASES)
+@pytest.mark.parametrize("gseed", [11, 12])
+def test_brute_force_path_probabilities(algo, p, q, schema, gseed):
+    g = synth.random_graph(8, 0.45, seed=gseed, weighted=True, nlabels=3)
+    L = 4
+    for start in range(8):
+        bf = _bf_paths(g, start, L, algo, p, q, schema)
+        assert abs(sum(bf.values()) - 1.0) < 1e-12
+        for path, pb in bf.items():
+            # product of the oracle's per-hop probabilities along the path
+            prob, prev = 1.0, -1
+            for j in range(L):
+                v, u = path[j], path[j + 1]
+                if u == -1:
+                    assert oracle.transition_probs(g, v, prev, j, algo, p, q, schema).sum() == 0
+                    break
+                pr = oracle.transition_probs(g, v, prev, j, algo, p, q, schema)
+                nb = list(g.cols[g.offsets[v]:g.offsets[v + 1]])
+                prob *= pr[nb.index(u)]
+                prev = v
+            assert prob == pytest.approx(pb, rel=2e-6, abs=1e-12)
+
+
+@pytest.mark.parametrize("algo,p,q,schema", CASES)
+def test_brute_force_sampler_frequencies(algo, p, q, schema):
+    """Exact-mode walks from one start, many walker ids: path frequencies
+    match brute-force path probabilities (chi-square, merged bins)."""
+    g = synth.random_graph(8, 0.45, seed=11, weighted=True, nlabels=3)
+    L, W, start = 4, 60000, 0
+    bf = _bf_paths(g, start, L, algo, p, q, schema)
+    out, _ = oracle.walk(g, np.full(W, start, np.int32), L, algo, p, q, schema, seed=7)
+    keys = list(bf.keys())
+    index = {k: i for i, k in enumerate(keys)}
+    counts = np.zeros(len(keys))
+    for row in map(tuple, out.tolist()):
+        assert row in index, f"walk {row} has probability zero"
+        counts[index[row]] += 1
+    exp = np.array([bf[k] for k in keys]) * W
+    order = np.argsort(exp)
+    obs_m, exp_m, acc_o, acc_e = [], [], 0.0, 0.0
+    for i in order:  # merge the smallest bins until expected >= 5
+        acc_o += counts[i]
+        acc_e += exp[i]
+        if acc_e >= 5:
+            obs_m.append(acc_o)
+            exp_m.append(acc_e)
+            acc_o = acc_e = 0.0
+    if acc_e > 0:
+        obs_m[-1] += acc_o
+        exp_m[-1] += acc_e
+    assert stats.chisquare(obs_m, exp_m).pvalue > 1e-3
+
+
+# --------------------------------------------------------- reductions / invariants
+def test_node2vec_p1q1_equals_weighted_walk():
+    """node2vec with p = q = 1 has w = 1 everywhere, so its walks equal the
+    weighted first-order walk bit for bit under the same draws."""
+    g = synth.workload_graph("small")
+    starts = np.arange(g.n, dtype=np.int32)
+    a, ha = oracle.walk(g, starts, 20, "node2vec", 1.0, 1.0, seed=42)
+    b, hb = oracle.walk(g, starts, 20, "weighted", seed=42)
+    assert ha == hb
+    np.testing.assert_array_equal(a, b)
+
+
+def _check_walk_invariants(g, starts, out, algo, schema=None):
+    L = out.shape[1] - 1
+    assert np.array_equal(out[:, 0], starts)
+    for row in out:
+        alive = True
+        for j in range(L):
+            v, u = row[j], row[j + 1]
+            if u == -1:
+                alive = False
+                continue
+            assert alive, "-1 only as a suffix"
+            nb = g.cols[g.offsets[v]:g.offsets[v + 1]]
+            k = np.searchsorted(nb, u)
+            assert k < len(nb) and nb[k] == u, "hop is not an edge"
+            if algo == "metapath":
+                assert g.labels[g.offsets[v] + k] == schema[j % len(schema)]
+
+
+@pytest.mark.parametrize("algo,schema", [("node2vec", None), ("metapath", [0, 1, 2, 3, 4]), ("weighted", None)])
+def test_walk_invariants_small(algo, schema):
+    g = synth.workload_graph("small")
+    starts = np.arange(g.n, dtype=np.int32)
+    out, hops = oracle.walk(g, starts, 20, algo, 2.0, 0.5, schema, seed=42)
+    _check_walk_invariants(g, starts[:600], out[:600], algo, schema)
+    assert hops == int((out[:, 1:] >= 0).sum())
+    # dead ends only where the total transition weight is zero
+    for i in range(0, g.n, 7):
+        row = out[i]
+        if row[-1] == -1:
+            j = int(np.argmax(row == -1)) - 1
+            prev = int(row[j - 1]) if j >= 1 else -1
+            assert oracle.transition_probs(g, int(row[j]), prev, j, algo, 2.0, 0.5, schema).sum() == 0
+
+
+def test_walk_rejects_bad_arguments():
+    g = synth.workload_graph("small")
+    with pytest.raises(ValueError):
+        oracle.walk(g, np.array([g.n], np.int32), 5, "weighted")
+    with pytest.raises(ValueError):
+        oracle.walk(g, np.array([0], np.int32), 5, "node2vec", 0.0, 1.0)
+
+
+def test_walker_base_shifts_random_stream():
+    g = synth.workload_graph("small")
+    starts = np.arange(64, dtype=np.int32)
+    full, _ = oracle.walk(g, np.concatenate([starts, starts]), 10, "node2vec", 2.0, 0.5, seed=5)
+    tail, _ = oracle.walk(g, starts, 10, "node2vec", 2.0, 0.5, seed=5, walker_base=64)
+    np.testing.assert_array_equal(full[64:], tail)
+
+
+# ------------------------------------------------------------ preprocess + plan
+def test_node_stats_match_library_reductions():
+    g = synth.workload_graph("small")
+    hmax, hsum = oracle.node_stats(g)
+    deg = g.degrees()
+    nz = deg > 0
+    idx = g.offsets[:-1][nz]
+    np.testing.assert_array_equal(hmax[nz], np.maximum.reduceat(g.h, idx))
+    np.testing.assert_allclose(hsum[nz], np.add.reduceat(g.h.astype(np.float64), idx), rtol=1e-12)
+    assert np.all(hmax[~nz] == 0) and np.all(hsum[~nz] == 0)
+    g2 = synth.Csr(g.offsets, g.cols)
+    hmax2, hsum2 = oracle.node_stats(g2)
+    np.testing.assert_array_equal(hsum2, deg)
+    np.testing.assert_array_equal(hmax2[nz], 1.0)
+
+
+@pytest.mark.parametrize("algo,p,q", [("node2vec", 2.0, 0.5), ("node2vec", 0.25, 4.0), ("node2vec", 4.0, 0.25),
+                                      ("metapath", 1, 1), ("weighted", 1, 1)])
+def test_bound_dominates_every_weight(algo, p, q):
+    """eRJS is exact only if B >= max w~ (Sec. 3.3 proof): check on every
+    (v, v') state of a graph."""
+    g = synth.random_graph(40, 0.2, seed=3, weighted=True, nlabels=5)
+    hmax, hsum = oracle.node_stats(g)
+    schema = [0, 1, 2, 3, 4]
+    for v in range(g.n):
+        prevs = [-1] + list(g.cols[g.offsets[v]:g.offsets[v + 1]])
+        for vp in prevs:
+            for step in ([0] if vp < 0 else [1, 2]):
+                wt = oracle.transition_weights(g, v, int(vp), step, algo, p, q, schema)
+                _, B, _ = oracle.step_plan(float(hmax[v]), float(hsum[v]), vp >= 0, algo, p, q, 4.0)
+                if len(wt):
+                    assert wt.max() <= B
+
+
+def test_cost_model_hand_made():
+    """Eq. (runtime): eRJS iff r*B < sum-hat."""
+    # weighted: B = h_MAX, sum-hat = h_SUM
+    assert oracle.step_plan(1.0, 10.0, True, "weighted", r=4.0)[0] == oracle.MODE_RJS
+    assert oracle.step_plan(1.0, 3.0, True, "weighted", r=4.0)[0] == oracle.MODE_RVS
+    assert oracle.step_plan(1.0, 4.0, True, "weighted", r=4.0)[0] == oracle.MODE_RVS  # strict <
+    # metapath: sum-hat = h_SUM * (1 + 0) / 2
+    m, B, S = oracle.step_plan(2.0, 20.0, True, "metapath", r=4.0)
+    assert (B, S) == (2.0, 10.0) and m == oracle.MODE_RJS
+    m, B, S = oracle.step_plan(2.0, 15.0, True, "metapath", r=4.0)
+    assert m == oracle.MODE_RVS
+    # node2vec p=2, q=0.5: max w = 2, mean w = (0.5 + 1 + 2) / 3
+    m, B, S = oracle.step_plan(1.0, 30.0, True, "node2vec", 2.0, 0.5, r=4.0)
+    assert B == 2.0 and S == pytest.approx(30.0 * 3.5 / 3, rel=1e-7)
+    assert m == oracle.MODE_RJS
+    m, B, S = oracle.step_plan(1.0, 6.0, True, "node2vec", 2.0, 0.5, r=4.0)
+    assert m == oracle.MODE_RVS
+    # hop 0 of node2vec: first-order (B = h_MAX, sum-hat = h_SUM)
+    m, B, S = oracle.step_plan(1.0, 6.0, False, "node2vec", 2.0, 0.5, r=4.0)
+    assert (B, S, m) == (1.0, 6.0, oracle.MODE_RJS)
