@@ -1,0 +1,412 @@
+// fw_api.cu -- the C ABI declared in include/flexiwalk.h.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fw_internal.h"
+
+namespace fw {
+
+std::atomic<unsigned long long> g_launches{0};
+
+static thread_local std::string t_last_error;
+
+fw_status set_error(fw_status st, const std::string& msg) {
+  t_last_error = msg;
+  return st;
+}
+
+fw_status cuda_error(cudaError_t err, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorName(err) + " (" + cudaGetErrorString(err) + ")";
+  return set_error(err == cudaErrorMemoryAllocation ? FW_ERR_OOM : FW_ERR_CUDA, m);
+}
+
+DevGraph dev_graph(const fw_graph* g) {
+  DevGraph d;
+  d.off = g->d_off;
+  d.col = g->d_col;
+  d.h = g->d_h;
+  d.lab = g->d_lab;
+  d.hmax = g->d_hmax;
+  d.hsum = g->d_hsum;
+  d.n = g->n;
+  return d;
+}
+
+static float recip_f32(float p) { return (float)(1.0 / (double)p); }
+
+fw_status make_job(const fw_graph* g, int32_t algo, const fw_params* params, uint64_t seed, Job* job) {
+  fw_params P;
+  if (params) P = *params;
+  else fw_params_default(&P);
+  if (algo != ALGO_WEIGHTED && algo != ALGO_NODE2VEC && algo != ALGO_METAPATH)
+    return set_error(FW_ERR_ARG, "unknown algo");
+  if (P.mode < MODE_AUTO || P.mode > MODE_EXACT) return set_error(FW_ERR_ARG, "unknown mode");
+  if (algo == ALGO_NODE2VEC && !(P.p > 0.0f && P.q > 0.0f && std::isfinite(P.p) && std::isfinite(P.q)))
+    return set_error(FW_ERR_ARG, "node2vec needs finite p, q > 0");
+  if (algo == ALGO_METAPATH) {
+    if (!g->d_lab) return set_error(FW_ERR_ARG, "metapath needs edge labels");
+    if (P.schema_len < 1 || P.schema_len > 16) return set_error(FW_ERR_ARG, "metapath schema_len must be 1..16");
+  }
+  if (P.cost_ratio > 0.0f && !std::isfinite(P.cost_ratio)) return set_error(FW_ERR_ARG, "cost_ratio not finite");
+  std::memset(job, 0, sizeof(Job));
+  job->algo = algo;
+  job->mode = P.mode;
+  job->flags = P.flags;
+  job->rjs_cap = P.rjs_cap > 0 ? P.rjs_cap : 64;
+  job->schema_len = algo == ALGO_METAPATH ? P.schema_len : 1;
+  std::memcpy(job->schema, P.schema, 16);
+  job->weighted = (g->d_h != nullptr && !(P.flags & FW_FLAG_UNWEIGHTED)) ? 1 : 0;
+  if (algo == ALGO_NODE2VEC) {
+    const float ip = recip_f32(P.p), iq = recip_f32(P.q);
+    job->inv_p = ip;
+    job->inv_q = iq;
+    job->wmax1 = std::fmax(std::fmax(ip, 1.0f), iq);
+    job->wmean1 = (float)(((double)ip + 1.0 + (double)iq) / 3.0);
+    job->wlo1 = std::fmin(1.0f, iq);
+    job->whi1 = std::fmax(1.0f, iq);
+    job->need_member = (iq != 1.0f) ? 1 : 0;
+  } else {
+    job->inv_p = job->inv_q = 1.0f;
+    job->wmax1 = job->wlo1 = job->whi1 = 1.0f;
+    job->wmean1 = algo == ALGO_METAPATH ? 0.5f : 1.0f;
+  }
+  job->ratio = P.cost_ratio > 0.0f ? P.cost_ratio : g->ratio;
+  job->key0 = (uint32_t)seed;
+  job->key1 = (uint32_t)(seed >> 32);
+  job->walker_base = P.walker_base;
+  return FW_OK;
+}
+
+static fw_status with_qctr(const fw_graph* g, const Job* jobs, int njobs, long long total, bool count,
+                           cudaStream_t st) {
+  unsigned long long* q = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&q), sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync(queue counter)");
+  e = cudaMemsetAsync(q, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = launch_walk(g, jobs, njobs, total, count, q, st);
+  cudaError_t e2 = cudaFreeAsync(q, st);
+  if (e != cudaSuccess) return cuda_error(e, "walk launch");
+  if (e2 != cudaSuccess) return cuda_error(e2, "cudaFreeAsync(queue counter)");
+  return FW_OK;
+}
+
+}  // namespace fw
+
+using namespace fw;
+
+// ---------------------------------------------------------------------------
+extern "C" void fw_params_default(fw_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->p = 1.0f;
+  p->q = 1.0f;
+  p->mode = FW_MODE_AUTO;
+}
+
+extern "C" const char* fw_last_error(void) { return t_last_error.c_str(); }
+
+extern "C" const char* fw_status_string(fw_status s) {
+  switch (s) {
+    case FW_OK: return "FW_OK";
+    case FW_ERR_ARG: return "FW_ERR_ARG";
+    case FW_ERR_CSR: return "FW_ERR_CSR";
+    case FW_ERR_OOM: return "FW_ERR_OOM";
+    case FW_ERR_CUDA: return "FW_ERR_CUDA";
+    case FW_ERR_TIMEOUT: return "FW_ERR_TIMEOUT";
+    case FW_ERR_DEVICE_CHECK: return "FW_ERR_DEVICE_CHECK";
+    case FW_ERR_BUSY: return "FW_ERR_BUSY";
+    case FW_ERR_UNSUPPORTED: return "FW_ERR_UNSUPPORTED";
+  }
+  return "FW_ERR_UNKNOWN";
+}
+
+extern "C" uint64_t fw_launch_count(void) { return g_launches.load(); }
+
+// Host-side CSR validation (runs before any CUDA call).
+static fw_status validate_host_csr(const int32_t* off, const int32_t* col, const float* h, int32_t n, int64_t e) {
+  if (off[0] != 0) return set_error(FW_ERR_CSR, "offsets[0] != 0");
+  for (int32_t v = 0; v < n; ++v)
+    if (off[v + 1] < off[v]) return set_error(FW_ERR_CSR, "offsets not monotone at node " + std::to_string(v));
+  if ((int64_t)off[n] != e) return set_error(FW_ERR_CSR, "offsets[n] != e");
+  for (int32_t v = 0; v < n; ++v) {
+    for (int32_t i = off[v]; i < off[v + 1]; ++i) {
+      if (col[i] < 0 || col[i] >= n) return set_error(FW_ERR_CSR, "column out of range in row " + std::to_string(v));
+      if (i + 1 < off[v + 1] && col[i + 1] <= col[i])
+        return set_error(FW_ERR_CSR, "row " + std::to_string(v) + " not strictly increasing");
+    }
+  }
+  if (h) {
+    for (int64_t i = 0; i < e; ++i)
+      if (!(h[i] > 0.0f) || !std::isfinite(h[i]))
+        return set_error(FW_ERR_CSR, "weight " + std::to_string(i) + " not finite and > 0");
+  }
+  return FW_OK;
+}
+
+static void free_graph(fw_graph* g) {
+  if (!g) return;
+  cudaFree(g->d_off);
+  cudaFree(g->d_col);
+  cudaFree(g->d_h);
+  cudaFree(g->d_lab);
+  cudaFree(g->d_hmax);
+  cudaFree(g->d_hsum);
+  cudaFree(g->d_err);
+  cudaFree(g->d_cnt);
+  cudaFree(g->d_stage_starts);
+  cudaFree(g->d_stage_out);
+  delete g;
+}
+
+#define FW_TRY(call, what)                                   \
+  do {                                                       \
+    cudaError_t _e = (call);                                 \
+    if (_e != cudaSuccess) {                                 \
+      fw_status _s = cuda_error(_e, what);                   \
+      free_graph(g);                                         \
+      return _s;                                             \
+    }                                                        \
+  } while (0)
+
+extern "C" fw_status fw_graph_create(const int32_t* offsets, const int32_t* cols, const float* weights,
+                                     const uint8_t* labels, int32_t n, int64_t e, int32_t ptr_kind, void* stream,
+                                     fw_graph** out) {
+  if (!out) return set_error(FW_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!offsets || n < 0 || e < 0 || e > 2147483647LL || (e > 0 && !cols))
+    return set_error(FW_ERR_ARG, "bad sizes or NULL arrays");
+  if (ptr_kind != FW_PTR_HOST && ptr_kind != FW_PTR_DEVICE) return set_error(FW_ERR_ARG, "bad ptr_kind");
+  if (ptr_kind == FW_PTR_HOST) {
+    fw_status s = validate_host_csr(offsets, cols, weights, n, e);
+    if (s != FW_OK) return s;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  fw_graph* g = new (std::nothrow) fw_graph();
+  if (!g) return set_error(FW_ERR_OOM, "host allocation");
+  g->n = n;
+  g->e = e;
+  FW_TRY(cudaGetDevice(&g->device), "cudaGetDevice");
+  FW_TRY(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device), "cudaDeviceGetAttribute");
+  const cudaMemcpyKind kind = ptr_kind == FW_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const size_t eb = (size_t)(e > 0 ? e : 1);
+  FW_TRY(cudaMalloc(&g->d_off, sizeof(int32_t) * ((size_t)n + 1)), "cudaMalloc(offsets)");
+  FW_TRY(cudaMalloc(&g->d_col, sizeof(int32_t) * eb), "cudaMalloc(cols)");
+  if (weights) FW_TRY(cudaMalloc(&g->d_h, sizeof(float) * eb), "cudaMalloc(weights)");
+  if (labels) FW_TRY(cudaMalloc(&g->d_lab, eb), "cudaMalloc(labels)");
+  FW_TRY(cudaMalloc(&g->d_hmax, sizeof(float) * ((size_t)n + 1)), "cudaMalloc(h_MAX)");
+  FW_TRY(cudaMalloc(&g->d_hsum, sizeof(float) * ((size_t)n + 1)), "cudaMalloc(h_SUM)");
+  FW_TRY(cudaMalloc(&g->d_err, 64), "cudaMalloc(error word)");
+  FW_TRY(cudaMalloc(&g->d_cnt, sizeof(DevCounters)), "cudaMalloc(counters)");
+  g->bytes = sizeof(int32_t) * ((size_t)n + 1) + eb * (4 + (weights ? 4 : 0) + (labels ? 1 : 0)) +
+             2 * sizeof(float) * ((size_t)n + 1) + 64 + sizeof(DevCounters);
+  FW_TRY(cudaMemsetAsync(g->d_err, 0, 64, st), "cudaMemsetAsync");
+  FW_TRY(cudaMemsetAsync(g->d_cnt, 0, sizeof(DevCounters), st), "cudaMemsetAsync");
+  FW_TRY(cudaMemcpyAsync(g->d_off, offsets, sizeof(int32_t) * ((size_t)n + 1), kind, st), "copy offsets");
+  if (e > 0) FW_TRY(cudaMemcpyAsync(g->d_col, cols, sizeof(int32_t) * (size_t)e, kind, st), "copy cols");
+  if (weights && e > 0) FW_TRY(cudaMemcpyAsync(g->d_h, weights, sizeof(float) * (size_t)e, kind, st), "copy weights");
+  if (labels && e > 0) FW_TRY(cudaMemcpyAsync(g->d_lab, labels, (size_t)e, kind, st), "copy labels");
+  if (ptr_kind == FW_PTR_DEVICE) {
+    unsigned bits = 0;
+    FW_TRY(launch_check_offsets(g->d_off, n, e, g->d_err, g->num_sms, st), "check offsets");
+    FW_TRY(cudaMemcpyAsync(&bits, g->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "read check");
+    FW_TRY(cudaStreamSynchronize(st), "sync");
+    if (bits == 0) {
+      FW_TRY(launch_check_rows(g->d_off, g->d_col, g->d_h, n, g->d_err, g->num_sms, st), "check rows");
+      FW_TRY(cudaMemcpyAsync(&bits, g->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "read check");
+      FW_TRY(cudaStreamSynchronize(st), "sync");
+    }
+    if (bits != 0) {
+      free_graph(g);
+      std::string why = (bits & 1u) ? "offsets invalid" : (bits & 2u) ? "column out of range"
+                        : (bits & 4u) ? "row not strictly increasing" : "weight not finite and > 0";
+      return set_error(FW_ERR_CSR, why);
+    }
+  }
+  // preprocessing: h_MAX, h_SUM, max degree
+  int* d_maxdeg = reinterpret_cast<int*>(g->d_err) + 8;
+  FW_TRY(cudaMemsetAsync(d_maxdeg, 0, sizeof(int), st), "cudaMemsetAsync");
+  cudaEvent_t e0, e1;
+  FW_TRY(cudaEventCreate(&e0), "cudaEventCreate");
+  FW_TRY(cudaEventCreate(&e1), "cudaEventCreate");
+  cudaEventRecord(e0, st);
+  cudaError_t le = launch_node_stats(g->d_off, g->d_h, n, g->d_hmax, g->d_hsum, d_maxdeg, g->num_sms, st);
+  cudaEventRecord(e1, st);
+  int maxdeg = 0;
+  cudaError_t ce = cudaMemcpyAsync(&maxdeg, d_maxdeg, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaError_t se = cudaStreamSynchronize(st);
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  FW_TRY(le, "node stats kernel");
+  FW_TRY(ce, "read max degree");
+  FW_TRY(se, "sync after preprocessing");
+  FW_TRY(cudaMemsetAsync(d_maxdeg, 0, sizeof(int), st), "cudaMemsetAsync");
+  g->max_degree = maxdeg;
+  g->preprocess_ms = ms;
+  *out = g;
+  return FW_OK;
+}
+
+extern "C" fw_status fw_graph_destroy(fw_graph* g) {
+  if (!g) return set_error(FW_ERR_ARG, "graph is NULL");
+  cudaDeviceSynchronize();
+  free_graph(g);
+  return FW_OK;
+}
+
+extern "C" fw_status fw_graph_info(const fw_graph* g, fw_graph_info_t* info) {
+  if (!g || !info) return set_error(FW_ERR_ARG, "NULL argument");
+  info->n = g->n;
+  info->e = g->e;
+  info->max_degree = g->max_degree;
+  info->has_weights = g->d_h != nullptr;
+  info->has_labels = g->d_lab != nullptr;
+  info->cost_ratio = g->ratio;
+  info->preprocess_ms = g->preprocess_ms;
+  info->device_bytes = g->bytes;
+  return FW_OK;
+}
+
+extern "C" fw_status fw_graph_node_stats(const fw_graph* g, float* hmax, float* hsum, void* stream) {
+  if (!g) return set_error(FW_ERR_ARG, "graph is NULL");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  if (hmax && g->n > 0) e = cudaMemcpyAsync(hmax, g->d_hmax, sizeof(float) * g->n, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && hsum && g->n > 0)
+    e = cudaMemcpyAsync(hsum, g->d_hsum, sizeof(float) * g->n, cudaMemcpyDeviceToDevice, st);
+  return e == cudaSuccess ? FW_OK : cuda_error(e, "copy node stats");
+}
+
+extern "C" fw_status fw_graph_set_cost_ratio(fw_graph* g, float ratio) {
+  if (!g || !(ratio > 0.0f) || !std::isfinite(ratio)) return set_error(FW_ERR_ARG, "bad ratio");
+  g->ratio = ratio;
+  return FW_OK;
+}
+
+extern "C" fw_status fw_walk(const fw_graph* g, const int32_t* starts, int32_t num_walkers, int32_t len, int32_t algo,
+                             const fw_params* params, uint64_t seed, int32_t* out, void* stream) {
+  if (!g) return set_error(FW_ERR_ARG, "graph is NULL");
+  if (num_walkers < 0 || len < 0) return set_error(FW_ERR_ARG, "negative size");
+  if (num_walkers > 0 && (!starts || !out)) return set_error(FW_ERR_ARG, "NULL starts/out");
+  Job J;
+  fw_status s = make_job(g, algo, params, seed, &J);
+  if (s != FW_OK) return s;
+  if (num_walkers == 0) return FW_OK;
+  J.kind = JOB_WALK;
+  J.starts = starts;
+  J.out = out;
+  J.num_walkers = num_walkers;
+  J.len = len;
+  J.gbase = 0;
+  const bool count = params && (params->flags & FW_FLAG_COUNTERS);
+  return with_qctr(g, &J, 1, num_walkers, count, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" fw_status fw_walk_host(fw_graph* g, const int32_t* starts, int32_t num_walkers, int32_t len, int32_t algo,
+                                  const fw_params* params, uint64_t seed, int32_t* out, void* stream) {
+  if (!g) return set_error(FW_ERR_ARG, "graph is NULL");
+  if (num_walkers < 0 || len < 0) return set_error(FW_ERR_ARG, "negative size");
+  if (num_walkers > 0 && (!starts || !out)) return set_error(FW_ERR_ARG, "NULL starts/out");
+  std::unique_lock<std::mutex> lk(g->stage_mu, std::try_to_lock);
+  if (!lk.owns_lock()) return set_error(FW_ERR_BUSY, "another fw_walk_host call is using this graph");
+  if (num_walkers == 0) return FW_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t nin = (size_t)num_walkers, nout = (size_t)num_walkers * ((size_t)len + 1);
+  if (g->stage_starts_cap < nin) {
+    cudaFree(g->d_stage_starts);
+    g->d_stage_starts = nullptr;
+    g->stage_starts_cap = 0;
+    cudaError_t e = cudaMalloc(&g->d_stage_starts, nin * sizeof(int32_t));
+    if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(staging starts)");
+    g->stage_starts_cap = nin;
+  }
+  if (g->stage_out_cap < nout) {
+    cudaFree(g->d_stage_out);
+    g->d_stage_out = nullptr;
+    g->stage_out_cap = 0;
+    cudaError_t e = cudaMalloc(&g->d_stage_out, nout * sizeof(int32_t));
+    if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(staging out)");
+    g->stage_out_cap = nout;
+  }
+  cudaError_t e = cudaMemcpyAsync(g->d_stage_starts, starts, nin * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_error(e, "copy starts");
+  fw_status s = fw_walk(g, g->d_stage_starts, num_walkers, len, algo, params, seed, g->d_stage_out, stream);
+  if (s != FW_OK) return s;
+  e = cudaMemcpyAsync(out, g->d_stage_out, nout * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_error(e, "copy out");
+  e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? FW_OK : cuda_error(e, "sync");
+}
+
+extern "C" fw_status fw_sample_hist(const fw_graph* g, int32_t v, int32_t v_prev, int32_t step, int32_t algo,
+                                    const fw_params* params, uint64_t seed, int64_t ndraws, uint64_t* counts,
+                                    void* stream) {
+  if (!g) return set_error(FW_ERR_ARG, "graph is NULL");
+  if (v < 0 || v >= g->n || v_prev < -1 || v_prev >= g->n || step < 0 || ndraws < 0 || !counts)
+    return set_error(FW_ERR_ARG, "bad state or sizes");
+  Job J;
+  fw_status s = make_job(g, algo, params, seed, &J);
+  if (s != FW_OK) return s;
+  J.kind = JOB_HIST;
+  J.hist = reinterpret_cast<unsigned long long*>(counts);
+  J.hv = v;
+  J.hprev = v_prev;
+  J.hstep = step;
+  const bool count = params && (params->flags & FW_FLAG_COUNTERS);
+  const uint32_t base0 = J.walker_base;
+  for (int64_t done = 0; done < ndraws;) {
+    const int64_t chunk = (ndraws - done) < (1LL << 30) ? (ndraws - done) : (1LL << 30);
+    J.walker_base = base0 + (uint32_t)done;
+    J.num_walkers = (int32_t)chunk;
+    J.len = 1;
+    s = with_qctr(g, &J, 1, chunk, count, reinterpret_cast<cudaStream_t>(stream));
+    if (s != FW_OK) return s;
+    done += chunk;
+  }
+  return FW_OK;
+}
+
+extern "C" fw_status fw_step_plan(const fw_graph* g, const int32_t* v, const int32_t* has_prev, int32_t count,
+                                  int32_t algo, const fw_params* params, float* bound, float* sum_hat, int32_t* mode,
+                                  void* stream) {
+  if (!g || count < 0 || (count > 0 && (!v || !has_prev || !bound || !sum_hat || !mode)))
+    return set_error(FW_ERR_ARG, "bad arguments");
+  Job J;
+  fw_status s = make_job(g, algo, params, 0, &J);
+  if (s != FW_OK) return s;
+  cudaError_t e = launch_step_plan(g, J, v, has_prev, count, bound, sum_hat, mode, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? FW_OK : cuda_error(e, "step plan kernel");
+}
+
+extern "C" fw_status fw_counters_read(const fw_graph* g, fw_counters* out, void* stream) {
+  if (!g || !out) return set_error(FW_ERR_ARG, "NULL argument");
+  static_assert(sizeof(fw_counters) == sizeof(DevCounters), "counter layout");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(out, g->d_cnt, sizeof(fw_counters), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? FW_OK : cuda_error(e, "read counters");
+}
+
+extern "C" fw_status fw_counters_reset(fw_graph* g, void* stream) {
+  if (!g) return set_error(FW_ERR_ARG, "graph is NULL");
+  cudaError_t e = cudaMemsetAsync(g->d_cnt, 0, sizeof(DevCounters), reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? FW_OK : cuda_error(e, "reset counters");
+}
+
+extern "C" fw_status fw_graph_check(fw_graph* g, void* stream) {
+  if (!g) return set_error(FW_ERR_ARG, "graph is NULL");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  unsigned bits = 0;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemcpy(&bits, g->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(g->d_err, 0, sizeof(unsigned));
+  if (e != cudaSuccess) return cuda_error(e, "check");
+  if (bits) return set_error(FW_ERR_DEVICE_CHECK, (bits & DEVERR_START) ? "a start node was outside [0, n)"
+                                                                       : "device check failed");
+  return FW_OK;
+}

@@ -1,0 +1,402 @@
+// fw_device.cuh -- device building blocks of the dynamic-random-walk engine.
+//
+// Every sampler here draws the next node of one walker-step from
+//   p(u) = w~(v,u) / sum_t w~(v,t),  w~ = w * h          [Sec. 2.1, Eq. (prob)]
+// with w from Eq. (node2vec), the MetaPath label rule, or w = 1 (weighted).
+//   * eRJS   [Sec. 3.3]: propose X uniform over N(v), accept iff U*B < w~(X),
+//            B = max(w) * h_MAX[v] >= max w~ (the proof in Sec. 3.3 shows the
+//            accepted value follows p for any such bound).
+//   * eRVS   [Sec. 3.2, Alg. 1, Eq. (jump)]: exponential keys
+//            K_i = ln(u_i) / w~_i (the log of u_i^(1/w~_i)), argmax wins;
+//            with jumps, a lane skips items until its cumulative weight passes
+//            ln(r) / K_ref and draws the crossing item's key conditioned on
+//            beating K_ref (A-ExpJ of Efraimidis & Spirakis, IPL 2006).
+//   * exact  [Sec. 2.2, ITS]: FP32 prefix in neighbour order, t = u * W_{d-1},
+//            first k with t < W_k (fallback: last k with w~_k > 0).
+// Random numbers come from Philox4x32-10 (Salmon et al., SC'11) keyed by the
+// walk seed with counter (walker id, hop, stream, draw); stream 0 is the exact
+// mode, 1 eRJS (draw = trial), 2 eRVS (draw = neighbour position).  No draw
+// depends on the lane, block or co-running walkers.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+namespace fw {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxJobs = 64;
+constexpr int kThreadRvsMaxDeg = 8;  // eRVS steps with d <= this run on one lane
+
+enum : int32_t { ALGO_WEIGHTED = 0, ALGO_NODE2VEC = 1, ALGO_METAPATH = 2 };
+enum : int32_t { MODE_AUTO = 0, MODE_RJS = 1, MODE_RVS = 2, MODE_EXACT = 3 };
+enum : int32_t { JOB_WALK = 0, JOB_HIST = 1 };
+enum : int32_t { PLAN_NONE = 0, PLAN_RJS = 1, PLAN_RVS_T = 2, PLAN_RVS_W = 3, PLAN_EXACT_T = 4, PLAN_EXACT_W = 5 };
+enum : uint32_t { DEVERR_START = 1u };
+
+struct DevGraph {
+  const int32_t* __restrict__ off;
+  const int32_t* __restrict__ col;
+  const float* __restrict__ h;     // nullptr: h = 1
+  const uint8_t* __restrict__ lab; // nullptr: no labels
+  const float* __restrict__ hmax;
+  const float* __restrict__ hsum;
+  int32_t n;
+};
+
+// One walk job (a batch is a table of these).  Walkers of all jobs form one
+// global index space: job j owns [gbase, gbase + num_walkers).
+struct Job {
+  const int32_t* starts;
+  int32_t* out;
+  unsigned long long* hist;
+  long long gbase;
+  int32_t num_walkers, len;
+  int32_t kind, algo, mode, flags;
+  int32_t rjs_cap, schema_len;
+  int32_t weighted;        // 1: use h, 0: h = 1
+  int32_t need_member;     // node2vec with 1/q != 1: membership test needed
+  float inv_p, inv_q;      // FP32 1/p, 1/q
+  float wmax1, wmean1;     // max / mean of w when a previous node exists
+  float wlo1, whi1;        // min / max of {1, 1/q}: squeeze bounds of a non-return neighbour
+  float ratio;             // r of Eq. (runtime)
+  uint32_t key0, key1, walker_base;
+  int32_t hv, hprev, hstep;  // JOB_HIST: the fixed state
+  uint8_t schema[16];
+};
+
+struct JobTable {
+  Job jobs[kMaxJobs];
+};
+
+// Counters kept by the counting build of the kernel (FW_FLAG_COUNTERS).
+struct DevCounters {
+  unsigned long long hops, rjs_steps, rvs_steps, exact_steps, handoffs, rjs_trials, rvs_items, rvs_keys,
+      probes, dead_ends, bytes;
+};
+
+struct LaneCounters {
+  uint32_t hops, rjs_steps, rvs_steps, exact_steps, handoffs, rjs_trials, rvs_items, rvs_keys, probes,
+      dead_ends;
+  unsigned long long bytes;
+  __device__ void zero() {
+    hops = rjs_steps = rvs_steps = exact_steps = handoffs = rjs_trials = rvs_items = rvs_keys = probes = dead_ends = 0;
+    bytes = 0;
+  }
+};
+
+// ---------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplies with the published multipliers; high halves are XORed
+// with the other counter words and the round key; the key advances by the
+// published Weyl increments between rounds.
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// [0,1) on a 2^-24 grid
+__device__ __forceinline__ float u01(uint32_t x) { return (float)(x >> 8) * 0x1.0p-24f; }
+// (0,1): odd multiples of 2^-24, never 0 or 1 (safe for log)
+__device__ __forceinline__ float u01_open(uint32_t x) { return (float)(((x >> 9) << 1) | 1u) * 0x1.0p-24f; }
+
+// ---------------------------------------------------------------- per-step context
+struct StepCtx {
+  int32_t v, vp;    // current and previous node (vp < 0: none)
+  int32_t s, d;     // row start and degree of v
+  int32_t ps, pe;   // row range of vp (node2vec membership)
+  int32_t step;     // hop index
+  uint32_t wid;     // random-stream walker id
+};
+
+// u in N(x) for the sorted row col[lo, hi)?  Binary search with early exit.
+__device__ __forceinline__ bool row_contains(const int32_t* __restrict__ col, int32_t lo, int32_t hi, int32_t u,
+                                             uint32_t& probes) {
+  int32_t len = hi - lo;
+  while (len > 0) {
+    const int32_t half = len >> 1;
+    const int32_t c = __ldg(col + lo + half);
+    ++probes;
+    if (c == u) return true;
+    if (c < u) {
+      lo += half + 1;
+      len -= half + 1;
+    } else {
+      len = half;
+    }
+  }
+  return false;
+}
+
+__device__ __forceinline__ float load_h(const DevGraph& g, const Job& J, int32_t i) {
+  return J.weighted ? __ldg(g.h + i) : 1.0f;
+}
+
+// Transition weight of the neighbour at CSR index i (= s + k) of step c.
+__device__ __forceinline__ float item_weight(const DevGraph& g, const Job& J, const StepCtx& c, int32_t i,
+                                             uint32_t& probes) {
+  const float hk = load_h(g, J, i);
+  if (J.algo == ALGO_NODE2VEC) {
+    if (c.vp < 0) return hk;
+    const int32_t u = __ldg(g.col + i);
+    float w;
+    if (u == c.vp) w = J.inv_p;                       // dist(v',u) = 0
+    else if (!J.need_member) w = 1.0f;                // 1/q == 1: distances 1 and 2 weigh the same
+    else w = row_contains(g.col, c.ps, c.pe, u, probes) ? 1.0f : J.inv_q;
+    return __fmul_rn(w, hk);
+  }
+  if (J.algo == ALGO_METAPATH) {
+    const uint8_t want = J.schema[c.step % J.schema_len];
+    return (__ldg(g.lab + i) == want) ? hk : 0.0f;    // w in {0, 1}
+  }
+  return hk;
+}
+
+// ---------------------------------------------------------------- plan
+// Bound (Sec. 3.3), sum estimate (Eq. sum_estimation) and choice (Eq. runtime).
+__device__ __forceinline__ int32_t plan_choice(const Job& J, float hm, float hs, bool has_prev, float& B,
+                                               float& S) {
+  const bool second = (J.algo == ALGO_NODE2VEC) && has_prev;
+  const float wmax = second ? J.wmax1 : ((J.algo == ALGO_METAPATH) ? 1.0f : 1.0f);
+  const float wmean = second ? J.wmean1 : ((J.algo == ALGO_METAPATH) ? 0.5f : 1.0f);
+  B = __fmul_rn(wmax, hm);
+  S = __fmul_rn(hs, wmean);
+  return (__fmul_rn(J.ratio, B) < S) ? MODE_RJS : MODE_RVS;
+}
+
+// ---------------------------------------------------------------- eRJS
+// Run trials [t0, t0+nt) of one walker-step; returns the accepted neighbour
+// position or -1.  Trial t uses Philox counter (wid, hop, 1, t): x.x (x.y on
+// Lemire's rare retry) proposes X uniformly in [0,d) by Lemire's
+// multiply-shift with rejection (ACM TOMACS 2019); x.z gives U in [0,1).
+template <bool COUNT>
+__device__ __forceinline__ int32_t rjs_trials(const DevGraph& g, const Job& J, const StepCtx& c, float B, int32_t t0,
+                                              int32_t nt, int32_t& node, LaneCounters& lc) {
+  const uint32_t d = (uint32_t)c.d;
+  const uint8_t want = (J.algo == ALGO_METAPATH) ? J.schema[c.step % J.schema_len] : 0;
+  uint32_t probes = 0;
+  int32_t found = -1;
+  for (int32_t t = t0; t < t0 + nt; ++t) {
+    const uint4 x = philox(make_uint4(c.wid, (uint32_t)c.step, 1u, (uint32_t)t), J.key0, J.key1);
+    if (COUNT) { lc.rjs_trials++; }
+    unsigned long long m = (unsigned long long)x.x * d;
+    uint32_t l = (uint32_t)m;
+    if (l < d) {
+      const uint32_t thr = (0u - d) % d;
+      if (l < thr) {
+        m = (unsigned long long)x.y * d;
+        l = (uint32_t)m;
+        if (l < thr) continue;  // this trial proposes nothing; trials stay i.i.d.
+      }
+    }
+    const int32_t k = (int32_t)(m >> 32);
+    const int32_t i = c.s + k;
+    const float UB = __fmul_rn(u01(x.z), B);
+    bool accept;
+    int32_t u = -1;
+    if (J.algo == ALGO_NODE2VEC && c.vp >= 0) {
+      u = __ldg(g.col + i);
+      const float hk = load_h(g, J, i);
+      if (COUNT) lc.bytes += J.weighted ? 64 : 32;
+      if (u == c.vp) {
+        accept = UB < __fmul_rn(J.inv_p, hk);
+      } else if (UB >= __fmul_rn(J.whi1, hk)) {
+        accept = false;                         // squeeze: above the largest possible weight
+      } else if (UB < __fmul_rn(J.wlo1, hk)) {
+        accept = true;                          // squeeze: below the smallest possible weight
+      } else {
+        uint32_t pb = 0;
+        const float w = row_contains(g.col, c.ps, c.pe, u, pb) ? 1.0f : J.inv_q;
+        probes += pb;
+        accept = UB < __fmul_rn(w, hk);
+      }
+    } else if (J.algo == ALGO_METAPATH) {
+      const uint8_t lb = __ldg(g.lab + i);
+      const float hk = load_h(g, J, i);
+      if (COUNT) lc.bytes += J.weighted ? 64 : 32;
+      accept = (lb == want) && (UB < hk);
+    } else {
+      const float hk = load_h(g, J, i);
+      if (COUNT) lc.bytes += J.weighted ? 32 : 0;
+      accept = UB < hk;
+    }
+    if (accept) {
+      found = k;
+      node = (u >= 0) ? u : __ldg(g.col + i);
+      if (COUNT && u < 0) lc.bytes += 32;
+      break;
+    }
+  }
+  if (COUNT) {
+    lc.probes += probes;
+    lc.bytes += 32ull * probes;
+  }
+  return found;
+}
+
+// ---------------------------------------------------------------- reductions
+__device__ __forceinline__ float warp_max(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(kFull, x, o));
+  return x;
+}
+
+// argmax of (key, index); equal keys -> larger index (Alg. 1 uses >=)
+__device__ __forceinline__ void warp_argmax(float& key, int32_t& idx) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ok = __shfl_xor_sync(kFull, key, o);
+    const int32_t oi = __shfl_xor_sync(kFull, idx, o);
+    if (ok > key || (ok == key && oi > idx)) {
+      key = ok;
+      idx = oi;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- eRVS
+// T lanes cooperate on one walker-step (T = 1: a single lane; T = 32: the
+// warp, all lanes converged with identical arguments).  Lane `lane` scans
+// positions lane, lane+T, ...  Phase 1 keys the first T positions; their
+// maximum is the reference K_ref from which every lane jumps over its own
+// subsequence; the final argmax over lanes picks the neighbour.  Counter
+// draws: (wid, hop, 2, k): x.x = phase-1 key, x.y = key at a crossing,
+// x.z = the lane's next jump threshold.  Returns position k or -1 (all
+// weights zero: dead end).
+template <int T, bool COUNT>
+__device__ __forceinline__ int32_t rvs_pick(const DevGraph& g, const Job& J, const StepCtx& c, int lane, bool jump,
+                                            LaneCounters& lc) {
+  uint32_t probes = 0;
+  float bestK = -CUDART_INF_F;
+  int32_t best = -1;
+  uint32_t xz = 0;
+  int32_t scanned = 0, keys = 0;
+  if (lane < c.d) {
+    const float wt = item_weight(g, J, c, c.s + lane, probes);
+    const uint4 x = philox(make_uint4(c.wid, (uint32_t)c.step, 2u, (uint32_t)lane), J.key0, J.key1);
+    xz = x.z;
+    ++scanned;
+    if (wt > 0.0f) {
+      bestK = logf(u01_open(x.x)) / wt;
+      best = lane;
+      ++keys;
+    }
+  }
+  if (c.d > T) {
+    float ref = bestK;
+    if (T > 1) ref = warp_max(bestK);
+    // remaining weight before the next crossing; K_ref = -inf: first positive item crosses
+    float rem = (ref == -CUDART_INF_F) ? 0.0f : ((ref < 0.0f) ? logf(u01_open(xz)) / ref : CUDART_INF_F);
+    for (int32_t k = lane + T; k < c.d; k += T) {
+      const float wt = item_weight(g, J, c, c.s + k, probes);
+      ++scanned;
+      if (!(wt > 0.0f)) continue;
+      if (!jump) {
+        const uint4 x = philox(make_uint4(c.wid, (uint32_t)c.step, 2u, (uint32_t)k), J.key0, J.key1);
+        const float K = logf(u01_open(x.x)) / wt;
+        ++keys;
+        if (K >= bestK) {
+          bestK = K;
+          best = k;
+        }
+      } else {
+        rem -= wt;
+        if (rem <= 0.0f) {
+          const uint4 x = philox(make_uint4(c.wid, (uint32_t)c.step, 2u, (uint32_t)k), J.key0, J.key1);
+          // key conditioned on beating ref: u' ~ U(exp(ref*wt), 1), K = ln(u') / wt
+          const float a = ref * wt;
+          const float K = log1pf(expm1f(a) * u01_open(x.y)) / wt;
+          ++keys;
+          bestK = K;
+          best = k;
+          ref = K;
+          rem = (ref < 0.0f) ? logf(u01_open(x.z)) / ref : CUDART_INF_F;
+        }
+      }
+    }
+  }
+  if (T > 1) warp_argmax(bestK, best);
+  if (COUNT) {
+    // per-lane shares; summed over the T lanes they give the step's totals
+    lc.rvs_items += scanned;
+    lc.rvs_keys += keys;
+    lc.probes += probes;
+    const int per = (J.algo == ALGO_NODE2VEC) ? (J.weighted ? 8 : 4) : (J.algo == ALGO_METAPATH ? (J.weighted ? 5 : 1) : (J.weighted ? 4 : 0));
+    lc.bytes += (unsigned long long)scanned * per + 32ull * probes;
+  }
+  return (bestK == -CUDART_INF_F) ? -1 : best;
+}
+
+// ---------------------------------------------------------------- exact
+// Exact inverse CDF with one uniform u: W_k accumulated with FP32 adds in
+// neighbour order (T = 32: the warp loads 32 weights at a time and replays
+// the additions in order through shuffles, so the sum is the serial one).
+template <int T, bool COUNT>
+__device__ __forceinline__ int32_t exact_pick(const DevGraph& g, const Job& J, const StepCtx& c, int lane, float u,
+                                              LaneCounters& lc) {
+  uint32_t probes = 0;
+  float total = 0.0f;
+  for (int32_t base = 0; base < c.d; base += T) {
+    const int32_t k = base + lane;
+    const float wt = (k < c.d) ? item_weight(g, J, c, c.s + k, probes) : 0.0f;
+    const int32_t cnt = min(T, c.d - base);
+    if (T == 1) {
+      total = __fadd_rn(total, wt);
+    } else {
+      for (int32_t j = 0; j < cnt; ++j) total = __fadd_rn(total, __shfl_sync(kFull, wt, j));
+    }
+  }
+  int32_t pick = -1;
+  if (total > 0.0f) {
+    const float t = __fmul_rn(u, total);
+    float run = 0.0f;
+    for (int32_t base = 0; base < c.d && pick < 0; base += T) {
+      const int32_t k = base + lane;
+      const float wt = (k < c.d) ? item_weight(g, J, c, c.s + k, probes) : 0.0f;
+      const int32_t cnt = min(T, c.d - base);
+      if (T == 1) {
+        run = __fadd_rn(run, wt);
+        if (t < run) pick = k;
+      } else {
+        float mine = 0.0f;
+        for (int32_t j = 0; j < cnt; ++j) {
+          run = __fadd_rn(run, __shfl_sync(kFull, wt, j));
+          if (j == lane) mine = run;
+        }
+        const unsigned hit = __ballot_sync(kFull, lane < cnt && t < mine);
+        if (hit) pick = base + __ffs(hit) - 1;
+      }
+    }
+    if (pick < 0) {  // rounding left t >= W_{d-1}: last positive weight
+      for (int32_t base = ((c.d - 1) / T) * T; base >= 0 && pick < 0; base -= T) {
+        const int32_t k = base + lane;
+        const float wt = (k < c.d) ? item_weight(g, J, c, c.s + k, probes) : 0.0f;
+        if (T == 1) {
+          if (wt > 0.0f) pick = k;
+        } else {
+          const unsigned hit = __ballot_sync(kFull, wt > 0.0f);
+          if (hit) pick = base + 31 - __clz(hit);
+        }
+      }
+    }
+  }
+  if (COUNT) {
+    lc.probes += probes;
+    const int per = (J.algo == ALGO_NODE2VEC) ? (J.weighted ? 8 : 4) : (J.algo == ALGO_METAPATH ? (J.weighted ? 5 : 1) : (J.weighted ? 4 : 0));
+    const int32_t mine = (lane < c.d) ? (c.d - lane + T - 1) / T : 0;
+    lc.bytes += 2ull * mine * per + 32ull * probes;
+  }
+  return pick;
+}
+
+}  // namespace fw

@@ -1,0 +1,65 @@
+// fw_internal.h -- host-side internals shared by the library's translation units.
+#pragma once
+
+#include <atomic>
+#include <cstdint>
+#include <mutex>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "fw_device.cuh"
+#include "../../include/flexiwalk.h"
+
+struct fw_graph {
+  int device = 0;
+  int num_sms = 0;
+  int32_t n = 0;
+  int64_t e = 0;
+  int32_t max_degree = 0;
+  int32_t* d_off = nullptr;
+  int32_t* d_col = nullptr;
+  float* d_h = nullptr;
+  uint8_t* d_lab = nullptr;
+  float* d_hmax = nullptr;
+  float* d_hsum = nullptr;
+  unsigned* d_err = nullptr;
+  fw::DevCounters* d_cnt = nullptr;
+  float ratio = 4.0f;
+  double preprocess_ms = 0.0;
+  size_t bytes = 0;
+  // staging of fw_walk_host
+  std::mutex stage_mu;
+  int32_t* d_stage_starts = nullptr;
+  size_t stage_starts_cap = 0;
+  int32_t* d_stage_out = nullptr;
+  size_t stage_out_cap = 0;
+};
+
+namespace fw {
+
+extern std::atomic<unsigned long long> g_launches;
+
+fw_status set_error(fw_status st, const std::string& msg);
+fw_status cuda_error(cudaError_t err, const char* what);
+
+DevGraph dev_graph(const fw_graph* g);
+
+// Fill a job from the public parameters (validates them).
+fw_status make_job(const fw_graph* g, int32_t algo, const fw_params* params, uint64_t seed, Job* job);
+
+// Launch the unified walk kernel over `njobs` jobs (total walkers `total`).
+// `qctr` is a zeroed device counter the launch may use as its walker queue.
+cudaError_t launch_walk(const fw_graph* g, const Job* jobs, int njobs, long long total, bool count,
+                        unsigned long long* qctr, cudaStream_t stream);
+
+cudaError_t launch_node_stats(const int32_t* off, const float* h, int32_t n, float* hmax, float* hsum, int* maxdeg,
+                              int num_sms, cudaStream_t stream);
+cudaError_t launch_check_offsets(const int32_t* off, int32_t n, int64_t e, unsigned* err, int num_sms,
+                                 cudaStream_t stream);
+cudaError_t launch_check_rows(const int32_t* off, const int32_t* col, const float* h, int32_t n, unsigned* err,
+                              int num_sms, cudaStream_t stream);
+cudaError_t launch_step_plan(const fw_graph* g, const Job& job, const int32_t* v, const int32_t* has_prev,
+                             int32_t count, float* bound, float* sum_hat, int32_t* mode, cudaStream_t stream);
+
+}  // namespace fw

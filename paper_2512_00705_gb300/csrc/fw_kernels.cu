@@ -1,0 +1,414 @@
+// fw_kernels.cu -- the walk kernel and the preprocessing / validation kernels.
+//
+// walk_kernel is one persistent kernel for every job kind and sampling mode:
+//   * query fetch   [Sec. 5.3]: lanes without a walker take the next global
+//                   walker indices with one warp-aggregated atomicAdd on a
+//                   queue counter; a batch of jobs is one concatenated index
+//                   space (job j owns [gbase_j, gbase_j + W_j)).
+//   * plan          [Sec. 3.3, Sec. 4.1]: per walker-step the bound B and the
+//                   sum estimate give the eRJS / eRVS choice (or a forced mode).
+//   * eRJS          [Sec. 3.3, Sec. 5.2]: one walker per lane; a fixed number
+//                   of trials per round, then the warp checks by ballot which
+//                   lanes need a reservoir step (chosen eRVS, or trial cap hit).
+//   * eRVS / exact  [Sec. 3.2, Sec. 5.2]: steps of degree <= a small threshold
+//                   run on their own lane; larger ones are handed to the whole
+//                   warp one at a time (shuffle of the walker's state), and
+//                   the result goes back to the owning lane.
+//   * update        [Sec. 4.2, update()]: prev <- cur, cur <- next, row write.
+// All loops are bounded (trial cap, degree, walk length); there are no waits.
+#include "fw_internal.h"
+
+namespace fw {
+
+constexpr int kBlock = 256;
+constexpr int kRjsBatch = 2;           // eRJS trials per round before the warp ballot
+constexpr int kThreadExactMaxDeg = 16; // exact steps with d <= this run on one lane
+
+template <int NJ>
+struct JobTableN {
+  Job jobs[NJ];
+};
+
+template <int NJ, bool COUNT>
+__global__ void __launch_bounds__(kBlock) walk_kernel(DevGraph g, JobTableN<NJ> tab, int njobs, long long total,
+                                                      unsigned long long* __restrict__ qctr,
+                                                      unsigned* __restrict__ err, DevCounters* __restrict__ cnt) {
+  __shared__ Job sj[NJ];
+  {
+    const int words = njobs * (int)(sizeof(Job) / 4);
+    const int* src = reinterpret_cast<const int*>(tab.jobs);
+    int* dst = reinterpret_cast<int*>(sj);
+    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  LaneCounters lc;
+  lc.zero();
+
+  int32_t job = 0, widx = -1, cur = 0, prev = -1, step = 0, end = 0;
+  int32_t plan = PLAN_NONE, trials = 0, pick = -2, node = -1;
+  float B = 0.0f;
+  StepCtx c;
+  c.v = c.vp = c.s = c.d = c.ps = c.pe = c.step = 0;
+  c.wid = 0;
+  bool exhausted = false;  // warp-uniform
+
+  while (true) {
+    // ------------------------------------------------------------ fetch
+    const bool need = widx < 0;
+    const unsigned nm = __ballot_sync(kFull, need);
+    if (nm != 0u && !exhausted) {
+      const int leader = __ffs(nm) - 1;
+      const unsigned cntw = __popc(nm);
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(qctr, (unsigned long long)cntw);
+      base = __shfl_sync(kFull, base, leader);
+      if (base + cntw >= (unsigned long long)total) exhausted = true;
+      if (need) {
+        const long long gi = (long long)base + __popc(nm & lt_mask);
+        if (gi < total) {
+          int j = 0;
+          while (j + 1 < njobs && sj[j + 1].gbase <= gi) ++j;
+          const Job& J = sj[j];
+          job = j;
+          widx = (int32_t)(gi - J.gbase);
+          if (J.kind == JOB_WALK) {
+            const int32_t st = __ldg(J.starts + widx);
+            int32_t* row = J.out + (long long)widx * (J.len + 1);
+            if (st < 0 || st >= g.n) {
+              atomicOr(err, DEVERR_START);
+              for (int r = 0; r <= J.len; ++r) row[r] = -1;
+              widx = -1;
+            } else {
+              row[0] = st;
+              cur = st;
+              prev = -1;
+              step = 0;
+              end = J.len;
+              if (end == 0) widx = -1;
+            }
+          } else {
+            cur = J.hv;
+            prev = J.hprev;
+            step = J.hstep;
+            end = J.hstep + 1;
+          }
+          plan = PLAN_NONE;
+          pick = -2;
+        }
+      }
+    }
+    if (!__any_sync(kFull, widx >= 0)) {
+      if (exhausted) break;
+      continue;
+    }
+
+    const Job& J = sj[job];
+    // ------------------------------------------------------------ plan
+    if (widx >= 0 && plan == PLAN_NONE) {
+      c.v = cur;
+      c.vp = prev;
+      c.step = step;
+      c.wid = J.walker_base + (uint32_t)widx;
+      c.s = __ldg(g.off + cur);
+      c.d = __ldg(g.off + cur + 1) - c.s;
+      trials = 0;
+      pick = -2;
+      if (COUNT) lc.bytes += 8;
+      if (c.d == 0) {
+        pick = -1;
+        plan = PLAN_RJS;
+      } else {
+        if (J.algo == ALGO_NODE2VEC && prev >= 0 && J.need_member) {
+          c.ps = __ldg(g.off + prev);
+          c.pe = __ldg(g.off + prev + 1);
+        } else {
+          c.ps = c.pe = 0;
+        }
+        int32_t m = J.mode;
+        if (m == MODE_EXACT) {
+          plan = (c.d <= kThreadExactMaxDeg) ? PLAN_EXACT_T : PLAN_EXACT_W;
+        } else {
+          float hm, hs, S;
+          if (J.weighted) {
+            hm = __ldg(g.hmax + cur);
+            hs = __ldg(g.hsum + cur);
+            if (COUNT) lc.bytes += 8;
+          } else {
+            hm = 1.0f;
+            hs = (float)c.d;
+          }
+          const int32_t choice = plan_choice(J, hm, hs, prev >= 0, B, S);
+          if (m == MODE_AUTO) m = choice;
+          plan = (m == MODE_RJS) ? PLAN_RJS : ((c.d <= kThreadRvsMaxDeg) ? PLAN_RVS_T : PLAN_RVS_W);
+        }
+      }
+    }
+    // ------------------------------------------------------------ eRJS trials
+    if (widx >= 0 && plan == PLAN_RJS && pick == -2) {
+      int32_t nd = -1;
+      const int32_t k = rjs_trials<COUNT>(g, J, c, B, trials, kRjsBatch, nd, lc);
+      if (k >= 0) {
+        pick = k;
+        node = nd;
+        if (COUNT) lc.rjs_steps++;
+      } else {
+        trials += kRjsBatch;
+        if (trials >= J.rjs_cap) {
+          plan = (c.d <= kThreadRvsMaxDeg) ? PLAN_RVS_T : PLAN_RVS_W;
+          if (COUNT) lc.handoffs++;
+        }
+      }
+    }
+    // ------------------------------------------------------------ single-lane eRVS / exact
+    if (widx >= 0 && pick == -2 && plan == PLAN_RVS_T) {
+      pick = rvs_pick<1, COUNT>(g, J, c, 0, !(J.flags & FW_FLAG_RVS_NOJUMP), lc);
+      if (pick >= 0) node = __ldg(g.col + c.s + pick);
+      if (COUNT) lc.rvs_steps++;
+    }
+    if (widx >= 0 && pick == -2 && plan == PLAN_EXACT_T) {
+      const float u = u01(philox(make_uint4(c.wid, (uint32_t)c.step, 0u, 0u), J.key0, J.key1).x);
+      pick = exact_pick<1, COUNT>(g, J, c, 0, u, lc);
+      if (pick >= 0) node = __ldg(g.col + c.s + pick);
+      if (COUNT) lc.exact_steps++;
+    }
+    // ------------------------------------------------------------ warp hand-off
+    unsigned wm = __ballot_sync(kFull, widx >= 0 && pick == -2 && (plan == PLAN_RVS_W || plan == PLAN_EXACT_W));
+    while (wm != 0u) {
+      const int src = __ffs(wm) - 1;
+      wm &= wm - 1u;
+      StepCtx w;
+      w.v = __shfl_sync(kFull, c.v, src);
+      w.vp = __shfl_sync(kFull, c.vp, src);
+      w.s = __shfl_sync(kFull, c.s, src);
+      w.d = __shfl_sync(kFull, c.d, src);
+      w.ps = __shfl_sync(kFull, c.ps, src);
+      w.pe = __shfl_sync(kFull, c.pe, src);
+      w.step = __shfl_sync(kFull, c.step, src);
+      w.wid = __shfl_sync(kFull, c.wid, src);
+      const int jb = __shfl_sync(kFull, job, src);
+      const int pl = __shfl_sync(kFull, plan, src);
+      const Job& JW = sj[jb];
+      int32_t k;
+      if (pl == PLAN_EXACT_W) {
+        const float u = u01(philox(make_uint4(w.wid, (uint32_t)w.step, 0u, 0u), JW.key0, JW.key1).x);
+        k = exact_pick<32, COUNT>(g, JW, w, lane, u, lc);
+      } else {
+        k = rvs_pick<32, COUNT>(g, JW, w, lane, !(JW.flags & FW_FLAG_RVS_NOJUMP), lc);
+      }
+      if (lane == src) {
+        pick = k;
+        if (k >= 0) node = __ldg(g.col + w.s + k);
+        if (COUNT) {
+          if (pl == PLAN_EXACT_W) lc.exact_steps++;
+          else lc.rvs_steps++;
+        }
+      }
+    }
+    // ------------------------------------------------------------ commit
+    if (widx >= 0 && pick != -2) {
+      if (J.kind == JOB_WALK) {
+        int32_t* row = J.out + (long long)widx * (J.len + 1);
+        if (pick >= 0) {
+          row[step + 1] = node;
+        } else {
+          for (int r = step + 1; r <= J.len; ++r) row[r] = -1;
+        }
+      } else if (pick >= 0) {
+        atomicAdd(J.hist + pick, 1ull);
+      }
+      if (pick >= 0) {
+        prev = cur;
+        cur = node;
+        ++step;
+        if (COUNT) {
+          lc.hops++;
+          lc.bytes += 4;
+        }
+        if (step >= end) widx = -1;
+      } else {
+        if (COUNT) lc.dead_ends++;
+        widx = -1;
+      }
+      plan = PLAN_NONE;
+      pick = -2;
+    }
+  }
+
+  if (COUNT) {
+    const unsigned long long v[11] = {lc.hops,     lc.rjs_steps, lc.rvs_steps, lc.exact_steps,
+                                      lc.handoffs, lc.rjs_trials, lc.rvs_items, lc.rvs_keys,
+                                      lc.probes,   lc.dead_ends, lc.bytes};
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(cnt);
+#pragma unroll
+    for (int f = 0; f < 11; ++f) {
+      unsigned long long x = v[f];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+      if (lane == 0 && x) atomicAdd(dst + f, x);
+    }
+  }
+}
+
+template <int NJ, bool COUNT>
+static cudaError_t launch_walk_t(const fw_graph* g, const Job* jobs, int njobs, long long total,
+                                 unsigned long long* qctr, cudaStream_t stream) {
+  static int blocks_per_sm = 0;
+  if (blocks_per_sm == 0) {
+    int b = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, walk_kernel<NJ, COUNT>, kBlock, 0);
+    if (e != cudaSuccess) return e;
+    blocks_per_sm = b > 0 ? b : 1;
+  }
+  JobTableN<NJ> tab;
+  for (int i = 0; i < njobs; ++i) tab.jobs[i] = jobs[i];
+  const long long want = (total + kBlock - 1) / kBlock;
+  const long long cap = (long long)g->num_sms * blocks_per_sm;
+  const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
+  walk_kernel<NJ, COUNT><<<grid, kBlock, 0, stream>>>(dev_graph(g), tab, njobs, total, qctr, g->d_err, g->d_cnt);
+  g_launches.fetch_add(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_walk(const fw_graph* g, const Job* jobs, int njobs, long long total, bool count,
+                        unsigned long long* qctr, cudaStream_t stream) {
+  if (njobs == 1) {
+    return count ? launch_walk_t<1, true>(g, jobs, njobs, total, qctr, stream)
+                 : launch_walk_t<1, false>(g, jobs, njobs, total, qctr, stream);
+  }
+  return count ? launch_walk_t<kMaxJobs, true>(g, jobs, njobs, total, qctr, stream)
+               : launch_walk_t<kMaxJobs, false>(g, jobs, njobs, total, qctr, stream);
+}
+
+// ---------------------------------------------------------------- preprocessing
+// h_MAX[v] and h_SUM[v]: one warp per node, lanes stride over the row
+// (coalesced), then a shuffle-tree max and sum (Sec. 4.2 preprocess()).
+__global__ void node_stats_kernel(const int32_t* __restrict__ off, const float* __restrict__ h, int32_t n,
+                                  float* __restrict__ hmax, float* __restrict__ hsum, int* __restrict__ maxdeg) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  int localmax = 0;
+  for (long long v = warp; v < n; v += nwarps) {
+    const int32_t s = off[v], e = off[v + 1];
+    float m = 0.0f, sum = 0.0f;
+    if (h) {
+      for (int32_t i = s + lane; i < e; i += 32) {
+        const float x = h[i];
+        m = fmaxf(m, x);
+        sum += x;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
+        sum += __shfl_xor_sync(kFull, sum, o);
+      }
+    } else {
+      m = (e > s) ? 1.0f : 0.0f;
+      sum = (float)(e - s);
+    }
+    if (lane == 0) {
+      hmax[v] = m;
+      hsum[v] = sum;
+    }
+    localmax = max(localmax, e - s);
+  }
+  if (lane == 0 && localmax > 0) atomicMax(maxdeg, localmax);
+}
+
+cudaError_t launch_node_stats(const int32_t* off, const float* h, int32_t n, float* hmax, float* hsum, int* maxdeg,
+                              int num_sms, cudaStream_t stream) {
+  if (n == 0) return cudaSuccess;
+  const long long want = ((long long)n * 32 + 255) / 256;
+  const int grid = (int)(want < (long long)num_sms * 8 ? want : (long long)num_sms * 8);
+  node_stats_kernel<<<grid, 256, 0, stream>>>(off, h, n, hmax, hsum, maxdeg);
+  g_launches.fetch_add(1);
+  return cudaGetLastError();
+}
+
+// CSR validation of device-resident input: bit 1 = offsets, bit 2 = column
+// range, bit 4 = row order, bit 8 = weights.
+__global__ void check_offsets_kernel(const int32_t* __restrict__ off, int32_t n, int64_t e, unsigned* err) {
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += (long long)gridDim.x * blockDim.x) {
+    const int32_t o = off[v];
+    bool bad = (v == 0 && o != 0) || (v == n && (int64_t)o != e) || (v < n && off[v + 1] < o) || o < 0;
+    if (bad) atomicOr(err, 1u);
+  }
+}
+
+__global__ void check_rows_kernel(const int32_t* __restrict__ off, const int32_t* __restrict__ col,
+                                  const float* __restrict__ h, int32_t n, unsigned* err) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long v = warp; v < n; v += nwarps) {
+    const int32_t s = off[v], e = off[v + 1];
+    unsigned bits = 0;
+    for (int32_t i = s + lane; i < e; i += 32) {
+      const int32_t c = col[i];
+      if (c < 0 || c >= n) bits |= 2u;
+      if (i + 1 < e && col[i + 1] <= c) bits |= 4u;
+      if (h) {
+        const float x = h[i];
+        if (!(x > 0.0f) || !isfinite(x)) bits |= 8u;
+      }
+    }
+    if (bits) atomicOr(err, bits);
+  }
+}
+
+cudaError_t launch_check_offsets(const int32_t* off, int32_t n, int64_t e, unsigned* err, int num_sms,
+                                 cudaStream_t stream) {
+  const long long want = ((long long)n + 1 + 255) / 256;
+  const int grid = (int)(want < (long long)num_sms * 8 ? want : (long long)num_sms * 8);
+  check_offsets_kernel<<<grid > 0 ? grid : 1, 256, 0, stream>>>(off, n, e, err);
+  g_launches.fetch_add(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_rows(const int32_t* off, const int32_t* col, const float* h, int32_t n, unsigned* err,
+                              int num_sms, cudaStream_t stream) {
+  if (n == 0) return cudaSuccess;
+  const long long want = ((long long)n * 32 + 255) / 256;
+  const int grid = (int)(want < (long long)num_sms * 8 ? want : (long long)num_sms * 8);
+  check_rows_kernel<<<grid, 256, 0, stream>>>(off, col, h, n, err);
+  g_launches.fetch_add(1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- plan test hook
+__global__ void step_plan_kernel(DevGraph g, Job J, const int32_t* __restrict__ v, const int32_t* __restrict__ hp,
+                                 int32_t count, float* __restrict__ bound, float* __restrict__ sum_hat,
+                                 int32_t* __restrict__ mode) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int32_t x = v[i];
+  if (x < 0 || x >= g.n) {
+    mode[i] = -1;
+    return;
+  }
+  float hm, hs, B, S;
+  if (J.weighted) {
+    hm = g.hmax[x];
+    hs = g.hsum[x];
+  } else {
+    hm = 1.0f;
+    hs = (float)(g.off[x + 1] - g.off[x]);
+  }
+  mode[i] = plan_choice(J, hm, hs, hp[i] != 0, B, S);
+  bound[i] = B;
+  sum_hat[i] = S;
+}
+
+cudaError_t launch_step_plan(const fw_graph* g, const Job& job, const int32_t* v, const int32_t* has_prev,
+                             int32_t count, float* bound, float* sum_hat, int32_t* mode, cudaStream_t stream) {
+  if (count <= 0) return cudaSuccess;
+  step_plan_kernel<<<(count + 255) / 256, 256, 0, stream>>>(dev_graph(g), job, v, has_prev, count, bound, sum_hat,
+                                                            mode);
+  g_launches.fetch_add(1);
+  return cudaGetLastError();
+}
+
+}  // namespace fw

@@ -1,0 +1,302 @@
+"""Thin Python binding of the C ABI in include/flexiwalk.h (argument
+marshalling only).  Every step of the walk runs in the CUDA library; torch
+supplies device memory and streams.  If the library is missing the calls
+raise -- there is no fallback.
+
+Functions carry the C names (fw_graph_create, fw_walk, ...); `Graph` wraps a
+handle for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _build
+
+ALGO = {"weighted": 0, "node2vec": 1, "metapath": 2}
+MODE = {"auto": 0, "rjs": 1, "rvs": 2, "exact": 3}
+FLAG_RVS_NOJUMP, FLAG_COUNTERS, FLAG_UNWEIGHTED = 1, 2, 4
+PTR_HOST, PTR_DEVICE = 0, 1
+STATUS = {0: "FW_OK", -1: "FW_ERR_ARG", -2: "FW_ERR_CSR", -3: "FW_ERR_OOM", -4: "FW_ERR_CUDA",
+          -5: "FW_ERR_TIMEOUT", -6: "FW_ERR_DEVICE_CHECK", -7: "FW_ERR_BUSY", -8: "FW_ERR_UNSUPPORTED"}
+
+
+class FlexiWalkError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class fw_params(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_float), ("q", ctypes.c_float), ("schema", ctypes.c_uint8 * 16),
+                ("schema_len", ctypes.c_int32), ("mode", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("cost_ratio", ctypes.c_float), ("rjs_cap", ctypes.c_int32), ("walker_base", ctypes.c_uint32)]
+
+
+class fw_graph_info_t(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("e", ctypes.c_int64), ("max_degree", ctypes.c_int32),
+                ("has_weights", ctypes.c_int32), ("has_labels", ctypes.c_int32), ("cost_ratio", ctypes.c_float),
+                ("preprocess_ms", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
+
+
+COUNTER_FIELDS = ["hops", "rjs_steps", "rvs_steps", "exact_steps", "handoffs", "rjs_trials", "rvs_items",
+                  "rvs_keys", "probes", "dead_ends", "bytes"]
+
+
+class fw_counters(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in COUNTER_FIELDS]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """Load libflexiwalk.so (built by __graft_entry__.build()).  Raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError(f"CUDA library not built: {_build.LIB} missing (run __graft_entry__.build())")
+            L = ctypes.CDLL(_build.LIB)
+            vp, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+            P = ctypes.POINTER
+            sig = {
+                "fw_params_default": (None, [P(fw_params)]),
+                "fw_graph_create": (ctypes.c_int, [vp, vp, vp, vp, i32, i64, i32, vp, P(vp)]),
+                "fw_graph_destroy": (ctypes.c_int, [vp]),
+                "fw_graph_info": (ctypes.c_int, [vp, P(fw_graph_info_t)]),
+                "fw_graph_node_stats": (ctypes.c_int, [vp, vp, vp, vp]),
+                "fw_graph_set_cost_ratio": (ctypes.c_int, [vp, ctypes.c_float]),
+                "fw_walk": (ctypes.c_int, [vp, vp, i32, i32, i32, P(fw_params), u64, vp, vp]),
+                "fw_walk_host": (ctypes.c_int, [vp, vp, i32, i32, i32, P(fw_params), u64, vp, vp]),
+                "fw_sample_hist": (ctypes.c_int, [vp, i32, i32, i32, i32, P(fw_params), u64, i64, vp, vp]),
+                "fw_step_plan": (ctypes.c_int, [vp, vp, vp, i32, i32, P(fw_params), vp, vp, vp, vp]),
+                "fw_counters_read": (ctypes.c_int, [vp, P(fw_counters), vp]),
+                "fw_counters_reset": (ctypes.c_int, [vp, vp]),
+                "fw_graph_check": (ctypes.c_int, [vp, vp]),
+                "fw_launch_count": (ctypes.c_uint64, []),
+                "fw_last_error": (ctypes.c_char_p, []),
+                "fw_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise FlexiWalkError(status, lib().fw_last_error().decode(errors="replace"))
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_params(p: float = 1.0, q: float = 1.0, schema: Optional[Sequence[int]] = None, mode="auto", flags: int = 0,
+                cost_ratio: float = 0.0, rjs_cap: int = 0, walker_base: int = 0) -> fw_params:
+    prm = fw_params()
+    lib().fw_params_default(ctypes.byref(prm))
+    prm.p, prm.q = float(p), float(q)
+    if schema is not None:
+        s = list(schema)
+        if not 1 <= len(s) <= 16:
+            raise ValueError("schema length must be 1..16")
+        for i, x in enumerate(s):
+            prm.schema[i] = int(x)
+        prm.schema_len = len(s)
+    prm.mode = MODE[mode] if isinstance(mode, str) else int(mode)
+    prm.flags = int(flags)
+    prm.cost_ratio = float(cost_ratio)
+    prm.rjs_cap = int(rjs_cap)
+    prm.walker_base = int(walker_base)
+    return prm
+
+
+def _ptr(a) -> Optional[int]:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def fw_graph_create(offsets, cols, weights=None, labels=None, stream=None) -> int:
+    """Arrays may be numpy (host) or torch CUDA tensors (device); all of one kind."""
+    is_np = isinstance(offsets, np.ndarray)
+    if is_np:
+        offsets = np.ascontiguousarray(offsets, dtype=np.int32)
+        cols = np.ascontiguousarray(cols, dtype=np.int32)
+        weights = None if weights is None else np.ascontiguousarray(weights, dtype=np.float32)
+        labels = None if labels is None else np.ascontiguousarray(labels, dtype=np.uint8)
+        n, e = offsets.shape[0] - 1, cols.shape[0]
+        kind = PTR_HOST
+    else:
+        n, e = offsets.numel() - 1, cols.numel()
+        kind = PTR_DEVICE
+    h = ctypes.c_void_p()
+    _check(lib().fw_graph_create(_ptr(offsets), _ptr(cols), _ptr(weights), _ptr(labels), n, e, kind,
+                                 _stream_ptr(stream) if kind == PTR_DEVICE or stream is not None else None,
+                                 ctypes.byref(h)))
+    return h.value
+
+
+def fw_graph_destroy(handle: int):
+    _check(lib().fw_graph_destroy(handle))
+
+
+def fw_graph_info(handle: int) -> dict:
+    info = fw_graph_info_t()
+    _check(lib().fw_graph_info(handle, ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in fw_graph_info_t._fields_}
+
+
+def fw_walk(handle: int, starts, length: int, algo, params: fw_params, seed: int, out, stream=None):
+    """starts: CUDA int32 [W]; out: CUDA int32 [W, length+1]."""
+    _check(lib().fw_walk(handle, _ptr(starts), starts.numel(), length, ALGO.get(algo, algo), ctypes.byref(params),
+                         seed, _ptr(out), _stream_ptr(stream)))
+
+
+def fw_walk_host(handle: int, starts: np.ndarray, length: int, algo, params: fw_params, seed: int, out: np.ndarray,
+                 stream=None):
+    """starts / out are host buffers (numpy or pinned torch CPU tensors)."""
+    n = starts.shape[0] if isinstance(starts, np.ndarray) else starts.numel()
+    _check(lib().fw_walk_host(handle, _ptr(starts), n, length, ALGO.get(algo, algo), ctypes.byref(params), seed,
+                              _ptr(out), _stream_ptr(stream)))
+
+
+def fw_sample_hist(handle: int, v: int, v_prev: int, step: int, algo, params: fw_params, seed: int, ndraws: int,
+                   counts, stream=None):
+    _check(lib().fw_sample_hist(handle, v, v_prev, step, ALGO.get(algo, algo), ctypes.byref(params), seed, ndraws,
+                                _ptr(counts), _stream_ptr(stream)))
+
+
+def fw_step_plan(handle: int, v, has_prev, algo, params: fw_params, bound, sum_hat, mode, stream=None):
+    _check(lib().fw_step_plan(handle, _ptr(v), _ptr(has_prev), v.numel(), ALGO.get(algo, algo), ctypes.byref(params),
+                              _ptr(bound), _ptr(sum_hat), _ptr(mode), _stream_ptr(stream)))
+
+
+def fw_graph_node_stats(handle: int, hmax, hsum, stream=None):
+    _check(lib().fw_graph_node_stats(handle, _ptr(hmax), _ptr(hsum), _stream_ptr(stream)))
+
+
+def fw_graph_set_cost_ratio(handle: int, ratio: float):
+    _check(lib().fw_graph_set_cost_ratio(handle, float(ratio)))
+
+
+def fw_counters_read(handle: int, stream=None) -> dict:
+    c = fw_counters()
+    _check(lib().fw_counters_read(handle, ctypes.byref(c), _stream_ptr(stream)))
+    return {f: int(getattr(c, f)) for f in COUNTER_FIELDS}
+
+
+def fw_counters_reset(handle: int, stream=None):
+    _check(lib().fw_counters_reset(handle, _stream_ptr(stream)))
+
+
+def fw_graph_check(handle: int, stream=None):
+    _check(lib().fw_graph_check(handle, _stream_ptr(stream)))
+
+
+def fw_launch_count() -> int:
+    return int(lib().fw_launch_count())
+
+
+class Graph:
+    """A device-resident graph: CSR int32 offsets / cols, optional FP32
+    property weights h and uint8 labels."""
+
+    def __init__(self, csr=None, *, offsets=None, cols=None, weights=None, labels=None, stream=None):
+        if csr is not None:
+            offsets, cols = csr.offsets, csr.cols
+            weights, labels = getattr(csr, "h", None), getattr(csr, "labels", None)
+        self._off = np.asarray(offsets) if isinstance(offsets, np.ndarray) else offsets.cpu().numpy()
+        self.handle = fw_graph_create(offsets, cols, weights, labels, stream)
+        self.info = fw_graph_info(self.handle)
+        self.n, self.e = self.info["n"], self.info["e"]
+
+    def close(self):
+        if self.handle:
+            fw_graph_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def walk(self, starts, length: int, algo="node2vec", *, p=1.0, q=1.0, schema=None, mode="auto", seed=42,
+             flags=0, cost_ratio=0.0, rjs_cap=0, walker_base=0, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((starts.numel(), length + 1), dtype=torch.int32, device=starts.device)
+        prm = make_params(p, q, schema, mode, flags, cost_ratio, rjs_cap, walker_base)
+        fw_walk(self.handle, starts, length, algo, prm, seed, out, stream)
+        return out
+
+    def walk_host(self, starts, length: int, algo="node2vec", *, p=1.0, q=1.0, schema=None, mode="auto", seed=42,
+                  flags=0, cost_ratio=0.0, rjs_cap=0, walker_base=0, out=None, stream=None):
+        if out is None:
+            out = np.empty((len(starts), length + 1), dtype=np.int32)
+        prm = make_params(p, q, schema, mode, flags, cost_ratio, rjs_cap, walker_base)
+        fw_walk_host(self.handle, starts, length, algo, prm, seed, out, stream)
+        return out
+
+    def sample_hist(self, v: int, v_prev: int, step: int, algo="node2vec", ndraws: int = 1_000_000, *, p=1.0, q=1.0,
+                    schema=None, mode="auto", seed=42, flags=0, cost_ratio=0.0, rjs_cap=0, walker_base=0,
+                    stream=None):
+        import torch
+        d = self.degree(v)
+        counts = torch.zeros(max(d, 1), dtype=torch.int64, device="cuda")
+        prm = make_params(p, q, schema, mode, flags, cost_ratio, rjs_cap, walker_base)
+        fw_sample_hist(self.handle, v, v_prev, step, algo, prm, seed, ndraws, counts, stream)
+        return counts[:d]
+
+    def step_plan(self, v, has_prev, algo="node2vec", *, p=1.0, q=1.0, schema=None, cost_ratio=0.0, stream=None):
+        import torch
+        bound = torch.empty(v.numel(), dtype=torch.float32, device=v.device)
+        s = torch.empty_like(bound)
+        m = torch.empty(v.numel(), dtype=torch.int32, device=v.device)
+        prm = make_params(p, q, schema, "auto", 0, cost_ratio)
+        fw_step_plan(self.handle, v, has_prev, algo, prm, bound, s, m, stream)
+        return m, bound, s
+
+    def node_stats(self, stream=None):
+        import torch
+        hmax = torch.empty(self.n, dtype=torch.float32, device="cuda")
+        hsum = torch.empty_like(hmax)
+        fw_graph_node_stats(self.handle, hmax, hsum, stream)
+        return hmax, hsum
+
+    def counters(self, stream=None) -> dict:
+        return fw_counters_read(self.handle, stream)
+
+    def reset_counters(self, stream=None):
+        fw_counters_reset(self.handle, stream)
+
+    def check(self, stream=None):
+        fw_graph_check(self.handle, stream)
+
+    def set_cost_ratio(self, r: float):
+        fw_graph_set_cost_ratio(self.handle, r)
+        self.info = fw_graph_info(self.handle)
+
+    def degree(self, v: int) -> int:
+        return int(self._off[v + 1] - self._off[v])

@@ -1,0 +1,108 @@
+"""The C ABI library loads and exports every entry point declared in
+include/flexiwalk.h; host-side argument and CSR validation (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2512_00705_gb300 import _build
+from paper_2512_00705_gb300 import flexiwalk as fw
+from paper_2512_00705_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    _build.build()
+    yield
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "flexiwalk.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fw_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ["fw_graph_create", "fw_graph_destroy", "fw_walk", "fw_walk_host", "fw_sample_hist",
+                 "fw_step_plan", "fw_last_error"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    out = subprocess.run(["nm", "-D", "--defined-only", _build.LIB], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (fw_\w+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    L = ctypes.CDLL(_build.LIB)
+    for n in declared_functions():
+        assert hasattr(L, n)
+
+
+def test_params_default():
+    p = fw.make_params()
+    assert (p.p, p.q, p.mode, p.flags, p.schema_len, p.rjs_cap, p.walker_base) == (1.0, 1.0, 0, 0, 0, 0, 0)
+
+
+def _create_status(offsets, cols, h=None, labels=None):
+    L = fw.lib()
+    out = ctypes.c_void_p()
+    offsets = np.ascontiguousarray(offsets, np.int32)
+    cols = np.ascontiguousarray(cols, np.int32)
+    hp = None if h is None else np.ascontiguousarray(h, np.float32)
+    return L.fw_graph_create(offsets.ctypes.data, cols.ctypes.data, None if hp is None else hp.ctypes.data, None,
+                             offsets.shape[0] - 1, cols.shape[0], fw.PTR_HOST, None, ctypes.byref(out)), out
+
+
+@pytest.mark.parametrize("offsets,cols,h,why", [
+    ([1, 2, 3], [1, 0], None, "offsets[0]"),
+    ([0, 2, 1, 3], [1, 2, 0], None, "monotone"),
+    ([0, 1, 2], [1, 0, 0], None, "offsets[n]"),
+    ([0, 2, 3, 4], [2, 1, 0, 0], None, "increasing"),
+    ([0, 2, 3, 4], [1, 1, 0, 0], None, "increasing"),
+    ([0, 1, 2], [1, 5], None, "range"),
+    ([0, 1, 2], [1, -1], None, "range"),
+    ([0, 1, 2], [1, 0], [1.0, 0.0], "weight"),
+    ([0, 1, 2], [1, 0], [1.0, float("nan")], "weight"),
+    ([0, 1, 2], [1, 0], [float("inf"), 1.0], "weight"),
+    ([0, 1, 2], [1, 0], [-2.0, 1.0], "weight"),
+])
+def test_host_csr_validation(offsets, cols, h, why):
+    st, out = _create_status(offsets, cols, h)
+    assert st == -2, (st, fw.lib().fw_last_error())
+    assert out.value is None
+    assert why in fw.lib().fw_last_error().decode()
+
+
+def test_argument_errors_without_device():
+    L = fw.lib()
+    out = ctypes.c_void_p()
+    assert L.fw_graph_create(None, None, None, None, 3, 0, fw.PTR_HOST, None, ctypes.byref(out)) == -1
+    assert L.fw_graph_create(None, None, None, None, -1, 0, fw.PTR_HOST, None, ctypes.byref(out)) == -1
+    o = np.array([0, 0], np.int32)
+    assert L.fw_graph_create(o.ctypes.data, o.ctypes.data, None, None, 1, 0, 7, None, ctypes.byref(out)) == -1
+    prm = fw.make_params()
+    assert L.fw_walk(None, None, 0, 1, 0, ctypes.byref(prm), 1, None, None) == -1
+    assert L.fw_graph_destroy(None) == -1
+    assert L.fw_status_string(-2) == b"FW_ERR_CSR"
+
+
+def test_valid_host_graph_passes_validation():
+    """A valid CSR gets past host validation; without a GPU the next step
+    (device selection) fails with FW_ERR_CUDA, never FW_ERR_CSR."""
+    g = synth.workload_graph("small")
+    st, _ = _create_status(g.offsets, g.cols, g.h)
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except Exception:
+        has_gpu = False
+    if has_gpu:
+        assert st == 0
+    else:
+        assert st == -4

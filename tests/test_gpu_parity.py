@@ -1,0 +1,268 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Exact mode must equal the oracle's walks bit for bit; the fast modes (eRJS,
+eRVS with and without jumps, cost-model auto) must reproduce the oracle's
+exact per-step distributions (chi-square p > 1e-4 and TV < 2e-3 at >= 4e6
+draws for non-hub states) and keep the walk invariants."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_00705_gb300 import flexiwalk as fw
+from paper_2512_00705_gb300 import synth
+from statcheck import chisq_pvalue, tv_distance
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ALGOS = [("node2vec", 2.0, 0.5, None), ("node2vec", 0.25, 4.0, None), ("node2vec", 4.0, 0.25, None),
+         ("node2vec", 1.0, 1.0, None), ("metapath", 1.0, 1.0, [0, 1, 2, 3, 4]), ("weighted", 1.0, 1.0, None)]
+
+
+@pytest.fixture(scope="module")
+def small():
+    g = synth.workload_graph("small")
+    G = fw.Graph(g)
+    yield g, G
+    G.close()
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+# ------------------------------------------------------------ exact mode
+@pytest.mark.parametrize("algo,p,q,schema", ALGOS)
+def test_exact_mode_bit_identical_small(small, algo, p, q, schema):
+    g, G = small
+    starts = np.arange(g.n, dtype=np.int32)
+    out = G.walk(_cuda(starts), 20, algo, p=p, q=q, schema=schema, mode="exact", seed=42).cpu().numpy()
+    ref, hops = oracle.walk(g, starts, 20, algo, p, q, schema, seed=42)
+    assert np.array_equal(out, ref), f"{(out != ref).any(axis=1).sum()} rows differ"
+    G.check()
+
+
+@pytest.mark.parametrize("W,L,base", [(4093, 20, 0), (31, 7, 1000), (1, 1, 5), (257, 0, 0), (0, 5, 0)])
+def test_exact_mode_ragged_sizes(small, W, L, base):
+    g, G = small
+    starts = synth.random_starts(g.n, W, seed=W + 1)
+    if W == 0:
+        out = torch.empty((0, L + 1), dtype=torch.int32, device="cuda")
+        G.walk(_cuda(starts), L, "node2vec", p=2.0, q=0.5, mode="exact", out=out)
+        return
+    out = G.walk(_cuda(starts), L, "node2vec", p=2.0, q=0.5, mode="exact", seed=7, walker_base=base).cpu().numpy()
+    ref, _ = oracle.walk(g, starts, L, "node2vec", 2.0, 0.5, seed=7, walker_base=base)
+    assert np.array_equal(out, ref)
+
+
+def test_exact_mode_unweighted(small):
+    g, G = small
+    starts = np.arange(g.n, dtype=np.int32)
+    out = G.walk(_cuda(starts), 15, "node2vec", p=1.0, q=0.5, mode="exact", seed=3,
+                 flags=fw.FLAG_UNWEIGHTED).cpu().numpy()
+    ref, _ = oracle.walk(synth.Csr(g.offsets, g.cols), starts, 15, "node2vec", 1.0, 0.5, seed=3)
+    assert np.array_equal(out, ref)
+    # a graph created without weights gives the same walks
+    G2 = fw.Graph(offsets=g.offsets, cols=g.cols)
+    out2 = G2.walk(_cuda(starts), 15, "node2vec", p=1.0, q=0.5, mode="exact", seed=3).cpu().numpy()
+    G2.close()
+    assert np.array_equal(out2, ref)
+
+
+def test_graph_from_device_arrays(small):
+    g, _ = small
+    G = fw.Graph(offsets=_cuda(g.offsets), cols=_cuda(g.cols), weights=_cuda(g.h), labels=_cuda(g.labels))
+    starts = np.arange(0, g.n, 3, dtype=np.int32)
+    out = G.walk(_cuda(starts), 10, "metapath", schema=[0, 1, 2, 3, 4], mode="exact", seed=9).cpu().numpy()
+    ref, _ = oracle.walk(g, starts, 10, "metapath", schema=[0, 1, 2, 3, 4], seed=9)
+    assert np.array_equal(out, ref)
+    G.close()
+
+
+def test_device_csr_validation():
+    g = synth.from_edges(4, [(0, 1), (1, 2), (2, 3)])
+    cols = g.cols.copy()
+    cols[1], cols[2] = cols[2], cols[1]  # row 1 no longer sorted
+    with pytest.raises(fw.FlexiWalkError) as e:
+        fw.Graph(offsets=_cuda(g.offsets), cols=_cuda(cols))
+    assert e.value.status == -2
+    bad_w = np.ones(g.e, np.float32)
+    bad_w[0] = 0.0
+    with pytest.raises(fw.FlexiWalkError) as e:
+        fw.Graph(offsets=_cuda(g.offsets), cols=_cuda(g.cols), weights=_cuda(bad_w))
+    assert e.value.status == -2
+
+
+def test_bad_start_is_reported(small):
+    g, G = small
+    starts = np.array([0, g.n + 5, 1], dtype=np.int32)
+    out = G.walk(_cuda(starts), 4, "weighted", mode="exact").cpu().numpy()
+    assert np.all(out[1] == -1)
+    with pytest.raises(fw.FlexiWalkError) as e:
+        G.check()
+    assert e.value.status == -6
+    G.check()  # cleared
+
+
+def test_walk_host_matches_device(small):
+    g, G = small
+    starts = np.arange(g.n, dtype=np.int32)
+    a = G.walk_host(starts, 12, "node2vec", p=2.0, q=0.5, mode="auto", seed=11)
+    b = G.walk(_cuda(starts), 12, "node2vec", p=2.0, q=0.5, mode="auto", seed=11).cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+# ------------------------------------------------------------ preprocessing / plan
+def test_node_stats_parity(small):
+    g, G = small
+    hmax, hsum = G.node_stats()
+    rmax, rsum = oracle.node_stats(g)
+    assert np.array_equal(hmax.cpu().numpy(), rmax)
+    np.testing.assert_allclose(hsum.cpu().numpy(), rsum, rtol=2e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("algo,p,q", [("node2vec", 2.0, 0.5), ("node2vec", 0.25, 4.0), ("metapath", 1, 1),
+                                      ("weighted", 1, 1)])
+def test_step_plan_parity(small, algo, p, q):
+    g, G = small
+    v = np.arange(g.n, dtype=np.int32)
+    hp = (v % 2).astype(np.int32)
+    r = 4.0
+    m, B, S = G.step_plan(_cuda(v), _cuda(hp), algo, p=p, q=q, schema=[0, 1, 2, 3, 4], cost_ratio=r)
+    m, B, S = m.cpu().numpy(), B.cpu().numpy(), S.cpu().numpy()
+    rmax, rsum = oracle.node_stats(g)
+    ghmax, ghsum = [t.cpu().numpy() for t in G.node_stats()]
+    for i in range(g.n):
+        om, oB, oS = oracle.step_plan(float(ghmax[i]), float(ghsum[i]), hp[i], algo, p, q, r)
+        assert B[i] == oB and S[i] == oS and m[i] == om, i
+        # and against the oracle's own fp64 sums, away from the decision boundary
+        om2, oB2, oS2 = oracle.step_plan(float(rmax[i]), float(rsum[i]), hp[i], algo, p, q, r)
+        assert oB2 == B[i]
+        if abs(r * oB2 - oS2) > 1e-4 * max(1.0, oS2):
+            assert om2 == m[i]
+
+
+# ------------------------------------------------------------ fast-mode distributions
+def _states(g):
+    """(v, v_prev, step) states covering degrees 1, 2, ~4, ~32, ~300, max."""
+    deg = g.degrees()
+    out = []
+    for target in [1, 2, 4, 32, 300, int(deg.max())]:
+        v = int(np.argmin(np.abs(deg - target) + (deg == 0) * 10**9))
+        nb = g.cols[g.offsets[v]:g.offsets[v + 1]]
+        hub_prev = int(nb[np.argmax(deg[nb])])
+        out.append((v, -1, 0))
+        out.append((v, hub_prev, 1))
+    return out
+
+
+@pytest.mark.parametrize("mode,flags", [("rjs", 0), ("rvs", 0), ("rvs", fw.FLAG_RVS_NOJUMP), ("auto", 0)])
+@pytest.mark.parametrize("algo,p,q,schema", [("node2vec", 2.0, 0.5, None), ("node2vec", 0.25, 4.0, None),
+                                             ("metapath", 1.0, 1.0, [0, 1, 2, 3, 4]), ("weighted", 1.0, 1.0, None)])
+def test_fast_mode_distributions(small, mode, flags, algo, p, q, schema):
+    g, G = small
+    ndraws = 4_000_000
+    for (v, vp, step) in _states(g):
+        probs = oracle.transition_probs(g, v, vp, step, algo, p, q, schema)
+        counts = G.sample_hist(v, vp, step, algo, ndraws, p=p, q=q, schema=schema, mode=mode, flags=flags,
+                               seed=1234 + v).cpu().numpy()
+        if probs.sum() == 0:
+            assert counts.sum() == 0
+            continue
+        assert counts.sum() == ndraws
+        pv = chisq_pvalue(counts, probs)
+        tv = tv_distance(counts, probs)
+        assert pv > 1e-4, (v, vp, step, pv)
+        assert tv < 2e-3, (v, vp, step, tv)
+
+
+def test_worked_example_distribution():
+    """Fig. 2: weights {3,2,4,1} -> {0.3,0.2,0.4,0.1} for every mode."""
+    g = synth.from_edges(5, [(0, 1), (0, 2), (0, 3), (0, 4)], h=[3.0, 2.0, 4.0, 1.0])
+    G = fw.Graph(g)
+    for mode in ["rjs", "rvs", "auto", "exact"]:
+        counts = G.sample_hist(0, -1, 0, "weighted", 4_000_000, mode=mode, seed=99).cpu().numpy()
+        f = counts / counts.sum()
+        assert np.abs(f - [0.3, 0.2, 0.4, 0.1]).max() < 1.5e-3, (mode, f)
+    G.close()
+
+
+def test_rjs_bound_invariance(small):
+    """Sec. 3.3: the accepted distribution does not depend on the bound; a
+    10x looser cost ratio only changes the choice, and a trial cap of 1
+    (almost every step handed to eRVS) keeps the distribution too."""
+    g, G = small
+    deg = g.degrees()
+    v = int(np.argmax(deg))
+    probs = oracle.transition_probs(g, v, -1, 0, "weighted")
+    for cap in [1, 2, 1000]:
+        counts = G.sample_hist(v, -1, 0, "weighted", 4_000_000, mode="rjs", rjs_cap=cap, seed=5).cpu().numpy()
+        assert chisq_pvalue(counts, probs) > 1e-4
+        assert tv_distance(counts, probs) < 2e-3
+
+
+def test_dead_end_states(small):
+    g, G = small
+    deg = g.degrees()
+    iso = int(np.argmax(deg == 0))
+    for mode in ["rjs", "rvs", "auto", "exact"]:
+        c = G.sample_hist(iso, -1, 0, "weighted", 1000, mode=mode).cpu().numpy()
+        assert c.sum() == 0
+    # metapath state with no matching label: every mode ends the walk
+    for v in range(g.n):
+        if 0 < deg[v] <= 6 and oracle.transition_probs(g, v, -1, 0, "metapath", schema=[4]).sum() == 0:
+            for mode in ["rjs", "rvs", "auto", "exact"]:
+                c = G.sample_hist(v, -1, 0, "metapath", 5000, schema=[4], mode=mode).cpu().numpy()
+                assert c.sum() == 0
+            break
+
+
+# ------------------------------------------------------------ invariants / determinism
+def _invariants(g, starts, out, algo, schema=None, check_dead=True, p=1.0, q=1.0):
+    L = out.shape[1] - 1
+    assert np.array_equal(out[:, 0], starts)
+    n = np.int64(g.n)
+    keys = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.offsets)) * n + g.cols
+    alive = out[:, 1:] >= 0
+    # -1 only as a suffix
+    assert np.all(alive[:, :-1] | ~alive[:, 1:])
+    v = out[:, :-1].astype(np.int64)
+    u = out[:, 1:].astype(np.int64)
+    q_ = (v * n + u)[alive]
+    pos = np.searchsorted(keys, q_)
+    assert np.all(pos < len(keys)) and np.all(keys[np.minimum(pos, len(keys) - 1)] == q_), "hop is not an edge"
+    if algo == "metapath":
+        lab = g.labels[pos]
+        hop = np.broadcast_to(np.arange(L), alive.shape)[alive]
+        assert np.all(lab == np.asarray(schema)[hop % len(schema)])
+    if check_dead:
+        dead = np.nonzero(~alive.all(axis=1))[0][:200]
+        for r in dead:
+            j = int(np.argmin(alive[r]))
+            prev = int(out[r, j - 1]) if j >= 1 else -1
+            assert oracle.transition_probs(g, int(out[r, j]), prev, j, algo, p, q, schema).sum() == 0
+
+
+@pytest.mark.parametrize("algo,p,q,schema", ALGOS)
+@pytest.mark.parametrize("mode", ["auto", "rjs", "rvs"])
+def test_fast_walk_invariants_small(small, algo, p, q, schema, mode):
+    g, G = small
+    starts = np.arange(g.n, dtype=np.int32)
+    out = G.walk(_cuda(starts), 20, algo, p=p, q=q, schema=schema, mode=mode, seed=5).cpu().numpy()
+    _invariants(g, starts, out, algo, schema, p=p, q=q)
+    again = G.walk(_cuda(starts), 20, algo, p=p, q=q, schema=schema, mode=mode, seed=5).cpu().numpy()
+    assert np.array_equal(out, again), "fast modes must be deterministic for a fixed seed"
+
+
+def test_counters(small):
+    g, G = small
+    starts = np.arange(g.n, dtype=np.int32)
+    G.reset_counters()
+    out = G.walk(_cuda(starts), 20, "node2vec", p=2.0, q=0.5, flags=fw.FLAG_COUNTERS, seed=5)
+    c = G.counters()
+    o = out.cpu().numpy()
+    assert c["hops"] == int((o[:, 1:] >= 0).sum())
+    assert c["rjs_steps"] + c["rvs_steps"] == c["hops"]
+    assert c["dead_ends"] == int((o[:, -1] < 0).sum())
+    plain = G.walk(_cuda(starts), 20, "node2vec", p=2.0, q=0.5, seed=5).cpu().numpy()
+    assert np.array_equal(o, plain), "counting build must not change the walks"
