@@ -57,6 +57,7 @@ fw_status make_job(const fw_graph* g, int32_t algo, const fw_params* params, uin
   job->mode = P.mode;
   job->flags = P.flags;
   job->rjs_cap = P.rjs_cap > 0 ? P.rjs_cap : 64;
+  job->fixed_cap = P.rjs_cap > 0 ? 1 : 0;
   job->schema_len = algo == ALGO_METAPATH ? P.schema_len : 1;
   std::memcpy(job->schema, P.schema, 16);
   job->weighted = (g->d_h != nullptr && !(P.flags & FW_FLAG_UNWEIGHTED)) ? 1 : 0;
@@ -69,6 +70,7 @@ fw_status make_job(const fw_graph* g, int32_t algo, const fw_params* params, uin
     job->wlo1 = std::fmin(1.0f, iq);
     job->whi1 = std::fmax(1.0f, iq);
     job->need_member = (iq != 1.0f) ? 1 : 0;
+    job->second_order = (ip != 1.0f || iq != 1.0f) ? 1 : 0;
   } else {
     job->inv_p = job->inv_q = 1.0f;
     job->wmax1 = job->wlo1 = job->whi1 = 1.0f;

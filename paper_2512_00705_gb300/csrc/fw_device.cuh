@@ -56,7 +56,9 @@ struct Job {
   int32_t kind, algo, mode, flags;
   int32_t rjs_cap, schema_len;
   int32_t weighted;        // 1: use h, 0: h = 1
+  int32_t second_order;    // node2vec with (1/p, 1/q) != (1, 1): w depends on v'
   int32_t need_member;     // node2vec with 1/q != 1: membership test needed
+  int32_t fixed_cap;       // 1: rjs_cap is a fixed trial cap; 0: cap = max(rjs_cap, ceil(d / ratio))
   float inv_p, inv_q;      // FP32 1/p, 1/q
   float wmax1, wmean1;     // max / mean of w when a previous node exists
   float wlo1, whi1;        // min / max of {1, 1/q}: squeeze bounds of a non-return neighbour
@@ -147,7 +149,7 @@ __device__ __forceinline__ float item_weight(const DevGraph& g, const Job& J, co
                                              uint32_t& probes) {
   const float hk = load_h(g, J, i);
   if (J.algo == ALGO_NODE2VEC) {
-    if (c.vp < 0) return hk;
+    if (c.vp < 0 || !J.second_order) return hk;
     const int32_t u = __ldg(g.col + i);
     float w;
     if (u == c.vp) w = J.inv_p;                       // dist(v',u) = 0
@@ -204,7 +206,7 @@ __device__ __forceinline__ int32_t rjs_trials(const DevGraph& g, const Job& J, c
     const float UB = __fmul_rn(u01(x.z), B);
     bool accept;
     int32_t u = -1;
-    if (J.algo == ALGO_NODE2VEC && c.vp >= 0) {
+    if (J.algo == ALGO_NODE2VEC && c.vp >= 0 && J.second_order) {
       u = __ldg(g.col + i);
       const float hk = load_h(g, J, i);
       if (COUNT) lc.bytes += J.weighted ? 64 : 32;

@@ -24,6 +24,14 @@ constexpr int kBlock = 256;
 constexpr int kRjsBatch = 2;           // eRJS trials per round before the warp ballot
 constexpr int kThreadExactMaxDeg = 16; // exact steps with d <= this run on one lane
 
+// row[from, to) = -1, with 16-byte stores where the row is aligned
+__device__ __forceinline__ void fill_minus_one(int32_t* row, int32_t from, int32_t to) {
+  int32_t r = from;
+  while (r < to && ((reinterpret_cast<uintptr_t>(row + r) & 15u) != 0)) row[r++] = -1;
+  for (; r + 4 <= to; r += 4) *reinterpret_cast<int4*>(row + r) = make_int4(-1, -1, -1, -1);
+  for (; r < to; ++r) row[r] = -1;
+}
+
 template <int NJ>
 struct JobTableN {
   Job jobs[NJ];
@@ -79,7 +87,7 @@ __global__ void __launch_bounds__(kBlock) walk_kernel(DevGraph g, JobTableN<NJ> 
             int32_t* row = J.out + (long long)widx * (J.len + 1);
             if (st < 0 || st >= g.n) {
               atomicOr(err, DEVERR_START);
-              for (int r = 0; r <= J.len; ++r) row[r] = -1;
+              fill_minus_one(row, 0, J.len + 1);
               widx = -1;
             } else {
               row[0] = st;
@@ -156,7 +164,10 @@ __global__ void __launch_bounds__(kBlock) walk_kernel(DevGraph g, JobTableN<NJ> 
         if (COUNT) lc.rjs_steps++;
       } else {
         trials += kRjsBatch;
-        if (trials >= J.rjs_cap) {
+        // trial budget: the cap, or (default) as many trials as the eRVS scan
+        // they stand in for would cost under the cost model, d / r
+        const int32_t cap = J.fixed_cap ? J.rjs_cap : max(J.rjs_cap, (int32_t)ceilf((float)c.d / J.ratio));
+        if (trials >= cap) {
           plan = (c.d <= kThreadRvsMaxDeg) ? PLAN_RVS_T : PLAN_RVS_W;
           if (COUNT) lc.handoffs++;
         }
@@ -214,7 +225,7 @@ __global__ void __launch_bounds__(kBlock) walk_kernel(DevGraph g, JobTableN<NJ> 
         if (pick >= 0) {
           row[step + 1] = node;
         } else {
-          for (int r = step + 1; r <= J.len; ++r) row[r] = -1;
+          fill_minus_one(row, step + 1, J.len + 1);
         }
       } else if (pick >= 0) {
         atomicAdd(J.hist + pick, 1ull);
