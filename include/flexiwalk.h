@@ -210,6 +210,27 @@ fw_status fw_counters_reset(fw_graph* graph, void* stream);
  * of earlier asynchronous calls on this graph: FW_OK or FW_ERR_DEVICE_CHECK. */
 fw_status fw_graph_check(fw_graph* graph, void* stream);
 
+/*
+ * fw_walk_host without any device allocation (the paper has no counterpart;
+ * this is a deployment convenience).  For callers that cannot allocate
+ * device memory when they walk: hosts whose own pool or arena owns the GPU
+ * memory, real-time services that forbid allocation after start-up, and
+ * plug-ins running under a fixed memory budget.  Same arguments, layout and
+ * result as fw_walk_host (host starts / host out, returns when out is
+ * filled); the device scratch it needs -- the staged starts, the staged
+ * rows and the walk queue counter -- lives in one fixed 16 MiB array inside
+ * the library, which every GPU that loads the library holds until exit.
+ * Limit: starts (4*num_walkers bytes, rounded up to 256) plus rows
+ * (4*num_walkers*(len+1) bytes) must fit in 16 MiB - 256 bytes, else
+ * FW_ERR_ARG; larger requests belong to fw_walk_host.  Calls share the
+ * array and serialise on a process-wide lock (FW_ERR_BUSY if one is in
+ * progress); calls that overlap on the GPU race on it.  The first call on a
+ * device looks up the array's device address; make it before any stream
+ * capture.  The current device must be the graph's device.
+ */
+fw_status fw_walk_host_noalloc(const fw_graph* graph, const int32_t* starts, int32_t num_walkers, int32_t len,
+                               int32_t algo, const fw_params* params, uint64_t seed, int32_t* out, void* stream);
+
 /* Number of kernel launches this library has issued (process-wide). */
 uint64_t fw_launch_count(void);
 
