@@ -32,6 +32,7 @@ DevGraph dev_graph(const fw_graph* g) {
   d.lab = g->d_lab;
   d.hmax = g->d_hmax;
   d.hsum = g->d_hsum;
+  d.nrec = g->d_nrec;
   d.n = g->n;
   return d;
 }
@@ -157,6 +158,7 @@ static void free_graph(fw_graph* g) {
   cudaFree(g->d_lab);
   cudaFree(g->d_hmax);
   cudaFree(g->d_hsum);
+  cudaFree(g->d_nrec);
   cudaFree(g->d_err);
   cudaFree(g->d_cnt);
   cudaFree(g->d_stage_starts);
@@ -201,10 +203,11 @@ extern "C" fw_status fw_graph_create(const int32_t* offsets, const int32_t* cols
   if (labels) FW_TRY(cudaMalloc(&g->d_lab, eb), "cudaMalloc(labels)");
   FW_TRY(cudaMalloc(&g->d_hmax, sizeof(float) * ((size_t)n + 1)), "cudaMalloc(h_MAX)");
   FW_TRY(cudaMalloc(&g->d_hsum, sizeof(float) * ((size_t)n + 1)), "cudaMalloc(h_SUM)");
+  FW_TRY(cudaMalloc(&g->d_nrec, sizeof(int4) * ((size_t)n + 1)), "cudaMalloc(node records)");
   FW_TRY(cudaMalloc(&g->d_err, 64), "cudaMalloc(error word)");
   FW_TRY(cudaMalloc(&g->d_cnt, sizeof(DevCounters)), "cudaMalloc(counters)");
   g->bytes = sizeof(int32_t) * ((size_t)n + 1) + eb * (4 + (weights ? 4 : 0) + (labels ? 1 : 0)) +
-             2 * sizeof(float) * ((size_t)n + 1) + 64 + sizeof(DevCounters);
+             2 * sizeof(float) * ((size_t)n + 1) + sizeof(int4) * ((size_t)n + 1) + 64 + sizeof(DevCounters);
   FW_TRY(cudaMemsetAsync(g->d_err, 0, 64, st), "cudaMemsetAsync");
   FW_TRY(cudaMemsetAsync(g->d_cnt, 0, sizeof(DevCounters), st), "cudaMemsetAsync");
   FW_TRY(cudaMemcpyAsync(g->d_off, offsets, sizeof(int32_t) * ((size_t)n + 1), kind, st), "copy offsets");
@@ -235,7 +238,7 @@ extern "C" fw_status fw_graph_create(const int32_t* offsets, const int32_t* cols
   FW_TRY(cudaEventCreate(&e0), "cudaEventCreate");
   FW_TRY(cudaEventCreate(&e1), "cudaEventCreate");
   cudaEventRecord(e0, st);
-  cudaError_t le = launch_node_stats(g->d_off, g->d_h, n, g->d_hmax, g->d_hsum, d_maxdeg, g->num_sms, st);
+  cudaError_t le = launch_node_stats(g->d_off, g->d_h, n, g->d_hmax, g->d_hsum, g->d_nrec, d_maxdeg, g->num_sms, st);
   cudaEventRecord(e1, st);
   int maxdeg = 0;
   cudaError_t ce = cudaMemcpyAsync(&maxdeg, d_maxdeg, sizeof(int), cudaMemcpyDeviceToHost, st);

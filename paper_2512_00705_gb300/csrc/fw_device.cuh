@@ -42,6 +42,7 @@ struct DevGraph {
   const uint8_t* __restrict__ lab; // nullptr: no labels
   const float* __restrict__ hmax;
   const float* __restrict__ hsum;
+  const int4* __restrict__ nrec;   // per node {row start, degree, h_MAX bits, h_SUM bits}: one sector per plan
   int32_t n;
 };
 
@@ -121,9 +122,32 @@ struct StepCtx {
   uint32_t wid;     // random-stream walker id
 };
 
-// u in N(x) for the sorted row col[lo, hi)?  Binary search with early exit.
+// u in N(x) for the sorted row col[lo, hi)?  All ids lie in [0, n).  A few
+// interpolation probes first (position guessed from u's place between the
+// bracketing values; a row of a graph with randomly permuted ids is close
+// to a uniform sample of [0, n), so the guess lands within a few entries),
+// then bisection of what is left.  Exits early on a hit.  At most
+// kInterpProbes + ceil(log2(d + 1)) probes.
+constexpr int kInterpProbes = 4;
 __device__ __forceinline__ bool row_contains(const int32_t* __restrict__ col, int32_t lo, int32_t hi, int32_t u,
-                                             uint32_t& probes) {
+                                             int32_t n, uint32_t& probes) {
+  float va = -1.0f, vb = (float)n;  // every id in [lo, hi) lies strictly between va and vb
+#pragma unroll 1
+  for (int it = 0; it < kInterpProbes && hi - lo > 8; ++it) {
+    const float f = ((float)u - va) / (vb - va);
+    int32_t g = lo + (int32_t)(f * (float)(hi - lo));
+    g = min(max(g, lo), hi - 1);
+    const int32_t c = __ldg(col + g);
+    ++probes;
+    if (c == u) return true;
+    if (c < u) {
+      lo = g + 1;
+      va = (float)c;
+    } else {
+      hi = g;
+      vb = (float)c;
+    }
+  }
   int32_t len = hi - lo;
   while (len > 0) {
     const int32_t half = len >> 1;
@@ -154,7 +178,7 @@ __device__ __forceinline__ float item_weight(const DevGraph& g, const Job& J, co
     float w;
     if (u == c.vp) w = J.inv_p;                       // dist(v',u) = 0
     else if (!J.need_member) w = 1.0f;                // 1/q == 1: distances 1 and 2 weigh the same
-    else w = row_contains(g.col, c.ps, c.pe, u, probes) ? 1.0f : J.inv_q;
+    else w = row_contains(g.col, c.ps, c.pe, u, g.n, probes) ? 1.0f : J.inv_q;
     return __fmul_rn(w, hk);
   }
   if (J.algo == ALGO_METAPATH) {
@@ -218,7 +242,7 @@ __device__ __forceinline__ int32_t rjs_trials(const DevGraph& g, const Job& J, c
         accept = true;                          // squeeze: below the smallest possible weight
       } else {
         uint32_t pb = 0;
-        const float w = row_contains(g.col, c.ps, c.pe, u, pb) ? 1.0f : J.inv_q;
+        const float w = row_contains(g.col, c.ps, c.pe, u, g.n, pb) ? 1.0f : J.inv_q;
         probes += pb;
         accept = UB < __fmul_rn(w, hk);
       }

@@ -23,6 +23,7 @@ struct fw_graph {
   uint8_t* d_lab = nullptr;
   float* d_hmax = nullptr;
   float* d_hsum = nullptr;
+  int4* d_nrec = nullptr;
   unsigned* d_err = nullptr;
   fw::DevCounters* d_cnt = nullptr;
   float ratio = 4.0f;
@@ -53,8 +54,8 @@ fw_status make_job(const fw_graph* g, int32_t algo, const fw_params* params, uin
 cudaError_t launch_walk(const fw_graph* g, const Job* jobs, int njobs, long long total, bool count,
                         unsigned long long* qctr, cudaStream_t stream);
 
-cudaError_t launch_node_stats(const int32_t* off, const float* h, int32_t n, float* hmax, float* hsum, int* maxdeg,
-                              int num_sms, cudaStream_t stream);
+cudaError_t launch_node_stats(const int32_t* off, const float* h, int32_t n, float* hmax, float* hsum, int4* nrec,
+                              int* maxdeg, int num_sms, cudaStream_t stream);
 cudaError_t launch_check_offsets(const int32_t* off, int32_t n, int64_t e, unsigned* err, int num_sms,
                                  cudaStream_t stream);
 cudaError_t launch_check_rows(const int32_t* off, const int32_t* col, const float* h, int32_t n, unsigned* err,

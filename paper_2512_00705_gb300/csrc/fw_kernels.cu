@@ -24,12 +24,56 @@ constexpr int kBlock = 256;
 constexpr int kRjsBatch = 2;           // eRJS trials per round before the warp ballot
 constexpr int kThreadExactMaxDeg = 16; // exact steps with d <= this run on one lane
 
-// row[from, to) = -1, with 16-byte stores where the row is aligned
-__device__ __forceinline__ void fill_minus_one(int32_t* row, int32_t from, int32_t to) {
-  int32_t r = from;
-  while (r < to && ((reinterpret_cast<uintptr_t>(row + r) & 15u) != 0)) row[r++] = -1;
-  for (; r + 4 <= to; r += 4) *reinterpret_cast<int4*>(row + r) = make_int4(-1, -1, -1, -1);
-  for (; r < to; ++r) row[r] = -1;
+// Row writes are staged per lane in shared memory, one aligned 32-byte
+// sector at a time, and written out when the sector (or the row) is
+// complete: scattered 4-byte stores would each cost a DRAM sector write.
+// Slot s of lane t lives at obuf[s * kBlock + t] (no bank conflicts).
+struct RowStage {
+  int32_t* row;   // current row (nullptr: none)
+  int32_t first;  // first valid slot of the staged sector
+};
+
+__device__ __forceinline__ int32_t sector_slot(const int32_t* a) {
+  return (int32_t)((reinterpret_cast<uintptr_t>(a) >> 2) & 7u);
+}
+
+// write the staged slots [first, last] of the sector holding `a` (a = address of slot `last`)
+__device__ __forceinline__ void stage_flush(const int32_t* obuf, int tid, int32_t* a, int32_t first, int32_t last) {
+  int32_t* base = a - last;
+  if (first == 0 && last == 7) {
+    const int4 lo = make_int4(obuf[0 * kBlock + tid], obuf[1 * kBlock + tid], obuf[2 * kBlock + tid], obuf[3 * kBlock + tid]);
+    const int4 hi = make_int4(obuf[4 * kBlock + tid], obuf[5 * kBlock + tid], obuf[6 * kBlock + tid], obuf[7 * kBlock + tid]);
+    reinterpret_cast<int4*>(base)[0] = lo;
+    reinterpret_cast<int4*>(base)[1] = hi;
+  } else {
+    for (int32_t k = first; k <= last; ++k) base[k] = obuf[k * kBlock + tid];
+  }
+}
+
+// stage row[p] = val; `final` marks the last entry the lane will write in this row
+__device__ __forceinline__ void stage_put(int32_t* obuf, int tid, RowStage& rs, int32_t p, int32_t val, bool final) {
+  int32_t* a = rs.row + p;
+  const int32_t slot = sector_slot(a);
+  obuf[slot * kBlock + tid] = val;
+  if (slot == 7 || final) {
+    stage_flush(obuf, tid, a, rs.first, slot);
+    rs.first = 0;
+  }
+}
+
+// row[from, to) = -1 after a dead end: finish the staged sector, then whole sectors, then the tail
+__device__ __forceinline__ void stage_fill_minus_one(int32_t* obuf, int tid, RowStage& rs, int32_t from, int32_t to) {
+  int32_t p = from;
+  while (p < to && (p == from || sector_slot(rs.row + p) != 0)) {
+    stage_put(obuf, tid, rs, p, -1, p + 1 == to);
+    ++p;
+  }
+  for (; p + 8 <= to; p += 8) {
+    int4* q = reinterpret_cast<int4*>(rs.row + p);
+    q[0] = make_int4(-1, -1, -1, -1);
+    q[1] = make_int4(-1, -1, -1, -1);
+  }
+  for (; p < to; ++p) rs.row[p] = -1;
 }
 
 template <int NJ>
@@ -42,6 +86,7 @@ __global__ void __launch_bounds__(kBlock) walk_kernel(DevGraph g, JobTableN<NJ> 
                                                       unsigned long long* __restrict__ qctr,
                                                       unsigned* __restrict__ err, DevCounters* __restrict__ cnt) {
   __shared__ Job sj[NJ];
+  __shared__ int32_t obuf[8 * kBlock];
   {
     const int words = njobs * (int)(sizeof(Job) / 4);
     const int* src = reinterpret_cast<const int*>(tab.jobs);
@@ -51,7 +96,11 @@ __global__ void __launch_bounds__(kBlock) walk_kernel(DevGraph g, JobTableN<NJ> 
   __syncthreads();
 
   const int lane = threadIdx.x & 31;
+  const int tid = threadIdx.x;
   const unsigned lt_mask = (1u << lane) - 1u;
+  RowStage rs;
+  rs.row = nullptr;
+  rs.first = 0;
   LaneCounters lc;
   lc.zero();
 
@@ -84,13 +133,14 @@ __global__ void __launch_bounds__(kBlock) walk_kernel(DevGraph g, JobTableN<NJ> 
           widx = (int32_t)(gi - J.gbase);
           if (J.kind == JOB_WALK) {
             const int32_t st = __ldg(J.starts + widx);
-            int32_t* row = J.out + (long long)widx * (J.len + 1);
+            rs.row = J.out + (long long)widx * (J.len + 1);
+            rs.first = sector_slot(rs.row);
             if (st < 0 || st >= g.n) {
               atomicOr(err, DEVERR_START);
-              fill_minus_one(row, 0, J.len + 1);
+              stage_fill_minus_one(obuf, tid, rs, 0, J.len + 1);
               widx = -1;
             } else {
-              row[0] = st;
+              stage_put(obuf, tid, rs, 0, st, J.len == 0);
               cur = st;
               prev = -1;
               step = 0;
@@ -102,6 +152,11 @@ __global__ void __launch_bounds__(kBlock) walk_kernel(DevGraph g, JobTableN<NJ> 
             prev = J.hprev;
             step = J.hstep;
             end = J.hstep + 1;
+            if (prev >= 0) {  // the row range of v' is carried along during walks; load it here
+              const int4 pr = __ldg(g.nrec + prev);
+              c.s = pr.x;
+              c.d = pr.y;
+            }
           }
           plan = PLAN_NONE;
           pick = -2;
@@ -116,34 +171,31 @@ __global__ void __launch_bounds__(kBlock) walk_kernel(DevGraph g, JobTableN<NJ> 
     const Job& J = sj[job];
     // ------------------------------------------------------------ plan
     if (widx >= 0 && plan == PLAN_NONE) {
+      // v' row range = the previous step's row range (prev = the node we left)
+      c.ps = c.s;
+      c.pe = c.s + c.d;
       c.v = cur;
       c.vp = prev;
       c.step = step;
       c.wid = J.walker_base + (uint32_t)widx;
-      c.s = __ldg(g.off + cur);
-      c.d = __ldg(g.off + cur + 1) - c.s;
+      const int4 nr = __ldg(g.nrec + cur);  // one 16-byte record: row start, degree, h_MAX, h_SUM
+      c.s = nr.x;
+      c.d = nr.y;
       trials = 0;
       pick = -2;
-      if (COUNT) lc.bytes += 8;
+      if (COUNT) lc.bytes += 16;
       if (c.d == 0) {
         pick = -1;
         plan = PLAN_RJS;
       } else {
-        if (J.algo == ALGO_NODE2VEC && prev >= 0 && J.need_member) {
-          c.ps = __ldg(g.off + prev);
-          c.pe = __ldg(g.off + prev + 1);
-        } else {
-          c.ps = c.pe = 0;
-        }
         int32_t m = J.mode;
         if (m == MODE_EXACT) {
           plan = (c.d <= kThreadExactMaxDeg) ? PLAN_EXACT_T : PLAN_EXACT_W;
         } else {
           float hm, hs, S;
           if (J.weighted) {
-            hm = __ldg(g.hmax + cur);
-            hs = __ldg(g.hsum + cur);
-            if (COUNT) lc.bytes += 8;
+            hm = __int_as_float(nr.z);
+            hs = __int_as_float(nr.w);
           } else {
             hm = 1.0f;
             hs = (float)c.d;
@@ -221,11 +273,10 @@ __global__ void __launch_bounds__(kBlock) walk_kernel(DevGraph g, JobTableN<NJ> 
     // ------------------------------------------------------------ commit
     if (widx >= 0 && pick != -2) {
       if (J.kind == JOB_WALK) {
-        int32_t* row = J.out + (long long)widx * (J.len + 1);
         if (pick >= 0) {
-          row[step + 1] = node;
+          stage_put(obuf, tid, rs, step + 1, node, step + 1 == end);
         } else {
-          fill_minus_one(row, step + 1, J.len + 1);
+          stage_fill_minus_one(obuf, tid, rs, step + 1, J.len + 1);
         }
       } else if (pick >= 0) {
         atomicAdd(J.hist + pick, 1ull);
@@ -297,7 +348,8 @@ cudaError_t launch_walk(const fw_graph* g, const Job* jobs, int njobs, long long
 // h_MAX[v] and h_SUM[v]: one warp per node, lanes stride over the row
 // (coalesced), then a shuffle-tree max and sum (Sec. 4.2 preprocess()).
 __global__ void node_stats_kernel(const int32_t* __restrict__ off, const float* __restrict__ h, int32_t n,
-                                  float* __restrict__ hmax, float* __restrict__ hsum, int* __restrict__ maxdeg) {
+                                  float* __restrict__ hmax, float* __restrict__ hsum, int4* __restrict__ nrec,
+                                  int* __restrict__ maxdeg) {
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -323,18 +375,19 @@ __global__ void node_stats_kernel(const int32_t* __restrict__ off, const float* 
     if (lane == 0) {
       hmax[v] = m;
       hsum[v] = sum;
+      nrec[v] = make_int4(s, e - s, __float_as_int(m), __float_as_int(sum));
     }
     localmax = max(localmax, e - s);
   }
   if (lane == 0 && localmax > 0) atomicMax(maxdeg, localmax);
 }
 
-cudaError_t launch_node_stats(const int32_t* off, const float* h, int32_t n, float* hmax, float* hsum, int* maxdeg,
-                              int num_sms, cudaStream_t stream) {
+cudaError_t launch_node_stats(const int32_t* off, const float* h, int32_t n, float* hmax, float* hsum, int4* nrec,
+                              int* maxdeg, int num_sms, cudaStream_t stream) {
   if (n == 0) return cudaSuccess;
   const long long want = ((long long)n * 32 + 255) / 256;
   const int grid = (int)(want < (long long)num_sms * 8 ? want : (long long)num_sms * 8);
-  node_stats_kernel<<<grid, 256, 0, stream>>>(off, h, n, hmax, hsum, maxdeg);
+  node_stats_kernel<<<grid, 256, 0, stream>>>(off, h, n, hmax, hsum, nrec, maxdeg);
   g_launches.fetch_add(1);
   return cudaGetLastError();
 }
