@@ -69,7 +69,10 @@ enum { FW_PTR_HOST = 0, FW_PTR_DEVICE = 1 };
 enum {
   FW_FLAG_RVS_NOJUMP = 1, /* eRVS with exponential keys only (Alg. 1), no jumps */
   FW_FLAG_COUNTERS = 2,   /* accumulate per-walk counters (slower build path)    */
-  FW_FLAG_UNWEIGHTED = 4  /* ignore h: every property weight is 1 (Sec. 5.1)     */
+  FW_FLAG_UNWEIGHTED = 4, /* ignore h: every property weight is 1 (Sec. 5.1)     */
+  FW_FLAG_PLAIN_RJS = 8   /* eRJS exactly as Sec. 3.3 (uniform proposal, bound
+                             max(w) * h_MAX) even when node2vec's return edge
+                             could be proposed separately                        */
 };
 
 /* Parameters of one walk job.  Initialise with fw_params_default(). */
@@ -97,6 +100,8 @@ typedef struct {
   float cost_ratio;          /* current tuned r                                  */
   double preprocess_ms;      /* h_MAX / h_SUM reductions, Sec. 4.2 preprocess()  */
   size_t device_bytes;       /* device memory held by the graph                  */
+  int32_t symmetric;         /* 1: every edge (v,u) has a mirror (u,v) with the
+                                same weight (found at creation)                   */
 } fw_graph_info_t;
 
 /* Per-walk counters (FW_FLAG_COUNTERS).  Byte figures follow the

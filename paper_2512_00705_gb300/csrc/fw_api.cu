@@ -33,7 +33,9 @@ DevGraph dev_graph(const fw_graph* g) {
   d.hmax = g->d_hmax;
   d.hsum = g->d_hsum;
   d.nrec = g->d_nrec;
+  d.erec = g->d_erec;
   d.n = g->n;
+  d.sym = g->sym;
   return d;
 }
 
@@ -72,6 +74,7 @@ fw_status make_job(const fw_graph* g, int32_t algo, const fw_params* params, uin
     job->whi1 = std::fmax(1.0f, iq);
     job->need_member = (iq != 1.0f) ? 1 : 0;
     job->second_order = (ip != 1.0f || iq != 1.0f) ? 1 : 0;
+    job->split_return = (ip > job->whi1 && !(P.flags & FW_FLAG_PLAIN_RJS)) ? 1 : 0;
   } else {
     job->inv_p = job->inv_q = 1.0f;
     job->wmax1 = job->wlo1 = job->whi1 = 1.0f;
@@ -159,6 +162,7 @@ static void free_graph(fw_graph* g) {
   cudaFree(g->d_hmax);
   cudaFree(g->d_hsum);
   cudaFree(g->d_nrec);
+  cudaFree(g->d_erec);
   cudaFree(g->d_err);
   cudaFree(g->d_cnt);
   cudaFree(g->d_stage_starts);
@@ -204,10 +208,12 @@ extern "C" fw_status fw_graph_create(const int32_t* offsets, const int32_t* cols
   FW_TRY(cudaMalloc(&g->d_hmax, sizeof(float) * ((size_t)n + 1)), "cudaMalloc(h_MAX)");
   FW_TRY(cudaMalloc(&g->d_hsum, sizeof(float) * ((size_t)n + 1)), "cudaMalloc(h_SUM)");
   FW_TRY(cudaMalloc(&g->d_nrec, sizeof(int4) * ((size_t)n + 1)), "cudaMalloc(node records)");
+  FW_TRY(cudaMalloc(&g->d_erec, 2 * sizeof(int4) * eb), "cudaMalloc(edge records)");
   FW_TRY(cudaMalloc(&g->d_err, 64), "cudaMalloc(error word)");
   FW_TRY(cudaMalloc(&g->d_cnt, sizeof(DevCounters)), "cudaMalloc(counters)");
   g->bytes = sizeof(int32_t) * ((size_t)n + 1) + eb * (4 + (weights ? 4 : 0) + (labels ? 1 : 0)) +
-             2 * sizeof(float) * ((size_t)n + 1) + sizeof(int4) * ((size_t)n + 1) + 64 + sizeof(DevCounters);
+             2 * sizeof(float) * ((size_t)n + 1) + sizeof(int4) * ((size_t)n + 1) + 2 * sizeof(int4) * eb + 64 +
+             sizeof(DevCounters);
   FW_TRY(cudaMemsetAsync(g->d_err, 0, 64, st), "cudaMemsetAsync");
   FW_TRY(cudaMemsetAsync(g->d_cnt, 0, sizeof(DevCounters), st), "cudaMemsetAsync");
   FW_TRY(cudaMemcpyAsync(g->d_off, offsets, sizeof(int32_t) * ((size_t)n + 1), kind, st), "copy offsets");
@@ -238,10 +244,17 @@ extern "C" fw_status fw_graph_create(const int32_t* offsets, const int32_t* cols
   FW_TRY(cudaEventCreate(&e0), "cudaEventCreate");
   FW_TRY(cudaEventCreate(&e1), "cudaEventCreate");
   cudaEventRecord(e0, st);
-  cudaError_t le = launch_node_stats(g->d_off, g->d_h, n, g->d_hmax, g->d_hsum, g->d_nrec, d_maxdeg, g->num_sms, st);
+  unsigned* d_asym = g->d_err + 12;
+  cudaError_t le = cudaMemsetAsync(d_asym, 0, sizeof(unsigned), st);
+  if (le == cudaSuccess)
+    le = launch_node_stats(g->d_off, g->d_h, n, g->d_hmax, g->d_hsum, g->d_nrec, d_maxdeg, g->num_sms, st);
+  if (le == cudaSuccess) le = launch_edge_records(g->d_col, g->d_h, g->d_lab, g->d_nrec, e, g->d_erec, g->num_sms, st);
+  if (le == cudaSuccess) le = launch_symmetry(g->d_off, g->d_col, g->d_h, n, d_asym, g->num_sms, st);
   cudaEventRecord(e1, st);
   int maxdeg = 0;
+  unsigned asym = 1;
   cudaError_t ce = cudaMemcpyAsync(&maxdeg, d_maxdeg, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(&asym, d_asym, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
   cudaError_t se = cudaStreamSynchronize(st);
   float ms = 0.0f;
   cudaEventElapsedTime(&ms, e0, e1);
@@ -252,6 +265,7 @@ extern "C" fw_status fw_graph_create(const int32_t* offsets, const int32_t* cols
   FW_TRY(se, "sync after preprocessing");
   FW_TRY(cudaMemsetAsync(d_maxdeg, 0, sizeof(int), st), "cudaMemsetAsync");
   g->max_degree = maxdeg;
+  g->sym = asym == 0 ? 1 : 0;
   g->preprocess_ms = ms;
   *out = g;
   return FW_OK;
@@ -274,6 +288,7 @@ extern "C" fw_status fw_graph_info(const fw_graph* g, fw_graph_info_t* info) {
   info->cost_ratio = g->ratio;
   info->preprocess_ms = g->preprocess_ms;
   info->device_bytes = g->bytes;
+  info->symmetric = g->sym;
   return FW_OK;
 }
 

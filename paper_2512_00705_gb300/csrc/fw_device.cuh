@@ -43,7 +43,10 @@ struct DevGraph {
   const float* __restrict__ hmax;
   const float* __restrict__ hsum;
   const int4* __restrict__ nrec;   // per node {row start, degree, h_MAX bits, h_SUM bits}: one sector per plan
+  const int4* __restrict__ erec;   // per edge 32 bytes: {col, h bits, target row start, target degree},
+                                   // {target h_MAX bits, target h_SUM bits, label, 0}: one sector per eRJS trial
   int32_t n;
+  int32_t sym;                     // 1: h(v,u) = h(u,v) for every edge (checked at creation)
 };
 
 // One walk job (a batch is a table of these).  Walkers of all jobs form one
@@ -60,6 +63,7 @@ struct Job {
   int32_t second_order;    // node2vec with (1/p, 1/q) != (1, 1): w depends on v'
   int32_t need_member;     // node2vec with 1/q != 1: membership test needed
   int32_t fixed_cap;       // 1: rjs_cap is a fixed trial cap; 0: cap = max(rjs_cap, ceil(d / ratio))
+  int32_t split_return;    // node2vec with 1/p > max(1, 1/q): eRJS proposes the return edge separately
   float inv_p, inv_q;      // FP32 1/p, 1/q
   float wmax1, wmean1;     // max / mean of w when a previous node exists
   float wlo1, whi1;        // min / max of {1, 1/q}: squeeze bounds of a non-return neighbour
@@ -122,15 +126,19 @@ struct StepCtx {
   uint32_t wid;     // random-stream walker id
 };
 
-// u in N(x) for the sorted row col[lo, hi)?  All ids lie in [0, n).  A few
-// interpolation probes first (position guessed from u's place between the
-// bracketing values; a row of a graph with randomly permuted ids is close
-// to a uniform sample of [0, n), so the guess lands within a few entries),
-// then bisection of what is left.  Exits early on a hit.  At most
-// kInterpProbes + ceil(log2(d + 1)) probes.
+// Position of u in the sorted row col[lo, hi) (all ids in [0, n)), or -1.
+// A few interpolation probes first -- the guess puts u at its place between
+// the bracketing values; a row of a graph with randomly permuted ids is close
+// to a uniform sample of [0, n), so it lands within a few entries -- then
+// bisection of the remaining window of at most 8 entries (one or two
+// sectors, already in L1).  Exits early on a hit.  At most
+// kInterpProbes + ceil(log2(d + 1)) probes.  (Probes that read a whole
+// 32-byte sector, and searching the shorter of N(u) and N(v') on symmetric
+// graphs, were measured slower: each probe costs more and lands in colder
+// rows.)
 constexpr int kInterpProbes = 4;
-__device__ __forceinline__ bool row_contains(const int32_t* __restrict__ col, int32_t lo, int32_t hi, int32_t u,
-                                             int32_t n, uint32_t& probes) {
+__device__ __forceinline__ int32_t row_find(const int32_t* __restrict__ col, int32_t lo, int32_t hi, int32_t u,
+                                            int32_t n, uint32_t& probes) {
   float va = -1.0f, vb = (float)n;  // every id in [lo, hi) lies strictly between va and vb
 #pragma unroll 1
   for (int it = 0; it < kInterpProbes && hi - lo > 8; ++it) {
@@ -139,7 +147,7 @@ __device__ __forceinline__ bool row_contains(const int32_t* __restrict__ col, in
     g = min(max(g, lo), hi - 1);
     const int32_t c = __ldg(col + g);
     ++probes;
-    if (c == u) return true;
+    if (c == u) return g;
     if (c < u) {
       lo = g + 1;
       va = (float)c;
@@ -153,7 +161,7 @@ __device__ __forceinline__ bool row_contains(const int32_t* __restrict__ col, in
     const int32_t half = len >> 1;
     const int32_t c = __ldg(col + lo + half);
     ++probes;
-    if (c == u) return true;
+    if (c == u) return lo + half;
     if (c < u) {
       lo += half + 1;
       len -= half + 1;
@@ -161,7 +169,12 @@ __device__ __forceinline__ bool row_contains(const int32_t* __restrict__ col, in
       len = half;
     }
   }
-  return false;
+  return -1;
+}
+
+__device__ __forceinline__ bool row_contains(const int32_t* __restrict__ col, int32_t lo, int32_t hi, int32_t u,
+                                             int32_t n, uint32_t& probes) {
+  return row_find(col, lo, hi, u, n, probes) >= 0;
 }
 
 __device__ __forceinline__ float load_h(const DevGraph& g, const Job& J, int32_t i) {
@@ -201,20 +214,48 @@ __device__ __forceinline__ int32_t plan_choice(const Job& J, float hm, float hs,
 }
 
 // ---------------------------------------------------------------- eRJS
-// Run trials [t0, t0+nt) of one walker-step; returns the accepted neighbour
-// position or -1.  Trial t uses Philox counter (wid, hop, 1, t): x.x (x.y on
-// Lemire's rare retry) proposes X uniformly in [0,d) by Lemire's
-// multiply-shift with rejection (ACM TOMACS 2019); x.z gives U in [0,1).
+// One eRJS acceptance: the neighbour position, the node, its effective
+// property weight, and the target's node record (rec_ok = 0: unknown).
+struct Accept {
+  int32_t k, node;
+  float h;
+  int4 rec;
+  bool rec_ok;
+};
+
+// Run trials [t0, t0+nt) of one walker-step; returns true on acceptance.
+// Trial t uses Philox counter (wid, hop, 1, t): x.x (x.y on Lemire's rare
+// retry) proposes X uniformly in [0,d) by Lemire's multiply-shift with
+// rejection (ACM TOMACS 2019); x.z gives U in [0,1); x.w picks the return
+// component when the return edge is split off (beta > 0).
+//
+// Plain eRJS (Sec. 3.3): accept X iff U*B < w~(X).
+// Split return edge (node2vec when 1/p dominates the bound): with
+// probability beta = w~_ret / (w~_ret + d*B) the trial proposes v' and
+// accepts it; otherwise X is uniform over N(v), X = v' proposes nothing, and
+// X != v' is accepted iff U*B < w~(X) with B = max(1, 1/q) * h_MAX[v].
+// Accepted v' has probability beta and accepted x has (1-beta) w~(x)/(d B):
+// both proportional to w~, so the accepted draw follows Eq. (prob).
 template <bool COUNT>
-__device__ __forceinline__ int32_t rjs_trials(const DevGraph& g, const Job& J, const StepCtx& c, float B, int32_t t0,
-                                              int32_t nt, int32_t& node, LaneCounters& lc) {
+__device__ __forceinline__ bool rjs_trials(const DevGraph& g, const Job& J, const StepCtx& c, float B, bool split,
+                                           float beta, int32_t pos_ret, float h_ret, int32_t t0, int32_t nt,
+                                           Accept& acc, LaneCounters& lc) {
   const uint32_t d = (uint32_t)c.d;
   const uint8_t want = (J.algo == ALGO_METAPATH) ? J.schema[c.step % J.schema_len] : 0;
+  const bool second = (J.algo == ALGO_NODE2VEC) && c.vp >= 0 && J.second_order;
   uint32_t probes = 0;
-  int32_t found = -1;
+  bool found = false;
   for (int32_t t = t0; t < t0 + nt; ++t) {
     const uint4 x = philox(make_uint4(c.wid, (uint32_t)c.step, 1u, (uint32_t)t), J.key0, J.key1);
-    if (COUNT) { lc.rjs_trials++; }
+    if (COUNT) lc.rjs_trials++;
+    if (beta > 0.0f && u01(x.w) < beta) {
+      acc.k = pos_ret >= 0 ? pos_ret : 0;
+      acc.node = c.vp;
+      acc.h = h_ret;
+      acc.rec_ok = false;
+      found = true;
+      break;
+    }
     unsigned long long m = (unsigned long long)x.x * d;
     uint32_t l = (uint32_t)m;
     if (l < d) {
@@ -226,15 +267,17 @@ __device__ __forceinline__ int32_t rjs_trials(const DevGraph& g, const Job& J, c
       }
     }
     const int32_t k = (int32_t)(m >> 32);
-    const int32_t i = c.s + k;
+    const int4* er = g.erec + 2ll * (c.s + k);
+    const int4 a = __ldg(er);      // col, h, target row start, target degree
+    const int4 b = __ldg(er + 1);  // target h_MAX, target h_SUM, label
+    if (COUNT) lc.bytes += 32;
+    const int32_t u = a.x;
+    const float hk = J.weighted ? __int_as_float(a.y) : 1.0f;
     const float UB = __fmul_rn(u01(x.z), B);
     bool accept;
-    int32_t u = -1;
-    if (J.algo == ALGO_NODE2VEC && c.vp >= 0 && J.second_order) {
-      u = __ldg(g.col + i);
-      const float hk = load_h(g, J, i);
-      if (COUNT) lc.bytes += J.weighted ? 64 : 32;
+    if (second) {
       if (u == c.vp) {
+        if (split) continue;                    // the return component owns v'
         accept = UB < __fmul_rn(J.inv_p, hk);
       } else if (UB >= __fmul_rn(J.whi1, hk)) {
         accept = false;                         // squeeze: above the largest possible weight
@@ -242,24 +285,22 @@ __device__ __forceinline__ int32_t rjs_trials(const DevGraph& g, const Job& J, c
         accept = true;                          // squeeze: below the smallest possible weight
       } else {
         uint32_t pb = 0;
-        const float w = row_contains(g.col, c.ps, c.pe, u, g.n, pb) ? 1.0f : J.inv_q;
+        const bool adj = row_contains(g.col, c.ps, c.pe, u, g.n, pb);
         probes += pb;
-        accept = UB < __fmul_rn(w, hk);
+        accept = UB < __fmul_rn(adj ? 1.0f : J.inv_q, hk);
       }
     } else if (J.algo == ALGO_METAPATH) {
-      const uint8_t lb = __ldg(g.lab + i);
-      const float hk = load_h(g, J, i);
-      if (COUNT) lc.bytes += J.weighted ? 64 : 32;
-      accept = (lb == want) && (UB < hk);
+      accept = ((uint8_t)b.z == want) && (UB < hk);
     } else {
-      const float hk = load_h(g, J, i);
-      if (COUNT) lc.bytes += J.weighted ? 32 : 0;
       accept = UB < hk;
     }
     if (accept) {
-      found = k;
-      node = (u >= 0) ? u : __ldg(g.col + i);
-      if (COUNT && u < 0) lc.bytes += 32;
+      acc.k = k;
+      acc.node = u;
+      acc.h = hk;
+      acc.rec = make_int4(a.z, a.w, b.x, b.y);
+      acc.rec_ok = true;
+      found = true;
       break;
     }
   }

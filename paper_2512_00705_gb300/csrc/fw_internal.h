@@ -24,6 +24,8 @@ struct fw_graph {
   float* d_hmax = nullptr;
   float* d_hsum = nullptr;
   int4* d_nrec = nullptr;
+  int4* d_erec = nullptr;
+  int32_t sym = 0;
   unsigned* d_err = nullptr;
   fw::DevCounters* d_cnt = nullptr;
   float ratio = 4.0f;
@@ -56,6 +58,10 @@ cudaError_t launch_walk(const fw_graph* g, const Job* jobs, int njobs, long long
 
 cudaError_t launch_node_stats(const int32_t* off, const float* h, int32_t n, float* hmax, float* hsum, int4* nrec,
                               int* maxdeg, int num_sms, cudaStream_t stream);
+cudaError_t launch_edge_records(const int32_t* col, const float* h, const uint8_t* lab, const int4* nrec, long long e,
+                                int4* erec, int num_sms, cudaStream_t stream);
+cudaError_t launch_symmetry(const int32_t* off, const int32_t* col, const float* h, int32_t n, unsigned* flag,
+                            int num_sms, cudaStream_t stream);
 cudaError_t launch_check_offsets(const int32_t* off, int32_t n, int64_t e, unsigned* err, int num_sms,
                                  cudaStream_t stream);
 cudaError_t launch_check_rows(const int32_t* off, const int32_t* col, const float* h, int32_t n, unsigned* err,

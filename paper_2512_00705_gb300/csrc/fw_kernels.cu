@@ -21,6 +21,7 @@
 namespace fw {
 
 constexpr int kBlock = 256;
+constexpr int kMinBlocks = 4;       // 4 x 256 threads per SM: at most 64 registers per thread
 constexpr int kRjsBatch = 2;           // eRJS trials per round before the warp ballot
 constexpr int kThreadExactMaxDeg = 16; // exact steps with d <= this run on one lane
 
@@ -82,7 +83,7 @@ struct JobTableN {
 };
 
 template <int NJ, bool COUNT>
-__global__ void __launch_bounds__(kBlock) walk_kernel(DevGraph g, JobTableN<NJ> tab, int njobs, long long total,
+__global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, JobTableN<NJ> tab, int njobs, long long total,
                                                       unsigned long long* __restrict__ qctr,
                                                       unsigned* __restrict__ err, DevCounters* __restrict__ cnt) {
   __shared__ Job sj[NJ];
@@ -104,12 +105,23 @@ __global__ void __launch_bounds__(kBlock) walk_kernel(DevGraph g, JobTableN<NJ> 
   LaneCounters lc;
   lc.zero();
 
-  int32_t job = 0, widx = -1, cur = 0, prev = -1, step = 0, end = 0;
-  int32_t plan = PLAN_NONE, trials = 0, pick = -2, node = -1;
-  float B = 0.0f;
+  // walker state: c.v current node, c.vp previous node (-1: none), c.step hop,
+  // c.s / c.d row of c.v, c.ps / c.pe row of c.vp
   StepCtx c;
   c.v = c.vp = c.s = c.d = c.ps = c.pe = c.step = 0;
   c.wid = 0;
+  int32_t job = 0, widx = -1;
+  int32_t plan = PLAN_NONE, trials = 0, pick = -2, node = -1;
+  float B = 0.0f;
+  // eRJS with the return edge split off: probability of the return component,
+  // position of v' in N(v) (-1: unknown) and h(v, v')
+  bool split = false;
+  float beta = 0.0f, h_ret = 0.0f;
+  int32_t pos_ret = -1;
+  // from the accepted trial: the next node's record, and h of the edge taken (-1: unknown)
+  int4 nxt = make_int4(0, 0, 0, 0);
+  bool nxt_ok = false;
+  float h_in = -1.0f;
   bool exhausted = false;  // warp-uniform
 
   while (true) {
@@ -141,25 +153,25 @@ __global__ void __launch_bounds__(kBlock) walk_kernel(DevGraph g, JobTableN<NJ> 
               widx = -1;
             } else {
               stage_put(obuf, tid, rs, 0, st, J.len == 0);
-              cur = st;
-              prev = -1;
-              step = 0;
-              end = J.len;
-              if (end == 0) widx = -1;
+              c.v = st;
+              c.vp = -1;
+              c.step = 0;
+              if (J.len == 0) widx = -1;
             }
           } else {
-            cur = J.hv;
-            prev = J.hprev;
-            step = J.hstep;
-            end = J.hstep + 1;
-            if (prev >= 0) {  // the row range of v' is carried along during walks; load it here
-              const int4 pr = __ldg(g.nrec + prev);
+            c.v = J.hv;
+            c.vp = J.hprev;
+            c.step = J.hstep;
+            if (c.vp >= 0) {  // during walks the row of v' is carried along; here it is loaded
+              const int4 pr = __ldg(g.nrec + c.vp);
               c.s = pr.x;
               c.d = pr.y;
             }
           }
           plan = PLAN_NONE;
           pick = -2;
+          nxt_ok = false;
+          h_in = -1.0f;
         }
       }
     }
@@ -171,19 +183,23 @@ __global__ void __launch_bounds__(kBlock) walk_kernel(DevGraph g, JobTableN<NJ> 
     const Job& J = sj[job];
     // ------------------------------------------------------------ plan
     if (widx >= 0 && plan == PLAN_NONE) {
-      // v' row range = the previous step's row range (prev = the node we left)
-      c.ps = c.s;
+      c.ps = c.s;  // the row of v' is the previous step's row
       c.pe = c.s + c.d;
-      c.v = cur;
-      c.vp = prev;
-      c.step = step;
       c.wid = J.walker_base + (uint32_t)widx;
-      const int4 nr = __ldg(g.nrec + cur);  // one 16-byte record: row start, degree, h_MAX, h_SUM
+      int4 nr;  // row start, degree, h_MAX, h_SUM of v: from the accepted trial's edge record, or one load
+      if (nxt_ok) {
+        nr = nxt;
+      } else {
+        nr = __ldg(g.nrec + c.v);
+        if (COUNT) lc.bytes += 16;
+      }
+      nxt_ok = false;
       c.s = nr.x;
       c.d = nr.y;
       trials = 0;
       pick = -2;
-      if (COUNT) lc.bytes += 16;
+      split = false;
+      beta = 0.0f;
       if (c.d == 0) {
         pick = -1;
         plan = PLAN_RJS;
@@ -200,19 +216,49 @@ __global__ void __launch_bounds__(kBlock) walk_kernel(DevGraph g, JobTableN<NJ> 
             hm = 1.0f;
             hs = (float)c.d;
           }
-          const int32_t choice = plan_choice(J, hm, hs, prev >= 0, B, S);
+          const int32_t choice = plan_choice(J, hm, hs, c.vp >= 0, B, S);
           if (m == MODE_AUTO) m = choice;
           plan = (m == MODE_RJS) ? PLAN_RJS : ((c.d <= kThreadRvsMaxDeg) ? PLAN_RVS_T : PLAN_RVS_W);
+          if (plan == PLAN_RJS && J.split_return && c.vp >= 0) {
+            // the return edge alone sets max(w) = 1/p: propose it separately and
+            // bound the other neighbours by max(1, 1/q) * h_MAX[v]
+            split = true;
+            B = __fmul_rn(J.whi1, hm);
+            pos_ret = -1;
+            bool have = false;
+            if (g.sym && h_in >= 0.0f && J.kind == JOB_WALK) {
+              h_ret = h_in;  // symmetric weights: h(v, v') = h(v', v), the edge just taken
+              have = true;
+            } else {
+              uint32_t pb = 0;
+              pos_ret = row_find(g.col, c.s, c.s + c.d, c.vp, g.n, pb);
+              if (COUNT) {
+                lc.probes += pb;
+                lc.bytes += 32ull * pb;
+              }
+              if (pos_ret >= 0) {
+                h_ret = load_h(g, J, pos_ret);
+                pos_ret -= c.s;
+                have = true;
+              }
+            }
+            if (have) {
+              const float wret = __fmul_rn(J.inv_p, h_ret);
+              beta = wret / (wret + (float)c.d * B);
+            }
+          }
         }
       }
     }
     // ------------------------------------------------------------ eRJS trials
     if (widx >= 0 && plan == PLAN_RJS && pick == -2) {
-      int32_t nd = -1;
-      const int32_t k = rjs_trials<COUNT>(g, J, c, B, trials, kRjsBatch, nd, lc);
-      if (k >= 0) {
-        pick = k;
-        node = nd;
+      Accept acc;
+      if (rjs_trials<COUNT>(g, J, c, B, split, beta, pos_ret, h_ret, trials, kRjsBatch, acc, lc)) {
+        pick = acc.k;
+        node = acc.node;
+        h_in = acc.h;
+        nxt = acc.rec;
+        nxt_ok = acc.rec_ok;
         if (COUNT) lc.rjs_steps++;
       } else {
         trials += kRjsBatch;
@@ -229,12 +275,14 @@ __global__ void __launch_bounds__(kBlock) walk_kernel(DevGraph g, JobTableN<NJ> 
     if (widx >= 0 && pick == -2 && plan == PLAN_RVS_T) {
       pick = rvs_pick<1, COUNT>(g, J, c, 0, !(J.flags & FW_FLAG_RVS_NOJUMP), lc);
       if (pick >= 0) node = __ldg(g.col + c.s + pick);
+      h_in = -1.0f;
       if (COUNT) lc.rvs_steps++;
     }
     if (widx >= 0 && pick == -2 && plan == PLAN_EXACT_T) {
       const float u = u01(philox(make_uint4(c.wid, (uint32_t)c.step, 0u, 0u), J.key0, J.key1).x);
       pick = exact_pick<1, COUNT>(g, J, c, 0, u, lc);
       if (pick >= 0) node = __ldg(g.col + c.s + pick);
+      h_in = -1.0f;
       if (COUNT) lc.exact_steps++;
     }
     // ------------------------------------------------------------ warp hand-off
@@ -264,6 +312,7 @@ __global__ void __launch_bounds__(kBlock) walk_kernel(DevGraph g, JobTableN<NJ> 
       if (lane == src) {
         pick = k;
         if (k >= 0) node = __ldg(g.col + w.s + k);
+        h_in = -1.0f;
         if (COUNT) {
           if (pl == PLAN_EXACT_W) lc.exact_steps++;
           else lc.rvs_steps++;
@@ -272,24 +321,25 @@ __global__ void __launch_bounds__(kBlock) walk_kernel(DevGraph g, JobTableN<NJ> 
     }
     // ------------------------------------------------------------ commit
     if (widx >= 0 && pick != -2) {
+      const int32_t end = (J.kind == JOB_WALK) ? J.len : J.hstep + 1;
       if (J.kind == JOB_WALK) {
         if (pick >= 0) {
-          stage_put(obuf, tid, rs, step + 1, node, step + 1 == end);
+          stage_put(obuf, tid, rs, c.step + 1, node, c.step + 1 == end);
         } else {
-          stage_fill_minus_one(obuf, tid, rs, step + 1, J.len + 1);
+          stage_fill_minus_one(obuf, tid, rs, c.step + 1, J.len + 1);
         }
       } else if (pick >= 0) {
         atomicAdd(J.hist + pick, 1ull);
       }
       if (pick >= 0) {
-        prev = cur;
-        cur = node;
-        ++step;
+        c.vp = c.v;
+        c.v = node;
+        ++c.step;
         if (COUNT) {
           lc.hops++;
           lc.bytes += 4;
         }
-        if (step >= end) widx = -1;
+        if (c.step >= end) widx = -1;
       } else {
         if (COUNT) lc.dead_ends++;
         widx = -1;
@@ -388,6 +438,60 @@ cudaError_t launch_node_stats(const int32_t* off, const float* h, int32_t n, flo
   const long long want = ((long long)n * 32 + 255) / 256;
   const int grid = (int)(want < (long long)num_sms * 8 ? want : (long long)num_sms * 8);
   node_stats_kernel<<<grid, 256, 0, stream>>>(off, h, n, hmax, hsum, nrec, maxdeg);
+  g_launches.fetch_add(1);
+  return cudaGetLastError();
+}
+
+// Edge records (32 bytes per CSR entry): everything one eRJS trial needs and
+// everything the next step's plan needs if the trial is accepted.
+__global__ void edge_rec_kernel(const int32_t* __restrict__ col, const float* __restrict__ h,
+                                const uint8_t* __restrict__ lab, const int4* __restrict__ nrec, long long e,
+                                int4* __restrict__ erec) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < e; i += (long long)gridDim.x * blockDim.x) {
+    const int32_t u = col[i];
+    const int4 nr = nrec[u];
+    const int hb = h ? __float_as_int(h[i]) : __float_as_int(1.0f);
+    const int lb = lab ? (int)lab[i] : 0;
+    erec[2 * i] = make_int4(u, hb, nr.x, nr.y);
+    erec[2 * i + 1] = make_int4(nr.z, nr.w, lb, 0);
+  }
+}
+
+cudaError_t launch_edge_records(const int32_t* col, const float* h, const uint8_t* lab, const int4* nrec, long long e,
+                                int4* erec, int num_sms, cudaStream_t stream) {
+  if (e == 0) return cudaSuccess;
+  const long long want = (e + 255) / 256;
+  const int grid = (int)(want < (long long)num_sms * 16 ? want : (long long)num_sms * 16);
+  edge_rec_kernel<<<grid, 256, 0, stream>>>(col, h, lab, nrec, e, erec);
+  g_launches.fetch_add(1);
+  return cudaGetLastError();
+}
+
+// Sets *flag if some edge (v, u) has no mirror (u, v) with the same weight.
+__global__ void symmetry_kernel(const int32_t* __restrict__ off, const int32_t* __restrict__ col,
+                                const float* __restrict__ h, int32_t n, unsigned* __restrict__ flag) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long v = warp; v < n; v += nwarps) {
+    const int32_t s = off[v], e = off[v + 1];
+    bool bad = false;
+    for (int32_t i = s + lane; i < e; i += 32) {
+      const int32_t u = col[i];
+      uint32_t pb = 0;
+      const int32_t j = row_find(col, off[u], off[u + 1], (int32_t)v, n, pb);
+      if (j < 0 || (h && h[j] != h[i])) bad = true;
+    }
+    if (bad) atomicOr(flag, 1u);
+  }
+}
+
+cudaError_t launch_symmetry(const int32_t* off, const int32_t* col, const float* h, int32_t n, unsigned* flag,
+                            int num_sms, cudaStream_t stream) {
+  if (n == 0) return cudaSuccess;
+  const long long want = ((long long)n * 32 + 255) / 256;
+  const int grid = (int)(want < (long long)num_sms * 8 ? want : (long long)num_sms * 8);
+  symmetry_kernel<<<grid, 256, 0, stream>>>(off, col, h, n, flag);
   g_launches.fetch_add(1);
   return cudaGetLastError();
 }

@@ -19,7 +19,7 @@ from . import _build
 
 ALGO = {"weighted": 0, "node2vec": 1, "metapath": 2}
 MODE = {"auto": 0, "rjs": 1, "rvs": 2, "exact": 3}
-FLAG_RVS_NOJUMP, FLAG_COUNTERS, FLAG_UNWEIGHTED = 1, 2, 4
+FLAG_RVS_NOJUMP, FLAG_COUNTERS, FLAG_UNWEIGHTED, FLAG_PLAIN_RJS = 1, 2, 4, 8
 PTR_HOST, PTR_DEVICE = 0, 1
 STATUS = {0: "FW_OK", -1: "FW_ERR_ARG", -2: "FW_ERR_CSR", -3: "FW_ERR_OOM", -4: "FW_ERR_CUDA",
           -5: "FW_ERR_TIMEOUT", -6: "FW_ERR_DEVICE_CHECK", -7: "FW_ERR_BUSY", -8: "FW_ERR_UNSUPPORTED"}
@@ -40,7 +40,7 @@ class fw_params(ctypes.Structure):
 class fw_graph_info_t(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("e", ctypes.c_int64), ("max_degree", ctypes.c_int32),
                 ("has_weights", ctypes.c_int32), ("has_labels", ctypes.c_int32), ("cost_ratio", ctypes.c_float),
-                ("preprocess_ms", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
+                ("preprocess_ms", ctypes.c_double), ("device_bytes", ctypes.c_size_t), ("symmetric", ctypes.c_int32)]
 
 
 COUNTER_FIELDS = ["hops", "rjs_steps", "rvs_steps", "exact_steps", "handoffs", "rjs_trials", "rvs_items",
@@ -56,7 +56,8 @@ _lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The built library; FLEXIWALK_LIB overrides it (e.g. to compare builds)."""
+    return os.environ.get("FLEXIWALK_LIB") or _build.LIB
 
 
 def lib() -> ctypes.CDLL:
@@ -64,9 +65,10 @@ def lib() -> ctypes.CDLL:
     global _lib
     with _lock:
         if _lib is None:
-            if not os.path.exists(_build.LIB):
-                raise RuntimeError(f"CUDA library not built: {_build.LIB} missing (run __graft_entry__.build())")
-            L = ctypes.CDLL(_build.LIB)
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library not built: {path} missing (run __graft_entry__.build())")
+            L = ctypes.CDLL(path)
             vp, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
             P = ctypes.POINTER
             sig = {

@@ -10,6 +10,7 @@ import pytest
 import oracle
 from paper_2512_00705_gb300 import flexiwalk as fw
 from paper_2512_00705_gb300 import synth
+from bruteforce import bf_paths, merged_chisquare
 from statcheck import chisq_pvalue, tv_distance
 
 torch = pytest.importorskip("torch")
@@ -266,3 +267,41 @@ def test_counters(small):
     assert c["dead_ends"] == int((o[:, -1] < 0).sum())
     plain = G.walk(_cuda(starts), 20, "node2vec", p=2.0, q=0.5, seed=5).cpu().numpy()
     assert np.array_equal(o, plain), "counting build must not change the walks"
+
+
+# ------------------------------------------------------------ whole-walk distributions
+def _asymmetric(g, seed):
+    """Same structure, an independent weight on each direction of every edge."""
+    rng = np.random.default_rng(seed)
+    return synth.Csr(g.offsets, g.cols, (1.0 - rng.random(g.e)).astype(np.float32), g.labels)
+
+
+WALK_CASES = [("node2vec", 0.25, 4.0, None), ("node2vec", 2.0, 0.5, None), ("node2vec", 4.0, 0.25, None),
+              ("metapath", 1.0, 1.0, [0, 1, 2]), ("weighted", 1.0, 1.0, None)]
+
+
+@pytest.mark.parametrize("graph", ["sparse", "sparse-asym", "dense"])
+@pytest.mark.parametrize("mode,flags", [("rjs", 0), ("rjs", fw.FLAG_PLAIN_RJS), ("rvs", 0), ("auto", 0)])
+@pytest.mark.parametrize("algo,p,q,schema", WALK_CASES)
+def test_fast_walk_path_distribution(graph, mode, flags, algo, p, q, schema):
+    """GPU walks from one start, many walker ids: frequencies of whole paths
+    match brute-force path probabilities (chi-square, merged bins).  This
+    covers the walk-only paths: edge records carried between steps, the
+    split return edge fed by the arriving edge (symmetric weights) or by a
+    search (asymmetric), and warp-level eRVS (dense graph)."""
+    if graph == "dense":
+        g = synth.random_graph(24, 0.85, seed=21, weighted=True, nlabels=3)
+        L = 3
+    else:
+        g = synth.random_graph(8, 0.45, seed=11, weighted=True, nlabels=3)
+        L = 4
+        if graph == "sparse-asym":
+            g = _asymmetric(g, 3)
+    G = fw.Graph(g)
+    assert G.info["symmetric"] == (0 if graph == "sparse-asym" else 1)
+    W, start = 300_000, 0
+    starts = torch.full((W,), start, dtype=torch.int32, device="cuda")
+    out = G.walk(starts, L, algo, p=p, q=q, schema=schema, mode=mode, flags=flags, seed=17).cpu().numpy()
+    G.close()
+    bf = bf_paths(g, start, L, algo, p, q, schema)
+    assert merged_chisquare(bf, out) > 1e-4

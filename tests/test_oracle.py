@@ -139,52 +139,7 @@ def test_metapath_filter():
 
 
 # ------------------------------------------------------- brute force, 8 nodes
-def _bf_weight(adj, h, lab, v, u, vprev, hop, algo, p, q, schema):
-    """Eq. (prob) / Eq. (node2vec) / MetaPath written out on adjacency sets."""
-    hv = h[(v, u)]
-    if algo == "weighted":
-        return hv
-    if algo == "node2vec":
-        if vprev is None:
-            return hv
-        if u == vprev:
-            return hv / p
-        if u in adj[vprev]:
-            return hv
-        return hv / q
-    return hv if lab[(v, u)] == schema[hop % len(schema)] else 0.0
-
-
-def _bf_paths(g, start, length, algo, p, q, schema):
-    n = g.n
-    adj = [set(g.cols[g.offsets[i]:g.offsets[i + 1]].tolist()) for i in range(n)]
-    h, lab = {}, {}
-    for v in range(n):
-        for k in range(g.offsets[v], g.offsets[v + 1]):
-            u = int(g.cols[k])
-            h[(v, u)] = float(g.h[k]) if g.h is not None else 1.0
-            lab[(v, u)] = int(g.labels[k]) if g.labels is not None else 0
-    out = {}
-
-    def rec(path, prob):
-        hop = len(path) - 1
-        if hop == length:
-            out[tuple(path)] = out.get(tuple(path), 0.0) + prob
-            return
-        v = path[-1]
-        vprev = path[-2] if len(path) > 1 else None
-        ws = {u: _bf_weight(adj, h, lab, v, u, vprev, hop, algo, p, q, schema) for u in sorted(adj[v])}
-        tot = sum(ws.values())
-        if tot <= 0:
-            padded = tuple(path) + (-1,) * (length - hop)
-            out[padded] = out.get(padded, 0.0) + prob
-            return
-        for u, w in ws.items():
-            if w > 0:
-                rec(path + [u], prob * w / tot)
-
-    rec([start], 1.0)
-    return out
+from bruteforce import bf_paths as _bf_paths, merged_chisquare
 
 
 CASES = [("weighted", 1.0, 1.0, None), ("node2vec", 2.0, 0.5, None), ("node2vec", 0.25, 4.0, None),
@@ -222,26 +177,7 @@ def test_brute_force_sampler_frequencies(algo, p, q, schema):
     L, W, start = 4, 60000, 0
     bf = _bf_paths(g, start, L, algo, p, q, schema)
     out, _ = oracle.walk(g, np.full(W, start, np.int32), L, algo, p, q, schema, seed=7)
-    keys = list(bf.keys())
-    index = {k: i for i, k in enumerate(keys)}
-    counts = np.zeros(len(keys))
-    for row in map(tuple, out.tolist()):
-        assert row in index, f"walk {row} has probability zero"
-        counts[index[row]] += 1
-    exp = np.array([bf[k] for k in keys]) * W
-    order = np.argsort(exp)
-    obs_m, exp_m, acc_o, acc_e = [], [], 0.0, 0.0
-    for i in order:  # merge the smallest bins until expected >= 5
-        acc_o += counts[i]
-        acc_e += exp[i]
-        if acc_e >= 5:
-            obs_m.append(acc_o)
-            exp_m.append(acc_e)
-            acc_o = acc_e = 0.0
-    if acc_e > 0:
-        obs_m[-1] += acc_o
-        exp_m[-1] += acc_e
-    assert stats.chisquare(obs_m, exp_m).pvalue > 1e-3
+    assert merged_chisquare(bf, out) > 1e-3
 
 
 # --------------------------------------------------------- reductions / invariants
