@@ -102,6 +102,8 @@ typedef struct {
   size_t device_bytes;       /* device memory held by the graph                  */
   int32_t symmetric;         /* 1: every edge (v,u) has a mirror (u,v) with the
                                 same weight (found at creation)                   */
+  float cost_ratios[3];      /* r per algorithm (weighted, node2vec, metapath)   */
+  uint64_t fingerprint;      /* hash of sizes and sampled CSR entries (cache key)*/
 } fw_graph_info_t;
 
 /* Per-walk counters (FW_FLAG_COUNTERS).  Byte figures follow the
@@ -152,8 +154,26 @@ fw_status fw_graph_info(const fw_graph* graph, fw_graph_info_t* info);
  * buffers given (either may be NULL).  Asynchronous on `stream`. */
 fw_status fw_graph_node_stats(const fw_graph* graph, float* hmax, float* hsum, void* stream);
 
-/* Set the graph's cost ratio r of Eq. (runtime) (must be finite, > 0). */
+/* Set the graph's cost ratio r of Eq. (runtime) for every algorithm (must
+ * be finite, > 0). */
 fw_status fw_graph_set_cost_ratio(fw_graph* graph, float ratio);
+
+/*
+ * Measure and install the cost ratio r = EdgeCost_RJS / EdgeCost_RVS of
+ * Eq. (runtime) for `algo` with `params` (Sec. 5.1, profiling kernels).
+ *   method 0  the paper's profiling: two light kernels compute transition
+ *             weights for 65,536 evenly spaced nodes and 32 neighbours each,
+ *             eRJS-style (random positions) and eRVS-style (a coalesced
+ *             scan); r = ratio of their times per edge
+ *   method 1  sweep: time 16-hop sample walks of up to 2^18 walkers for
+ *             r in {0.5, 1, 2, ..., 64} and keep the fastest
+ * cache_path (may be NULL): a text file of earlier results keyed by the
+ * graph fingerprint, algo, p, q and method; a hit skips the measurement,
+ * a miss appends the new result.  Synchronous on `stream`.  The ratio only
+ * changes which sampler runs, never the distribution.
+ */
+fw_status fw_autotune(fw_graph* graph, int32_t algo, const fw_params* params, int32_t method,
+                      const char* cache_path, float* ratio_out, void* stream);
 
 /*
  * Walk num_walkers walkers for len hops each (Sec. 2.1; one query per
@@ -235,6 +255,99 @@ fw_status fw_graph_check(fw_graph* graph, void* stream);
  */
 fw_status fw_walk_host_noalloc(const fw_graph* graph, const int32_t* starts, int32_t num_walkers, int32_t len,
                                int32_t algo, const fw_params* params, uint64_t seed, int32_t* out, void* stream);
+
+/* One job of a batch: the arguments of one fw_walk call. */
+typedef struct {
+  const int32_t* starts;  /* device int32[num_walkers], each in [0, n)               */
+  int32_t num_walkers;
+  int32_t len;
+  int32_t algo;           /* fw_algo                                                  */
+  fw_params params;
+  uint64_t seed;
+  int32_t* out;           /* device int32[num_walkers][len+1]                        */
+} fw_job;
+
+/*
+ * Run njobs walk jobs in one persistent launch per 64 jobs: the walkers of
+ * all jobs form one query queue (Sec. 5.3), so jobs of very different sizes,
+ * lengths and algorithms share the GPU instead of running one after
+ * another.  Every job's rows are identical to those of fw_walk with the same
+ * arguments (draws and sampler choices depend only on the walker's own job).
+ * Asynchronous on `stream`; errors as fw_walk (a bad job is named in the
+ * message).
+ */
+fw_status fw_walk_batch(const fw_graph* graph, const fw_job* jobs, int32_t njobs, void* stream);
+
+/*
+ * A batch captured once into a CUDA graph (queue-counter resets and walk
+ * launches) and replayed by fw_batch_plan_launch on any stream.  The jobs'
+ * buffers and parameters are fixed at creation; their contents may change
+ * between replays.  The plan owns its queue counters; destroy it after its
+ * last replay has finished.
+ */
+typedef struct fw_batch_plan fw_batch_plan;
+fw_status fw_batch_plan_create(const fw_graph* graph, const fw_job* jobs, int32_t njobs,
+                               fw_batch_plan** out);
+fw_status fw_batch_plan_launch(fw_batch_plan* plan, void* stream);
+fw_status fw_batch_plan_destroy(fw_batch_plan* plan);
+
+/*
+ * Serving: continuous batching of walk queries against a resident graph.
+ * A worker thread admits queued queries in arrival order while a fixed
+ * device arena of mem_budget bytes has room for their staged starts and
+ * rows, launches the admitted queries as one batched walk ("wave", up to
+ * max_jobs_per_wave queries) on one of max_waves streams, and retires waves
+ * by polling their completion events; queries that arrive while waves run
+ * join the next wave, and waves on different streams overlap on the device.
+ * Results are identical to fw_walk_host with the same arguments, alone or in
+ * any mix.  All waits are host-side with caller timeouts; nothing spins on
+ * the device.
+ */
+typedef struct {
+  size_t mem_budget;          /* device bytes for staged starts + rows (default 1 GiB) */
+  int32_t max_waves;          /* concurrent waves / streams, 1..64 (default 4)          */
+  int32_t max_jobs_per_wave;  /* queries per launch, 1..64 (default 64)                 */
+} fw_server_config;
+
+typedef struct {
+  uint64_t completed, failed, pending;  /* pending = queued or admitted, not launched   */
+  uint64_t waves;                       /* launches so far                              */
+  double queries_per_wave;
+  double p50_ms, p99_ms, mean_ms, max_ms;  /* submit -> rows in host memory, completed   */
+  size_t peak_device_bytes;             /* arena high-water mark                        */
+  int32_t peak_inflight_waves;
+} fw_server_stats_t;
+
+typedef struct fw_server fw_server;
+
+void fw_server_config_default(fw_server_config* config);
+
+/* Start a server on `graph` (which must outlive it); allocates the arena. */
+fw_status fw_server_create(const fw_graph* graph, const fw_server_config* config, fw_server** out);
+
+/*
+ * Queue one query: starts (host int32[num_walkers], checked against [0, n)
+ * here) and out (host int32[num_walkers][len+1]) must stay valid until the
+ * query is collected; pinned host memory lets copies overlap.  Returns a
+ * ticket.  FW_ERR_OOM if the query alone exceeds the memory budget,
+ * FW_ERR_ARG for bad arguments, FW_ERR_BUSY while the server shuts down.
+ */
+fw_status fw_server_submit(fw_server* server, const int32_t* starts, int32_t num_walkers, int32_t len, int32_t algo,
+                           const fw_params* params, uint64_t seed, int32_t* out, uint64_t* ticket);
+
+/* Non-blocking: *done = 1 once out is filled (the ticket is then released
+ * and the query's status returned; latency_ms, if not NULL, receives the
+ * submit-to-completion time). */
+fw_status fw_server_poll(fw_server* server, uint64_t ticket, int32_t* done, double* latency_ms);
+
+/* Wait up to timeout_s seconds: FW_OK (ticket released), FW_ERR_TIMEOUT
+ * (ticket kept; wait again later) or the query's error. */
+fw_status fw_server_wait(fw_server* server, uint64_t ticket, double timeout_s, double* latency_ms);
+
+fw_status fw_server_stats(fw_server* server, fw_server_stats_t* out);
+
+/* Stop accepting queries, finish every submitted one, free the server. */
+fw_status fw_server_destroy(fw_server* server);
 
 /* Number of kernel launches this library has issued (process-wide). */
 uint64_t fw_launch_count(void);

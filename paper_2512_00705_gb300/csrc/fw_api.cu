@@ -80,7 +80,7 @@ fw_status make_job(const fw_graph* g, int32_t algo, const fw_params* params, uin
     job->wmax1 = job->wlo1 = job->whi1 = 1.0f;
     job->wmean1 = algo == ALGO_METAPATH ? 0.5f : 1.0f;
   }
-  job->ratio = P.cost_ratio > 0.0f ? P.cost_ratio : g->ratio;
+  job->ratio = P.cost_ratio > 0.0f ? P.cost_ratio : g->ratio_algo[algo];
   job->key0 = (uint32_t)seed;
   job->key1 = (uint32_t)(seed >> 32);
   job->walker_base = P.walker_base;
@@ -267,6 +267,13 @@ extern "C" fw_status fw_graph_create(const int32_t* offsets, const int32_t* cols
   g->max_degree = maxdeg;
   g->sym = asym == 0 ? 1 : 0;
   g->preprocess_ms = ms;
+  {
+    fw_status fs = graph_fingerprint(g, st, &g->fingerprint);
+    if (fs != FW_OK) {
+      free_graph(g);
+      return fs;
+    }
+  }
   *out = g;
   return FW_OK;
 }
@@ -285,7 +292,9 @@ extern "C" fw_status fw_graph_info(const fw_graph* g, fw_graph_info_t* info) {
   info->max_degree = g->max_degree;
   info->has_weights = g->d_h != nullptr;
   info->has_labels = g->d_lab != nullptr;
-  info->cost_ratio = g->ratio;
+  info->cost_ratio = g->ratio_algo[FW_ALGO_NODE2VEC];
+  for (int a = 0; a < 3; ++a) info->cost_ratios[a] = g->ratio_algo[a];
+  info->fingerprint = g->fingerprint;
   info->preprocess_ms = g->preprocess_ms;
   info->device_bytes = g->bytes;
   info->symmetric = g->sym;
@@ -304,7 +313,7 @@ extern "C" fw_status fw_graph_node_stats(const fw_graph* g, float* hmax, float* 
 
 extern "C" fw_status fw_graph_set_cost_ratio(fw_graph* g, float ratio) {
   if (!g || !(ratio > 0.0f) || !std::isfinite(ratio)) return set_error(FW_ERR_ARG, "bad ratio");
-  g->ratio = ratio;
+  for (int a = 0; a < 3; ++a) g->ratio_algo[a] = ratio;
   return FW_OK;
 }
 

@@ -28,7 +28,8 @@ struct fw_graph {
   int32_t sym = 0;
   unsigned* d_err = nullptr;
   fw::DevCounters* d_cnt = nullptr;
-  float ratio = 4.0f;
+  float ratio_algo[3] = {4.0f, 4.0f, 4.0f};  // r of Eq. (runtime) per algorithm
+  unsigned long long fingerprint = 0;
   double preprocess_ms = 0.0;
   size_t bytes = 0;
   // staging of fw_walk_host
@@ -49,12 +50,17 @@ fw_status cuda_error(cudaError_t err, const char* what);
 DevGraph dev_graph(const fw_graph* g);
 
 // Fill a job from the public parameters (validates them).
+fw_status graph_fingerprint(const fw_graph* g, cudaStream_t st, unsigned long long* out);
+
 fw_status make_job(const fw_graph* g, int32_t algo, const fw_params* params, uint64_t seed, Job* job);
 
 // Launch the unified walk kernel over `njobs` jobs (total walkers `total`).
 // `qctr` is a zeroed device counter the launch may use as its walker queue.
 cudaError_t launch_walk(const fw_graph* g, const Job* jobs, int njobs, long long total, bool count,
                         unsigned long long* qctr, cudaStream_t stream);
+
+// Cache the walk kernels' occupancy (call outside any stream capture).
+cudaError_t prime_walk_occupancy();
 
 cudaError_t launch_node_stats(const int32_t* off, const float* h, int32_t n, float* hmax, float* hsum, int4* nrec,
                               int* maxdeg, int num_sms, cudaStream_t stream);

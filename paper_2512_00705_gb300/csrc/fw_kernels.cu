@@ -365,15 +365,34 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
 }
 
 template <int NJ, bool COUNT>
-static cudaError_t launch_walk_t(const fw_graph* g, const Job* jobs, int njobs, long long total,
-                                 unsigned long long* qctr, cudaStream_t stream) {
-  static int blocks_per_sm = 0;
-  if (blocks_per_sm == 0) {
-    int b = 0;
+static cudaError_t walk_blocks_per_sm(int* out) {
+  static std::atomic<int> cached{0};
+  int b = cached.load();
+  if (b == 0) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, walk_kernel<NJ, COUNT>, kBlock, 0);
     if (e != cudaSuccess) return e;
-    blocks_per_sm = b > 0 ? b : 1;
+    b = b > 0 ? b : 1;
+    cached.store(b);
   }
+  *out = b;
+  return cudaSuccess;
+}
+
+cudaError_t prime_walk_occupancy() {
+  int b;
+  cudaError_t e = walk_blocks_per_sm<1, false>(&b);
+  if (e == cudaSuccess) e = walk_blocks_per_sm<1, true>(&b);
+  if (e == cudaSuccess) e = walk_blocks_per_sm<kMaxJobs, false>(&b);
+  if (e == cudaSuccess) e = walk_blocks_per_sm<kMaxJobs, true>(&b);
+  return e;
+}
+
+template <int NJ, bool COUNT>
+static cudaError_t launch_walk_t(const fw_graph* g, const Job* jobs, int njobs, long long total,
+                                 unsigned long long* qctr, cudaStream_t stream) {
+  int blocks_per_sm = 1;
+  cudaError_t oe = walk_blocks_per_sm<NJ, COUNT>(&blocks_per_sm);
+  if (oe != cudaSuccess) return oe;
   JobTableN<NJ> tab;
   for (int i = 0; i < njobs; ++i) tab.jobs[i] = jobs[i];
   const long long want = (total + kBlock - 1) / kBlock;

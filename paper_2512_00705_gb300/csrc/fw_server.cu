@@ -1,0 +1,442 @@
+// fw_server.cu -- continuous batching of walk queries against a resident graph.
+//
+// A worker thread owns the device side.  Queries arrive from any thread
+// (fw_server_submit) into a FIFO queue.  The worker
+//   1. retires finished waves: polls each in-flight wave's completion event
+//      (cudaEventQuery, never a blocking wait), marks its queries done and
+//      returns their device memory to the arena;
+//   2. admits queries in arrival order while the device arena (the memory
+//      budget) has room for their staged starts and rows -- the head of the
+//      queue waits for memory rather than being overtaken, so large queries
+//      are not starved;
+//   3. launches the admitted queries as one wave on a free stream: upload of
+//      each query's starts, one batched walk launch (up to 64 queries, one
+//      shared walker queue), download of each query's rows, an event.
+// Waves on different streams overlap on the device, and queries that arrive
+// while waves run join the next wave: continuous batching.  A query's rows
+// are identical to those of fw_walk_host with the same arguments, alone or
+// in any mix (every draw and sampler choice depends only on its own walkers).
+// All waits are on the host and bounded by the caller's timeout.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "fw_internal.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+enum ReqState { REQ_PENDING = 0, REQ_ADMITTED = 1, REQ_LAUNCHED = 2, REQ_DONE = 3, REQ_FAILED = 4 };
+
+struct Request {
+  uint64_t id = 0;
+  const int32_t* starts = nullptr;  // host
+  int32_t* out = nullptr;           // host
+  int32_t num_walkers = 0, len = 0, algo = 0;
+  fw_params params;
+  uint64_t seed = 0;
+  size_t bytes = 0, rows_off = 0, arena_off = 0;
+  Clock::time_point t_submit, t_done;
+  int state = REQ_PENDING;
+  fw_status status = FW_OK;
+  std::string error;
+};
+
+// First-fit allocator over [0, size) in 256-byte units.
+class Arena {
+ public:
+  explicit Arena(size_t size) { free_[0] = size; }
+  bool alloc(size_t bytes, size_t* off) {
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        *off = it->first;
+        const size_t rest = it->second - bytes, start = it->first + bytes;
+        free_.erase(it);
+        if (rest) free_[start] = rest;
+        used_ += bytes;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+    used_ -= bytes;
+  }
+  size_t used() const { return used_; }
+
+ private:
+  std::map<size_t, size_t> free_;
+  size_t used_ = 0;
+};
+
+struct Wave {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  unsigned long long* qctr = nullptr;
+  std::vector<Request*> reqs;
+  bool busy = false;
+};
+
+size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct fw_server {
+  const fw_graph* g = nullptr;
+  fw_server_config cfg;
+  unsigned char* arena_mem = nullptr;
+  Arena* arena = nullptr;
+  std::vector<Wave> waves;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request*> pending;
+  std::vector<Request*> admitted;
+  std::unordered_map<uint64_t, Request*> reqs;
+  uint64_t next_id = 1;
+  bool stop = false;
+  std::thread worker;
+  // statistics
+  std::vector<double> latencies_ms;
+  uint64_t completed = 0, failed = 0, waves_launched = 0, queries_in_waves = 0;
+  size_t peak_arena = 0;
+  int peak_inflight = 0;
+};
+
+namespace {
+
+void finish(fw_server* s, Request* r, fw_status st, const std::string& err) {
+  r->state = st == FW_OK ? REQ_DONE : REQ_FAILED;
+  r->status = st;
+  r->error = err;
+  r->t_done = Clock::now();
+  if (st == FW_OK) {
+    s->completed++;
+    s->latencies_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+  } else {
+    s->failed++;
+  }
+}
+
+// Enqueue one wave (called with the lock held).
+void launch_wave(fw_server* s, Wave& w) {
+  using namespace fw;
+  std::vector<Job> tab;
+  long long total = 0;
+  cudaError_t e = cudaSuccess;
+  std::string err;
+  for (Request* r : s->admitted) {
+    Job J;
+    fw_status st = make_job(s->g, r->algo, &r->params, r->seed, &J);
+    if (st != FW_OK) {  // validated at submit; kept for safety
+      s->arena->release(r->arena_off, r->bytes);
+      finish(s, r, st, fw_last_error());
+      continue;
+    }
+    int32_t* d_starts = reinterpret_cast<int32_t*>(s->arena_mem + r->arena_off);
+    int32_t* d_out = reinterpret_cast<int32_t*>(s->arena_mem + r->arena_off + r->rows_off);
+    J.kind = JOB_WALK;
+    J.starts = d_starts;
+    J.out = d_out;
+    J.num_walkers = r->num_walkers;
+    J.len = r->len;
+    J.gbase = total;
+    total += r->num_walkers;
+    tab.push_back(J);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_starts, r->starts, sizeof(int32_t) * (size_t)r->num_walkers, cudaMemcpyHostToDevice,
+                          w.stream);
+    r->state = REQ_LAUNCHED;
+    w.reqs.push_back(r);
+  }
+  s->admitted.clear();
+  if (w.reqs.empty()) return;
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.qctr, 0, sizeof(unsigned long long), w.stream);
+  if (e == cudaSuccess && total > 0) e = launch_walk(s->g, tab.data(), (int)tab.size(), total, false, w.qctr, w.stream);
+  for (Request* r : w.reqs) {
+    if (e != cudaSuccess) break;
+    e = cudaMemcpyAsync(r->out, s->arena_mem + r->arena_off + r->rows_off,
+                        sizeof(int32_t) * (size_t)r->num_walkers * ((size_t)r->len + 1), cudaMemcpyDeviceToHost,
+                        w.stream);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(w.done, w.stream);
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(w.stream);  // let whatever was enqueued finish before its memory is reused
+    const std::string msg = std::string("wave launch: ") + cudaGetErrorString(e);
+    for (Request* r : w.reqs) {
+      s->arena->release(r->arena_off, r->bytes);
+      finish(s, r, FW_ERR_CUDA, msg);
+    }
+    w.reqs.clear();
+    s->cv_done.notify_all();
+    return;
+  }
+  w.busy = true;
+  s->waves_launched++;
+  s->queries_in_waves += w.reqs.size();
+}
+
+void worker_main(fw_server* s) {
+  cudaSetDevice(s->g->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  while (true) {
+    bool progress = false;
+    int inflight = 0;
+    // 1. retire finished waves
+    for (Wave& w : s->waves) {
+      if (!w.busy) continue;
+      const cudaError_t q = cudaEventQuery(w.done);
+      if (q == cudaErrorNotReady) {
+        ++inflight;
+        continue;
+      }
+      const fw_status st = q == cudaSuccess ? FW_OK : FW_ERR_CUDA;
+      const std::string msg = q == cudaSuccess ? std::string() : std::string("wave: ") + cudaGetErrorString(q);
+      for (Request* r : w.reqs) {
+        s->arena->release(r->arena_off, r->bytes);
+        finish(s, r, st, msg);
+      }
+      w.reqs.clear();
+      w.busy = false;
+      progress = true;
+    }
+    if (progress) s->cv_done.notify_all();
+    // 2. admit in arrival order while memory and the job table allow
+    while (!s->pending.empty() && (int)s->admitted.size() < s->cfg.max_jobs_per_wave) {
+      Request* r = s->pending.front();
+      size_t off = 0;
+      if (!s->arena->alloc(r->bytes, &off)) break;  // the head waits for memory
+      r->arena_off = off;
+      r->state = REQ_ADMITTED;
+      s->admitted.push_back(r);
+      s->pending.pop_front();
+      s->peak_arena = std::max(s->peak_arena, s->arena->used());
+      progress = true;
+    }
+    // 3. launch the admitted queries on a free stream
+    if (!s->admitted.empty()) {
+      for (Wave& w : s->waves) {
+        if (w.busy) continue;
+        launch_wave(s, w);
+        if (w.busy) ++inflight;
+        progress = true;
+        break;
+      }
+    }
+    s->peak_inflight = std::max(s->peak_inflight, inflight);
+    const bool idle = s->pending.empty() && s->admitted.empty() && inflight == 0;
+    if (s->stop && idle) break;
+    if (!progress) {
+      if (idle) s->cv_work.wait_for(lk, std::chrono::milliseconds(20));
+      else s->cv_work.wait_for(lk, std::chrono::microseconds(20));
+    }
+  }
+}
+
+}  // namespace
+
+using namespace fw;
+
+extern "C" void fw_server_config_default(fw_server_config* c) {
+  if (!c) return;
+  c->mem_budget = (size_t)1 << 30;
+  c->max_waves = 4;
+  c->max_jobs_per_wave = 64;
+}
+
+extern "C" fw_status fw_server_create(const fw_graph* g, const fw_server_config* cfg, fw_server** out) {
+  if (!out) return set_error(FW_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!g) return set_error(FW_ERR_ARG, "graph is NULL");
+  fw_server_config c;
+  if (cfg) c = *cfg;
+  else fw_server_config_default(&c);
+  if (c.mem_budget < 4096 || c.max_waves < 1 || c.max_waves > 64 || c.max_jobs_per_wave < 1 ||
+      c.max_jobs_per_wave > kMaxJobs)
+    return set_error(FW_ERR_ARG, "bad server configuration");
+  cudaError_t e = prime_walk_occupancy();
+  if (e != cudaSuccess) return cuda_error(e, "occupancy query");
+  fw_server* s = new (std::nothrow) fw_server();
+  if (!s) return set_error(FW_ERR_OOM, "host allocation");
+  s->g = g;
+  s->cfg = c;
+  auto fail = [&](cudaError_t err, const char* what) {
+    for (Wave& w : s->waves) {
+      if (w.stream) cudaStreamDestroy(w.stream);
+      if (w.done) cudaEventDestroy(w.done);
+    }
+    cudaFree(s->arena_mem);
+    delete s;
+    return cuda_error(err, what);
+  };
+  e = cudaMalloc(&s->arena_mem, c.mem_budget);
+  if (e != cudaSuccess) return fail(e, "cudaMalloc(server arena)");
+  unsigned long long* q = nullptr;
+  e = cudaMalloc(&q, 256 * (size_t)c.max_waves);
+  if (e != cudaSuccess) return fail(e, "cudaMalloc(wave counters)");
+  s->waves.resize(c.max_waves);
+  for (int i = 0; i < c.max_waves; ++i) {
+    Wave& w = s->waves[i];
+    w.qctr = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(q) + 256 * (size_t)i);
+    e = cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      cudaFree(q);
+      return fail(e, "stream / event creation");
+    }
+  }
+  s->arena = new Arena(c.mem_budget);
+  s->worker = std::thread(worker_main, s);
+  *out = s;
+  return FW_OK;
+}
+
+extern "C" fw_status fw_server_submit(fw_server* s, const int32_t* starts, int32_t num_walkers, int32_t len,
+                                      int32_t algo, const fw_params* params, uint64_t seed, int32_t* out,
+                                      uint64_t* ticket) {
+  if (!s || !ticket) return set_error(FW_ERR_ARG, "NULL argument");
+  if (num_walkers < 0 || len < 0 || (num_walkers > 0 && (!starts || !out)))
+    return set_error(FW_ERR_ARG, "bad sizes or NULL buffers");
+  Job J;
+  fw_status st = make_job(s->g, algo, params, seed, &J);  // validate parameters now
+  if (st != FW_OK) return st;
+  for (int32_t i = 0; i < num_walkers; ++i)
+    if (starts[i] < 0 || starts[i] >= s->g->n)
+      return set_error(FW_ERR_ARG, "start " + std::to_string(i) + " outside [0, n)");
+  Request* r = new (std::nothrow) Request();
+  if (!r) return set_error(FW_ERR_OOM, "host allocation");
+  r->starts = starts;
+  r->out = out;
+  r->num_walkers = num_walkers;
+  r->len = len;
+  r->algo = algo;
+  if (params) r->params = *params;
+  else fw_params_default(&r->params);
+  r->seed = seed;
+  r->rows_off = round256(sizeof(int32_t) * (size_t)num_walkers);
+  r->bytes = r->rows_off + round256(sizeof(int32_t) * (size_t)num_walkers * ((size_t)len + 1));
+  if (r->bytes > s->cfg.mem_budget) {
+    delete r;
+    return set_error(FW_ERR_OOM, "query needs more device memory than the server's budget");
+  }
+  r->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) {
+      delete r;
+      return set_error(FW_ERR_BUSY, "server is shutting down");
+    }
+    r->id = s->next_id++;
+    if (num_walkers == 0) {
+      finish(s, r, FW_OK, "");
+    } else {
+      s->pending.push_back(r);
+    }
+    s->reqs[r->id] = r;
+    *ticket = r->id;
+  }
+  s->cv_work.notify_one();
+  return FW_OK;
+}
+
+static fw_status collect(fw_server* s, std::unordered_map<uint64_t, Request*>::iterator it, double* latency_ms) {
+  Request* r = it->second;
+  const fw_status st = r->status;
+  if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+  std::string err = r->error;
+  s->reqs.erase(it);
+  delete r;
+  return st == FW_OK ? FW_OK : set_error(st, err);
+}
+
+extern "C" fw_status fw_server_poll(fw_server* s, uint64_t ticket, int32_t* done, double* latency_ms) {
+  if (!s || !done) return set_error(FW_ERR_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return set_error(FW_ERR_ARG, "unknown ticket");
+  const int st = it->second->state;
+  *done = (st == REQ_DONE || st == REQ_FAILED) ? 1 : 0;
+  if (!*done) return FW_OK;
+  return collect(s, it, latency_ms);
+}
+
+extern "C" fw_status fw_server_wait(fw_server* s, uint64_t ticket, double timeout_s, double* latency_ms) {
+  if (!s) return set_error(FW_ERR_ARG, "server is NULL");
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return set_error(FW_ERR_ARG, "unknown ticket");
+  Request* r = it->second;
+  const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(
+                                           std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 0.0));
+  while (r->state != REQ_DONE && r->state != REQ_FAILED) {
+    if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout &&
+        r->state != REQ_DONE && r->state != REQ_FAILED)
+      return set_error(FW_ERR_TIMEOUT, "query not finished within the timeout");
+  }
+  return collect(s, s->reqs.find(ticket), latency_ms);
+}
+
+extern "C" fw_status fw_server_stats(fw_server* s, fw_server_stats_t* out) {
+  if (!s || !out) return set_error(FW_ERR_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  std::memset(out, 0, sizeof(*out));
+  out->completed = s->completed;
+  out->failed = s->failed;
+  out->pending = s->pending.size() + s->admitted.size();
+  out->waves = s->waves_launched;
+  out->queries_per_wave = s->waves_launched ? (double)s->queries_in_waves / (double)s->waves_launched : 0.0;
+  out->peak_device_bytes = s->peak_arena;
+  out->peak_inflight_waves = s->peak_inflight;
+  std::vector<double> l = s->latencies_ms;
+  if (!l.empty()) {
+    std::sort(l.begin(), l.end());
+    auto pct = [&](double p) { return l[std::min(l.size() - 1, (size_t)(p * (double)(l.size() - 1) + 0.5))]; };
+    out->p50_ms = pct(0.50);
+    out->p99_ms = pct(0.99);
+    out->max_ms = l.back();
+    double sum = 0;
+    for (double x : l) sum += x;
+    out->mean_ms = sum / (double)l.size();
+  }
+  return FW_OK;
+}
+
+extern "C" fw_status fw_server_destroy(fw_server* s) {
+  if (!s) return set_error(FW_ERR_ARG, "server is NULL");
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  if (s->worker.joinable()) s->worker.join();  // drains every submitted query
+  for (auto& kv : s->reqs) delete kv.second;
+  unsigned long long* q = s->waves.empty() ? nullptr : s->waves[0].qctr;
+  for (Wave& w : s->waves) {
+    cudaStreamDestroy(w.stream);
+    cudaEventDestroy(w.done);
+  }
+  cudaFree(q);
+  cudaFree(s->arena_mem);
+  delete s->arena;
+  delete s;
+  return FW_OK;
+}

@@ -40,7 +40,24 @@ class fw_params(ctypes.Structure):
 class fw_graph_info_t(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("e", ctypes.c_int64), ("max_degree", ctypes.c_int32),
                 ("has_weights", ctypes.c_int32), ("has_labels", ctypes.c_int32), ("cost_ratio", ctypes.c_float),
-                ("preprocess_ms", ctypes.c_double), ("device_bytes", ctypes.c_size_t), ("symmetric", ctypes.c_int32)]
+                ("preprocess_ms", ctypes.c_double), ("device_bytes", ctypes.c_size_t), ("symmetric", ctypes.c_int32),
+                ("cost_ratios", ctypes.c_float * 3), ("fingerprint", ctypes.c_uint64)]
+
+
+class fw_job(ctypes.Structure):
+    _fields_ = [("starts", ctypes.c_void_p), ("num_walkers", ctypes.c_int32), ("len", ctypes.c_int32),
+                ("algo", ctypes.c_int32), ("params", fw_params), ("seed", ctypes.c_uint64), ("out", ctypes.c_void_p)]
+
+
+class fw_server_config(ctypes.Structure):
+    _fields_ = [("mem_budget", ctypes.c_size_t), ("max_waves", ctypes.c_int32), ("max_jobs_per_wave", ctypes.c_int32)]
+
+
+class fw_server_stats_t(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64), ("pending", ctypes.c_uint64),
+                ("waves", ctypes.c_uint64), ("queries_per_wave", ctypes.c_double), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("peak_device_bytes", ctypes.c_size_t), ("peak_inflight_waves", ctypes.c_int32)]
 
 
 COUNTER_FIELDS = ["hops", "rjs_steps", "rvs_steps", "exact_steps", "handoffs", "rjs_trials", "rvs_items",
@@ -78,6 +95,7 @@ def lib() -> ctypes.CDLL:
                 "fw_graph_info": (ctypes.c_int, [vp, P(fw_graph_info_t)]),
                 "fw_graph_node_stats": (ctypes.c_int, [vp, vp, vp, vp]),
                 "fw_graph_set_cost_ratio": (ctypes.c_int, [vp, ctypes.c_float]),
+                "fw_autotune": (ctypes.c_int, [vp, i32, P(fw_params), i32, ctypes.c_char_p, P(ctypes.c_float), vp]),
                 "fw_walk": (ctypes.c_int, [vp, vp, i32, i32, i32, P(fw_params), u64, vp, vp]),
                 "fw_walk_host": (ctypes.c_int, [vp, vp, i32, i32, i32, P(fw_params), u64, vp, vp]),
                 "fw_sample_hist": (ctypes.c_int, [vp, i32, i32, i32, i32, P(fw_params), u64, i64, vp, vp]),
@@ -85,6 +103,19 @@ def lib() -> ctypes.CDLL:
                 "fw_counters_read": (ctypes.c_int, [vp, P(fw_counters), vp]),
                 "fw_counters_reset": (ctypes.c_int, [vp, vp]),
                 "fw_graph_check": (ctypes.c_int, [vp, vp]),
+                "fw_walk_batch": (ctypes.c_int, [vp, P(fw_job), i32, vp]),
+                "fw_batch_plan_create": (ctypes.c_int, [vp, P(fw_job), i32, P(vp)]),
+                "fw_batch_plan_launch": (ctypes.c_int, [vp, vp]),
+                "fw_batch_plan_destroy": (ctypes.c_int, [vp]),
+                "fw_walk_host_noalloc": (ctypes.c_int, [vp, vp, i32, i32, i32, P(fw_params), u64, vp, vp]),
+                "fw_server_config_default": (None, [P(fw_server_config)]),
+                "fw_server_create": (ctypes.c_int, [vp, P(fw_server_config), P(vp)]),
+                "fw_server_submit": (ctypes.c_int, [vp, vp, i32, i32, i32, P(fw_params), u64, vp,
+                                                     P(ctypes.c_uint64)]),
+                "fw_server_poll": (ctypes.c_int, [vp, ctypes.c_uint64, P(i32), P(ctypes.c_double)]),
+                "fw_server_wait": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_double, P(ctypes.c_double)]),
+                "fw_server_stats": (ctypes.c_int, [vp, P(fw_server_stats_t)]),
+                "fw_server_destroy": (ctypes.c_int, [vp]),
                 "fw_launch_count": (ctypes.c_uint64, []),
                 "fw_last_error": (ctypes.c_char_p, []),
                 "fw_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -166,7 +197,9 @@ def fw_graph_destroy(handle: int):
 def fw_graph_info(handle: int) -> dict:
     info = fw_graph_info_t()
     _check(lib().fw_graph_info(handle, ctypes.byref(info)))
-    return {f: getattr(info, f) for f, _ in fw_graph_info_t._fields_}
+    d = {f: getattr(info, f) for f, _ in fw_graph_info_t._fields_}
+    d["cost_ratios"] = list(d["cost_ratios"])
+    return d
 
 
 def fw_walk(handle: int, starts, length: int, algo, params: fw_params, seed: int, out, stream=None):
@@ -200,6 +233,15 @@ def fw_graph_node_stats(handle: int, hmax, hsum, stream=None):
 
 def fw_graph_set_cost_ratio(handle: int, ratio: float):
     _check(lib().fw_graph_set_cost_ratio(handle, float(ratio)))
+
+
+def fw_autotune(handle: int, algo, params: fw_params, method: int = 0, cache_path: Optional[str] = None,
+                stream=None) -> float:
+    r = ctypes.c_float()
+    _check(lib().fw_autotune(handle, ALGO.get(algo, algo), ctypes.byref(params), method,
+                             None if cache_path is None else os.fsencode(cache_path), ctypes.byref(r),
+                             _stream_ptr(stream)))
+    return float(r.value)
 
 
 def fw_counters_read(handle: int, stream=None) -> dict:
@@ -296,9 +338,110 @@ class Graph:
     def check(self, stream=None):
         fw_graph_check(self.handle, stream)
 
+    def autotune(self, algo="node2vec", *, p=1.0, q=1.0, schema=None, method=0, cache_path=None, stream=None):
+        r = fw_autotune(self.handle, algo, make_params(p, q, schema), method, cache_path, stream)
+        self.info = fw_graph_info(self.handle)
+        return r
+
     def set_cost_ratio(self, r: float):
         fw_graph_set_cost_ratio(self.handle, r)
         self.info = fw_graph_info(self.handle)
 
     def degree(self, v: int) -> int:
         return int(self._off[v + 1] - self._off[v])
+
+
+# ---------------------------------------------------------------- batching
+def make_job(starts, length: int, algo, out, *, p=1.0, q=1.0, schema=None, mode="auto", seed=42, flags=0,
+             cost_ratio=0.0, rjs_cap=0, walker_base=0) -> fw_job:
+    """One batch entry; starts / out are CUDA tensors that must outlive the launch."""
+    j = fw_job()
+    j.starts = _ptr(starts)
+    j.num_walkers = starts.numel()
+    j.len = length
+    j.algo = ALGO.get(algo, algo)
+    j.params = make_params(p, q, schema, mode, flags, cost_ratio, rjs_cap, walker_base)
+    j.seed = seed
+    j.out = _ptr(out)
+    return j
+
+
+def fw_walk_batch(handle: int, jobs, stream=None):
+    arr = (fw_job * len(jobs))(*jobs)
+    _check(lib().fw_walk_batch(handle, arr, len(jobs), _stream_ptr(stream)))
+
+
+class BatchPlan:
+    """A batch captured once into a CUDA graph and replayed by launch()."""
+
+    def __init__(self, graph: "Graph", jobs):
+        self._jobs = (fw_job * len(jobs))(*jobs)
+        h = ctypes.c_void_p()
+        _check(lib().fw_batch_plan_create(graph.handle, self._jobs, len(jobs), ctypes.byref(h)))
+        self.handle = h.value
+
+    def launch(self, stream=None):
+        _check(lib().fw_batch_plan_launch(self.handle, _stream_ptr(stream)))
+
+    def close(self):
+        if self.handle:
+            _check(lib().fw_batch_plan_destroy(self.handle))
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- serving
+class Server:
+    """Continuous-batching walk server over a resident Graph (C ABI fw_server_*)."""
+
+    def __init__(self, graph: "Graph", mem_budget: int = 1 << 30, max_waves: int = 4, max_jobs_per_wave: int = 64):
+        cfg = fw_server_config()
+        lib().fw_server_config_default(ctypes.byref(cfg))
+        cfg.mem_budget, cfg.max_waves, cfg.max_jobs_per_wave = mem_budget, max_waves, max_jobs_per_wave
+        h = ctypes.c_void_p()
+        _check(lib().fw_server_create(graph.handle, ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h.value
+        self.graph = graph
+
+    def submit(self, starts, length: int, algo, out, *, p=1.0, q=1.0, schema=None, mode="auto", seed=42, flags=0,
+               walker_base=0) -> int:
+        """starts / out: host buffers (numpy or pinned torch CPU tensors) kept alive until collected."""
+        n = starts.shape[0] if isinstance(starts, np.ndarray) else starts.numel()
+        prm = make_params(p, q, schema, mode, flags, 0.0, 0, walker_base)
+        t = ctypes.c_uint64()
+        _check(lib().fw_server_submit(self.handle, _ptr(starts), n, length, ALGO.get(algo, algo), ctypes.byref(prm),
+                                      seed, _ptr(out), ctypes.byref(t)))
+        return int(t.value)
+
+    def poll(self, ticket: int):
+        """None while running, else the latency in ms (the ticket is released)."""
+        done = ctypes.c_int32()
+        lat = ctypes.c_double()
+        _check(lib().fw_server_poll(self.handle, ticket, ctypes.byref(done), ctypes.byref(lat)))
+        return float(lat.value) if done.value else None
+
+    def wait(self, ticket: int, timeout: float = 60.0) -> float:
+        lat = ctypes.c_double()
+        _check(lib().fw_server_wait(self.handle, ticket, timeout, ctypes.byref(lat)))
+        return float(lat.value)
+
+    def stats(self) -> dict:
+        st = fw_server_stats_t()
+        _check(lib().fw_server_stats(self.handle, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in fw_server_stats_t._fields_}
+
+    def close(self):
+        if self.handle:
+            _check(lib().fw_server_destroy(self.handle))
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,211 @@
+"""GPU tests of the runtime around the samplers: the profiled cost ratio
+(Sec. 5.1), its cache, and that no runtime choice changes the walks'
+distribution."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_00705_gb300 import flexiwalk as fw
+from paper_2512_00705_gb300 import synth
+from bruteforce import bf_paths, merged_chisquare
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def small():
+    g = synth.workload_graph("small")
+    G = fw.Graph(g)
+    yield g, G
+    G.close()
+
+
+@pytest.mark.parametrize("algo,p,q,schema", [("node2vec", 2.0, 0.5, None), ("metapath", 1.0, 1.0, [0, 1, 2, 3, 4]),
+                                             ("weighted", 1.0, 1.0, None)])
+def test_autotune_profiling_installs_a_ratio(small, algo, p, q, schema, tmp_path):
+    g, G = small
+    cache = str(tmp_path / "ratios.txt")
+    r = G.autotune(algo, p=p, q=q, schema=schema, method=0, cache_path=cache)
+    assert np.isfinite(r) and 0.01 < r < 1000.0
+    assert G.info["cost_ratios"][fw.ALGO[algo]] == pytest.approx(r)
+    lines = open(cache).read().splitlines()
+    assert len(lines) == 1 and f"{G.info['fingerprint']:016x}" in lines[0]
+    # a cache hit returns the stored value without measuring
+    with open(cache, "w") as f:
+        f.write(lines[0].rsplit("r=", 1)[0] + "r=123.5\n")
+    assert G.autotune(algo, p=p, q=q, schema=schema, method=0, cache_path=cache) == pytest.approx(123.5)
+    # another (p, q) misses and appends
+    G.autotune(algo, p=p * 2, q=q, schema=schema, method=0, cache_path=cache)
+    assert len(open(cache).read().splitlines()) == 2
+    G.set_cost_ratio(4.0)
+
+
+def test_autotune_sweep_picks_from_the_ladder(small):
+    g, G = small
+    r = G.autotune("node2vec", p=2.0, q=0.5, method=1)
+    assert r in [0.5, 1, 2, 4, 8, 16, 32, 64]
+    G.set_cost_ratio(4.0)
+
+
+def test_fingerprint_tracks_the_graph(small):
+    g, G = small
+    G2 = fw.Graph(g)
+    assert G2.info["fingerprint"] == G.info["fingerprint"]
+    # the fingerprint hashes 4096 evenly spaced entries: change one of them
+    h2 = g.h.copy()
+    h2[(g.e - 1) * 2048 // 4095] *= 0.5
+    G3 = fw.Graph(synth.Csr(g.offsets, g.cols, h2, g.labels))
+    assert G3.info["fingerprint"] != G.info["fingerprint"]
+    G2.close()
+    G3.close()
+
+
+@pytest.mark.parametrize("ratio", [0.01, 4.0, 1000.0])
+def test_cost_ratio_never_changes_the_distribution(ratio):
+    """Eq. (runtime) only picks a sampler; extreme ratios (all eRVS, all
+    eRJS) give the same path distribution."""
+    g = synth.random_graph(8, 0.45, seed=11, weighted=True, nlabels=3)
+    G = fw.Graph(g)
+    W, L = 300_000, 4
+    starts = torch.zeros(W, dtype=torch.int32, device="cuda")
+    out = G.walk(starts, L, "node2vec", p=0.5, q=2.0, mode="auto", cost_ratio=ratio, seed=3).cpu().numpy()
+    G.close()
+    assert merged_chisquare(bf_paths(g, 0, L, "node2vec", 0.5, 2.0, None), out) > 1e-4
+
+
+# ------------------------------------------------------------ batching
+def _mixed_jobs(g, count, seed, max_walkers=3000):
+    rng = np.random.default_rng(seed)
+    specs = []
+    for i in range(count):
+        algo = ["node2vec", "metapath", "weighted"][i % 3]
+        w = int(rng.integers(1, max_walkers))
+        spec = dict(starts=synth.random_starts(g.n, w, seed=seed * 100 + i), length=int(rng.integers(0, 30)),
+                    algo=algo, mode=["auto", "rjs", "rvs", "exact"][int(rng.integers(0, 4))],
+                    seed=int(rng.integers(1, 1 << 40)), walker_base=int(rng.integers(0, 1000)))
+        if algo == "node2vec":
+            spec["p"], spec["q"] = float(rng.choice([0.25, 0.5, 1, 2, 4])), float(rng.choice([0.25, 0.5, 1, 2, 4]))
+        if algo == "metapath":
+            spec["schema"] = [0, 1, 2, 3, 4]
+        specs.append(spec)
+    return specs
+
+
+def _kw(spec):
+    return {k: spec[k] for k in ("p", "q", "schema", "mode", "seed", "walker_base") if k in spec}
+
+
+@pytest.mark.parametrize("count", [10, 70])
+def test_batch_rows_equal_separate_walks(small, count):
+    """A job's rows in a batch equal its rows from its own fw_walk."""
+    g, G = small
+    specs = _mixed_jobs(g, count, seed=count)
+    jobs, outs = [], []
+    for sp in specs:
+        st = torch.from_numpy(sp["starts"]).cuda()
+        out = torch.full((st.numel(), sp["length"] + 1), -7, dtype=torch.int32, device="cuda")
+        sp["_st"] = st
+        outs.append(out)
+        jobs.append(fw.make_job(st, sp["length"], sp["algo"], out, **_kw(sp)))
+    fw.fw_walk_batch(G.handle, jobs)
+    for sp, out in zip(specs, outs):
+        alone = G.walk(sp["_st"], sp["length"], sp["algo"], **_kw(sp))
+        assert torch.equal(out, alone), sp["algo"]
+
+
+def test_batch_plan_replays(small):
+    g, G = small
+    specs = _mixed_jobs(g, 12, seed=5)
+    jobs, outs, sts = [], [], []
+    for sp in specs:
+        st = torch.from_numpy(sp["starts"]).cuda()
+        out = torch.empty((st.numel(), sp["length"] + 1), dtype=torch.int32, device="cuda")
+        sts.append(st)
+        outs.append(out)
+        jobs.append(fw.make_job(st, sp["length"], sp["algo"], out, **_kw(sp)))
+    plan = fw.BatchPlan(G, jobs)
+    n0 = fw.fw_launch_count()
+    plan.launch()
+    torch.cuda.synchronize()
+    assert fw.fw_launch_count() - n0 == 1
+    first = [o.clone() for o in outs]
+    for sp, st, o in zip(specs, sts, first):
+        assert torch.equal(o, G.walk(st, sp["length"], sp["algo"], **_kw(sp)))
+    # new start contents, same buffers: the replay follows them
+    for st in sts:
+        st.copy_(torch.randint(0, g.n, st.shape, dtype=torch.int32, device="cuda"))
+    plan.launch()
+    torch.cuda.synchronize()
+    for sp, st, o in zip(specs, sts, outs):
+        assert torch.equal(o, G.walk(st, sp["length"], sp["algo"], **_kw(sp)))
+    plan.close()
+
+
+# ------------------------------------------------------------ serving
+def test_server_results_equal_alone_in_a_concurrent_mix(small):
+    """Queries submitted from several threads while others run on the GPU
+    give exactly the rows of fw_walk_host alone (0 differing entries)."""
+    import threading
+    g, G = small
+    srv = fw.Server(G, mem_budget=64 << 20, max_waves=3, max_jobs_per_wave=16)
+    specs = _mixed_jobs(g, 160, seed=9, max_walkers=5000)
+    outs = [np.full((len(sp["starts"]), sp["length"] + 1), -7, dtype=np.int32) for sp in specs]
+    tickets = [None] * len(specs)
+
+    def client(k):
+        for i in range(k, len(specs), 4):
+            sp = specs[i]
+            tickets[i] = srv.submit(sp["starts"], sp["length"], sp["algo"], outs[i], **_kw(sp))
+
+    th = [threading.Thread(target=client, args=(k,)) for k in range(4)]
+    [t.start() for t in th]
+    [t.join() for t in th]
+    lat = [srv.wait(t, timeout=60.0) for t in tickets]
+    assert all(x >= 0 for x in lat)
+    st = srv.stats()
+    assert st["completed"] == len(specs) and st["failed"] == 0 and st["pending"] == 0
+    assert st["peak_device_bytes"] <= 64 << 20
+    srv.close()
+    for sp, out in zip(specs, outs):
+        alone = G.walk_host(sp["starts"], sp["length"], sp["algo"], **_kw(sp))
+        assert np.array_equal(out, alone)
+
+
+def test_server_errors_and_timeouts(small):
+    g, G = small
+    srv = fw.Server(G, mem_budget=1 << 20, max_waves=2)
+    big = np.zeros(1 << 17, dtype=np.int32)                 # 2^17 walkers x 11 entries > 1 MiB
+    with pytest.raises(fw.FlexiWalkError) as e:
+        srv.submit(big, 10, "weighted", np.empty((big.shape[0], 11), np.int32))
+    assert e.value.status == -3
+    bad = np.array([0, g.n], dtype=np.int32)
+    with pytest.raises(fw.FlexiWalkError) as e:
+        srv.submit(bad, 3, "weighted", np.empty((2, 4), np.int32))
+    assert e.value.status == -1
+    with pytest.raises(fw.FlexiWalkError):
+        srv.submit(np.zeros(4, np.int32), 3, "node2vec", np.empty((4, 4), np.int32), p=0.0)
+    starts = np.arange(4000, dtype=np.int32) % g.n
+    out = np.empty((4000, 31), np.int32)
+    t = srv.submit(starts, 30, "node2vec", out, p=2.0, q=0.5)
+    try:
+        srv.wait(t, timeout=0.0)
+        timed_out = False
+    except fw.FlexiWalkError as err:
+        assert err.status == -5
+        timed_out = True
+    if timed_out:
+        srv.wait(t, timeout=30.0)
+    with pytest.raises(fw.FlexiWalkError):
+        srv.wait(t, timeout=1.0)  # released after collection
+    # destroy drains queries never waited for
+    outs = []
+    for i in range(20):
+        o = np.full((100, 6), -7, np.int32)
+        outs.append(o)
+        srv.submit(np.arange(100, dtype=np.int32), 5, "weighted", o, seed=i)
+    srv.close()
+    for i, o in enumerate(outs):
+        assert np.array_equal(o, G.walk_host(np.arange(100, dtype=np.int32), 5, "weighted", seed=i))
