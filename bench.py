@@ -56,6 +56,12 @@ def parse():
                     "scales are for profiling captures)")
     ap.add_argument("--pq", action="append", default=None, help="restrict to one (p,q), e.g. --pq 4,0.25")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--suite", default="walk", choices=["walk", "batch", "serve", "metapath"],
+                    help="walk: the headline node2vec s22 line; batch: 64 mixed jobs on skewed R-MAT s24, "
+                    "batched vs one launch per job; serve: Poisson query stream on s22, continuous batching vs "
+                    "serial calls; metapath: metapath walks on R-MAT s23")
+    ap.add_argument("--duration", type=float, default=10.0, help="serve suite: seconds of offered load")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve suite: mean arrivals per second")
     a = ap.parse_args()
     global PQ
     if a.pq:
@@ -205,10 +211,249 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ====================================================================== suites
+def _hops(rows):
+    import torch
+    return int((rows[:, 1:] >= 0).sum().item()) if isinstance(rows, torch.Tensor) else int((rows[:, 1:] >= 0).sum())
+
+
+def _line(metric, value, unit, args, extra):
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def run_batch(args):
+    """64 independent jobs on a skewed R-MAT s24 graph (a=.7, b=c=.1, edge
+    factor 24): start sets log-uniform in [1K, 1M] walkers, lengths uniform
+    in {5..80}, algorithms node2vec (p, q log-uniform in [0.25, 4]) /
+    metapath (schema 0-1-2-3-4) / weighted, cost ratio profiled per
+    algorithm; one batched launch (a replayed CUDA-graph plan) against one
+    fw_walk launch per job on the same stream."""
+    import torch
+    from paper_2512_00705_gb300 import _build, synth
+    from paper_2512_00705_gb300 import flexiwalk as fw
+    _build.build()
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    g = synth.workload_graph("s24_skew")
+    gen_s = time.perf_counter() - t0
+    G = fw.Graph(g)
+    ratios = {a: G.autotune(a, p=1.0, q=1.0, schema=[0, 1, 2, 3, 4] if a == "metapath" else None)
+              for a in ["node2vec", "metapath", "weighted"]}
+    rng = np.random.default_rng(44)
+    specs = []
+    for j in range(64):
+        algo = ["node2vec", "metapath", "weighted"][j % 3]
+        w = int(np.exp(rng.uniform(np.log(1e3), np.log(1e6))))
+        sp = dict(algo=algo, w=w, L=int(rng.integers(5, 81)), seed=1000 + j,
+                  starts=torch.from_numpy(synth.random_starts(g.n, w, seed=500 + j)).cuda())
+        if algo == "node2vec":
+            sp["p"], sp["q"] = [float(np.exp(rng.uniform(np.log(0.25), np.log(4.0)))) for _ in range(2)]
+        sp["out"] = torch.empty((w, sp["L"] + 1), dtype=torch.int32, device="cuda")
+        specs.append(sp)
+
+    def kw(sp):
+        d = {"seed": sp["seed"]}
+        if "p" in sp:
+            d["p"], d["q"] = sp["p"], sp["q"]
+        if sp["algo"] == "metapath":
+            d["schema"] = [0, 1, 2, 3, 4]
+        return d
+
+    jobs = [fw.make_job(sp["starts"], sp["L"], sp["algo"], sp["out"], **kw(sp)) for sp in specs]
+    plan = fw.BatchPlan(G, jobs)
+
+    def per_job():
+        for sp in specs:
+            G.walk(sp["starts"], sp["L"], sp["algo"], out=sp["out"], **kw(sp))
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    for _ in range(args.warmup):
+        per_job()
+        plan.launch()
+    torch.cuda.synchronize()
+    per_ms, bat_ms = [], []
+    for _ in range(args.steps):
+        per_ms.append(timed(per_job))
+        ref = [sp["out"].clone() for sp in specs[:4]]
+        bat_ms.append(timed(plan.launch))
+    same = all(torch.equal(r, sp["out"]) for r, sp in zip(ref, specs[:4]))
+    hops = sum(_hops(sp["out"]) for sp in specs)
+    per, bat = statistics.median(per_ms), statistics.median(bat_ms)
+    plan.close()
+    _line("walker-steps/sec (batched)", hops / (bat / 1e3), "walker-steps/s", args, {
+        "ms_per_step": bat,
+        "config": {"workload": "64 jobs on skewed R-MAT s24 ef24 (a=.7,b=c=.1), W log-U[1K,1M], L U{5..80}, "
+                               "node2vec/metapath/weighted mixed", "nodes": g.n, "edges": g.e,
+                   "max_degree": int(G.info["max_degree"]), "walkers": sum(sp["w"] for sp in specs),
+                   "hops_per_step": hops, "generation_s": gen_s, "cost_ratios": ratios},
+        "per_job": {"value": hops / (per / 1e3), "ms_per_step": per, "launches": 64},
+        "batched_over_per_job": per / bat, "rows_identical": same})
+    G.close()
+
+
+def run_metapath(args):
+    """Metapath walks (schema 0-1-2-3-4, cyclic) on R-MAT s23 ef16 with
+    lognormal(0,1) weights and labels U{0..4}: 2M random starts, length 5
+    and 40."""
+    import torch
+    from paper_2512_00705_gb300 import _build, synth
+    from paper_2512_00705_gb300 import flexiwalk as fw
+    _build.build()
+    torch.cuda.set_device(0)
+    g = synth.workload_graph("s23_meta")
+    G = fw.Graph(g)
+    starts = torch.from_numpy(synth.random_starts(g.n, 2_000_000, seed=43)).cuda()
+    res = {}
+    for L in (5, 40):
+        out = torch.empty((starts.numel(), L + 1), dtype=torch.int32, device="cuda")
+        for _ in range(args.warmup):
+            G.walk(starts, L, "metapath", schema=[0, 1, 2, 3, 4], out=out, seed=SEED)
+        ms = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            G.walk(starts, L, "metapath", schema=[0, 1, 2, 3, 4], out=out, seed=SEED)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        res[L] = (_hops(out), statistics.median(ms))
+    hops = sum(h for h, _ in res.values())
+    tot = sum(t for _, t in res.values())
+    _line("walker-steps/sec (metapath)", hops / (tot / 1e3), "walker-steps/s", args, {
+        "ms_per_step": tot,
+        "config": {"workload": "metapath 0-1-2-3-4 on R-MAT s23 ef16, h~lognormal(0,1), labels U{0..4}, "
+                               "2M random starts (seed 43), L=5 and L=40", "nodes": g.n, "edges": g.e,
+                   "per_length": {str(L): {"hops": h, "ms": t} for L, (h, t) in res.items()}}})
+    G.close()
+
+
+def run_serve(args):
+    """Poisson stream of walk queries (mean `rate`/s) against the resident
+    s22 graph: W log-uniform in [1, 1e5] walkers, length uniform in
+    {10..100}, algorithm uniform over node2vec (p=2, q=0.5) / metapath /
+    weighted.  Continuous batching (fw_server) against serial fw_walk_host
+    calls on the same arrival sequence; latency = completion - arrival."""
+    import threading
+    import torch
+    from paper_2512_00705_gb300 import _build, synth
+    from paper_2512_00705_gb300 import flexiwalk as fw
+    _build.build()
+    torch.cuda.set_device(0)
+    g = synth.workload_graph("s22")
+    G = fw.Graph(g)
+    rng = np.random.default_rng(45)
+    n_req = int(args.rate * args.duration)
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, n_req))
+    W = np.exp(rng.uniform(0, np.log(1e5), n_req)).astype(np.int64)
+    Ls = rng.integers(10, 101, n_req)
+    algos = rng.integers(0, 3, n_req)
+    pool_words = int(W.max() * 4) + 1
+    starts_pool = torch.from_numpy(synth.random_starts(g.n, pool_words, seed=46)).pin_memory().numpy()
+    # pinned ring for the rows: a query takes the next slot range, reused after it completes
+    ring_words = 1 << 30  # 4 GiB
+    ring = torch.empty(ring_words, dtype=torch.int32).pin_memory().numpy()
+
+    def kw(i):
+        a = ["node2vec", "metapath", "weighted"][algos[i]]
+        d = {"seed": int(1000 + i)}
+        if a == "node2vec":
+            d["p"], d["q"] = 2.0, 0.5
+        if a == "metapath":
+            d["schema"] = [0, 1, 2, 3, 4]
+        return a, d
+
+    def run(mode, count):
+        lat = np.zeros(count)
+        hops = [0]
+        head = [0]
+        inflight = []  # (index, ring start, words, ticket, submit lag)
+        srv = fw.Server(G, mem_budget=8 << 30, max_waves=4) if mode == "server" else None
+
+        def reap(block):
+            # collect finished queries in submission order; latency = submit lag + submit-to-done
+            while inflight:
+                i, off, words, t, lag = inflight[0]
+                if srv is not None:
+                    r = srv.wait(t, 120.0) if block else srv.poll(t)
+                    if r is None:
+                        return
+                    lat[i] = lag + r / 1e3
+                rows = ring[off:off + words].reshape(W[i], Ls[i] + 1)
+                hops[0] += int((rows[:, 1:] >= 0).sum())
+                inflight.pop(0)
+
+        t_base = time.perf_counter()
+        for i in range(count):
+            while time.perf_counter() - t_base < arrivals[i]:
+                if srv is not None:
+                    reap(False)
+            words = int(W[i] * (Ls[i] + 1))
+            if head[0] + words > ring_words:
+                head[0] = 0
+            while inflight and head[0] <= inflight[0][1] < head[0] + words:
+                reap(True)
+            off = head[0]
+            head[0] += words
+            st = starts_pool[(i * 7919) % (pool_words - W[i]):][:W[i]]
+            out = ring[off:off + words].reshape(W[i], Ls[i] + 1)
+            a, d = kw(i)
+            lag = time.perf_counter() - t_base - arrivals[i]
+            if srv is not None:
+                t = srv.submit(st, int(Ls[i]), a, out, **d)
+                inflight.append((i, off, words, t, lag))
+            else:
+                G.walk_host(st, int(Ls[i]), a, out=out, **d)
+                lat[i] = time.perf_counter() - t_base - arrivals[i]
+                inflight.append((i, off, words, None, lag))
+                reap(True)
+        reap(True)
+        stats = None
+        if srv is not None:
+            stats = srv.stats()
+            srv.close()
+        wall = time.perf_counter() - t_base
+        return lat * 1e3, hops[0], wall, stats
+
+    run("server", min(n_req, 400))  # warm-up (module load, arena, caches), discarded
+    res = {m: run(m, n_req) for m in ("server", "serial")}
+    out = {}
+    for m, (lat, hops, wall, stats) in res.items():
+        out[m] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                  "mean_ms": float(lat.mean()), "walker_steps_per_s": hops / wall, "wall_s": wall, "hops": hops}
+        if stats:
+            out[m]["waves"] = stats["waves"]
+            out[m]["queries_per_wave"] = stats["queries_per_wave"]
+            out[m]["peak_inflight_waves"] = stats["peak_inflight_waves"]
+    _line("walker-steps/sec (served)", out["server"]["walker_steps_per_s"], "walker-steps/s", args, {
+        "ms_per_step": None, "higher_is_better": True,
+        "config": {"workload": f"Poisson {args.rate:g}/s for {args.duration:g} s on R-MAT s22; W log-U[1,1e5], "
+                               "L U{10..100}, node2vec(2,.5)/metapath/weighted", "queries": n_req,
+                   "offered_walker_steps_per_s": float((W * Ls).sum() / args.duration)},
+        "serving": out,
+        "p99_server_over_serial": out["server"]["p99_ms"] / out["serial"]["p99_ms"]})
+    G.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.suite == "batch":
+        return run_batch(args)
+    if args.suite == "metapath":
+        return run_metapath(args)
+    if args.suite == "serve":
+        return run_serve(args)
     import torch
     import torch.distributed as dist
 
