@@ -70,9 +70,12 @@ enum {
   FW_FLAG_RVS_NOJUMP = 1, /* eRVS with exponential keys only (Alg. 1), no jumps */
   FW_FLAG_COUNTERS = 2,   /* accumulate per-walk counters (slower build path)    */
   FW_FLAG_UNWEIGHTED = 4, /* ignore h: every property weight is 1 (Sec. 5.1)     */
-  FW_FLAG_PLAIN_RJS = 8   /* eRJS exactly as Sec. 3.3 (uniform proposal, bound
+  FW_FLAG_PLAIN_RJS = 8,  /* eRJS exactly as Sec. 3.3 (uniform proposal, bound
                              max(w) * h_MAX) even when node2vec's return edge
                              could be proposed separately                        */
+  FW_FLAG_PAPER_SUM = 16  /* metapath: plan with the Sec. 4.2 rule (B = h_MAX,
+                             sum-hat = h_SUM / 2) even when per-label node
+                             statistics exist                                    */
 };
 
 /* Parameters of one walk job.  Initialise with fw_params_default(). */
@@ -153,6 +156,14 @@ fw_status fw_graph_info(const fw_graph* graph, fw_graph_info_t* info);
 /* Copy the preprocessed h_MAX[n] and h_SUM[n] (float32) into the device
  * buffers given (either may be NULL).  Asynchronous on `stream`. */
 fw_status fw_graph_node_stats(const fw_graph* graph, float* hmax, float* hsum, void* stream);
+
+/* Copy the per-label node statistics into `stats` (device float32
+ * [n][8][2]: for node v and label l, the maximum and the sum of h over the
+ * edges of v labelled l; h = 1 without weights).  They exist when the graph
+ * has labels, all below 8 (FW_ERR_UNSUPPORTED otherwise).  The metapath
+ * plan uses them for the required label: B = max, exact sum for Eq.
+ * (runtime), and zero sum = dead end.  Asynchronous on `stream`. */
+fw_status fw_graph_label_stats(const fw_graph* graph, float* stats, void* stream);
 
 /* Set the graph's cost ratio r of Eq. (runtime) for every algorithm (must
  * be finite, > 0). */

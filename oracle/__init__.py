@@ -17,6 +17,7 @@ sampling, its own Philox4x32-10), compiled here with gcc and
   node_stats            h_MAX / h_SUM preprocessing, Sec. 4.2
   step_plan             bound (Sec. 3.3) + sum estimate (Eq. sum_estimation)
                         + cost-model choice (Eq. runtime)
+  label_stats           per-node, per-label max / sum of h (labels < 8)
 
 Graph arguments are any object with ``offsets``, ``cols``, ``h`` (or None)
 and ``labels`` (or None) numpy attributes.
@@ -80,6 +81,8 @@ def _load():
             L.or_node_stats.restype = ctypes.c_int
             L.or_step_plan.argtypes = [f32, f32, i32, i32, f32, f32, f32, vp, vp]
             L.or_step_plan.restype = ctypes.c_int
+            L.or_label_stats.argtypes = [vp, vp, vp, i32, vp, vp]
+            L.or_label_stats.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -190,3 +193,14 @@ def step_plan(hmax, hsum, has_prev, algo, p=1.0, q=1.0, r=4.0):
     if m < 0:
         raise ValueError("or_step_plan: bad arguments")
     return m, B.value, S.value
+
+
+def label_stats(g):
+    """(max float32[n][8], sum float64[n][8]) of h per node and label."""
+    offsets, _, h, labels = _graph_args(g)
+    n = offsets.shape[0] - 1
+    lmax = np.zeros((n, 8), dtype=np.float32)
+    lsum = np.zeros((n, 8), dtype=np.float64)
+    if _load().or_label_stats(_ptr(offsets), _ptr(h), _ptr(labels), n, _ptr(lmax), _ptr(lsum)) != 0:
+        raise ValueError("labels missing or >= 8")
+    return lmax, lsum

@@ -298,3 +298,26 @@ int or_step_plan(float hmax, float hsum, int32_t has_prev, int32_t algo, float p
   if (sum_hat) *sum_hat = S;
   return (r * B < S) ? OR_MODE_RJS : OR_MODE_RVS;
 }
+
+/* Per-label node statistics (the Sec. 4.2 preprocessing of h restricted to
+ * the edges of one label): for node v and label l in [0, 8), the maximum
+ * (FP32, exact) and the sum (fp64) of h over the edges of v labelled l;
+ * h == NULL means h = 1.  Returns -1 if a label >= 8 occurs. */
+int or_label_stats(const int32_t *offsets, const float *h, const uint8_t *labels, int32_t n, float *lmax,
+                   double *lsum) {
+  if (!offsets || !labels || n < 0 || !lmax || !lsum) return -1;
+  for (int32_t v = 0; v < n; ++v) {
+    for (int l = 0; l < 8; ++l) {
+      lmax[v * 8 + l] = 0.0f;
+      lsum[v * 8 + l] = 0.0;
+    }
+    for (int64_t i = offsets[v]; i < offsets[v + 1]; ++i) {
+      const int l = labels[i];
+      if (l >= 8) return -1;
+      const float x = h ? h[i] : 1.0f;
+      if (x > lmax[v * 8 + l]) lmax[v * 8 + l] = x;
+      lsum[v * 8 + l] += (double)x;
+    }
+  }
+  return 0;
+}

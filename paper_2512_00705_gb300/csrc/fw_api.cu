@@ -34,6 +34,7 @@ DevGraph dev_graph(const fw_graph* g) {
   d.hsum = g->d_hsum;
   d.nrec = g->d_nrec;
   d.erec = g->d_erec;
+  d.lstat = g->d_lstat;
   d.n = g->n;
   d.sym = g->sym;
   return d;
@@ -84,6 +85,8 @@ fw_status make_job(const fw_graph* g, int32_t algo, const fw_params* params, uin
   job->key0 = (uint32_t)seed;
   job->key1 = (uint32_t)(seed >> 32);
   job->walker_base = P.walker_base;
+  job->label_stats = (algo == ALGO_METAPATH && g->d_lstat && !(P.flags & FW_FLAG_PAPER_SUM) &&
+                      (job->weighted || !g->d_h)) ? 1 : 0;
   return FW_OK;
 }
 
@@ -163,6 +166,7 @@ static void free_graph(fw_graph* g) {
   cudaFree(g->d_hsum);
   cudaFree(g->d_nrec);
   cudaFree(g->d_erec);
+  cudaFree(g->d_lstat);
   cudaFree(g->d_err);
   cudaFree(g->d_cnt);
   cudaFree(g->d_stage_starts);
@@ -250,11 +254,20 @@ extern "C" fw_status fw_graph_create(const int32_t* offsets, const int32_t* cols
     le = launch_node_stats(g->d_off, g->d_h, n, g->d_hmax, g->d_hsum, g->d_nrec, d_maxdeg, g->num_sms, st);
   if (le == cudaSuccess) le = launch_edge_records(g->d_col, g->d_h, g->d_lab, g->d_nrec, e, g->d_erec, g->num_sms, st);
   if (le == cudaSuccess) le = launch_symmetry(g->d_off, g->d_col, g->d_h, n, d_asym, g->num_sms, st);
+  unsigned* d_lbad = g->d_err + 13;
+  if (le == cudaSuccess && labels) {
+    le = cudaMalloc(&g->d_lstat, sizeof(float2) * kLabelStats * ((size_t)n + 1));
+    if (le == cudaSuccess) le = cudaMemsetAsync(d_lbad, 0, sizeof(unsigned), st);
+    if (le == cudaSuccess)
+      le = launch_label_stats(g->d_off, g->d_h, g->d_lab, n, g->d_lstat, d_lbad, g->num_sms, st);
+  }
   cudaEventRecord(e1, st);
   int maxdeg = 0;
   unsigned asym = 1;
   cudaError_t ce = cudaMemcpyAsync(&maxdeg, d_maxdeg, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(&asym, d_asym, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  unsigned lbad = 1;
+  if (ce == cudaSuccess && labels) ce = cudaMemcpyAsync(&lbad, d_lbad, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
   cudaError_t se = cudaStreamSynchronize(st);
   float ms = 0.0f;
   cudaEventElapsedTime(&ms, e0, e1);
@@ -266,6 +279,11 @@ extern "C" fw_status fw_graph_create(const int32_t* offsets, const int32_t* cols
   FW_TRY(cudaMemsetAsync(d_maxdeg, 0, sizeof(int), st), "cudaMemsetAsync");
   g->max_degree = maxdeg;
   g->sym = asym == 0 ? 1 : 0;
+  if (g->d_lstat && lbad != 0) {  // a label >= kLabelStats: per-label statistics unused
+    cudaFree(g->d_lstat);
+    g->d_lstat = nullptr;
+  }
+  if (g->d_lstat) g->bytes += sizeof(float2) * kLabelStats * ((size_t)n + 1);
   g->preprocess_ms = ms;
   {
     fw_status fs = graph_fingerprint(g, st, &g->fingerprint);
@@ -309,6 +327,14 @@ extern "C" fw_status fw_graph_node_stats(const fw_graph* g, float* hmax, float* 
   if (e == cudaSuccess && hsum && g->n > 0)
     e = cudaMemcpyAsync(hsum, g->d_hsum, sizeof(float) * g->n, cudaMemcpyDeviceToDevice, st);
   return e == cudaSuccess ? FW_OK : cuda_error(e, "copy node stats");
+}
+
+extern "C" fw_status fw_graph_label_stats(const fw_graph* g, float* stats, void* stream) {
+  if (!g || !stats) return set_error(FW_ERR_ARG, "NULL argument");
+  if (!g->d_lstat) return set_error(FW_ERR_UNSUPPORTED, "no per-label statistics (no labels, or a label >= 8)");
+  cudaError_t e = cudaMemcpyAsync(stats, g->d_lstat, sizeof(float2) * kLabelStats * (size_t)g->n,
+                                  cudaMemcpyDeviceToDevice, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? FW_OK : cuda_error(e, "copy label statistics");
 }
 
 extern "C" fw_status fw_graph_set_cost_ratio(fw_graph* g, float ratio) {

@@ -28,6 +28,7 @@ namespace fw {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxJobs = 64;
 constexpr int kThreadRvsMaxDeg = 8;  // eRVS steps with d <= this run on one lane
+constexpr int kLabelStats = 8;       // per-label node statistics for labels 0..7
 
 enum : int32_t { ALGO_WEIGHTED = 0, ALGO_NODE2VEC = 1, ALGO_METAPATH = 2 };
 enum : int32_t { MODE_AUTO = 0, MODE_RJS = 1, MODE_RVS = 2, MODE_EXACT = 3 };
@@ -45,6 +46,8 @@ struct DevGraph {
   const int4* __restrict__ nrec;   // per node {row start, degree, h_MAX bits, h_SUM bits}: one sector per plan
   const int4* __restrict__ erec;   // per edge 32 bytes: {col, h bits, target row start, target degree},
                                    // {target h_MAX bits, target h_SUM bits, label, 0}: one sector per eRJS trial
+  const float2* __restrict__ lstat; // per node and label l < kLabelStats: {max h, sum h} over the
+                                   // edges with that label (nullptr: labels absent or >= kLabelStats)
   int32_t n;
   int32_t sym;                     // 1: h(v,u) = h(u,v) for every edge (checked at creation)
 };
@@ -64,6 +67,7 @@ struct Job {
   int32_t need_member;     // node2vec with 1/q != 1: membership test needed
   int32_t fixed_cap;       // 1: rjs_cap is a fixed trial cap; 0: cap = max(rjs_cap, ceil(d / ratio))
   int32_t split_return;    // node2vec with 1/p > max(1, 1/q): eRJS proposes the return edge separately
+  int32_t label_stats;     // metapath: plan with the per-label h_MAX / h_SUM of the required label
   float inv_p, inv_q;      // FP32 1/p, 1/q
   float wmax1, wmean1;     // max / mean of w when a previous node exists
   float wlo1, whi1;        // min / max of {1, 1/q}: squeeze bounds of a non-return neighbour

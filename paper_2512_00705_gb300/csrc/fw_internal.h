@@ -25,6 +25,7 @@ struct fw_graph {
   float* d_hsum = nullptr;
   int4* d_nrec = nullptr;
   int4* d_erec = nullptr;
+  float2* d_lstat = nullptr;  // per-label node statistics (nullptr: not available)
   int32_t sym = 0;
   unsigned* d_err = nullptr;
   fw::DevCounters* d_cnt = nullptr;
@@ -66,6 +67,8 @@ cudaError_t launch_node_stats(const int32_t* off, const float* h, int32_t n, flo
                               int* maxdeg, int num_sms, cudaStream_t stream);
 cudaError_t launch_edge_records(const int32_t* col, const float* h, const uint8_t* lab, const int4* nrec, long long e,
                                 int4* erec, int num_sms, cudaStream_t stream);
+cudaError_t launch_label_stats(const int32_t* off, const float* h, const uint8_t* lab, int32_t n, float2* out,
+                               unsigned* bad, int num_sms, cudaStream_t stream);
 cudaError_t launch_symmetry(const int32_t* off, const int32_t* col, const float* h, int32_t n, unsigned* flag,
                             int num_sms, cudaStream_t stream);
 cudaError_t launch_check_offsets(const int32_t* off, int32_t n, int64_t e, unsigned* err, int num_sms,

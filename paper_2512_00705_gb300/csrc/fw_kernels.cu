@@ -216,7 +216,23 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
             hm = 1.0f;
             hs = (float)c.d;
           }
-          const int32_t choice = plan_choice(J, hm, hs, c.vp >= 0, B, S);
+          int32_t choice;
+          if (J.label_stats) {
+            // metapath with per-label statistics: exact bound and exact sum over
+            // the edges whose label the step requires; none -> dead end now
+            const uint8_t want = J.schema[c.step % J.schema_len];
+            float2 ls = make_float2(0.0f, 0.0f);
+            if (want < kLabelStats) {
+              ls = __ldg(g.lstat + (long long)c.v * kLabelStats + want);
+              if (COUNT) lc.bytes += 8;
+            }
+            B = ls.x;
+            S = ls.y;
+            choice = (__fmul_rn(J.ratio, B) < S) ? MODE_RJS : MODE_RVS;
+            if (!(S > 0.0f)) pick = -1;
+          } else {
+            choice = plan_choice(J, hm, hs, c.vp >= 0, B, S);
+          }
           if (m == MODE_AUTO) m = choice;
           plan = (m == MODE_RJS) ? PLAN_RJS : ((c.d <= kThreadRvsMaxDeg) ? PLAN_RVS_T : PLAN_RVS_W);
           if (plan == PLAN_RJS && J.split_return && c.vp >= 0) {
@@ -457,6 +473,63 @@ cudaError_t launch_node_stats(const int32_t* off, const float* h, int32_t n, flo
   const long long want = ((long long)n * 32 + 255) / 256;
   const int grid = (int)(want < (long long)num_sms * 8 ? want : (long long)num_sms * 8);
   node_stats_kernel<<<grid, 256, 0, stream>>>(off, h, n, hmax, hsum, nrec, maxdeg);
+  g_launches.fetch_add(1);
+  return cudaGetLastError();
+}
+
+// Per-label node statistics: {max h, sum h} over the edges of each label
+// l < kLabelStats (h = 1 without weights); one warp per node.  Sets *bad if
+// a label >= kLabelStats occurs (the statistics are then not used).
+__global__ void label_stats_kernel(const int32_t* __restrict__ off, const float* __restrict__ h,
+                                   const uint8_t* __restrict__ lab, int32_t n, float2* __restrict__ out,
+                                   unsigned* __restrict__ bad) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long v = warp; v < n; v += nwarps) {
+    float mx[kLabelStats], sm[kLabelStats];
+#pragma unroll
+    for (int l = 0; l < kLabelStats; ++l) mx[l] = sm[l] = 0.0f;
+    bool over = false;
+    for (int32_t i = off[v] + lane; i < off[v + 1]; i += 32) {
+      const int l = lab[i];
+      const float x = h ? h[i] : 1.0f;
+      over |= l >= kLabelStats;
+#pragma unroll
+      for (int k = 0; k < kLabelStats; ++k)
+        if (k == l) {
+          mx[k] = fmaxf(mx[k], x);
+          sm[k] += x;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kLabelStats; ++k) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        mx[k] = fmaxf(mx[k], __shfl_xor_sync(kFull, mx[k], o));
+        sm[k] += __shfl_xor_sync(kFull, sm[k], o);
+      }
+    }
+    if (lane < kLabelStats) {
+      float a = 0.0f, b = 0.0f;
+#pragma unroll
+      for (int k = 0; k < kLabelStats; ++k)
+        if (k == lane) {
+          a = mx[k];
+          b = sm[k];
+        }
+      out[v * kLabelStats + lane] = make_float2(a, b);
+    }
+    if (__any_sync(kFull, over) && lane == 0) atomicOr(bad, 1u);
+  }
+}
+
+cudaError_t launch_label_stats(const int32_t* off, const float* h, const uint8_t* lab, int32_t n, float2* out,
+                               unsigned* bad, int num_sms, cudaStream_t stream) {
+  if (n == 0) return cudaSuccess;
+  const long long want = ((long long)n * 32 + 255) / 256;
+  const int grid = (int)(want < (long long)num_sms * 8 ? want : (long long)num_sms * 8);
+  label_stats_kernel<<<grid, 256, 0, stream>>>(off, h, lab, n, out, bad);
   g_launches.fetch_add(1);
   return cudaGetLastError();
 }

@@ -19,7 +19,7 @@ from . import _build
 
 ALGO = {"weighted": 0, "node2vec": 1, "metapath": 2}
 MODE = {"auto": 0, "rjs": 1, "rvs": 2, "exact": 3}
-FLAG_RVS_NOJUMP, FLAG_COUNTERS, FLAG_UNWEIGHTED, FLAG_PLAIN_RJS = 1, 2, 4, 8
+FLAG_RVS_NOJUMP, FLAG_COUNTERS, FLAG_UNWEIGHTED, FLAG_PLAIN_RJS, FLAG_PAPER_SUM = 1, 2, 4, 8, 16
 PTR_HOST, PTR_DEVICE = 0, 1
 STATUS = {0: "FW_OK", -1: "FW_ERR_ARG", -2: "FW_ERR_CSR", -3: "FW_ERR_OOM", -4: "FW_ERR_CUDA",
           -5: "FW_ERR_TIMEOUT", -6: "FW_ERR_DEVICE_CHECK", -7: "FW_ERR_BUSY", -8: "FW_ERR_UNSUPPORTED"}
@@ -95,6 +95,7 @@ def lib() -> ctypes.CDLL:
                 "fw_graph_info": (ctypes.c_int, [vp, P(fw_graph_info_t)]),
                 "fw_graph_node_stats": (ctypes.c_int, [vp, vp, vp, vp]),
                 "fw_graph_set_cost_ratio": (ctypes.c_int, [vp, ctypes.c_float]),
+                "fw_graph_label_stats": (ctypes.c_int, [vp, vp, vp]),
                 "fw_autotune": (ctypes.c_int, [vp, i32, P(fw_params), i32, ctypes.c_char_p, P(ctypes.c_float), vp]),
                 "fw_walk": (ctypes.c_int, [vp, vp, i32, i32, i32, P(fw_params), u64, vp, vp]),
                 "fw_walk_host": (ctypes.c_int, [vp, vp, i32, i32, i32, P(fw_params), u64, vp, vp]),
@@ -328,6 +329,13 @@ class Graph:
         hsum = torch.empty_like(hmax)
         fw_graph_node_stats(self.handle, hmax, hsum, stream)
         return hmax, hsum
+
+    def label_stats(self, stream=None):
+        """Per-label node statistics as a CUDA float32 tensor [n, 8, 2] (max, sum)."""
+        import torch
+        out = torch.empty((self.n, 8, 2), dtype=torch.float32, device="cuda")
+        _check(lib().fw_graph_label_stats(self.handle, _ptr(out), _stream_ptr(stream)))
+        return out
 
     def counters(self, stream=None) -> dict:
         return fw_counters_read(self.handle, stream)

@@ -114,6 +114,14 @@ def test_walk_host_matches_device(small):
 
 
 # ------------------------------------------------------------ preprocessing / plan
+def test_label_stats_parity(small):
+    g, G = small
+    st = G.label_stats().cpu().numpy()
+    lmax, lsum = oracle.label_stats(g)
+    assert np.array_equal(st[:, :, 0], lmax)
+    np.testing.assert_allclose(st[:, :, 1], lsum, rtol=2e-6, atol=1e-6)
+
+
 def test_node_stats_parity(small):
     g, G = small
     hmax, hsum = G.node_stats()
@@ -281,7 +289,8 @@ WALK_CASES = [("node2vec", 0.25, 4.0, None), ("node2vec", 2.0, 0.5, None), ("nod
 
 
 @pytest.mark.parametrize("graph", ["sparse", "sparse-asym", "dense"])
-@pytest.mark.parametrize("mode,flags", [("rjs", 0), ("rjs", fw.FLAG_PLAIN_RJS), ("rvs", 0), ("auto", 0)])
+@pytest.mark.parametrize("mode,flags", [("rjs", 0), ("rjs", fw.FLAG_PLAIN_RJS), ("rvs", 0), ("auto", 0),
+                                        ("auto", fw.FLAG_PAPER_SUM)])
 @pytest.mark.parametrize("algo,p,q,schema", WALK_CASES)
 def test_fast_walk_path_distribution(graph, mode, flags, algo, p, q, schema):
     """GPU walks from one start, many walker ids: frequencies of whole paths

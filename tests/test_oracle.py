@@ -258,6 +258,22 @@ def test_node_stats_match_library_reductions():
     np.testing.assert_array_equal(hmax2[nz], 1.0)
 
 
+def test_label_stats_match_library_reductions():
+    g = synth.workload_graph("small")
+    lmax, lsum = oracle.label_stats(g)
+    rows = np.repeat(np.arange(g.n), g.degrees())
+    for l in range(8):
+        sel = g.labels == l
+        want_sum = np.bincount(rows[sel], weights=g.h[sel].astype(np.float64), minlength=g.n)
+        want_max = np.zeros(g.n, np.float32)
+        np.maximum.at(want_max, rows[sel], g.h[sel])
+        np.testing.assert_allclose(lsum[:, l], want_sum, rtol=1e-12)
+        np.testing.assert_array_equal(lmax[:, l], want_max)
+    # the per-label sums add up to h_SUM
+    _, hsum = oracle.node_stats(g)
+    np.testing.assert_allclose(lsum.sum(axis=1), hsum, rtol=1e-12)
+
+
 @pytest.mark.parametrize("algo,p,q", [("node2vec", 2.0, 0.5), ("node2vec", 0.25, 4.0), ("node2vec", 4.0, 0.25),
                                       ("metapath", 1, 1), ("weighted", 1, 1)])
 def test_bound_dominates_every_weight(algo, p, q):
