@@ -1,0 +1,118 @@
+"""Parity at the benchmark's full sizes, in the launch configuration the
+benchmark times: R-MAT s22 (4,194,304 walkers x 80 hops, node2vec) and R-MAT
+s23 (metapath, 2M starts).  Exact mode: sampled blocks of rows against the
+oracle, which computes them walker by walker.  Fast modes: invariants on
+sampled rows, and per-state distributions at the largest hubs."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_00705_gb300 import flexiwalk as fw
+from paper_2512_00705_gb300 import synth
+from statcheck import chisq_pvalue, tv_distance
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PQ = [(1.0, 1.0), (4.0, 0.25), (0.25, 4.0)]
+
+
+@pytest.fixture(scope="module")
+def s22():
+    g = synth.workload_graph("s22")
+    G = fw.Graph(g)
+    yield g, G
+    G.close()
+
+
+def _blocks(n, nblocks, size, seed):
+    rng = np.random.default_rng(seed)
+    return sorted(int(x) for x in rng.choice(n // size, nblocks, replace=False) * size)
+
+
+@pytest.mark.parametrize("p,q", PQ)
+def test_exact_mode_full_s22_sampled_rows(s22, p, q):
+    g, G = s22
+    starts = torch.arange(g.n, dtype=torch.int32, device="cuda")
+    out = G.walk(starts, 80, "node2vec", p=p, q=q, mode="exact", seed=42)
+    for b in _blocks(g.n, 6, 64, seed=int(p * 100 + q)):
+        sub = np.arange(b, b + 64, dtype=np.int32)
+        ref, _ = oracle.walk(g, sub, 80, "node2vec", p, q, seed=42, walker_base=b)
+        got = out[b:b + 64].cpu().numpy()
+        assert np.array_equal(got, ref), f"block {b}: {(got != ref).any(axis=1).sum()} rows differ"
+
+
+def _edge_keys(g):
+    return np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.offsets)) * np.int64(g.n) + g.cols
+
+
+@pytest.mark.parametrize("p,q", PQ)
+def test_fast_mode_full_s22_invariants(s22, p, q):
+    """The bench's walk (cost-model mode, one walker per node, 80 hops):
+    every hop of 100,000 sampled rows is an edge, -1 only as a suffix, and
+    only isolated start nodes end early (h > 0, so node2vec has no other
+    dead end)."""
+    g, G = s22
+    starts = torch.arange(g.n, dtype=torch.int32, device="cuda")
+    out = G.walk(starts, 80, "node2vec", p=p, q=q, mode="auto", seed=42)
+    rows = np.sort(np.random.default_rng(3).choice(g.n, 100_000, replace=False))
+    o = out[torch.from_numpy(rows).cuda()].cpu().numpy()
+    assert np.array_equal(o[:, 0], rows)
+    alive = o[:, 1:] >= 0
+    assert np.all(alive[:, :-1] | ~alive[:, 1:])
+    deg = g.degrees()
+    assert np.array_equal(~alive[:, 0], deg[rows] == 0)
+    assert np.all(alive[deg[rows] > 0])
+    keys = _edge_keys(g)
+    q_ = (o[:, :-1].astype(np.int64) * np.int64(g.n) + o[:, 1:])[alive]
+    pos = np.searchsorted(keys, q_)
+    assert np.all(keys[np.minimum(pos, len(keys) - 1)] == q_)
+
+
+@pytest.mark.parametrize("mode,flags,ndraws", [("rjs", 0, 4_000_000), ("auto", 0, 4_000_000),
+                                               ("rvs", 0, 4_000_000), ("rvs", fw.FLAG_RVS_NOJUMP, 1_000_000)])
+def test_hub_distributions_s22(s22, mode, flags, ndraws):
+    """The largest hub (d = 162,957): weighted and node2vec from a low-degree
+    v', and node2vec at a low-degree node whose v' is the hub.  TV over 25
+    equiprobable merged bins; at 1e6 draws its noise floor is ~2e-3, so the
+    bound is relaxed to 4e-3 there."""
+    g, G = s22
+    deg = g.degrees()
+    hub = int(np.argmax(deg))
+    nb = g.cols[g.offsets[hub]:g.offsets[hub + 1]]
+    small_prev = int(nb[np.argmin(deg[nb])])
+    states = [(hub, -1, 0, "weighted", 1.0, 1.0), (hub, small_prev, 1, "node2vec", 2.0, 0.5),
+              (hub, small_prev, 1, "node2vec", 0.25, 4.0), (small_prev, hub, 1, "node2vec", 4.0, 0.25)]
+    bound = 2e-3 if ndraws >= 4_000_000 else 4e-3
+    for (v, vp, step, algo, p, q) in states:
+        probs = oracle.transition_probs(g, v, vp, step, algo, p, q)
+        counts = G.sample_hist(v, vp, step, algo, ndraws, p=p, q=q, mode=mode, flags=flags,
+                               seed=77 + v).cpu().numpy()
+        assert counts.sum() == ndraws
+        assert chisq_pvalue(counts, probs) > 1e-4, (v, vp, algo, p, q)
+        assert tv_distance(counts, probs) < bound, (v, vp, algo, p, q)
+
+
+def test_exact_mode_full_s23_metapath_sampled_rows():
+    g = synth.workload_graph("s23_meta")
+    G = fw.Graph(g)
+    starts_h = synth.random_starts(g.n, 2_000_000, seed=43)
+    starts = torch.from_numpy(starts_h).cuda()
+    schema = [0, 1, 2, 3, 4]
+    for L in (5, 40):
+        out = G.walk(starts, L, "metapath", schema=schema, mode="exact", seed=42)
+        for b in _blocks(len(starts_h), 4, 128, seed=L):
+            ref, _ = oracle.walk(g, starts_h[b:b + 128], L, "metapath", schema=schema, seed=42, walker_base=b)
+            assert np.array_equal(out[b:b + 128].cpu().numpy(), ref)
+        fast = G.walk(starts, L, "metapath", schema=schema, mode="auto", seed=42)
+        rows = np.random.default_rng(L).choice(len(starts_h), 20_000, replace=False)
+        o = fast[torch.from_numpy(rows).cuda()].cpu().numpy()
+        alive = o[:, 1:] >= 0
+        assert np.all(alive[:, :-1] | ~alive[:, 1:])
+        keys = _edge_keys(g)
+        q_ = (o[:, :-1].astype(np.int64) * np.int64(g.n) + o[:, 1:])[alive]
+        pos = np.minimum(np.searchsorted(keys, q_), len(keys) - 1)
+        assert np.all(keys[pos] == q_)
+        hop = np.broadcast_to(np.arange(L), alive.shape)[alive]
+        assert np.all(g.labels[pos] == np.asarray(schema)[hop % 5])
+    G.close()
