@@ -157,28 +157,23 @@ class ClockSampler:
 
 
 def oracle_sample(g, cpu_seconds, threads):
-    """Time the CPU oracle on a seeded sample of the workload's walkers."""
+    """Time the CPU oracle on a seeded sample of the workload's walkers,
+    growing the sample until one timed pass takes about `cpu_seconds`."""
     import oracle
     rng = np.random.default_rng(7)
-    nonzero = np.nonzero(np.diff(g.offsets) > 0)[0]
-    # calibrate on a small sample, then size the timed sample to ~cpu_seconds
-    cal = rng.choice(nonzero, 64, replace=False).astype(np.int32)
-    t0 = time.perf_counter()
-    hops = 0
-    for (p, q) in PQ:
-        _, h = oracle.walk(g, cal, LENGTH, "node2vec", p, q, seed=SEED, threads=threads)
-        hops += h
-    dt = max(time.perf_counter() - t0, 1e-3)
-    per_walker = dt / (64 * len(PQ))
-    nw = int(max(64, min(len(nonzero), cpu_seconds / per_walker / len(PQ))))
-    starts = rng.choice(nonzero, nw, replace=False).astype(np.int32)
-    t0 = time.perf_counter()
-    hops = 0
-    for (p, q) in PQ:
-        _, h = oracle.walk(g, starts, LENGTH, "node2vec", p, q, seed=SEED, threads=threads)
-        hops += h
-    dt = time.perf_counter() - t0
-    return hops / dt, nw, hops, dt
+    nonzero = rng.permutation(np.nonzero(np.diff(g.offsets) > 0)[0]).astype(np.int32)
+    nw = 256
+    while True:
+        starts = nonzero[:nw]
+        t0 = time.perf_counter()
+        hops = 0
+        for (p, q) in PQ:
+            _, h = oracle.walk(g, starts, LENGTH, "node2vec", p, q, seed=SEED, threads=threads)
+            hops += h
+        dt = time.perf_counter() - t0
+        if dt >= 0.6 * cpu_seconds or nw >= len(nonzero):
+            return hops / dt, nw, hops, dt
+        nw = int(min(len(nonzero), nw * max(2.0, 1.2 * cpu_seconds / max(dt, 1e-3))))
 
 
 def run_reference(args):
@@ -477,13 +472,26 @@ def main():
     G = fw.Graph(g)
     n = g.n
     stream = torch.cuda.current_stream()
-    starts = torch.arange(n, dtype=torch.int32, device=dev)
-    out = torch.empty((n, LENGTH + 1), dtype=torch.int32, device=dev)
+    from paper_2512_00705_gb300 import sharding
+    if world == 1:
+        starts = torch.arange(n, dtype=torch.int32, device=dev)
+        wids = None
+    else:
+        # weak scaling: `world` replicas of the workload, spread over the GPUs by
+        # a hash of the start node (Sec. 5.6); a query's global index is its stream id
+        glob = np.tile(np.arange(n, dtype=np.int32), world)
+        idx = sharding.shard(glob, rank, world)
+        starts = torch.from_numpy(glob[idx]).to(dev)
+        wids = torch.from_numpy(idx.astype(np.int32)).to(dev)
+    nw = starts.numel()
+    out = torch.empty((nw, LENGTH + 1), dtype=torch.int32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
-    base = rank * n  # each rank's replica uses its own random streams
 
     def walk(p, q, flags=0):
-        G.walk(starts, LENGTH, "node2vec", p=p, q=q, mode="auto", seed=SEED, flags=flags, walker_base=base, out=out)
+        if wids is None:
+            G.walk(starts, LENGTH, "node2vec", p=p, q=q, mode="auto", seed=SEED, flags=flags, out=out)
+        else:
+            G.walk_ids(starts, wids, LENGTH, "node2vec", p=p, q=q, mode="auto", seed=SEED, flags=flags, out=out)
 
     # counted run: hops and algorithmic bytes per launch (untimed)
     counts = {}
@@ -534,35 +542,37 @@ def main():
     clocks = sampler.stop()
     G.check()
 
-    ms_per_step = sum(step_ms) / len(step_ms)
+    ms_per_step = sharding.max_over_ranks(sum(step_ms) / len(step_ms))
+    hops_all = hops_per_step
     if world > 1:
-        t = torch.tensor([ms_per_step], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_per_step = float(t.item())
-    value = world * hops_per_step / (ms_per_step / 1000.0)
+        t = torch.tensor([float(hops_per_step)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        hops_all = int(t.item())
+    value = hops_all / (ms_per_step / 1000.0)
 
     # ---- e2e through the host-buffer entry point (pinned buffers)
     e2e_line = None
     if not args.no_e2e:
-        starts_h = torch.arange(n, dtype=torch.int32).pin_memory()
-        out_h = torch.empty((n, LENGTH + 1), dtype=torch.int32).pin_memory()
+        starts_h = starts.cpu().pin_memory()
+        out_h = torch.empty((nw, LENGTH + 1), dtype=torch.int32).pin_memory()
         e2e_ms = []
         for i in range(2 + max(2, args.steps // 2)):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for (p, q) in PQ:
-                G.walk_host(starts_h, LENGTH, "node2vec", p=p, q=q, mode="auto", seed=SEED, walker_base=base,
-                            out=out_h)
+                G.walk_host(starts_h, LENGTH, "node2vec", p=p, q=q, mode="auto", seed=SEED, out=out_h)
             dt = (time.perf_counter() - t0) * 1000.0
             if i >= 2:
                 e2e_ms.append(dt)
         e2e_step = statistics.median(e2e_ms)
-        # sanity: host rows equal device rows for the last (p, q)
-        walk(*PQ[-1])
+        # sanity: host rows equal device rows for the last (p, q) (same random streams)
+        p_, q_ = PQ[-1]
+        G.walk(starts, LENGTH, "node2vec", p=p_, q=q_, mode="auto", seed=SEED, out=out)
         torch.cuda.synchronize()
         assert torch.equal(out.cpu(), out_h), "host-buffer walk differs from device walk"
-        e2e_line = {"value": world * hops_per_step / (e2e_step / 1000.0), "unit": "walker-steps/s",
-                    "h2d_bytes_per_step": len(PQ) * n * 4, "d2h_bytes_per_step": len(PQ) * n * (LENGTH + 1) * 4}
+        e2e_ms_all = sharding.max_over_ranks(e2e_step)
+        e2e_line = {"value": hops_all / (e2e_ms_all / 1000.0), "unit": "walker-steps/s",
+                    "h2d_bytes_per_step": len(PQ) * nw * 4, "d2h_bytes_per_step": len(PQ) * nw * (LENGTH + 1) * 4}
 
     # ---- roofline of the walk kernel
     peak, peak_kind = measured_peaks()
@@ -578,8 +588,10 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD if args.scale == 22 and len(PQ) == 3 else
-                   f"node2vec R-MAT s{args.scale} ef16 (profiling case), (p,q)={PQ}", "walkers": n, "walk_length": LENGTH, "edges": g.e,
-                   "hops_per_step": hops_per_step, "l2": "256 MiB write between steps; graph and rows > L2",
+                   f"node2vec R-MAT s{args.scale} ef16 (profiling case), (p,q)={PQ}", "walkers": n * world,
+                   "walkers_per_gpu": nw, "sharding": "replicas of the workload hashed by start node" if world > 1
+                   else "none", "walk_length": LENGTH, "edges": g.e,
+                   "hops_per_step": hops_all, "l2": "256 MiB write between steps; graph and rows > L2",
                    "per_pq_ms": {f"p{p:g}_q{q:g}": statistics.median(per_launch[(p, q)]) for (p, q) in PQ},
                    "per_pq_hops": {f"p{p:g}_q{q:g}": counts[(p, q)]["hops"] for (p, q) in PQ},
                    "wall_s": wall},

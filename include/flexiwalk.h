@@ -203,6 +203,17 @@ fw_status fw_walk(const fw_graph* graph, const int32_t* starts, int32_t num_walk
                   void* stream);
 
 /*
+ * fw_walk with an explicit random-stream id per walker: walker i draws from
+ * the streams of walker_ids[i] (device uint32[num_walkers]) instead of
+ * params->walker_base + i.  A shard of a larger query set (Sec. 5.6 spreads
+ * queries over GPUs by a hash of the start node) passes the queries'
+ * global indices and gets exactly the rows the whole set would give on one
+ * GPU.  Asynchronous; errors as fw_walk.
+ */
+fw_status fw_walk_ids(const fw_graph* graph, const int32_t* starts, const uint32_t* walker_ids, int32_t num_walkers,
+                      int32_t len, int32_t algo, const fw_params* params, uint64_t seed, int32_t* out, void* stream);
+
+/*
  * fw_walk with HOST buffers: copies starts (host int32[num_walkers]) to the
  * device, walks, and copies the rows back into out (host
  * int32[num_walkers][len+1]); returns when out is filled.  Pinned host

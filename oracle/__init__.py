@@ -77,6 +77,8 @@ def _load():
             L.or_icdf_pick.restype = i64
             L.or_walk.argtypes = [vp, vp, vp, vp, i32, vp, i32, i32, i32, f32, f32, vp, i32, u64, u32, vp, i32]
             L.or_walk.restype = i64
+            L.or_walk_ids.argtypes = [vp, vp, vp, vp, i32, vp, vp, i32, i32, i32, f32, f32, vp, i32, u64, vp, i32]
+            L.or_walk_ids.restype = i64
             L.or_node_stats.argtypes = [vp, vp, i32, vp, vp]
             L.or_node_stats.restype = ctypes.c_int
             L.or_step_plan.argtypes = [f32, f32, i32, i32, f32, f32, f32, vp, vp]
@@ -171,6 +173,22 @@ def walk(g, starts, length, algo, p=1.0, q=1.0, schema=None, seed=42, walker_bas
                      _ptr(out), threads)
     if hops < 0:
         raise ValueError("or_walk: bad arguments")
+    return out, int(hops)
+
+
+def walk_ids(g, starts, ids, length, algo, p=1.0, q=1.0, schema=None, seed=42, threads=0):
+    """Exact-mode walks with an explicit random-stream id per walker."""
+    L = _load()
+    offsets, cols, h, labels = _graph_args(g)
+    st = np.ascontiguousarray(starts, dtype=np.int32)
+    wi = np.ascontiguousarray(ids, dtype=np.uint32)
+    assert wi.shape == st.shape
+    s, slen = _schema_arr(schema)
+    out = np.empty((st.shape[0], length + 1), dtype=np.int32)
+    hops = L.or_walk_ids(_ptr(offsets), _ptr(cols), _ptr(h), _ptr(labels), offsets.shape[0] - 1, _ptr(st), _ptr(wi),
+                         st.shape[0], length, ALGOS.get(algo, algo), p, q, _ptr(s), slen, seed, _ptr(out), threads)
+    if hops < 0:
+        raise ValueError("or_walk_ids: bad arguments")
     return out, int(hops)
 
 

@@ -184,11 +184,38 @@ int64_t or_icdf_pick(const float *wt, int64_t d, float u) {
  * Returns the number of hops taken (entries other than the start and -1),
  * or -1 on bad arguments.
  */
+static int64_t walk_impl(const int32_t *offsets, const int32_t *cols, const float *h,
+                         const uint8_t *labels, int32_t n, const int32_t *starts, int32_t num_walkers,
+                         int32_t len, int32_t algo, float p, float q, const uint8_t *schema,
+                         int32_t schema_len, uint64_t seed, uint32_t walker_base, const uint32_t *ids,
+                         int32_t *out, int32_t nthreads);
+
 int64_t or_walk(const int32_t *offsets, const int32_t *cols, const float *h,
                 const uint8_t *labels, int32_t n, const int32_t *starts, int32_t num_walkers,
                 int32_t len, int32_t algo, float p, float q, const uint8_t *schema,
                 int32_t schema_len, uint64_t seed, uint32_t walker_base, int32_t *out,
                 int32_t nthreads) {
+  return walk_impl(offsets, cols, h, labels, n, starts, num_walkers, len, algo, p, q, schema, schema_len, seed,
+                   walker_base, NULL, out, nthreads);
+}
+
+/* Same walks with an explicit random-stream id per walker (ids[i] instead
+ * of walker_base + i); ids are inputs, no arithmetic changes. */
+int64_t or_walk_ids(const int32_t *offsets, const int32_t *cols, const float *h,
+                    const uint8_t *labels, int32_t n, const int32_t *starts, const uint32_t *ids,
+                    int32_t num_walkers, int32_t len, int32_t algo, float p, float q,
+                    const uint8_t *schema, int32_t schema_len, uint64_t seed, int32_t *out,
+                    int32_t nthreads) {
+  if (!ids && num_walkers > 0) return -1;
+  return walk_impl(offsets, cols, h, labels, n, starts, num_walkers, len, algo, p, q, schema, schema_len, seed,
+                   0, ids, out, nthreads);
+}
+
+static int64_t walk_impl(const int32_t *offsets, const int32_t *cols, const float *h,
+                         const uint8_t *labels, int32_t n, const int32_t *starts, int32_t num_walkers,
+                         int32_t len, int32_t algo, float p, float q, const uint8_t *schema,
+                         int32_t schema_len, uint64_t seed, uint32_t walker_base, const uint32_t *ids,
+                         int32_t *out, int32_t nthreads) {
   if (!offsets || !cols || !starts || !out || num_walkers < 0 || len < 0 || n < 0) return -1;
   for (int32_t i = 0; i < num_walkers; ++i)
     if (starts[i] < 0 || starts[i] >= n) return -1;
@@ -221,7 +248,8 @@ int64_t or_walk(const int32_t *offsets, const int32_t *cols, const float *h,
       for (; j < len; ++j) {
         int64_t d = or_transition_weights(offsets, cols, h, labels, n, cur, prev, j, algo, p, q,
                                           schema, schema_len, wt);
-        float u = or_exact_uniform(seed, walker_base + (uint32_t)i, (uint32_t)j);
+        const uint32_t wid = ids ? ids[i] : walker_base + (uint32_t)i;
+        float u = or_exact_uniform(seed, wid, (uint32_t)j);
         int64_t k = or_icdf_pick(wt, d, u);
         if (k < 0) break;
         int32_t nxt = cols[offsets[cur] + k];

@@ -362,6 +362,27 @@ extern "C" fw_status fw_walk(const fw_graph* g, const int32_t* starts, int32_t n
   return with_qctr(g, &J, 1, num_walkers, count, reinterpret_cast<cudaStream_t>(stream));
 }
 
+extern "C" fw_status fw_walk_ids(const fw_graph* g, const int32_t* starts, const uint32_t* walker_ids,
+                                 int32_t num_walkers, int32_t len, int32_t algo, const fw_params* params, uint64_t seed,
+                                 int32_t* out, void* stream) {
+  if (!g) return set_error(FW_ERR_ARG, "graph is NULL");
+  if (num_walkers < 0 || len < 0) return set_error(FW_ERR_ARG, "negative size");
+  if (num_walkers > 0 && (!starts || !walker_ids || !out)) return set_error(FW_ERR_ARG, "NULL starts/ids/out");
+  Job J;
+  fw_status s = make_job(g, algo, params, seed, &J);
+  if (s != FW_OK) return s;
+  if (num_walkers == 0) return FW_OK;
+  J.kind = JOB_WALK;
+  J.starts = starts;
+  J.wids = walker_ids;
+  J.out = out;
+  J.num_walkers = num_walkers;
+  J.len = len;
+  J.gbase = 0;
+  const bool count = params && (params->flags & FW_FLAG_COUNTERS);
+  return with_qctr(g, &J, 1, num_walkers, count, reinterpret_cast<cudaStream_t>(stream));
+}
+
 extern "C" fw_status fw_walk_host(fw_graph* g, const int32_t* starts, int32_t num_walkers, int32_t len, int32_t algo,
                                   const fw_params* params, uint64_t seed, int32_t* out, void* stream) {
   if (!g) return set_error(FW_ERR_ARG, "graph is NULL");

@@ -56,6 +56,7 @@ struct DevGraph {
 // global index space: job j owns [gbase, gbase + num_walkers).
 struct Job {
   const int32_t* starts;
+  const uint32_t* wids;    // random-stream id per walker (nullptr: walker_base + index)
   int32_t* out;
   unsigned long long* hist;
   long long gbase;

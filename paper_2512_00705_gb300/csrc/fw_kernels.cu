@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
     if (widx >= 0 && plan == PLAN_NONE) {
       c.ps = c.s;  // the row of v' is the previous step's row
       c.pe = c.s + c.d;
-      c.wid = J.walker_base + (uint32_t)widx;
+      c.wid = J.wids ? __ldg(J.wids + widx) : J.walker_base + (uint32_t)widx;
       int4 nr;  // row start, degree, h_MAX, h_SUM of v: from the accepted trial's edge record, or one load
       if (nxt_ok) {
         nr = nxt;

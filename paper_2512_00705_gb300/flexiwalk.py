@@ -99,6 +99,7 @@ def lib() -> ctypes.CDLL:
                 "fw_autotune": (ctypes.c_int, [vp, i32, P(fw_params), i32, ctypes.c_char_p, P(ctypes.c_float), vp]),
                 "fw_walk": (ctypes.c_int, [vp, vp, i32, i32, i32, P(fw_params), u64, vp, vp]),
                 "fw_walk_host": (ctypes.c_int, [vp, vp, i32, i32, i32, P(fw_params), u64, vp, vp]),
+                "fw_walk_ids": (ctypes.c_int, [vp, vp, vp, i32, i32, i32, P(fw_params), u64, vp, vp]),
                 "fw_sample_hist": (ctypes.c_int, [vp, i32, i32, i32, i32, P(fw_params), u64, i64, vp, vp]),
                 "fw_step_plan": (ctypes.c_int, [vp, vp, vp, i32, i32, P(fw_params), vp, vp, vp, vp]),
                 "fw_counters_read": (ctypes.c_int, [vp, P(fw_counters), vp]),
@@ -209,6 +210,12 @@ def fw_walk(handle: int, starts, length: int, algo, params: fw_params, seed: int
                          seed, _ptr(out), _stream_ptr(stream)))
 
 
+def fw_walk_ids(handle: int, starts, walker_ids, length: int, algo, params: fw_params, seed: int, out, stream=None):
+    """starts: CUDA int32 [W]; walker_ids: CUDA int32/uint32 [W]; out: CUDA int32 [W, length+1]."""
+    _check(lib().fw_walk_ids(handle, _ptr(starts), _ptr(walker_ids), starts.numel(), length, ALGO.get(algo, algo),
+                             ctypes.byref(params), seed, _ptr(out), _stream_ptr(stream)))
+
+
 def fw_walk_host(handle: int, starts: np.ndarray, length: int, algo, params: fw_params, seed: int, out: np.ndarray,
                  stream=None):
     """starts / out are host buffers (numpy or pinned torch CPU tensors)."""
@@ -294,6 +301,15 @@ class Graph:
             out = torch.empty((starts.numel(), length + 1), dtype=torch.int32, device=starts.device)
         prm = make_params(p, q, schema, mode, flags, cost_ratio, rjs_cap, walker_base)
         fw_walk(self.handle, starts, length, algo, prm, seed, out, stream)
+        return out
+
+    def walk_ids(self, starts, walker_ids, length: int, algo="node2vec", *, p=1.0, q=1.0, schema=None, mode="auto",
+                 seed=42, flags=0, cost_ratio=0.0, rjs_cap=0, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((starts.numel(), length + 1), dtype=torch.int32, device=starts.device)
+        prm = make_params(p, q, schema, mode, flags, cost_ratio, rjs_cap, 0)
+        fw_walk_ids(self.handle, starts, walker_ids, length, algo, prm, seed, out, stream)
         return out
 
     def walk_host(self, starts, length: int, algo="node2vec", *, p=1.0, q=1.0, schema=None, mode="auto", seed=42,

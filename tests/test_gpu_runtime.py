@@ -209,3 +209,21 @@ def test_server_errors_and_timeouts(small):
     srv.close()
     for i, o in enumerate(outs):
         assert np.array_equal(o, G.walk_host(np.arange(100, dtype=np.int32), 5, "weighted", seed=i))
+
+
+def test_sharded_walks_reassemble_to_the_single_walk(small):
+    """Queries spread over 3 'GPUs' by the start-node hash (Sec. 5.6), each
+    shard walked with its global indices as stream ids: the reassembled rows
+    equal one walk over all queries, in every mode."""
+    from paper_2512_00705_gb300 import sharding
+    g, G = small
+    starts = np.tile(np.arange(g.n, dtype=np.int32), 2)
+    for mode in ["auto", "rjs", "rvs", "exact"]:
+        full = G.walk(torch.from_numpy(starts).cuda(), 15, "node2vec", p=0.5, q=2.0, mode=mode, seed=9).cpu().numpy()
+        parts = []
+        for r in range(3):
+            idx = sharding.shard(starts, r, 3)
+            rows = G.walk_ids(torch.from_numpy(starts[idx]).cuda(), torch.from_numpy(idx.astype(np.int32)).cuda(), 15,
+                              "node2vec", p=0.5, q=2.0, mode=mode, seed=9).cpu().numpy()
+            parts.append((idx, rows))
+        assert np.array_equal(sharding.assemble(parts, len(starts), 16), full), mode
