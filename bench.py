@@ -308,16 +308,17 @@ def run_metapath(args):
     g = synth.workload_graph("s23_meta")
     G = fw.Graph(g)
     starts = torch.from_numpy(synth.random_starts(g.n, 2_000_000, seed=43)).cuda()
+    r_meta = G.autotune("metapath", schema=[0, 1, 2, 3, 4], method=0)
     res = {}
     for L in (5, 40):
         out = torch.empty((starts.numel(), L + 1), dtype=torch.int32, device="cuda")
         for _ in range(args.warmup):
-            G.walk(starts, L, "metapath", schema=[0, 1, 2, 3, 4], out=out, seed=SEED)
+            G.walk(starts, L, "metapath", schema=[0, 1, 2, 3, 4], out=out, seed=SEED, cost_ratio=r_meta)
         ms = []
         for _ in range(args.steps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            G.walk(starts, L, "metapath", schema=[0, 1, 2, 3, 4], out=out, seed=SEED)
+            G.walk(starts, L, "metapath", schema=[0, 1, 2, 3, 4], out=out, seed=SEED, cost_ratio=r_meta)
             e1.record()
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
@@ -327,7 +328,7 @@ def run_metapath(args):
     _line("walker-steps/sec (metapath)", hops / (tot / 1e3), "walker-steps/s", args, {
         "ms_per_step": tot,
         "config": {"workload": "metapath 0-1-2-3-4 on R-MAT s23 ef16, h~lognormal(0,1), labels U{0..4}, "
-                               "2M random starts (seed 43), L=5 and L=40", "nodes": g.n, "edges": g.e,
+                               "2M random starts (seed 43), L=5 and L=40", "nodes": g.n, "edges": g.e, "cost_ratio": r_meta,
                    "per_length": {str(L): {"hops": h, "ms": t} for L, (h, t) in res.items()}}})
     G.close()
 
@@ -346,6 +347,8 @@ def run_serve(args):
     torch.cuda.set_device(0)
     g = synth.workload_graph("s22")
     G = fw.Graph(g)
+    ratios = {"node2vec": G.autotune("node2vec", p=2.0, q=0.5), "metapath": G.autotune("metapath", schema=[0, 1, 2, 3, 4]),
+              "weighted": G.autotune("weighted")}
     rng = np.random.default_rng(45)
     n_req = int(args.rate * args.duration)
     arrivals = np.cumsum(rng.exponential(1.0 / args.rate, n_req))
@@ -433,6 +436,7 @@ def run_serve(args):
         "ms_per_step": None, "higher_is_better": True,
         "config": {"workload": f"Poisson {args.rate:g}/s for {args.duration:g} s on R-MAT s22; W log-U[1,1e5], "
                                "L U{10..100}, node2vec(2,.5)/metapath/weighted", "queries": n_req,
+                   "cost_ratios": ratios,
                    "offered_walker_steps_per_s": float((W * Ls).sum() / args.duration)},
         "serving": out,
         "p99_server_over_serial": out["server"]["p99_ms"] / out["serial"]["p99_ms"]})
@@ -487,11 +491,19 @@ def main():
     out = torch.empty((nw, LENGTH + 1), dtype=torch.int32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
 
+    # the runtime's profiling step (Sec. 5.1): r = EdgeCost_RJS / EdgeCost_RVS per (p, q),
+    # measured by the two profiling kernels before sampling; reported, not timed
+    t_prof = time.perf_counter()
+    ratio = {(p, q): G.autotune("node2vec", p=p, q=q, method=0) for (p, q) in PQ}
+    profile_ms = (time.perf_counter() - t_prof) * 1e3
+
     def walk(p, q, flags=0):
+        r = ratio[(p, q)]
         if wids is None:
-            G.walk(starts, LENGTH, "node2vec", p=p, q=q, mode="auto", seed=SEED, flags=flags, out=out)
+            G.walk(starts, LENGTH, "node2vec", p=p, q=q, mode="auto", seed=SEED, flags=flags, cost_ratio=r, out=out)
         else:
-            G.walk_ids(starts, wids, LENGTH, "node2vec", p=p, q=q, mode="auto", seed=SEED, flags=flags, out=out)
+            G.walk_ids(starts, wids, LENGTH, "node2vec", p=p, q=q, mode="auto", seed=SEED, flags=flags, cost_ratio=r,
+                       out=out)
 
     # counted run: hops and algorithmic bytes per launch (untimed)
     counts = {}
@@ -560,14 +572,15 @@ def main():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for (p, q) in PQ:
-                G.walk_host(starts_h, LENGTH, "node2vec", p=p, q=q, mode="auto", seed=SEED, out=out_h)
+                G.walk_host(starts_h, LENGTH, "node2vec", p=p, q=q, mode="auto", seed=SEED, cost_ratio=ratio[(p, q)],
+                            out=out_h)
             dt = (time.perf_counter() - t0) * 1000.0
             if i >= 2:
                 e2e_ms.append(dt)
         e2e_step = statistics.median(e2e_ms)
         # sanity: host rows equal device rows for the last (p, q) (same random streams)
         p_, q_ = PQ[-1]
-        G.walk(starts, LENGTH, "node2vec", p=p_, q=q_, mode="auto", seed=SEED, out=out)
+        G.walk(starts, LENGTH, "node2vec", p=p_, q=q_, mode="auto", seed=SEED, cost_ratio=ratio[(p_, q_)], out=out)
         torch.cuda.synchronize()
         assert torch.equal(out.cpu(), out_h), "host-buffer walk differs from device walk"
         e2e_ms_all = sharding.max_over_ranks(e2e_step)
@@ -592,6 +605,8 @@ def main():
                    "walkers_per_gpu": nw, "sharding": "replicas of the workload hashed by start node" if world > 1
                    else "none", "walk_length": LENGTH, "edges": g.e,
                    "hops_per_step": hops_all, "l2": "256 MiB write between steps; graph and rows > L2",
+                   "cost_ratio": {f"p{p:g}_q{q:g}": ratio[(p, q)] for (p, q) in PQ},
+                   "profile_ms": profile_ms, "preprocess_ms": G.info["preprocess_ms"],
                    "per_pq_ms": {f"p{p:g}_q{q:g}": statistics.median(per_launch[(p, q)]) for (p, q) in PQ},
                    "per_pq_hops": {f"p{p:g}_q{q:g}": counts[(p, q)]["hops"] for (p, q) in PQ},
                    "wall_s": wall},
