@@ -55,7 +55,14 @@ typedef enum {
   FW_ERR_UNSUPPORTED = -8   /* feature not available for these inputs             */
 } fw_status;
 
-typedef enum { FW_ALGO_WEIGHTED = 0, FW_ALGO_NODE2VEC = 1, FW_ALGO_METAPATH = 2 } fw_algo;
+typedef enum {
+  FW_ALGO_WEIGHTED = 0,
+  FW_ALGO_NODE2VEC = 1,
+  FW_ALGO_METAPATH = 2,
+  FW_ALGO_PAGERANK2 = 3  /* second-order PageRank, Eq. (2ndpr): with max_d = max(d(v), d(v')),
+                            w = ((1-g)/d(v) + g/d(v')) * max_d if u in N(v'), else
+                            ((1-g)/d(v)) * max_d (u = v' included); hop 0 first-order */
+} fw_algo;
 
 typedef enum {
   FW_MODE_AUTO = 0,  /* cost model per walker-step, Eq. (runtime)          */
@@ -91,6 +98,7 @@ typedef struct {
                             <= 0 selects 64                                      */
   uint32_t walker_base;  /* random-stream id of starts[0]; walker i uses
                             walker_base + i                                      */
+  float gamma;           /* second-order PageRank parameter in [0, 1]            */
 } fw_params;
 
 /* Filled in by fw_graph_info(). */
@@ -128,8 +136,8 @@ typedef struct {
 
 typedef struct fw_graph fw_graph;
 
-/* Fill p = q = 1, mode AUTO, cost_ratio = 0 (tuned), rjs_cap = 0 (64),
- * flags 0, walker_base 0, empty schema. */
+/* Fill p = q = 1, gamma = 0.2, mode AUTO, cost_ratio = 0 (tuned),
+ * rjs_cap = 0 (64), flags 0, walker_base 0, empty schema. */
 void fw_params_default(fw_params* params);
 
 /*
@@ -241,13 +249,13 @@ fw_status fw_sample_hist(const fw_graph* graph, int32_t v, int32_t v_prev, int32
 /*
  * Test hook for the per-step plan (Sec. 3.3 bound, Eq. (sum_estimation),
  * Eq. (runtime)), evaluated by the walk kernel's device code for the
- * `count` states (v[i], has_prev[i]):
+ * `count` states (v[i], v_prev[i]) -- v_prev[i] = -1 for no previous node:
  *   bound[i] = B, sum_hat[i] = estimated total weight, mode[i] = 1 (eRJS) or
- *   2 (eRVS).  All arrays device, length count.  Asynchronous.
+ *   2 (eRVS).  Metapath uses the Sec. 4.2 rule here (B = h_MAX, sum-hat =
+ *   h_SUM/2).  All arrays device, length count.  Asynchronous.
  */
-fw_status fw_step_plan(const fw_graph* graph, const int32_t* v, const int32_t* has_prev,
-                       int32_t count, int32_t algo, const fw_params* params, float* bound,
-                       float* sum_hat, int32_t* mode, void* stream);
+fw_status fw_step_plan(const fw_graph* graph, const int32_t* v, const int32_t* v_prev, int32_t count, int32_t algo,
+                       const fw_params* params, float* bound, float* sum_hat, int32_t* mode, void* stream);
 
 /* Read (synchronising `stream`) or clear the graph's counters. */
 fw_status fw_counters_read(const fw_graph* graph, fw_counters* out, void* stream);

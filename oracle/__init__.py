@@ -10,7 +10,7 @@ sampling, its own Philox4x32-10), compiled here with gcc and
 
   philox4x32_10         Salmon et al., SC'11
   exact_uniform         exact-mode uniform for (seed, walker, hop)
-  transition_weights    Eq. (prob) with Eq. (node2vec) / MetaPath rule, FP32
+  transition_weights    Eq. (prob) with Eq. (node2vec) / MetaPath rule / Eq. (2ndpr), FP32
   transition_probs      Eq. (prob), fp64
   icdf_pick             Sec. 2.2 inverse transform sampling, FP32
   walk                  full exact-mode walks
@@ -37,9 +37,9 @@ _SO = os.path.join(_HERE, "_build", "libfw_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-WEIGHTED, NODE2VEC, METAPATH = 0, 1, 2
+WEIGHTED, NODE2VEC, METAPATH, PAGERANK2 = 0, 1, 2, 3
 MODE_RJS, MODE_RVS = 1, 2
-ALGOS = {"weighted": WEIGHTED, "node2vec": NODE2VEC, "metapath": METAPATH}
+ALGOS = {"weighted": WEIGHTED, "node2vec": NODE2VEC, "metapath": METAPATH, "pagerank2": PAGERANK2}
 
 CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared"]
 
@@ -68,20 +68,21 @@ def _load():
             L.or_exact_uniform.restype = f32
             L.or_recip.argtypes = [f32]
             L.or_recip.restype = f32
-            wargs = [vp, vp, vp, vp, i32, i32, i32, i32, i32, f32, f32, vp, i32, vp]
+            wargs = [vp, vp, vp, vp, i32, i32, i32, i32, i32, f32, f32, f32, vp, i32, vp]
             L.or_transition_weights.argtypes = wargs
             L.or_transition_weights.restype = i64
             L.or_transition_probs.argtypes = wargs
             L.or_transition_probs.restype = i64
             L.or_icdf_pick.argtypes = [vp, i64, f32]
             L.or_icdf_pick.restype = i64
-            L.or_walk.argtypes = [vp, vp, vp, vp, i32, vp, i32, i32, i32, f32, f32, vp, i32, u64, u32, vp, i32]
+            L.or_walk.argtypes = [vp, vp, vp, vp, i32, vp, i32, i32, i32, f32, f32, f32, vp, i32, u64, u32, vp, i32]
             L.or_walk.restype = i64
-            L.or_walk_ids.argtypes = [vp, vp, vp, vp, i32, vp, vp, i32, i32, i32, f32, f32, vp, i32, u64, vp, i32]
+            L.or_walk_ids.argtypes = [vp, vp, vp, vp, i32, vp, vp, i32, i32, i32, f32, f32, f32, vp, i32, u64, vp,
+                                      i32]
             L.or_walk_ids.restype = i64
             L.or_node_stats.argtypes = [vp, vp, i32, vp, vp]
             L.or_node_stats.restype = ctypes.c_int
-            L.or_step_plan.argtypes = [f32, f32, i32, i32, f32, f32, f32, vp, vp]
+            L.or_step_plan.argtypes = [f32, f32, i32, i32, i32, i32, f32, f32, f32, f32, vp, vp]
             L.or_step_plan.restype = ctypes.c_int
             L.or_label_stats.argtypes = [vp, vp, vp, i32, vp, vp]
             L.or_label_stats.restype = ctypes.c_int
@@ -125,23 +126,23 @@ def recip(p: float) -> float:
     return float(_load().or_recip(p))
 
 
-def transition_weights(g, v, vprev, step, algo, p=1.0, q=1.0, schema=None):
+def transition_weights(g, v, vprev, step, algo, p=1.0, q=1.0, schema=None, gamma=0.2):
     """FP32 transition weights of v's neighbours in CSR order."""
     L = _load()
     offsets, cols, h, labels = _graph_args(g)
     s, slen = _schema_arr(schema)
     a = ALGOS.get(algo, algo)
     d = L.or_transition_weights(_ptr(offsets), _ptr(cols), _ptr(h), _ptr(labels), offsets.shape[0] - 1,
-                                v, vprev, step, a, p, q, _ptr(s), slen, None)
+                                v, vprev, step, a, p, q, gamma, _ptr(s), slen, None)
     if d < 0:
         raise ValueError("or_transition_weights: bad arguments")
     wt = np.zeros(d, dtype=np.float32)
     L.or_transition_weights(_ptr(offsets), _ptr(cols), _ptr(h), _ptr(labels), offsets.shape[0] - 1,
-                            v, vprev, step, a, p, q, _ptr(s), slen, _ptr(wt))
+                            v, vprev, step, a, p, q, gamma, _ptr(s), slen, _ptr(wt))
     return wt
 
 
-def transition_probs(g, v, vprev, step, algo, p=1.0, q=1.0, schema=None):
+def transition_probs(g, v, vprev, step, algo, p=1.0, q=1.0, schema=None, gamma=0.2):
     """fp64 transition probabilities of v's neighbours in CSR order."""
     L = _load()
     offsets, cols, h, labels = _graph_args(g)
@@ -150,7 +151,7 @@ def transition_probs(g, v, vprev, step, algo, p=1.0, q=1.0, schema=None):
     d = int(offsets[v + 1] - offsets[v]) if 0 <= v < offsets.shape[0] - 1 else 0
     pr = np.zeros(max(d, 1), dtype=np.float64)
     r = L.or_transition_probs(_ptr(offsets), _ptr(cols), _ptr(h), _ptr(labels), offsets.shape[0] - 1,
-                              v, vprev, step, a, p, q, _ptr(s), slen, _ptr(pr))
+                              v, vprev, step, a, p, q, gamma, _ptr(s), slen, _ptr(pr))
     if r < 0:
         raise ValueError("or_transition_probs: bad arguments")
     return pr[:d]
@@ -161,7 +162,7 @@ def icdf_pick(wt, u: float) -> int:
     return int(_load().or_icdf_pick(_ptr(w), w.shape[0], u))
 
 
-def walk(g, starts, length, algo, p=1.0, q=1.0, schema=None, seed=42, walker_base=0, threads=0):
+def walk(g, starts, length, algo, p=1.0, q=1.0, schema=None, seed=42, walker_base=0, threads=0, gamma=0.2):
     """Exact-mode walks: returns (out int32[W][L+1], hops)."""
     L = _load()
     offsets, cols, h, labels = _graph_args(g)
@@ -169,14 +170,14 @@ def walk(g, starts, length, algo, p=1.0, q=1.0, schema=None, seed=42, walker_bas
     s, slen = _schema_arr(schema)
     out = np.empty((st.shape[0], length + 1), dtype=np.int32)
     hops = L.or_walk(_ptr(offsets), _ptr(cols), _ptr(h), _ptr(labels), offsets.shape[0] - 1, _ptr(st),
-                     st.shape[0], length, ALGOS.get(algo, algo), p, q, _ptr(s), slen, seed, walker_base,
+                     st.shape[0], length, ALGOS.get(algo, algo), p, q, gamma, _ptr(s), slen, seed, walker_base,
                      _ptr(out), threads)
     if hops < 0:
         raise ValueError("or_walk: bad arguments")
     return out, int(hops)
 
 
-def walk_ids(g, starts, ids, length, algo, p=1.0, q=1.0, schema=None, seed=42, threads=0):
+def walk_ids(g, starts, ids, length, algo, p=1.0, q=1.0, schema=None, seed=42, threads=0, gamma=0.2):
     """Exact-mode walks with an explicit random-stream id per walker."""
     L = _load()
     offsets, cols, h, labels = _graph_args(g)
@@ -186,7 +187,8 @@ def walk_ids(g, starts, ids, length, algo, p=1.0, q=1.0, schema=None, seed=42, t
     s, slen = _schema_arr(schema)
     out = np.empty((st.shape[0], length + 1), dtype=np.int32)
     hops = L.or_walk_ids(_ptr(offsets), _ptr(cols), _ptr(h), _ptr(labels), offsets.shape[0] - 1, _ptr(st), _ptr(wi),
-                         st.shape[0], length, ALGOS.get(algo, algo), p, q, _ptr(s), slen, seed, _ptr(out), threads)
+                         st.shape[0], length, ALGOS.get(algo, algo), p, q, gamma, _ptr(s), slen, seed, _ptr(out),
+                         threads)
     if hops < 0:
         raise ValueError("or_walk_ids: bad arguments")
     return out, int(hops)
@@ -202,12 +204,13 @@ def node_stats(g):
     return hmax, hsum
 
 
-def step_plan(hmax, hsum, has_prev, algo, p=1.0, q=1.0, r=4.0):
-    """(mode, B, sum_hat) for one walker step; mode MODE_RJS or MODE_RVS."""
+def step_plan(hmax, hsum, has_prev, algo, p=1.0, q=1.0, r=4.0, dv=1, dprev=1, gamma=0.2):
+    """(mode, B, sum_hat) for one walker step; mode MODE_RJS or MODE_RVS.
+    dv / dprev (degrees of v and v') matter for second-order PageRank only."""
     B = ctypes.c_float()
     S = ctypes.c_float()
-    m = _load().or_step_plan(hmax, hsum, int(bool(has_prev)), ALGOS.get(algo, algo), p, q, r,
-                             ctypes.addressof(B), ctypes.addressof(S))
+    m = _load().or_step_plan(hmax, hsum, int(bool(has_prev)), int(dv), int(dprev), ALGOS.get(algo, algo), p, q, gamma,
+                             r, ctypes.addressof(B), ctypes.addressof(S))
     if m < 0:
         raise ValueError("or_step_plan: bad arguments")
     return m, B.value, S.value

@@ -17,6 +17,9 @@
  *   Eq. (node2vec), Sec. 2.1  w = 1/a if dist(v',u)=0, 1 if dist(v',u)=1, 1/b if dist(v',u)=2
  *                             (the paper's a, b are node2vec's p, q)
  *   MetaPath, Sec. 2.1        w in {0,1}: 1 iff the edge label equals the schema entry of the step
+ *   Eq. (2ndpr), Sec. 2.1     second-order PageRank: with max_d = max(d(v), d(v')),
+ *                             w = ((1-g)/d(v) + g/d(v')) * max_d if dist(v',u) = 1,
+ *                             else ((1-g)/d(v)) * max_d
  *   ITS, Sec. 2.2             one uniform, cumulative weights, first index whose cumulative
  *                             weight exceeds the scaled uniform
  *   Sec. 3.3 (bound), Sec. 4.1 Eq. (runtime), Eq. (sum_estimation), Sec. 4.2 (sum helper):
@@ -34,6 +37,10 @@
  *     weight (no neighbours, or no neighbour with a matching label) stops and
  *     the rest of its row is -1.
  *   - The metapath label required at hop j is schema[j mod S].
+ *   - Second-order PageRank: u = v' (distance 0) takes the "otherwise" weight;
+ *     hop 0 (no v') is a first-order step (w = 1).  FP32 recipe:
+ *     t1 = (1 - g) / d(v), t2 = g / d(v'), m = max(d(v), d(v')),
+ *     w = (t1 + t2) * m or t1 * m, each operation rounded once.
  *   - Exact-mode uniform: Philox4x32-10 with key = (seed low 32, seed high 32)
  *     and counter = (walker id, hop index, 0, 0); u = (x0 >> 8) * 2^-24.
  *   - Exact-mode pick: W_k = W_{k-1} + w~_k in FP32 in neighbour order,
@@ -48,7 +55,7 @@
 #include <omp.h>
 #endif
 
-enum { OR_WEIGHTED = 0, OR_NODE2VEC = 1, OR_METAPATH = 2 };
+enum { OR_WEIGHTED = 0, OR_NODE2VEC = 1, OR_METAPATH = 2, OR_PAGERANK2 = 3 };
 enum { OR_MODE_RJS = 1, OR_MODE_RVS = 2 };
 
 /* ---------------------------------------------------------------------------
@@ -113,15 +120,25 @@ static int is_neighbour(const int32_t *offsets, const int32_t *cols, int32_t x, 
  */
 int64_t or_transition_weights(const int32_t *offsets, const int32_t *cols, const float *h,
                               const uint8_t *labels, int32_t n, int32_t v, int32_t vprev,
-                              int32_t step, int32_t algo, float p, float q,
+                              int32_t step, int32_t algo, float p, float q, float gamma,
                               const uint8_t *schema, int32_t schema_len, float *wt) {
   if (!offsets || !cols || v < 0 || v >= n || vprev >= n || step < 0) return -1;
   if (algo == OR_NODE2VEC && !(p > 0 && q > 0 && isfinite(p) && isfinite(q))) return -1;
   if (algo == OR_METAPATH && (!labels || !schema || schema_len < 1)) return -1;
-  if (algo != OR_WEIGHTED && algo != OR_NODE2VEC && algo != OR_METAPATH) return -1;
+  if (algo == OR_PAGERANK2 && !(gamma >= 0.0f && gamma <= 1.0f)) return -1;
+  if (algo != OR_WEIGHTED && algo != OR_NODE2VEC && algo != OR_METAPATH && algo != OR_PAGERANK2) return -1;
   const int64_t s = offsets[v], d = (int64_t)offsets[v + 1] - s;
   if (!wt) return d;
   const float inv_p = or_recip(p), inv_q = or_recip(q);
+  float pr_w1 = 1.0f, pr_w2 = 1.0f; /* second-order PageRank weights of this step */
+  if (algo == OR_PAGERANK2 && vprev >= 0) {
+    const float dv = (float)d, dp = (float)(offsets[vprev + 1] - offsets[vprev]);
+    const float t1 = (1.0f - gamma) / dv;
+    const float t2 = gamma / dp;
+    const float m = dv > dp ? dv : dp;
+    pr_w1 = (t1 + t2) * m;
+    pr_w2 = t1 * m;
+  }
   for (int64_t k = 0; k < d; ++k) {
     const int32_t u = cols[s + k];
     const float hk = h ? h[s + k] : 1.0f;
@@ -133,6 +150,9 @@ int64_t or_transition_weights(const int32_t *offsets, const int32_t *cols, const
       else if (u == vprev) w = inv_p;                                /* dist(v',u) = 0     */
       else if (is_neighbour(offsets, cols, vprev, u)) w = 1.0f;      /* dist(v',u) = 1     */
       else w = inv_q;                                                /* dist(v',u) = 2     */
+    } else if (algo == OR_PAGERANK2) {
+      if (vprev < 0) w = 1.0f;                                       /* reading: no v'     */
+      else w = is_neighbour(offsets, cols, vprev, u) ? pr_w1 : pr_w2; /* dist 1 / otherwise */
     } else {
       w = (labels[s + k] == schema[step % schema_len]) ? 1.0f : 0.0f;
     }
@@ -145,14 +165,14 @@ int64_t or_transition_weights(const int32_t *offsets, const int32_t *cols, const
  * weight is zero (a dead end).  Returns d or -1. */
 int64_t or_transition_probs(const int32_t *offsets, const int32_t *cols, const float *h,
                             const uint8_t *labels, int32_t n, int32_t v, int32_t vprev,
-                            int32_t step, int32_t algo, float p, float q, const uint8_t *schema,
-                            int32_t schema_len, double *probs) {
-  int64_t d = or_transition_weights(offsets, cols, h, labels, n, v, vprev, step, algo, p, q,
+                            int32_t step, int32_t algo, float p, float q, float gamma,
+                            const uint8_t *schema, int32_t schema_len, double *probs) {
+  int64_t d = or_transition_weights(offsets, cols, h, labels, n, v, vprev, step, algo, p, q, gamma,
                                     schema, schema_len, NULL);
   if (d < 0 || !probs) return d;
   float *wt = (float *)malloc((size_t)(d > 0 ? d : 1) * sizeof(float));
   if (!wt) return -1;
-  or_transition_weights(offsets, cols, h, labels, n, v, vprev, step, algo, p, q, schema,
+  or_transition_weights(offsets, cols, h, labels, n, v, vprev, step, algo, p, q, gamma, schema,
                         schema_len, wt);
   double total = 0.0;
   for (int64_t k = 0; k < d; ++k) total += (double)wt[k];
@@ -186,34 +206,34 @@ int64_t or_icdf_pick(const float *wt, int64_t d, float u) {
  */
 static int64_t walk_impl(const int32_t *offsets, const int32_t *cols, const float *h,
                          const uint8_t *labels, int32_t n, const int32_t *starts, int32_t num_walkers,
-                         int32_t len, int32_t algo, float p, float q, const uint8_t *schema,
+                         int32_t len, int32_t algo, float p, float q, float gamma, const uint8_t *schema,
                          int32_t schema_len, uint64_t seed, uint32_t walker_base, const uint32_t *ids,
                          int32_t *out, int32_t nthreads);
 
 int64_t or_walk(const int32_t *offsets, const int32_t *cols, const float *h,
                 const uint8_t *labels, int32_t n, const int32_t *starts, int32_t num_walkers,
-                int32_t len, int32_t algo, float p, float q, const uint8_t *schema,
+                int32_t len, int32_t algo, float p, float q, float gamma, const uint8_t *schema,
                 int32_t schema_len, uint64_t seed, uint32_t walker_base, int32_t *out,
                 int32_t nthreads) {
-  return walk_impl(offsets, cols, h, labels, n, starts, num_walkers, len, algo, p, q, schema, schema_len, seed,
-                   walker_base, NULL, out, nthreads);
+  return walk_impl(offsets, cols, h, labels, n, starts, num_walkers, len, algo, p, q, gamma, schema, schema_len,
+                   seed, walker_base, NULL, out, nthreads);
 }
 
 /* Same walks with an explicit random-stream id per walker (ids[i] instead
  * of walker_base + i); ids are inputs, no arithmetic changes. */
 int64_t or_walk_ids(const int32_t *offsets, const int32_t *cols, const float *h,
                     const uint8_t *labels, int32_t n, const int32_t *starts, const uint32_t *ids,
-                    int32_t num_walkers, int32_t len, int32_t algo, float p, float q,
+                    int32_t num_walkers, int32_t len, int32_t algo, float p, float q, float gamma,
                     const uint8_t *schema, int32_t schema_len, uint64_t seed, int32_t *out,
                     int32_t nthreads) {
   if (!ids && num_walkers > 0) return -1;
-  return walk_impl(offsets, cols, h, labels, n, starts, num_walkers, len, algo, p, q, schema, schema_len, seed,
-                   0, ids, out, nthreads);
+  return walk_impl(offsets, cols, h, labels, n, starts, num_walkers, len, algo, p, q, gamma, schema, schema_len,
+                   seed, 0, ids, out, nthreads);
 }
 
 static int64_t walk_impl(const int32_t *offsets, const int32_t *cols, const float *h,
                          const uint8_t *labels, int32_t n, const int32_t *starts, int32_t num_walkers,
-                         int32_t len, int32_t algo, float p, float q, const uint8_t *schema,
+                         int32_t len, int32_t algo, float p, float q, float gamma, const uint8_t *schema,
                          int32_t schema_len, uint64_t seed, uint32_t walker_base, const uint32_t *ids,
                          int32_t *out, int32_t nthreads) {
   if (!offsets || !cols || !starts || !out || num_walkers < 0 || len < 0 || n < 0) return -1;
@@ -221,6 +241,7 @@ static int64_t walk_impl(const int32_t *offsets, const int32_t *cols, const floa
     if (starts[i] < 0 || starts[i] >= n) return -1;
   if (algo == OR_NODE2VEC && !(p > 0 && q > 0 && isfinite(p) && isfinite(q))) return -1;
   if (algo == OR_METAPATH && (!labels || !schema || schema_len < 1)) return -1;
+  if (algo == OR_PAGERANK2 && !(gamma >= 0.0f && gamma <= 1.0f)) return -1;
   int32_t maxd = 0;
   for (int32_t v = 0; v < n; ++v)
     if (offsets[v + 1] - offsets[v] > maxd) maxd = offsets[v + 1] - offsets[v];
@@ -246,7 +267,7 @@ static int64_t walk_impl(const int32_t *offsets, const int32_t *cols, const floa
       row[0] = cur;
       int32_t j = 0;
       for (; j < len; ++j) {
-        int64_t d = or_transition_weights(offsets, cols, h, labels, n, cur, prev, j, algo, p, q,
+        int64_t d = or_transition_weights(offsets, cols, h, labels, n, cur, prev, j, algo, p, q, gamma,
                                           schema, schema_len, wt);
         const uint32_t wid = ids ? ids[i] : walker_base + (uint32_t)i;
         float u = or_exact_uniform(seed, wid, (uint32_t)j);
@@ -286,19 +307,22 @@ int or_node_stats(const int32_t *offsets, const float *h, int32_t n, float *hmax
 
 /*
  * The per-step plan of the runtime (Sec. 3.3 bound, Sec. 4.1 cost model,
- * Sec. 4.2 helper functions), for one walker at v (has_prev = 0 when there
- * is no previous node, i.e. on hop 0):
+ * Sec. 4.2 helper functions), for one walker at v of degree dv with
+ * previous node of degree dprev (has_prev = 0 when there is no previous
+ * node, i.e. on hop 0):
  *   B       = max(w) * h_MAX[v]        (FP32 product; max(w) of the algorithm)
  *   sum_hat = h_SUM[v] * mean_w        (FP32 product; mean of the distinct return
  *                                       expressions of get_weight, Eq. (sum_estimation))
  *   mode    = eRJS iff r * B < sum_hat (FP32), else eRVS   (Eq. (runtime))
  * Distinct return expressions: node2vec {h/a, h, h/b} (3; without v': {h}),
- * metapath {h, 0} (2), weighted {h} (1).  The means are taken in double and
- * rounded once to FP32.  With h = 1 (unweighted) h_MAX = 1 and h_SUM = d(v),
- * which is the paper's PER_KERNEL rule (mean times degree).
+ * metapath {h, 0} (2), weighted {h} (1), second-order PageRank {w1 h, w2 h}
+ * (2; without v': {h}).  The node2vec mean is taken in double and rounded
+ * once to FP32; the PageRank one is (w1 + w2) * 0.5 in FP32.  With h = 1
+ * (unweighted) h_MAX = 1 and h_SUM = d(v), which is the paper's PER_KERNEL
+ * rule (mean times degree).
  */
-int or_step_plan(float hmax, float hsum, int32_t has_prev, int32_t algo, float p, float q, float r,
-                 float *bound, float *sum_hat) {
+int or_step_plan(float hmax, float hsum, int32_t has_prev, int32_t dv, int32_t dprev, int32_t algo, float p,
+                 float q, float gamma, float r, float *bound, float *sum_hat) {
   float wmax, wmean;
   if (algo == OR_NODE2VEC) {
     if (!(p > 0 && q > 0)) return -1;
@@ -310,6 +334,20 @@ int or_step_plan(float hmax, float hsum, int32_t has_prev, int32_t algo, float p
       wmax = ip > 1.0f ? ip : 1.0f;
       if (iq > wmax) wmax = iq;
       wmean = (float)(((double)ip + 1.0 + (double)iq) / 3.0);
+    }
+  } else if (algo == OR_PAGERANK2) {
+    if (!has_prev) {
+      wmax = 1.0f;
+      wmean = 1.0f;
+    } else {
+      if (dv < 1 || dprev < 1) return -1;
+      const float fv = (float)dv, fp = (float)dprev;
+      const float t1 = (1.0f - gamma) / fv;
+      const float t2 = gamma / fp;
+      const float m = fv > fp ? fv : fp;
+      const float w1 = (t1 + t2) * m, w2 = t1 * m;
+      wmax = w1;
+      wmean = (w1 + w2) * 0.5f;
     }
   } else if (algo == OR_METAPATH) {
     wmax = 1.0f;

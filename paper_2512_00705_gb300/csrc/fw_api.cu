@@ -46,8 +46,10 @@ fw_status make_job(const fw_graph* g, int32_t algo, const fw_params* params, uin
   fw_params P;
   if (params) P = *params;
   else fw_params_default(&P);
-  if (algo != ALGO_WEIGHTED && algo != ALGO_NODE2VEC && algo != ALGO_METAPATH)
+  if (algo != ALGO_WEIGHTED && algo != ALGO_NODE2VEC && algo != ALGO_METAPATH && algo != ALGO_PAGERANK2)
     return set_error(FW_ERR_ARG, "unknown algo");
+  if (algo == ALGO_PAGERANK2 && !(P.gamma >= 0.0f && P.gamma <= 1.0f))
+    return set_error(FW_ERR_ARG, "second-order PageRank needs gamma in [0, 1]");
   if (P.mode < MODE_AUTO || P.mode > MODE_EXACT) return set_error(FW_ERR_ARG, "unknown mode");
   if (algo == ALGO_NODE2VEC && !(P.p > 0.0f && P.q > 0.0f && std::isfinite(P.p) && std::isfinite(P.q)))
     return set_error(FW_ERR_ARG, "node2vec needs finite p, q > 0");
@@ -85,6 +87,8 @@ fw_status make_job(const fw_graph* g, int32_t algo, const fw_params* params, uin
   job->key0 = (uint32_t)seed;
   job->key1 = (uint32_t)(seed >> 32);
   job->walker_base = P.walker_base;
+  job->pr_g = P.gamma;
+  job->pr_1g = 1.0f - P.gamma;
   job->label_stats = (algo == ALGO_METAPATH && g->d_lstat && !(P.flags & FW_FLAG_PAPER_SUM) &&
                       (job->weighted || !g->d_h)) ? 1 : 0;
   return FW_OK;
@@ -113,6 +117,7 @@ extern "C" void fw_params_default(fw_params* p) {
   std::memset(p, 0, sizeof(*p));
   p->p = 1.0f;
   p->q = 1.0f;
+  p->gamma = 0.2f;
   p->mode = FW_MODE_AUTO;
 }
 
@@ -447,15 +452,15 @@ extern "C" fw_status fw_sample_hist(const fw_graph* g, int32_t v, int32_t v_prev
   return FW_OK;
 }
 
-extern "C" fw_status fw_step_plan(const fw_graph* g, const int32_t* v, const int32_t* has_prev, int32_t count,
+extern "C" fw_status fw_step_plan(const fw_graph* g, const int32_t* v, const int32_t* v_prev, int32_t count,
                                   int32_t algo, const fw_params* params, float* bound, float* sum_hat, int32_t* mode,
                                   void* stream) {
-  if (!g || count < 0 || (count > 0 && (!v || !has_prev || !bound || !sum_hat || !mode)))
+  if (!g || count < 0 || (count > 0 && (!v || !v_prev || !bound || !sum_hat || !mode)))
     return set_error(FW_ERR_ARG, "bad arguments");
   Job J;
   fw_status s = make_job(g, algo, params, 0, &J);
   if (s != FW_OK) return s;
-  cudaError_t e = launch_step_plan(g, J, v, has_prev, count, bound, sum_hat, mode, reinterpret_cast<cudaStream_t>(stream));
+  cudaError_t e = launch_step_plan(g, J, v, v_prev, count, bound, sum_hat, mode, reinterpret_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? FW_OK : cuda_error(e, "step plan kernel");
 }
 

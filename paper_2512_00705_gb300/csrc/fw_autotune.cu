@@ -37,11 +37,13 @@ __device__ __forceinline__ bool profile_ctx(const DevGraph& g, const Job& J, int
   c.s = nr.x;
   c.d = nr.y;
   c.step = 1;
-  c.vp = (J.algo == ALGO_NODE2VEC) ? __ldg(g.col + nr.x) : -1;
+  c.vp = (J.algo == ALGO_NODE2VEC || J.algo == ALGO_PAGERANK2) ? __ldg(g.col + nr.x) : -1;
+  c.w1 = c.w2 = 1.0f;
   if (c.vp >= 0) {
     const int4 pr = __ldg(g.nrec + c.vp);
     c.ps = pr.x;
     c.pe = pr.x + pr.y;
+    if (J.algo == ALGO_PAGERANK2) pagerank2_weights(J, c.d, pr.y, c.w1, c.w2);
   } else {
     c.ps = c.pe = 0;
   }
@@ -59,7 +61,7 @@ __global__ void profile_rjs_kernel(DevGraph g, Job J, int32_t count, int32_t str
     if (profile_ctx(g, J, i, stride, c)) {
       const bool second = J.algo == ALGO_NODE2VEC && c.vp >= 0;
       const float hm = J.weighted ? __int_as_float(__ldg(g.nrec + c.v).z) : 1.0f;
-      const float B = __fmul_rn(second ? J.wmax1 : 1.0f, hm);
+      const float B = __fmul_rn(second ? J.wmax1 : (J.algo == ALGO_PAGERANK2 && c.vp >= 0 ? c.w1 : 1.0f), hm);
       Accept acc;
       LaneCounters lc;
       found = rjs_trials<false>(g, J, c, B, false, 0.0f, -1, 0.0f, j, 1, acc, lc) ? 1u : 0u;

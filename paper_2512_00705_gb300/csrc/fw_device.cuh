@@ -30,7 +30,7 @@ constexpr int kMaxJobs = 64;
 constexpr int kThreadRvsMaxDeg = 8;  // eRVS steps with d <= this run on one lane
 constexpr int kLabelStats = 8;       // per-label node statistics for labels 0..7
 
-enum : int32_t { ALGO_WEIGHTED = 0, ALGO_NODE2VEC = 1, ALGO_METAPATH = 2 };
+enum : int32_t { ALGO_WEIGHTED = 0, ALGO_NODE2VEC = 1, ALGO_METAPATH = 2, ALGO_PAGERANK2 = 3 };
 enum : int32_t { MODE_AUTO = 0, MODE_RJS = 1, MODE_RVS = 2, MODE_EXACT = 3 };
 enum : int32_t { JOB_WALK = 0, JOB_HIST = 1 };
 enum : int32_t { PLAN_NONE = 0, PLAN_RJS = 1, PLAN_RVS_T = 2, PLAN_RVS_W = 3, PLAN_EXACT_T = 4, PLAN_EXACT_W = 5 };
@@ -73,6 +73,7 @@ struct Job {
   float wmax1, wmean1;     // max / mean of w when a previous node exists
   float wlo1, whi1;        // min / max of {1, 1/q}: squeeze bounds of a non-return neighbour
   float ratio;             // r of Eq. (runtime)
+  float pr_g, pr_1g;       // second-order PageRank: gamma and 1 - gamma (FP32)
   uint32_t key0, key1, walker_base;
   int32_t hv, hprev, hstep;  // JOB_HIST: the fixed state
   uint8_t schema[16];
@@ -141,7 +142,19 @@ struct StepCtx {
   int32_t ps, pe;   // row range of vp (node2vec membership)
   int32_t step;     // hop index
   uint32_t wid;     // random-stream walker id
+  float w1, w2;     // second-order PageRank weights of this step: u in N(v') / otherwise
 };
+
+// Eq. (2ndpr) weights for degrees dv = d(v), dp = d(v'):
+// t1 = (1-g)/dv, t2 = g/dp, m = max(dv, dp), w1 = (t1 + t2) * m, w2 = t1 * m.
+__device__ __forceinline__ void pagerank2_weights(const Job& J, int32_t dv, int32_t dp, float& w1, float& w2) {
+  const float fv = (float)dv, fp = (float)dp;
+  const float t1 = __fdiv_rn(J.pr_1g, fv);
+  const float t2 = __fdiv_rn(J.pr_g, fp);
+  const float m = fmaxf(fv, fp);
+  w1 = __fmul_rn(__fadd_rn(t1, t2), m);
+  w2 = __fmul_rn(t1, m);
+}
 
 // Position of u in the sorted row col[lo, hi) (all ids in [0, n)), or -1.
 // A few interpolation probes first -- the guess puts u at its place between
@@ -215,16 +228,22 @@ __device__ __forceinline__ float item_weight(const DevGraph& g, const Job& J, co
     const uint8_t want = J.schema[c.step % J.schema_len];
     return (__ldg(g.lab + i) == want) ? hk : 0.0f;    // w in {0, 1}
   }
+  if (J.algo == ALGO_PAGERANK2 && c.vp >= 0) {
+    const int32_t u = __ldg(g.col + i);
+    return __fmul_rn(row_contains(g.col, c.ps, c.pe, u, g.n, probes) ? c.w1 : c.w2, hk);
+  }
   return hk;
 }
 
 // ---------------------------------------------------------------- plan
 // Bound (Sec. 3.3), sum estimate (Eq. sum_estimation) and choice (Eq. runtime).
-__device__ __forceinline__ int32_t plan_choice(const Job& J, float hm, float hs, bool has_prev, float& B,
-                                               float& S) {
+__device__ __forceinline__ int32_t plan_choice(const Job& J, float hm, float hs, bool has_prev, float w1, float w2,
+                                               float& B, float& S) {
   const bool second = (J.algo == ALGO_NODE2VEC) && has_prev;
-  const float wmax = second ? J.wmax1 : ((J.algo == ALGO_METAPATH) ? 1.0f : 1.0f);
-  const float wmean = second ? J.wmean1 : ((J.algo == ALGO_METAPATH) ? 0.5f : 1.0f);
+  const bool pr2 = (J.algo == ALGO_PAGERANK2) && has_prev;
+  const float wmax = second ? J.wmax1 : (pr2 ? w1 : 1.0f);
+  const float wmean = second ? J.wmean1 : (pr2 ? __fmul_rn(__fadd_rn(w1, w2), 0.5f)
+                                               : ((J.algo == ALGO_METAPATH) ? 0.5f : 1.0f));
   B = __fmul_rn(wmax, hm);
   S = __fmul_rn(hs, wmean);
   return (__fmul_rn(J.ratio, B) < S) ? MODE_RJS : MODE_RVS;
@@ -308,6 +327,17 @@ __device__ __forceinline__ bool rjs_trials(const DevGraph& g, const Job& J, cons
       }
     } else if (J.algo == ALGO_METAPATH) {
       accept = ((uint8_t)b.z == want) && (UB < hk);
+    } else if (J.algo == ALGO_PAGERANK2 && c.vp >= 0) {
+      if (UB >= __fmul_rn(c.w1, hk)) {
+        accept = false;                         // squeeze: above the larger weight
+      } else if (UB < __fmul_rn(c.w2, hk)) {
+        accept = true;                          // squeeze: below the smaller weight
+      } else {
+        uint32_t pb = 0;
+        const bool adj = row_contains(g.col, c.ps, c.pe, u, g.n, pb);
+        probes += pb;
+        accept = UB < __fmul_rn(adj ? c.w1 : c.w2, hk);
+      }
     } else {
       accept = UB < hk;
     }

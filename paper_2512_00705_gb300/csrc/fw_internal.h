@@ -75,7 +75,7 @@ cudaError_t launch_check_offsets(const int32_t* off, int32_t n, int64_t e, unsig
                                  cudaStream_t stream);
 cudaError_t launch_check_rows(const int32_t* off, const int32_t* col, const float* h, int32_t n, unsigned* err,
                               int num_sms, cudaStream_t stream);
-cudaError_t launch_step_plan(const fw_graph* g, const Job& job, const int32_t* v, const int32_t* has_prev,
+cudaError_t launch_step_plan(const fw_graph* g, const Job& job, const int32_t* v, const int32_t* v_prev,
                              int32_t count, float* bound, float* sum_hat, int32_t* mode, cudaStream_t stream);
 
 }  // namespace fw

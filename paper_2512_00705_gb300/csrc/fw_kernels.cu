@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
   StepCtx c;
   c.v = c.vp = c.s = c.d = c.ps = c.pe = c.step = 0;
   c.wid = 0;
+  c.w1 = c.w2 = 1.0f;
   int32_t job = 0, widx = -1;
   int32_t plan = PLAN_NONE, trials = 0, pick = -2, node = -1;
   float B = 0.0f;
@@ -206,6 +207,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
       } else {
         int32_t m = J.mode;
         if (m == MODE_EXACT) {
+          if (J.algo == ALGO_PAGERANK2 && c.vp >= 0) pagerank2_weights(J, c.d, c.pe - c.ps, c.w1, c.w2);
           plan = (c.d <= kThreadExactMaxDeg) ? PLAN_EXACT_T : PLAN_EXACT_W;
         } else {
           float hm, hs, S;
@@ -231,7 +233,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
             choice = (__fmul_rn(J.ratio, B) < S) ? MODE_RJS : MODE_RVS;
             if (!(S > 0.0f)) pick = -1;
           } else {
-            choice = plan_choice(J, hm, hs, c.vp >= 0, B, S);
+            if (J.algo == ALGO_PAGERANK2 && c.vp >= 0) pagerank2_weights(J, c.d, c.pe - c.ps, c.w1, c.w2);
+            choice = plan_choice(J, hm, hs, c.vp >= 0, c.w1, c.w2, B, S);
           }
           if (m == MODE_AUTO) m = choice;
           plan = (m == MODE_RJS) ? PLAN_RJS : ((c.d <= kThreadRvsMaxDeg) ? PLAN_RVS_T : PLAN_RVS_W);
@@ -315,6 +318,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
       w.pe = __shfl_sync(kFull, c.pe, src);
       w.step = __shfl_sync(kFull, c.step, src);
       w.wid = __shfl_sync(kFull, c.wid, src);
+      w.w1 = __shfl_sync(kFull, c.w1, src);
+      w.w2 = __shfl_sync(kFull, c.w2, src);
       const int jb = __shfl_sync(kFull, job, src);
       const int pl = __shfl_sync(kFull, plan, src);
       const Job& JW = sj[jb];
@@ -639,34 +644,42 @@ cudaError_t launch_check_rows(const int32_t* off, const int32_t* col, const floa
 }
 
 // ---------------------------------------------------------------- plan test hook
-__global__ void step_plan_kernel(DevGraph g, Job J, const int32_t* __restrict__ v, const int32_t* __restrict__ hp,
+__global__ void step_plan_kernel(DevGraph g, Job J, const int32_t* __restrict__ v, const int32_t* __restrict__ vp,
                                  int32_t count, float* __restrict__ bound, float* __restrict__ sum_hat,
                                  int32_t* __restrict__ mode) {
   const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
-  const int32_t x = v[i];
-  if (x < 0 || x >= g.n) {
+  const int32_t x = v[i], y = vp[i];
+  if (x < 0 || x >= g.n || y < -1 || y >= g.n) {
     mode[i] = -1;
     return;
   }
-  float hm, hs, B, S;
+  float hm, hs, B, S, w1 = 1.0f, w2 = 1.0f;
+  const int32_t d = g.off[x + 1] - g.off[x];
   if (J.weighted) {
     hm = g.hmax[x];
     hs = g.hsum[x];
   } else {
     hm = 1.0f;
-    hs = (float)(g.off[x + 1] - g.off[x]);
+    hs = (float)d;
   }
-  mode[i] = plan_choice(J, hm, hs, hp[i] != 0, B, S);
+  if (J.algo == ALGO_PAGERANK2 && y >= 0) {
+    const int32_t dp = g.off[y + 1] - g.off[y];
+    if (d < 1 || dp < 1) {
+      mode[i] = -1;
+      return;
+    }
+    pagerank2_weights(J, d, dp, w1, w2);
+  }
+  mode[i] = plan_choice(J, hm, hs, y >= 0, w1, w2, B, S);
   bound[i] = B;
   sum_hat[i] = S;
 }
 
-cudaError_t launch_step_plan(const fw_graph* g, const Job& job, const int32_t* v, const int32_t* has_prev,
-                             int32_t count, float* bound, float* sum_hat, int32_t* mode, cudaStream_t stream) {
+cudaError_t launch_step_plan(const fw_graph* g, const Job& job, const int32_t* v, const int32_t* vp, int32_t count,
+                             float* bound, float* sum_hat, int32_t* mode, cudaStream_t stream) {
   if (count <= 0) return cudaSuccess;
-  step_plan_kernel<<<(count + 255) / 256, 256, 0, stream>>>(dev_graph(g), job, v, has_prev, count, bound, sum_hat,
-                                                            mode);
+  step_plan_kernel<<<(count + 255) / 256, 256, 0, stream>>>(dev_graph(g), job, v, vp, count, bound, sum_hat, mode);
   g_launches.fetch_add(1);
   return cudaGetLastError();
 }

@@ -17,7 +17,7 @@ import numpy as np
 
 from . import _build
 
-ALGO = {"weighted": 0, "node2vec": 1, "metapath": 2}
+ALGO = {"weighted": 0, "node2vec": 1, "metapath": 2, "pagerank2": 3}
 MODE = {"auto": 0, "rjs": 1, "rvs": 2, "exact": 3}
 FLAG_RVS_NOJUMP, FLAG_COUNTERS, FLAG_UNWEIGHTED, FLAG_PLAIN_RJS, FLAG_PAPER_SUM = 1, 2, 4, 8, 16
 PTR_HOST, PTR_DEVICE = 0, 1
@@ -34,7 +34,8 @@ class FlexiWalkError(RuntimeError):
 class fw_params(ctypes.Structure):
     _fields_ = [("p", ctypes.c_float), ("q", ctypes.c_float), ("schema", ctypes.c_uint8 * 16),
                 ("schema_len", ctypes.c_int32), ("mode", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("cost_ratio", ctypes.c_float), ("rjs_cap", ctypes.c_int32), ("walker_base", ctypes.c_uint32)]
+                ("cost_ratio", ctypes.c_float), ("rjs_cap", ctypes.c_int32), ("walker_base", ctypes.c_uint32),
+                ("gamma", ctypes.c_float)]
 
 
 class fw_graph_info_t(ctypes.Structure):
@@ -145,10 +146,11 @@ def _stream_ptr(stream) -> Optional[int]:
 
 
 def make_params(p: float = 1.0, q: float = 1.0, schema: Optional[Sequence[int]] = None, mode="auto", flags: int = 0,
-                cost_ratio: float = 0.0, rjs_cap: int = 0, walker_base: int = 0) -> fw_params:
+                cost_ratio: float = 0.0, rjs_cap: int = 0, walker_base: int = 0, gamma: float = 0.2) -> fw_params:
     prm = fw_params()
     lib().fw_params_default(ctypes.byref(prm))
     prm.p, prm.q = float(p), float(q)
+    prm.gamma = float(gamma)
     if schema is not None:
         s = list(schema)
         if not 1 <= len(s) <= 16:
@@ -230,8 +232,8 @@ def fw_sample_hist(handle: int, v: int, v_prev: int, step: int, algo, params: fw
                                 _ptr(counts), _stream_ptr(stream)))
 
 
-def fw_step_plan(handle: int, v, has_prev, algo, params: fw_params, bound, sum_hat, mode, stream=None):
-    _check(lib().fw_step_plan(handle, _ptr(v), _ptr(has_prev), v.numel(), ALGO.get(algo, algo), ctypes.byref(params),
+def fw_step_plan(handle: int, v, v_prev, algo, params: fw_params, bound, sum_hat, mode, stream=None):
+    _check(lib().fw_step_plan(handle, _ptr(v), _ptr(v_prev), v.numel(), ALGO.get(algo, algo), ctypes.byref(params),
                               _ptr(bound), _ptr(sum_hat), _ptr(mode), _stream_ptr(stream)))
 
 
@@ -295,48 +297,50 @@ class Graph:
             pass
 
     def walk(self, starts, length: int, algo="node2vec", *, p=1.0, q=1.0, schema=None, mode="auto", seed=42,
-             flags=0, cost_ratio=0.0, rjs_cap=0, walker_base=0, out=None, stream=None):
+             flags=0, cost_ratio=0.0, rjs_cap=0, walker_base=0, gamma=0.2, out=None, stream=None):
         import torch
         if out is None:
             out = torch.empty((starts.numel(), length + 1), dtype=torch.int32, device=starts.device)
-        prm = make_params(p, q, schema, mode, flags, cost_ratio, rjs_cap, walker_base)
+        prm = make_params(p, q, schema, mode, flags, cost_ratio, rjs_cap, walker_base, gamma)
         fw_walk(self.handle, starts, length, algo, prm, seed, out, stream)
         return out
 
     def walk_ids(self, starts, walker_ids, length: int, algo="node2vec", *, p=1.0, q=1.0, schema=None, mode="auto",
-                 seed=42, flags=0, cost_ratio=0.0, rjs_cap=0, out=None, stream=None):
+                 seed=42, flags=0, cost_ratio=0.0, rjs_cap=0, gamma=0.2, out=None, stream=None):
         import torch
         if out is None:
             out = torch.empty((starts.numel(), length + 1), dtype=torch.int32, device=starts.device)
-        prm = make_params(p, q, schema, mode, flags, cost_ratio, rjs_cap, 0)
+        prm = make_params(p, q, schema, mode, flags, cost_ratio, rjs_cap, 0, gamma)
         fw_walk_ids(self.handle, starts, walker_ids, length, algo, prm, seed, out, stream)
         return out
 
     def walk_host(self, starts, length: int, algo="node2vec", *, p=1.0, q=1.0, schema=None, mode="auto", seed=42,
-                  flags=0, cost_ratio=0.0, rjs_cap=0, walker_base=0, out=None, stream=None):
+                  flags=0, cost_ratio=0.0, rjs_cap=0, walker_base=0, gamma=0.2, out=None, stream=None):
         if out is None:
             out = np.empty((len(starts), length + 1), dtype=np.int32)
-        prm = make_params(p, q, schema, mode, flags, cost_ratio, rjs_cap, walker_base)
+        prm = make_params(p, q, schema, mode, flags, cost_ratio, rjs_cap, walker_base, gamma)
         fw_walk_host(self.handle, starts, length, algo, prm, seed, out, stream)
         return out
 
     def sample_hist(self, v: int, v_prev: int, step: int, algo="node2vec", ndraws: int = 1_000_000, *, p=1.0, q=1.0,
                     schema=None, mode="auto", seed=42, flags=0, cost_ratio=0.0, rjs_cap=0, walker_base=0,
-                    stream=None):
+                    gamma=0.2, stream=None):
         import torch
         d = self.degree(v)
         counts = torch.zeros(max(d, 1), dtype=torch.int64, device="cuda")
-        prm = make_params(p, q, schema, mode, flags, cost_ratio, rjs_cap, walker_base)
+        prm = make_params(p, q, schema, mode, flags, cost_ratio, rjs_cap, walker_base, gamma)
         fw_sample_hist(self.handle, v, v_prev, step, algo, prm, seed, ndraws, counts, stream)
         return counts[:d]
 
-    def step_plan(self, v, has_prev, algo="node2vec", *, p=1.0, q=1.0, schema=None, cost_ratio=0.0, stream=None):
+    def step_plan(self, v, v_prev, algo="node2vec", *, p=1.0, q=1.0, schema=None, cost_ratio=0.0, gamma=0.2,
+                  stream=None):
+        """(mode, B, sum_hat) for states (v[i], v_prev[i]); v_prev[i] = -1: no previous node."""
         import torch
         bound = torch.empty(v.numel(), dtype=torch.float32, device=v.device)
         s = torch.empty_like(bound)
         m = torch.empty(v.numel(), dtype=torch.int32, device=v.device)
-        prm = make_params(p, q, schema, "auto", 0, cost_ratio)
-        fw_step_plan(self.handle, v, has_prev, algo, prm, bound, s, m, stream)
+        prm = make_params(p, q, schema, "auto", 0, cost_ratio, 0, 0, gamma)
+        fw_step_plan(self.handle, v, v_prev, algo, prm, bound, s, m, stream)
         return m, bound, s
 
     def node_stats(self, stream=None):
@@ -362,8 +366,9 @@ class Graph:
     def check(self, stream=None):
         fw_graph_check(self.handle, stream)
 
-    def autotune(self, algo="node2vec", *, p=1.0, q=1.0, schema=None, method=0, cache_path=None, stream=None):
-        r = fw_autotune(self.handle, algo, make_params(p, q, schema), method, cache_path, stream)
+    def autotune(self, algo="node2vec", *, p=1.0, q=1.0, schema=None, gamma=0.2, method=0, cache_path=None,
+                 stream=None):
+        r = fw_autotune(self.handle, algo, make_params(p, q, schema, gamma=gamma), method, cache_path, stream)
         self.info = fw_graph_info(self.handle)
         return r
 
@@ -377,14 +382,14 @@ class Graph:
 
 # ---------------------------------------------------------------- batching
 def make_job(starts, length: int, algo, out, *, p=1.0, q=1.0, schema=None, mode="auto", seed=42, flags=0,
-             cost_ratio=0.0, rjs_cap=0, walker_base=0) -> fw_job:
+             cost_ratio=0.0, rjs_cap=0, walker_base=0, gamma=0.2) -> fw_job:
     """One batch entry; starts / out are CUDA tensors that must outlive the launch."""
     j = fw_job()
     j.starts = _ptr(starts)
     j.num_walkers = starts.numel()
     j.len = length
     j.algo = ALGO.get(algo, algo)
-    j.params = make_params(p, q, schema, mode, flags, cost_ratio, rjs_cap, walker_base)
+    j.params = make_params(p, q, schema, mode, flags, cost_ratio, rjs_cap, walker_base, gamma)
     j.seed = seed
     j.out = _ptr(out)
     return j
@@ -433,10 +438,10 @@ class Server:
         self.graph = graph
 
     def submit(self, starts, length: int, algo, out, *, p=1.0, q=1.0, schema=None, mode="auto", seed=42, flags=0,
-               walker_base=0) -> int:
+               walker_base=0, gamma=0.2) -> int:
         """starts / out: host buffers (numpy or pinned torch CPU tensors) kept alive until collected."""
         n = starts.shape[0] if isinstance(starts, np.ndarray) else starts.numel()
-        prm = make_params(p, q, schema, mode, flags, 0.0, 0, walker_base)
+        prm = make_params(p, q, schema, mode, flags, 0.0, 0, walker_base, gamma)
         t = ctypes.c_uint64()
         _check(lib().fw_server_submit(self.handle, _ptr(starts), n, length, ALGO.get(algo, algo), ctypes.byref(prm),
                                       seed, _ptr(out), ctypes.byref(t)))

@@ -5,8 +5,16 @@ import numpy as np
 from scipy import stats
 
 
-def _bf_weight(adj, h, lab, v, u, vprev, hop, algo, p, q, schema):
+def _bf_weight(adj, h, lab, v, u, vprev, hop, algo, p, q, schema, gamma=0.2):
     hv = h[(v, u)]
+    if algo == "pagerank2":  # Eq. (2ndpr); u = v' takes the "otherwise" branch, hop 0 is first-order
+        if vprev is None:
+            return hv
+        dv, dp = len(adj[v]), len(adj[vprev])
+        md = max(dv, dp)
+        if u in adj[vprev]:
+            return hv * ((1 - gamma) / dv + gamma / dp) * md
+        return hv * ((1 - gamma) / dv) * md
     if algo == "weighted":
         return hv
     if algo == "node2vec":
@@ -20,7 +28,7 @@ def _bf_weight(adj, h, lab, v, u, vprev, hop, algo, p, q, schema):
     return hv if lab[(v, u)] == schema[hop % len(schema)] else 0.0
 
 
-def bf_paths(g, start, length, algo, p, q, schema):
+def bf_paths(g, start, length, algo, p, q, schema, gamma=0.2):
     """{path tuple (padded with -1 after a dead end): probability}."""
     n = g.n
     adj = [set(g.cols[g.offsets[i]:g.offsets[i + 1]].tolist()) for i in range(n)]
@@ -39,7 +47,7 @@ def bf_paths(g, start, length, algo, p, q, schema):
             return
         v = path[-1]
         vprev = path[-2] if len(path) > 1 else None
-        ws = {u: _bf_weight(adj, h, lab, v, u, vprev, hop, algo, p, q, schema) for u in sorted(adj[v])}
+        ws = {u: _bf_weight(adj, h, lab, v, u, vprev, hop, algo, p, q, schema, gamma) for u in sorted(adj[v])}
         tot = sum(ws.values())
         if tot <= 0:
             padded = tuple(path) + (-1,) * (length - hop)

@@ -17,7 +17,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 ALGOS = [("node2vec", 2.0, 0.5, None), ("node2vec", 0.25, 4.0, None), ("node2vec", 4.0, 0.25, None),
-         ("node2vec", 1.0, 1.0, None), ("metapath", 1.0, 1.0, [0, 1, 2, 3, 4]), ("weighted", 1.0, 1.0, None)]
+         ("node2vec", 1.0, 1.0, None), ("metapath", 1.0, 1.0, [0, 1, 2, 3, 4]), ("weighted", 1.0, 1.0, None),
+         ("pagerank2", 1.0, 1.0, None)]
 
 
 @pytest.fixture(scope="module")
@@ -131,21 +132,25 @@ def test_node_stats_parity(small):
 
 
 @pytest.mark.parametrize("algo,p,q", [("node2vec", 2.0, 0.5), ("node2vec", 0.25, 4.0), ("metapath", 1, 1),
-                                      ("weighted", 1, 1)])
+                                      ("weighted", 1, 1), ("pagerank2", 1, 1)])
 def test_step_plan_parity(small, algo, p, q):
     g, G = small
+    deg = g.degrees()
     v = np.arange(g.n, dtype=np.int32)
-    hp = (v % 2).astype(np.int32)
+    vp = np.where((v % 2 == 1) & (deg > 0), g.cols[np.minimum(g.offsets[:-1], g.e - 1)], -1).astype(np.int32)
     r = 4.0
-    m, B, S = G.step_plan(_cuda(v), _cuda(hp), algo, p=p, q=q, schema=[0, 1, 2, 3, 4], cost_ratio=r)
+    m, B, S = G.step_plan(_cuda(v), _cuda(vp), algo, p=p, q=q, schema=[0, 1, 2, 3, 4], cost_ratio=r)
     m, B, S = m.cpu().numpy(), B.cpu().numpy(), S.cpu().numpy()
     rmax, rsum = oracle.node_stats(g)
     ghmax, ghsum = [t.cpu().numpy() for t in G.node_stats()]
     for i in range(g.n):
-        om, oB, oS = oracle.step_plan(float(ghmax[i]), float(ghsum[i]), hp[i], algo, p, q, r)
+        dv, dp = int(deg[i]), (int(deg[vp[i]]) if vp[i] >= 0 else 1)
+        if algo == "pagerank2" and vp[i] >= 0 and dv == 0:
+            continue
+        om, oB, oS = oracle.step_plan(float(ghmax[i]), float(ghsum[i]), vp[i] >= 0, algo, p, q, r, dv=dv, dprev=dp)
         assert B[i] == oB and S[i] == oS and m[i] == om, i
         # and against the oracle's own fp64 sums, away from the decision boundary
-        om2, oB2, oS2 = oracle.step_plan(float(rmax[i]), float(rsum[i]), hp[i], algo, p, q, r)
+        om2, oB2, oS2 = oracle.step_plan(float(rmax[i]), float(rsum[i]), vp[i] >= 0, algo, p, q, r, dv=dv, dprev=dp)
         assert oB2 == B[i]
         if abs(r * oB2 - oS2) > 1e-4 * max(1.0, oS2):
             assert om2 == m[i]
@@ -167,7 +172,8 @@ def _states(g):
 
 @pytest.mark.parametrize("mode,flags", [("rjs", 0), ("rvs", 0), ("rvs", fw.FLAG_RVS_NOJUMP), ("auto", 0)])
 @pytest.mark.parametrize("algo,p,q,schema", [("node2vec", 2.0, 0.5, None), ("node2vec", 0.25, 4.0, None),
-                                             ("metapath", 1.0, 1.0, [0, 1, 2, 3, 4]), ("weighted", 1.0, 1.0, None)])
+                                             ("metapath", 1.0, 1.0, [0, 1, 2, 3, 4]), ("weighted", 1.0, 1.0, None),
+                                             ("pagerank2", 1.0, 1.0, None)])
 def test_fast_mode_distributions(small, mode, flags, algo, p, q, schema):
     g, G = small
     ndraws = 4_000_000
@@ -285,7 +291,7 @@ def _asymmetric(g, seed):
 
 
 WALK_CASES = [("node2vec", 0.25, 4.0, None), ("node2vec", 2.0, 0.5, None), ("node2vec", 4.0, 0.25, None),
-              ("metapath", 1.0, 1.0, [0, 1, 2]), ("weighted", 1.0, 1.0, None)]
+              ("metapath", 1.0, 1.0, [0, 1, 2]), ("weighted", 1.0, 1.0, None), ("pagerank2", 1.0, 1.0, None)]
 
 
 @pytest.mark.parametrize("graph", ["sparse", "sparse-asym", "dense"])

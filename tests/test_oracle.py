@@ -125,6 +125,34 @@ def test_known_bound_unweighted_node2vec():
     assert wt.max() == B
 
 
+# ------------------------------------------------------- second-order PageRank
+def test_pagerank2_closed_forms():
+    """Eq. (2ndpr), gamma = 0.2, h = 1: triangle at v=1 from v'=0 (d = d' = 2):
+    neighbour 2 is adjacent to v' -> (0.8/2 + 0.2/2) * 2 = 1.0; the return to
+    v' takes the other branch -> (0.8/2) * 2 = 0.8."""
+    g = _cycle(3)
+    pr = oracle.transition_probs(g, 1, 0, 1, "pagerank2")
+    np.testing.assert_allclose(pr, [0.8 / 1.8, 1.0 / 1.8], rtol=1e-6)
+    # star centre 0 with 4 leaves, at leaf 1 from the centre: d(v)=1, d(v')=4, max_d = 4;
+    # the only neighbour is v' itself -> probability 1
+    g = synth.from_edges(5, [(0, i) for i in range(1, 5)])
+    np.testing.assert_allclose(oracle.transition_probs(g, 1, 0, 1, "pagerank2"), [1.0])
+    # at the centre from leaf 1: d(v)=4, d(v')=1, max_d=4; no leaf is adjacent to leaf 1,
+    # all weights ((1-g)/4)*4 = 0.8 -> uniform
+    np.testing.assert_allclose(oracle.transition_probs(g, 0, 1, 1, "pagerank2"), [0.25] * 4, rtol=1e-6)
+    # K_4 at v=3 from v'=0: the others adjacent to v' get (0.8/3 + 0.2/3)*3 = 1, return 0.8
+    g = _complete(4)
+    np.testing.assert_allclose(oracle.transition_probs(g, 3, 0, 1, "pagerank2"),
+                               np.array([0.8, 1.0, 1.0]) / 2.8, rtol=1e-6)
+    # gamma = 0 reduces to a first-order walk
+    g = synth.random_graph(12, 0.4, seed=4, weighted=True)
+    for v in range(12):
+        nb = g.cols[g.offsets[v]:g.offsets[v + 1]]
+        if len(nb):
+            np.testing.assert_allclose(oracle.transition_probs(g, v, int(nb[0]), 1, "pagerank2", gamma=0.0),
+                                       oracle.transition_probs(g, v, -1, 0, "weighted"), rtol=1e-6)
+
+
 # ------------------------------------------------------------------ metapath
 def test_metapath_filter():
     g = synth.from_edges(5, [(0, 1), (0, 2), (0, 3), (0, 4)], h=[1.0, 2.0, 3.0, 4.0], labels=[0, 1, 1, 2])
@@ -143,7 +171,7 @@ from bruteforce import bf_paths as _bf_paths, merged_chisquare
 
 
 CASES = [("weighted", 1.0, 1.0, None), ("node2vec", 2.0, 0.5, None), ("node2vec", 0.25, 4.0, None),
-         ("node2vec", 3.0, 0.7, None), ("metapath", 1.0, 1.0, [0, 1, 2])]
+         ("node2vec", 3.0, 0.7, None), ("metapath", 1.0, 1.0, [0, 1, 2]), ("pagerank2", 1.0, 1.0, None)]
 
 
 @pytest.mark.parametrize("algo,p,q,schema", CASES)
@@ -275,7 +303,7 @@ def test_label_stats_match_library_reductions():
 
 
 @pytest.mark.parametrize("algo,p,q", [("node2vec", 2.0, 0.5), ("node2vec", 0.25, 4.0), ("node2vec", 4.0, 0.25),
-                                      ("metapath", 1, 1), ("weighted", 1, 1)])
+                                      ("metapath", 1, 1), ("weighted", 1, 1), ("pagerank2", 1, 1)])
 def test_bound_dominates_every_weight(algo, p, q):
     """eRJS is exact only if B >= max w~ (Sec. 3.3 proof): check on every
     (v, v') state of a graph."""
@@ -287,7 +315,9 @@ def test_bound_dominates_every_weight(algo, p, q):
         for vp in prevs:
             for step in ([0] if vp < 0 else [1, 2]):
                 wt = oracle.transition_weights(g, v, int(vp), step, algo, p, q, schema)
-                _, B, _ = oracle.step_plan(float(hmax[v]), float(hsum[v]), vp >= 0, algo, p, q, 4.0)
+                dv = int(g.offsets[v + 1] - g.offsets[v])
+                dp = int(g.offsets[vp + 1] - g.offsets[vp]) if vp >= 0 else 1
+                _, B, _ = oracle.step_plan(float(hmax[v]), float(hsum[v]), vp >= 0, algo, p, q, 4.0, dv=dv, dprev=dp)
                 if len(wt):
                     assert wt.max() <= B
 
