@@ -56,10 +56,11 @@ def parse():
                     "scales are for profiling captures)")
     ap.add_argument("--pq", action="append", default=None, help="restrict to one (p,q), e.g. --pq 4,0.25")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--suite", default="walk", choices=["walk", "batch", "serve", "metapath"],
+    ap.add_argument("--suite", default="walk", choices=["walk", "batch", "serve", "metapath", "skew"],
                     help="walk: the headline node2vec s22 line; batch: 64 mixed jobs on skewed R-MAT s24, "
                     "batched vs one launch per job; serve: Poisson query stream on s22, continuous batching vs "
-                    "serial calls; metapath: metapath walks on R-MAT s23")
+                    "serial calls; metapath: metapath walks on R-MAT s23; skew: Pareto / degree-based weights on "
+                    "s22, cost model vs eRJS-only / eRVS-only / random / degree-rule selection")
     ap.add_argument("--duration", type=float, default=10.0, help="serve suite: seconds of offered load")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve suite: mean arrivals per second")
     a = ap.parse_args()
@@ -235,7 +236,7 @@ def run_batch(args):
     g = synth.workload_graph("s24_skew")
     gen_s = time.perf_counter() - t0
     G = fw.Graph(g)
-    ratios = {a: G.autotune(a, p=1.0, q=1.0, schema=[0, 1, 2, 3, 4] if a == "metapath" else None)
+    ratios = {a: G.autotune(a, p=1.0, q=1.0, schema=[0, 1, 2, 3, 4] if a == "metapath" else None, method=1)
               for a in ["node2vec", "metapath", "weighted"]}
     rng = np.random.default_rng(44)
     specs = []
@@ -308,7 +309,7 @@ def run_metapath(args):
     g = synth.workload_graph("s23_meta")
     G = fw.Graph(g)
     starts = torch.from_numpy(synth.random_starts(g.n, 2_000_000, seed=43)).cuda()
-    r_meta = G.autotune("metapath", schema=[0, 1, 2, 3, 4], method=0)
+    r_meta = G.autotune("metapath", schema=[0, 1, 2, 3, 4], method=1)
     res = {}
     for L in (5, 40):
         out = torch.empty((starts.numel(), L + 1), dtype=torch.int32, device="cuda")
@@ -347,8 +348,9 @@ def run_serve(args):
     torch.cuda.set_device(0)
     g = synth.workload_graph("s22")
     G = fw.Graph(g)
-    ratios = {"node2vec": G.autotune("node2vec", p=2.0, q=0.5), "metapath": G.autotune("metapath", schema=[0, 1, 2, 3, 4]),
-              "weighted": G.autotune("weighted")}
+    ratios = {"node2vec": G.autotune("node2vec", p=2.0, q=0.5, method=1),
+              "metapath": G.autotune("metapath", schema=[0, 1, 2, 3, 4], method=1),
+              "weighted": G.autotune("weighted", method=1)}
     rng = np.random.default_rng(45)
     n_req = int(args.rate * args.duration)
     arrivals = np.cumsum(rng.exponential(1.0 / args.rate, n_req))
@@ -443,6 +445,68 @@ def run_serve(args):
     G.close()
 
 
+def run_skew(args):
+    """Weight skew (Sec. 5.2 power-law / degree-based weights, Sec. 5.3-5.4
+    ablations): the s22 structure with classical Pareto weights (x_m = 1,
+    shape alpha in {1, 1.5, 2, 3, 4}) and with degree-based weights
+    h(v, u) = d(u); weighted node2vec p = 2, q = 0.5; 2^18 random starts x 40
+    hops per run.  For each weight set: the cost model (profiled r) against
+    eRJS-only, eRVS-only, random and degree-rule (< 1K -> eRVS) selection,
+    with the share of steps the cost model gave eRJS."""
+    import torch
+    from paper_2512_00705_gb300 import _build, synth
+    from paper_2512_00705_gb300 import flexiwalk as fw
+    _build.build()
+    torch.cuda.set_device(0)
+    base = synth.rmat(22, 16, 0.57, 0.19, 0.19, seed=1)
+    starts = torch.from_numpy(synth.random_starts(base.n, 1 << 18, seed=47)).cuda()
+    L = 40
+    out = torch.empty((starts.numel(), L + 1), dtype=torch.int32, device="cuda")
+    sets = [(f"pareto{a:g}", synth.edge_weights(base, "pareto", a, seed=2)) for a in (1.0, 1.5, 2.0, 3.0, 4.0)]
+    sets.append(("degree", synth.degree_weights(base)))
+    res = {}
+    for name, h in sets:
+        G = fw.Graph(synth.Csr(base.offsets, base.cols, h))
+        r_sweep = G.autotune("node2vec", p=2.0, q=0.5, method=1)
+        r = G.autotune("node2vec", p=2.0, q=0.5, method=0)
+        row = {"cost_ratio_profiled": r, "cost_ratio_sweep": r_sweep}
+        for mode in ("auto", "auto_sweep", "rjs", "rvs", "random", "degree"):
+            rr = r_sweep if mode == "auto_sweep" else r
+            md = "auto" if mode == "auto_sweep" else mode
+            def go(flags=0):
+                G.walk(starts, L, "node2vec", p=2.0, q=0.5, mode=md, cost_ratio=rr, seed=SEED, flags=flags, out=out)
+            go()
+            ms = []
+            for _ in range(max(1, args.steps)):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                go()
+                e1.record()
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            row[f"{mode}_ms"] = statistics.median(ms)
+            if mode == "auto":
+                G.reset_counters()
+                go(fw.FLAG_COUNTERS)
+                c = G.counters()
+                row["hops"] = c["hops"]
+                row["rjs_share"] = c["rjs_steps"] / max(1, c["hops"])
+                row["rjs_trials_per_rjs_step"] = c["rjs_trials"] / max(1, c["rjs_steps"])
+        row["auto_speedup_vs_best_single"] = min(row["rjs_ms"], row["rvs_ms"]) / row["auto_ms"]
+        row["auto_sweep_speedup_vs_best_single"] = min(row["rjs_ms"], row["rvs_ms"]) / row["auto_sweep_ms"]
+        row["auto_speedup_vs_random"] = row["random_ms"] / row["auto_ms"]
+        row["auto_speedup_vs_degree_rule"] = row["degree_ms"] / row["auto_ms"]
+        res[name] = row
+        G.close()
+    hops = sum(r_["hops"] for r_ in res.values())
+    tot = sum(r_["auto_ms"] for r_ in res.values())
+    _line("walker-steps/sec (skewed weights, cost model)", hops / (tot / 1e3), "walker-steps/s", args, {
+        "ms_per_step": tot,
+        "config": {"workload": "weighted node2vec p=2 q=0.5 on R-MAT s22 structure, Pareto(alpha) and degree-based "
+                               "weights, 2^18 random starts x 40 hops"},
+        "skew": res})
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -453,6 +517,8 @@ def main():
         return run_metapath(args)
     if args.suite == "serve":
         return run_serve(args)
+    if args.suite == "skew":
+        return run_skew(args)
     import torch
     import torch.distributed as dist
 
@@ -491,11 +557,14 @@ def main():
     out = torch.empty((nw, LENGTH + 1), dtype=torch.int32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
 
-    # the runtime's profiling step (Sec. 5.1): r = EdgeCost_RJS / EdgeCost_RVS per (p, q),
-    # measured by the two profiling kernels before sampling; reported, not timed
+    # tuning before sampling, reported and not timed: r of Eq. (runtime) per (p, q) from the
+    # autotuner's sample-walk sweep; the Sec. 5.1 profiling kernels' r is reported beside it
     t_prof = time.perf_counter()
-    ratio = {(p, q): G.autotune("node2vec", p=p, q=q, method=0) for (p, q) in PQ}
+    ratio_profiled = {(p, q): G.autotune("node2vec", p=p, q=q, method=0) for (p, q) in PQ}
     profile_ms = (time.perf_counter() - t_prof) * 1e3
+    t_prof = time.perf_counter()
+    ratio = {(p, q): G.autotune("node2vec", p=p, q=q, method=1) for (p, q) in PQ}
+    sweep_ms = (time.perf_counter() - t_prof) * 1e3
 
     def walk(p, q, flags=0):
         r = ratio[(p, q)]
@@ -606,7 +675,8 @@ def main():
                    else "none", "walk_length": LENGTH, "edges": g.e,
                    "hops_per_step": hops_all, "l2": "256 MiB write between steps; graph and rows > L2",
                    "cost_ratio": {f"p{p:g}_q{q:g}": ratio[(p, q)] for (p, q) in PQ},
-                   "profile_ms": profile_ms, "preprocess_ms": G.info["preprocess_ms"],
+                   "cost_ratio_profiled": {f"p{p:g}_q{q:g}": ratio_profiled[(p, q)] for (p, q) in PQ},
+                   "profile_ms": profile_ms, "sweep_ms": sweep_ms, "preprocess_ms": G.info["preprocess_ms"],
                    "per_pq_ms": {f"p{p:g}_q{q:g}": statistics.median(per_launch[(p, q)]) for (p, q) in PQ},
                    "per_pq_hops": {f"p{p:g}_q{q:g}": counts[(p, q)]["hops"] for (p, q) in PQ},
                    "wall_s": wall},

@@ -68,7 +68,11 @@ typedef enum {
   FW_MODE_AUTO = 0,  /* cost model per walker-step, Eq. (runtime)          */
   FW_MODE_RJS = 1,   /* eRJS only (capped; a capped step finishes by eRVS) */
   FW_MODE_RVS = 2,   /* eRVS only                                           */
-  FW_MODE_EXACT = 3  /* exact FP32 inverse CDF (bit-exact parity mode)      */
+  FW_MODE_EXACT = 3,  /* exact FP32 inverse CDF (bit-exact parity mode)     */
+  FW_MODE_RANDOM = 4, /* baseline selection of Sec. 5.4: eRJS or eRVS by a
+                         fair coin per walker-step                             */
+  FW_MODE_DEGREE = 5  /* baseline selection of Sec. 5.4: eRVS when d(v) < 1000,
+                         eRJS otherwise                                        */
 } fw_mode;
 
 enum { FW_PTR_HOST = 0, FW_PTR_DEVICE = 1 };

@@ -50,7 +50,7 @@ fw_status make_job(const fw_graph* g, int32_t algo, const fw_params* params, uin
     return set_error(FW_ERR_ARG, "unknown algo");
   if (algo == ALGO_PAGERANK2 && !(P.gamma >= 0.0f && P.gamma <= 1.0f))
     return set_error(FW_ERR_ARG, "second-order PageRank needs gamma in [0, 1]");
-  if (P.mode < MODE_AUTO || P.mode > MODE_EXACT) return set_error(FW_ERR_ARG, "unknown mode");
+  if (P.mode < MODE_AUTO || P.mode > MODE_DEGREE) return set_error(FW_ERR_ARG, "unknown mode");
   if (algo == ALGO_NODE2VEC && !(P.p > 0.0f && P.q > 0.0f && std::isfinite(P.p) && std::isfinite(P.q)))
     return set_error(FW_ERR_ARG, "node2vec needs finite p, q > 0");
   if (algo == ALGO_METAPATH) {

@@ -5,8 +5,9 @@
 // for a fixed sample of nodes and a fixed number of their neighbours, one
 // the eRJS way (each thread one trial at a random neighbour position: Philox
 // draw, edge-record gather, squeeze / membership test) and one the eRVS way
-// (a warp keys the first neighbours of a node: coalesced loads, weights,
-// exponential keys, argmax); r is the ratio of their times per edge.  The
+// (a warp scans the first 256 neighbours of a node as eRVS does: coalesced
+// loads, weights, phase-1 keys, jumps, argmax); r is the ratio of their
+// times per edge.  The
 // kernels run the walk kernel's own device functions, so the ratio reflects
 // this GPU's caches and this graph.
 // Method 1 (an extension): time short sample walks for a ladder of r values
@@ -25,7 +26,8 @@ namespace fw {
 namespace {
 
 constexpr int kProfileNodes = 65536;  // sampled nodes (evenly spaced ids)
-constexpr int kProfileEdges = 32;     // neighbours evaluated per sampled node
+constexpr int kProfileEdges = 32;     // eRJS trials per sampled node
+constexpr int kProfileScan = 256;     // neighbours an eRVS scan covers per sampled node (jumps included)
 
 // Sample node i -> its id, a previous node (its first neighbour) and the rows.
 __device__ __forceinline__ bool profile_ctx(const DevGraph& g, const Job& J, int32_t i, int32_t stride, StepCtx& c) {
@@ -82,7 +84,7 @@ __global__ void profile_rvs_kernel(DevGraph g, Job J, int32_t count, int32_t str
   if (i >= count) return;  // warp-uniform
   StepCtx c;
   if (!profile_ctx(g, J, i, stride, c)) return;  // warp-uniform (same node for the whole warp)
-  c.d = min(c.d, kProfileEdges);
+  c.d = min(c.d, kProfileScan);
   LaneCounters lc;
   const int32_t k = rvs_pick<32, false>(g, J, c, lane, true, lc);
   if (lane == 0) {

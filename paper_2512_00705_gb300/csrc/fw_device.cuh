@@ -31,7 +31,8 @@ constexpr int kThreadRvsMaxDeg = 8;  // eRVS steps with d <= this run on one lan
 constexpr int kLabelStats = 8;       // per-label node statistics for labels 0..7
 
 enum : int32_t { ALGO_WEIGHTED = 0, ALGO_NODE2VEC = 1, ALGO_METAPATH = 2, ALGO_PAGERANK2 = 3 };
-enum : int32_t { MODE_AUTO = 0, MODE_RJS = 1, MODE_RVS = 2, MODE_EXACT = 3 };
+enum : int32_t { MODE_AUTO = 0, MODE_RJS = 1, MODE_RVS = 2, MODE_EXACT = 3, MODE_RANDOM = 4, MODE_DEGREE = 5 };
+constexpr int32_t kDegreeRuleThreshold = 1000;  // Sec. 5.4 degree-based selection
 enum : int32_t { JOB_WALK = 0, JOB_HIST = 1 };
 enum : int32_t { PLAN_NONE = 0, PLAN_RJS = 1, PLAN_RVS_T = 2, PLAN_RVS_W = 3, PLAN_EXACT_T = 4, PLAN_EXACT_W = 5 };
 enum : uint32_t { DEVERR_START = 1u };

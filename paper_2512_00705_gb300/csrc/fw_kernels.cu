@@ -236,7 +236,13 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
             if (J.algo == ALGO_PAGERANK2 && c.vp >= 0) pagerank2_weights(J, c.d, c.pe - c.ps, c.w1, c.w2);
             choice = plan_choice(J, hm, hs, c.vp >= 0, c.w1, c.w2, B, S);
           }
-          if (m == MODE_AUTO) m = choice;
+          if (m == MODE_AUTO) {
+            m = choice;
+          } else if (m == MODE_RANDOM) {  // coin from Philox counter (wid, hop, 4, 0)
+            m = (philox(make_uint4(c.wid, (uint32_t)c.step, 4u, 0u), J.key0, J.key1).x >> 31) ? MODE_RJS : MODE_RVS;
+          } else if (m == MODE_DEGREE) {
+            m = (c.d < kDegreeRuleThreshold) ? MODE_RVS : MODE_RJS;
+          }
           plan = (m == MODE_RJS) ? PLAN_RJS : ((c.d <= kThreadRvsMaxDeg) ? PLAN_RVS_T : PLAN_RVS_W);
           if (plan == PLAN_RJS && J.split_return && c.vp >= 0) {
             // the return edge alone sets max(w) = 1/p: propose it separately and

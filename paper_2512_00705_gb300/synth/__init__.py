@@ -119,6 +119,12 @@ def edge_weights(g: Csr, kind: str = "uniform01", param: float = 1.0, seed: int 
     return out
 
 
+def degree_weights(g: Csr) -> np.ndarray:
+    """Degree-based property weights: h(v, u) = d(u), the target's degree
+    (not symmetric: h(v, u) != h(u, v) in general)."""
+    return g.degrees()[g.cols].astype(np.float32)
+
+
 def edge_labels(g: Csr, nlabels: int = 5, seed: int = 3, threads: int = 0) -> np.ndarray:
     """One label in {0..nlabels-1} per undirected edge (mirrored entries equal)."""
     lib = _load()

@@ -170,7 +170,8 @@ def _states(g):
     return out
 
 
-@pytest.mark.parametrize("mode,flags", [("rjs", 0), ("rvs", 0), ("rvs", fw.FLAG_RVS_NOJUMP), ("auto", 0)])
+@pytest.mark.parametrize("mode,flags", [("rjs", 0), ("rvs", 0), ("rvs", fw.FLAG_RVS_NOJUMP), ("auto", 0), ("random", 0),
+                                        ("degree", 0)])
 @pytest.mark.parametrize("algo,p,q,schema", [("node2vec", 2.0, 0.5, None), ("node2vec", 0.25, 4.0, None),
                                              ("metapath", 1.0, 1.0, [0, 1, 2, 3, 4]), ("weighted", 1.0, 1.0, None),
                                              ("pagerank2", 1.0, 1.0, None)])
