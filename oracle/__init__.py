@@ -18,6 +18,8 @@ sampling, its own Philox4x32-10), compiled here with gcc and
   step_plan             bound (Sec. 3.3) + sum estimate (Eq. sum_estimation)
                         + cost-model choice (Eq. runtime)
   label_stats           per-node, per-label max / sum of h (labels < 8)
+  quantize_weights      8-bit weight codes with one scale per graph (Sec. 6.2
+                        names low-precision weights as an extension)
 
 Graph arguments are any object with ``offsets``, ``cols``, ``h`` (or None)
 and ``labels`` (or None) numpy attributes.
@@ -86,6 +88,8 @@ def _load():
             L.or_step_plan.restype = ctypes.c_int
             L.or_label_stats.argtypes = [vp, vp, vp, i32, vp, vp]
             L.or_label_stats.restype = ctypes.c_int
+            L.or_quantize_weights.argtypes = [vp, i64, vp, vp]
+            L.or_quantize_weights.restype = f32
             _lib = L
     return _lib
 
@@ -225,3 +229,12 @@ def label_stats(g):
     if _load().or_label_stats(_ptr(offsets), _ptr(h), _ptr(labels), n, _ptr(lmax), _ptr(lsum)) != 0:
         raise ValueError("labels missing or >= 8")
     return lmax, lsum
+
+
+def quantize_weights(h):
+    """(codes uint8[e], scale float, dequantized float32[e]) of property weights h."""
+    hh = np.ascontiguousarray(h, dtype=np.float32)
+    codes = np.zeros(hh.shape[0], dtype=np.uint8)
+    hq = np.zeros(hh.shape[0], dtype=np.float32)
+    s = _load().or_quantize_weights(_ptr(hh), hh.shape[0], _ptr(codes), _ptr(hq))
+    return codes, float(np.float32(s)), hq

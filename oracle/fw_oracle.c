@@ -27,6 +27,9 @@
  *                             distinct return values of w; eRJS iff r * B < sum-hat
  *   Philox4x32-10             Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
  *                             as 1, 2, 3", SC'11.
+ *   8-bit weights, Sec. 6.2   (an extension the paper names, not specified by it) symmetric
+ *                             linear quantization with one scale per graph:
+ *                             s = max h / 255, code = clamp(rint(h / s), 1, 255), h' = code * s
  *
  * Readings where the paper is silent (each also listed in the design notes):
  *   - Hop 0 of node2vec has no previous node (vprev < 0): w = 1 for every
@@ -386,4 +389,26 @@ int or_label_stats(const int32_t *offsets, const float *h, const uint8_t *labels
     }
   }
   return 0;
+}
+
+/* 8-bit property weights (Sec. 6.2 names low-precision weights as an
+ * extension; the format is this reading): one FP32 scale per graph,
+ * s = (max over all edges of h) / 255, each weight stored as the nearest
+ * integer multiple of s (ties to even), kept within 1..255 so that no edge
+ * loses its weight, and read back as code * s.  FP32 throughout, each
+ * operation rounded once.  codes / hq may be NULL.  Returns s (0 if e = 0). */
+float or_quantize_weights(const float *h, int64_t e, uint8_t *codes, float *hq) {
+  if (e <= 0) return 0.0f;
+  float hmax = h[0];
+  for (int64_t i = 1; i < e; ++i)
+    if (h[i] > hmax) hmax = h[i];
+  const float s = hmax / 255.0f;
+  for (int64_t i = 0; i < e; ++i) {
+    float c = rintf(h[i] / s);
+    if (c < 1.0f) c = 1.0f;
+    if (c > 255.0f) c = 255.0f;
+    if (codes) codes[i] = (uint8_t)c;
+    if (hq) hq[i] = c * s;
+  }
+  return s;
 }

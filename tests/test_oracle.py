@@ -302,6 +302,64 @@ def test_label_stats_match_library_reductions():
     np.testing.assert_allclose(lsum.sum(axis=1), hsum, rtol=1e-12)
 
 
+# ------------------------------------------------------ 8-bit weights
+def test_quantize_on_the_integer_grid():
+    """max h = 255 makes the scale exactly 1: codes are h rounded to the
+    nearest integer with ties to even, kept in 1..255, and read back exactly."""
+    h = np.array([255.0, 1.0, 2.0, 0.4, 2.5, 3.5, 254.5, 100.49, 0.5, 1.5, 17.0], np.float32)
+    codes, s, hq = oracle.quantize_weights(h)
+    assert s == 1.0
+    np.testing.assert_array_equal(codes, [255, 1, 2, 1, 2, 4, 254, 100, 1, 2, 17])
+    np.testing.assert_array_equal(hq, codes.astype(np.float32))
+    c0, s0, _ = oracle.quantize_weights(np.zeros(0, np.float32))
+    assert s0 == 0.0 and c0.shape == (0,)
+
+
+@pytest.mark.parametrize("kind,param", [("uniform01", 1.0), ("lognormal", 1.0), ("pareto", 1.5)])
+def test_quantize_is_nearest_code_within_half_a_step(kind, param):
+    """Against fp64: s is max(h)/255 rounded once, every unclamped code is the
+    nearest integer to h/s (|code - h/s| <= 1/2, so a floor or a ceiling
+    fails), the largest weight gets 255, and only weights below s/2 clamp."""
+    g = synth.rmat(12, 16, seed=5)
+    h = synth.edge_weights(g, kind, param, seed=6)
+    codes, s, hq = oracle.quantize_weights(h)
+    hmax = float(h.max())
+    assert s == float(np.float32(hmax / 255.0))
+    assert codes.min() >= 1 and codes[np.argmax(h)] == 255
+    ratio = h.astype(np.float64) / s
+    un = ratio >= 0.5 + 1e-6
+    assert np.all(np.abs(codes[un] - ratio[un]) <= 0.5 + 1e-5)
+    assert np.all(codes[~un] == 1)
+    np.testing.assert_array_equal(hq, (codes.astype(np.float64) * s).astype(np.float32))
+    assert np.all(np.abs(hq[un].astype(np.float64) - h[un]) <= 0.5 * s * (1 + 1e-5))
+
+
+def test_quantize_commutes_with_power_of_two_scaling():
+    """Scaling every weight by 2^k scales s by 2^k exactly and keeps the codes."""
+    h = synth.edge_weights(synth.rmat(10, 8, seed=2), "lognormal", 1.0, seed=3)
+    c, s, _ = oracle.quantize_weights(h)
+    for k in (-3, 5):
+        ck, sk, _ = oracle.quantize_weights(h * np.float32(2.0 ** k))
+        assert sk == s * 2.0 ** k
+        np.testing.assert_array_equal(ck, c)
+
+
+def test_quantized_integer_weights_leave_walks_unchanged():
+    """Integer weights with maximum 255 are their own codes, so exact-mode
+    walks over the dequantized weights equal those over the originals."""
+    g = synth.rmat(10, 8, seed=4)
+    rng = np.random.default_rng(1)
+    w = synth.edge_weights(g, "uniform01", seed=5)
+    h = np.ceil(w * 255.0).astype(np.float32)
+    h[np.argmax(h)] = 255.0
+    _, s, hq = oracle.quantize_weights(h)
+    assert s == 1.0 and np.array_equal(hq, h)
+    starts = rng.integers(0, g.n, 500).astype(np.int32)
+    a, _ = oracle.walk(synth.Csr(g.offsets, g.cols, h), starts, 12, "node2vec", 2.0, 0.5, seed=8)
+    b, _ = oracle.walk(synth.Csr(g.offsets, g.cols, hq), starts, 12, "node2vec", 2.0, 0.5, seed=8)
+    assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("algo,p,q", [("node2vec", 2.0, 0.5), ("node2vec", 0.25, 4.0), ("node2vec", 4.0, 0.25),
                                       ("metapath", 1, 1), ("weighted", 1, 1), ("pagerank2", 1, 1)])
 def test_bound_dominates_every_weight(algo, p, q):
