@@ -61,6 +61,8 @@ def parse():
                     "batched vs one launch per job; serve: Poisson query stream on s22, continuous batching vs "
                     "serial calls; metapath: metapath walks on R-MAT s23; skew: Pareto / degree-based weights on "
                     "s22, cost model vs eRJS-only / eRVS-only / random / degree-rule selection")
+    ap.add_argument("--int8", action="store_true", help="walk suite: store the weights as 8-bit codes "
+                    "(fw_graph_quantize_weights) before tuning and timing")
     ap.add_argument("--duration", type=float, default=10.0, help="serve suite: seconds of offered load")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve suite: mean arrivals per second")
     a = ap.parse_args()
@@ -448,11 +450,13 @@ def run_serve(args):
 def run_skew(args):
     """Weight skew (Sec. 5.2 power-law / degree-based weights, Sec. 5.3-5.4
     ablations): the s22 structure with classical Pareto weights (x_m = 1,
-    shape alpha in {1, 1.5, 2, 3, 4}) and with degree-based weights
-    h(v, u) = d(u); weighted node2vec p = 2, q = 0.5; 2^18 random starts x 40
-    hops per run.  For each weight set: the cost model (profiled r) against
-    eRJS-only, eRVS-only, random and degree-rule (< 1K -> eRVS) selection,
-    with the share of steps the cost model gave eRJS."""
+    shape alpha in {1, 1.5, 2, 3, 4}), degree-based weights h(v, u) = d(u),
+    U(0,1] weights and no weights (h = 1); weighted node2vec p = 2, q = 0.5;
+    2^18 random starts x 40 hops per run.  For each weight set: the cost
+    model (profiled r, and the sweep's r) against eRJS-only, eRVS-only,
+    random and degree-rule (< 1K -> eRVS) selection, with the share of steps
+    the cost model gave eRJS; then the weights as 8-bit codes (Sec. 6.2
+    extension), re-tuned, under the cost model."""
     import torch
     from paper_2512_00705_gb300 import _build, synth
     from paper_2512_00705_gb300 import flexiwalk as fw
@@ -464,6 +468,8 @@ def run_skew(args):
     out = torch.empty((starts.numel(), L + 1), dtype=torch.int32, device="cuda")
     sets = [(f"pareto{a:g}", synth.edge_weights(base, "pareto", a, seed=2)) for a in (1.0, 1.5, 2.0, 3.0, 4.0)]
     sets.append(("degree", synth.degree_weights(base)))
+    sets.append(("uniform01", synth.edge_weights(base, "uniform01", seed=2)))
+    sets.append(("unweighted", None))
     res = {}
     for name, h in sets:
         G = fw.Graph(synth.Csr(base.offsets, base.cols, h))
@@ -492,6 +498,21 @@ def run_skew(args):
                 row["hops"] = c["hops"]
                 row["rjs_share"] = c["rjs_steps"] / max(1, c["hops"])
                 row["rjs_trials_per_rjs_step"] = c["rjs_trials"] / max(1, c["rjs_steps"])
+        if h is not None:
+            # the same weights as 8-bit codes: re-tuned, cost model only
+            row["int8_scale"] = G.quantize_weights()
+            r8 = G.autotune("node2vec", p=2.0, q=0.5, method=1)
+            row["cost_ratio_sweep_int8"] = r8
+            G.walk(starts, L, "node2vec", p=2.0, q=0.5, mode="auto", cost_ratio=r8, seed=SEED, out=out)
+            ms = []
+            for _ in range(max(1, args.steps)):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                G.walk(starts, L, "node2vec", p=2.0, q=0.5, mode="auto", cost_ratio=r8, seed=SEED, out=out)
+                e1.record()
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            row["auto_int8_ms"] = statistics.median(ms)
         row["auto_speedup_vs_best_single"] = min(row["rjs_ms"], row["rvs_ms"]) / row["auto_ms"]
         row["auto_sweep_speedup_vs_best_single"] = min(row["rjs_ms"], row["rvs_ms"]) / row["auto_sweep_ms"]
         row["auto_speedup_vs_random"] = row["random_ms"] / row["auto_ms"]
@@ -502,8 +523,8 @@ def run_skew(args):
     tot = sum(r_["auto_ms"] for r_ in res.values())
     _line("walker-steps/sec (skewed weights, cost model)", hops / (tot / 1e3), "walker-steps/s", args, {
         "ms_per_step": tot,
-        "config": {"workload": "weighted node2vec p=2 q=0.5 on R-MAT s22 structure, Pareto(alpha) and degree-based "
-                               "weights, 2^18 random starts x 40 hops"},
+        "config": {"workload": "weighted node2vec p=2 q=0.5 on R-MAT s22 structure, Pareto(alpha), degree-based, "
+                               "U(0,1] and no weights, 2^18 random starts x 40 hops"},
         "skew": res})
 
 
@@ -540,6 +561,8 @@ def main():
         g = synth.rmat(args.scale, 16, 0.57, 0.19, 0.19, seed=1)
         g.h = synth.edge_weights(g, "uniform01", seed=2)
     G = fw.Graph(g)
+    if args.int8:
+        G.quantize_weights()
     n = g.n
     stream = torch.cuda.current_stream()
     from paper_2512_00705_gb300 import sharding
@@ -660,7 +683,7 @@ def main():
     peak, peak_kind = measured_peaks()
     kern_ms = sum(sum(v) for v in per_launch.values()) / args.steps
     achieved = bytes_per_step / (kern_ms / 1000.0) / 1e9
-    traffic = read_traffic() if args.scale == 22 else None
+    traffic = read_traffic() if args.scale == 22 and not args.int8 else None
     traffic_per_launch = None
     if traffic is not None:
         traffic_per_launch = sum(traffic[pq] * counts[pq]["hops"] for pq in PQ) / len(PQ)
@@ -669,8 +692,9 @@ def main():
         "metric": "walker-steps/sec", "value": value, "unit": "walker-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.scale == 22 and len(PQ) == 3 else
-                   f"node2vec R-MAT s{args.scale} ef16 (profiling case), (p,q)={PQ}", "walkers": n * world,
+        "config": {"workload": (WORKLOAD if args.scale == 22 and len(PQ) == 3 else
+                                f"node2vec R-MAT s{args.scale} ef16 (profiling case), (p,q)={PQ}")
+                   + ("; weights stored as 8-bit codes x FP32 scale" if args.int8 else ""), "walkers": n * world,
                    "walkers_per_gpu": nw, "sharding": "replicas of the workload hashed by start node" if world > 1
                    else "none", "walk_length": LENGTH, "edges": g.e,
                    "hops_per_step": hops_all, "l2": "256 MiB write between steps; graph and rows > L2",

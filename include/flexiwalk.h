@@ -119,6 +119,7 @@ typedef struct {
                                 same weight (found at creation)                   */
   float cost_ratios[3];      /* r per algorithm (weighted, node2vec, metapath)   */
   uint64_t fingerprint;      /* hash of sizes and sampled CSR entries (cache key)*/
+  float weight_scale;        /* s after fw_graph_quantize_weights, else 0        */
 } fw_graph_info_t;
 
 /* Per-walk counters (FW_FLAG_COUNTERS).  Byte figures follow the
@@ -176,6 +177,24 @@ fw_status fw_graph_node_stats(const fw_graph* graph, float* hmax, float* hsum, v
  * plan uses them for the required label: B = max, exact sum for Eq.
  * (runtime), and zero sum = dead end.  Asynchronous on `stream`. */
 fw_status fw_graph_label_stats(const fw_graph* graph, float* stats, void* stream);
+
+/*
+ * Store the property weights as 8-bit codes (a low-precision weight format,
+ * named in Sec. 6.2 as an extension of the method): with the per-graph
+ * scale s = max_e h_e / 255 (FP32 division), each weight becomes
+ *   code_e = clamp(rint(h_e / s), 1, 255)       (round half to even)
+ * and from then on the graph samples with the dequantized weights
+ *   h'_e = code_e * s                            (FP32 product).
+ * Codes never round to 0, so every edge keeps a positive weight.  The
+ * preprocessing (h_MAX, h_SUM, edge records, label statistics) and the
+ * fingerprint are recomputed from h'; scans in eRVS and exact mode then read
+ * one byte per weight.  *scale_out (may be NULL) receives s.  A second call
+ * is a no-op.  Synchronous on `stream`; no walk may run on the graph
+ * meanwhile.  Errors: FW_ERR_ARG, FW_ERR_UNSUPPORTED (graph without
+ * weights), FW_ERR_OOM / FW_ERR_CUDA (the graph is unchanged when the codes
+ * cannot be allocated).
+ */
+fw_status fw_graph_quantize_weights(fw_graph* graph, float* scale_out, void* stream);
 
 /* Set the graph's cost ratio r of Eq. (runtime) for every algorithm (must
  * be finite, > 0). */

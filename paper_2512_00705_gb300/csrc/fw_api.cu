@@ -29,6 +29,8 @@ DevGraph dev_graph(const fw_graph* g) {
   d.off = g->d_off;
   d.col = g->d_col;
   d.h = g->d_h;
+  d.h8 = g->d_h8;
+  d.hscale = g->hscale;
   d.lab = g->d_lab;
   d.hmax = g->d_hmax;
   d.hsum = g->d_hsum;
@@ -91,6 +93,57 @@ fw_status make_job(const fw_graph* g, int32_t algo, const fw_params* params, uin
   job->pr_1g = 1.0f - P.gamma;
   job->label_stats = (algo == ALGO_METAPATH && g->d_lstat && !(P.flags & FW_FLAG_PAPER_SUM) &&
                       (job->weighted || !g->d_h)) ? 1 : 0;
+  return FW_OK;
+}
+
+// The per-graph preprocessing (Sec. 4.2 preprocess()): node records with
+// h_MAX / h_SUM and the maximum degree, 32-byte edge records, the weight
+// symmetry check and per-label statistics, all from the current weights.
+fw_status rebuild_derived(fw_graph* g, cudaStream_t st) {
+  const int32_t n = g->n;
+  const int64_t e = g->e;
+  int* d_maxdeg = reinterpret_cast<int*>(g->d_err) + 8;
+  unsigned* d_asym = g->d_err + 12;
+  unsigned* d_lbad = g->d_err + 13;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaError_t le = cudaMemsetAsync(d_maxdeg, 0, sizeof(int), st);
+  if (le == cudaSuccess) le = cudaMemsetAsync(d_asym, 0, 2 * sizeof(unsigned), st);
+  cudaEventRecord(e0, st);
+  if (le == cudaSuccess)
+    le = launch_node_stats(g->d_off, g->d_h, n, g->d_hmax, g->d_hsum, g->d_nrec, d_maxdeg, g->num_sms, st);
+  if (le == cudaSuccess) le = launch_edge_records(g->d_col, g->d_h, g->d_lab, g->d_nrec, e, g->d_erec, g->num_sms, st);
+  if (le == cudaSuccess) le = launch_symmetry(g->d_off, g->d_col, g->d_h, n, d_asym, g->num_sms, st);
+  const bool want_labels = g->d_lab != nullptr && !g->lstat_bad;
+  if (le == cudaSuccess && want_labels && !g->d_lstat) {
+    le = cudaMalloc(&g->d_lstat, sizeof(float2) * kLabelStats * ((size_t)n + 1));
+    if (le == cudaSuccess) g->bytes += sizeof(float2) * kLabelStats * ((size_t)n + 1);
+  }
+  if (le == cudaSuccess && want_labels)
+    le = launch_label_stats(g->d_off, g->d_h, g->d_lab, n, g->d_lstat, d_lbad, g->num_sms, st);
+  cudaEventRecord(e1, st);
+  int maxdeg = 0;
+  unsigned flags[2] = {1, 0};
+  cudaError_t ce = cudaMemcpyAsync(&maxdeg, d_maxdeg, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(flags, d_asym, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  cudaError_t se = cudaStreamSynchronize(st);
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (le != cudaSuccess) return cuda_error(le, "preprocessing kernels");
+  if (ce != cudaSuccess) return cuda_error(ce, "read preprocessing results");
+  if (se != cudaSuccess) return cuda_error(se, "sync after preprocessing");
+  g->max_degree = maxdeg;
+  g->sym = flags[0] == 0 ? 1 : 0;
+  if (want_labels && flags[1] != 0) {  // a label >= kLabelStats: per-label statistics unused
+    cudaFree(g->d_lstat);
+    g->d_lstat = nullptr;
+    g->bytes -= sizeof(float2) * kLabelStats * ((size_t)n + 1);
+    g->lstat_bad = true;
+  }
+  g->preprocess_ms += ms;
   return FW_OK;
 }
 
@@ -172,6 +225,7 @@ static void free_graph(fw_graph* g) {
   cudaFree(g->d_nrec);
   cudaFree(g->d_erec);
   cudaFree(g->d_lstat);
+  cudaFree(g->d_h8);
   cudaFree(g->d_err);
   cudaFree(g->d_cnt);
   cudaFree(g->d_stage_starts);
@@ -246,50 +300,13 @@ extern "C" fw_status fw_graph_create(const int32_t* offsets, const int32_t* cols
       return set_error(FW_ERR_CSR, why);
     }
   }
-  // preprocessing: h_MAX, h_SUM, max degree
-  int* d_maxdeg = reinterpret_cast<int*>(g->d_err) + 8;
-  FW_TRY(cudaMemsetAsync(d_maxdeg, 0, sizeof(int), st), "cudaMemsetAsync");
-  cudaEvent_t e0, e1;
-  FW_TRY(cudaEventCreate(&e0), "cudaEventCreate");
-  FW_TRY(cudaEventCreate(&e1), "cudaEventCreate");
-  cudaEventRecord(e0, st);
-  unsigned* d_asym = g->d_err + 12;
-  cudaError_t le = cudaMemsetAsync(d_asym, 0, sizeof(unsigned), st);
-  if (le == cudaSuccess)
-    le = launch_node_stats(g->d_off, g->d_h, n, g->d_hmax, g->d_hsum, g->d_nrec, d_maxdeg, g->num_sms, st);
-  if (le == cudaSuccess) le = launch_edge_records(g->d_col, g->d_h, g->d_lab, g->d_nrec, e, g->d_erec, g->num_sms, st);
-  if (le == cudaSuccess) le = launch_symmetry(g->d_off, g->d_col, g->d_h, n, d_asym, g->num_sms, st);
-  unsigned* d_lbad = g->d_err + 13;
-  if (le == cudaSuccess && labels) {
-    le = cudaMalloc(&g->d_lstat, sizeof(float2) * kLabelStats * ((size_t)n + 1));
-    if (le == cudaSuccess) le = cudaMemsetAsync(d_lbad, 0, sizeof(unsigned), st);
-    if (le == cudaSuccess)
-      le = launch_label_stats(g->d_off, g->d_h, g->d_lab, n, g->d_lstat, d_lbad, g->num_sms, st);
+  {
+    fw_status fs = rebuild_derived(g, st);
+    if (fs != FW_OK) {
+      free_graph(g);
+      return fs;
+    }
   }
-  cudaEventRecord(e1, st);
-  int maxdeg = 0;
-  unsigned asym = 1;
-  cudaError_t ce = cudaMemcpyAsync(&maxdeg, d_maxdeg, sizeof(int), cudaMemcpyDeviceToHost, st);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(&asym, d_asym, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
-  unsigned lbad = 1;
-  if (ce == cudaSuccess && labels) ce = cudaMemcpyAsync(&lbad, d_lbad, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
-  cudaError_t se = cudaStreamSynchronize(st);
-  float ms = 0.0f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  FW_TRY(le, "node stats kernel");
-  FW_TRY(ce, "read max degree");
-  FW_TRY(se, "sync after preprocessing");
-  FW_TRY(cudaMemsetAsync(d_maxdeg, 0, sizeof(int), st), "cudaMemsetAsync");
-  g->max_degree = maxdeg;
-  g->sym = asym == 0 ? 1 : 0;
-  if (g->d_lstat && lbad != 0) {  // a label >= kLabelStats: per-label statistics unused
-    cudaFree(g->d_lstat);
-    g->d_lstat = nullptr;
-  }
-  if (g->d_lstat) g->bytes += sizeof(float2) * kLabelStats * ((size_t)n + 1);
-  g->preprocess_ms = ms;
   {
     fw_status fs = graph_fingerprint(g, st, &g->fingerprint);
     if (fs != FW_OK) {
@@ -321,6 +338,7 @@ extern "C" fw_status fw_graph_info(const fw_graph* g, fw_graph_info_t* info) {
   info->preprocess_ms = g->preprocess_ms;
   info->device_bytes = g->bytes;
   info->symmetric = g->sym;
+  info->weight_scale = g->d_h8 ? g->hscale : 0.0f;
   return FW_OK;
 }
 
@@ -340,6 +358,37 @@ extern "C" fw_status fw_graph_label_stats(const fw_graph* g, float* stats, void*
   cudaError_t e = cudaMemcpyAsync(stats, g->d_lstat, sizeof(float2) * kLabelStats * (size_t)g->n,
                                   cudaMemcpyDeviceToDevice, reinterpret_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? FW_OK : cuda_error(e, "copy label statistics");
+}
+
+extern "C" fw_status fw_graph_quantize_weights(fw_graph* g, float* scale_out, void* stream) {
+  if (!g) return set_error(FW_ERR_ARG, "graph is NULL");
+  if (!g->d_h) return set_error(FW_ERR_UNSUPPORTED, "the graph has no weights");
+  if (g->d_h8) {
+    if (scale_out) *scale_out = g->hscale;
+    return FW_OK;  // already quantized
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  uint8_t* codes = nullptr;
+  cudaError_t e = cudaMalloc(&codes, (size_t)(g->e > 0 ? g->e : 1));
+  if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(weight codes)");
+  float scale = 0.0f;
+  if (g->e > 0) {
+    e = launch_quantize(g->d_h, g->e, codes, &scale, g->d_err + 14, g->num_sms, st);
+    // the FP32 copy now holds the dequantized weights every derived structure is rebuilt from
+    if (e == cudaSuccess) e = launch_dequantize(codes, g->e, scale, g->d_h, g->num_sms, st);
+  }
+  if (e != cudaSuccess) {
+    cudaFree(codes);
+    return cuda_error(e, "weight quantization");
+  }
+  g->d_h8 = codes;
+  g->hscale = scale;
+  g->bytes += (size_t)g->e;
+  fw_status s = rebuild_derived(g, st);
+  if (s == FW_OK) s = graph_fingerprint(g, st, &g->fingerprint);
+  if (s != FW_OK) return s;
+  if (scale_out) *scale_out = scale;
+  return FW_OK;
 }
 
 extern "C" fw_status fw_graph_set_cost_ratio(fw_graph* g, float ratio) {

@@ -41,6 +41,8 @@ struct DevGraph {
   const int32_t* __restrict__ off;
   const int32_t* __restrict__ col;
   const float* __restrict__ h;     // nullptr: h = 1
+  const uint8_t* __restrict__ h8;  // 8-bit weight codes (nullptr: FP32 weights); h = code * hscale
+  float hscale;
   const uint8_t* __restrict__ lab; // nullptr: no labels
   const float* __restrict__ hmax;
   const float* __restrict__ hsum;
@@ -208,8 +210,10 @@ __device__ __forceinline__ bool row_contains(const int32_t* __restrict__ col, in
   return row_find(col, lo, hi, u, n, probes) >= 0;
 }
 
+// Property weight of CSR entry i: FP32, or an 8-bit code times the graph's scale.
 __device__ __forceinline__ float load_h(const DevGraph& g, const Job& J, int32_t i) {
-  return J.weighted ? __ldg(g.h + i) : 1.0f;
+  if (!J.weighted) return 1.0f;
+  return g.h8 ? __fmul_rn((float)__ldg(g.h8 + i), g.hscale) : __ldg(g.h + i);
 }
 
 // Transition weight of the neighbour at CSR index i (= s + k) of step c.

@@ -16,6 +16,8 @@
 //                   the result goes back to the owning lane.
 //   * update        [Sec. 4.2, update()]: prev <- cur, cur <- next, row write.
 // All loops are bounded (trial cap, degree, walk length); there are no waits.
+#include <cstring>
+
 #include "fw_internal.h"
 
 namespace fw {
@@ -595,6 +597,57 @@ cudaError_t launch_symmetry(const int32_t* off, const int32_t* col, const float*
   const long long want = ((long long)n * 32 + 255) / 256;
   const int grid = (int)(want < (long long)num_sms * 8 ? want : (long long)num_sms * 8);
   symmetry_kernel<<<grid, 256, 0, stream>>>(off, col, h, n, flag);
+  g_launches.fetch_add(1);
+  return cudaGetLastError();
+}
+
+// 8-bit weights: scale = max(h) / 255 (FP32 division), code = rint(h / scale)
+// clamped to [1, 255] (h > 0 stays > 0); the walks then use code * scale.
+__global__ void max_bits_kernel(const float* __restrict__ h, long long e, unsigned* __restrict__ maxbits) {
+  unsigned m = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < e; i += (long long)gridDim.x * blockDim.x)
+    m = max(m, __float_as_uint(h[i]));  // h > 0: the bit patterns order like the values
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(maxbits, m);
+}
+
+__global__ void quantize_kernel(const float* __restrict__ h, long long e, const unsigned* __restrict__ maxbits,
+                                uint8_t* __restrict__ codes) {
+  const float scale = __fdiv_rn(__uint_as_float(*maxbits), 255.0f);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < e; i += (long long)gridDim.x * blockDim.x) {
+    const float c = rintf(__fdiv_rn(h[i], scale));
+    codes[i] = (uint8_t)fminf(255.0f, fmaxf(1.0f, c));
+  }
+}
+
+__global__ void dequantize_kernel(const uint8_t* __restrict__ codes, long long e, float scale, float* __restrict__ h) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < e; i += (long long)gridDim.x * blockDim.x)
+    h[i] = __fmul_rn((float)codes[i], scale);
+}
+
+cudaError_t launch_quantize(float* h, long long e, uint8_t* codes, float* scale_out, unsigned* maxbits, int num_sms,
+                            cudaStream_t stream) {
+  const int grid = num_sms * 8;
+  cudaError_t err = cudaMemsetAsync(maxbits, 0, sizeof(unsigned), stream);
+  if (err != cudaSuccess) return err;
+  max_bits_kernel<<<grid, 256, 0, stream>>>(h, e, maxbits);
+  quantize_kernel<<<grid, 256, 0, stream>>>(h, e, maxbits, codes);
+  g_launches.fetch_add(2);
+  err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  unsigned bits = 0;
+  err = cudaMemcpyAsync(&bits, maxbits, sizeof(unsigned), cudaMemcpyDeviceToHost, stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
+  if (err != cudaSuccess) return err;
+  float mx;
+  std::memcpy(&mx, &bits, sizeof(float));
+  *scale_out = mx / 255.0f;  // the same FP32 division as the kernel
+  return cudaSuccess;
+}
+
+cudaError_t launch_dequantize(const uint8_t* codes, long long e, float scale, float* h, int num_sms, cudaStream_t stream) {
+  dequantize_kernel<<<num_sms * 8, 256, 0, stream>>>(codes, e, scale, h);
   g_launches.fetch_add(1);
   return cudaGetLastError();
 }

@@ -42,7 +42,8 @@ class fw_graph_info_t(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("e", ctypes.c_int64), ("max_degree", ctypes.c_int32),
                 ("has_weights", ctypes.c_int32), ("has_labels", ctypes.c_int32), ("cost_ratio", ctypes.c_float),
                 ("preprocess_ms", ctypes.c_double), ("device_bytes", ctypes.c_size_t), ("symmetric", ctypes.c_int32),
-                ("cost_ratios", ctypes.c_float * 3), ("fingerprint", ctypes.c_uint64)]
+                ("cost_ratios", ctypes.c_float * 3), ("fingerprint", ctypes.c_uint64),
+                ("weight_scale", ctypes.c_float)]
 
 
 class fw_job(ctypes.Structure):
@@ -97,6 +98,7 @@ def lib() -> ctypes.CDLL:
                 "fw_graph_node_stats": (ctypes.c_int, [vp, vp, vp, vp]),
                 "fw_graph_set_cost_ratio": (ctypes.c_int, [vp, ctypes.c_float]),
                 "fw_graph_label_stats": (ctypes.c_int, [vp, vp, vp]),
+                "fw_graph_quantize_weights": (ctypes.c_int, [vp, P(ctypes.c_float), vp]),
                 "fw_autotune": (ctypes.c_int, [vp, i32, P(fw_params), i32, ctypes.c_char_p, P(ctypes.c_float), vp]),
                 "fw_walk": (ctypes.c_int, [vp, vp, i32, i32, i32, P(fw_params), u64, vp, vp]),
                 "fw_walk_host": (ctypes.c_int, [vp, vp, i32, i32, i32, P(fw_params), u64, vp, vp]),
@@ -375,6 +377,13 @@ class Graph:
     def set_cost_ratio(self, r: float):
         fw_graph_set_cost_ratio(self.handle, r)
         self.info = fw_graph_info(self.handle)
+
+    def quantize_weights(self, stream=None) -> float:
+        """Switch the graph to 8-bit weight codes (code * scale); returns the scale."""
+        s = ctypes.c_float()
+        _check(lib().fw_graph_quantize_weights(self.handle, ctypes.byref(s), _stream_ptr(stream)))
+        self.info = fw_graph_info(self.handle)
+        return float(s.value)
 
     def degree(self, v: int) -> int:
         return int(self._off[v + 1] - self._off[v])
