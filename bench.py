@@ -61,6 +61,8 @@ def parse():
                     "batched vs one launch per job; serve: Poisson query stream on s22, continuous batching vs "
                     "serial calls; metapath: metapath walks on R-MAT s23; skew: Pareto / degree-based weights on "
                     "s22, cost model vs eRJS-only / eRVS-only / random / degree-rule selection")
+    ap.add_argument("--cost-ratio", type=float, default=None, help="walk suite: use this r of Eq. (runtime) for "
+                    "every (p,q) instead of tuning it (profiling captures)")
     ap.add_argument("--int8", action="store_true", help="walk suite: store the weights as 8-bit codes "
                     "(fw_graph_quantize_weights) before tuning and timing")
     ap.add_argument("--duration", type=float, default=10.0, help="serve suite: seconds of offered load")
@@ -582,12 +584,16 @@ def main():
 
     # tuning before sampling, reported and not timed: r of Eq. (runtime) per (p, q) from the
     # autotuner's sample-walk sweep; the Sec. 5.1 profiling kernels' r is reported beside it
-    t_prof = time.perf_counter()
-    ratio_profiled = {(p, q): G.autotune("node2vec", p=p, q=q, method=0) for (p, q) in PQ}
-    profile_ms = (time.perf_counter() - t_prof) * 1e3
-    t_prof = time.perf_counter()
-    ratio = {(p, q): G.autotune("node2vec", p=p, q=q, method=1) for (p, q) in PQ}
-    sweep_ms = (time.perf_counter() - t_prof) * 1e3
+    if args.cost_ratio is None:
+        t_prof = time.perf_counter()
+        ratio_profiled = {(p, q): G.autotune("node2vec", p=p, q=q, method=0) for (p, q) in PQ}
+        profile_ms = (time.perf_counter() - t_prof) * 1e3
+        t_prof = time.perf_counter()
+        ratio = {(p, q): G.autotune("node2vec", p=p, q=q, method=1) for (p, q) in PQ}
+        sweep_ms = (time.perf_counter() - t_prof) * 1e3
+    else:
+        ratio = {pq: args.cost_ratio for pq in PQ}
+        ratio_profiled, profile_ms, sweep_ms = {pq: None for pq in PQ}, 0.0, 0.0
 
     def walk(p, q, flags=0):
         r = ratio[(p, q)]

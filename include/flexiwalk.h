@@ -84,9 +84,12 @@ enum {
   FW_FLAG_PLAIN_RJS = 8,  /* eRJS exactly as Sec. 3.3 (uniform proposal, bound
                              max(w) * h_MAX) even when node2vec's return edge
                              could be proposed separately                        */
-  FW_FLAG_PAPER_SUM = 16  /* metapath: plan with the Sec. 4.2 rule (B = h_MAX,
+  FW_FLAG_PAPER_SUM = 16, /* metapath: plan with the Sec. 4.2 rule (B = h_MAX,
                              sum-hat = h_SUM / 2) even when per-label node
                              statistics exist                                    */
+  FW_FLAG_NO_BLOOM = 32   /* membership tests in N(v') search the sorted row
+                             only, without the per-row Bloom pre-check (the
+                             answers, and so the walks, are the same)            */
 };
 
 /* Parameters of one walk job.  Initialise with fw_params_default(). */

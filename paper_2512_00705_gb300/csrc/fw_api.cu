@@ -37,6 +37,7 @@ DevGraph dev_graph(const fw_graph* g) {
   d.nrec = g->d_nrec;
   d.erec = g->d_erec;
   d.lstat = g->d_lstat;
+  d.bloom = g->d_bloom;
   d.n = g->n;
   d.sym = g->sym;
   return d;
@@ -91,6 +92,7 @@ fw_status make_job(const fw_graph* g, int32_t algo, const fw_params* params, uin
   job->walker_base = P.walker_base;
   job->pr_g = P.gamma;
   job->pr_1g = 1.0f - P.gamma;
+  job->bloom = (g->d_bloom && !(P.flags & FW_FLAG_NO_BLOOM)) ? 1 : 0;
   job->label_stats = (algo == ALGO_METAPATH && g->d_lstat && !(P.flags & FW_FLAG_PAPER_SUM) &&
                       (job->weighted || !g->d_h)) ? 1 : 0;
   return FW_OK;
@@ -105,6 +107,28 @@ fw_status rebuild_derived(fw_graph* g, cudaStream_t st) {
   int* d_maxdeg = reinterpret_cast<int*>(g->d_err) + 8;
   unsigned* d_asym = g->d_err + 12;
   unsigned* d_lbad = g->d_err + 13;
+  const bool want_labels = g->d_lab != nullptr && !g->lstat_bad;
+  const bool build_bloom = g->d_bloom == nullptr;  // depends on the structure only: built once
+  if (build_bloom) {
+    cudaError_t ae = cudaMalloc(&g->d_bloom, bloom_bytes(n, e));
+    if (ae != cudaSuccess) {
+      g->d_bloom = nullptr;
+      return cuda_error(ae, "cudaMalloc(row filters)");
+    }
+    g->bytes += bloom_bytes(n, e);
+  }
+  if (want_labels && !g->d_lstat) {
+    cudaError_t ae = cudaMalloc(&g->d_lstat, sizeof(float2) * kLabelStats * ((size_t)n + 1));
+    if (ae != cudaSuccess) {
+      g->d_lstat = nullptr;
+      return cuda_error(ae, "cudaMalloc(label statistics)");
+    }
+    g->bytes += sizeof(float2) * kLabelStats * ((size_t)n + 1);
+  }
+  {
+    cudaError_t pe = prime_preprocess_kernels();
+    if (pe != cudaSuccess) return cuda_error(pe, "load preprocessing kernels");
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -115,11 +139,7 @@ fw_status rebuild_derived(fw_graph* g, cudaStream_t st) {
     le = launch_node_stats(g->d_off, g->d_h, n, g->d_hmax, g->d_hsum, g->d_nrec, d_maxdeg, g->num_sms, st);
   if (le == cudaSuccess) le = launch_edge_records(g->d_col, g->d_h, g->d_lab, g->d_nrec, e, g->d_erec, g->num_sms, st);
   if (le == cudaSuccess) le = launch_symmetry(g->d_off, g->d_col, g->d_h, n, d_asym, g->num_sms, st);
-  const bool want_labels = g->d_lab != nullptr && !g->lstat_bad;
-  if (le == cudaSuccess && want_labels && !g->d_lstat) {
-    le = cudaMalloc(&g->d_lstat, sizeof(float2) * kLabelStats * ((size_t)n + 1));
-    if (le == cudaSuccess) g->bytes += sizeof(float2) * kLabelStats * ((size_t)n + 1);
-  }
+  if (le == cudaSuccess && build_bloom) le = launch_bloom(g->d_off, g->d_col, n, e, g->d_bloom, g->num_sms, st);
   if (le == cudaSuccess && want_labels)
     le = launch_label_stats(g->d_off, g->d_h, g->d_lab, n, g->d_lstat, d_lbad, g->num_sms, st);
   cudaEventRecord(e1, st);
@@ -226,6 +246,7 @@ static void free_graph(fw_graph* g) {
   cudaFree(g->d_erec);
   cudaFree(g->d_lstat);
   cudaFree(g->d_h8);
+  cudaFree(g->d_bloom);
   cudaFree(g->d_err);
   cudaFree(g->d_cnt);
   cudaFree(g->d_stage_starts);

@@ -51,6 +51,7 @@ struct DevGraph {
                                    // {target h_MAX bits, target h_SUM bits, label, 0}: one sector per eRJS trial
   const float2* __restrict__ lstat; // per node and label l < kLabelStats: {max h, sum h} over the
                                    // edges with that label (nullptr: labels absent or >= kLabelStats)
+  const uint32_t* __restrict__ bloom; // blocked Bloom filters of the rows (nullptr: none)
   int32_t n;
   int32_t sym;                     // 1: h(v,u) = h(u,v) for every edge (checked at creation)
 };
@@ -72,6 +73,7 @@ struct Job {
   int32_t fixed_cap;       // 1: rjs_cap is a fixed trial cap; 0: cap = max(rjs_cap, ceil(d / ratio))
   int32_t split_return;    // node2vec with 1/p > max(1, 1/q): eRJS proposes the return edge separately
   int32_t label_stats;     // metapath: plan with the per-label h_MAX / h_SUM of the required label
+  int32_t bloom;           // 1: membership tests in N(v') consult the row's Bloom filter first
   float inv_p, inv_q;      // FP32 1/p, 1/q
   float wmax1, wmean1;     // max / mean of w when a previous node exists
   float wlo1, whi1;        // min / max of {1, 1/q}: squeeze bounds of a non-return neighbour
@@ -205,9 +207,52 @@ __device__ __forceinline__ int32_t row_find(const int32_t* __restrict__ col, int
   return -1;
 }
 
-__device__ __forceinline__ bool row_contains(const int32_t* __restrict__ col, int32_t lo, int32_t hi, int32_t u,
-                                             int32_t n, uint32_t& probes) {
-  return row_find(col, lo, hi, u, n, probes) >= 0;
+// ---------------------------------------------------------------- membership
+// Blocked Bloom filters over the rows: a pre-check in front of row_find that
+// never changes an answer, it only skips searches whose answer is "absent"
+// (most node2vec candidates with q > 1 lie at distance 2 from v').  Node x
+// owns the 256-bit blocks [bb(x), bb(x+1)) with bb(x) = floor(off[x]/32) + x,
+// one block per 32 row entries plus one; entry u of the row sets kBloomBits
+// bits of one of them, so a filter holds at least 8 bits per entry (false
+// positive rate about 3 %).  Block and bits come from a 64-bit mix of u (the
+// 64-bit finalizer of MurmurHash3, A. Appleby).  Rows shorter than
+// kBloomMinDeg span one or two sectors and are searched directly.
+constexpr int32_t kBloomMinDeg = 16;
+constexpr int kBloomBits = 4;
+
+__device__ __forceinline__ unsigned long long bloom_mix(uint32_t u) {
+  unsigned long long k = (unsigned long long)u + 0x9E3779B97F4A7C15ull;
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+
+// First word of the block of row x = [rs, re) that entry hash hk maps to.
+__device__ __forceinline__ long long bloom_word(int32_t x, int32_t rs, int32_t re, unsigned long long hk) {
+  const long long b0 = (long long)(rs >> 5) + x;
+  const uint32_t nb = (uint32_t)((re >> 5) - (rs >> 5) + 1);
+  return 8ll * (b0 + (long long)__umulhi((uint32_t)(hk >> 32), nb));
+}
+
+// Is u in N(v') (the row [c.ps, c.pe) of c.vp)?  Exact; a filter test counts as one probe.
+__device__ __forceinline__ bool prev_contains(const DevGraph& g, const Job& J, const StepCtx& c, int32_t u,
+                                              uint32_t& probes) {
+  if (J.bloom && c.pe - c.ps >= kBloomMinDeg) {
+    const unsigned long long hk = bloom_mix((uint32_t)u);
+    const uint32_t* blk = g.bloom + bloom_word(c.vp, c.ps, c.pe, hk);
+    ++probes;
+    uint32_t hit = 1u;
+#pragma unroll
+    for (int j = 0; j < kBloomBits; ++j) {
+      const uint32_t bit = (uint32_t)(hk >> (8 * j)) & 255u;
+      hit &= __ldg(blk + (bit >> 5)) >> (bit & 31u);
+    }
+    if (!(hit & 1u)) return false;
+  }
+  return row_find(g.col, c.ps, c.pe, u, g.n, probes) >= 0;
 }
 
 // Property weight of CSR entry i: FP32, or an 8-bit code times the graph's scale.
@@ -226,7 +271,7 @@ __device__ __forceinline__ float item_weight(const DevGraph& g, const Job& J, co
     float w;
     if (u == c.vp) w = J.inv_p;                       // dist(v',u) = 0
     else if (!J.need_member) w = 1.0f;                // 1/q == 1: distances 1 and 2 weigh the same
-    else w = row_contains(g.col, c.ps, c.pe, u, g.n, probes) ? 1.0f : J.inv_q;
+    else w = prev_contains(g, J, c, u, probes) ? 1.0f : J.inv_q;
     return __fmul_rn(w, hk);
   }
   if (J.algo == ALGO_METAPATH) {
@@ -235,7 +280,7 @@ __device__ __forceinline__ float item_weight(const DevGraph& g, const Job& J, co
   }
   if (J.algo == ALGO_PAGERANK2 && c.vp >= 0) {
     const int32_t u = __ldg(g.col + i);
-    return __fmul_rn(row_contains(g.col, c.ps, c.pe, u, g.n, probes) ? c.w1 : c.w2, hk);
+    return __fmul_rn(prev_contains(g, J, c, u, probes) ? c.w1 : c.w2, hk);
   }
   return hk;
 }
@@ -326,7 +371,7 @@ __device__ __forceinline__ bool rjs_trials(const DevGraph& g, const Job& J, cons
         accept = true;                          // squeeze: below the smallest possible weight
       } else {
         uint32_t pb = 0;
-        const bool adj = row_contains(g.col, c.ps, c.pe, u, g.n, pb);
+        const bool adj = prev_contains(g, J, c, u, pb);
         probes += pb;
         accept = UB < __fmul_rn(adj ? 1.0f : J.inv_q, hk);
       }
@@ -339,7 +384,7 @@ __device__ __forceinline__ bool rjs_trials(const DevGraph& g, const Job& J, cons
         accept = true;                          // squeeze: below the smaller weight
       } else {
         uint32_t pb = 0;
-        const bool adj = row_contains(g.col, c.ps, c.pe, u, g.n, pb);
+        const bool adj = prev_contains(g, J, c, u, pb);
         probes += pb;
         accept = UB < __fmul_rn(adj ? c.w1 : c.w2, hk);
       }

@@ -27,6 +27,7 @@ struct fw_graph {
   int4* d_erec = nullptr;
   float2* d_lstat = nullptr;  // per-label node statistics (nullptr: not available)
   bool lstat_bad = false;     // a label >= kLabelStats occurs
+  uint32_t* d_bloom = nullptr; // blocked Bloom filters of the rows (membership pre-check)
   uint8_t* d_h8 = nullptr;    // 8-bit weight codes after fw_graph_quantize_weights
   float hscale = 0.0f;
   int32_t sym = 0;
@@ -77,6 +78,10 @@ cudaError_t launch_symmetry(const int32_t* off, const int32_t* col, const float*
 cudaError_t launch_quantize(float* h, long long e, uint8_t* codes, float* scale_out, unsigned* maxbits, int num_sms,
                             cudaStream_t stream);
 cudaError_t launch_dequantize(const uint8_t* codes, long long e, float scale, float* h, int num_sms, cudaStream_t stream);
+size_t bloom_bytes(int32_t n, long long e);
+cudaError_t prime_preprocess_kernels();
+cudaError_t launch_bloom(const int32_t* off, const int32_t* col, int32_t n, long long e, uint32_t* bloom, int num_sms,
+                         cudaStream_t stream);
 fw_status rebuild_derived(fw_graph* g, cudaStream_t stream);
 cudaError_t launch_check_offsets(const int32_t* off, int32_t n, int64_t e, unsigned* err, int num_sms,
                                  cudaStream_t stream);

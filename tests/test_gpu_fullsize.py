@@ -69,6 +69,16 @@ def test_fast_mode_full_s22_invariants(s22, p, q):
     assert np.all(keys[np.minimum(pos, len(keys) - 1)] == q_)
 
 
+@pytest.mark.parametrize("p,q", PQ)
+def test_bench_walk_identical_without_row_filters(s22, p, q):
+    """The bench's launch with and without the Bloom pre-check: equal rows."""
+    g, G = s22
+    starts = torch.arange(g.n, dtype=torch.int32, device="cuda")
+    a = G.walk(starts, 80, "node2vec", p=p, q=q, mode="auto", seed=42)
+    b = G.walk(starts, 80, "node2vec", p=p, q=q, mode="auto", seed=42, flags=fw.FLAG_NO_BLOOM)
+    assert torch.equal(a, b)
+
+
 @pytest.mark.parametrize("mode,flags,ndraws", [("rjs", 0, 4_000_000), ("auto", 0, 4_000_000),
                                                ("rvs", 0, 4_000_000), ("rvs", fw.FLAG_RVS_NOJUMP, 1_000_000)])
 def test_hub_distributions_s22(s22, mode, flags, ndraws):
