@@ -56,11 +56,13 @@ def parse():
                     "scales are for profiling captures)")
     ap.add_argument("--pq", action="append", default=None, help="restrict to one (p,q), e.g. --pq 4,0.25")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--suite", default="walk", choices=["walk", "batch", "serve", "metapath", "skew"],
+    ap.add_argument("--suite", default="walk", choices=["walk", "batch", "serve", "metapath", "skew", "ablation"],
                     help="walk: the headline node2vec s22 line; batch: 64 mixed jobs on skewed R-MAT s24, "
                     "batched vs one launch per job; serve: Poisson query stream on s22, continuous batching vs "
                     "serial calls; metapath: metapath walks on R-MAT s23; skew: Pareto / degree-based weights on "
-                    "s22, cost model vs eRJS-only / eRVS-only / random / degree-rule selection")
+                    "s22, cost model vs eRJS-only / eRVS-only / random / degree-rule selection; ablation: the "
+                    "headline s22 walk for node2vec (weighted and unweighted), weighted and second-order PageRank, "
+                    "cost model vs eRJS-only / eRVS-only")
     ap.add_argument("--cost-ratio", type=float, default=None, help="walk suite: use this r of Eq. (runtime) for "
                     "every (p,q) instead of tuning it (profiling captures)")
     ap.add_argument("--int8", action="store_true", help="walk suite: store the weights as 8-bit codes "
@@ -505,16 +507,19 @@ def run_skew(args):
             row["int8_scale"] = G.quantize_weights()
             r8 = G.autotune("node2vec", p=2.0, q=0.5, method=1)
             row["cost_ratio_sweep_int8"] = r8
-            G.walk(starts, L, "node2vec", p=2.0, q=0.5, mode="auto", cost_ratio=r8, seed=SEED, out=out)
-            ms = []
-            for _ in range(max(1, args.steps)):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                G.walk(starts, L, "node2vec", p=2.0, q=0.5, mode="auto", cost_ratio=r8, seed=SEED, out=out)
-                e1.record()
-                torch.cuda.synchronize()
-                ms.append(e0.elapsed_time(e1))
-            row["auto_int8_ms"] = statistics.median(ms)
+            for md in ("auto", "rvs"):  # eRVS-only: scans read 1-byte weights
+                G.walk(starts, L, "node2vec", p=2.0, q=0.5, mode=md, cost_ratio=r8, seed=SEED, out=out)
+                ms = []
+                for _ in range(max(1, args.steps)):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    G.walk(starts, L, "node2vec", p=2.0, q=0.5, mode=md, cost_ratio=r8, seed=SEED, out=out)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                row[f"{md}_int8_ms"] = statistics.median(ms)
+            # weights below half a step are stored as code 1: how much of the tail the codes keep
+            row["int8_clamped_share"] = float(np.mean(h.astype(np.float64) < 0.5 * row["int8_scale"]))
         row["auto_speedup_vs_best_single"] = min(row["rjs_ms"], row["rvs_ms"]) / row["auto_ms"]
         row["auto_sweep_speedup_vs_best_single"] = min(row["rjs_ms"], row["rvs_ms"]) / row["auto_sweep_ms"]
         row["auto_speedup_vs_random"] = row["random_ms"] / row["auto_ms"]
@@ -530,6 +535,70 @@ def run_skew(args):
         "skew": res})
 
 
+def run_ablation(args):
+    """Sampler ablation at the headline size (Sec. 5.3): R-MAT s22 with
+    h ~ U(0,1], one walker per node, 80 hops.  node2vec at the three (p, q)
+    with the weights and with h = 1 (unweighted, Sec. 5.1), the weighted
+    first-order walk, and second-order PageRank (Eq. 2ndpr, gamma = 0.2).
+    Each case: the cost model with the sweep-tuned r against eRJS-only and
+    eRVS-only (eRVS-only once timed: a single launch takes seconds)."""
+    import torch
+    from paper_2512_00705_gb300 import _build, synth
+    from paper_2512_00705_gb300 import flexiwalk as fw
+    _build.build()
+    torch.cuda.set_device(0)
+    g = synth.workload_graph("s22")
+    G = fw.Graph(g)
+    starts = torch.arange(g.n, dtype=torch.int32, device="cuda")
+    out = torch.empty((g.n, LENGTH + 1), dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    U = fw.FLAG_UNWEIGHTED
+    cases = [("node2vec", p, q, 0) for (p, q) in PQ] + [("node2vec", p, q, U) for (p, q) in PQ] + \
+            [("weighted", 1.0, 1.0, 0), ("pagerank2", 1.0, 1.0, 0)]
+    res = {}
+    for algo, p, q, flags in cases:
+        name = f"{algo}" + (f"_p{p:g}_q{q:g}" if algo == "node2vec" else "") + ("_unweighted" if flags else "")
+        r = G.autotune(algo, p=p, q=q, flags=flags, method=1)
+        row = {"cost_ratio": r}
+
+        def go(mode):
+            G.walk(starts, LENGTH, algo, p=p, q=q, mode=mode, cost_ratio=r, seed=SEED, flags=flags, out=out)
+
+        for mode in ("auto", "rjs", "rvs"):
+            go(mode)
+            reps = 1 if mode == "rvs" else max(1, args.steps)
+            ms = []
+            for _ in range(reps):
+                flush.fill_(1)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                go(mode)
+                e1.record()
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            row[f"{mode}_ms"] = statistics.median(ms)
+            if mode == "auto":
+                G.reset_counters()
+                G.walk(starts, LENGTH, algo, p=p, q=q, mode="auto", cost_ratio=r, seed=SEED,
+                       flags=flags | fw.FLAG_COUNTERS, out=out)
+                c = G.counters()
+                row["hops"] = c["hops"]
+                row["rjs_share"] = c["rjs_steps"] / max(1, c["hops"])
+        row["walker_steps_per_s"] = row["hops"] / (row["auto_ms"] / 1e3)
+        row["auto_vs_best_single"] = min(row["rjs_ms"], row["rvs_ms"]) / row["auto_ms"]
+        res[name] = row
+    G.close()
+    hops = sum(r_["hops"] for r_ in res.values())
+    tot = sum(r_["auto_ms"] for r_ in res.values())
+    _line("walker-steps/sec (sampler ablation, s22)", hops / (tot / 1e3), "walker-steps/s", args, {
+        "ms_per_step": tot,
+        "config": {"workload": "R-MAT s22 ef16, h~U(0,1] or h=1, one walker per node, 80 hops: node2vec x3 (p,q) "
+                               "weighted and unweighted, weighted walk, second-order PageRank gamma=0.2; cost model "
+                               "(sweep r) vs eRJS-only vs eRVS-only",
+                   "l2": "256 MiB write before every timed launch; graph and rows > L2"},
+        "ablation": res})
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -542,6 +611,8 @@ def main():
         return run_serve(args)
     if args.suite == "skew":
         return run_skew(args)
+    if args.suite == "ablation":
+        return run_ablation(args)
     import torch
     import torch.distributed as dist
 

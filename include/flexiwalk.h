@@ -120,7 +120,7 @@ typedef struct {
   size_t device_bytes;       /* device memory held by the graph                  */
   int32_t symmetric;         /* 1: every edge (v,u) has a mirror (u,v) with the
                                 same weight (found at creation)                   */
-  float cost_ratios[3];      /* r per algorithm (weighted, node2vec, metapath)   */
+  float cost_ratios[4];      /* r per algorithm, indexed by fw_algo             */
   uint64_t fingerprint;      /* hash of sizes and sampled CSR entries (cache key)*/
   float weight_scale;        /* s after fw_graph_quantize_weights, else 0        */
 } fw_graph_info_t;
@@ -207,15 +207,17 @@ fw_status fw_graph_set_cost_ratio(fw_graph* graph, float ratio);
  * Measure and install the cost ratio r = EdgeCost_RJS / EdgeCost_RVS of
  * Eq. (runtime) for `algo` with `params` (Sec. 5.1, profiling kernels).
  *   method 0  the paper's profiling: two light kernels compute transition
- *             weights for 65,536 evenly spaced nodes and 32 neighbours each,
- *             eRJS-style (random positions) and eRVS-style (a coalesced
- *             scan); r = ratio of their times per edge
+ *             weights for 65,536 evenly spaced nodes, eRJS-style (32 random
+ *             positions per node, one thread each) and eRVS-style (a
+ *             coalesced warp scan of up to 256 neighbours with keys and
+ *             jumps); r = ratio of their times per edge
  *   method 1  sweep: time 16-hop sample walks of up to 2^18 walkers for
  *             r in {0.5, 1, 2, ..., 64} and keep the fastest
  * cache_path (may be NULL): a text file of earlier results keyed by the
- * graph fingerprint, algo, p, q and method; a hit skips the measurement,
- * a miss appends the new result.  Synchronous on `stream`.  The ratio only
- * changes which sampler runs, never the distribution.
+ * graph fingerprint, algo, p, q, gamma, flags, schema and method; a hit
+ * skips the measurement, a miss appends the new result.  Synchronous on
+ * `stream`.  The ratio only changes which sampler runs, never the
+ * distribution.
  */
 fw_status fw_autotune(fw_graph* graph, int32_t algo, const fw_params* params, int32_t method,
                       const char* cache_path, float* ratio_out, void* stream);

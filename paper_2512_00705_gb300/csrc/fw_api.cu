@@ -354,7 +354,7 @@ extern "C" fw_status fw_graph_info(const fw_graph* g, fw_graph_info_t* info) {
   info->has_weights = g->d_h != nullptr;
   info->has_labels = g->d_lab != nullptr;
   info->cost_ratio = g->ratio_algo[FW_ALGO_NODE2VEC];
-  for (int a = 0; a < 3; ++a) info->cost_ratios[a] = g->ratio_algo[a];
+  for (int a = 0; a < 4; ++a) info->cost_ratios[a] = g->ratio_algo[a];
   info->fingerprint = g->fingerprint;
   info->preprocess_ms = g->preprocess_ms;
   info->device_bytes = g->bytes;
@@ -414,7 +414,7 @@ extern "C" fw_status fw_graph_quantize_weights(fw_graph* g, float* scale_out, vo
 
 extern "C" fw_status fw_graph_set_cost_ratio(fw_graph* g, float ratio) {
   if (!g || !(ratio > 0.0f) || !std::isfinite(ratio)) return set_error(FW_ERR_ARG, "bad ratio");
-  for (int a = 0; a < 3; ++a) g->ratio_algo[a] = ratio;
+  for (int a = 0; a < 4; ++a) g->ratio_algo[a] = ratio;
   return FW_OK;
 }
 

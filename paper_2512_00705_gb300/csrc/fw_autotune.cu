@@ -102,10 +102,14 @@ uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
   return h;
 }
 
+// A tuned r is stored per graph fingerprint and per everything that changes
+// the walk's cost: algorithm, p, q, gamma, the sampler flags and the schema.
 struct CacheKey {
   unsigned long long fp;
   int algo;
-  float p, q;
+  float p, q, gamma;
+  int flags;
+  unsigned schema;  // FNV-1a of the schema entries in use
   int method;
 };
 
@@ -116,10 +120,13 @@ bool cache_lookup(const char* path, const CacheKey& k, float* r) {
   bool hit = false;
   while (std::fgets(line, sizeof(line), f)) {
     unsigned long long fp;
-    int algo, method;
-    float p, q, rv;
-    if (std::sscanf(line, "fp=%llx algo=%d p=%g q=%g method=%d r=%g", &fp, &algo, &p, &q, &method, &rv) == 6 &&
-        fp == k.fp && algo == k.algo && p == k.p && q == k.q && method == k.method && rv > 0.0f) {
+    int algo, method, flags;
+    unsigned schema;
+    float p, q, gamma, rv;
+    if (std::sscanf(line, "fp=%llx algo=%d p=%g q=%g gamma=%g flags=%d schema=%x method=%d r=%g", &fp, &algo, &p,
+                    &q, &gamma, &flags, &schema, &method, &rv) == 9 &&
+        fp == k.fp && algo == k.algo && p == k.p && q == k.q && gamma == k.gamma && flags == k.flags &&
+        schema == k.schema && method == k.method && rv > 0.0f) {
       *r = rv;
       hit = true;  // the last matching line wins
     }
@@ -131,7 +138,8 @@ bool cache_lookup(const char* path, const CacheKey& k, float* r) {
 void cache_store(const char* path, const CacheKey& k, float r) {
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "fp=%016llx algo=%d p=%.9g q=%.9g method=%d r=%.9g\n", k.fp, k.algo, k.p, k.q, k.method, r);
+  std::fprintf(f, "fp=%016llx algo=%d p=%.9g q=%.9g gamma=%.9g flags=%d schema=%08x method=%d r=%.9g\n", k.fp,
+               k.algo, k.p, k.q, k.gamma, k.flags, k.schema, k.method, r);
   std::fclose(f);
 }
 
@@ -294,6 +302,10 @@ extern "C" fw_status fw_autotune(fw_graph* g, int32_t algo, const fw_params* par
   key.algo = algo;
   key.p = params ? params->p : 1.0f;
   key.q = params ? params->q : 1.0f;
+  key.gamma = params ? params->gamma : 0.2f;
+  key.flags = params ? (params->flags & ~FW_FLAG_COUNTERS) : 0;
+  key.schema = 2166136261u;
+  for (int i = 0; i < J.schema_len; ++i) key.schema = (key.schema ^ J.schema[i]) * 16777619u;
   key.method = method;
   key.fp = g->fingerprint;
   float r = 0.0f;

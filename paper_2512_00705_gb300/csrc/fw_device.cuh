@@ -104,6 +104,11 @@ struct LaneCounters {
   }
 };
 
+// Algorithm of job J.  Kernels specialised to one algorithm pass it as the
+// template argument ALG >= 0, so the other algorithms' code folds away;
+// ALG = -1 reads it from the job (batches of mixed jobs).
+#define FW_ALGO(J) ((ALG) >= 0 ? (ALG) : (J).algo)
+
 // ---------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
 // 32x32->64 multiplies with the published multipliers; high halves are XORed
@@ -129,13 +134,14 @@ __device__ __forceinline__ float u01(uint32_t x) { return (float)(x >> 8) * 0x1.
 __device__ __forceinline__ float u01_open(uint32_t x) { return (float)(((x >> 9) << 1) | 1u) * 0x1.0p-24f; }
 
 // ---------------------------------------------------------------- gathers
-// One 32-byte edge record in a single 256-bit read-only load.  (Measured
-// against two 128-bit loads: equal or slightly faster.  Loads that skip L1
-// -- ld.global.cg or .L1::no_allocate, which avoid filling a 128-byte line
-// for a 32-byte gather -- were measured slower: the kernel is bound by load
-// latency more than by DRAM bytes.)
+// One 32-byte edge record in a single 256-bit read-only load that does not
+// allocate in L1: records are gathered at random, so L1 lines would only
+// evict the rows that membership searches and scans reuse.  (Measured on
+// R-MAT s22 node2vec: 2-3 % faster than an allocating load, and ld.global.cg
+// 5-14 % slower; DRAM bytes per hop are the same for all three, about four
+// sectors per record.)
 __device__ __forceinline__ void ld_record(const int4* p, int4& a, int4& b) {
-  asm volatile("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+  asm volatile("ld.global.nc.L1::no_allocate.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
                : "l"(p));
 }
@@ -219,6 +225,7 @@ __device__ __forceinline__ int32_t row_find(const int32_t* __restrict__ col, int
 // kBloomMinDeg span one or two sectors and are searched directly.
 constexpr int32_t kBloomMinDeg = 16;
 constexpr int kBloomBits = 4;
+constexpr int32_t kPr2SplitMaxPrev = 64;  // second-order PageRank: longest N(v') enumerated for the split
 
 __device__ __forceinline__ unsigned long long bloom_mix(uint32_t u) {
   unsigned long long k = (unsigned long long)u + 0x9E3779B97F4A7C15ull;
@@ -237,12 +244,14 @@ __device__ __forceinline__ long long bloom_word(int32_t x, int32_t rs, int32_t r
   return 8ll * (b0 + (long long)__umulhi((uint32_t)(hk >> 32), nb));
 }
 
-// Is u in N(v') (the row [c.ps, c.pe) of c.vp)?  Exact; a filter test counts as one probe.
-__device__ __forceinline__ bool prev_contains(const DevGraph& g, const Job& J, const StepCtx& c, int32_t u,
-                                              uint32_t& probes) {
-  if (J.bloom && c.pe - c.ps >= kBloomMinDeg) {
+// Position of u in the row [rs, re) of node x, or -1: the filter first (rows
+// of at least kBloomMinDeg entries; a filter test counts as one probe), then
+// the search.  Exact.
+__device__ __forceinline__ int32_t row_lookup(const DevGraph& g, const Job& J, int32_t x, int32_t rs, int32_t re,
+                                              int32_t u, uint32_t& probes) {
+  if (J.bloom && re - rs >= kBloomMinDeg) {
     const unsigned long long hk = bloom_mix((uint32_t)u);
-    const uint32_t* blk = g.bloom + bloom_word(c.vp, c.ps, c.pe, hk);
+    const uint32_t* blk = g.bloom + bloom_word(x, rs, re, hk);
     ++probes;
     uint32_t hit = 1u;
 #pragma unroll
@@ -250,10 +259,17 @@ __device__ __forceinline__ bool prev_contains(const DevGraph& g, const Job& J, c
       const uint32_t bit = (uint32_t)(hk >> (8 * j)) & 255u;
       hit &= __ldg(blk + (bit >> 5)) >> (bit & 31u);
     }
-    if (!(hit & 1u)) return false;
+    if (!(hit & 1u)) return -1;
   }
-  return row_find(g.col, c.ps, c.pe, u, g.n, probes) >= 0;
+  return row_find(g.col, rs, re, u, g.n, probes);
 }
+
+// Is u in N(v') (the row [c.ps, c.pe) of c.vp)?
+__device__ __forceinline__ bool prev_contains(const DevGraph& g, const Job& J, const StepCtx& c, int32_t u,
+                                              uint32_t& probes) {
+  return row_lookup(g, J, c.vp, c.ps, c.pe, u, probes) >= 0;
+}
+
 
 // Property weight of CSR entry i: FP32, or an 8-bit code times the graph's scale.
 __device__ __forceinline__ float load_h(const DevGraph& g, const Job& J, int32_t i) {
@@ -261,11 +277,45 @@ __device__ __forceinline__ float load_h(const DevGraph& g, const Job& J, int32_t
   return g.h8 ? __fmul_rn((float)__ldg(g.h8 + i), g.hscale) : __ldg(g.h + i);
 }
 
+// Second-order PageRank with a short row of v' (Eq. 2ndpr): the common
+// neighbours C = N(v) and N(v') carry w1 > w2, all others w2.  Enumerating
+// N(v') finds C and S_C = sum of h(v, x) over x in C (FP32, in N(v') order).
+// With t in [0, S_C), common_pick returns the x in C where that running sum
+// first exceeds t (the last one if rounding leaves none), its position in
+// N(v) relative to the row start, and h(v, x).
+static __device__ __noinline__ float common_h_sum(const DevGraph& g, const Job& J, const StepCtx& c, uint32_t& probes) {
+  float sc = 0.0f;
+  for (int32_t j = c.ps; j < c.pe; ++j) {
+    const int32_t pos = row_lookup(g, J, c.v, c.s, c.s + c.d, __ldg(g.col + j), probes);
+    if (pos >= 0) sc = __fadd_rn(sc, load_h(g, J, pos));
+  }
+  return sc;
+}
+
+static __device__ __noinline__ int32_t common_pick(const DevGraph& g, const Job& J, const StepCtx& c, float t,
+                                               int32_t& k, float& hx, uint32_t& probes) {
+  float run = 0.0f;
+  int32_t node = -1;
+  for (int32_t j = c.ps; j < c.pe; ++j) {
+    const int32_t x = __ldg(g.col + j);
+    const int32_t pos = row_lookup(g, J, c.v, c.s, c.s + c.d, x, probes);
+    if (pos < 0) continue;
+    const float h = load_h(g, J, pos);
+    run = __fadd_rn(run, h);
+    node = x;
+    k = pos - c.s;
+    hx = h;
+    if (t < run) break;
+  }
+  return node;
+}
+
 // Transition weight of the neighbour at CSR index i (= s + k) of step c.
+template <int ALG = -1>
 __device__ __forceinline__ float item_weight(const DevGraph& g, const Job& J, const StepCtx& c, int32_t i,
                                              uint32_t& probes) {
   const float hk = load_h(g, J, i);
-  if (J.algo == ALGO_NODE2VEC) {
+  if (FW_ALGO(J) == ALGO_NODE2VEC) {
     if (c.vp < 0 || !J.second_order) return hk;
     const int32_t u = __ldg(g.col + i);
     float w;
@@ -274,11 +324,11 @@ __device__ __forceinline__ float item_weight(const DevGraph& g, const Job& J, co
     else w = prev_contains(g, J, c, u, probes) ? 1.0f : J.inv_q;
     return __fmul_rn(w, hk);
   }
-  if (J.algo == ALGO_METAPATH) {
+  if (FW_ALGO(J) == ALGO_METAPATH) {
     const uint8_t want = J.schema[c.step % J.schema_len];
     return (__ldg(g.lab + i) == want) ? hk : 0.0f;    // w in {0, 1}
   }
-  if (J.algo == ALGO_PAGERANK2 && c.vp >= 0) {
+  if (FW_ALGO(J) == ALGO_PAGERANK2 && c.vp >= 0) {
     const int32_t u = __ldg(g.col + i);
     return __fmul_rn(prev_contains(g, J, c, u, probes) ? c.w1 : c.w2, hk);
   }
@@ -287,13 +337,14 @@ __device__ __forceinline__ float item_weight(const DevGraph& g, const Job& J, co
 
 // ---------------------------------------------------------------- plan
 // Bound (Sec. 3.3), sum estimate (Eq. sum_estimation) and choice (Eq. runtime).
+template <int ALG = -1>
 __device__ __forceinline__ int32_t plan_choice(const Job& J, float hm, float hs, bool has_prev, float w1, float w2,
                                                float& B, float& S) {
-  const bool second = (J.algo == ALGO_NODE2VEC) && has_prev;
-  const bool pr2 = (J.algo == ALGO_PAGERANK2) && has_prev;
+  const bool second = (FW_ALGO(J) == ALGO_NODE2VEC) && has_prev;
+  const bool pr2 = (FW_ALGO(J) == ALGO_PAGERANK2) && has_prev;
   const float wmax = second ? J.wmax1 : (pr2 ? w1 : 1.0f);
   const float wmean = second ? J.wmean1 : (pr2 ? __fmul_rn(__fadd_rn(w1, w2), 0.5f)
-                                               : ((J.algo == ALGO_METAPATH) ? 0.5f : 1.0f));
+                                               : ((FW_ALGO(J) == ALGO_METAPATH) ? 0.5f : 1.0f));
   B = __fmul_rn(wmax, hm);
   S = __fmul_rn(hs, wmean);
   return (__fmul_rn(J.ratio, B) < S) ? MODE_RJS : MODE_RVS;
@@ -322,22 +373,35 @@ struct Accept {
 // X != v' is accepted iff U*B < w~(X) with B = max(1, 1/q) * h_MAX[v].
 // Accepted v' has probability beta and accepted x has (1-beta) w~(x)/(d B):
 // both proportional to w~, so the accepted draw follows Eq. (prob).
-template <bool COUNT>
+// Split common neighbours (second-order PageRank, short N(v'), w1 > 2 w2):
+// w~(x) = w2 h(x) + (w1 - w2) h(x) [x in C].  With probability
+// beta = (w1-w2) S_C / ((w1-w2) S_C + d*B), B = w2 * h_MAX[v], the trial
+// picks x in C with probability h(x) / S_C (h_ret holds S_C) and accepts it;
+// otherwise X is uniform over N(v) and accepted iff U*B < w2 h(X).  The two
+// parts are proportional to the two terms of w~, so again the accepted
+// draw follows Eq. (prob).
+template <bool COUNT, int ALG = -1>
 __device__ __forceinline__ bool rjs_trials(const DevGraph& g, const Job& J, const StepCtx& c, float B, bool split,
                                            float beta, int32_t pos_ret, float h_ret, int32_t t0, int32_t nt,
                                            Accept& acc, LaneCounters& lc) {
   const uint32_t d = (uint32_t)c.d;
-  const uint8_t want = (J.algo == ALGO_METAPATH) ? J.schema[c.step % J.schema_len] : 0;
-  const bool second = (J.algo == ALGO_NODE2VEC) && c.vp >= 0 && J.second_order;
+  const uint8_t want = (FW_ALGO(J) == ALGO_METAPATH) ? J.schema[c.step % J.schema_len] : 0;
+  const bool second = (FW_ALGO(J) == ALGO_NODE2VEC) && c.vp >= 0 && J.second_order;
   uint32_t probes = 0;
   bool found = false;
   for (int32_t t = t0; t < t0 + nt; ++t) {
     const uint4 x = philox(make_uint4(c.wid, (uint32_t)c.step, 1u, (uint32_t)t), J.key0, J.key1);
     if (COUNT) lc.rjs_trials++;
     if (beta > 0.0f && u01(x.w) < beta) {
-      acc.k = pos_ret >= 0 ? pos_ret : 0;
-      acc.node = c.vp;
-      acc.h = h_ret;
+      if (FW_ALGO(J) == ALGO_PAGERANK2) {
+        uint32_t pb = 0;
+        acc.node = common_pick(g, J, c, __fmul_rn(u01(x.z), h_ret), acc.k, acc.h, pb);
+        probes += pb;
+      } else {
+        acc.k = pos_ret >= 0 ? pos_ret : 0;
+        acc.node = c.vp;
+        acc.h = h_ret;
+      }
       acc.rec_ok = false;
       found = true;
       break;
@@ -375,9 +439,11 @@ __device__ __forceinline__ bool rjs_trials(const DevGraph& g, const Job& J, cons
         probes += pb;
         accept = UB < __fmul_rn(adj ? 1.0f : J.inv_q, hk);
       }
-    } else if (J.algo == ALGO_METAPATH) {
+    } else if (FW_ALGO(J) == ALGO_METAPATH) {
       accept = ((uint8_t)b.z == want) && (UB < hk);
-    } else if (J.algo == ALGO_PAGERANK2 && c.vp >= 0) {
+    } else if (FW_ALGO(J) == ALGO_PAGERANK2 && c.vp >= 0 && split) {
+      accept = UB < __fmul_rn(c.w2, hk);        // the w2 part; C is proposed by the split
+    } else if (FW_ALGO(J) == ALGO_PAGERANK2 && c.vp >= 0) {
       if (UB >= __fmul_rn(c.w1, hk)) {
         accept = false;                         // squeeze: above the larger weight
       } else if (UB < __fmul_rn(c.w2, hk)) {
@@ -437,7 +503,7 @@ __device__ __forceinline__ void warp_argmax(float& key, int32_t& idx) {
 // draws: (wid, hop, 2, k): x.x = phase-1 key, x.y = key at a crossing,
 // x.z = the lane's next jump threshold.  Returns position k or -1 (all
 // weights zero: dead end).
-template <int T, bool COUNT>
+template <int T, bool COUNT, int ALG = -1>
 __device__ __forceinline__ int32_t rvs_pick(const DevGraph& g, const Job& J, const StepCtx& c, int lane, bool jump,
                                             LaneCounters& lc) {
   uint32_t probes = 0;
@@ -446,7 +512,7 @@ __device__ __forceinline__ int32_t rvs_pick(const DevGraph& g, const Job& J, con
   uint32_t xz = 0;
   int32_t scanned = 0, keys = 0;
   if (lane < c.d) {
-    const float wt = item_weight(g, J, c, c.s + lane, probes);
+    const float wt = item_weight<ALG>(g, J, c, c.s + lane, probes);
     const uint4 x = philox(make_uint4(c.wid, (uint32_t)c.step, 2u, (uint32_t)lane), J.key0, J.key1);
     xz = x.z;
     ++scanned;
@@ -462,7 +528,7 @@ __device__ __forceinline__ int32_t rvs_pick(const DevGraph& g, const Job& J, con
     // remaining weight before the next crossing; K_ref = -inf: first positive item crosses
     float rem = (ref == -CUDART_INF_F) ? 0.0f : ((ref < 0.0f) ? logf(u01_open(xz)) / ref : CUDART_INF_F);
     for (int32_t k = lane + T; k < c.d; k += T) {
-      const float wt = item_weight(g, J, c, c.s + k, probes);
+      const float wt = item_weight<ALG>(g, J, c, c.s + k, probes);
       ++scanned;
       if (!(wt > 0.0f)) continue;
       if (!jump) {
@@ -495,7 +561,7 @@ __device__ __forceinline__ int32_t rvs_pick(const DevGraph& g, const Job& J, con
     lc.rvs_items += scanned;
     lc.rvs_keys += keys;
     lc.probes += probes;
-    const int per = (J.algo == ALGO_NODE2VEC) ? (J.weighted ? 8 : 4) : (J.algo == ALGO_METAPATH ? (J.weighted ? 5 : 1) : (J.weighted ? 4 : 0));
+    const int per = (FW_ALGO(J) == ALGO_NODE2VEC) ? (J.weighted ? 8 : 4) : (FW_ALGO(J) == ALGO_METAPATH ? (J.weighted ? 5 : 1) : (J.weighted ? 4 : 0));
     lc.bytes += (unsigned long long)scanned * per + 32ull * probes;
   }
   return (bestK == -CUDART_INF_F) ? -1 : best;
@@ -505,14 +571,14 @@ __device__ __forceinline__ int32_t rvs_pick(const DevGraph& g, const Job& J, con
 // Exact inverse CDF with one uniform u: W_k accumulated with FP32 adds in
 // neighbour order (T = 32: the warp loads 32 weights at a time and replays
 // the additions in order through shuffles, so the sum is the serial one).
-template <int T, bool COUNT>
+template <int T, bool COUNT, int ALG = -1>
 __device__ __forceinline__ int32_t exact_pick(const DevGraph& g, const Job& J, const StepCtx& c, int lane, float u,
                                               LaneCounters& lc) {
   uint32_t probes = 0;
   float total = 0.0f;
   for (int32_t base = 0; base < c.d; base += T) {
     const int32_t k = base + lane;
-    const float wt = (k < c.d) ? item_weight(g, J, c, c.s + k, probes) : 0.0f;
+    const float wt = (k < c.d) ? item_weight<ALG>(g, J, c, c.s + k, probes) : 0.0f;
     const int32_t cnt = min(T, c.d - base);
     if (T == 1) {
       total = __fadd_rn(total, wt);
@@ -526,7 +592,7 @@ __device__ __forceinline__ int32_t exact_pick(const DevGraph& g, const Job& J, c
     float run = 0.0f;
     for (int32_t base = 0; base < c.d && pick < 0; base += T) {
       const int32_t k = base + lane;
-      const float wt = (k < c.d) ? item_weight(g, J, c, c.s + k, probes) : 0.0f;
+      const float wt = (k < c.d) ? item_weight<ALG>(g, J, c, c.s + k, probes) : 0.0f;
       const int32_t cnt = min(T, c.d - base);
       if (T == 1) {
         run = __fadd_rn(run, wt);
@@ -544,7 +610,7 @@ __device__ __forceinline__ int32_t exact_pick(const DevGraph& g, const Job& J, c
     if (pick < 0) {  // rounding left t >= W_{d-1}: last positive weight
       for (int32_t base = ((c.d - 1) / T) * T; base >= 0 && pick < 0; base -= T) {
         const int32_t k = base + lane;
-        const float wt = (k < c.d) ? item_weight(g, J, c, c.s + k, probes) : 0.0f;
+        const float wt = (k < c.d) ? item_weight<ALG>(g, J, c, c.s + k, probes) : 0.0f;
         if (T == 1) {
           if (wt > 0.0f) pick = k;
         } else {
@@ -556,7 +622,7 @@ __device__ __forceinline__ int32_t exact_pick(const DevGraph& g, const Job& J, c
   }
   if (COUNT) {
     lc.probes += probes;
-    const int per = (J.algo == ALGO_NODE2VEC) ? (J.weighted ? 8 : 4) : (J.algo == ALGO_METAPATH ? (J.weighted ? 5 : 1) : (J.weighted ? 4 : 0));
+    const int per = (FW_ALGO(J) == ALGO_NODE2VEC) ? (J.weighted ? 8 : 4) : (FW_ALGO(J) == ALGO_METAPATH ? (J.weighted ? 5 : 1) : (J.weighted ? 4 : 0));
     const int32_t mine = (lane < c.d) ? (c.d - lane + T - 1) / T : 0;
     lc.bytes += 2ull * mine * per + 32ull * probes;
   }

@@ -33,7 +33,7 @@ struct fw_graph {
   int32_t sym = 0;
   unsigned* d_err = nullptr;
   fw::DevCounters* d_cnt = nullptr;
-  float ratio_algo[3] = {4.0f, 4.0f, 4.0f};  // r of Eq. (runtime) per algorithm
+  float ratio_algo[4] = {4.0f, 4.0f, 4.0f, 4.0f};  // r of Eq. (runtime) per algorithm (fw_algo order)
   unsigned long long fingerprint = 0;
   double preprocess_ms = 0.0;
   size_t bytes = 0;

@@ -84,7 +84,7 @@ struct JobTableN {
   Job jobs[NJ];
 };
 
-template <int NJ, bool COUNT>
+template <int NJ, bool COUNT, int ALG>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, JobTableN<NJ> tab, int njobs, long long total,
                                                       unsigned long long* __restrict__ qctr,
                                                       unsigned* __restrict__ err, DevCounters* __restrict__ cnt) {
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
       } else {
         int32_t m = J.mode;
         if (m == MODE_EXACT) {
-          if (J.algo == ALGO_PAGERANK2 && c.vp >= 0) pagerank2_weights(J, c.d, c.pe - c.ps, c.w1, c.w2);
+          if (FW_ALGO(J) == ALGO_PAGERANK2 && c.vp >= 0) pagerank2_weights(J, c.d, c.pe - c.ps, c.w1, c.w2);
           plan = (c.d <= kThreadExactMaxDeg) ? PLAN_EXACT_T : PLAN_EXACT_W;
         } else {
           float hm, hs, S;
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
             hs = (float)c.d;
           }
           int32_t choice;
-          if (J.label_stats) {
+          if (FW_ALGO(J) == ALGO_METAPATH && J.label_stats) {
             // metapath with per-label statistics: exact bound and exact sum over
             // the edges whose label the step requires; none -> dead end now
             const uint8_t want = J.schema[c.step % J.schema_len];
@@ -235,8 +235,16 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
             choice = (__fmul_rn(J.ratio, B) < S) ? MODE_RJS : MODE_RVS;
             if (!(S > 0.0f)) pick = -1;
           } else {
-            if (J.algo == ALGO_PAGERANK2 && c.vp >= 0) pagerank2_weights(J, c.d, c.pe - c.ps, c.w1, c.w2);
-            choice = plan_choice(J, hm, hs, c.vp >= 0, c.w1, c.w2, B, S);
+            if (FW_ALGO(J) == ALGO_PAGERANK2 && c.vp >= 0) pagerank2_weights(J, c.d, c.pe - c.ps, c.w1, c.w2);
+            choice = plan_choice<ALG>(J, hm, hs, c.vp >= 0, c.w1, c.w2, B, S);
+            if (FW_ALGO(J) == ALGO_PAGERANK2 && c.vp >= 0 && !(J.flags & FW_FLAG_PLAIN_RJS) &&
+                c.pe - c.ps <= kPr2SplitMaxPrev && c.w1 > __fmul_rn(2.0f, c.w2)) {
+              // common neighbours split off: eRJS then costs as a first-order walk with bound w2 h_MAX
+              split = true;
+              B = __fmul_rn(c.w2, hm);
+              S = __fmul_rn(c.w2, hs);
+              choice = (__fmul_rn(J.ratio, B) < S) ? MODE_RJS : MODE_RVS;
+            }
           }
           if (m == MODE_AUTO) {
             m = choice;
@@ -246,7 +254,19 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
             m = (c.d < kDegreeRuleThreshold) ? MODE_RVS : MODE_RJS;
           }
           plan = (m == MODE_RJS) ? PLAN_RJS : ((c.d <= kThreadRvsMaxDeg) ? PLAN_RVS_T : PLAN_RVS_W);
-          if (plan == PLAN_RJS && J.split_return && c.vp >= 0) {
+          if (split) {  // second-order PageRank: S_C and the probability of the common-neighbour part
+            split = plan == PLAN_RJS;
+            if (split) {
+              uint32_t pb = 0;
+              h_ret = common_h_sum(g, J, c, pb);
+              if (COUNT) {
+                lc.probes += pb;
+                lc.bytes += 32ull * pb + 4ull * (uint32_t)(c.pe - c.ps);
+              }
+              const float wc = __fmul_rn(__fsub_rn(c.w1, c.w2), h_ret);
+              beta = wc / (wc + (float)c.d * B);
+            }
+          } else if (FW_ALGO(J) == ALGO_NODE2VEC && plan == PLAN_RJS && J.split_return && c.vp >= 0) {
             // the return edge alone sets max(w) = 1/p: propose it separately and
             // bound the other neighbours by max(1, 1/q) * h_MAX[v]
             split = true;
@@ -280,7 +300,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
     // ------------------------------------------------------------ eRJS trials
     if (widx >= 0 && plan == PLAN_RJS && pick == -2) {
       Accept acc;
-      if (rjs_trials<COUNT>(g, J, c, B, split, beta, pos_ret, h_ret, trials, kRjsBatch, acc, lc)) {
+      if (rjs_trials<COUNT, ALG>(g, J, c, B, split, beta, pos_ret, h_ret, trials, kRjsBatch, acc, lc)) {
         pick = acc.k;
         node = acc.node;
         h_in = acc.h;
@@ -300,14 +320,14 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
     }
     // ------------------------------------------------------------ single-lane eRVS / exact
     if (widx >= 0 && pick == -2 && plan == PLAN_RVS_T) {
-      pick = rvs_pick<1, COUNT>(g, J, c, 0, !(J.flags & FW_FLAG_RVS_NOJUMP), lc);
+      pick = rvs_pick<1, COUNT, ALG>(g, J, c, 0, !(J.flags & FW_FLAG_RVS_NOJUMP), lc);
       if (pick >= 0) node = __ldg(g.col + c.s + pick);
       h_in = -1.0f;
       if (COUNT) lc.rvs_steps++;
     }
     if (widx >= 0 && pick == -2 && plan == PLAN_EXACT_T) {
       const float u = u01(philox(make_uint4(c.wid, (uint32_t)c.step, 0u, 0u), J.key0, J.key1).x);
-      pick = exact_pick<1, COUNT>(g, J, c, 0, u, lc);
+      pick = exact_pick<1, COUNT, ALG>(g, J, c, 0, u, lc);
       if (pick >= 0) node = __ldg(g.col + c.s + pick);
       h_in = -1.0f;
       if (COUNT) lc.exact_steps++;
@@ -326,17 +346,19 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
       w.pe = __shfl_sync(kFull, c.pe, src);
       w.step = __shfl_sync(kFull, c.step, src);
       w.wid = __shfl_sync(kFull, c.wid, src);
-      w.w1 = __shfl_sync(kFull, c.w1, src);
-      w.w2 = __shfl_sync(kFull, c.w2, src);
+      if (ALG < 0 || ALG == ALGO_PAGERANK2) {
+        w.w1 = __shfl_sync(kFull, c.w1, src);
+        w.w2 = __shfl_sync(kFull, c.w2, src);
+      }
       const int jb = __shfl_sync(kFull, job, src);
       const int pl = __shfl_sync(kFull, plan, src);
       const Job& JW = sj[jb];
       int32_t k;
       if (pl == PLAN_EXACT_W) {
         const float u = u01(philox(make_uint4(w.wid, (uint32_t)w.step, 0u, 0u), JW.key0, JW.key1).x);
-        k = exact_pick<32, COUNT>(g, JW, w, lane, u, lc);
+        k = exact_pick<32, COUNT, ALG>(g, JW, w, lane, u, lc);
       } else {
-        k = rvs_pick<32, COUNT>(g, JW, w, lane, !(JW.flags & FW_FLAG_RVS_NOJUMP), lc);
+        k = rvs_pick<32, COUNT, ALG>(g, JW, w, lane, !(JW.flags & FW_FLAG_RVS_NOJUMP), lc);
       }
       if (lane == src) {
         pick = k;
@@ -393,12 +415,12 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
   }
 }
 
-template <int NJ, bool COUNT>
+template <int NJ, bool COUNT, int ALG>
 static cudaError_t walk_blocks_per_sm(int* out) {
   static std::atomic<int> cached{0};
   int b = cached.load();
   if (b == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, walk_kernel<NJ, COUNT>, kBlock, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, walk_kernel<NJ, COUNT, ALG>, kBlock, 0);
     if (e != cudaSuccess) return e;
     b = b > 0 ? b : 1;
     cached.store(b);
@@ -407,39 +429,60 @@ static cudaError_t walk_blocks_per_sm(int* out) {
   return cudaSuccess;
 }
 
-cudaError_t prime_walk_occupancy() {
-  int b;
-  cudaError_t e = walk_blocks_per_sm<1, false>(&b);
-  if (e == cudaSuccess) e = walk_blocks_per_sm<1, true>(&b);
-  if (e == cudaSuccess) e = walk_blocks_per_sm<kMaxJobs, false>(&b);
-  if (e == cudaSuccess) e = walk_blocks_per_sm<kMaxJobs, true>(&b);
+template <bool COUNT>
+static cudaError_t prime_single(int* b) {
+  cudaError_t e = walk_blocks_per_sm<1, COUNT, ALGO_WEIGHTED>(b);
+  if (e == cudaSuccess) e = walk_blocks_per_sm<1, COUNT, ALGO_NODE2VEC>(b);
+  if (e == cudaSuccess) e = walk_blocks_per_sm<1, COUNT, ALGO_METAPATH>(b);
+  if (e == cudaSuccess) e = walk_blocks_per_sm<1, COUNT, ALGO_PAGERANK2>(b);
   return e;
 }
 
-template <int NJ, bool COUNT>
+cudaError_t prime_walk_occupancy() {
+  int b;
+  cudaError_t e = prime_single<false>(&b);
+  if (e == cudaSuccess) e = prime_single<true>(&b);
+  if (e == cudaSuccess) e = walk_blocks_per_sm<kMaxJobs, false, -1>(&b);
+  if (e == cudaSuccess) e = walk_blocks_per_sm<kMaxJobs, true, -1>(&b);
+  return e;
+}
+
+template <int NJ, bool COUNT, int ALG>
 static cudaError_t launch_walk_t(const fw_graph* g, const Job* jobs, int njobs, long long total,
                                  unsigned long long* qctr, cudaStream_t stream) {
   int blocks_per_sm = 1;
-  cudaError_t oe = walk_blocks_per_sm<NJ, COUNT>(&blocks_per_sm);
+  cudaError_t oe = walk_blocks_per_sm<NJ, COUNT, ALG>(&blocks_per_sm);
   if (oe != cudaSuccess) return oe;
   JobTableN<NJ> tab;
   for (int i = 0; i < njobs; ++i) tab.jobs[i] = jobs[i];
   const long long want = (total + kBlock - 1) / kBlock;
   const long long cap = (long long)g->num_sms * blocks_per_sm;
   const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
-  walk_kernel<NJ, COUNT><<<grid, kBlock, 0, stream>>>(dev_graph(g), tab, njobs, total, qctr, g->d_err, g->d_cnt);
+  walk_kernel<NJ, COUNT, ALG><<<grid, kBlock, 0, stream>>>(dev_graph(g), tab, njobs, total, qctr, g->d_err, g->d_cnt);
   g_launches.fetch_add(1);
   return cudaGetLastError();
+}
+
+// One job: the kernel specialised to its algorithm.  Several: one kernel for
+// any mix (the algorithm is read per job).
+template <bool COUNT>
+static cudaError_t launch_single(const fw_graph* g, const Job* jobs, long long total, unsigned long long* qctr,
+                                 cudaStream_t stream) {
+  switch (jobs[0].algo) {
+    case ALGO_WEIGHTED: return launch_walk_t<1, COUNT, ALGO_WEIGHTED>(g, jobs, 1, total, qctr, stream);
+    case ALGO_NODE2VEC: return launch_walk_t<1, COUNT, ALGO_NODE2VEC>(g, jobs, 1, total, qctr, stream);
+    case ALGO_METAPATH: return launch_walk_t<1, COUNT, ALGO_METAPATH>(g, jobs, 1, total, qctr, stream);
+    default: return launch_walk_t<1, COUNT, ALGO_PAGERANK2>(g, jobs, 1, total, qctr, stream);
+  }
 }
 
 cudaError_t launch_walk(const fw_graph* g, const Job* jobs, int njobs, long long total, bool count,
                         unsigned long long* qctr, cudaStream_t stream) {
   if (njobs == 1) {
-    return count ? launch_walk_t<1, true>(g, jobs, njobs, total, qctr, stream)
-                 : launch_walk_t<1, false>(g, jobs, njobs, total, qctr, stream);
+    return count ? launch_single<true>(g, jobs, total, qctr, stream) : launch_single<false>(g, jobs, total, qctr, stream);
   }
-  return count ? launch_walk_t<kMaxJobs, true>(g, jobs, njobs, total, qctr, stream)
-               : launch_walk_t<kMaxJobs, false>(g, jobs, njobs, total, qctr, stream);
+  return count ? launch_walk_t<kMaxJobs, true, -1>(g, jobs, njobs, total, qctr, stream)
+               : launch_walk_t<kMaxJobs, false, -1>(g, jobs, njobs, total, qctr, stream);
 }
 
 // ---------------------------------------------------------------- preprocessing

@@ -42,7 +42,7 @@ class fw_graph_info_t(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("e", ctypes.c_int64), ("max_degree", ctypes.c_int32),
                 ("has_weights", ctypes.c_int32), ("has_labels", ctypes.c_int32), ("cost_ratio", ctypes.c_float),
                 ("preprocess_ms", ctypes.c_double), ("device_bytes", ctypes.c_size_t), ("symmetric", ctypes.c_int32),
-                ("cost_ratios", ctypes.c_float * 3), ("fingerprint", ctypes.c_uint64),
+                ("cost_ratios", ctypes.c_float * 4), ("fingerprint", ctypes.c_uint64),
                 ("weight_scale", ctypes.c_float)]
 
 
@@ -368,9 +368,10 @@ class Graph:
     def check(self, stream=None):
         fw_graph_check(self.handle, stream)
 
-    def autotune(self, algo="node2vec", *, p=1.0, q=1.0, schema=None, gamma=0.2, method=0, cache_path=None,
-                 stream=None):
-        r = fw_autotune(self.handle, algo, make_params(p, q, schema, gamma=gamma), method, cache_path, stream)
+    def autotune(self, algo="node2vec", *, p=1.0, q=1.0, schema=None, gamma=0.2, flags=0, method=0,
+                 cache_path=None, stream=None):
+        r = fw_autotune(self.handle, algo, make_params(p, q, schema, flags=flags, gamma=gamma), method, cache_path,
+                        stream)
         self.info = fw_graph_info(self.handle)
         return r
 

@@ -92,7 +92,8 @@ def test_hub_distributions_s22(s22, mode, flags, ndraws):
     nb = g.cols[g.offsets[hub]:g.offsets[hub + 1]]
     small_prev = int(nb[np.argmin(deg[nb])])
     states = [(hub, -1, 0, "weighted", 1.0, 1.0), (hub, small_prev, 1, "node2vec", 2.0, 0.5),
-              (hub, small_prev, 1, "node2vec", 0.25, 4.0), (small_prev, hub, 1, "node2vec", 4.0, 0.25)]
+              (hub, small_prev, 1, "node2vec", 0.25, 4.0), (small_prev, hub, 1, "node2vec", 4.0, 0.25),
+              (hub, small_prev, 1, "pagerank2", 1.0, 1.0), (small_prev, hub, 1, "pagerank2", 1.0, 1.0)]
     bound = 2e-3 if ndraws >= 4_000_000 else 4e-3
     for (v, vp, step, algo, p, q) in states:
         probs = oracle.transition_probs(g, v, vp, step, algo, p, q)

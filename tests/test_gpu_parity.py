@@ -158,7 +158,10 @@ def test_step_plan_parity(small, algo, p, q):
 
 # ------------------------------------------------------------ fast-mode distributions
 def _states(g):
-    """(v, v_prev, step) states covering degrees 1, 2, ~4, ~32, ~300, max."""
+    """(v, v_prev, step) states covering degrees 1, 2, ~4, ~32, ~300, max,
+    each with no v', with the highest-degree neighbour as v', and (d > 4)
+    with the lowest-degree neighbour as v' (short N(v'): second-order
+    PageRank then splits the common neighbours off)."""
     deg = g.degrees()
     out = []
     for target in [1, 2, 4, 32, 300, int(deg.max())]:
@@ -167,6 +170,8 @@ def _states(g):
         hub_prev = int(nb[np.argmax(deg[nb])])
         out.append((v, -1, 0))
         out.append((v, hub_prev, 1))
+        if target > 4:
+            out.append((v, int(nb[np.argmin(deg[nb])]), 1))
     return out
 
 
@@ -321,3 +326,20 @@ def test_fast_walk_path_distribution(graph, mode, flags, algo, p, q, schema):
     G.close()
     bf = bf_paths(g, start, L, algo, p, q, schema)
     assert merged_chisquare(bf, out) > 1e-4
+
+
+@pytest.mark.parametrize("gamma", [0.2, 0.8])
+@pytest.mark.parametrize("mode,flags", [("rjs", 0), ("auto", 0), ("rjs", fw.FLAG_PLAIN_RJS)])
+def test_pagerank2_common_neighbour_split_paths(gamma, mode, flags):
+    """A hub whose leaves have short rows: stepping from a leaf v' onto the
+    hub v gives w1 / w2 = 1 + gamma/(1-gamma) * d(v)/d(v') > 2, where eRJS
+    splits the common neighbours off (FLAG_PLAIN_RJS: the plain bound).
+    Whole 4-hop path frequencies against brute force."""
+    edges = [(0, k) for k in range(1, 10)] + [(1, 2), (2, 3), (4, 5), (6, 7), (7, 8), (8, 9), (1, 10), (10, 11)]
+    g = synth.from_edges(12, edges, h=[0.25 + 0.07 * i for i in range(len(edges))])
+    G = fw.Graph(g)
+    W, L = 400_000, 4
+    out = G.walk(torch.full((W,), 1, dtype=torch.int32, device="cuda"), L, "pagerank2", gamma=gamma, mode=mode,
+                 flags=flags, seed=29).cpu().numpy()
+    G.close()
+    assert merged_chisquare(bf_paths(g, 1, L, "pagerank2", 1.0, 1.0, None, gamma=gamma), out) > 1e-4

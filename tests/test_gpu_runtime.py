@@ -24,7 +24,7 @@ def small():
 
 
 @pytest.mark.parametrize("algo,p,q,schema", [("node2vec", 2.0, 0.5, None), ("metapath", 1.0, 1.0, [0, 1, 2, 3, 4]),
-                                             ("weighted", 1.0, 1.0, None)])
+                                             ("weighted", 1.0, 1.0, None), ("pagerank2", 1.0, 1.0, None)])
 def test_autotune_profiling_installs_a_ratio(small, algo, p, q, schema, tmp_path):
     g, G = small
     cache = str(tmp_path / "ratios.txt")
@@ -37,9 +37,18 @@ def test_autotune_profiling_installs_a_ratio(small, algo, p, q, schema, tmp_path
     with open(cache, "w") as f:
         f.write(lines[0].rsplit("r=", 1)[0] + "r=123.5\n")
     assert G.autotune(algo, p=p, q=q, schema=schema, method=0, cache_path=cache) == pytest.approx(123.5)
-    # another (p, q) misses and appends
+    # another (p, q), other sampler flags, or another gamma miss and append
     G.autotune(algo, p=p * 2, q=q, schema=schema, method=0, cache_path=cache)
     assert len(open(cache).read().splitlines()) == 2
+    G.autotune(algo, p=p, q=q, schema=schema, flags=fw.FLAG_UNWEIGHTED, method=0, cache_path=cache)
+    assert len(open(cache).read().splitlines()) == 3
+    G.autotune(algo, p=p, q=q, schema=schema, gamma=0.5, method=0, cache_path=cache)
+    assert len(open(cache).read().splitlines()) == 4
+    # every algorithm keeps its own ratio
+    G.set_cost_ratio(4.0)
+    G.autotune(algo, p=p, q=q, schema=schema, method=0)
+    others = [a for a in range(4) if a != fw.ALGO[algo]]
+    assert all(G.info["cost_ratios"][a] == 4.0 for a in others)
     G.set_cost_ratio(4.0)
 
 
