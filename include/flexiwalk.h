@@ -83,7 +83,10 @@ enum {
   FW_FLAG_UNWEIGHTED = 4, /* ignore h: every property weight is 1 (Sec. 5.1)     */
   FW_FLAG_PLAIN_RJS = 8,  /* eRJS exactly as Sec. 3.3 (uniform proposal, bound
                              max(w) * h_MAX) even when node2vec's return edge
-                             could be proposed separately                        */
+                             could be proposed separately, when node2vec with
+                             q > 1 could propose from two envelopes, or when
+                             second-order PageRank could split off the common
+                             neighbours                                          */
   FW_FLAG_PAPER_SUM = 16, /* metapath: plan with the Sec. 4.2 rule (B = h_MAX,
                              sum-hat = h_SUM / 2) even when per-label node
                              statistics exist                                    */

@@ -81,6 +81,7 @@ fw_status make_job(const fw_graph* g, int32_t algo, const fw_params* params, uin
     job->need_member = (iq != 1.0f) ? 1 : 0;
     job->second_order = (ip != 1.0f || iq != 1.0f) ? 1 : 0;
     job->split_return = (ip > job->whi1 && !(P.flags & FW_FLAG_PLAIN_RJS)) ? 1 : 0;
+    job->split_common = (iq < 1.0f && !(P.flags & FW_FLAG_PLAIN_RJS)) ? 1 : 0;
   } else {
     job->inv_p = job->inv_q = 1.0f;
     job->wmax1 = job->wlo1 = job->whi1 = 1.0f;

@@ -72,6 +72,7 @@ struct Job {
   int32_t need_member;     // node2vec with 1/q != 1: membership test needed
   int32_t fixed_cap;       // 1: rjs_cap is a fixed trial cap; 0: cap = max(rjs_cap, ceil(d / ratio))
   int32_t split_return;    // node2vec with 1/p > max(1, 1/q): eRJS proposes the return edge separately
+  int32_t split_common;    // node2vec with 1/q < 1: eRJS may use the two-envelope proposal (d(v') < d(v))
   int32_t label_stats;     // metapath: plan with the per-label h_MAX / h_SUM of the required label
   int32_t bloom;           // 1: membership tests in N(v') consult the row's Bloom filter first
   float inv_p, inv_q;      // FP32 1/p, 1/q
@@ -351,6 +352,24 @@ __device__ __forceinline__ int32_t plan_choice(const Job& J, float hm, float hs,
 }
 
 // ---------------------------------------------------------------- eRJS
+// Exactly uniform index in [0, d) by Lemire's multiply-shift with rejection
+// (ACM TOMACS 2019): x0 proposes, x1 is the one retry; false when both fall
+// in the rejection zone (the trial then proposes nothing).
+__device__ __forceinline__ bool lemire_index(uint32_t x0, uint32_t x1, uint32_t d, uint32_t& k) {
+  unsigned long long m = (unsigned long long)x0 * d;
+  uint32_t l = (uint32_t)m;
+  if (l < d) {
+    const uint32_t thr = (0u - d) % d;
+    if (l < thr) {
+      m = (unsigned long long)x1 * d;
+      l = (uint32_t)m;
+      if (l < thr) return false;
+    }
+  }
+  k = (uint32_t)(m >> 32);
+  return true;
+}
+
 // One eRJS acceptance: the neighbour position, the node, its effective
 // property weight, and the target's node record (rec_ok = 0: unknown).
 struct Accept {
@@ -380,10 +399,24 @@ struct Accept {
 // otherwise X is uniform over N(v) and accepted iff U*B < w2 h(X).  The two
 // parts are proportional to the two terms of w~, so again the accepted
 // draw follows Eq. (prob).
+// Two envelopes (node2vec with 1/q < 1 and d(v') < d(v)): write
+// w~(x) = (1/q) h(x) + (1 - 1/q) h(x) [x in N(v')] for x != v'.  The first
+// term is covered by (1/q) h_MAX[v] on N(v), the second by
+// (1 - 1/q) h_MAX[v] on N(v'); with the return edge as a third component,
+// a trial picks a component in proportion to its envelope mass
+// (E3 = w~_ret, E2 = (1 - 1/q) d(v') h_MAX, E1 = (1/q) d(v) h_MAX; `beta`
+// and `beta2` are E3 / E and (E3 + E2) / E) and accepts with probability
+// target / envelope: component 1 proposes X uniform over N(v) (X = v'
+// proposes nothing) and accepts iff U h_MAX < h(X), with no membership test;
+// component 2 proposes X uniform over N(v') and accepts iff X is in N(v) and
+// U h_MAX < h(v, X).  The accepted x carries (1/q) h(x) from the first and
+// (1 - 1/q) h(x) [x in N(v')] from the second: w~(x) in total.  The envelope
+// mass is (1/q) d + (1 - 1/q) d' < d, so fewer trials than the one-envelope
+// bound max(1, 1/q) h_MAX = h_MAX (B = h_MAX is passed in this case).
 template <bool COUNT, int ALG = -1>
 __device__ __forceinline__ bool rjs_trials(const DevGraph& g, const Job& J, const StepCtx& c, float B, bool split,
                                            float beta, int32_t pos_ret, float h_ret, int32_t t0, int32_t nt,
-                                           Accept& acc, LaneCounters& lc) {
+                                           Accept& acc, LaneCounters& lc, bool csplit = false, float beta2 = 0.0f) {
   const uint32_t d = (uint32_t)c.d;
   const uint8_t want = (FW_ALGO(J) == ALGO_METAPATH) ? J.schema[c.step % J.schema_len] : 0;
   const bool second = (FW_ALGO(J) == ALGO_NODE2VEC) && c.vp >= 0 && J.second_order;
@@ -392,7 +425,8 @@ __device__ __forceinline__ bool rjs_trials(const DevGraph& g, const Job& J, cons
   for (int32_t t = t0; t < t0 + nt; ++t) {
     const uint4 x = philox(make_uint4(c.wid, (uint32_t)c.step, 1u, (uint32_t)t), J.key0, J.key1);
     if (COUNT) lc.rjs_trials++;
-    if (beta > 0.0f && u01(x.w) < beta) {
+    const float ucomp = u01(x.w);
+    if (beta > 0.0f && ucomp < beta) {
       if (FW_ALGO(J) == ALGO_PAGERANK2) {
         uint32_t pb = 0;
         acc.node = common_pick(g, J, c, __fmul_rn(u01(x.z), h_ret), acc.k, acc.h, pb);
@@ -406,19 +440,35 @@ __device__ __forceinline__ bool rjs_trials(const DevGraph& g, const Job& J, cons
       found = true;
       break;
     }
-    unsigned long long m = (unsigned long long)x.x * d;
-    uint32_t l = (uint32_t)m;
-    if (l < d) {
-      const uint32_t thr = (0u - d) % d;
-      if (l < thr) {
-        m = (unsigned long long)x.y * d;
-        l = (uint32_t)m;
-        if (l < thr) continue;  // this trial proposes nothing; trials stay i.i.d.
-      }
-    }
-    const int32_t k = (int32_t)(m >> 32);
-    const int4* er = g.erec + 2ll * (c.s + k);
     int4 a, b;  // {col, h, target row start, target degree}, {target h_MAX, target h_SUM, label, 0}
+    if ((FW_ALGO(J) == ALGO_NODE2VEC) && csplit && ucomp < beta2) {
+      // component 2: X uniform over N(v'), accepted iff X in N(v) and U h_MAX < h(v, X)
+      uint32_t k2;
+      if (!lemire_index(x.x, x.y, (uint32_t)(c.pe - c.ps), k2)) continue;
+      const int32_t X = __ldg(g.col + c.ps + (int32_t)k2);
+      uint32_t pb = 0;
+      const int32_t pos = row_lookup(g, J, c.v, c.s, c.s + c.d, X, pb);  // X = v is never in N(v)
+      probes += pb;
+      if (COUNT) lc.bytes += 32;
+      if (pos < 0) continue;
+      ld_record(g.erec + 2ll * pos, a, b);
+      if (COUNT) lc.bytes += 32;
+      const float hx = J.weighted ? __int_as_float(a.y) : 1.0f;
+      if (__fmul_rn(u01(x.z), B) < hx) {
+        acc.k = pos - c.s;
+        acc.node = X;
+        acc.h = hx;
+        acc.rec = make_int4(a.z, a.w, b.x, b.y);
+        acc.rec_ok = true;
+        found = true;
+        break;
+      }
+      continue;
+    }
+    uint32_t ku;
+    if (!lemire_index(x.x, x.y, d, ku)) continue;  // this trial proposes nothing; trials stay i.i.d.
+    const int32_t k = (int32_t)ku;
+    const int4* er = g.erec + 2ll * (c.s + k);
     ld_record(er, a, b);
     if (COUNT) lc.bytes += 32;
     const int32_t u = a.x;
@@ -429,6 +479,8 @@ __device__ __forceinline__ bool rjs_trials(const DevGraph& g, const Job& J, cons
       if (u == c.vp) {
         if (split) continue;                    // the return component owns v'
         accept = UB < __fmul_rn(J.inv_p, hk);
+      } else if (csplit) {
+        accept = UB < hk;                       // component 1: (1/q) h against (1/q) h_MAX
       } else if (UB >= __fmul_rn(J.whi1, hk)) {
         accept = false;                         // squeeze: above the largest possible weight
       } else if (UB < __fmul_rn(J.wlo1, hk)) {

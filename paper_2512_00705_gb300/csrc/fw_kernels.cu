@@ -120,6 +120,9 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
   // position of v' in N(v) (-1: unknown) and h(v, v')
   bool split = false;
   float beta = 0.0f, h_ret = 0.0f;
+  // node2vec with 1/q < 1 and d(v') < d(v): two envelopes; beta2 = (E3 + E2) / E
+  bool csplit = false;
+  float beta2 = 0.0f;
   int32_t pos_ret = -1;
   // from the accepted trial: the next node's record, and h of the edge taken (-1: unknown)
   int4 nxt = make_int4(0, 0, 0, 0);
@@ -202,6 +205,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
       trials = 0;
       pick = -2;
       split = false;
+      csplit = false;
       beta = 0.0f;
       if (c.d == 0) {
         pick = -1;
@@ -266,11 +270,14 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
               const float wc = __fmul_rn(__fsub_rn(c.w1, c.w2), h_ret);
               beta = wc / (wc + (float)c.d * B);
             }
-          } else if (FW_ALGO(J) == ALGO_NODE2VEC && plan == PLAN_RJS && J.split_return && c.vp >= 0) {
+          } else if (FW_ALGO(J) == ALGO_NODE2VEC && plan == PLAN_RJS && c.vp >= 0 &&
+                     (J.split_return || (J.split_common && c.pe - c.ps < c.d))) {
             // the return edge alone sets max(w) = 1/p: propose it separately and
-            // bound the other neighbours by max(1, 1/q) * h_MAX[v]
+            // bound the other neighbours by max(1, 1/q) * h_MAX[v]; with 1/q < 1 and
+            // a shorter row of v', two envelopes (see rjs_trials) instead
             split = true;
-            B = __fmul_rn(J.whi1, hm);
+            csplit = J.split_common && c.pe - c.ps < c.d;
+            B = csplit ? hm : __fmul_rn(J.whi1, hm);
             pos_ret = -1;
             bool have = false;
             if (g.sym && h_in >= 0.0f && J.kind == JOB_WALK) {
@@ -289,7 +296,14 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
                 have = true;
               }
             }
-            if (have) {
+            if (csplit) {
+              const float e3 = have ? __fmul_rn(J.inv_p, h_ret) : 0.0f;
+              const float e2 = __fmul_rn(__fmul_rn(__fsub_rn(1.0f, J.inv_q), (float)(c.pe - c.ps)), hm);
+              const float e1 = __fmul_rn(__fmul_rn(J.inv_q, (float)c.d), hm);
+              const float tot = __fadd_rn(__fadd_rn(e3, e2), e1);
+              beta = e3 / tot;
+              beta2 = __fadd_rn(e3, e2) / tot;
+            } else if (have) {
               const float wret = __fmul_rn(J.inv_p, h_ret);
               beta = wret / (wret + (float)c.d * B);
             }
@@ -300,7 +314,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
     // ------------------------------------------------------------ eRJS trials
     if (widx >= 0 && plan == PLAN_RJS && pick == -2) {
       Accept acc;
-      if (rjs_trials<COUNT, ALG>(g, J, c, B, split, beta, pos_ret, h_ret, trials, kRjsBatch, acc, lc)) {
+      if (rjs_trials<COUNT, ALG>(g, J, c, B, split, beta, pos_ret, h_ret, trials, kRjsBatch, acc, lc, csplit, beta2)) {
         pick = acc.k;
         node = acc.node;
         h_in = acc.h;

@@ -178,6 +178,7 @@ def _states(g):
 @pytest.mark.parametrize("mode,flags", [("rjs", 0), ("rvs", 0), ("rvs", fw.FLAG_RVS_NOJUMP), ("auto", 0), ("random", 0),
                                         ("degree", 0)])
 @pytest.mark.parametrize("algo,p,q,schema", [("node2vec", 2.0, 0.5, None), ("node2vec", 0.25, 4.0, None),
+                                             ("node2vec", 2.0, 4.0, None),
                                              ("metapath", 1.0, 1.0, [0, 1, 2, 3, 4]), ("weighted", 1.0, 1.0, None),
                                              ("pagerank2", 1.0, 1.0, None)])
 def test_fast_mode_distributions(small, mode, flags, algo, p, q, schema):
@@ -297,6 +298,7 @@ def _asymmetric(g, seed):
 
 
 WALK_CASES = [("node2vec", 0.25, 4.0, None), ("node2vec", 2.0, 0.5, None), ("node2vec", 4.0, 0.25, None),
+              ("node2vec", 2.0, 4.0, None),
               ("metapath", 1.0, 1.0, [0, 1, 2]), ("weighted", 1.0, 1.0, None), ("pagerank2", 1.0, 1.0, None)]
 
 
