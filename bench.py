@@ -756,6 +756,13 @@ def main():
         e2e_line = {"value": hops_all / (e2e_ms_all / 1000.0), "unit": "walker-steps/s",
                     "h2d_bytes_per_step": len(PQ) * nw * 4, "d2h_bytes_per_step": len(PQ) * nw * (LENGTH + 1) * 4}
 
+    # ---- random-access ceiling of the device memory (the walk kernel's operative roof):
+    # dependent 32-byte gathers over a 4 GiB table, the walk kernel's launch shape
+    table = torch.empty(4 << 30, dtype=torch.uint8, device=dev)
+    gather_ceiling = fw.fw_gather_ceiling(table)
+    del table
+    torch.cuda.empty_cache()
+
     # ---- roofline of the walk kernel
     peak, peak_kind = measured_peaks()
     kern_ms = sum(sum(v) for v in per_launch.values()) / args.steps
@@ -786,6 +793,13 @@ def main():
                      "peak_kind": peak_kind, "kernel": "walk_kernel<1,false>",
                      "algorithmic_bytes_per_launch": bytes_per_step / len(PQ),
                      "avg_launch_ms": kern_ms / len(PQ)},
+        "roofline_random_access": {
+            "bound": "dram_random_access", "unit": "G sector accesses/s",
+            "achieved": bytes_per_step / 32.0 / (kern_ms / 1000.0) / 1e9,
+            "peak": gather_ceiling / 1e9, "frac": bytes_per_step / 32.0 / (kern_ms / 1000.0) / gather_ceiling,
+            "peak_kind": "measured in this run by fw_gather_ceiling (dependent 32-B gathers, 4 GiB table, "
+                         "5x256 threads per SM)",
+            "note": "algorithmic bytes are sector-granular (32 B per random access), so bytes/32 = accesses"},
         "e2e": e2e_line,
         "gpu_launches": launches,
         "clocks": clocks,

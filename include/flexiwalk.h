@@ -258,7 +258,12 @@ fw_status fw_walk_ids(const fw_graph* graph, const int32_t* starts, const uint32
  * int32[num_walkers][len+1]); returns when out is filled.  Pinned host
  * memory gives the fastest copies.  Device staging buffers are owned by the
  * graph and reused across calls (one call at a time per graph: FW_ERR_BUSY
- * otherwise).
+ * otherwise).  Requests whose rows take 128 MiB or more are walked in up to
+ * 16 chunks of consecutive walkers, on `stream` and a second stream owned by
+ * the graph, and each chunk's rows are copied out on a third while later
+ * chunks still walk; walker i keeps random-stream id walker_base + i, so the
+ * rows are those of one fw_walk.  Work already queued on `stream` runs
+ * first.
  */
 fw_status fw_walk_host(fw_graph* graph, const int32_t* starts, int32_t num_walkers, int32_t len,
                        int32_t algo, const fw_params* params, uint64_t seed, int32_t* out,
@@ -411,6 +416,23 @@ fw_status fw_server_stats(fw_server* server, fw_server_stats_t* out);
 fw_status fw_server_destroy(fw_server* server);
 
 /* Number of kernel launches this library has issued (process-wide). */
+/*
+ * Measurement hook for the walk kernel's roofline (no counterpart in the
+ * paper, whose kernels it does not change).  eRJS trials, node-record
+ * fetches and membership probes are dependent 32-byte gathers at random
+ * addresses; on HBM each costs a DRAM access whatever its width, so they
+ * are bound by the random accesses per second the memory completes, not by
+ * the copy bandwidth.  This call measures that ceiling with the walk
+ * kernel's launch shape (5 blocks of 256 threads per SM, each thread a chain
+ * of 64 dependent gathers whose addresses come from the loaded data).
+ * table: caller-owned device buffer of table_bytes bytes, a power of two of
+ * at least 64 MiB (use one well above the L2 size), 32-byte aligned; it is
+ * overwritten.  rate_out: host double, gathers per second (best of three
+ * launches after one warm-up, CUDA events on `stream`).  Synchronises
+ * `stream`; allocates nothing.  FW_ERR_ARG on a bad size or pointer.
+ */
+fw_status fw_gather_ceiling(void* table, uint64_t table_bytes, double* rate_out, void* stream);
+
 uint64_t fw_launch_count(void);
 
 const char* fw_last_error(void);

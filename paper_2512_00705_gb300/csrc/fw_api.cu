@@ -1,4 +1,5 @@
 // fw_api.cu -- the C ABI declared in include/flexiwalk.h.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -252,6 +253,10 @@ static void free_graph(fw_graph* g) {
   cudaFree(g->d_cnt);
   cudaFree(g->d_stage_starts);
   cudaFree(g->d_stage_out);
+  if (g->host_walk2) cudaStreamDestroy(g->host_walk2);
+  if (g->host_copy) cudaStreamDestroy(g->host_copy);
+  for (cudaEvent_t ev : g->host_ev)
+    if (ev) cudaEventDestroy(ev);
   delete g;
 }
 
@@ -459,16 +464,24 @@ extern "C" fw_status fw_walk_ids(const fw_graph* g, const int32_t* starts, const
   return with_qctr(g, &J, 1, num_walkers, count, reinterpret_cast<cudaStream_t>(stream));
 }
 
+// Rows of at least this many bytes are walked in chunks so that the copy of
+// finished chunks overlaps the walk of later ones.
+static constexpr size_t kHostChunkBytes = 64ull << 20;
+
 extern "C" fw_status fw_walk_host(fw_graph* g, const int32_t* starts, int32_t num_walkers, int32_t len, int32_t algo,
                                   const fw_params* params, uint64_t seed, int32_t* out, void* stream) {
   if (!g) return set_error(FW_ERR_ARG, "graph is NULL");
   if (num_walkers < 0 || len < 0) return set_error(FW_ERR_ARG, "negative size");
   if (num_walkers > 0 && (!starts || !out)) return set_error(FW_ERR_ARG, "NULL starts/out");
+  Job J;
+  fw_status s = make_job(g, algo, params, seed, &J);
+  if (s != FW_OK) return s;
   std::unique_lock<std::mutex> lk(g->stage_mu, std::try_to_lock);
   if (!lk.owns_lock()) return set_error(FW_ERR_BUSY, "another fw_walk_host call is using this graph");
   if (num_walkers == 0) return FW_OK;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const size_t nin = (size_t)num_walkers, nout = (size_t)num_walkers * ((size_t)len + 1);
+  const size_t row = (size_t)len + 1;
+  const size_t nin = (size_t)num_walkers, nout = (size_t)num_walkers * row;
   if (g->stage_starts_cap < nin) {
     cudaFree(g->d_stage_starts);
     g->d_stage_starts = nullptr;
@@ -485,14 +498,59 @@ extern "C" fw_status fw_walk_host(fw_graph* g, const int32_t* starts, int32_t nu
     if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(staging out)");
     g->stage_out_cap = nout;
   }
+  if (!g->host_copy) {
+    cudaError_t e = cudaStreamCreateWithFlags(&g->host_walk2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->host_copy, cudaStreamNonBlocking);
+    for (int i = 0; i <= kHostChunksMax && e == cudaSuccess; ++i)
+      e = cudaEventCreateWithFlags(&g->host_ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_error(e, "create fw_walk_host streams");
+  }
+  // Chunk c holds walkers [c*W/K, (c+1)*W/K).  Chunks are walked alternately
+  // on `stream` and a second stream (a chunk's last blocks share the GPU with
+  // the next chunk's first ones) and each chunk's rows are copied out on a
+  // third stream as soon as its walk ends.  Chunk c's walkers keep their
+  // random-stream ids walker_base + index, so the rows equal one fw_walk.
+  const size_t bytes_out = nout * sizeof(int32_t);
+  const int K = (int)std::min<size_t>((size_t)kHostChunksMax, std::max<size_t>(1, bytes_out / kHostChunkBytes));
+  const bool count = params && (params->flags & FW_FLAG_COUNTERS);
+  cudaEvent_t* ev = g->host_ev;
   cudaError_t e = cudaMemcpyAsync(g->d_stage_starts, starts, nin * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[kHostChunksMax], st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(g->host_walk2, ev[kHostChunksMax], 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(g->host_copy, ev[kHostChunksMax], 0);
   if (e != cudaSuccess) return cuda_error(e, "copy starts");
-  fw_status s = fw_walk(g, g->d_stage_starts, num_walkers, len, algo, params, seed, g->d_stage_out, stream);
+  s = FW_OK;
+  for (int c = 0; c < K && s == FW_OK; ++c) {
+    const size_t lo = nin * (size_t)c / (size_t)K, hi = nin * (size_t)(c + 1) / (size_t)K;
+    if (hi == lo) continue;
+    cudaStream_t ws = (c & 1) ? g->host_walk2 : st;
+    Job Jc = J;
+    Jc.kind = JOB_WALK;
+    Jc.starts = g->d_stage_starts + lo;
+    Jc.out = g->d_stage_out + lo * row;
+    Jc.num_walkers = (int32_t)(hi - lo);
+    Jc.len = len;
+    Jc.gbase = 0;
+    Jc.walker_base = J.walker_base + (uint32_t)lo;
+    s = with_qctr(g, &Jc, 1, (long long)(hi - lo), count, ws);
+    if (s != FW_OK) break;
+    e = cudaEventRecord(ev[c], ws);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(g->host_copy, ev[c], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out + lo * row, g->d_stage_out + lo * row, (hi - lo) * row * sizeof(int32_t),
+                          cudaMemcpyDeviceToHost, g->host_copy);
+    if (e != cudaSuccess) s = cuda_error(e, "copy out");
+  }
+  // join: `stream` waits for the copies (later work on it sees the rows), then all three drain
+  cudaError_t e1 = cudaEventRecord(ev[kHostChunksMax], g->host_copy);
+  if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(st, ev[kHostChunksMax], 0);
+  cudaError_t e2 = cudaStreamSynchronize(g->host_copy);
+  cudaError_t e3 = cudaStreamSynchronize(g->host_walk2);
+  cudaError_t e4 = cudaStreamSynchronize(st);
   if (s != FW_OK) return s;
-  e = cudaMemcpyAsync(out, g->d_stage_out, nout * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
-  if (e != cudaSuccess) return cuda_error(e, "copy out");
-  e = cudaStreamSynchronize(st);
-  return e == cudaSuccess ? FW_OK : cuda_error(e, "sync");
+  for (cudaError_t x : {e1, e2, e3, e4})
+    if (x != cudaSuccess) return cuda_error(x, "sync");
+  return FW_OK;
 }
 
 extern "C" fw_status fw_sample_hist(const fw_graph* g, int32_t v, int32_t v_prev, int32_t step, int32_t algo,

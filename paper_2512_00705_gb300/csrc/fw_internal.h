@@ -11,6 +11,9 @@
 #include "fw_device.cuh"
 #include "../../include/flexiwalk.h"
 
+// fw_walk_host splits large requests into at most this many chunks
+constexpr int kHostChunksMax = 16;
+
 struct fw_graph {
   int device = 0;
   int num_sms = 0;
@@ -43,6 +46,10 @@ struct fw_graph {
   size_t stage_starts_cap = 0;
   int32_t* d_stage_out = nullptr;
   size_t stage_out_cap = 0;
+  // pipelined fw_walk_host: a second walk stream, a copy stream and one event per chunk
+  cudaStream_t host_walk2 = nullptr;
+  cudaStream_t host_copy = nullptr;
+  cudaEvent_t host_ev[kHostChunksMax + 1] = {};
 };
 
 namespace fw {

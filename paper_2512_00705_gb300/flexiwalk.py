@@ -121,6 +121,7 @@ def lib() -> ctypes.CDLL:
                 "fw_server_wait": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_double, P(ctypes.c_double)]),
                 "fw_server_stats": (ctypes.c_int, [vp, P(fw_server_stats_t)]),
                 "fw_server_destroy": (ctypes.c_int, [vp]),
+                "fw_gather_ceiling": (ctypes.c_int, [vp, u64, P(ctypes.c_double), vp]),
                 "fw_launch_count": (ctypes.c_uint64, []),
                 "fw_last_error": (ctypes.c_char_p, []),
                 "fw_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -218,6 +219,15 @@ def fw_walk_ids(handle: int, starts, walker_ids, length: int, algo, params: fw_p
     """starts: CUDA int32 [W]; walker_ids: CUDA int32/uint32 [W]; out: CUDA int32 [W, length+1]."""
     _check(lib().fw_walk_ids(handle, _ptr(starts), _ptr(walker_ids), starts.numel(), length, ALGO.get(algo, algo),
                              ctypes.byref(params), seed, _ptr(out), _stream_ptr(stream)))
+
+
+def fw_gather_ceiling(table, stream=None) -> float:
+    """Random 32-byte gathers per second over `table` (a CUDA tensor of a
+    power-of-two size >= 64 MiB, overwritten); synchronises the stream."""
+    rate = ctypes.c_double()
+    _check(lib().fw_gather_ceiling(_ptr(table), table.numel() * table.element_size(), ctypes.byref(rate),
+                                   _stream_ptr(stream)))
+    return rate.value
 
 
 def fw_walk_host(handle: int, starts: np.ndarray, length: int, algo, params: fw_params, seed: int, out: np.ndarray,

@@ -90,6 +90,10 @@ def test_argument_errors_without_device():
     assert L.fw_walk(None, None, 0, 1, 0, ctypes.byref(prm), 1, None, None) == -1
     assert L.fw_graph_destroy(None) == -1
     assert L.fw_status_string(-2) == b"FW_ERR_CSR"
+    rate = ctypes.c_double()
+    assert L.fw_gather_ceiling(None, 1 << 30, ctypes.byref(rate), None) == -1
+    assert L.fw_gather_ceiling(ctypes.c_void_p(1 << 20), (1 << 30) + 32, ctypes.byref(rate), None) == -1
+    assert L.fw_gather_ceiling(ctypes.c_void_p(1 << 20), 1 << 20, ctypes.byref(rate), None) == -1
 
 
 def test_valid_host_graph_passes_validation():

@@ -236,3 +236,32 @@ def test_sharded_walks_reassemble_to_the_single_walk(small):
                               "node2vec", p=0.5, q=2.0, mode=mode, seed=9).cpu().numpy()
             parts.append((idx, rows))
         assert np.array_equal(sharding.assemble(parts, len(starts), 16), full), mode
+
+
+@pytest.mark.parametrize("algo,p,q,schema,base", [("node2vec", 0.25, 4.0, None, 0),
+                                                  ("metapath", 1.0, 1.0, [0, 1, 2, 3, 4], 77)])
+def test_chunked_host_walk_equals_device_walk(small, algo, p, q, schema, base):
+    """fw_walk_host splits rows of >= 128 MiB into chunks walked on two
+    streams and copied out on a third: 3.2M walkers x 21 entries (269 MB, 4
+    chunks, ragged: 3.2M is not a multiple of 4 * 256) must give exactly the
+    rows of one device walk, in pinned and in pageable host memory."""
+    g, G = small
+    W, L = 3_200_003, 20
+    starts = synth.random_starts(g.n, W, seed=31)
+    want = G.walk(torch.from_numpy(starts).cuda(), L, algo, p=p, q=q, schema=schema, mode="auto", seed=9,
+                  walker_base=base).cpu().numpy()
+    pinned_in = torch.from_numpy(starts).pin_memory().numpy()
+    pinned_out = torch.empty((W, L + 1), dtype=torch.int32).pin_memory().numpy()
+    for st_h, out in [(pinned_in, pinned_out), (starts, np.full((W, L + 1), -7, dtype=np.int32))]:
+        got = G.walk_host(st_h, L, algo, p=p, q=q, schema=schema, mode="auto", seed=9, walker_base=base, out=out)
+        assert np.array_equal(got, want), f"{(got != want).any(axis=1).sum()} rows differ"
+
+
+def test_gather_ceiling_probe():
+    """fw_gather_ceiling: a positive, finite rate of random 32-byte gathers
+    that does not exceed one gather per SM clock cycle."""
+    table = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    rate = fw.fw_gather_ceiling(table)
+    props = torch.cuda.get_device_properties(0)
+    assert np.isfinite(rate) and rate > 1e8
+    assert rate < props.multi_processor_count * 2.5e9
