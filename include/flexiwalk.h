@@ -90,9 +90,12 @@ enum {
   FW_FLAG_PAPER_SUM = 16, /* metapath: plan with the Sec. 4.2 rule (B = h_MAX,
                              sum-hat = h_SUM / 2) even when per-label node
                              statistics exist                                    */
-  FW_FLAG_NO_BLOOM = 32   /* membership tests in N(v') search the sorted row
+  FW_FLAG_NO_BLOOM = 32,  /* membership tests in N(v') search the sorted row
                              only, without the per-row Bloom pre-check (the
                              answers, and so the walks, are the same)            */
+  FW_FLAG_NO_GROUPS = 64  /* metapath: sample over the whole row of v (label
+                             test per entry) instead of inside the required
+                             label's segment of the label-grouped view           */
 };
 
 /* Parameters of one walk job.  Initialise with fw_params_default(). */
@@ -160,8 +163,12 @@ void fw_params_default(fw_params* params);
  *   labels   uint8[e] edge labels, or NULL (metapath then unavailable)
  *   ptr_kind FW_PTR_HOST or FW_PTR_DEVICE for all four arrays
  * The graph copies its inputs; the caller may free them once this call
- * returns.  Synchronous on `stream`.  Errors: FW_ERR_ARG, FW_ERR_CSR,
- * FW_ERR_OOM, FW_ERR_CUDA; *out is NULL on error.
+ * returns.  Besides the CSR it keeps 32-byte edge records, node records,
+ * per-row Bloom filters and, with labels all below 8, per-label node
+ * statistics and a label-grouped copy of the rows (36 bytes per entry) for
+ * metapath; if that copy does not fit, metapath samples over whole rows.
+ * Synchronous on `stream`.  Errors: FW_ERR_ARG, FW_ERR_CSR, FW_ERR_OOM,
+ * FW_ERR_CUDA; *out is NULL on error.
  */
 fw_status fw_graph_create(const int32_t* offsets, const int32_t* cols, const float* weights,
                           const uint8_t* labels, int32_t n, int64_t e, int32_t ptr_kind,
@@ -214,8 +221,11 @@ fw_status fw_graph_set_cost_ratio(fw_graph* graph, float ratio);
  *             positions per node, one thread each) and eRVS-style (a
  *             coalesced warp scan of up to 256 neighbours with keys and
  *             jumps); r = ratio of their times per edge
- *   method 1  sweep: time 16-hop sample walks of up to 2^18 walkers for
- *             r in {0.5, 1, 2, ..., 64} and keep the fastest
+ *   method 1  sweep: time 32-hop sample walks of up to 2^20 walkers that
+ *             start at the targets of evenly spaced CSR entries (nodes in
+ *             proportion to their degree, as in a mixed walk) for
+ *             r in {0.125, 0.25, 0.5, 1, 2, ..., 64}; of the ratios within
+ *             3 % of the fastest time, keep the median
  * cache_path (may be NULL): a text file of earlier results keyed by the
  * graph fingerprint, algo, p, q, gamma, flags, schema and method; a hit
  * skips the measurement, a miss appends the new result.  Synchronous on

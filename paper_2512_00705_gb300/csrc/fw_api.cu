@@ -39,6 +39,9 @@ DevGraph dev_graph(const fw_graph* g) {
   d.erec = g->d_erec;
   d.lstat = g->d_lstat;
   d.bloom = g->d_bloom;
+  d.lrec = g->d_lrec;
+  d.gerec = g->d_gerec;
+  d.gh = g->d_gh;
   d.n = g->n;
   d.sym = g->sym;
   return d;
@@ -97,12 +100,53 @@ fw_status make_job(const fw_graph* g, int32_t algo, const fw_params* params, uin
   job->bloom = (g->d_bloom && !(P.flags & FW_FLAG_NO_BLOOM)) ? 1 : 0;
   job->label_stats = (algo == ALGO_METAPATH && g->d_lstat && !(P.flags & FW_FLAG_PAPER_SUM) &&
                       (job->weighted || !g->d_h)) ? 1 : 0;
+  job->label_group = (job->label_stats && g->d_lrec && !(P.flags & FW_FLAG_NO_GROUPS)) ? 1 : 0;
   return FW_OK;
 }
 
 // The per-graph preprocessing (Sec. 4.2 preprocess()): node records with
 // h_MAX / h_SUM and the maximum degree, 32-byte edge records, the weight
 // symmetry check and per-label statistics, all from the current weights.
+// The label-grouped view of the rows (metapath's fast modes sample inside
+// the required label's segment).  Needs the per-label statistics.  If the
+// device has no room for it, metapath walks keep the full-row path.
+static fw_status build_label_groups(fw_graph* g, cudaStream_t st) {
+  const size_t lrec_bytes = sizeof(int4) * kLabelStats * ((size_t)g->n + 1);
+  const size_t gerec_bytes = 2 * sizeof(int4) * (size_t)g->e, gh_bytes = sizeof(float) * (size_t)g->e;
+  if (!g->d_lrec) {
+    cudaError_t a = cudaMalloc(&g->d_lrec, lrec_bytes);
+    if (a == cudaSuccess) a = cudaMalloc(&g->d_gerec, gerec_bytes);
+    if (a == cudaSuccess) a = cudaMalloc(&g->d_gh, gh_bytes);
+    if (a != cudaSuccess) {
+      cudaFree(g->d_lrec);
+      cudaFree(g->d_gerec);
+      cudaFree(g->d_gh);
+      g->d_lrec = nullptr;
+      g->d_gerec = nullptr;
+      g->d_gh = nullptr;
+      cudaGetLastError();  // an allocation failure is not sticky; walks use the full rows
+      return FW_OK;
+    }
+    g->bytes += lrec_bytes + gerec_bytes + gh_bytes;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  cudaError_t le = launch_label_group(g->d_off, g->d_col, g->d_h, g->d_lab, g->d_nrec, g->d_lstat, g->n, g->d_lrec,
+                                      g->d_gerec, g->d_gh, g->num_sms, st);
+  cudaEventRecord(e1, st);
+  cudaError_t se = cudaStreamSynchronize(st);
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (le != cudaSuccess) return cuda_error(le, "label-grouped view");
+  if (se != cudaSuccess) return cuda_error(se, "sync after label-grouped view");
+  g->preprocess_ms += ms;
+  return FW_OK;
+}
+
 fw_status rebuild_derived(fw_graph* g, cudaStream_t st) {
   const int32_t n = g->n;
   const int64_t e = g->e;
@@ -166,6 +210,10 @@ fw_status rebuild_derived(fw_graph* g, cudaStream_t st) {
     g->lstat_bad = true;
   }
   g->preprocess_ms += ms;
+  if (g->d_lstat && e > 0) {
+    fw_status gs = build_label_groups(g, st);
+    if (gs != FW_OK) return gs;
+  }
   return FW_OK;
 }
 
@@ -249,6 +297,9 @@ static void free_graph(fw_graph* g) {
   cudaFree(g->d_lstat);
   cudaFree(g->d_h8);
   cudaFree(g->d_bloom);
+  cudaFree(g->d_lrec);
+  cudaFree(g->d_gerec);
+  cudaFree(g->d_gh);
   cudaFree(g->d_err);
   cudaFree(g->d_cnt);
   cudaFree(g->d_stage_starts);

@@ -10,8 +10,8 @@
 // times per edge.  The
 // kernels run the walk kernel's own device functions, so the ratio reflects
 // this GPU's caches and this graph.
-// Method 1 (an extension): time short sample walks for a ladder of r values
-// and keep the fastest.
+// Method 1 (an extension): time short sample walks from degree-biased starts
+// for a ladder of r values and keep the fastest.
 // Results are cached in a text file keyed by a fingerprint of the graph,
 // the algorithm, p, q and the method.
 #include <cmath>
@@ -91,6 +91,15 @@ __global__ void profile_rvs_kernel(DevGraph g, Job J, int32_t count, int32_t str
     atomicAdd(evals, (unsigned long long)c.d);
     atomicAdd(sink, (unsigned)(k + 1));
   }
+}
+
+// Sweep starts: the targets of w evenly spaced CSR entries.  A node is then
+// picked in proportion to its degree, which is where a walk spends its steps
+// once it has mixed (the stationary law of a first-order walk on a symmetric
+// graph), so the sample walks weigh hubs as a long walk does.
+__global__ void sweep_starts_kernel(const int32_t* __restrict__ col, long long e, int32_t w, int32_t* __restrict__ out) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < w) out[i] = __ldg(col + (long long)((double)i * (double)e / (double)w));
 }
 
 uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
@@ -233,22 +242,27 @@ static fw_status profile_ratio(fw_graph* g, const Job& J, cudaStream_t st, float
 }
 
 static fw_status sweep_ratio(fw_graph* g, int32_t algo, const fw_params* params, cudaStream_t st, float* r_out) {
-  // sample walk: up to 2^18 walkers on evenly spaced nodes, 16 hops, per candidate r
-  const int32_t w = g->n < (1 << 18) ? g->n : (1 << 18);
-  const int32_t stride = g->n / (w > 0 ? w : 1);
-  const int32_t len = 16;
-  std::vector<int32_t> hs(w);
-  for (int32_t i = 0; i < w; ++i) hs[i] = i * stride;
+  // sample walk per candidate r: up to 2^20 walkers from degree-biased starts, 32 hops
+  if (g->e == 0) {
+    *r_out = 4.0f;
+    return FW_OK;
+  }
+  const int32_t w = (int32_t)(g->e < (1ll << 20) ? g->e : (1ll << 20));
+  const int32_t len = 32;
   int32_t *d_starts = nullptr, *d_out = nullptr;
   cudaError_t e = cudaMalloc(&d_starts, sizeof(int32_t) * (size_t)w);
   if (e == cudaSuccess) e = cudaMalloc(&d_out, sizeof(int32_t) * (size_t)w * (len + 1));
-  if (e == cudaSuccess) e = cudaMemcpy(d_starts, hs.data(), sizeof(int32_t) * (size_t)w, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    sweep_starts_kernel<<<(w + 255) / 256, 256, 0, st>>>(g->d_col, (long long)g->e, w, d_starts);
+    g_launches.fetch_add(1);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) {
     cudaFree(d_starts);
     cudaFree(d_out);
     return cuda_error(e, "sweep buffers");
   }
-  const float ladder[] = {0.5f, 1.0f, 2.0f, 4.0f, 8.0f, 16.0f, 32.0f, 64.0f};
+  const float ladder[] = {0.125f, 0.25f, 0.5f, 1.0f, 2.0f, 4.0f, 8.0f, 16.0f, 32.0f, 64.0f};
   fw_params P;
   if (params) P = *params;
   else fw_params_default(&P);
@@ -257,26 +271,35 @@ static fw_status sweep_ratio(fw_graph* g, int32_t algo, const fw_params* params,
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  float best = 1e30f, best_r = 4.0f;
+  constexpr int kLadder = (int)(sizeof(ladder) / sizeof(ladder[0]));
+  float times[kLadder];
+  for (int li = 0; li < kLadder; ++li) times[li] = 1e30f;
   fw_status s = FW_OK;
-  for (float r : ladder) {
-    P.cost_ratio = r;
+  P.cost_ratio = 4.0f;
+  s = fw_walk(g, d_starts, w, len, algo, &P, 7, d_out, st);  // warm-up
+  for (int li = 0; li < kLadder && s == FW_OK; ++li) {
+    P.cost_ratio = ladder[li];
     float t = 1e30f;
-    for (int rep = 0; rep < 3 && s == FW_OK; ++rep) {
+    for (int rep = 0; rep < 2 && s == FW_OK; ++rep) {
       cudaEventRecord(a, st);
       s = fw_walk(g, d_starts, w, len, algo, &P, 7, d_out, st);
       cudaEventRecord(b, st);
       cudaEventSynchronize(b);
       float ms = 0.0f;
       cudaEventElapsedTime(&ms, a, b);
-      if (rep > 0) t = std::fmin(t, ms);
+      t = std::fmin(t, ms);
     }
-    if (s != FW_OK) break;
-    if (t < best) {
-      best = t;
-      best_r = r;
-    }
+    times[li] = t;
   }
+  // Where the timing is flat, sample noise alone would decide; take the
+  // median (the ladder is geometric: the middle in log r) of the ratios
+  // within 3 % of the fastest instead, the smaller one of an even count.
+  float best = 1e30f;
+  for (int li = 0; li < kLadder; ++li) best = std::fmin(best, times[li]);
+  int near[kLadder], count = 0;
+  for (int li = 0; li < kLadder; ++li)
+    if (times[li] <= 1.03f * best) near[count++] = li;
+  const float best_r = count == 0 ? 4.0f : ladder[near[(count - 1) / 2]];
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   cudaFree(d_starts);

@@ -52,6 +52,14 @@ struct DevGraph {
   const float2* __restrict__ lstat; // per node and label l < kLabelStats: {max h, sum h} over the
                                    // edges with that label (nullptr: labels absent or >= kLabelStats)
   const uint32_t* __restrict__ bloom; // blocked Bloom filters of the rows (nullptr: none)
+  // label-grouped view of the rows (metapath; nullptr: not built): each row
+  // reordered stably by label.  lrec per node and label l < kLabelStats:
+  // {max h bits, sum h bits, segment start relative to the row start,
+  // segment length}; gerec: edge records in grouped order with the entry's
+  // original position in the row in place of the label; gh: h in grouped order.
+  const int4* __restrict__ lrec;
+  const int4* __restrict__ gerec;
+  const float* __restrict__ gh;
   int32_t n;
   int32_t sym;                     // 1: h(v,u) = h(u,v) for every edge (checked at creation)
 };
@@ -74,6 +82,7 @@ struct Job {
   int32_t split_return;    // node2vec with 1/p > max(1, 1/q): eRJS proposes the return edge separately
   int32_t split_common;    // node2vec with 1/q < 1: eRJS may use the two-envelope proposal (d(v') < d(v))
   int32_t label_stats;     // metapath: plan with the per-label h_MAX / h_SUM of the required label
+  int32_t label_group;     // metapath: fast modes sample inside the required label's segment
   int32_t bloom;           // 1: membership tests in N(v') consult the row's Bloom filter first
   float inv_p, inv_q;      // FP32 1/p, 1/q
   float wmax1, wmean1;     // max / mean of w when a previous node exists
@@ -416,7 +425,8 @@ struct Accept {
 template <bool COUNT, int ALG = -1>
 __device__ __forceinline__ bool rjs_trials(const DevGraph& g, const Job& J, const StepCtx& c, float B, bool split,
                                            float beta, int32_t pos_ret, float h_ret, int32_t t0, int32_t nt,
-                                           Accept& acc, LaneCounters& lc, bool csplit = false, float beta2 = 0.0f) {
+                                           Accept& acc, LaneCounters& lc, bool csplit = false, float beta2 = 0.0f,
+                                           bool grp = false) {
   const uint32_t d = (uint32_t)c.d;
   const uint8_t want = (FW_ALGO(J) == ALGO_METAPATH) ? J.schema[c.step % J.schema_len] : 0;
   const bool second = (FW_ALGO(J) == ALGO_NODE2VEC) && c.vp >= 0 && J.second_order;
@@ -441,6 +451,25 @@ __device__ __forceinline__ bool rjs_trials(const DevGraph& g, const Job& J, cons
       break;
     }
     int4 a, b;  // {col, h, target row start, target degree}, {target h_MAX, target h_SUM, label, 0}
+    if ((FW_ALGO(J) == ALGO_METAPATH) && grp) {
+      // metapath inside the required label's segment [c.ps, c.pe) of the grouped
+      // arrays: every entry there has w = 1, B = max h over the segment
+      uint32_t kg;
+      if (!lemire_index(x.x, x.y, (uint32_t)(c.pe - c.ps), kg)) continue;
+      ld_record(g.gerec + 2ll * (c.ps + (int32_t)kg), a, b);  // b.z: position in the row
+      if (COUNT) lc.bytes += 32;
+      const float hg = J.weighted ? __int_as_float(a.y) : 1.0f;
+      if (__fmul_rn(u01(x.z), B) < hg) {
+        acc.k = b.z;
+        acc.node = a.x;
+        acc.h = hg;
+        acc.rec = make_int4(a.z, a.w, b.x, b.y);
+        acc.rec_ok = true;
+        found = true;
+        break;
+      }
+      continue;
+    }
     if ((FW_ALGO(J) == ALGO_NODE2VEC) && csplit && ucomp < beta2) {
       // component 2: X uniform over N(v'), accepted iff X in N(v) and U h_MAX < h(v, X)
       uint32_t k2;
@@ -555,7 +584,16 @@ __device__ __forceinline__ void warp_argmax(float& key, int32_t& idx) {
 // draws: (wid, hop, 2, k): x.x = phase-1 key, x.y = key at a crossing,
 // x.z = the lane's next jump threshold.  Returns position k or -1 (all
 // weights zero: dead end).
-template <int T, bool COUNT, int ALG = -1>
+// GRP: scan the label-grouped h (c.s, c.d are a segment of the grouped
+// arrays, every entry of weight h); the result is a grouped position.
+template <int ALG, bool GRP>
+__device__ __forceinline__ float scan_weight(const DevGraph& g, const Job& J, const StepCtx& c, int32_t i,
+                                             uint32_t& probes) {
+  if (GRP) return J.weighted ? __ldg(g.gh + i) : 1.0f;
+  return item_weight<ALG>(g, J, c, i, probes);
+}
+
+template <int T, bool COUNT, int ALG = -1, bool GRP = false>
 __device__ __forceinline__ int32_t rvs_pick(const DevGraph& g, const Job& J, const StepCtx& c, int lane, bool jump,
                                             LaneCounters& lc) {
   uint32_t probes = 0;
@@ -564,7 +602,7 @@ __device__ __forceinline__ int32_t rvs_pick(const DevGraph& g, const Job& J, con
   uint32_t xz = 0;
   int32_t scanned = 0, keys = 0;
   if (lane < c.d) {
-    const float wt = item_weight<ALG>(g, J, c, c.s + lane, probes);
+    const float wt = scan_weight<ALG, GRP>(g, J, c, c.s + lane, probes);
     const uint4 x = philox(make_uint4(c.wid, (uint32_t)c.step, 2u, (uint32_t)lane), J.key0, J.key1);
     xz = x.z;
     ++scanned;
@@ -580,7 +618,7 @@ __device__ __forceinline__ int32_t rvs_pick(const DevGraph& g, const Job& J, con
     // remaining weight before the next crossing; K_ref = -inf: first positive item crosses
     float rem = (ref == -CUDART_INF_F) ? 0.0f : ((ref < 0.0f) ? logf(u01_open(xz)) / ref : CUDART_INF_F);
     for (int32_t k = lane + T; k < c.d; k += T) {
-      const float wt = item_weight<ALG>(g, J, c, c.s + k, probes);
+      const float wt = scan_weight<ALG, GRP>(g, J, c, c.s + k, probes);
       ++scanned;
       if (!(wt > 0.0f)) continue;
       if (!jump) {
@@ -613,7 +651,10 @@ __device__ __forceinline__ int32_t rvs_pick(const DevGraph& g, const Job& J, con
     lc.rvs_items += scanned;
     lc.rvs_keys += keys;
     lc.probes += probes;
-    const int per = (FW_ALGO(J) == ALGO_NODE2VEC) ? (J.weighted ? 8 : 4) : (FW_ALGO(J) == ALGO_METAPATH ? (J.weighted ? 5 : 1) : (J.weighted ? 4 : 0));
+    const int per = GRP ? (J.weighted ? 4 : 0)
+                        : ((FW_ALGO(J) == ALGO_NODE2VEC) ? (J.weighted ? 8 : 4)
+                                                         : (FW_ALGO(J) == ALGO_METAPATH ? (J.weighted ? 5 : 1)
+                                                                                        : (J.weighted ? 4 : 0)));
     lc.bytes += (unsigned long long)scanned * per + 32ull * probes;
   }
   return (bestK == -CUDART_INF_F) ? -1 : best;

@@ -31,6 +31,9 @@ struct fw_graph {
   float2* d_lstat = nullptr;  // per-label node statistics (nullptr: not available)
   bool lstat_bad = false;     // a label >= kLabelStats occurs
   uint32_t* d_bloom = nullptr; // blocked Bloom filters of the rows (membership pre-check)
+  int4* d_lrec = nullptr;      // label-grouped view for metapath (nullptr: not built)
+  int4* d_gerec = nullptr;
+  float* d_gh = nullptr;
   uint8_t* d_h8 = nullptr;    // 8-bit weight codes after fw_graph_quantize_weights
   float hscale = 0.0f;
   int32_t sym = 0;
@@ -80,6 +83,9 @@ cudaError_t launch_edge_records(const int32_t* col, const float* h, const uint8_
                                 int4* erec, int num_sms, cudaStream_t stream);
 cudaError_t launch_label_stats(const int32_t* off, const float* h, const uint8_t* lab, int32_t n, float2* out,
                                unsigned* bad, int num_sms, cudaStream_t stream);
+cudaError_t launch_label_group(const int32_t* off, const int32_t* col, const float* h, const uint8_t* lab,
+                               const int4* nrec, const float2* lstat, int32_t n, int4* lrec, int4* gerec, float* gh,
+                               int num_sms, cudaStream_t stream);
 cudaError_t launch_symmetry(const int32_t* off, const int32_t* col, const float* h, int32_t n, unsigned* flag,
                             int num_sms, cudaStream_t stream);
 cudaError_t launch_quantize(float* h, long long e, uint8_t* codes, float* scale_out, unsigned* maxbits, int num_sms,

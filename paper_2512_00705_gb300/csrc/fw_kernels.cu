@@ -123,6 +123,9 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
   // node2vec with 1/q < 1 and d(v') < d(v): two envelopes; beta2 = (E3 + E2) / E
   bool csplit = false;
   float beta2 = 0.0f;
+  // metapath in the label-grouped view: c.ps / c.pe then hold the required
+  // label's segment of the grouped arrays (metapath has no use for the row of v')
+  bool grp = false;
   int32_t pos_ret = -1;
   // from the accepted trial: the next node's record, and h of the edge taken (-1: unknown)
   int4 nxt = make_int4(0, 0, 0, 0);
@@ -206,6 +209,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
       pick = -2;
       split = false;
       csplit = false;
+      grp = false;
       beta = 0.0f;
       if (c.d == 0) {
         pick = -1;
@@ -225,7 +229,23 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
             hs = (float)c.d;
           }
           int32_t choice;
-          if (FW_ALGO(J) == ALGO_METAPATH && J.label_stats) {
+          if (FW_ALGO(J) == ALGO_METAPATH && J.label_group) {
+            // per-label record of v: exact bound and sum over the required label,
+            // and where its entries sit in the label-grouped view; none -> dead end
+            const uint8_t want = J.schema[c.step % J.schema_len];
+            int4 lr = make_int4(0, 0, 0, 0);
+            if (want < kLabelStats) {
+              lr = __ldg(g.lrec + (long long)c.v * kLabelStats + want);
+              if (COUNT) lc.bytes += 16;
+            }
+            B = __int_as_float(lr.x);
+            S = __int_as_float(lr.y);
+            choice = (__fmul_rn(J.ratio, B) < S) ? MODE_RJS : MODE_RVS;
+            if (!(S > 0.0f)) pick = -1;
+            grp = true;
+            c.ps = c.s + lr.z;
+            c.pe = c.ps + lr.w;
+          } else if (FW_ALGO(J) == ALGO_METAPATH && J.label_stats) {
             // metapath with per-label statistics: exact bound and exact sum over
             // the edges whose label the step requires; none -> dead end now
             const uint8_t want = J.schema[c.step % J.schema_len];
@@ -257,7 +277,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
           } else if (m == MODE_DEGREE) {
             m = (c.d < kDegreeRuleThreshold) ? MODE_RVS : MODE_RJS;
           }
-          plan = (m == MODE_RJS) ? PLAN_RJS : ((c.d <= kThreadRvsMaxDeg) ? PLAN_RVS_T : PLAN_RVS_W);
+          plan = (m == MODE_RJS) ? PLAN_RJS : (((grp ? c.pe - c.ps : c.d) <= kThreadRvsMaxDeg) ? PLAN_RVS_T : PLAN_RVS_W);
           if (split) {  // second-order PageRank: S_C and the probability of the common-neighbour part
             split = plan == PLAN_RJS;
             if (split) {
@@ -314,7 +334,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
     // ------------------------------------------------------------ eRJS trials
     if (widx >= 0 && plan == PLAN_RJS && pick == -2) {
       Accept acc;
-      if (rjs_trials<COUNT, ALG>(g, J, c, B, split, beta, pos_ret, h_ret, trials, kRjsBatch, acc, lc, csplit, beta2)) {
+      if (rjs_trials<COUNT, ALG>(g, J, c, B, split, beta, pos_ret, h_ret, trials, kRjsBatch, acc, lc, csplit, beta2,
+                                 grp)) {
         pick = acc.k;
         node = acc.node;
         h_in = acc.h;
@@ -325,17 +346,35 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
         trials += kRjsBatch;
         // trial budget: the cap, or (default) as many trials as the eRVS scan
         // they stand in for would cost under the cost model, d / r
-        const int32_t cap = J.fixed_cap ? J.rjs_cap : max(J.rjs_cap, (int32_t)ceilf((float)c.d / J.ratio));
+        const int32_t dd = grp ? c.pe - c.ps : c.d;  // entries the eRVS hand-off would scan
+        const int32_t cap = J.fixed_cap ? J.rjs_cap : max(J.rjs_cap, (int32_t)ceilf((float)dd / J.ratio));
         if (trials >= cap) {
-          plan = (c.d <= kThreadRvsMaxDeg) ? PLAN_RVS_T : PLAN_RVS_W;
+          plan = (dd <= kThreadRvsMaxDeg) ? PLAN_RVS_T : PLAN_RVS_W;
           if (COUNT) lc.handoffs++;
         }
       }
     }
     // ------------------------------------------------------------ single-lane eRVS / exact
     if (widx >= 0 && pick == -2 && plan == PLAN_RVS_T) {
-      pick = rvs_pick<1, COUNT, ALG>(g, J, c, 0, !(J.flags & FW_FLAG_RVS_NOJUMP), lc);
-      if (pick >= 0) node = __ldg(g.col + c.s + pick);
+      if ((FW_ALGO(J) == ALGO_METAPATH) && grp) {
+        StepCtx cg = c;
+        cg.s = c.ps;
+        cg.d = c.pe - c.ps;
+        const int32_t j = rvs_pick<1, COUNT, ALG, true>(g, J, cg, 0, !(J.flags & FW_FLAG_RVS_NOJUMP), lc);
+        pick = -1;
+        if (j >= 0) {  // the grouped record gives the node, its position in the row and its node record
+          int4 a, b;
+          ld_record(g.gerec + 2ll * (cg.s + j), a, b);
+          if (COUNT) lc.bytes += 32;
+          pick = b.z;
+          node = a.x;
+          nxt = make_int4(a.z, a.w, b.x, b.y);
+          nxt_ok = true;
+        }
+      } else {
+        pick = rvs_pick<1, COUNT, ALG>(g, J, c, 0, !(J.flags & FW_FLAG_RVS_NOJUMP), lc);
+        if (pick >= 0) node = __ldg(g.col + c.s + pick);
+      }
       h_in = -1.0f;
       if (COUNT) lc.rvs_steps++;
     }
@@ -366,15 +405,35 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
       }
       const int jb = __shfl_sync(kFull, job, src);
       const int pl = __shfl_sync(kFull, plan, src);
+      bool wg = false;
+      if (ALG < 0 || ALG == ALGO_METAPATH) wg = __shfl_sync(kFull, (int)grp, src) != 0;
       const Job& JW = sj[jb];
       int32_t k;
       if (pl == PLAN_EXACT_W) {
         const float u = u01(philox(make_uint4(w.wid, (uint32_t)w.step, 0u, 0u), JW.key0, JW.key1).x);
         k = exact_pick<32, COUNT, ALG>(g, JW, w, lane, u, lc);
+      } else if ((ALG < 0 || ALG == ALGO_METAPATH) && wg) {
+        StepCtx cg = w;
+        cg.s = w.ps;
+        cg.d = w.pe - w.ps;
+        k = rvs_pick<32, COUNT, ALG, true>(g, JW, cg, lane, !(JW.flags & FW_FLAG_RVS_NOJUMP), lc);
       } else {
         k = rvs_pick<32, COUNT, ALG>(g, JW, w, lane, !(JW.flags & FW_FLAG_RVS_NOJUMP), lc);
       }
-      if (lane == src) {
+      if (lane == src && (ALG < 0 || ALG == ALGO_METAPATH) && wg) {
+        pick = -1;
+        if (k >= 0) {  // grouped position -> node, position in the row, node record
+          int4 a, b;
+          ld_record(g.gerec + 2ll * (w.ps + k), a, b);
+          if (COUNT) lc.bytes += 32;
+          pick = b.z;
+          node = a.x;
+          nxt = make_int4(a.z, a.w, b.x, b.y);
+          nxt_ok = true;
+        }
+        h_in = -1.0f;
+        if (COUNT) lc.rvs_steps++;
+      } else if (lane == src) {
         pick = k;
         if (k >= 0) node = __ldg(g.col + w.s + k);
         h_in = -1.0f;
@@ -594,6 +653,75 @@ __global__ void label_stats_kernel(const int32_t* __restrict__ off, const float*
   }
 }
 
+// Label-grouped view (metapath): one warp per node reorders its row stably
+// by label (labels < kLabelStats; counting pass, exclusive prefix over the
+// labels, ballot-ranked scatter), writes grouped edge records whose fourth
+// word of the second half is the entry's position in the row, the grouped h,
+// and per label {max h, sum h (from the label statistics), segment start,
+// segment length}.
+__global__ void label_group_kernel(const int32_t* __restrict__ off, const int32_t* __restrict__ col,
+                                   const float* __restrict__ h, const uint8_t* __restrict__ lab,
+                                   const int4* __restrict__ nrec, const float2* __restrict__ lstat, int32_t n,
+                                   int4* __restrict__ lrec, int4* __restrict__ gerec, float* __restrict__ gh) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long v = warp; v < n; v += nwarps) {
+    const int32_t s = off[v], d = off[v + 1] - s;
+    int cnt = 0;  // lane l < kLabelStats: entries with label l
+    for (int32_t b = 0; b < d; b += 32) {
+      const int l = (b + lane < d) ? (int)lab[s + b + lane] : 255;
+#pragma unroll
+      for (int k = 0; k < kLabelStats; ++k) {
+        const unsigned m = __ballot_sync(kFull, l == k);
+        if (lane == k) cnt += __popc(m);
+      }
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < kLabelStats; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    int run = incl - cnt;  // lane l: start of label l's segment
+    if (lane < kLabelStats) {
+      const float2 ls = lstat[v * kLabelStats + lane];
+      lrec[v * kLabelStats + lane] = make_int4(__float_as_int(ls.x), __float_as_int(ls.y), run, cnt);
+    }
+    for (int32_t b = 0; b < d; b += 32) {
+      const bool valid = b + lane < d;
+      const long long i = (long long)s + b + lane;
+      const int l = valid ? (int)lab[i] : 255;
+      int dst = 0;
+#pragma unroll
+      for (int k = 0; k < kLabelStats; ++k) {
+        const unsigned m = __ballot_sync(kFull, l == k);
+        const int base = __shfl_sync(kFull, run, k);
+        if (l == k) dst = base + __popc(m & lt);
+        if (lane == k) run += __popc(m);
+      }
+      if (valid) {
+        const int32_t u = col[i];
+        const int4 nr = nrec[u];
+        const float hv = h ? h[i] : 1.0f;
+        const long long o = (long long)s + dst;
+        gerec[2 * o] = make_int4(u, __float_as_int(hv), nr.x, nr.y);
+        gerec[2 * o + 1] = make_int4(nr.z, nr.w, b + lane, 0);
+        gh[o] = hv;
+      }
+    }
+  }
+}
+
+cudaError_t launch_label_group(const int32_t* off, const int32_t* col, const float* h, const uint8_t* lab,
+                               const int4* nrec, const float2* lstat, int32_t n, int4* lrec, int4* gerec, float* gh,
+                               int num_sms, cudaStream_t stream) {
+  label_group_kernel<<<num_sms * 8, 256, 0, stream>>>(off, col, h, lab, nrec, lstat, n, lrec, gerec, gh);
+  g_launches.fetch_add(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_label_stats(const int32_t* off, const float* h, const uint8_t* lab, int32_t n, float2* out,
                                unsigned* bad, int num_sms, cudaStream_t stream) {
   if (n == 0) return cudaSuccess;
@@ -702,6 +830,7 @@ cudaError_t prime_preprocess_kernels() {
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, symmetry_kernel);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, bloom_kernel);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, label_stats_kernel);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, label_group_kernel);
   return e;
 }
 

@@ -198,6 +198,27 @@ def test_fast_mode_distributions(small, mode, flags, algo, p, q, schema):
         assert tv < 2e-3, (v, vp, step, tv)
 
 
+@pytest.mark.parametrize("mode,flags", [("rjs", 0), ("rvs", 0), ("rvs", fw.FLAG_RVS_NOJUMP), ("auto", 0),
+                                        ("rjs", fw.FLAG_NO_GROUPS), ("rvs", fw.FLAG_NO_GROUPS)])
+def test_metapath_every_label_distributions(small, mode, flags):
+    """Metapath inside each label's segment of the label-grouped view (and
+    over whole rows with FW_FLAG_NO_GROUPS): for every required label 0..4 at
+    the states of _states, the draws follow the oracle's probabilities."""
+    g, G = small
+    ndraws = 2_000_000
+    for (v, vp, step) in _states(g)[::2]:
+        for lab in range(5):
+            probs = oracle.transition_probs(g, v, -1, step, "metapath", schema=[lab])
+            counts = G.sample_hist(v, -1, step, "metapath", ndraws, schema=[lab], mode=mode, flags=flags,
+                                   seed=77 + v + lab).cpu().numpy()
+            if probs.sum() == 0:
+                assert counts.sum() == 0
+                continue
+            assert counts.sum() == ndraws
+            assert chisq_pvalue(counts, probs) > 1e-4, (v, lab)
+            assert tv_distance(counts, probs) < 3e-3, (v, lab)
+
+
 def test_worked_example_distribution():
     """Fig. 2: weights {3,2,4,1} -> {0.3,0.2,0.4,0.1} for every mode."""
     g = synth.from_edges(5, [(0, 1), (0, 2), (0, 3), (0, 4)], h=[3.0, 2.0, 4.0, 1.0])
@@ -304,7 +325,7 @@ WALK_CASES = [("node2vec", 0.25, 4.0, None), ("node2vec", 2.0, 0.5, None), ("nod
 
 @pytest.mark.parametrize("graph", ["sparse", "sparse-asym", "dense"])
 @pytest.mark.parametrize("mode,flags", [("rjs", 0), ("rjs", fw.FLAG_PLAIN_RJS), ("rvs", 0), ("auto", 0),
-                                        ("auto", fw.FLAG_PAPER_SUM)])
+                                        ("auto", fw.FLAG_PAPER_SUM), ("auto", fw.FLAG_NO_GROUPS)])
 @pytest.mark.parametrize("algo,p,q,schema", WALK_CASES)
 def test_fast_walk_path_distribution(graph, mode, flags, algo, p, q, schema):
     """GPU walks from one start, many walker ids: frequencies of whole paths

@@ -55,7 +55,7 @@ def test_autotune_profiling_installs_a_ratio(small, algo, p, q, schema, tmp_path
 def test_autotune_sweep_picks_from_the_ladder(small):
     g, G = small
     r = G.autotune("node2vec", p=2.0, q=0.5, method=1)
-    assert r in [0.5, 1, 2, 4, 8, 16, 32, 64]
+    assert r in [0.125, 0.25, 0.5, 1, 2, 4, 8, 16, 32, 64]
     G.set_cost_ratio(4.0)
 
 
