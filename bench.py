@@ -329,14 +329,25 @@ def run_metapath(args):
             e1.record()
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
-        res[L] = (_hops(out), statistics.median(ms))
-    hops = sum(h for h, _ in res.values())
-    tot = sum(t for _, t in res.values())
+        G.reset_counters()  # counted run (untimed): sampler shares and algorithmic bytes
+        G.walk(starts, L, "metapath", schema=[0, 1, 2, 3, 4], out=out, seed=SEED, cost_ratio=r_meta,
+               flags=fw.FLAG_COUNTERS)
+        c = G.counters()
+        res[L] = (_hops(out), statistics.median(ms), c)
+    hops = sum(h for h, _, _ in res.values())
+    tot = sum(t for _, t, _ in res.values())
+    per_len = {}
+    for L, (h, t, c) in res.items():
+        per_len[str(L)] = {"hops": h, "ms": t, "rjs_share": c["rjs_steps"] / max(1, c["hops"]),
+                           "rjs_trials_per_rjs_step": c["rjs_trials"] / max(1, c["rjs_steps"]),
+                           "rvs_items_per_rvs_step": c["rvs_items"] / max(1, c["rvs_steps"]),
+                           "dead_ends": c["dead_ends"], "algorithmic_bytes_per_hop": c["bytes"] / max(1, c["hops"]),
+                           "algorithmic_GBps": c["bytes"] / (t / 1e3) / 1e9}
     _line("walker-steps/sec (metapath)", hops / (tot / 1e3), "walker-steps/s", args, {
         "ms_per_step": tot,
         "config": {"workload": "metapath 0-1-2-3-4 on R-MAT s23 ef16, h~lognormal(0,1), labels U{0..4}, "
                                "2M random starts (seed 43), L=5 and L=40", "nodes": g.n, "edges": g.e, "cost_ratio": r_meta,
-                   "per_length": {str(L): {"hops": h, "ms": t} for L, (h, t) in res.items()}}})
+                   "per_length": per_len}})
     G.close()
 
 

@@ -344,22 +344,25 @@ typedef struct {
 } fw_job;
 
 /*
- * Run njobs walk jobs in one persistent launch per 64 jobs: the walkers of
- * all jobs form one query queue (Sec. 5.3), so jobs of very different sizes,
- * lengths and algorithms share the GPU instead of running one after
- * another.  Every job's rows are identical to those of fw_walk with the same
- * arguments (draws and sampler choices depend only on the walker's own job).
- * Asynchronous on `stream`; errors as fw_walk (a bad job is named in the
- * message).
+ * Run njobs walk jobs in batches of up to 64: within a batch the walkers of
+ * all jobs of one algorithm form one query queue (Sec. 5.3) walked by one
+ * persistent launch of the kernel compiled for that algorithm, so jobs of
+ * very different sizes and lengths share the GPU instead of running one
+ * after another.  The per-algorithm launches of a batch follow each other
+ * on `stream` (a batch plan runs them side by side).  Every job's rows are
+ * identical to those of fw_walk with the same arguments (draws and sampler
+ * choices depend only on the walker's own job).  Asynchronous on `stream`;
+ * errors as fw_walk (a bad job is named in the message).
  */
 fw_status fw_walk_batch(const fw_graph* graph, const fw_job* jobs, int32_t njobs, void* stream);
 
 /*
  * A batch captured once into a CUDA graph (queue-counter resets and walk
- * launches) and replayed by fw_batch_plan_launch on any stream.  The jobs'
- * buffers and parameters are fixed at creation; their contents may change
- * between replays.  The plan owns its queue counters; destroy it after its
- * last replay has finished.
+ * launches; the per-algorithm launches of each 64-job chunk are parallel
+ * branches of the graph) and replayed by fw_batch_plan_launch on any
+ * stream as one graph launch.  The jobs' buffers and parameters are fixed
+ * at creation; their contents may change between replays.  The plan owns
+ * its queue counters; destroy it after its last replay has finished.
  */
 typedef struct fw_batch_plan fw_batch_plan;
 fw_status fw_batch_plan_create(const fw_graph* graph, const fw_job* jobs, int32_t njobs,

@@ -1,13 +1,14 @@
 // fw_batch.cu -- many walk jobs in one persistent launch, and a CUDA-graph
 // plan that replays such a launch.
 //
-// The walk kernel already treats its input as a table of jobs whose walkers
-// form one index space; a batch is that table with up to 64 jobs of any
-// sizes, lengths, algorithms and parameters.  Lanes take walkers from one
-// queue, so small jobs do not leave the GPU idle and long jobs do not hold
-// a launch of their own.  Each job's rows equal those of a separate fw_walk
-// call with the same arguments: every random draw and every sampler choice
-// depends only on the walker's own job.
+// A batch is a table of up to 64 jobs of any sizes, lengths, algorithms and
+// parameters walked by one persistent launch of the batch kernel
+// (fw_walk_mixed.cu): the jobs of one algorithm form one walker queue, and
+// warps run algorithm-specialised walk loops queue after queue, so small
+// jobs do not leave the GPU idle and long jobs do not hold a launch of their
+// own.  Each job's rows equal those of a separate fw_walk call with the same
+// arguments: every random draw and every sampler choice depends only on the
+// walker's own job.
 #include <vector>
 
 #include "fw_internal.h"
@@ -56,10 +57,10 @@ extern "C" fw_status fw_walk_batch(const fw_graph* g, const fw_job* jobs, int32_
     fw_status s = build_table(g, jobs + first, m, &tab, &total, &count);
     if (s != FW_OK) return s;
     if (total == 0) continue;
-    unsigned long long* q = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&q), sizeof(unsigned long long), st);
+    unsigned long long* q = nullptr;  // one walker queue per algorithm
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&q), sizeof(unsigned long long) * kQueueCounters, st);
     if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync(queue counter)");
-    e = cudaMemsetAsync(q, 0, sizeof(unsigned long long), st);
+    e = cudaMemsetAsync(q, 0, sizeof(unsigned long long) * kQueueCounters, st);
     if (e == cudaSuccess) e = launch_walk(g, tab.data(), (int)tab.size(), total, count, q, st);
     cudaError_t e2 = cudaFreeAsync(q, st);
     if (e != cudaSuccess) return cuda_error(e, "batch launch");
@@ -71,7 +72,7 @@ extern "C" fw_status fw_walk_batch(const fw_graph* g, const fw_job* jobs, int32_
 struct fw_batch_plan {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  unsigned long long* qctr = nullptr;  // one queue counter per chunk of 64 jobs
+  unsigned long long* qctr = nullptr;  // kQueueCounters queue counters per chunk of 64 jobs
   int kernels = 0;                     // walk kernels per replay
 };
 
@@ -102,7 +103,7 @@ extern "C" fw_status fw_batch_plan_create(const fw_graph* g, const fw_job* jobs,
   }
   fw_batch_plan* p = new (std::nothrow) fw_batch_plan();
   if (!p) return set_error(FW_ERR_OOM, "host allocation");
-  cudaError_t e = cudaMalloc(&p->qctr, sizeof(unsigned long long) * (chunks > 0 ? chunks : 1));
+  cudaError_t e = cudaMalloc(&p->qctr, sizeof(unsigned long long) * kQueueCounters * (chunks > 0 ? chunks : 1));
   if (e != cudaSuccess) {
     free_plan(p);
     return cuda_error(e, "cudaMalloc(plan counters)");
@@ -112,28 +113,38 @@ extern "C" fw_status fw_batch_plan_create(const fw_graph* g, const fw_job* jobs,
     free_plan(p);
     return cuda_error(e, "occupancy query");
   }
-  // capture on a private stream, then instantiate
-  cudaStream_t cap;
+  // capture on a private stream (the per-algorithm launches of a chunk fork
+  // onto helper streams and join back, so they overlap), then instantiate
+  cudaStream_t cap = nullptr, side[kAlgos - 1] = {};
+  cudaEvent_t ev[kAlgos] = {};
   e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
-  if (e != cudaSuccess) {
-    free_plan(p);
-    return cuda_error(e, "cudaStreamCreate");
-  }
-  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  for (int i = 0; i < kAlgos - 1 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking);
+  for (int i = 0; i < kAlgos && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  const bool capturing = e == cudaSuccess;
   for (int32_t c = 0; c < chunks && e == cudaSuccess; ++c) {
     if (totals[c] == 0) continue;
-    e = cudaMemsetAsync(p->qctr + c, 0, sizeof(unsigned long long), cap);
-    if (e == cudaSuccess)
-      e = launch_walk(g, tabs[c].data(), (int)tabs[c].size(), totals[c], counts[c], p->qctr + c, cap);
+    unsigned long long* q = p->qctr + (size_t)c * kQueueCounters;
+    e = cudaMemsetAsync(q, 0, sizeof(unsigned long long) * kQueueCounters, cap);
+    const unsigned long long before = g_launches.load();
     if (e == cudaSuccess) {
-      ++p->kernels;
-      g_launches.fetch_sub(1);  // counted when the plan is replayed
+      e = tabs[c].size() == 1 ? launch_walk(g, tabs[c].data(), 1, totals[c], counts[c], q, cap)
+                              : launch_walk_mixed(g, tabs[c].data(), (int)tabs[c].size(), counts[c], q, cap, side, ev);
     }
+    const unsigned long long launched = g_launches.load() - before;
+    p->kernels += (int)launched;
+    g_launches.fetch_sub(launched);  // counted when the plan is replayed
   }
-  cudaError_t e2 = cudaStreamEndCapture(cap, &p->graph);
-  if (e == cudaSuccess) e = e2;
+  if (capturing) {
+    cudaError_t e2 = cudaStreamEndCapture(cap, &p->graph);
+    if (e == cudaSuccess) e = e2;
+  }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
-  cudaStreamDestroy(cap);
+  for (cudaEvent_t x : ev)
+    if (x) cudaEventDestroy(x);
+  for (cudaStream_t x : side)
+    if (x) cudaStreamDestroy(x);
+  if (cap) cudaStreamDestroy(cap);
   if (e != cudaSuccess) {
     free_plan(p);
     return cuda_error(e, "capture of the batch launch");

@@ -31,6 +31,7 @@ constexpr int kThreadRvsMaxDeg = 8;  // eRVS steps with d <= this run on one lan
 constexpr int kLabelStats = 8;       // per-label node statistics for labels 0..7
 
 enum : int32_t { ALGO_WEIGHTED = 0, ALGO_NODE2VEC = 1, ALGO_METAPATH = 2, ALGO_PAGERANK2 = 3 };
+constexpr int kAlgos = 4;  // a multi-job launch keeps one walker queue per algorithm
 enum : int32_t { MODE_AUTO = 0, MODE_RJS = 1, MODE_RVS = 2, MODE_EXACT = 3, MODE_RANDOM = 4, MODE_DEGREE = 5 };
 constexpr int32_t kDegreeRuleThreshold = 1000;  // Sec. 5.4 degree-based selection
 enum : int32_t { JOB_WALK = 0, JOB_HIST = 1 };

@@ -69,13 +69,23 @@ fw_status graph_fingerprint(const fw_graph* g, cudaStream_t st, unsigned long lo
 
 fw_status make_job(const fw_graph* g, int32_t algo, const fw_params* params, uint64_t seed, Job* job);
 
-// Launch the unified walk kernel over `njobs` jobs (total walkers `total`).
-// `qctr` is a zeroed device counter the launch may use as its walker queue.
+// Launch the walk over `njobs` jobs (total walkers `total`; njobs <= kMaxJobs).
+// `qctr` points to zeroed device counters the launch uses as walker queues:
+// one for a single job, kAlgos (one per algorithm) for several.  Several
+// jobs give one kernel launch per algorithm present.
 cudaError_t launch_walk(const fw_graph* g, const Job* jobs, int njobs, long long total, bool count,
                         unsigned long long* qctr, cudaStream_t stream);
+// Several jobs of any algorithms: one launch per algorithm present, on
+// `stream` one after another, or (side: kAlgos - 1 helper streams, ev:
+// kAlgos events) side by side, joined back into `stream`.  qctr: kAlgos
+// zeroed counters.
+cudaError_t launch_walk_mixed(const fw_graph* g, const Job* jobs, int njobs, bool count, unsigned long long* qctr,
+                              cudaStream_t stream, const cudaStream_t* side = nullptr, cudaEvent_t* ev = nullptr);
+constexpr int kQueueCounters = fw::kAlgos;  // counters a multi-job launch needs
 
 // Cache the walk kernels' occupancy (call outside any stream capture).
 cudaError_t prime_walk_occupancy();
+cudaError_t prime_walk_mixed_occupancy();
 
 cudaError_t launch_node_stats(const int32_t* off, const float* h, int32_t n, float* hmax, float* hsum, int4* nrec,
                               int* maxdeg, int num_sms, cudaStream_t stream);

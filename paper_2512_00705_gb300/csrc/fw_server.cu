@@ -170,7 +170,7 @@ void launch_wave(fw_server* s, Wave& w) {
   }
   s->admitted.clear();
   if (w.reqs.empty()) return;
-  if (e == cudaSuccess) e = cudaMemsetAsync(w.qctr, 0, sizeof(unsigned long long), w.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.qctr, 0, sizeof(unsigned long long) * kQueueCounters, w.stream);
   if (e == cudaSuccess && total > 0) e = launch_walk(s->g, tab.data(), (int)tab.size(), total, false, w.qctr, w.stream);
   for (Request* r : w.reqs) {
     if (e != cudaSuccess) break;

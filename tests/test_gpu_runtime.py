@@ -90,7 +90,7 @@ def _mixed_jobs(g, count, seed, max_walkers=3000):
     rng = np.random.default_rng(seed)
     specs = []
     for i in range(count):
-        algo = ["node2vec", "metapath", "weighted"][i % 3]
+        algo = ["node2vec", "metapath", "weighted", "pagerank2"][i % 4]
         w = int(rng.integers(1, max_walkers))
         spec = dict(starts=synth.random_starts(g.n, w, seed=seed * 100 + i), length=int(rng.integers(0, 30)),
                     algo=algo, mode=["auto", "rjs", "rvs", "exact"][int(rng.integers(0, 4))],
@@ -139,7 +139,8 @@ def test_batch_plan_replays(small):
     n0 = fw.fw_launch_count()
     plan.launch()
     torch.cuda.synchronize()
-    assert fw.fw_launch_count() - n0 == 1
+    # one graph launch holding one walk kernel per algorithm present
+    assert fw.fw_launch_count() - n0 == len({sp["algo"] for sp in specs})
     first = [o.clone() for o in outs]
     for sp, st, o in zip(specs, sts, first):
         assert torch.equal(o, G.walk(st, sp["length"], sp["algo"], **_kw(sp)))
