@@ -42,7 +42,9 @@ def _inputs_digest() -> str:
         h.update(os.path.basename(f).encode())
         with open(f, "rb") as fh:
             h.update(fh.read())
-    h.update(" ".join(ARCH + NVCC_FLAGS).encode())
+    # the flags name the include directory by absolute path: hash them with the
+    # repository root factored out, so a checkout elsewhere has the same digest
+    h.update(" ".join(ARCH + NVCC_FLAGS).replace(ROOT, "<root>").encode())
     return h.hexdigest()
 
 
