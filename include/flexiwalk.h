@@ -82,11 +82,11 @@ enum {
   FW_FLAG_COUNTERS = 2,   /* accumulate per-walk counters (slower build path)    */
   FW_FLAG_UNWEIGHTED = 4, /* ignore h: every property weight is 1 (Sec. 5.1)     */
   FW_FLAG_PLAIN_RJS = 8,  /* eRJS exactly as Sec. 3.3 (uniform proposal, bound
-                             max(w) * h_MAX) even when node2vec's return edge
-                             could be proposed separately, when node2vec with
-                             q > 1 could propose from two envelopes, or when
-                             second-order PageRank could split off the common
-                             neighbours                                          */
+                             max(w) * h_MAX) instead of the refined envelopes:
+                             two weight classes (h above / below h_MAX / 2),
+                             node2vec's return edge proposed separately, two
+                             envelopes for node2vec with q > 1, the common
+                             neighbours of second-order PageRank split off       */
   FW_FLAG_PAPER_SUM = 16, /* metapath: plan with the Sec. 4.2 rule (B = h_MAX,
                              sum-hat = h_SUM / 2) even when per-label node
                              statistics exist                                    */
@@ -163,10 +163,12 @@ void fw_params_default(fw_params* params);
  *   labels   uint8[e] edge labels, or NULL (metapath then unavailable)
  *   ptr_kind FW_PTR_HOST or FW_PTR_DEVICE for all four arrays
  * The graph copies its inputs; the caller may free them once this call
- * returns.  Besides the CSR it keeps 32-byte edge records, node records,
- * per-row Bloom filters and, with labels all below 8, per-label node
- * statistics and a label-grouped copy of the rows (36 bytes per entry) for
- * metapath; if that copy does not fit, metapath samples over whole rows.
+ * returns.  Besides the CSR it keeps 32-byte edge records (twice with
+ * weights: in CSR order and with each row partitioned by weight class),
+ * 32-byte node records, per-row Bloom filters and, with labels all below
+ * 8, per-label node statistics and a label-grouped copy of the rows (36
+ * bytes per entry) for metapath; if that copy does not fit, metapath
+ * samples over whole rows.
  * Synchronous on `stream`.  Errors: FW_ERR_ARG, FW_ERR_CSR, FW_ERR_OOM,
  * FW_ERR_CUDA; *out is NULL on error.
  */

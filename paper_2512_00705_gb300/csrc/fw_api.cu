@@ -37,6 +37,7 @@ DevGraph dev_graph(const fw_graph* g) {
   d.hsum = g->d_hsum;
   d.nrec = g->d_nrec;
   d.erec = g->d_erec;
+  d.cerec = g->d_cerec;
   d.lstat = g->d_lstat;
   d.bloom = g->d_bloom;
   d.lrec = g->d_lrec;
@@ -101,6 +102,7 @@ fw_status make_job(const fw_graph* g, int32_t algo, const fw_params* params, uin
   job->label_stats = (algo == ALGO_METAPATH && g->d_lstat && !(P.flags & FW_FLAG_PAPER_SUM) &&
                       (job->weighted || !g->d_h)) ? 1 : 0;
   job->label_group = (job->label_stats && g->d_lrec && !(P.flags & FW_FLAG_NO_GROUPS)) ? 1 : 0;
+  job->classes = (job->weighted && g->d_cerec && !(P.flags & FW_FLAG_PLAIN_RJS)) ? 1 : 0;
   return FW_OK;
 }
 
@@ -184,6 +186,8 @@ fw_status rebuild_derived(fw_graph* g, cudaStream_t st) {
   if (le == cudaSuccess)
     le = launch_node_stats(g->d_off, g->d_h, n, g->d_hmax, g->d_hsum, g->d_nrec, d_maxdeg, g->num_sms, st);
   if (le == cudaSuccess) le = launch_edge_records(g->d_col, g->d_h, g->d_lab, g->d_nrec, e, g->d_erec, g->num_sms, st);
+  if (le == cudaSuccess && g->d_cerec)
+    le = launch_class_group(g->d_off, g->d_h, g->d_nrec, g->d_erec, n, g->d_cerec, g->num_sms, st);
   if (le == cudaSuccess) le = launch_symmetry(g->d_off, g->d_col, g->d_h, n, d_asym, g->num_sms, st);
   if (le == cudaSuccess && build_bloom) le = launch_bloom(g->d_off, g->d_col, n, e, g->d_bloom, g->num_sms, st);
   if (le == cudaSuccess && want_labels)
@@ -294,6 +298,7 @@ static void free_graph(fw_graph* g) {
   cudaFree(g->d_hsum);
   cudaFree(g->d_nrec);
   cudaFree(g->d_erec);
+  cudaFree(g->d_cerec);
   cudaFree(g->d_lstat);
   cudaFree(g->d_h8);
   cudaFree(g->d_bloom);
@@ -348,13 +353,14 @@ extern "C" fw_status fw_graph_create(const int32_t* offsets, const int32_t* cols
   if (labels) FW_TRY(cudaMalloc(&g->d_lab, eb), "cudaMalloc(labels)");
   FW_TRY(cudaMalloc(&g->d_hmax, sizeof(float) * ((size_t)n + 1)), "cudaMalloc(h_MAX)");
   FW_TRY(cudaMalloc(&g->d_hsum, sizeof(float) * ((size_t)n + 1)), "cudaMalloc(h_SUM)");
-  FW_TRY(cudaMalloc(&g->d_nrec, sizeof(int4) * ((size_t)n + 1)), "cudaMalloc(node records)");
+  FW_TRY(cudaMalloc(&g->d_nrec, 2 * sizeof(int4) * ((size_t)n + 1)), "cudaMalloc(node records)");
   FW_TRY(cudaMalloc(&g->d_erec, 2 * sizeof(int4) * eb), "cudaMalloc(edge records)");
+  if (weights) FW_TRY(cudaMalloc(&g->d_cerec, 2 * sizeof(int4) * eb), "cudaMalloc(class-ordered edge records)");
   FW_TRY(cudaMalloc(&g->d_err, 64), "cudaMalloc(error word)");
   FW_TRY(cudaMalloc(&g->d_cnt, sizeof(DevCounters)), "cudaMalloc(counters)");
   g->bytes = sizeof(int32_t) * ((size_t)n + 1) + eb * (4 + (weights ? 4 : 0) + (labels ? 1 : 0)) +
-             2 * sizeof(float) * ((size_t)n + 1) + sizeof(int4) * ((size_t)n + 1) + 2 * sizeof(int4) * eb + 64 +
-             sizeof(DevCounters);
+             2 * sizeof(float) * ((size_t)n + 1) + 2 * sizeof(int4) * ((size_t)n + 1) +
+             (weights ? 4 : 2) * sizeof(int4) * eb + 64 + sizeof(DevCounters);
   FW_TRY(cudaMemsetAsync(g->d_err, 0, 64, st), "cudaMemsetAsync");
   FW_TRY(cudaMemsetAsync(g->d_cnt, 0, sizeof(DevCounters), st), "cudaMemsetAsync");
   FW_TRY(cudaMemcpyAsync(g->d_off, offsets, sizeof(int32_t) * ((size_t)n + 1), kind, st), "copy offsets");

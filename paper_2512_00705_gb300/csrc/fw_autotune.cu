@@ -33,7 +33,7 @@ constexpr int kProfileScan = 256;     // neighbours an eRVS scan covers per samp
 __device__ __forceinline__ bool profile_ctx(const DevGraph& g, const Job& J, int32_t i, int32_t stride, StepCtx& c) {
   const int32_t v = i * stride;
   if (v >= g.n) return false;
-  const int4 nr = __ldg(g.nrec + v);
+  const int4 nr = __ldg(g.nrec + 2ll * v);
   if (nr.y == 0) return false;
   c.v = v;
   c.s = nr.x;
@@ -42,7 +42,7 @@ __device__ __forceinline__ bool profile_ctx(const DevGraph& g, const Job& J, int
   c.vp = (J.algo == ALGO_NODE2VEC || J.algo == ALGO_PAGERANK2) ? __ldg(g.col + nr.x) : -1;
   c.w1 = c.w2 = 1.0f;
   if (c.vp >= 0) {
-    const int4 pr = __ldg(g.nrec + c.vp);
+    const int4 pr = __ldg(g.nrec + 2ll * c.vp);
     c.ps = pr.x;
     c.pe = pr.x + pr.y;
     if (J.algo == ALGO_PAGERANK2) pagerank2_weights(J, c.d, pr.y, c.w1, c.w2);
@@ -50,6 +50,7 @@ __device__ __forceinline__ bool profile_ctx(const DevGraph& g, const Job& J, int
     c.ps = c.pe = 0;
   }
   c.wid = (uint32_t)i;
+  c.na = -1;  // one weight class: the paper's eRJS
   return true;
 }
 
@@ -62,7 +63,7 @@ __global__ void profile_rjs_kernel(DevGraph g, Job J, int32_t count, int32_t str
     StepCtx c;
     if (profile_ctx(g, J, i, stride, c)) {
       const bool second = J.algo == ALGO_NODE2VEC && c.vp >= 0;
-      const float hm = J.weighted ? __int_as_float(__ldg(g.nrec + c.v).z) : 1.0f;
+      const float hm = J.weighted ? __int_as_float(__ldg(g.nrec + 2ll * c.v).z) : 1.0f;
       const float B = __fmul_rn(second ? J.wmax1 : (J.algo == ALGO_PAGERANK2 && c.vp >= 0 ? c.w1 : 1.0f), hm);
       Accept acc;
       LaneCounters lc;

@@ -47,9 +47,13 @@ struct DevGraph {
   const uint8_t* __restrict__ lab; // nullptr: no labels
   const float* __restrict__ hmax;
   const float* __restrict__ hsum;
-  const int4* __restrict__ nrec;   // per node {row start, degree, h_MAX bits, h_SUM bits}: one sector per plan
+  const int4* __restrict__ nrec;   // per node 32 bytes: {row start, degree, h_MAX bits, h_SUM bits},
+                                   // {n_A, 0, 0, 0} (n_A: entries with h > h_MAX / 2): one sector per plan
   const int4* __restrict__ erec;   // per edge 32 bytes: {col, h bits, target row start, target degree},
-                                   // {target h_MAX bits, target h_SUM bits, label, 0}: one sector per eRJS trial
+                                   // {target h_MAX bits, target h_SUM bits, label, target n_A}: one
+                                   // sector per eRJS trial
+  const int4* __restrict__ cerec;  // the edge records with every row partitioned stably into its
+                                   // entries with h > h_MAX / 2 and the rest (nullptr: no weights)
   const float2* __restrict__ lstat; // per node and label l < kLabelStats: {max h, sum h} over the
                                    // edges with that label (nullptr: labels absent or >= kLabelStats)
   const uint32_t* __restrict__ bloom; // blocked Bloom filters of the rows (nullptr: none)
@@ -84,6 +88,7 @@ struct Job {
   int32_t split_common;    // node2vec with 1/q < 1: eRJS may use the two-envelope proposal (d(v') < d(v))
   int32_t label_stats;     // metapath: plan with the per-label h_MAX / h_SUM of the required label
   int32_t label_group;     // metapath: fast modes sample inside the required label's segment
+  int32_t classes;         // eRJS proposes from two weight classes (h above / below h_MAX / 2)
   int32_t bloom;           // 1: membership tests in N(v') consult the row's Bloom filter first
   float inv_p, inv_q;      // FP32 1/p, 1/q
   float wmax1, wmean1;     // max / mean of w when a previous node exists
@@ -115,9 +120,9 @@ struct LaneCounters {
   }
 };
 
-// Algorithm of job J.  Kernels specialised to one algorithm pass it as the
-// template argument ALG >= 0, so the other algorithms' code folds away;
-// ALG = -1 reads it from the job (batches of mixed jobs).
+// Algorithm of job J.  The walk kernels pass it as the template argument
+// ALG >= 0, so the other algorithms' code folds away; ALG = -1 reads it
+// from the job (the autotuner's profiling kernels).
 #define FW_ALGO(J) ((ALG) >= 0 ? (ALG) : (J).algo)
 
 // ---------------------------------------------------------------- Philox
@@ -165,6 +170,7 @@ struct StepCtx {
   int32_t step;     // hop index
   uint32_t wid;     // random-stream walker id
   float w1, w2;     // second-order PageRank weights of this step: u in N(v') / otherwise
+  int32_t na;       // eRJS weight classes: entries of v with h > h_MAX / 2 (< 0: one class)
 };
 
 // Eq. (2ndpr) weights for degrees dv = d(v), dp = d(v'):
@@ -385,7 +391,8 @@ __device__ __forceinline__ bool lemire_index(uint32_t x0, uint32_t x1, uint32_t 
 struct Accept {
   int32_t k, node;
   float h;
-  int4 rec;
+  int4 rec;        // target's {row start, degree, h_MAX bits, h_SUM bits}
+  int32_t rec_na;  // target's n_A
   bool rec_ok;
 };
 
@@ -465,6 +472,7 @@ __device__ __forceinline__ bool rjs_trials(const DevGraph& g, const Job& J, cons
         acc.node = a.x;
         acc.h = hg;
         acc.rec = make_int4(a.z, a.w, b.x, b.y);
+        acc.rec_na = b.w;
         acc.rec_ok = true;
         found = true;
         break;
@@ -489,6 +497,7 @@ __device__ __forceinline__ bool rjs_trials(const DevGraph& g, const Job& J, cons
         acc.node = X;
         acc.h = hx;
         acc.rec = make_int4(a.z, a.w, b.x, b.y);
+        acc.rec_na = b.w;
         acc.rec_ok = true;
         found = true;
         break;
@@ -496,14 +505,27 @@ __device__ __forceinline__ bool rjs_trials(const DevGraph& g, const Job& J, cons
       continue;
     }
     uint32_t ku;
-    if (!lemire_index(x.x, x.y, d, ku)) continue;  // this trial proposes nothing; trials stay i.i.d.
+    float Bc = B;  // bound of the proposed entry's class
+    const int4* er;
+    if (c.na >= 0) {
+      // two weight classes: slot t of d + n_A; t < 2 n_A proposes upper entry t / 2 (bound B),
+      // otherwise lower entry t - n_A (bound B / 2, as h <= h_MAX / 2 there)
+      uint32_t t;
+      if (!lemire_index(x.x, x.y, d + (uint32_t)c.na, t)) continue;
+      const bool up = t < 2u * (uint32_t)c.na;
+      ku = up ? (t >> 1) : (t - (uint32_t)c.na);
+      if (!up) Bc = __fmul_rn(0.5f, B);
+      er = g.cerec + 2ll * (c.s + (int32_t)ku);
+    } else {
+      if (!lemire_index(x.x, x.y, d, ku)) continue;  // this trial proposes nothing; trials stay i.i.d.
+      er = g.erec + 2ll * (c.s + (int32_t)ku);
+    }
     const int32_t k = (int32_t)ku;
-    const int4* er = g.erec + 2ll * (c.s + k);
     ld_record(er, a, b);
     if (COUNT) lc.bytes += 32;
     const int32_t u = a.x;
     const float hk = J.weighted ? __int_as_float(a.y) : 1.0f;
-    const float UB = __fmul_rn(u01(x.z), B);
+    const float UB = __fmul_rn(u01(x.z), Bc);
     bool accept;
     if (second) {
       if (u == c.vp) {
@@ -541,9 +563,14 @@ __device__ __forceinline__ bool rjs_trials(const DevGraph& g, const Job& J, cons
     }
     if (accept) {
       acc.k = k;
+      if (c.na >= 0 && J.kind == JOB_HIST) {  // class order: the histogram wants the position in the row
+        uint32_t pq = 0;
+        acc.k = row_find(g.col, c.s, c.s + c.d, u, g.n, pq) - c.s;
+      }
       acc.node = u;
       acc.h = hk;
       acc.rec = make_int4(a.z, a.w, b.x, b.y);
+      acc.rec_na = b.w;
       acc.rec_ok = true;
       found = true;
       break;

@@ -28,6 +28,7 @@ struct fw_graph {
   float* d_hsum = nullptr;
   int4* d_nrec = nullptr;
   int4* d_erec = nullptr;
+  int4* d_cerec = nullptr;     // edge records, rows partitioned by weight class (weighted graphs)
   float2* d_lstat = nullptr;  // per-label node statistics (nullptr: not available)
   bool lstat_bad = false;     // a label >= kLabelStats occurs
   uint32_t* d_bloom = nullptr; // blocked Bloom filters of the rows (membership pre-check)
@@ -93,6 +94,8 @@ cudaError_t launch_edge_records(const int32_t* col, const float* h, const uint8_
                                 int4* erec, int num_sms, cudaStream_t stream);
 cudaError_t launch_label_stats(const int32_t* off, const float* h, const uint8_t* lab, int32_t n, float2* out,
                                unsigned* bad, int num_sms, cudaStream_t stream);
+cudaError_t launch_class_group(const int32_t* off, const float* h, const int4* nrec, const int4* erec, int32_t n,
+                               int4* cerec, int num_sms, cudaStream_t stream);
 cudaError_t launch_label_group(const int32_t* off, const int32_t* col, const float* h, const uint8_t* lab,
                                const int4* nrec, const float2* lstat, int32_t n, int4* lrec, int4* gerec, float* gh,
                                int num_sms, cudaStream_t stream);

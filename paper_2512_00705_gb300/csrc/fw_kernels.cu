@@ -77,10 +77,20 @@ __global__ void node_stats_kernel(const int32_t* __restrict__ off, const float* 
       m = (e > s) ? 1.0f : 0.0f;
       sum = (float)(e - s);
     }
+    // entries of the upper weight class, h > h_MAX / 2 (all of them without weights)
+    int na = e - s;
+    if (h) {
+      const float half = 0.5f * m;
+      na = 0;
+      for (int32_t i = s + lane; i < e; i += 32) na += (h[i] > half) ? 1 : 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) na += __shfl_xor_sync(kFull, na, o);
+    }
     if (lane == 0) {
       hmax[v] = m;
       hsum[v] = sum;
-      nrec[v] = make_int4(s, e - s, __float_as_int(m), __float_as_int(sum));
+      nrec[2 * v] = make_int4(s, e - s, __float_as_int(m), __float_as_int(sum));
+      nrec[2 * v + 1] = make_int4(na, 0, 0, 0);
     }
     localmax = max(localmax, e - s);
   }
@@ -194,11 +204,12 @@ __global__ void label_group_kernel(const int32_t* __restrict__ off, const int32_
       }
       if (valid) {
         const int32_t u = col[i];
-        const int4 nr = nrec[u];
+        const int4 nr = nrec[2 * u];
+        const int na = nrec[2 * u + 1].x;
         const float hv = h ? h[i] : 1.0f;
         const long long o = (long long)s + dst;
         gerec[2 * o] = make_int4(u, __float_as_int(hv), nr.x, nr.y);
-        gerec[2 * o + 1] = make_int4(nr.z, nr.w, b + lane, 0);
+        gerec[2 * o + 1] = make_int4(nr.z, nr.w, b + lane, na);
         gh[o] = hv;
       }
     }
@@ -230,12 +241,51 @@ __global__ void edge_rec_kernel(const int32_t* __restrict__ col, const float* __
                                 int4* __restrict__ erec) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < e; i += (long long)gridDim.x * blockDim.x) {
     const int32_t u = col[i];
-    const int4 nr = nrec[u];
+    const int4 nr = nrec[2 * u];
+    const int na = nrec[2 * u + 1].x;
     const int hb = h ? __float_as_int(h[i]) : __float_as_int(1.0f);
     const int lb = lab ? (int)lab[i] : 0;
     erec[2 * i] = make_int4(u, hb, nr.x, nr.y);
-    erec[2 * i + 1] = make_int4(nr.z, nr.w, lb, 0);
+    erec[2 * i + 1] = make_int4(nr.z, nr.w, lb, na);
   }
+}
+
+// Class-ordered copy of the edge records: each row stably partitioned into
+// the entries with h > h_MAX / 2 (first) and the rest (one warp per row,
+// ballot-ranked scatter).
+__global__ void class_group_kernel(const int32_t* __restrict__ off, const float* __restrict__ h,
+                                   const int4* __restrict__ nrec, const int4* __restrict__ erec, int32_t n,
+                                   int4* __restrict__ cerec) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long v = warp; v < n; v += nwarps) {
+    const int32_t s = off[v], d = off[v + 1] - s;
+    const float half = 0.5f * __int_as_float(nrec[2 * v].z);
+    const int na = nrec[2 * v + 1].x;
+    int hi_run = 0, lo_run = na;
+    for (int32_t b = 0; b < d; b += 32) {
+      const bool valid = b + lane < d;
+      const long long i = (long long)s + b + lane;
+      const bool upper = valid && h[i] > half;
+      const unsigned mu = __ballot_sync(kFull, upper), ml = __ballot_sync(kFull, valid && !upper);
+      if (valid) {
+        const long long o = (long long)s + (upper ? hi_run + __popc(mu & lt) : lo_run + __popc(ml & lt));
+        cerec[2 * o] = erec[2 * i];
+        cerec[2 * o + 1] = erec[2 * i + 1];
+      }
+      hi_run += __popc(mu);
+      lo_run += __popc(ml);
+    }
+  }
+}
+
+cudaError_t launch_class_group(const int32_t* off, const float* h, const int4* nrec, const int4* erec, int32_t n,
+                               int4* cerec, int num_sms, cudaStream_t stream) {
+  class_group_kernel<<<num_sms * 8, 256, 0, stream>>>(off, h, nrec, erec, n, cerec);
+  g_launches.fetch_add(1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_edge_records(const int32_t* col, const float* h, const uint8_t* lab, const int4* nrec, long long e,
@@ -322,6 +372,7 @@ cudaError_t prime_preprocess_kernels() {
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, bloom_kernel);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, label_stats_kernel);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, label_group_kernel);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, class_group_kernel);
   return e;
 }
 

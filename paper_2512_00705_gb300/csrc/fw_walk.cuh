@@ -90,11 +90,12 @@ struct JobTableN {
 // write rows until the queue is exhausted and the warp holds no walker.
 // `sj` (shared memory) is the queue's job table: its jobs' walkers form the
 // index space [0, total), job j owning [sj[j].gbase, sj[j].gbase + W_j).
-// ALG >= 0 fixes the algorithm of every job at compile time.
+// ALG fixes the algorithm of every job at compile time.
 template <bool COUNT, int ALG>
 __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int njobs, long long total,
                                           unsigned long long* __restrict__ qctr, unsigned* __restrict__ err,
                                           int32_t* obuf, LaneCounters& lc) {
+  static_assert(ALG >= 0 && ALG < kAlgos, "the walk loop is compiled for one algorithm");
   const int lane = threadIdx.x & 31;
   const int tid = threadIdx.x;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -108,6 +109,7 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
   c.v = c.vp = c.s = c.d = c.ps = c.pe = c.step = 0;
   c.wid = 0;
   c.w1 = c.w2 = 1.0f;
+  c.na = -1;
   int32_t job = 0, widx = -1;
   int32_t plan = PLAN_NONE, trials = 0, pick = -2, node = -1;
   float B = 0.0f;
@@ -124,6 +126,7 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
   int32_t pos_ret = -1;
   // from the accepted trial: the next node's record, and h of the edge taken (-1: unknown)
   int4 nxt = make_int4(0, 0, 0, 0);
+  int32_t nxt_na = 0;
   bool nxt_ok = false;
   float h_in = -1.0f;
   bool exhausted = false;  // warp-uniform
@@ -167,7 +170,7 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
             c.vp = J.hprev;
             c.step = J.hstep;
             if (c.vp >= 0) {  // during walks the row of v' is carried along; here it is loaded
-              const int4 pr = __ldg(g.nrec + c.vp);
+              const int4 pr = __ldg(g.nrec + 2ll * c.vp);
               c.s = pr.x;
               c.d = pr.y;
             }
@@ -190,16 +193,25 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
       c.ps = c.s;  // the row of v' is the previous step's row
       c.pe = c.s + c.d;
       c.wid = J.wids ? __ldg(J.wids + widx) : J.walker_base + (uint32_t)widx;
-      int4 nr;  // row start, degree, h_MAX, h_SUM of v: from the accepted trial's edge record, or one load
+      // row start, degree, h_MAX, h_SUM and n_A of v: from the accepted trial's edge record, or one load
+      int4 nr;
+      int32_t na;
       if (nxt_ok) {
         nr = nxt;
+        na = nxt_na;
       } else {
-        nr = __ldg(g.nrec + c.v);
-        if (COUNT) lc.bytes += 16;
+        int4 nr2;
+        ld_record(g.nrec + 2ll * c.v, nr, nr2);
+        na = nr2.x;
+        if (COUNT) lc.bytes += 32;
       }
       nxt_ok = false;
       c.s = nr.x;
       c.d = nr.y;
+      // two weight classes in eRJS wherever the bound is a multiple of h_MAX[v]
+      c.na = (J.classes && !(FW_ALGO(J) == ALGO_METAPATH && J.label_stats)) ? na : -1;
+      // eRJS envelope mass in units of the upper class bound: d + n_A half-bound slots
+      const float dsl = c.na >= 0 ? __fmul_rn(0.5f, (float)(c.d + c.na)) : (float)c.d;
       trials = 0;
       pick = -2;
       split = false;
@@ -256,13 +268,16 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
           } else {
             if (FW_ALGO(J) == ALGO_PAGERANK2 && c.vp >= 0) pagerank2_weights(J, c.d, c.pe - c.ps, c.w1, c.w2);
             choice = plan_choice<ALG>(J, hm, hs, c.vp >= 0, c.w1, c.w2, B, S);
+            // with weight classes the expected trials scale with the envelope mass dsl * B
+            const float frac = dsl / (float)c.d;
+            if (c.na >= 0) choice = (__fmul_rn(J.ratio, __fmul_rn(B, frac)) < S) ? MODE_RJS : MODE_RVS;
             if (FW_ALGO(J) == ALGO_PAGERANK2 && c.vp >= 0 && !(J.flags & FW_FLAG_PLAIN_RJS) &&
                 c.pe - c.ps <= kPr2SplitMaxPrev && c.w1 > __fmul_rn(2.0f, c.w2)) {
               // common neighbours split off: eRJS then costs as a first-order walk with bound w2 h_MAX
               split = true;
               B = __fmul_rn(c.w2, hm);
               S = __fmul_rn(c.w2, hs);
-              choice = (__fmul_rn(J.ratio, B) < S) ? MODE_RJS : MODE_RVS;
+              choice = (__fmul_rn(J.ratio, __fmul_rn(B, frac)) < S) ? MODE_RJS : MODE_RVS;
             }
           }
           if (m == MODE_AUTO) {
@@ -283,15 +298,15 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
                 lc.bytes += 32ull * pb + 4ull * (uint32_t)(c.pe - c.ps);
               }
               const float wc = __fmul_rn(__fsub_rn(c.w1, c.w2), h_ret);
-              beta = wc / (wc + (float)c.d * B);
+              beta = wc / (wc + dsl * B);
             }
           } else if (FW_ALGO(J) == ALGO_NODE2VEC && plan == PLAN_RJS && c.vp >= 0 &&
-                     (J.split_return || (J.split_common && c.pe - c.ps < c.d))) {
+                     (J.split_return || (J.split_common && (float)(c.pe - c.ps) < dsl))) {
             // the return edge alone sets max(w) = 1/p: propose it separately and
             // bound the other neighbours by max(1, 1/q) * h_MAX[v]; with 1/q < 1 and
-            // a shorter row of v', two envelopes (see rjs_trials) instead
+            // a row of v' shorter than the envelope of N(v), two envelopes (see rjs_trials)
             split = true;
-            csplit = J.split_common && c.pe - c.ps < c.d;
+            csplit = J.split_common && (float)(c.pe - c.ps) < dsl;
             B = csplit ? hm : __fmul_rn(J.whi1, hm);
             pos_ret = -1;
             bool have = false;
@@ -314,13 +329,13 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
             if (csplit) {
               const float e3 = have ? __fmul_rn(J.inv_p, h_ret) : 0.0f;
               const float e2 = __fmul_rn(__fmul_rn(__fsub_rn(1.0f, J.inv_q), (float)(c.pe - c.ps)), hm);
-              const float e1 = __fmul_rn(__fmul_rn(J.inv_q, (float)c.d), hm);
+              const float e1 = __fmul_rn(__fmul_rn(J.inv_q, dsl), hm);
               const float tot = __fadd_rn(__fadd_rn(e3, e2), e1);
               beta = e3 / tot;
               beta2 = __fadd_rn(e3, e2) / tot;
             } else if (have) {
               const float wret = __fmul_rn(J.inv_p, h_ret);
-              beta = wret / (wret + (float)c.d * B);
+              beta = wret / (wret + dsl * B);
             }
           }
         }
@@ -335,6 +350,7 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
         node = acc.node;
         h_in = acc.h;
         nxt = acc.rec;
+        nxt_na = acc.rec_na;
         nxt_ok = acc.rec_ok;
         if (COUNT) lc.rjs_steps++;
       } else {
@@ -364,6 +380,7 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
           pick = b.z;
           node = a.x;
           nxt = make_int4(a.z, a.w, b.x, b.y);
+          nxt_na = b.w;
           nxt_ok = true;
         }
       } else {
@@ -394,20 +411,20 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
       w.pe = __shfl_sync(kFull, c.pe, src);
       w.step = __shfl_sync(kFull, c.step, src);
       w.wid = __shfl_sync(kFull, c.wid, src);
-      if (ALG < 0 || ALG == ALGO_PAGERANK2) {
+      if (ALG == ALGO_PAGERANK2) {
         w.w1 = __shfl_sync(kFull, c.w1, src);
         w.w2 = __shfl_sync(kFull, c.w2, src);
       }
       const int jb = __shfl_sync(kFull, job, src);
       const int pl = __shfl_sync(kFull, plan, src);
       bool wg = false;
-      if (ALG < 0 || ALG == ALGO_METAPATH) wg = __shfl_sync(kFull, (int)grp, src) != 0;
+      if (ALG == ALGO_METAPATH) wg = __shfl_sync(kFull, (int)grp, src) != 0;
       const Job& JW = sj[jb];
       int32_t k;
       if (pl == PLAN_EXACT_W) {
         const float u = u01(philox(make_uint4(w.wid, (uint32_t)w.step, 0u, 0u), JW.key0, JW.key1).x);
         k = exact_pick<32, COUNT, ALG>(g, JW, w, lane, u, lc);
-      } else if ((ALG < 0 || ALG == ALGO_METAPATH) && wg) {
+      } else if (ALG == ALGO_METAPATH && wg) {
         StepCtx cg = w;
         cg.s = w.ps;
         cg.d = w.pe - w.ps;
@@ -415,7 +432,7 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
       } else {
         k = rvs_pick<32, COUNT, ALG>(g, JW, w, lane, !(JW.flags & FW_FLAG_RVS_NOJUMP), lc);
       }
-      if (lane == src && (ALG < 0 || ALG == ALGO_METAPATH) && wg) {
+      if (lane == src && ALG == ALGO_METAPATH && wg) {
         pick = -1;
         if (k >= 0) {  // grouped position -> node, position in the row, node record
           int4 a, b;
@@ -424,6 +441,7 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
           pick = b.z;
           node = a.x;
           nxt = make_int4(a.z, a.w, b.x, b.y);
+          nxt_na = b.w;
           nxt_ok = true;
         }
         h_in = -1.0f;
