@@ -809,7 +809,7 @@ def main():
             "achieved": bytes_per_step / 32.0 / (kern_ms / 1000.0) / 1e9,
             "peak": gather_ceiling / 1e9, "frac": bytes_per_step / 32.0 / (kern_ms / 1000.0) / gather_ceiling,
             "peak_kind": "measured in this run by fw_gather_ceiling (dependent 32-B gathers, 4 GiB table, "
-                         "5x256 threads per SM)",
+                         "5x256 threads per SM; the rate is flat from 5 to 8 blocks per SM)",
             "note": "algorithmic bytes are sector-granular (32 B per random access), so bytes/32 = accesses"},
         "e2e": e2e_line,
         "gpu_launches": launches,

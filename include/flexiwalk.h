@@ -437,9 +437,9 @@ fw_status fw_server_destroy(fw_server* server);
  * fetches and membership probes are dependent 32-byte gathers at random
  * addresses; on HBM each costs a DRAM access whatever its width, so they
  * are bound by the random accesses per second the memory completes, not by
- * the copy bandwidth.  This call measures that ceiling with the walk
- * kernel's launch shape (5 blocks of 256 threads per SM, each thread a chain
- * of 64 dependent gathers whose addresses come from the loaded data).
+ * the copy bandwidth.  This call measures that ceiling (5 blocks of 256
+ * threads per SM, each thread a chain of 64 dependent gathers whose
+ * addresses come from the loaded data; more chains do not raise the rate).
  * table: caller-owned device buffer of table_bytes bytes, a power of two of
  * at least 64 MiB (use one well above the L2 size), 32-byte aligned; it is
  * overwritten.  rate_out: host double, gathers per second (best of three

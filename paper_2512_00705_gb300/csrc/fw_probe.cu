@@ -7,17 +7,19 @@
 // (a 4-byte and a 32-byte gather take the same time, and the DRAM moves 64 to
 // 128 bytes for either), so a kernel made of them is bound by the number of
 // random accesses the memory system completes per second, well before the
-// streaming copy bandwidth.  fw_gather_ceiling measures that number with the
-// walk kernel's launch shape: every thread runs a chain of dependent 32-byte
-// gathers over a caller-supplied table much larger than L2, each address
-// derived from the previous load.
+// streaming copy bandwidth.  fw_gather_ceiling measures that number: every
+// thread of 5 blocks of 256 per SM runs a chain of dependent 32-byte gathers
+// over a caller-supplied table much larger than L2, each address derived
+// from the previous load (the rate is the same from 5 to 8 blocks per SM, so
+// this is the memory's limit, not the chains' latency; the walk kernel runs
+// 4 blocks per SM).
 #include "fw_internal.h"
 
 namespace fw {
 namespace {
 
 constexpr int kProbeBlock = 256;
-constexpr int kProbeBlocksPerSm = 5;  // the walk kernel's residency
+constexpr int kProbeBlocksPerSm = 5;  // enough chains to saturate the memory system
 constexpr int kProbeChain = 64;       // dependent gathers per thread
 
 __device__ __forceinline__ uint32_t probe_mix(uint32_t x) {

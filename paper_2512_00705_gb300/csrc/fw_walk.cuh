@@ -25,8 +25,8 @@
 namespace fw {
 
 constexpr int kBlock = 256;
-constexpr int kMinBlocks = 5;  // 5 x 256 threads per SM (48 registers; 4 and 6 blocks measured slower)
-constexpr int kRjsBatch = 2;  // eRJS trials per round before the warp ballot (1 and 4 measured slower)
+constexpr int kMinBlocks = 4;  // 4 x 256 threads per SM (64 registers; 3, 5 and 6 blocks measured slower)
+constexpr int kRjsBatch = 2;  // eRJS trials per round before the warp ballot (1, 3 and 4 measured slower)
 constexpr int kThreadExactMaxDeg = 16; // exact steps with d <= this run on one lane
 
 // Row writes are staged per lane in shared memory, one aligned 32-byte
