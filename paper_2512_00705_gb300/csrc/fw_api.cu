@@ -113,7 +113,7 @@ fw_status make_job(const fw_graph* g, int32_t algo, const fw_params* params, uin
 // the required label's segment).  Needs the per-label statistics.  If the
 // device has no room for it, metapath walks keep the full-row path.
 static fw_status build_label_groups(fw_graph* g, cudaStream_t st) {
-  const size_t lrec_bytes = sizeof(int4) * kLabelStats * ((size_t)g->n + 1);
+  const size_t lrec_bytes = 2 * sizeof(int4) * kLabelStats * ((size_t)g->n + 1);
   const size_t gerec_bytes = 2 * sizeof(int4) * (size_t)g->e, gh_bytes = sizeof(float) * (size_t)g->e;
   if (!g->d_lrec) {
     cudaError_t a = cudaMalloc(&g->d_lrec, lrec_bytes);

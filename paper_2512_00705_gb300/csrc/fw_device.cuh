@@ -29,6 +29,7 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxJobs = 64;
 constexpr int kThreadRvsMaxDeg = 8;  // eRVS steps with d <= this run on one lane
 constexpr int kLabelStats = 8;       // per-label node statistics for labels 0..7
+constexpr int kWClasses = 5;         // weight classes inside a metapath label segment
 
 enum : int32_t { ALGO_WEIGHTED = 0, ALGO_NODE2VEC = 1, ALGO_METAPATH = 2, ALGO_PAGERANK2 = 3 };
 constexpr int kAlgos = 4;  // a multi-job launch keeps one walker queue per algorithm
@@ -58,10 +59,13 @@ struct DevGraph {
                                    // edges with that label (nullptr: labels absent or >= kLabelStats)
   const uint32_t* __restrict__ bloom; // blocked Bloom filters of the rows (nullptr: none)
   // label-grouped view of the rows (metapath; nullptr: not built): each row
-  // reordered stably by label.  lrec per node and label l < kLabelStats:
-  // {max h bits, sum h bits, segment start relative to the row start,
-  // segment length}; gerec: edge records in grouped order with the entry's
-  // original position in the row in place of the label; gh: h in grouped order.
+  // reordered stably by (label, weight class).  lrec per node and label
+  // l < kLabelStats, 32 bytes: {max h bits, sum h bits, segment start
+  // relative to the row start, segment length}, {entries of classes
+  // 0 .. kWClasses-2}; class c holds h in (max / 2^(c+1), max / 2^c], the
+  // last class the rest.  gerec: edge records in grouped order with the
+  // entry's original position in the row in place of the label; gh: h in
+  // grouped order.
   const int4* __restrict__ lrec;
   const int4* __restrict__ gerec;
   const float* __restrict__ gh;
@@ -171,7 +175,15 @@ struct StepCtx {
   uint32_t wid;     // random-stream walker id
   float w1, w2;     // second-order PageRank weights of this step: u in N(v') / otherwise
   int32_t na;       // eRJS weight classes: entries of v with h > h_MAX / 2 (< 0: one class)
+  int4 gcls;        // grouped metapath: entries of weight classes 0..3 in the label segment [ps, pe)
 };
+
+// Slots of a label segment's weight-class envelope: class c < kWClasses
+// gives each of its entries 2^(kWClasses-1-c) slots (its bound is max / 2^c).
+__device__ __forceinline__ uint32_t class_slots(const int4& n, int32_t len) {
+  const uint32_t n4 = (uint32_t)(len - n.x - n.y - n.z - n.w);
+  return 16u * (uint32_t)n.x + 8u * (uint32_t)n.y + 4u * (uint32_t)n.z + 2u * (uint32_t)n.w + n4;
+}
 
 // Eq. (2ndpr) weights for degrees dv = d(v), dp = d(v'):
 // t1 = (1-g)/dv, t2 = g/dp, m = max(dv, dp), w1 = (t1 + t2) * m, w2 = t1 * m.
@@ -461,13 +473,47 @@ __device__ __forceinline__ bool rjs_trials(const DevGraph& g, const Job& J, cons
     int4 a, b;  // {col, h, target row start, target degree}, {target h_MAX, target h_SUM, label, 0}
     if ((FW_ALGO(J) == ALGO_METAPATH) && grp) {
       // metapath inside the required label's segment [c.ps, c.pe) of the grouped
-      // arrays: every entry there has w = 1, B = max h over the segment
-      uint32_t kg;
-      if (!lemire_index(x.x, x.y, (uint32_t)(c.pe - c.ps), kg)) continue;
+      // arrays, every entry of w = 1, ordered by weight class: slot t of the
+      // class envelope (class_slots) proposes an entry of class c in proportion
+      // to its bound B / 2^c, B = max h over the segment; accept iff U * bound < h
+      static_assert(kWClasses == 5, "slot walk below is written for five classes");
+      uint32_t t;
+      if (!lemire_index(x.x, x.y, class_slots(c.gcls, c.pe - c.ps), t)) continue;
+      uint32_t base = 0, kg;
+      float Bg = B;
+      const uint32_t n0 = (uint32_t)c.gcls.x, n1 = (uint32_t)c.gcls.y, n2 = (uint32_t)c.gcls.z,
+                     n3 = (uint32_t)c.gcls.w;
+      if (t < 16u * n0) {
+        kg = t >> 4;
+      } else {
+        t -= 16u * n0;
+        base = n0;
+        Bg = __fmul_rn(0.5f, B);
+        if (t < 8u * n1) {
+          kg = base + (t >> 3);
+        } else {
+          t -= 8u * n1;
+          base += n1;
+          Bg = __fmul_rn(0.25f, B);
+          if (t < 4u * n2) {
+            kg = base + (t >> 2);
+          } else {
+            t -= 4u * n2;
+            base += n2;
+            Bg = __fmul_rn(0.125f, B);
+            if (t < 2u * n3) {
+              kg = base + (t >> 1);
+            } else {
+              kg = base + n3 + (t - 2u * n3);
+              Bg = __fmul_rn(0.0625f, B);
+            }
+          }
+        }
+      }
       ld_record(g.gerec + 2ll * (c.ps + (int32_t)kg), a, b);  // b.z: position in the row
       if (COUNT) lc.bytes += 32;
       const float hg = J.weighted ? __int_as_float(a.y) : 1.0f;
-      if (__fmul_rn(u01(x.z), B) < hg) {
+      if (__fmul_rn(u01(x.z), Bg) < hg) {
         acc.k = b.z;
         acc.node = a.x;
         acc.h = hg;

@@ -155,54 +155,101 @@ __global__ void label_stats_kernel(const int32_t* __restrict__ off, const float*
 }
 
 // Label-grouped view (metapath): one warp per node reorders its row stably
-// by label (labels < kLabelStats; counting pass, exclusive prefix over the
-// labels, ballot-ranked scatter), writes grouped edge records whose fourth
-// word of the second half is the entry's position in the row, the grouped h,
-// and per label {max h, sum h (from the label statistics), segment start,
-// segment length}.
+// by (label, weight class) -- labels < kLabelStats; within a label, class c
+// < kWClasses - 1 holds h in (M / 2^(c+1), M / 2^c] and the last class h <=
+// M / 2^(kWClasses-1), M the label's max h -- by a counting pass over the
+// kLabelStats * kWClasses buckets, an exclusive prefix over them and a
+// ballot-ranked scatter.  It writes grouped edge records (the second half's
+// third word is the entry's position in the row, the fourth the target's
+// n_A), the grouped h, and per label a 32-byte record {max h, sum h (from
+// the label statistics), segment start, segment length}, {counts of classes
+// 0 .. kWClasses-2}.
 __global__ void label_group_kernel(const int32_t* __restrict__ off, const int32_t* __restrict__ col,
                                    const float* __restrict__ h, const uint8_t* __restrict__ lab,
                                    const int4* __restrict__ nrec, const float2* __restrict__ lstat, int32_t n,
                                    int4* __restrict__ lrec, int4* __restrict__ gerec, float* __restrict__ gh) {
+  constexpr int kB = kLabelStats * kWClasses;  // buckets; bucket k lives in lane k % 32 of (k < 32 ? lo : hi)
+  static_assert(kB <= 64, "two registers of bucket counters per lane");
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long v = warp; v < n; v += nwarps) {
     const int32_t s = off[v], d = off[v + 1] - s;
-    int cnt = 0;  // lane l < kLabelStats: entries with label l
+    const float2 ls = lane < kLabelStats ? lstat[v * kLabelStats + lane] : make_float2(0.0f, 0.0f);
+    // bucket of entry i of the row (kB for lanes past the row end)
+    auto bucket = [&](int32_t i, bool valid) -> int {
+      const int l = valid ? (int)lab[s + i] : 0;
+      const float m = __shfl_sync(kFull, ls.x, l);
+      if (!valid) return kB;
+      const float x = h ? h[s + i] : 1.0f;
+      int c = 0;
+      float t = 0.5f * m;
+      while (c < kWClasses - 1 && !(x > t)) {
+        ++c;
+        t *= 0.5f;
+      }
+      return l * kWClasses + c;
+    };
+    int lo = 0, hi = 0;  // bucket counts
     for (int32_t b = 0; b < d; b += 32) {
-      const int l = (b + lane < d) ? (int)lab[s + b + lane] : 255;
-#pragma unroll
-      for (int k = 0; k < kLabelStats; ++k) {
-        const unsigned m = __ballot_sync(kFull, l == k);
-        if (lane == k) cnt += __popc(m);
+      const int k = bucket(b + lane, b + lane < d);
+#pragma unroll 8
+      for (int q = 0; q < kB; ++q) {
+        const int cnt = __popc(__ballot_sync(kFull, k == q));
+        if (lane == (q & 31)) {
+          if (q < 32) lo += cnt;
+          else hi += cnt;
+        }
       }
     }
-    int incl = cnt;
+    // exclusive prefix over the buckets: lo holds buckets 0..31, hi buckets 32..kB-1
+    int ilo = lo, ihi = hi;
 #pragma unroll
-    for (int o = 1; o < kLabelStats; o <<= 1) {
-      const int y = __shfl_up_sync(kFull, incl, o);
-      if (lane >= o) incl += y;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, ilo, o), z = __shfl_up_sync(kFull, ihi, o);
+      if (lane >= o) {
+        ilo += y;
+        ihi += z;
+      }
     }
-    int run = incl - cnt;  // lane l: start of label l's segment
-    if (lane < kLabelStats) {
-      const float2 ls = lstat[v * kLabelStats + lane];
-      lrec[v * kLabelStats + lane] = make_int4(__float_as_int(ls.x), __float_as_int(ls.y), run, cnt);
+    const int total_lo = __shfl_sync(kFull, ilo, 31);
+    int run_lo = ilo - lo, run_hi = total_lo + ihi - hi;  // start of bucket lane / 32 + lane
+    // per-label record: lane l < kLabelStats gathers its kWClasses buckets
+    {
+      int cnt[kWClasses], start0 = 0;
+#pragma unroll
+      for (int c = 0; c < kWClasses; ++c) {
+        const int q = (lane < kLabelStats ? lane : 0) * kWClasses + c;
+        const int a = __shfl_sync(kFull, lo, q & 31), bb = __shfl_sync(kFull, hi, q & 31);
+        const int sa = __shfl_sync(kFull, run_lo, q & 31), sb = __shfl_sync(kFull, run_hi, q & 31);
+        cnt[c] = q < 32 ? a : bb;
+        if (c == 0) start0 = q < 32 ? sa : sb;
+      }
+      int len = 0;
+#pragma unroll
+      for (int c = 0; c < kWClasses; ++c) len += cnt[c];
+      if (lane < kLabelStats) {
+        lrec[2 * (v * kLabelStats + lane)] = make_int4(__float_as_int(ls.x), __float_as_int(ls.y), start0, len);
+        lrec[2 * (v * kLabelStats + lane) + 1] = make_int4(cnt[0], cnt[1], cnt[2], cnt[3]);
+      }
     }
     for (int32_t b = 0; b < d; b += 32) {
       const bool valid = b + lane < d;
-      const long long i = (long long)s + b + lane;
-      const int l = valid ? (int)lab[i] : 255;
+      const int k = bucket(b + lane, valid);
       int dst = 0;
-#pragma unroll
-      for (int k = 0; k < kLabelStats; ++k) {
-        const unsigned m = __ballot_sync(kFull, l == k);
-        const int base = __shfl_sync(kFull, run, k);
-        if (l == k) dst = base + __popc(m & lt);
-        if (lane == k) run += __popc(m);
+#pragma unroll 8
+      for (int q = 0; q < kB; ++q) {
+        const unsigned m = __ballot_sync(kFull, k == q);
+        const int base = q < 32 ? __shfl_sync(kFull, run_lo, q & 31) : __shfl_sync(kFull, run_hi, q & 31);
+        if (k == q) dst = base + __popc(m & lt);
+        if (lane == (q & 31)) {
+          if (q < 32) run_lo += __popc(m);
+          else run_hi += __popc(m);
+        }
       }
       if (valid) {
+        const long long i = (long long)s + b + lane;
         const int32_t u = col[i];
         const int4 nr = nrec[2 * u];
         const int na = nrec[2 * u + 1].x;

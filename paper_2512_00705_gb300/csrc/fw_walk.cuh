@@ -240,18 +240,21 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
             // per-label record of v: exact bound and sum over the required label,
             // and where its entries sit in the label-grouped view; none -> dead end
             const uint8_t want = J.schema[c.step % J.schema_len];
-            int4 lr = make_int4(0, 0, 0, 0);
+            int4 lr = make_int4(0, 0, 0, 0), lr2 = make_int4(0, 0, 0, 0);
             if (want < kLabelStats) {
-              lr = __ldg(g.lrec + (long long)c.v * kLabelStats + want);
-              if (COUNT) lc.bytes += 16;
+              ld_record(g.lrec + 2ll * ((long long)c.v * kLabelStats + want), lr, lr2);
+              if (COUNT) lc.bytes += 32;
             }
             B = __int_as_float(lr.x);
             S = __int_as_float(lr.y);
-            choice = (__fmul_rn(J.ratio, B) < S) ? MODE_RJS : MODE_RVS;
-            if (!(S > 0.0f)) pick = -1;
             grp = true;
             c.ps = c.s + lr.z;
             c.pe = c.ps + lr.w;
+            c.gcls = lr2;
+            // expected eRJS trials follow the class envelope: bound B * slots / (16 len)
+            const float beff = lr.w > 0 ? __fmul_rn(B, (float)class_slots(lr2, lr.w) / (16.0f * (float)lr.w)) : B;
+            choice = (__fmul_rn(J.ratio, beff) < S) ? MODE_RJS : MODE_RVS;
+            if (!(S > 0.0f)) pick = -1;
           } else if (FW_ALGO(J) == ALGO_METAPATH && J.label_stats) {
             // metapath with per-label statistics: exact bound and exact sum over
             // the edges whose label the step requires; none -> dead end now
