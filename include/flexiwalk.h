@@ -83,7 +83,7 @@ enum {
   FW_FLAG_UNWEIGHTED = 4, /* ignore h: every property weight is 1 (Sec. 5.1)     */
   FW_FLAG_PLAIN_RJS = 8,  /* eRJS exactly as Sec. 3.3 (uniform proposal, bound
                              max(w) * h_MAX) instead of the refined envelopes:
-                             two weight classes (h above / below h_MAX / 2),
+                             three weight classes (bounds B, B/2, B/4),
                              node2vec's return edge proposed separately, two
                              envelopes for node2vec with q > 1, the common
                              neighbours of second-order PageRank split off       */
@@ -164,7 +164,8 @@ void fw_params_default(fw_params* params);
  *   ptr_kind FW_PTR_HOST or FW_PTR_DEVICE for all four arrays
  * The graph copies its inputs; the caller may free them once this call
  * returns.  Besides the CSR it keeps 32-byte edge records (twice with
- * weights: in CSR order and with each row partitioned by weight class),
+ * weights and degrees below 2^24: in CSR order and with each row
+ * partitioned by weight class),
  * 32-byte node records, per-row Bloom filters and, with labels all below
  * 8, per-label node statistics and a label-grouped copy of the rows (36
  * bytes per entry) for metapath; if that copy does not fit, metapath

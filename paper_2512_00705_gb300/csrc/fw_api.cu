@@ -207,6 +207,11 @@ fw_status rebuild_derived(fw_graph* g, cudaStream_t st) {
   if (se != cudaSuccess) return cuda_error(se, "sync after preprocessing");
   g->max_degree = maxdeg;
   g->sym = flags[0] == 0 ? 1 : 0;
+  if (g->d_cerec && maxdeg >= (1 << 24)) {  // edge records carry class counts in 24 bits
+    cudaFree(g->d_cerec);
+    g->d_cerec = nullptr;
+    g->bytes -= 2 * sizeof(int4) * (size_t)e;
+  }
   if (want_labels && flags[1] != 0) {  // a label >= kLabelStats: per-label statistics unused
     cudaFree(g->d_lstat);
     g->d_lstat = nullptr;

@@ -50,7 +50,8 @@ __device__ __forceinline__ bool profile_ctx(const DevGraph& g, const Job& J, int
     c.ps = c.pe = 0;
   }
   c.wid = (uint32_t)i;
-  c.na = -1;  // one weight class: the paper's eRJS
+  c.n0 = -1;  // one weight class: the paper's eRJS
+  c.n1 = 0;
   return true;
 }
 

@@ -49,12 +49,13 @@ struct DevGraph {
   const float* __restrict__ hmax;
   const float* __restrict__ hsum;
   const int4* __restrict__ nrec;   // per node 32 bytes: {row start, degree, h_MAX bits, h_SUM bits},
-                                   // {n_A, 0, 0, 0} (n_A: entries with h > h_MAX / 2): one sector per plan
+                                   // {n0, n1, 0, 0}: entries of weight class 0 (h > h_MAX / 2) and
+                                   // class 1 (h_MAX / 4 < h <= h_MAX / 2); one sector per plan
   const int4* __restrict__ erec;   // per edge 32 bytes: {col, h bits, target row start, target degree},
-                                   // {target h_MAX bits, target h_SUM bits, label, target n_A}: one
-                                   // sector per eRJS trial
-  const int4* __restrict__ cerec;  // the edge records with every row partitioned stably into its
-                                   // entries with h > h_MAX / 2 and the rest (nullptr: no weights)
+                                   // {target h_MAX bits, target h_SUM bits, label | target n0 << 8,
+                                   // target n1}: one sector per eRJS trial
+  const int4* __restrict__ cerec;  // the edge records with every row partitioned stably into weight
+                                   // classes 0, 1, 2 (class 2: h <= h_MAX / 4); nullptr: no classes
   const float2* __restrict__ lstat; // per node and label l < kLabelStats: {max h, sum h} over the
                                    // edges with that label (nullptr: labels absent or >= kLabelStats)
   const uint32_t* __restrict__ bloom; // blocked Bloom filters of the rows (nullptr: none)
@@ -92,7 +93,7 @@ struct Job {
   int32_t split_common;    // node2vec with 1/q < 1: eRJS may use the two-envelope proposal (d(v') < d(v))
   int32_t label_stats;     // metapath: plan with the per-label h_MAX / h_SUM of the required label
   int32_t label_group;     // metapath: fast modes sample inside the required label's segment
-  int32_t classes;         // eRJS proposes from two weight classes (h above / below h_MAX / 2)
+  int32_t classes;         // eRJS proposes from three weight classes (bounds B, B / 2, B / 4)
   int32_t bloom;           // 1: membership tests in N(v') consult the row's Bloom filter first
   float inv_p, inv_q;      // FP32 1/p, 1/q
   float wmax1, wmean1;     // max / mean of w when a previous node exists
@@ -174,7 +175,7 @@ struct StepCtx {
   int32_t step;     // hop index
   uint32_t wid;     // random-stream walker id
   float w1, w2;     // second-order PageRank weights of this step: u in N(v') / otherwise
-  int32_t na;       // eRJS weight classes: entries of v with h > h_MAX / 2 (< 0: one class)
+  int32_t n0, n1;   // eRJS weight classes: entries of v in classes 0 and 1 (n0 < 0: one class)
   int4 gcls;        // grouped metapath: entries of weight classes 0..3 in the label segment [ps, pe)
 };
 
@@ -404,7 +405,7 @@ struct Accept {
   int32_t k, node;
   float h;
   int4 rec;        // target's {row start, degree, h_MAX bits, h_SUM bits}
-  int32_t rec_na;  // target's n_A
+  int32_t rec_n0, rec_n1;  // target's weight-class counts
   bool rec_ok;
 };
 
@@ -518,7 +519,7 @@ __device__ __forceinline__ bool rjs_trials(const DevGraph& g, const Job& J, cons
         acc.node = a.x;
         acc.h = hg;
         acc.rec = make_int4(a.z, a.w, b.x, b.y);
-        acc.rec_na = b.w;
+        acc.rec_n0 = acc.rec_n1 = 0;  // the label-grouped path plans without weight classes
         acc.rec_ok = true;
         found = true;
         break;
@@ -543,7 +544,8 @@ __device__ __forceinline__ bool rjs_trials(const DevGraph& g, const Job& J, cons
         acc.node = X;
         acc.h = hx;
         acc.rec = make_int4(a.z, a.w, b.x, b.y);
-        acc.rec_na = b.w;
+        acc.rec_n0 = (int32_t)((uint32_t)b.z >> 8);
+        acc.rec_n1 = b.w;
         acc.rec_ok = true;
         found = true;
         break;
@@ -553,14 +555,21 @@ __device__ __forceinline__ bool rjs_trials(const DevGraph& g, const Job& J, cons
     uint32_t ku;
     float Bc = B;  // bound of the proposed entry's class
     const int4* er;
-    if (c.na >= 0) {
-      // two weight classes: slot t of d + n_A; t < 2 n_A proposes upper entry t / 2 (bound B),
-      // otherwise lower entry t - n_A (bound B / 2, as h <= h_MAX / 2 there)
+    if (c.n0 >= 0) {
+      // three weight classes of bounds B, B / 2, B / 4 (h <= h_MAX / 2^c in class c): slot t of
+      // 4 n0 + 2 n1 + n2 proposes an entry of class c in proportion to its bound
+      const uint32_t n0 = (uint32_t)c.n0, n1 = (uint32_t)c.n1;
       uint32_t t;
-      if (!lemire_index(x.x, x.y, d + (uint32_t)c.na, t)) continue;
-      const bool up = t < 2u * (uint32_t)c.na;
-      ku = up ? (t >> 1) : (t - (uint32_t)c.na);
-      if (!up) Bc = __fmul_rn(0.5f, B);
+      if (!lemire_index(x.x, x.y, 4u * n0 + 2u * n1 + (d - n0 - n1), t)) continue;
+      if (t < 4u * n0) {
+        ku = t >> 2;
+      } else if (t - 4u * n0 < 2u * n1) {
+        ku = n0 + ((t - 4u * n0) >> 1);
+        Bc = __fmul_rn(0.5f, B);
+      } else {
+        ku = n0 + n1 + (t - 4u * n0 - 2u * n1);
+        Bc = __fmul_rn(0.25f, B);
+      }
       er = g.cerec + 2ll * (c.s + (int32_t)ku);
     } else {
       if (!lemire_index(x.x, x.y, d, ku)) continue;  // this trial proposes nothing; trials stay i.i.d.
@@ -609,14 +618,15 @@ __device__ __forceinline__ bool rjs_trials(const DevGraph& g, const Job& J, cons
     }
     if (accept) {
       acc.k = k;
-      if (c.na >= 0 && J.kind == JOB_HIST) {  // class order: the histogram wants the position in the row
+      if (c.n0 >= 0 && J.kind == JOB_HIST) {  // class order: the histogram wants the position in the row
         uint32_t pq = 0;
         acc.k = row_find(g.col, c.s, c.s + c.d, u, g.n, pq) - c.s;
       }
       acc.node = u;
       acc.h = hk;
       acc.rec = make_int4(a.z, a.w, b.x, b.y);
-      acc.rec_na = b.w;
+      acc.rec_n0 = (int32_t)((uint32_t)b.z >> 8);
+      acc.rec_n1 = b.w;
       acc.rec_ok = true;
       found = true;
       break;

@@ -77,20 +77,28 @@ __global__ void node_stats_kernel(const int32_t* __restrict__ off, const float* 
       m = (e > s) ? 1.0f : 0.0f;
       sum = (float)(e - s);
     }
-    // entries of the upper weight class, h > h_MAX / 2 (all of them without weights)
-    int na = e - s;
+    // entries of weight classes 0 (h > h_MAX / 2) and 1 (h_MAX / 4 < h <= h_MAX / 2);
+    // without weights every entry is in class 0
+    int n0 = e - s, n1 = 0;
     if (h) {
-      const float half = 0.5f * m;
-      na = 0;
-      for (int32_t i = s + lane; i < e; i += 32) na += (h[i] > half) ? 1 : 0;
+      const float half = 0.5f * m, quarter = 0.25f * m;
+      n0 = 0;
+      for (int32_t i = s + lane; i < e; i += 32) {
+        const float x = h[i];
+        n0 += (x > half) ? 1 : 0;
+        n1 += (x > quarter && !(x > half)) ? 1 : 0;
+      }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) na += __shfl_xor_sync(kFull, na, o);
+      for (int o = 16; o > 0; o >>= 1) {
+        n0 += __shfl_xor_sync(kFull, n0, o);
+        n1 += __shfl_xor_sync(kFull, n1, o);
+      }
     }
     if (lane == 0) {
       hmax[v] = m;
       hsum[v] = sum;
       nrec[2 * v] = make_int4(s, e - s, __float_as_int(m), __float_as_int(sum));
-      nrec[2 * v + 1] = make_int4(na, 0, 0, 0);
+      nrec[2 * v + 1] = make_int4(n0, n1, 0, 0);
     }
     localmax = max(localmax, e - s);
   }
@@ -252,11 +260,10 @@ __global__ void label_group_kernel(const int32_t* __restrict__ off, const int32_
         const long long i = (long long)s + b + lane;
         const int32_t u = col[i];
         const int4 nr = nrec[2 * u];
-        const int na = nrec[2 * u + 1].x;
         const float hv = h ? h[i] : 1.0f;
         const long long o = (long long)s + dst;
         gerec[2 * o] = make_int4(u, __float_as_int(hv), nr.x, nr.y);
-        gerec[2 * o + 1] = make_int4(nr.z, nr.w, b + lane, na);
+        gerec[2 * o + 1] = make_int4(nr.z, nr.w, b + lane, 0);
         gh[o] = hv;
       }
     }
@@ -289,17 +296,18 @@ __global__ void edge_rec_kernel(const int32_t* __restrict__ col, const float* __
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < e; i += (long long)gridDim.x * blockDim.x) {
     const int32_t u = col[i];
     const int4 nr = nrec[2 * u];
-    const int na = nrec[2 * u + 1].x;
+    const int4 nc = nrec[2 * u + 1];
     const int hb = h ? __float_as_int(h[i]) : __float_as_int(1.0f);
     const int lb = lab ? (int)lab[i] : 0;
     erec[2 * i] = make_int4(u, hb, nr.x, nr.y);
-    erec[2 * i + 1] = make_int4(nr.z, nr.w, lb, na);
+    // label in the low byte, the target's class-0 count above it (degrees < 2^24)
+    erec[2 * i + 1] = make_int4(nr.z, nr.w, lb | (int)((unsigned)nc.x << 8), nc.y);
   }
 }
 
 // Class-ordered copy of the edge records: each row stably partitioned into
-// the entries with h > h_MAX / 2 (first) and the rest (one warp per row,
-// ballot-ranked scatter).
+// its weight classes 0 (h > h_MAX / 2), 1 (h_MAX / 4 < h <= h_MAX / 2) and
+// 2 (the rest), one warp per row, ballot-ranked scatter.
 __global__ void class_group_kernel(const int32_t* __restrict__ off, const float* __restrict__ h,
                                    const int4* __restrict__ nrec, const int4* __restrict__ erec, int32_t n,
                                    int4* __restrict__ cerec) {
@@ -309,21 +317,26 @@ __global__ void class_group_kernel(const int32_t* __restrict__ off, const float*
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long v = warp; v < n; v += nwarps) {
     const int32_t s = off[v], d = off[v + 1] - s;
-    const float half = 0.5f * __int_as_float(nrec[2 * v].z);
-    const int na = nrec[2 * v + 1].x;
-    int hi_run = 0, lo_run = na;
+    const float m = __int_as_float(nrec[2 * v].z);
+    const float half = 0.5f * m, quarter = 0.25f * m;
+    const int4 nc = nrec[2 * v + 1];
+    int run0 = 0, run1 = nc.x, run2 = nc.x + nc.y;
     for (int32_t b = 0; b < d; b += 32) {
       const bool valid = b + lane < d;
       const long long i = (long long)s + b + lane;
-      const bool upper = valid && h[i] > half;
-      const unsigned mu = __ballot_sync(kFull, upper), ml = __ballot_sync(kFull, valid && !upper);
+      const float x = valid ? h[i] : 0.0f;
+      const int cls = (x > half) ? 0 : ((x > quarter) ? 1 : 2);
+      const unsigned m0 = __ballot_sync(kFull, valid && cls == 0), m1 = __ballot_sync(kFull, valid && cls == 1),
+                     m2 = __ballot_sync(kFull, valid && cls == 2);
       if (valid) {
-        const long long o = (long long)s + (upper ? hi_run + __popc(mu & lt) : lo_run + __popc(ml & lt));
+        const int r = cls == 0 ? run0 + __popc(m0 & lt) : (cls == 1 ? run1 + __popc(m1 & lt) : run2 + __popc(m2 & lt));
+        const long long o = (long long)s + r;
         cerec[2 * o] = erec[2 * i];
         cerec[2 * o + 1] = erec[2 * i + 1];
       }
-      hi_run += __popc(mu);
-      lo_run += __popc(ml);
+      run0 += __popc(m0);
+      run1 += __popc(m1);
+      run2 += __popc(m2);
     }
   }
 }

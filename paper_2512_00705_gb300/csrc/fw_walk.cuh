@@ -109,7 +109,8 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
   c.v = c.vp = c.s = c.d = c.ps = c.pe = c.step = 0;
   c.wid = 0;
   c.w1 = c.w2 = 1.0f;
-  c.na = -1;
+  c.n0 = -1;
+  c.n1 = 0;
   int32_t job = 0, widx = -1;
   int32_t plan = PLAN_NONE, trials = 0, pick = -2, node = -1;
   float B = 0.0f;
@@ -126,7 +127,7 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
   int32_t pos_ret = -1;
   // from the accepted trial: the next node's record, and h of the edge taken (-1: unknown)
   int4 nxt = make_int4(0, 0, 0, 0);
-  int32_t nxt_na = 0;
+  int32_t nxt_n0 = 0, nxt_n1 = 0;
   bool nxt_ok = false;
   float h_in = -1.0f;
   bool exhausted = false;  // warp-uniform
@@ -193,25 +194,30 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
       c.ps = c.s;  // the row of v' is the previous step's row
       c.pe = c.s + c.d;
       c.wid = J.wids ? __ldg(J.wids + widx) : J.walker_base + (uint32_t)widx;
-      // row start, degree, h_MAX, h_SUM and n_A of v: from the accepted trial's edge record, or one load
+      // row start, degree, h_MAX, h_SUM and class counts of v: from the accepted trial's edge
+      // record, or one load
       int4 nr;
-      int32_t na;
+      int32_t n0, n1;
       if (nxt_ok) {
         nr = nxt;
-        na = nxt_na;
+        n0 = nxt_n0;
+        n1 = nxt_n1;
       } else {
         int4 nr2;
         ld_record(g.nrec + 2ll * c.v, nr, nr2);
-        na = nr2.x;
+        n0 = nr2.x;
+        n1 = nr2.y;
         if (COUNT) lc.bytes += 32;
       }
       nxt_ok = false;
       c.s = nr.x;
       c.d = nr.y;
-      // two weight classes in eRJS wherever the bound is a multiple of h_MAX[v]
-      c.na = (J.classes && !(FW_ALGO(J) == ALGO_METAPATH && J.label_stats)) ? na : -1;
-      // eRJS envelope mass in units of the upper class bound: d + n_A half-bound slots
-      const float dsl = c.na >= 0 ? __fmul_rn(0.5f, (float)(c.d + c.na)) : (float)c.d;
+      // weight classes in eRJS wherever the bound is a multiple of h_MAX[v]
+      const bool cls = J.classes && !(FW_ALGO(J) == ALGO_METAPATH && J.label_stats);
+      c.n0 = cls ? n0 : -1;
+      c.n1 = n1;
+      // eRJS envelope mass in units of the class-0 bound: (4 n0 + 2 n1 + n2) / 4
+      const float dsl = cls ? __fmul_rn(0.25f, (float)(c.d + 3 * n0 + n1)) : (float)c.d;
       trials = 0;
       pick = -2;
       split = false;
@@ -273,7 +279,7 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
             choice = plan_choice<ALG>(J, hm, hs, c.vp >= 0, c.w1, c.w2, B, S);
             // with weight classes the expected trials scale with the envelope mass dsl * B
             const float frac = dsl / (float)c.d;
-            if (c.na >= 0) choice = (__fmul_rn(J.ratio, __fmul_rn(B, frac)) < S) ? MODE_RJS : MODE_RVS;
+            if (cls) choice = (__fmul_rn(J.ratio, __fmul_rn(B, frac)) < S) ? MODE_RJS : MODE_RVS;
             if (FW_ALGO(J) == ALGO_PAGERANK2 && c.vp >= 0 && !(J.flags & FW_FLAG_PLAIN_RJS) &&
                 c.pe - c.ps <= kPr2SplitMaxPrev && c.w1 > __fmul_rn(2.0f, c.w2)) {
               // common neighbours split off: eRJS then costs as a first-order walk with bound w2 h_MAX
@@ -353,7 +359,8 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
         node = acc.node;
         h_in = acc.h;
         nxt = acc.rec;
-        nxt_na = acc.rec_na;
+        nxt_n0 = acc.rec_n0;
+        nxt_n1 = acc.rec_n1;
         nxt_ok = acc.rec_ok;
         if (COUNT) lc.rjs_steps++;
       } else {
@@ -383,7 +390,7 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
           pick = b.z;
           node = a.x;
           nxt = make_int4(a.z, a.w, b.x, b.y);
-          nxt_na = b.w;
+          nxt_n0 = nxt_n1 = 0;  // metapath plans without weight classes
           nxt_ok = true;
         }
       } else {
@@ -444,7 +451,7 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
           pick = b.z;
           node = a.x;
           nxt = make_int4(a.z, a.w, b.x, b.y);
-          nxt_na = b.w;
+          nxt_n0 = nxt_n1 = 0;  // metapath plans without weight classes
           nxt_ok = true;
         }
         h_in = -1.0f;
