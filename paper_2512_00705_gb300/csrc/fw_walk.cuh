@@ -29,27 +29,29 @@ constexpr int kMinBlocks = 4;  // 4 x 256 threads per SM (64 registers; 3, 5 and
 constexpr int kRjsBatch = 2;  // eRJS trials per round before the warp ballot (1, 3 and 4 measured slower)
 constexpr int kThreadExactMaxDeg = 16; // exact steps with d <= this run on one lane
 
-// Row writes are staged per lane in shared memory, one aligned 32-byte
-// sector at a time, and written out when the sector (or the row) is
-// complete: scattered 4-byte stores would each cost a DRAM sector write.
+// Row writes are staged per lane in shared memory, one aligned group of
+// kStageSlots entries at a time, and written out when the group (or the
+// row) is complete: scattered 4-byte stores would each cost a DRAM write.
 // Slot s of lane t lives at obuf[s * kBlock + t] (no bank conflicts).
+constexpr int kStageSlots = 8;  // 32-byte groups
+static_assert(kStageSlots % 4 == 0 && (kStageSlots & (kStageSlots - 1)) == 0, "whole int4s, power of two");
 struct RowStage {
   int32_t* row;   // current row (nullptr: none)
-  int32_t first;  // first valid slot of the staged sector
+  int32_t first;  // first valid slot of the staged group
 };
 
-__device__ __forceinline__ int32_t sector_slot(const int32_t* a) {
-  return (int32_t)((reinterpret_cast<uintptr_t>(a) >> 2) & 7u);
+__device__ __forceinline__ int32_t stage_slot(const int32_t* a) {
+  return (int32_t)((reinterpret_cast<uintptr_t>(a) >> 2) & (uintptr_t)(kStageSlots - 1));
 }
 
-// write the staged slots [first, last] of the sector holding `a` (a = address of slot `last`)
+// write the staged slots [first, last] of the group holding `a` (a = address of slot `last`)
 __device__ __forceinline__ void stage_flush(const int32_t* obuf, int tid, int32_t* a, int32_t first, int32_t last) {
   int32_t* base = a - last;
-  if (first == 0 && last == 7) {
-    const int4 lo = make_int4(obuf[0 * kBlock + tid], obuf[1 * kBlock + tid], obuf[2 * kBlock + tid], obuf[3 * kBlock + tid]);
-    const int4 hi = make_int4(obuf[4 * kBlock + tid], obuf[5 * kBlock + tid], obuf[6 * kBlock + tid], obuf[7 * kBlock + tid]);
-    reinterpret_cast<int4*>(base)[0] = lo;
-    reinterpret_cast<int4*>(base)[1] = hi;
+  if (first == 0 && last == kStageSlots - 1) {
+#pragma unroll
+    for (int q = 0; q < kStageSlots / 4; ++q)
+      reinterpret_cast<int4*>(base)[q] = make_int4(obuf[(4 * q) * kBlock + tid], obuf[(4 * q + 1) * kBlock + tid],
+                                                   obuf[(4 * q + 2) * kBlock + tid], obuf[(4 * q + 3) * kBlock + tid]);
   } else {
     for (int32_t k = first; k <= last; ++k) base[k] = obuf[k * kBlock + tid];
   }
@@ -58,25 +60,25 @@ __device__ __forceinline__ void stage_flush(const int32_t* obuf, int tid, int32_
 // stage row[p] = val; `final` marks the last entry the lane will write in this row
 __device__ __forceinline__ void stage_put(int32_t* obuf, int tid, RowStage& rs, int32_t p, int32_t val, bool final) {
   int32_t* a = rs.row + p;
-  const int32_t slot = sector_slot(a);
+  const int32_t slot = stage_slot(a);
   obuf[slot * kBlock + tid] = val;
-  if (slot == 7 || final) {
+  if (slot == kStageSlots - 1 || final) {
     stage_flush(obuf, tid, a, rs.first, slot);
     rs.first = 0;
   }
 }
 
-// row[from, to) = -1 after a dead end: finish the staged sector, then whole sectors, then the tail
+// row[from, to) = -1 after a dead end: finish the staged group, then whole groups, then the tail
 __device__ __forceinline__ void stage_fill_minus_one(int32_t* obuf, int tid, RowStage& rs, int32_t from, int32_t to) {
   int32_t p = from;
-  while (p < to && (p == from || sector_slot(rs.row + p) != 0)) {
+  while (p < to && (p == from || stage_slot(rs.row + p) != 0)) {
     stage_put(obuf, tid, rs, p, -1, p + 1 == to);
     ++p;
   }
-  for (; p + 8 <= to; p += 8) {
+  for (; p + kStageSlots <= to; p += kStageSlots) {
     int4* q = reinterpret_cast<int4*>(rs.row + p);
-    q[0] = make_int4(-1, -1, -1, -1);
-    q[1] = make_int4(-1, -1, -1, -1);
+#pragma unroll
+    for (int k = 0; k < kStageSlots / 4; ++k) q[k] = make_int4(-1, -1, -1, -1);
   }
   for (; p < to; ++p) rs.row[p] = -1;
 }
@@ -154,7 +156,7 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
           if (J.kind == JOB_WALK) {
             const int32_t st = __ldg(J.starts + widx);
             rs.row = J.out + (long long)widx * (J.len + 1);
-            rs.first = sector_slot(rs.row);
+            rs.first = stage_slot(rs.row);
             if (st < 0 || st >= g.n) {
               atomicOr(err, DEVERR_START);
               stage_fill_minus_one(obuf, tid, rs, 0, J.len + 1);
@@ -528,7 +530,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
                                                       unsigned long long* __restrict__ qctr,
                                                       unsigned* __restrict__ err, DevCounters* __restrict__ cnt) {
   __shared__ Job sj[NJ];
-  __shared__ int32_t obuf[8 * kBlock];
+  __shared__ int32_t obuf[kStageSlots * kBlock];
   load_jobs(tab.jobs, njobs, sj);
   __syncthreads();
   LaneCounters lc;
