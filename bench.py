@@ -801,7 +801,7 @@ def main():
                    "wall_s": wall},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic_per_launch,
-                     "peak_kind": peak_kind, "kernel": "walk_kernel<1,false>",
+                     "peak_kind": peak_kind, "kernel": "walk_kernel<1, 0, 1> (single job, uncounted, node2vec)",
                      "algorithmic_bytes_per_launch": bytes_per_step / len(PQ),
                      "avg_launch_ms": kern_ms / len(PQ)},
         "roofline_random_access": {
