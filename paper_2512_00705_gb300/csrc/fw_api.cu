@@ -188,7 +188,7 @@ fw_status rebuild_derived(fw_graph* g, cudaStream_t st) {
   if (le == cudaSuccess) le = launch_edge_records(g->d_col, g->d_h, g->d_lab, g->d_nrec, e, g->d_erec, g->num_sms, st);
   if (le == cudaSuccess && g->d_cerec)
     le = launch_class_group(g->d_off, g->d_h, g->d_nrec, g->d_erec, n, g->d_cerec, g->num_sms, st);
-  if (le == cudaSuccess) le = launch_symmetry(g->d_off, g->d_col, g->d_h, n, d_asym, g->num_sms, st);
+  if (le == cudaSuccess) le = launch_symmetry(g->d_off, g->d_col, g->d_h, n, e, d_asym, g->num_sms, st);
   if (le == cudaSuccess && build_bloom) le = launch_bloom(g->d_off, g->d_col, n, e, g->d_bloom, g->num_sms, st);
   if (le == cudaSuccess && want_labels)
     le = launch_label_stats(g->d_off, g->d_h, g->d_lab, n, g->d_lstat, d_lbad, g->num_sms, st);

@@ -99,8 +99,8 @@ cudaError_t launch_class_group(const int32_t* off, const float* h, const int4* n
 cudaError_t launch_label_group(const int32_t* off, const int32_t* col, const float* h, const uint8_t* lab,
                                const int4* nrec, const float2* lstat, int32_t n, int4* lrec, int4* gerec, float* gh,
                                int num_sms, cudaStream_t stream);
-cudaError_t launch_symmetry(const int32_t* off, const int32_t* col, const float* h, int32_t n, unsigned* flag,
-                            int num_sms, cudaStream_t stream);
+cudaError_t launch_symmetry(const int32_t* off, const int32_t* col, const float* h, int32_t n, long long e,
+                            unsigned* flag, int num_sms, cudaStream_t stream);
 cudaError_t launch_quantize(float* h, long long e, uint8_t* codes, float* scale_out, unsigned* maxbits, int num_sms,
                             cudaStream_t stream);
 cudaError_t launch_dequantize(const uint8_t* codes, long long e, float scale, float* h, int num_sms, cudaStream_t stream);

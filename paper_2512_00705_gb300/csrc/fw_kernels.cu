@@ -359,30 +359,32 @@ cudaError_t launch_edge_records(const int32_t* col, const float* h, const uint8_
 }
 
 // Sets *flag if some edge (v, u) has no mirror (u, v) with the same weight.
+// Weight symmetry: does every entry (v, u) have a mirror (u, v) of the same
+// weight?  One thread per entry (a node-per-warp split leaves the hub rows'
+// warps running long after the rest); the entry's row v comes from a binary
+// search of the offsets (L2-resident), its mirror from a search of row u.
 __global__ void symmetry_kernel(const int32_t* __restrict__ off, const int32_t* __restrict__ col,
-                                const float* __restrict__ h, int32_t n, unsigned* __restrict__ flag) {
-  const int lane = threadIdx.x & 31;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long v = warp; v < n; v += nwarps) {
-    const int32_t s = off[v], e = off[v + 1];
-    bool bad = false;
-    for (int32_t i = s + lane; i < e; i += 32) {
-      const int32_t u = col[i];
-      uint32_t pb = 0;
-      const int32_t j = row_find(col, off[u], off[u + 1], (int32_t)v, n, pb);
-      if (j < 0 || (h && h[j] != h[i])) bad = true;
+                                const float* __restrict__ h, int32_t n, long long e, unsigned* __restrict__ flag) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < e; i += (long long)gridDim.x * blockDim.x) {
+    int32_t lo = 0, hi = n;  // last v with off[v] <= i
+    while (hi - lo > 1) {
+      const int32_t mid = (lo + hi) >> 1;
+      if (__ldg(off + mid) <= i) lo = mid;
+      else hi = mid;
     }
-    if (bad) atomicOr(flag, 1u);
+    const int32_t u = col[i];
+    uint32_t pb = 0;
+    const int32_t j = row_find(col, off[u], off[u + 1], lo, n, pb);
+    if (j < 0 || (h && h[j] != h[i])) atomicOr(flag, 1u);
   }
 }
 
-cudaError_t launch_symmetry(const int32_t* off, const int32_t* col, const float* h, int32_t n, unsigned* flag,
-                            int num_sms, cudaStream_t stream) {
-  if (n == 0) return cudaSuccess;
-  const long long want = ((long long)n * 32 + 255) / 256;
-  const int grid = (int)(want < (long long)num_sms * 8 ? want : (long long)num_sms * 8);
-  symmetry_kernel<<<grid, 256, 0, stream>>>(off, col, h, n, flag);
+cudaError_t launch_symmetry(const int32_t* off, const int32_t* col, const float* h, int32_t n, long long e,
+                            unsigned* flag, int num_sms, cudaStream_t stream) {
+  if (n == 0 || e == 0) return cudaSuccess;
+  const long long want = (e + 255) / 256;
+  const int grid = (int)(want < (long long)num_sms * 16 ? want : (long long)num_sms * 16);
+  symmetry_kernel<<<grid, 256, 0, stream>>>(off, col, h, n, e, flag);
   g_launches.fetch_add(1);
   return cudaGetLastError();
 }

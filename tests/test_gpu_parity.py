@@ -219,6 +219,27 @@ def test_metapath_every_label_distributions(small, mode, flags):
             assert tv_distance(counts, probs) < 3e-3, (v, lab)
 
 
+@pytest.mark.parametrize("algo,p,q", [("weighted", 1.0, 1.0), ("node2vec", 0.25, 4.0), ("node2vec", 4.0, 0.25),
+                                      ("node2vec", 2.0, 4.0), ("pagerank2", 1.0, 1.0)])
+def test_weight_class_envelopes_with_skewed_weights(algo, p, q):
+    """eRJS with the weight-class envelope (default) and with the paper's
+    uniform proposal (FW_FLAG_PLAIN_RJS) on lognormal(0, 1.5) weights, where
+    every class is well populated and the split proposals' mixture weights
+    depend on the class counts: both follow the oracle's probabilities."""
+    g = synth.workload_graph("small")
+    g.h = synth.edge_weights(g, "lognormal", 1.5, seed=13)
+    G = fw.Graph(g)
+    for (v, vp, step) in _states(g):
+        probs = oracle.transition_probs(g, v, vp, step, algo, p, q)
+        for flags in (0, fw.FLAG_PLAIN_RJS):
+            counts = G.sample_hist(v, vp, step, algo, 2_000_000, p=p, q=q, mode="rjs", flags=flags,
+                                   seed=31 + v + flags).cpu().numpy()
+            assert counts.sum() == 2_000_000
+            assert chisq_pvalue(counts, probs) > 1e-4, (v, vp, flags)
+            assert tv_distance(counts, probs) < 3e-3, (v, vp, flags)
+    G.close()
+
+
 def test_worked_example_distribution():
     """Fig. 2: weights {3,2,4,1} -> {0.3,0.2,0.4,0.1} for every mode."""
     g = synth.from_edges(5, [(0, 1), (0, 2), (0, 3), (0, 4)], h=[3.0, 2.0, 4.0, 1.0])
