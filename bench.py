@@ -801,6 +801,12 @@ def main():
                    "wall_s": wall},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic_per_launch,
+                     # DRAM bytes ncu measured per launch over the same launch time: the bandwidth the
+                     # random gathers actually draw (each 32-byte access fetches 64-128 bytes)
+                     "traffic_GBps": (traffic_per_launch / (kern_ms / len(PQ) / 1000.0) / 1e9
+                                      if traffic_per_launch else None),
+                     "traffic_frac": (traffic_per_launch / (kern_ms / len(PQ) / 1000.0) / 1e9 / peak
+                                      if traffic_per_launch else None),
                      "peak_kind": peak_kind, "kernel": "walk_kernel<1, 0, 1> (single job, uncounted, node2vec)",
                      "algorithmic_bytes_per_launch": bytes_per_step / len(PQ),
                      "avg_launch_ms": kern_ms / len(PQ)},
