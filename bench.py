@@ -69,6 +69,8 @@ def parse():
                     "(fw_graph_quantize_weights) before tuning and timing")
     ap.add_argument("--duration", type=float, default=10.0, help="serve suite: seconds of offered load")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve suite: mean arrivals per second")
+    ap.add_argument("--no-serial", action="store_true", help="serve suite: skip the serial comparison (for "
+                    "arrival rates far above what serial calls sustain, e.g. capacity runs)")
     a = ap.parse_args()
     global PQ
     if a.pq:
@@ -389,11 +391,20 @@ def run_serve(args):
             d["schema"] = [0, 1, 2, 3, 4]
         return a, d
 
+    from collections import deque
+    from concurrent.futures import ThreadPoolExecutor
+    counter = ThreadPoolExecutor(max_workers=8)  # hop counting off the submit / poll loop
+
+    def row_hops(rows):
+        # -1 marks the steps after a dead end; the start column is never -1
+        return rows.shape[0] * (rows.shape[1] - 1) - int(np.count_nonzero(rows[:, 1:] < 0))
+
     def run(mode, count):
         lat = np.zeros(count)
         hops = [0]
         head = [0]
         inflight = []  # (index, ring start, words, ticket, submit lag)
+        counting = deque()  # (ring start, words, future of the hop count)
         srv = fw.Server(G, mem_budget=8 << 30, max_waves=4) if mode == "server" else None
 
         def reap(block):
@@ -406,8 +417,13 @@ def run_serve(args):
                         return
                     lat[i] = lag + r / 1e3
                 rows = ring[off:off + words].reshape(W[i], Ls[i] + 1)
-                hops[0] += int((rows[:, 1:] >= 0).sum())
+                counting.append((off, words, counter.submit(row_hops, rows)))
                 inflight.pop(0)
+
+        def drain_counts(lo, hi):
+            # finish the hop counts of ring ranges that start in [lo, hi) (hi = None: all)
+            while counting and (hi is None or lo <= counting[0][0] < hi):
+                hops[0] += counting.popleft()[2].result()
 
         t_base = time.perf_counter()
         for i in range(count):
@@ -419,6 +435,7 @@ def run_serve(args):
                 head[0] = 0
             while inflight and head[0] <= inflight[0][1] < head[0] + words:
                 reap(True)
+            drain_counts(head[0], head[0] + words)
             off = head[0]
             head[0] += words
             st = starts_pool[(i * 7919) % (pool_words - W[i]):][:W[i]]
@@ -434,6 +451,7 @@ def run_serve(args):
                 inflight.append((i, off, words, None, lag))
                 reap(True)
         reap(True)
+        drain_counts(0, None)
         stats = None
         if srv is not None:
             stats = srv.stats()
@@ -442,7 +460,7 @@ def run_serve(args):
         return lat * 1e3, hops[0], wall, stats
 
     run("server", min(n_req, 400))  # warm-up (module load, arena, caches), discarded
-    res = {m: run(m, n_req) for m in ("server", "serial")}
+    res = {m: run(m, n_req) for m in (("server",) if args.no_serial else ("server", "serial"))}
     out = {}
     for m, (lat, hops, wall, stats) in res.items():
         out[m] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
@@ -458,7 +476,7 @@ def run_serve(args):
                    "cost_ratios": ratios,
                    "offered_walker_steps_per_s": float((W * Ls).sum() / args.duration)},
         "serving": out,
-        "p99_server_over_serial": out["server"]["p99_ms"] / out["serial"]["p99_ms"]})
+        "p99_server_over_serial": (out["server"]["p99_ms"] / out["serial"]["p99_ms"]) if "serial" in out else None})
     G.close()
 
 
