@@ -69,6 +69,7 @@ def parse():
                     "(fw_graph_quantize_weights) before tuning and timing")
     ap.add_argument("--duration", type=float, default=10.0, help="serve suite: seconds of offered load")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve suite: mean arrivals per second")
+    ap.add_argument("--max-waves", type=int, default=4, help="serve suite: concurrent waves (streams) of the server")
     ap.add_argument("--no-serial", action="store_true", help="serve suite: skip the serial comparison (for "
                     "arrival rates far above what serial calls sustain, e.g. capacity runs)")
     a = ap.parse_args()
@@ -405,7 +406,7 @@ def run_serve(args):
         head = [0]
         inflight = []  # (index, ring start, words, ticket, submit lag)
         counting = deque()  # (ring start, words, future of the hop count)
-        srv = fw.Server(G, mem_budget=8 << 30, max_waves=4) if mode == "server" else None
+        srv = fw.Server(G, mem_budget=8 << 30, max_waves=args.max_waves) if mode == "server" else None
 
         def reap(block):
             # collect finished queries in submission order; latency = submit lag + submit-to-done
@@ -473,7 +474,7 @@ def run_serve(args):
         "ms_per_step": None, "higher_is_better": True,
         "config": {"workload": f"Poisson {args.rate:g}/s for {args.duration:g} s on R-MAT s22; W log-U[1,1e5], "
                                "L U{10..100}, node2vec(2,.5)/metapath/weighted", "queries": n_req,
-                   "cost_ratios": ratios,
+                   "cost_ratios": ratios, "max_waves": args.max_waves,
                    "offered_walker_steps_per_s": float((W * Ls).sum() / args.duration)},
         "serving": out,
         "p99_server_over_serial": (out["server"]["p99_ms"] / out["serial"]["p99_ms"]) if "serial" in out else None})
