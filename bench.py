@@ -767,7 +767,7 @@ def main():
         starts_h = starts.cpu().pin_memory()
         out_h = torch.empty((nw, LENGTH + 1), dtype=torch.int32).pin_memory()
         e2e_ms = []
-        for i in range(2 + max(2, args.steps // 2)):
+        for i in range(2 + max(4, args.steps)):  # 2 warm-up steps, then the median of the rest
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for (p, q) in PQ:
@@ -784,10 +784,11 @@ def main():
         assert torch.equal(out.cpu(), out_h), "host-buffer walk differs from device walk"
         e2e_ms_all = sharding.max_over_ranks(e2e_step)
         e2e_line = {"value": hops_all / (e2e_ms_all / 1000.0), "unit": "walker-steps/s",
-                    "h2d_bytes_per_step": len(PQ) * nw * 4, "d2h_bytes_per_step": len(PQ) * nw * (LENGTH + 1) * 4}
+                    "h2d_bytes_per_step": len(PQ) * nw * 4, "d2h_bytes_per_step": len(PQ) * nw * (LENGTH + 1) * 4,
+                    "ms_per_step": e2e_step, "ms_per_step_min_max": [min(e2e_ms), max(e2e_ms)]}
 
     # ---- random-access ceiling of the device memory (the walk kernel's operative roof):
-    # dependent 32-byte gathers over a 4 GiB table, the walk kernel's launch shape
+    # dependent 32-byte gathers over a 4 GiB table
     table = torch.empty(4 << 30, dtype=torch.uint8, device=dev)
     gather_ceiling = fw.fw_gather_ceiling(table)
     del table
