@@ -10,8 +10,11 @@
 //      queue waits for memory rather than being overtaken, so large queries
 //      are not starved;
 //   3. launches the admitted queries as one wave on a free stream: upload of
-//      each query's starts, one batched walk launch (up to 64 queries, one
-//      shared walker queue), download of each query's rows, an event.
+//      each query's starts, one batched walk (up to 64 queries; one launch
+//      per algorithm present, each algorithm's queries one shared walker
+//      queue), download of each query's rows, an event.  The CUDA calls run
+//      without the server lock, so submitting and polling threads are not
+//      held up by them.
 // Waves on different streams overlap on the device, and queries that arrive
 // while waves run join the next wave: continuous batching.  A query's rows
 // are identical to those of fw_walk_host with the same arguments, alone or
@@ -137,21 +140,20 @@ void finish(fw_server* s, Request* r, fw_status st, const std::string& err) {
   }
 }
 
-// Enqueue one wave (called with the lock held).
-void launch_wave(fw_server* s, Wave& w) {
+// Enqueue the GPU work of one wave: stage the starts, walk (one launch per
+// algorithm present), copy the rows out, record the wave's event.  Called
+// WITHOUT the server lock, so submit / poll are not held up by the CUDA
+// calls: it only reads the requests' immutable fields and uses the wave,
+// which the worker reserved.  Returns the first failing CUDA call's error.
+cudaError_t enqueue_wave(fw_server* s, Wave& w, const std::vector<Request*>& batch) {
   using namespace fw;
   std::vector<Job> tab;
+  tab.reserve(batch.size());
   long long total = 0;
   cudaError_t e = cudaSuccess;
-  std::string err;
-  for (Request* r : s->admitted) {
+  for (Request* r : batch) {
     Job J;
-    fw_status st = make_job(s->g, r->algo, &r->params, r->seed, &J);
-    if (st != FW_OK) {  // validated at submit; kept for safety
-      s->arena->release(r->arena_off, r->bytes);
-      finish(s, r, st, fw_last_error());
-      continue;
-    }
+    if (make_job(s->g, r->algo, &r->params, r->seed, &J) != FW_OK) return cudaErrorInvalidValue;  // checked at submit
     int32_t* d_starts = reinterpret_cast<int32_t*>(s->arena_mem + r->arena_off);
     int32_t* d_out = reinterpret_cast<int32_t*>(s->arena_mem + r->arena_off + r->rows_off);
     J.kind = JOB_WALK;
@@ -165,32 +167,41 @@ void launch_wave(fw_server* s, Wave& w) {
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(d_starts, r->starts, sizeof(int32_t) * (size_t)r->num_walkers, cudaMemcpyHostToDevice,
                           w.stream);
-    r->state = REQ_LAUNCHED;
-    w.reqs.push_back(r);
   }
-  s->admitted.clear();
-  if (w.reqs.empty()) return;
   if (e == cudaSuccess) e = cudaMemsetAsync(w.qctr, 0, sizeof(unsigned long long) * kQueueCounters, w.stream);
   if (e == cudaSuccess && total > 0) e = launch_walk(s->g, tab.data(), (int)tab.size(), total, false, w.qctr, w.stream);
-  for (Request* r : w.reqs) {
+  for (Request* r : batch) {
     if (e != cudaSuccess) break;
     e = cudaMemcpyAsync(r->out, s->arena_mem + r->arena_off + r->rows_off,
                         sizeof(int32_t) * (size_t)r->num_walkers * ((size_t)r->len + 1), cudaMemcpyDeviceToHost,
                         w.stream);
   }
   if (e == cudaSuccess) e = cudaEventRecord(w.done, w.stream);
+  if (e != cudaSuccess) cudaStreamSynchronize(w.stream);  // let what was enqueued finish before its memory is reused
+  return e;
+}
+
+// Launch the admitted queries as one wave on the free wave w.  Called and
+// returns with the lock held; drops it around the CUDA calls.
+void launch_wave(fw_server* s, Wave& w, std::unique_lock<std::mutex>& lk) {
+  std::vector<Request*> batch;
+  batch.swap(s->admitted);
+  for (Request* r : batch) r->state = REQ_LAUNCHED;
+  w.busy = true;  // reserved: no other launch takes this wave meanwhile
+  lk.unlock();
+  const cudaError_t e = enqueue_wave(s, w, batch);
+  lk.lock();
   if (e != cudaSuccess) {
-    cudaStreamSynchronize(w.stream);  // let whatever was enqueued finish before its memory is reused
     const std::string msg = std::string("wave launch: ") + cudaGetErrorString(e);
-    for (Request* r : w.reqs) {
+    for (Request* r : batch) {
       s->arena->release(r->arena_off, r->bytes);
       finish(s, r, FW_ERR_CUDA, msg);
     }
-    w.reqs.clear();
+    w.busy = false;
     s->cv_done.notify_all();
     return;
   }
-  w.busy = true;
+  w.reqs = std::move(batch);
   s->waves_launched++;
   s->queries_in_waves += w.reqs.size();
 }
@@ -236,7 +247,7 @@ void worker_main(fw_server* s) {
     if (!s->admitted.empty()) {
       for (Wave& w : s->waves) {
         if (w.busy) continue;
-        launch_wave(s, w);
+        launch_wave(s, w, lk);
         if (w.busy) ++inflight;
         progress = true;
         break;
