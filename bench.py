@@ -89,8 +89,9 @@ def measured_peaks():
 
 
 def source_digest():
+    """Digest of the walk kernel's sources (profiles of the kernel are keyed to it)."""
     from paper_2512_00705_gb300 import _build
-    return _build._inputs_digest()[:16]
+    return _build.walk_kernel_digest()[:16]
 
 
 def read_traffic():

@@ -48,6 +48,25 @@ def _inputs_digest() -> str:
     return h.hexdigest()
 
 
+# The files that define the walk kernel and the device data it reads (records,
+# filters, label-grouped view): profiles of the kernel are keyed to their digest.
+WALK_KERNEL_FILES = ["fw_device.cuh", "fw_walk.cuh", "fw_kernels.cu", "fw_walk_mixed.cu", "fw_internal.h", "fw_api.cu"]
+
+
+def walk_kernel_digest() -> str:
+    """Digest of the walk kernel's sources, the public header and the nvcc
+    flags (repository root factored out): a recorded profile of the walk
+    kernel applies while this is unchanged."""
+    h = hashlib.sha256()
+    paths = [os.path.join(CSRC, f) for f in WALK_KERNEL_FILES] + [os.path.join(ROOT, "include", "flexiwalk.h")]
+    for path in paths:
+        h.update(os.path.basename(path).encode())
+        with open(path, "rb") as fh:
+            h.update(fh.read())
+    h.update(" ".join(ARCH + NVCC_FLAGS).replace(ROOT, "<root>").encode())
+    return h.hexdigest()
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile every .cu under csrc/ and link libflexiwalk.so; returns its path.
     Skips the work when the sources are unchanged since the last build."""
