@@ -104,9 +104,38 @@ def test_hub_distributions_s22(s22, mode, flags, ndraws):
         assert tv_distance(counts, probs) < bound, (v, vp, algo, p, q)
 
 
-def test_exact_mode_full_s23_metapath_sampled_rows():
+@pytest.fixture(scope="module")
+def s23():
     g = synth.workload_graph("s23_meta")
     G = fw.Graph(g)
+    yield g, G
+    G.close()
+
+
+@pytest.mark.parametrize("mode,flags,hub_too", [("rjs", 0, True), ("auto", 0, True), ("rjs", fw.FLAG_NO_GROUPS, True),
+                                                 ("rvs", 0, False)])
+def test_hub_label_distributions_s23(s23, mode, flags, hub_too):
+    """Metapath at the largest hub of R-MAT s23 (lognormal(0,1) weights, where
+    the five weight classes of a label segment matter most) and at a node of
+    degree ~1000, for every required label: the label-grouped sampler (and the
+    whole-row sampler) against the oracle, 4e6 draws.  eRVS-only runs at the
+    smaller node alone (a hub scan per draw would take minutes)."""
+    g, G = s23
+    deg = g.degrees()
+    hub = int(np.argmax(deg))
+    mid = int(np.argmin(np.abs(deg - 1000)))
+    for v in ((hub, mid) if hub_too else (mid,)):
+        for lab in range(5):
+            probs = oracle.transition_probs(g, v, -1, 0, "metapath", schema=[lab])
+            counts = G.sample_hist(v, -1, 0, "metapath", 4_000_000, schema=[lab], mode=mode, flags=flags,
+                                   seed=91 + v + lab).cpu().numpy()
+            assert counts.sum() == 4_000_000
+            assert chisq_pvalue(counts, probs) > 1e-4, (v, lab)
+            assert tv_distance(counts, probs) < 2e-3, (v, lab)
+
+
+def test_exact_mode_full_s23_metapath_sampled_rows(s23):
+    g, G = s23
     starts_h = synth.random_starts(g.n, 2_000_000, seed=43)
     starts = torch.from_numpy(starts_h).cuda()
     schema = [0, 1, 2, 3, 4]
@@ -126,4 +155,3 @@ def test_exact_mode_full_s23_metapath_sampled_rows():
         assert np.all(keys[pos] == q_)
         hop = np.broadcast_to(np.arange(L), alive.shape)[alive]
         assert np.all(g.labels[pos] == np.asarray(schema)[hop % 5])
-    G.close()
