@@ -9,6 +9,7 @@ from __future__ import annotations
 import glob
 import hashlib
 import os
+import re
 import subprocess
 import sys
 from concurrent.futures import ThreadPoolExecutor
@@ -53,16 +54,24 @@ def _inputs_digest() -> str:
 WALK_KERNEL_FILES = ["fw_device.cuh", "fw_walk.cuh", "fw_kernels.cu", "fw_walk_mixed.cu", "fw_internal.h", "fw_api.cu"]
 
 
+def _code_only(text: str) -> str:
+    """C/C++ source without comments and with runs of whitespace collapsed
+    (the sources hold no string literals with comment markers)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def walk_kernel_digest() -> str:
-    """Digest of the walk kernel's sources, the public header and the nvcc
-    flags (repository root factored out): a recorded profile of the walk
-    kernel applies while this is unchanged."""
+    """Digest of the walk kernel's code (comments and layout ignored), the
+    public header and the nvcc flags (repository root factored out): a
+    recorded profile of the walk kernel applies while this is unchanged."""
     h = hashlib.sha256()
     paths = [os.path.join(CSRC, f) for f in WALK_KERNEL_FILES] + [os.path.join(ROOT, "include", "flexiwalk.h")]
     for path in paths:
         h.update(os.path.basename(path).encode())
-        with open(path, "rb") as fh:
-            h.update(fh.read())
+        with open(path, encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     h.update(" ".join(ARCH + NVCC_FLAGS).replace(ROOT, "<root>").encode())
     return h.hexdigest()
 

@@ -5,7 +5,11 @@
 // with w from Eq. (node2vec), the MetaPath label rule, or w = 1 (weighted).
 //   * eRJS   [Sec. 3.3]: propose X uniform over N(v), accept iff U*B < w~(X),
 //            B = max(w) * h_MAX[v] >= max w~ (the proof in Sec. 3.3 shows the
-//            accepted value follows p for any such bound).
+//            accepted value follows p for any such bound).  Refined envelopes
+//            keep that argument: X proposed in proportion to a per-entry
+//            bound (weight classes of h), or from a mixture of components
+//            each proposed and accepted against its own bound (return edge,
+//            common neighbours, label segments); see rjs_trials.
 //   * eRVS   [Sec. 3.2, Alg. 1, Eq. (jump)]: exponential keys
 //            K_i = ln(u_i) / w~_i (the log of u_i^(1/w~_i)), argmax wins;
 //            with jumps, a lane skips items until its cumulative weight passes
