@@ -1,14 +1,13 @@
-// fw_batch.cu -- many walk jobs in one persistent launch, and a CUDA-graph
-// plan that replays such a launch.
+// fw_batch.cu -- many walk jobs per launch, and a CUDA-graph plan that
+// replays such a batch.
 //
 // A batch is a table of up to 64 jobs of any sizes, lengths, algorithms and
-// parameters walked by one persistent launch of the batch kernel
-// (fw_walk_mixed.cu): the jobs of one algorithm form one walker queue, and
-// warps run algorithm-specialised walk loops queue after queue, so small
-// jobs do not leave the GPU idle and long jobs do not hold a launch of their
-// own.  Each job's rows equal those of a separate fw_walk call with the same
-// arguments: every random draw and every sampler choice depends only on the
-// walker's own job.
+// parameters (fw_walk_mixed.cu): the jobs of one algorithm form one walker
+// queue walked by one persistent launch of the kernel compiled for that
+// algorithm, so small jobs do not leave the GPU idle and long jobs do not
+// hold a launch of their own.  Each job's rows equal those of a separate
+// fw_walk call with the same arguments: every random draw and every sampler
+// choice depends only on the walker's own job.
 #include <vector>
 
 #include "fw_internal.h"
