@@ -12,11 +12,15 @@
  *                  [Eq. (node2vec); the paper writes a, b for p, q]
  *       metapath : w = 1 if label(v,u) = schema[hop mod S], else 0  [Sec. 2.1]
  *       weighted : w = 1  (static walk)  [Sec. 2.1]
+ *       second-order PageRank : see FW_ALGO_PAGERANK2  [Eq. (2ndpr)]
  *   - The draw is made by eRJS (rejection against the on-the-fly bound
- *     B = max(w) * h_MAX[v], [Sec. 3.3]) or by eRVS (single-pass reservoir
- *     sampling with exponential keys and jumps, [Sec. 3.2, Alg. 1,
- *     Eq. (jump)]); a first-order cost model picks eRJS iff
- *     r * B < sum-hat, with sum-hat = h_SUM[v] * mean(w)
+ *     B = max(w) * h_MAX[v], [Sec. 3.3]; by default with refined envelopes
+ *     that keep the draw exact: three weight classes of h, the return edge
+ *     and common neighbours proposed separately, label segments for
+ *     metapath -- FW_FLAG_PLAIN_RJS keeps the single uniform proposal) or
+ *     by eRVS (single-pass reservoir sampling with exponential keys and
+ *     jumps, [Sec. 3.2, Alg. 1, Eq. (jump)]); a first-order cost model
+ *     picks eRJS iff r * B < sum-hat, with sum-hat = h_SUM[v] * mean(w)
  *     [Sec. 4.1, Eq. (runtime), Eq. (sum_estimation)].
  *   - An exact inverse-CDF mode (FP32 prefix in neighbour order, one
  *     Philox4x32-10 uniform per hop) reproduces a plain CPU definition bit
