@@ -240,6 +240,32 @@ def test_weight_class_envelopes_with_skewed_weights(algo, p, q):
     G.close()
 
 
+@pytest.mark.parametrize("algo,p,q", [("node2vec", 0.25, 4.0), ("node2vec", 4.0, 0.25), ("pagerank2", 1.0, 1.0),
+                                      ("weighted", 1.0, 1.0)])
+@pytest.mark.parametrize("how", ["flag", "no-weights"])
+def test_unweighted_fast_mode_distributions(small, algo, p, q, how):
+    """h = 1, either by FW_FLAG_UNWEIGHTED on the weighted graph or on a
+    graph created without weights (no weight classes, no class-ordered
+    records): eRJS and the cost model against the oracle's unweighted
+    probabilities."""
+    g, G = small
+    gu = synth.Csr(g.offsets, g.cols)
+    if how == "flag":
+        Gx, flags = G, fw.FLAG_UNWEIGHTED
+    else:
+        Gx, flags = fw.Graph(gu), 0
+    for (v, vp, step) in _states(g)[::2]:
+        probs = oracle.transition_probs(gu, v, vp, step, algo, p, q)
+        for mode in ("rjs", "auto"):
+            counts = Gx.sample_hist(v, vp, step, algo, 2_000_000, p=p, q=q, mode=mode, flags=flags,
+                                    seed=51 + v).cpu().numpy()
+            assert counts.sum() == 2_000_000
+            assert chisq_pvalue(counts, probs) > 1e-4, (v, vp, mode)
+            assert tv_distance(counts, probs) < 3e-3, (v, vp, mode)
+    if how != "flag":
+        Gx.close()
+
+
 def test_worked_example_distribution():
     """Fig. 2: weights {3,2,4,1} -> {0.3,0.2,0.4,0.1} for every mode."""
     g = synth.from_edges(5, [(0, 1), (0, 2), (0, 3), (0, 4)], h=[3.0, 2.0, 4.0, 1.0])
