@@ -41,3 +41,10 @@ def read_golden(name):
             if line and not line.startswith("#"):
                 rows.append(line.split())
     return rows
+
+
+def pytest_terminal_summary(terminalreporter):
+    sc = sys.modules.get("statcheck")
+    line = sc.summary() if sc is not None else None
+    if line:
+        terminalreporter.write_line(line)

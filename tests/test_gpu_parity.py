@@ -2,8 +2,9 @@
 
 Exact mode must equal the oracle's walks bit for bit; the fast modes (eRJS,
 eRVS with and without jumps, cost-model auto) must reproduce the oracle's
-exact per-step distributions (chi-square p > 1e-4 and TV < 2e-3 at >= 4e6
-draws for non-hub states) and keep the walk invariants."""
+exact per-step distributions (per state: chi-square p > 0.01 and TV < 2e-3
+over 25 merged bins at >= 2e6 draws, with one redraw on fresh seeds, see
+statcheck.assert_follows) and keep the walk invariants."""
 import numpy as np
 import pytest
 
@@ -11,7 +12,7 @@ import oracle
 from paper_2512_00705_gb300 import flexiwalk as fw
 from paper_2512_00705_gb300 import synth
 from bruteforce import bf_paths, merged_chisquare
-from statcheck import chisq_pvalue, tv_distance
+from statcheck import assert_follows, assert_pvalue_follows
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -186,16 +187,12 @@ def test_fast_mode_distributions(small, mode, flags, algo, p, q, schema):
     ndraws = 4_000_000
     for (v, vp, step) in _states(g):
         probs = oracle.transition_probs(g, v, vp, step, algo, p, q, schema)
-        counts = G.sample_hist(v, vp, step, algo, ndraws, p=p, q=q, schema=schema, mode=mode, flags=flags,
-                               seed=1234 + v).cpu().numpy()
+        draw = lambda k: G.sample_hist(v, vp, step, algo, ndraws, p=p, q=q, schema=schema, mode=mode, flags=flags,
+                                       seed=1234 + v + 7919 * k).cpu().numpy()
         if probs.sum() == 0:
-            assert counts.sum() == 0
+            assert draw(0).sum() == 0
             continue
-        assert counts.sum() == ndraws
-        pv = chisq_pvalue(counts, probs)
-        tv = tv_distance(counts, probs)
-        assert pv > 1e-4, (v, vp, step, pv)
-        assert tv < 2e-3, (v, vp, step, tv)
+        assert_follows(draw, probs, (algo, p, q, mode, flags, v, vp, step), ndraws)
 
 
 @pytest.mark.parametrize("mode,flags", [("rjs", 0), ("rvs", 0), ("rvs", fw.FLAG_RVS_NOJUMP), ("auto", 0),
@@ -209,14 +206,12 @@ def test_metapath_every_label_distributions(small, mode, flags):
     for (v, vp, step) in _states(g)[::2]:
         for lab in range(5):
             probs = oracle.transition_probs(g, v, -1, step, "metapath", schema=[lab])
-            counts = G.sample_hist(v, -1, step, "metapath", ndraws, schema=[lab], mode=mode, flags=flags,
-                                   seed=77 + v + lab).cpu().numpy()
+            draw = lambda k: G.sample_hist(v, -1, step, "metapath", ndraws, schema=[lab], mode=mode, flags=flags,
+                                           seed=77 + v + lab + 7919 * k).cpu().numpy()
             if probs.sum() == 0:
-                assert counts.sum() == 0
+                assert draw(0).sum() == 0
                 continue
-            assert counts.sum() == ndraws
-            assert chisq_pvalue(counts, probs) > 1e-4, (v, lab)
-            assert tv_distance(counts, probs) < 3e-3, (v, lab)
+            assert_follows(draw, probs, ("metapath", mode, flags, v, lab), ndraws)
 
 
 @pytest.mark.parametrize("algo,p,q", [("weighted", 1.0, 1.0), ("node2vec", 0.25, 4.0), ("node2vec", 4.0, 0.25),
@@ -232,11 +227,9 @@ def test_weight_class_envelopes_with_skewed_weights(algo, p, q):
     for (v, vp, step) in _states(g):
         probs = oracle.transition_probs(g, v, vp, step, algo, p, q)
         for flags in (0, fw.FLAG_PLAIN_RJS):
-            counts = G.sample_hist(v, vp, step, algo, 2_000_000, p=p, q=q, mode="rjs", flags=flags,
-                                   seed=31 + v + flags).cpu().numpy()
-            assert counts.sum() == 2_000_000
-            assert chisq_pvalue(counts, probs) > 1e-4, (v, vp, flags)
-            assert tv_distance(counts, probs) < 3e-3, (v, vp, flags)
+            draw = lambda k: G.sample_hist(v, vp, step, algo, 2_000_000, p=p, q=q, mode="rjs", flags=flags,
+                                           seed=31 + v + flags + 7919 * k).cpu().numpy()
+            assert_follows(draw, probs, (algo, p, q, flags, v, vp), 2_000_000)
     G.close()
 
 
@@ -257,11 +250,9 @@ def test_unweighted_fast_mode_distributions(small, algo, p, q, how):
     for (v, vp, step) in _states(g)[::2]:
         probs = oracle.transition_probs(gu, v, vp, step, algo, p, q)
         for mode in ("rjs", "auto"):
-            counts = Gx.sample_hist(v, vp, step, algo, 2_000_000, p=p, q=q, mode=mode, flags=flags,
-                                    seed=51 + v).cpu().numpy()
-            assert counts.sum() == 2_000_000
-            assert chisq_pvalue(counts, probs) > 1e-4, (v, vp, mode)
-            assert tv_distance(counts, probs) < 3e-3, (v, vp, mode)
+            draw = lambda k: Gx.sample_hist(v, vp, step, algo, 2_000_000, p=p, q=q, mode=mode, flags=flags,
+                                            seed=51 + v + 7919 * k).cpu().numpy()
+            assert_follows(draw, probs, (algo, p, q, how, mode, v, vp), 2_000_000)
     if how != "flag":
         Gx.close()
 
@@ -286,9 +277,9 @@ def test_rjs_bound_invariance(small):
     v = int(np.argmax(deg))
     probs = oracle.transition_probs(g, v, -1, 0, "weighted")
     for cap in [1, 2, 1000]:
-        counts = G.sample_hist(v, -1, 0, "weighted", 4_000_000, mode="rjs", rjs_cap=cap, seed=5).cpu().numpy()
-        assert chisq_pvalue(counts, probs) > 1e-4
-        assert tv_distance(counts, probs) < 2e-3
+        draw = lambda k: G.sample_hist(v, -1, 0, "weighted", 4_000_000, mode="rjs", rjs_cap=cap,
+                                       seed=5 + 7919 * k).cpu().numpy()
+        assert_follows(draw, probs, ("rjs cap", cap), 4_000_000)
 
 
 def test_dead_end_states(small):
@@ -392,10 +383,11 @@ def test_fast_walk_path_distribution(graph, mode, flags, algo, p, q, schema):
     assert G.info["symmetric"] == (0 if graph == "sparse-asym" else 1)
     W, start = 300_000, 0
     starts = torch.full((W,), start, dtype=torch.int32, device="cuda")
-    out = G.walk(starts, L, algo, p=p, q=q, schema=schema, mode=mode, flags=flags, seed=17).cpu().numpy()
-    G.close()
     bf = bf_paths(g, start, L, algo, p, q, schema)
-    assert merged_chisquare(bf, out) > 1e-4
+    assert_pvalue_follows(lambda k: merged_chisquare(bf, G.walk(starts, L, algo, p=p, q=q, schema=schema, mode=mode,
+                                                                 flags=flags, seed=17 + 7919 * k).cpu().numpy()),
+                          (graph, algo, p, q, mode, flags))
+    G.close()
 
 
 @pytest.mark.parametrize("gamma", [0.2, 0.8])
@@ -409,7 +401,9 @@ def test_pagerank2_common_neighbour_split_paths(gamma, mode, flags):
     g = synth.from_edges(12, edges, h=[0.25 + 0.07 * i for i in range(len(edges))])
     G = fw.Graph(g)
     W, L = 400_000, 4
-    out = G.walk(torch.full((W,), 1, dtype=torch.int32, device="cuda"), L, "pagerank2", gamma=gamma, mode=mode,
-                 flags=flags, seed=29).cpu().numpy()
+    bf = bf_paths(g, 1, L, "pagerank2", 1.0, 1.0, None, gamma=gamma)
+    starts = torch.full((W,), 1, dtype=torch.int32, device="cuda")
+    assert_pvalue_follows(lambda k: merged_chisquare(bf, G.walk(starts, L, "pagerank2", gamma=gamma, mode=mode,
+                                                                 flags=flags, seed=29 + 7919 * k).cpu().numpy()),
+                          ("pagerank2 split", gamma, mode, flags))
     G.close()
-    assert merged_chisquare(bf_paths(g, 1, L, "pagerank2", 1.0, 1.0, None, gamma=gamma), out) > 1e-4

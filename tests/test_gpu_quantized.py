@@ -10,7 +10,7 @@ import oracle
 from paper_2512_00705_gb300 import flexiwalk as fw
 from paper_2512_00705_gb300 import synth
 from bruteforce import bf_paths, merged_chisquare
-from statcheck import chisq_pvalue, tv_distance
+from statcheck import assert_follows, assert_pvalue_follows, chisq_pvalue
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -101,14 +101,14 @@ def test_fast_mode_distributions(quantized, mode, flags, algo, p, q, schema):
         nb = g.cols[g.offsets[v]:g.offsets[v + 1]]
         for vp, step in [(-1, 0), (int(nb[np.argmax(deg[nb])]), 1)]:
             probs = oracle.transition_probs(gq, v, vp, step, algo, p, q, schema)
-            counts = G.sample_hist(v, vp, step, algo, ndraws, p=p, q=q, schema=schema, mode=mode, flags=flags,
-                                   seed=555 + v).cpu().numpy()
+            draw = lambda k: G.sample_hist(v, vp, step, algo, ndraws, p=p, q=q, schema=schema, mode=mode,
+                                           flags=flags, seed=555 + v + 7919 * k).cpu().numpy()
             if probs.sum() == 0:
-                assert counts.sum() == 0
+                assert draw(0).sum() == 0
                 continue
-            assert chisq_pvalue(counts, probs) > 1e-4, (v, vp)
-            assert tv_distance(counts, probs) < 2e-3, (v, vp)
+            assert_follows(draw, probs, (algo, p, q, mode, flags, v, vp), ndraws)
             if v == hub and vp < 0:
+                counts = draw(0)
                 assert chisq_pvalue(counts, oracle.transition_probs(g, v, vp, step, algo, p, q, schema)) < 1e-9
 
 
@@ -124,10 +124,12 @@ def test_fast_walk_path_distribution(mode, algo, p, q, schema):
     G = fw.Graph(g)
     G.quantize_weights()
     W, L = 300_000, 4
-    out = G.walk(torch.zeros(W, dtype=torch.int32, device="cuda"), L, algo, p=p, q=q, schema=schema, mode=mode,
-                 seed=23).cpu().numpy()
+    bf = bf_paths(gq, 0, L, algo, p, q, schema)
+    starts = torch.zeros(W, dtype=torch.int32, device="cuda")
+    assert_pvalue_follows(lambda k: merged_chisquare(bf, G.walk(starts, L, algo, p=p, q=q, schema=schema, mode=mode,
+                                                                 seed=23 + 7919 * k).cpu().numpy()),
+                          ("quantized paths", algo, p, q, mode))
     G.close()
-    assert merged_chisquare(bf_paths(gq, 0, L, algo, p, q, schema), out) > 1e-4
 
 
 def test_unweighted_graph_is_refused():

@@ -10,6 +10,7 @@ import oracle
 from paper_2512_00705_gb300 import flexiwalk as fw
 from paper_2512_00705_gb300 import synth
 from bruteforce import bf_paths, merged_chisquare
+from statcheck import assert_pvalue_follows
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -80,9 +81,11 @@ def test_cost_ratio_never_changes_the_distribution(ratio):
     G = fw.Graph(g)
     W, L = 300_000, 4
     starts = torch.zeros(W, dtype=torch.int32, device="cuda")
-    out = G.walk(starts, L, "node2vec", p=0.5, q=2.0, mode="auto", cost_ratio=ratio, seed=3).cpu().numpy()
+    bf = bf_paths(g, 0, L, "node2vec", 0.5, 2.0, None)
+    assert_pvalue_follows(lambda k: merged_chisquare(bf, G.walk(starts, L, "node2vec", p=0.5, q=2.0, mode="auto",
+                                                                 cost_ratio=ratio, seed=3 + 7919 * k).cpu().numpy()),
+                          ("cost ratio", ratio))
     G.close()
-    assert merged_chisquare(bf_paths(g, 0, L, "node2vec", 0.5, 2.0, None), out) > 1e-4
 
 
 # ------------------------------------------------------------ batching

@@ -30,7 +30,7 @@ def test_exact_uniform_range_and_uniformity():
     # on the 2^-24 grid
     assert np.all(us * 2**24 == np.floor(us * 2**24))
     # uniform (Kolmogorov-Smirnov against U[0,1))
-    assert stats.kstest(us, "uniform").pvalue > 1e-3
+    assert stats.kstest(us, "uniform").pvalue > 0.01
 
 
 # ------------------------------------------------------- worked example, Fig 2
@@ -168,6 +168,7 @@ def test_metapath_filter():
 
 # ------------------------------------------------------- brute force, 8 nodes
 from bruteforce import bf_paths as _bf_paths, merged_chisquare
+from statcheck import assert_pvalue_follows
 
 
 CASES = [("weighted", 1.0, 1.0, None), ("node2vec", 2.0, 0.5, None), ("node2vec", 0.25, 4.0, None),
@@ -204,8 +205,9 @@ def test_brute_force_sampler_frequencies(algo, p, q, schema):
     g = synth.random_graph(8, 0.45, seed=11, weighted=True, nlabels=3)
     L, W, start = 4, 60000, 0
     bf = _bf_paths(g, start, L, algo, p, q, schema)
-    out, _ = oracle.walk(g, np.full(W, start, np.int32), L, algo, p, q, schema, seed=7)
-    assert merged_chisquare(bf, out) > 1e-3
+    assert_pvalue_follows(lambda k: merged_chisquare(bf, oracle.walk(g, np.full(W, start, np.int32), L, algo, p, q,
+                                                                      schema, seed=7 + 7919 * k)[0]),
+                          ("oracle paths", algo, p, q))
 
 
 # --------------------------------------------------------- reductions / invariants
