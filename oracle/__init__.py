@@ -23,6 +23,11 @@ sampling, its own Philox4x32-10), compiled here with gcc and
 
 Graph arguments are any object with ``offsets``, ``cols``, ``h`` (or None)
 and ``labels`` (or None) numpy attributes.
+
+If the environment variable ``FW_ORACLE_LIB`` names a shared library, that
+prebuilt library is loaded instead of building ``fw_oracle.c``; the mutation
+tests use it to run the pins against copies of the oracle with a planted
+mistake.
 """
 from __future__ import annotations
 
@@ -60,8 +65,8 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = ctypes.CDLL(_SO)
+            so = os.environ.get("FW_ORACLE_LIB") or build()
+            L = ctypes.CDLL(so)
             vp, i32, i64, u32, u64, f32 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
                                            ctypes.c_uint64, ctypes.c_float)
             L.or_philox4x32_10.argtypes = [vp, vp, vp]

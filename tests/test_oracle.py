@@ -24,6 +24,16 @@ def test_philox_known_answers():
         assert oracle.philox4x32_10(ctr, key) == want
 
 
+def test_exact_uniform_from_published_vector():
+    """Exact-mode uniform: Philox4x32-10 at counter (walker, hop, 0, 0) under
+    key (seed low, seed high), u = (x0 >> 8) * 2^-24.  At seed, walker and hop
+    0 that is the all-zero published vector, so its x0 fixes u."""
+    zero = [r for r in read_golden("philox4x32_10_kat.txt") if all(int(x, 16) == 0 for x in r[:6])]
+    assert len(zero) == 1
+    x0 = int(zero[0][6], 16)
+    assert oracle.exact_uniform(0, 0, 0) == (x0 >> 8) / 2.0**24
+
+
 def test_exact_uniform_range_and_uniformity():
     us = np.array([oracle.exact_uniform(42, w, s) for w in range(2000) for s in range(5)])
     assert us.min() >= 0.0 and us.max() < 1.0

@@ -1,0 +1,107 @@
+"""Mutation check of the oracle's pins (CPU only).
+
+Each case plants one plausible mistake in a copy of ``oracle/fw_oracle.c``
+(a swapped parameter, a wrong index, a dropped term, a flipped comparison,
+a wrong constant), compiles the copy, and runs the pins of
+``tests/test_oracle.py`` against it in a child process: at least one pin must
+fail.  The unmodified source, built the same way, must pass them all, so a
+mutant's failure comes from the planted mistake and not from the harness.
+
+Mistakes that leave every probability unchanged in exact arithmetic (the
+max_d factor of Eq. (2ndpr) scales w1 and w2 alike; the hop-0 weight of
+node2vec is the same for every neighbour) are not listed: only the bit-exact
+GPU parity tests can tell those apart.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+import oracle
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(ROOT, "oracle", "fw_oracle.c")
+
+# name -> (text in fw_oracle.c, replacement)
+MUTANTS = {
+    # Philox4x32-10 (Salmon et al.): the second Weyl key increment
+    "philox_key_weyl": ("k1 += 0xBB67AE85u;", "k1 += 0x9E3779B9u;"),
+    # exact-mode uniform: which output word, and the 24-bit grid
+    "uniform_word": ("(float)(x[0] >> 8)", "(float)(x[1] >> 8)"),
+    "uniform_shift": ("(float)(x[0] >> 8)", "(float)(x[0] >> 9)"),
+    # Eq. (node2vec): 1/p and 1/q exchanged
+    "node2vec_swap_pq": ("const float inv_p = or_recip(p), inv_q = or_recip(q);",
+                         "const float inv_p = or_recip(q), inv_q = or_recip(p);"),
+    # Eq. (node2vec): membership tested in N(v) instead of N(v')
+    "node2vec_wrong_row": ("else if (is_neighbour(offsets, cols, vprev, u)) w = 1.0f;",
+                           "else if (is_neighbour(offsets, cols, v, u)) w = 1.0f;"),
+    # Eq. (node2vec): the return edge not recognised
+    "node2vec_no_return": ("else if (u == vprev) w = inv_p;", "else if (u == vprev + 1) w = inv_p;"),
+    # Eq. (prob): the property weight h dropped
+    "prob_drop_h": ("wt[k] = w * hk;", "wt[k] = w;"),
+    # MetaPath rule: schema index shifted by one hop
+    "metapath_schema_shift": ("schema[step % schema_len]", "schema[(step + 1) % schema_len]"),
+    # MetaPath rule: filter inverted
+    "metapath_filter_inverted": ("(labels[s + k] == schema[step % schema_len])",
+                                 "(labels[s + k] != schema[step % schema_len])"),
+    # Eq. (2ndpr): the two weights exchanged
+    "pagerank2_swap_weights": ("? pr_w1 : pr_w2;", "? pr_w2 : pr_w1;"),
+    # Eq. (2ndpr): gamma / d(v) instead of gamma / d(v')
+    "pagerank2_wrong_degree": ("const float t2 = gamma / dp;", "const float t2 = gamma / dv;"),
+    # ITS (Sec. 2.2): strict comparison made inclusive
+    "icdf_inclusive": ("if (t < run) return k;", "if (t <= run) return k;"),
+    # walk: the previous node never advances
+    "walk_prev_stuck": ("        prev = cur;\n        cur = nxt;", "        cur = nxt;"),
+    # Sec. 4.2 preprocessing: minimum instead of maximum
+    "node_stats_min": ("if (x > m) m = x;", "if (x < m || m == 0.0f) m = x;"),
+    # Sec. 3.3 bound: 1/p left out of max(w)
+    "bound_drop_inv_p": ("wmax = ip > 1.0f ? ip : 1.0f;", "wmax = 1.0f;"),
+    # Eq. (sum_estimation): mean over two values instead of three
+    "sum_estimate_mean": ("wmean = (float)(((double)ip + 1.0 + (double)iq) / 3.0);",
+                          "wmean = (float)(((double)ip + 1.0 + (double)iq) / 2.0);"),
+    # Eq. (runtime): the comparison reversed
+    "cost_model_reversed": ("return (r * B < S) ? OR_MODE_RJS : OR_MODE_RVS;",
+                            "return (r * B > S) ? OR_MODE_RJS : OR_MODE_RVS;"),
+    # per-label statistics: label sums into the wrong slot
+    "label_stats_slot": ("lsum[v * 8 + l] += (double)x;", "lsum[v * 8 + (l + 1) % 8] += (double)x;"),
+    # 8-bit weights: truncation instead of round-to-nearest
+    "quantize_truncate": ("float c = rintf(h[i] / s);", "float c = floorf(h[i] / s);"),
+}
+
+
+def _build(tmp_path, name, text):
+    src = tmp_path / f"{name}.c"
+    src.write_text(text)
+    so = tmp_path / f"lib{name}.so"
+    subprocess.run(["gcc", *oracle.CFLAGS, str(src), "-o", str(so), "-lm"], check=True, capture_output=True)
+    return str(so)
+
+
+def _run_pins(so):
+    env = dict(os.environ, FW_ORACLE_LIB=so, OMP_NUM_THREADS="4")
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(HERE, "test_oracle.py"), "-x", "-q",
+                        "-p", "no:cacheprovider", "-m", "not gpu"], cwd=ROOT, env=env, capture_output=True,
+                       text=True, timeout=600)
+    return r.returncode, r.stdout[-3000:] + r.stderr[-2000:]
+
+
+def test_unmodified_oracle_passes_through_the_harness(tmp_path):
+    with open(SRC) as f:
+        text = f.read()
+    rc, out = _run_pins(_build(tmp_path, "unmodified", text))
+    assert rc == 0, out
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_fails_a_pin(tmp_path, name):
+    old, new = MUTANTS[name]
+    with open(SRC) as f:
+        text = f.read()
+    assert text.count(old) == 1, f"{name}: the text to mutate must occur exactly once"
+    rc, out = _run_pins(_build(tmp_path, name, text.replace(old, new)))
+    # 1 = some test failed; anything else (0 = all passed, 2+ = harness or
+    # collection error) does not show that a pin caught the mistake
+    assert rc == 1, f"{name}: pins returned {rc}\n{out}"
+    assert " failed" in out, out
