@@ -154,6 +154,12 @@ def test_pagerank2_closed_forms():
     g = _complete(4)
     np.testing.assert_allclose(oracle.transition_probs(g, 3, 0, 1, "pagerank2"),
                                np.array([0.8, 1.0, 1.0]) / 2.8, rtol=1e-6)
+    # unequal degrees with a common neighbour: v'=0 has N = {1, 2}, v=1 has
+    # N = {0, 2, 3, 4}; from 0 to 1: d(v)=4, d(v')=2, max_d=4; neighbour 2 is
+    # adjacent to v' -> (0.8/4 + 0.2/2) * 4 = 1.2, the others (0.8/4) * 4 = 0.8
+    g = synth.from_edges(5, [(0, 1), (0, 2), (1, 2), (1, 3), (1, 4)])
+    np.testing.assert_allclose(oracle.transition_probs(g, 1, 0, 1, "pagerank2"),
+                               np.array([0.8, 1.2, 0.8, 0.8]) / 3.6, rtol=1e-6)
     # gamma = 0 reduces to a first-order walk
     g = synth.random_graph(12, 0.4, seed=4, weighted=True)
     for v in range(12):
