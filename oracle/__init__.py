@@ -14,6 +14,8 @@ sampling, its own Philox4x32-10), compiled here with gcc and
   transition_probs      Eq. (prob), fp64
   icdf_pick             Sec. 2.2 inverse transform sampling, FP32
   walk                  full exact-mode walks
+  walk_rjs              walks drawn hop by hop by rejection sampling (Sec. 3.3)
+                        with the bound B = max(w) * h_MAX[v]
   node_stats            h_MAX / h_SUM preprocessing, Sec. 4.2
   step_plan             bound (Sec. 3.3) + sum estimate (Eq. sum_estimation)
                         + cost-model choice (Eq. runtime)
@@ -87,6 +89,8 @@ def _load():
             L.or_walk_ids.argtypes = [vp, vp, vp, vp, i32, vp, vp, i32, i32, i32, f32, f32, f32, vp, i32, u64, vp,
                                       i32]
             L.or_walk_ids.restype = i64
+            L.or_walk_rjs.argtypes = [vp, vp, vp, i32, vp, i32, i32, i32, f32, f32, f32, u64, u32, vp, i32]
+            L.or_walk_rjs.restype = i64
             L.or_node_stats.argtypes = [vp, vp, i32, vp, vp]
             L.or_node_stats.restype = ctypes.c_int
             L.or_step_plan.argtypes = [f32, f32, i32, i32, i32, i32, f32, f32, f32, f32, vp, vp]
@@ -183,6 +187,23 @@ def walk(g, starts, length, algo, p=1.0, q=1.0, schema=None, seed=42, walker_bas
                      _ptr(out), threads)
     if hops < 0:
         raise ValueError("or_walk: bad arguments")
+    return out, int(hops)
+
+
+def walk_rjs(g, starts, length, algo, p=1.0, q=1.0, seed=42, walker_base=0, threads=0, gamma=0.2):
+    """Walks whose every hop is drawn by rejection sampling against
+    B = max(w) * h_MAX[v] (Sec. 3.3), trial t of hop j of walker i using
+    Philox4x32-10 counter (i, j, 1, t): an index by Lemire's method from x0
+    (else x1, else no proposal) and U = (x2 >> 8) * 2^-24.  Weighted, node2vec
+    and second-order PageRank.  Returns (out int32[W][L+1], hops)."""
+    L = _load()
+    offsets, cols, h, _ = _graph_args(g)
+    st = np.ascontiguousarray(starts, dtype=np.int32)
+    out = np.empty((st.shape[0], length + 1), dtype=np.int32)
+    hops = L.or_walk_rjs(_ptr(offsets), _ptr(cols), _ptr(h), offsets.shape[0] - 1, _ptr(st), st.shape[0], length,
+                         ALGOS.get(algo, algo), p, q, gamma, seed, walker_base, _ptr(out), threads)
+    if hops < 0:
+        raise ValueError("or_walk_rjs: bad arguments")
     return out, int(hops)
 
 

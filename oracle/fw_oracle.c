@@ -22,6 +22,11 @@
  *                             else ((1-g)/d(v)) * max_d
  *   ITS, Sec. 2.2             one uniform, cumulative weights, first index whose cumulative
  *                             weight exceeds the scaled uniform
+ *   RJS, Sec. 2.2 / 3.3       propose a neighbour uniformly, accept it iff U * B < w~, with the
+ *                             bound B = max(w) * h_MAX[v]; repeat until a proposal is accepted
+ *   Lemire, "Fast random integer generation in an interval", ACM TOMACS 29(1), 2019:
+ *                             index floor(x * d / 2^32) of a 32-bit word x, rejected when the
+ *                             low 32 bits of x * d fall below 2^32 mod d
  *   Sec. 3.3 (bound), Sec. 4.1 Eq. (runtime), Eq. (sum_estimation), Sec. 4.2 (sum helper):
  *                             B = max(w) * h_MAX[v]; sum-hat = h_SUM[v] * mean of the
  *                             distinct return values of w; eRJS iff r * B < sum-hat
@@ -49,6 +54,11 @@
  *   - Exact-mode pick: W_k = W_{k-1} + w~_k in FP32 in neighbour order,
  *     t = u * W_{d-1} in FP32, pick the smallest k with t < W_k; if rounding
  *     leaves none, pick the last k with w~_k > 0.
+ *   - RJS random numbers: trial t of hop j of walker i draws
+ *     x = Philox4x32-10(counter (i, j, 1, t), the exact-mode key); the proposal
+ *     is Lemire's index of x0, or of x1 when x0 is rejected, and the trial
+ *     proposes nothing when both are; U = (x2 >> 8) * 2^-24.  Trials run
+ *     t = 0, 1, 2, ... and the first accepted proposal is the hop.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -60,6 +70,9 @@
 
 enum { OR_WEIGHTED = 0, OR_NODE2VEC = 1, OR_METAPATH = 2, OR_PAGERANK2 = 3 };
 enum { OR_MODE_RJS = 1, OR_MODE_RVS = 2 };
+
+int or_step_plan(float hmax, float hsum, int32_t has_prev, int32_t dv, int32_t dprev, int32_t algo, float p,
+                 float q, float gamma, float r, float *bound, float *sum_hat);
 
 /* ---------------------------------------------------------------------------
  * Philox4x32-10 (Salmon et al., SC'11): a 10-round Feistel-like bijection on
@@ -211,7 +224,7 @@ static int64_t walk_impl(const int32_t *offsets, const int32_t *cols, const floa
                          const uint8_t *labels, int32_t n, const int32_t *starts, int32_t num_walkers,
                          int32_t len, int32_t algo, float p, float q, float gamma, const uint8_t *schema,
                          int32_t schema_len, uint64_t seed, uint32_t walker_base, const uint32_t *ids,
-                         int32_t *out, int32_t nthreads);
+                         int32_t sampler, int32_t *out, int32_t nthreads);
 
 int64_t or_walk(const int32_t *offsets, const int32_t *cols, const float *h,
                 const uint8_t *labels, int32_t n, const int32_t *starts, int32_t num_walkers,
@@ -219,7 +232,7 @@ int64_t or_walk(const int32_t *offsets, const int32_t *cols, const float *h,
                 int32_t schema_len, uint64_t seed, uint32_t walker_base, int32_t *out,
                 int32_t nthreads) {
   return walk_impl(offsets, cols, h, labels, n, starts, num_walkers, len, algo, p, q, gamma, schema, schema_len,
-                   seed, walker_base, NULL, out, nthreads);
+                   seed, walker_base, NULL, 0, out, nthreads);
 }
 
 /* Same walks with an explicit random-stream id per walker (ids[i] instead
@@ -231,14 +244,57 @@ int64_t or_walk_ids(const int32_t *offsets, const int32_t *cols, const float *h,
                     int32_t nthreads) {
   if (!ids && num_walkers > 0) return -1;
   return walk_impl(offsets, cols, h, labels, n, starts, num_walkers, len, algo, p, q, gamma, schema, schema_len,
-                   seed, 0, ids, out, nthreads);
+                   seed, 0, ids, 0, out, nthreads);
+}
+
+/* The same walks with every hop drawn by rejection sampling (RJS, Sec. 3.3)
+ * against the bound B = max(w) * h_MAX[v] of or_step_plan, with the random
+ * numbers of the RJS reading in the header.  Weighted, node2vec and
+ * second-order PageRank walks (metapath: -1).  Rows follow the same
+ * distribution as or_walk's; they are not the same rows. */
+int64_t or_walk_rjs(const int32_t *offsets, const int32_t *cols, const float *h, int32_t n, const int32_t *starts,
+                    int32_t num_walkers, int32_t len, int32_t algo, float p, float q, float gamma, uint64_t seed,
+                    uint32_t walker_base, int32_t *out, int32_t nthreads) {
+  if (algo != OR_WEIGHTED && algo != OR_NODE2VEC && algo != OR_PAGERANK2) return -1;
+  return walk_impl(offsets, cols, h, NULL, n, starts, num_walkers, len, algo, p, q, gamma, NULL, 0, seed,
+                   walker_base, NULL, 1, out, nthreads);
+}
+
+/* Lemire's map of a 32-bit word onto [0, d), d >= 1: *k = floor(x * d / 2^32)
+ * unless the low word of x * d is below 2^32 mod d (then 0 is returned and
+ * the word is not used); the accepted words give every index equally often. */
+static int lemire_index(uint32_t x, uint32_t d, uint32_t *k) {
+  const uint64_t m = (uint64_t)x * (uint64_t)d;
+  const uint32_t low = (uint32_t)m;
+  const uint32_t thr = (uint32_t)((UINT64_C(0x100000000) - d) % d); /* 2^32 mod d */
+  if (low < thr) return 0;
+  *k = (uint32_t)(m >> 32);
+  return 1;
+}
+
+/* One RJS hop at v with FP32 weights wt[0..d) and bound B (Sec. 3.3): trials
+ * t = 0, 1, ... until U * B < wt[k] for the proposed k.  Returns k, or -1 when
+ * no neighbour has weight (the proposal would never be accepted). */
+static int64_t rjs_pick(const float *wt, int64_t d, float B, uint64_t seed, uint32_t wid, uint32_t hop) {
+  int any = 0;
+  for (int64_t k = 0; k < d; ++k) any |= wt[k] > 0.0f;
+  if (!any) return -1;
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (uint32_t t = 0;; ++t) {
+    const uint32_t ctr[4] = {wid, hop, 1u, t};
+    uint32_t x[4], k;
+    or_philox4x32_10(ctr, key, x);
+    if (!lemire_index(x[0], (uint32_t)d, &k) && !lemire_index(x[1], (uint32_t)d, &k)) continue;
+    const float U = (float)(x[2] >> 8) * 0x1.0p-24f;
+    if (U * B < wt[k]) return (int64_t)k;
+  }
 }
 
 static int64_t walk_impl(const int32_t *offsets, const int32_t *cols, const float *h,
                          const uint8_t *labels, int32_t n, const int32_t *starts, int32_t num_walkers,
                          int32_t len, int32_t algo, float p, float q, float gamma, const uint8_t *schema,
                          int32_t schema_len, uint64_t seed, uint32_t walker_base, const uint32_t *ids,
-                         int32_t *out, int32_t nthreads) {
+                         int32_t sampler, int32_t *out, int32_t nthreads) {
   if (!offsets || !cols || !starts || !out || num_walkers < 0 || len < 0 || n < 0) return -1;
   for (int32_t i = 0; i < num_walkers; ++i)
     if (starts[i] < 0 || starts[i] >= n) return -1;
@@ -273,8 +329,20 @@ static int64_t walk_impl(const int32_t *offsets, const int32_t *cols, const floa
         int64_t d = or_transition_weights(offsets, cols, h, labels, n, cur, prev, j, algo, p, q, gamma,
                                           schema, schema_len, wt);
         const uint32_t wid = ids ? ids[i] : walker_base + (uint32_t)i;
-        float u = or_exact_uniform(seed, wid, (uint32_t)j);
-        int64_t k = or_icdf_pick(wt, d, u);
+        int64_t k;
+        if (sampler == 0) {
+          k = or_icdf_pick(wt, d, or_exact_uniform(seed, wid, (uint32_t)j));
+        } else {
+          float hmax = 0.0f, B;
+          for (int64_t e = offsets[cur]; e < offsets[cur + 1]; ++e) {
+            const float x = h ? h[e] : 1.0f;
+            if (x > hmax) hmax = x;
+          }
+          const int32_t dprev = prev >= 0 ? offsets[prev + 1] - offsets[prev] : 0;
+          if (d == 0 || or_step_plan(hmax, 0.0f, prev >= 0, (int32_t)d, dprev, algo, p, q, gamma, 1.0f, &B, NULL) < 0)
+            break;
+          k = rjs_pick(wt, d, B, seed, wid, (uint32_t)j);
+        }
         if (k < 0) break;
         int32_t nxt = cols[offsets[cur] + k];
         row[j + 1] = nxt;

@@ -1,8 +1,9 @@
 """Parity at the benchmark's full sizes, in the launch configuration the
 benchmark times: R-MAT s22 (4,194,304 walkers x 80 hops, node2vec) and R-MAT
-s23 (metapath, 2M starts).  Exact mode: sampled blocks of rows against the
-oracle, which computes them walker by walker.  Fast modes: invariants on
-sampled rows, and per-state distributions at the largest hubs."""
+s23 (metapath, 2M starts).  Exact mode and eRJS under the paper's single
+bound: sampled blocks of rows against the oracle, which computes them walker
+by walker.  Fast modes: invariants on sampled rows, and per-state
+distributions at the largest hubs."""
 import numpy as np
 import pytest
 
@@ -38,6 +39,21 @@ def test_exact_mode_full_s22_sampled_rows(s22, p, q):
     for b in _blocks(g.n, 6, 64, seed=int(p * 100 + q)):
         sub = np.arange(b, b + 64, dtype=np.int32)
         ref, _ = oracle.walk(g, sub, 80, "node2vec", p, q, seed=42, walker_base=b)
+        got = out[b:b + 64].cpu().numpy()
+        assert np.array_equal(got, ref), f"block {b}: {(got != ref).any(axis=1).sum()} rows differ"
+
+
+@pytest.mark.parametrize("p,q", PQ)
+def test_plain_rjs_full_s22_sampled_rows(s22, p, q):
+    """The bench's launch with every hop in eRJS under the paper's single
+    bound (FW_FLAG_PLAIN_RJS, no hand-off): sampled 64-row blocks equal the
+    oracle's rejection-sampled walks bit for bit."""
+    g, G = s22
+    starts = torch.arange(g.n, dtype=torch.int32, device="cuda")
+    out = G.walk(starts, 80, "node2vec", p=p, q=q, mode="rjs", flags=fw.FLAG_PLAIN_RJS, rjs_cap=1 << 30, seed=42)
+    for b in _blocks(g.n, 4, 64, seed=int(p * 100 + q) + 1):
+        sub = np.arange(b, b + 64, dtype=np.int32)
+        ref, _ = oracle.walk_rjs(g, sub, 80, "node2vec", p, q, seed=42, walker_base=b)
         got = out[b:b + 64].cpu().numpy()
         assert np.array_equal(got, ref), f"block {b}: {(got != ref).any(axis=1).sum()} rows differ"
 

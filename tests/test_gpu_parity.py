@@ -72,6 +72,31 @@ def test_exact_mode_unweighted(small):
     assert np.array_equal(out2, ref)
 
 
+# ------------------------------------------------- eRJS with the paper's bound
+RJS_ALGOS = [("node2vec", 2.0, 0.5), ("node2vec", 0.25, 4.0), ("node2vec", 4.0, 0.25), ("node2vec", 1.0, 1.0),
+             ("weighted", 1.0, 1.0), ("pagerank2", 1.0, 1.0)]
+NO_HANDOFF = 1 << 30  # a trial budget no step reaches: every hop stays in eRJS
+
+
+@pytest.mark.parametrize("algo,p,q", RJS_ALGOS)
+@pytest.mark.parametrize("unweighted", [False, True])
+def test_plain_rjs_walks_bit_identical_to_oracle_rjs(small, algo, p, q, unweighted):
+    """eRJS with the single bound B = max(w) h_MAX[v] and the uniform proposal
+    of Sec. 3.3 (FW_FLAG_PLAIN_RJS), every step kept in eRJS: the kernel
+    draws the oracle's proposals and uniforms trial by trial, so its rows
+    equal the oracle's rejection-sampled walks bit for bit (the squeeze tests,
+    the Bloom pre-check and the row search only shorten the work)."""
+    g, G = small
+    W, L = 4093, 20
+    starts = synth.random_starts(g.n, W, seed=17)
+    flags = fw.FLAG_PLAIN_RJS | (fw.FLAG_UNWEIGHTED if unweighted else 0)
+    out = G.walk(_cuda(starts), L, algo, p=p, q=q, mode="rjs", flags=flags, rjs_cap=NO_HANDOFF, seed=42,
+                 walker_base=11).cpu().numpy()
+    ref, _ = oracle.walk_rjs(synth.Csr(g.offsets, g.cols) if unweighted else g, starts, L, algo, p, q, seed=42,
+                             walker_base=11)
+    assert np.array_equal(out, ref), f"{(out != ref).any(axis=1).sum()} rows differ"
+
+
 def test_graph_from_device_arrays(small):
     g, _ = small
     G = fw.Graph(offsets=_cuda(g.offsets), cols=_cuda(g.cols), weights=_cuda(g.h), labels=_cuda(g.labels))

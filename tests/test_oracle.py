@@ -227,6 +227,44 @@ def test_brute_force_sampler_frequencies(algo, p, q, schema):
 
 
 # --------------------------------------------------------- reductions / invariants
+@pytest.mark.parametrize("algo,p,q", [(a, p, q) for (a, p, q, s) in CASES if a != "metapath"])
+@pytest.mark.parametrize("weighted", [True, False])
+def test_rjs_walk_frequencies(algo, p, q, weighted):
+    """Rejection-sampled walks (Sec. 3.3) from one start: path frequencies
+    match brute-force path probabilities, as the exact-mode walks' do, with
+    and without property weights (also where 1/p or 1/q sets max(w))."""
+    g = synth.random_graph(8, 0.45, seed=11, weighted=weighted, nlabels=3)
+    L, W, start = 4, 60000, 0
+    bf = _bf_paths(g, start, L, algo, p, q, None)
+    assert_pvalue_follows(lambda k: merged_chisquare(bf, oracle.walk_rjs(g, np.full(W, start, np.int32), L, algo, p,
+                                                                          q, seed=9 + 7919 * k)[0]),
+                          ("oracle rjs paths", algo, p, q, weighted))
+
+
+def _lemire(x, d):
+    """Lemire (ACM TOMACS 2019): floor(x d / 2^32), or None when the low word
+    of x d is below 2^32 mod d."""
+    m = x * d
+    return None if (m & 0xFFFFFFFF) < (2**32 % d) else m >> 32
+
+
+def test_rjs_proposal_is_lemire_index_of_the_trial_words():
+    """With equal weights every proposal is accepted (U * B < B for U < 1), so
+    hop 0 from the centre of a star is the first trial's proposal: Lemire's
+    index of x0 of Philox4x32-10 at counter (walker, 0, 1, 0), else of x1."""
+    for d in (1, 2, 3, 7, 1000, 65537):
+        g = synth.from_edges(d + 1, [(0, i) for i in range(1, d + 1)], h=[0.75] * d)
+        W, seed = 512, 0x1234_5678_9ABC
+        out, _ = oracle.walk_rjs(g, np.zeros(W, np.int32), 1, "weighted", seed=seed)
+        key = [seed & 0xFFFFFFFF, seed >> 32]
+        for w in range(W):
+            x = oracle.philox4x32_10([w, 0, 1, 0], key)
+            k = _lemire(x[0], d)
+            k = _lemire(x[1], d) if k is None else k
+            assert k is not None  # two rejections in a row: 2^-64 for these d
+            assert out[w, 1] == 1 + k, (d, w)
+
+
 def test_node2vec_p1q1_equals_weighted_walk():
     """node2vec with p = q = 1 has w = 1 everywhere, so its walks equal the
     weighted first-order walk bit for bit under the same draws."""

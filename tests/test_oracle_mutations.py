@@ -68,6 +68,14 @@ MUTANTS = {
     "label_stats_slot": ("lsum[v * 8 + l] += (double)x;", "lsum[v * 8 + (l + 1) % 8] += (double)x;"),
     # 8-bit weights: truncation instead of round-to-nearest
     "quantize_truncate": ("float c = rintf(h[i] / s);", "float c = floorf(h[i] / s);"),
+    # RJS (Sec. 3.3): the proposal taken from the word that also gives U
+    "rjs_index_word": ("lemire_index(x[0], (uint32_t)d, &k)", "lemire_index(x[2], (uint32_t)d, &k)"),
+    # RJS: the index taken as x mod d instead of Lemire's multiply-shift
+    "rjs_index_modulo": ("*k = (uint32_t)(m >> 32);", "*k = x % d;"),
+    # RJS: the bound from the row's first weight instead of h_MAX[v]
+    "rjs_bound_first_h": ("if (x > hmax) hmax = x;", "if (hmax == 0.0f) hmax = x;"),
+    # RJS: acceptance test reversed
+    "rjs_accept_reversed": ("if (U * B < wt[k]) return (int64_t)k;", "if (U * B > wt[k]) return (int64_t)k;"),
 }
 
 
