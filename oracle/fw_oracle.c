@@ -251,13 +251,26 @@ int64_t or_walk_ids(const int32_t *offsets, const int32_t *cols, const float *h,
  * against the bound B = max(w) * h_MAX[v] of or_step_plan, with the random
  * numbers of the RJS reading in the header.  Weighted, node2vec and
  * second-order PageRank walks (metapath: -1).  Rows follow the same
- * distribution as or_walk's; they are not the same rows. */
+ * distribution as or_walk's; they are not the same rows.
+ *
+ * envelope 0: the paper's proposal, one of the d neighbours uniformly, each
+ * bounded by B.  envelope 1 (weighted graphs; a refinement of the Sec. 3.3
+ * bound, not in the paper): the neighbours fall into weight classes,
+ * class 0 with h > h_MAX/2, class 1 with h_MAX/4 < h <= h_MAX/2, class 2 the
+ * rest, of n0, n1, n2 entries, bounded by B, B/2 and B/4; the row is read in
+ * class order (class 0 entries in row order, then class 1, then class 2) and
+ * a trial draws one of 4 n0 + 2 n1 + n2 slots, slot t naming entry t/4 of
+ * class 0, then (t - 4 n0)/2 of class 1, then t - 4 n0 - 2 n1 of class 2;
+ * it is accepted iff U * (bound of its class) < w~.  Each entry is proposed
+ * in proportion to its class bound, which is at least its w~, so accepted
+ * draws follow Eq. (prob) as with the single bound. */
 int64_t or_walk_rjs(const int32_t *offsets, const int32_t *cols, const float *h, int32_t n, const int32_t *starts,
                     int32_t num_walkers, int32_t len, int32_t algo, float p, float q, float gamma, uint64_t seed,
-                    uint32_t walker_base, int32_t *out, int32_t nthreads) {
+                    uint32_t walker_base, int32_t envelope, int32_t *out, int32_t nthreads) {
   if (algo != OR_WEIGHTED && algo != OR_NODE2VEC && algo != OR_PAGERANK2) return -1;
+  if (envelope != 0 && (envelope != 1 || !h)) return -1;
   return walk_impl(offsets, cols, h, NULL, n, starts, num_walkers, len, algo, p, q, gamma, NULL, 0, seed,
-                   walker_base, NULL, 1, out, nthreads);
+                   walker_base, NULL, 1 + envelope, out, nthreads);
 }
 
 /* Lemire's map of a 32-bit word onto [0, d), d >= 1: *k = floor(x * d / 2^32)
@@ -273,20 +286,50 @@ static int lemire_index(uint32_t x, uint32_t d, uint32_t *k) {
 }
 
 /* One RJS hop at v with FP32 weights wt[0..d) and bound B (Sec. 3.3): trials
- * t = 0, 1, ... until U * B < wt[k] for the proposed k.  Returns k, or -1 when
- * no neighbour has weight (the proposal would never be accepted). */
-static int64_t rjs_pick(const float *wt, int64_t d, float B, uint64_t seed, uint32_t wid, uint32_t hop) {
+ * t = 0, 1, ... until U * bound < wt[k] for the proposed k.  With hrow (the
+ * row's h, envelope 1 of or_walk_rjs) the proposal follows the weight-class
+ * slots, ord[] receiving the class order.  Returns k, or -1 when no
+ * neighbour has weight (the proposal would never be accepted). */
+static int64_t rjs_pick(const float *wt, int64_t d, float B, const float *hrow, float hmax, int32_t *ord,
+                        uint64_t seed, uint32_t wid, uint32_t hop) {
   int any = 0;
   for (int64_t k = 0; k < d; ++k) any |= wt[k] > 0.0f;
   if (!any) return -1;
+  uint32_t n0 = 0, n1 = 0, slots = (uint32_t)d;
+  if (hrow) {
+    const float half = 0.5f * hmax, quarter = 0.25f * hmax;
+    uint32_t m = 0;
+    for (int c = 0; c < 3; ++c) {
+      for (int64_t k = 0; k < d; ++k) {
+        const int ck = hrow[k] > half ? 0 : (hrow[k] > quarter ? 1 : 2);
+        if (ck == c) ord[m++] = (int32_t)k;
+      }
+      if (c == 0) n0 = m;
+      if (c == 1) n1 = m - n0;
+    }
+    slots = 4u * n0 + 2u * n1 + ((uint32_t)d - n0 - n1);
+  }
   const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   for (uint32_t t = 0;; ++t) {
     const uint32_t ctr[4] = {wid, hop, 1u, t};
-    uint32_t x[4], k;
+    uint32_t x[4], sl;
     or_philox4x32_10(ctr, key, x);
-    if (!lemire_index(x[0], (uint32_t)d, &k) && !lemire_index(x[1], (uint32_t)d, &k)) continue;
+    if (!lemire_index(x[0], slots, &sl) && !lemire_index(x[1], slots, &sl)) continue;
+    int64_t k = sl;
+    float bound = B;
+    if (hrow) {
+      if (sl < 4u * n0) {
+        k = ord[sl / 4u];
+      } else if (sl - 4u * n0 < 2u * n1) {
+        k = ord[n0 + (sl - 4u * n0) / 2u];
+        bound = 0.5f * B;
+      } else {
+        k = ord[n0 + n1 + (sl - 4u * n0 - 2u * n1)];
+        bound = 0.25f * B;
+      }
+    }
     const float U = (float)(x[2] >> 8) * 0x1.0p-24f;
-    if (U * B < wt[k]) return (int64_t)k;
+    if (U * bound < wt[k]) return k;
   }
 }
 
@@ -314,13 +357,14 @@ static int64_t walk_impl(const int32_t *offsets, const int32_t *cols, const floa
 #pragma omp parallel reduction(+ : hops)
   {
     float *wt = (float *)malloc((size_t)(maxd > 0 ? maxd : 1) * sizeof(float));
-    if (!wt) {
+    int32_t *ord = (int32_t *)malloc((size_t)(maxd > 0 ? maxd : 1) * sizeof(int32_t));
+    if (!wt || !ord) {
 #pragma omp atomic write
       failed = 1;
     }
 #pragma omp for schedule(dynamic, 64)
     for (int32_t i = 0; i < num_walkers; ++i) {
-      if (!wt) continue;
+      if (!wt || !ord) continue;
       int32_t *row = out + (int64_t)i * (len + 1);
       int32_t cur = starts[i], prev = -1;
       row[0] = cur;
@@ -341,7 +385,7 @@ static int64_t walk_impl(const int32_t *offsets, const int32_t *cols, const floa
           const int32_t dprev = prev >= 0 ? offsets[prev + 1] - offsets[prev] : 0;
           if (d == 0 || or_step_plan(hmax, 0.0f, prev >= 0, (int32_t)d, dprev, algo, p, q, gamma, 1.0f, &B, NULL) < 0)
             break;
-          k = rjs_pick(wt, d, B, seed, wid, (uint32_t)j);
+          k = rjs_pick(wt, d, B, sampler == 2 ? h + offsets[cur] : NULL, hmax, ord, seed, wid, (uint32_t)j);
         }
         if (k < 0) break;
         int32_t nxt = cols[offsets[cur] + k];
@@ -353,6 +397,7 @@ static int64_t walk_impl(const int32_t *offsets, const int32_t *cols, const floa
       for (int32_t r = j + 1; r <= len; ++r) row[r] = -1;
     }
     free(wt);
+    free(ord);
   }
   return failed ? -1 : hops;
 }

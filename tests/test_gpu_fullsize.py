@@ -43,17 +43,20 @@ def test_exact_mode_full_s22_sampled_rows(s22, p, q):
         assert np.array_equal(got, ref), f"block {b}: {(got != ref).any(axis=1).sum()} rows differ"
 
 
-@pytest.mark.parametrize("p,q", PQ)
-def test_plain_rjs_full_s22_sampled_rows(s22, p, q):
-    """The bench's launch with every hop in eRJS under the paper's single
-    bound (FW_FLAG_PLAIN_RJS, no hand-off): sampled 64-row blocks equal the
-    oracle's rejection-sampled walks bit for bit."""
+@pytest.mark.parametrize("p,q,envelope", [(1.0, 1.0, "single"), (4.0, 0.25, "single"), (0.25, 4.0, "single"),
+                                          (1.0, 1.0, "classes"), (4.0, 0.25, "classes")])
+def test_rjs_full_s22_sampled_rows(s22, p, q, envelope):
+    """The bench's launch with every hop in eRJS (no hand-off), under the
+    paper's single bound (FW_FLAG_PLAIN_RJS) and under the weight-class
+    envelope (the default; (0.25, 4) would add split proposals): sampled
+    64-row blocks equal the oracle's rejection-sampled walks bit for bit."""
     g, G = s22
     starts = torch.arange(g.n, dtype=torch.int32, device="cuda")
-    out = G.walk(starts, 80, "node2vec", p=p, q=q, mode="rjs", flags=fw.FLAG_PLAIN_RJS, rjs_cap=1 << 30, seed=42)
+    flags = fw.FLAG_PLAIN_RJS if envelope == "single" else 0
+    out = G.walk(starts, 80, "node2vec", p=p, q=q, mode="rjs", flags=flags, rjs_cap=1 << 30, seed=42)
     for b in _blocks(g.n, 4, 64, seed=int(p * 100 + q) + 1):
         sub = np.arange(b, b + 64, dtype=np.int32)
-        ref, _ = oracle.walk_rjs(g, sub, 80, "node2vec", p, q, seed=42, walker_base=b)
+        ref, _ = oracle.walk_rjs(g, sub, 80, "node2vec", p, q, seed=42, walker_base=b, envelope=envelope)
         got = out[b:b + 64].cpu().numpy()
         assert np.array_equal(got, ref), f"block {b}: {(got != ref).any(axis=1).sum()} rows differ"
 

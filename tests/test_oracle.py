@@ -265,6 +265,44 @@ def test_rjs_proposal_is_lemire_index_of_the_trial_words():
             assert out[w, 1] == 1 + k, (d, w)
 
 
+@pytest.mark.parametrize("algo,p,q", [(a, p, q) for (a, p, q, s) in CASES if a != "metapath"])
+def test_rjs_class_envelope_walk_frequencies(algo, p, q):
+    """Rejection sampling under the weight-class envelope (classes of h
+    relative to h_MAX with bounds B, B/2, B/4) on weights spread over three
+    decades, so that every class is populated: path frequencies match
+    brute-force path probabilities."""
+    g = synth.random_graph(8, 0.45, seed=11, weighted=True, nlabels=3)
+    g.h = (g.h ** 3 + np.float32(1e-3)).astype(np.float32)
+    L, W, start = 4, 60000, 0
+    bf = _bf_paths(g, start, L, algo, p, q, None)
+    assert_pvalue_follows(lambda k: merged_chisquare(bf, oracle.walk_rjs(g, np.full(W, start, np.int32), L, algo, p,
+                                                                          q, seed=19 + 7919 * k,
+                                                                          envelope="classes")[0]),
+                          ("oracle rjs class envelope paths", algo, p, q))
+
+
+def test_rjs_class_envelope_slots():
+    """Weights h = hmax, hmax/2, hmax/4 sit exactly on their class bounds, so
+    every proposal is accepted and hop 0 from the star centre is the entry
+    that the first trial's slot names: with row weights [.25, 1, .5, 1, .25]
+    the class order is positions 1, 3 (class 0), 2 (class 1), 0, 4 (class 2),
+    and the 4*2 + 2*1 + 2 = 12 slots map to 1,1,1,1, 3,3,3,3, 2,2, 0, 4."""
+    hs = [0.25, 1.0, 0.5, 1.0, 0.25]
+    slot_to_pos = [1] * 4 + [3] * 4 + [2] * 2 + [0, 4]
+    g = synth.from_edges(6, [(0, i) for i in range(1, 6)], h=hs)
+    W, seed = 4096, 99
+    out, _ = oracle.walk_rjs(g, np.zeros(W, np.int32), 1, "weighted", seed=seed, envelope="classes")
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for w in range(W):
+        x = oracle.philox4x32_10([w, 0, 1, 0], key)
+        t = _lemire(x[0], 12)
+        t = _lemire(x[1], 12) if t is None else t
+        assert out[w, 1] == 1 + slot_to_pos[t], w
+    # the uniform proposal of the single bound spreads over the 5 entries instead
+    single, _ = oracle.walk_rjs(g, np.zeros(W, np.int32), 1, "weighted", seed=seed)
+    assert not np.array_equal(single, out)
+
+
 def test_node2vec_p1q1_equals_weighted_walk():
     """node2vec with p = q = 1 has w = 1 everywhere, so its walks equal the
     weighted first-order walk bit for bit under the same draws."""

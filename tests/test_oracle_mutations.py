@@ -69,13 +69,17 @@ MUTANTS = {
     # 8-bit weights: truncation instead of round-to-nearest
     "quantize_truncate": ("float c = rintf(h[i] / s);", "float c = floorf(h[i] / s);"),
     # RJS (Sec. 3.3): the proposal taken from the word that also gives U
-    "rjs_index_word": ("lemire_index(x[0], (uint32_t)d, &k)", "lemire_index(x[2], (uint32_t)d, &k)"),
+    "rjs_index_word": ("lemire_index(x[0], slots, &sl)", "lemire_index(x[2], slots, &sl)"),
     # RJS: the index taken as x mod d instead of Lemire's multiply-shift
     "rjs_index_modulo": ("*k = (uint32_t)(m >> 32);", "*k = x % d;"),
     # RJS: the bound from the row's first weight instead of h_MAX[v]
     "rjs_bound_first_h": ("if (x > hmax) hmax = x;", "if (hmax == 0.0f) hmax = x;"),
+    # weight-class envelope: an entry at exactly h_MAX/2 put into class 0
+    "rjs_class_boundary": ("const int ck = hrow[k] > half ? 0", "const int ck = hrow[k] >= half ? 0"),
+    # weight-class envelope: class 1 proposed twice as often as class 2 but bounded by B
+    "rjs_class_bound": ("        bound = 0.5f * B;", "        bound = B;"),
     # RJS: acceptance test reversed
-    "rjs_accept_reversed": ("if (U * B < wt[k]) return (int64_t)k;", "if (U * B > wt[k]) return (int64_t)k;"),
+    "rjs_accept_reversed": ("if (U * bound < wt[k]) return k;", "if (U * bound > wt[k]) return k;"),
 }
 
 
