@@ -249,12 +249,17 @@ int64_t or_walk_ids(const int32_t *offsets, const int32_t *cols, const float *h,
 
 /* The same walks with every hop drawn by rejection sampling (RJS, Sec. 3.3)
  * against the bound B = max(w) * h_MAX[v] of or_step_plan, with the random
- * numbers of the RJS reading in the header.  Weighted, node2vec and
- * second-order PageRank walks (metapath: -1).  Rows follow the same
+ * numbers of the RJS reading in the header.  Rows follow the same
  * distribution as or_walk's; they are not the same rows.
  *
  * envelope 0: the paper's proposal, one of the d neighbours uniformly, each
- * bounded by B.  envelope 1 (weighted graphs; a refinement of the Sec. 3.3
+ * bounded by B.  envelope 1 for metapath (a data layout, not in the paper):
+ * only the entries whose label the hop requires are proposed, M being their
+ * largest h; class c < 4 holds h in (M/2^(c+1), M/2^c], class 4 the rest; the
+ * entries are read in class order (row order inside a class), a trial draws
+ * one of 16 n0 + 8 n1 + 4 n2 + 2 n3 + n4 slots (slot t naming entry t/16 of
+ * class 0, and so on) and accepts iff U * M/2^c < h; no such entry: a dead
+ * end.  envelope 1 otherwise (weighted graphs; a refinement of the Sec. 3.3
  * bound, not in the paper): the neighbours fall into weight classes,
  * class 0 with h > h_MAX/2, class 1 with h_MAX/4 < h <= h_MAX/2, class 2 the
  * rest, of n0, n1, n2 entries, bounded by B, B/2 and B/4; the row is read in
@@ -264,13 +269,14 @@ int64_t or_walk_ids(const int32_t *offsets, const int32_t *cols, const float *h,
  * it is accepted iff U * (bound of its class) < w~.  Each entry is proposed
  * in proportion to its class bound, which is at least its w~, so accepted
  * draws follow Eq. (prob) as with the single bound. */
-int64_t or_walk_rjs(const int32_t *offsets, const int32_t *cols, const float *h, int32_t n, const int32_t *starts,
-                    int32_t num_walkers, int32_t len, int32_t algo, float p, float q, float gamma, uint64_t seed,
-                    uint32_t walker_base, int32_t envelope, int32_t *out, int32_t nthreads) {
-  if (algo != OR_WEIGHTED && algo != OR_NODE2VEC && algo != OR_PAGERANK2) return -1;
-  if (envelope != 0 && (envelope != 1 || !h)) return -1;
-  return walk_impl(offsets, cols, h, NULL, n, starts, num_walkers, len, algo, p, q, gamma, NULL, 0, seed,
-                   walker_base, NULL, 1 + envelope, out, nthreads);
+int64_t or_walk_rjs(const int32_t *offsets, const int32_t *cols, const float *h, const uint8_t *labels, int32_t n,
+                    const int32_t *starts, int32_t num_walkers, int32_t len, int32_t algo, float p, float q,
+                    float gamma, const uint8_t *schema, int32_t schema_len, uint64_t seed, uint32_t walker_base,
+                    int32_t envelope, int32_t *out, int32_t nthreads) {
+  if (envelope != 0 && envelope != 1) return -1;
+  if (envelope == 1 && algo != OR_METAPATH && !h) return -1;
+  return walk_impl(offsets, cols, h, labels, n, starts, num_walkers, len, algo, p, q, gamma, schema, schema_len,
+                   seed, walker_base, NULL, 1 + envelope, out, nthreads);
 }
 
 /* Lemire's map of a 32-bit word onto [0, d), d >= 1: *k = floor(x * d / 2^32)
@@ -333,6 +339,58 @@ static int64_t rjs_pick(const float *wt, int64_t d, float B, const float *hrow, 
   }
 }
 
+/* One RJS hop of a metapath walk under the label-segment envelope of
+ * or_walk_rjs (envelope 1): entries of label `want` among the d of the row
+ * (labrow, hrow; hrow NULL: h = 1).  Returns the row position, or -1 when
+ * no entry has the label. */
+static int64_t rjs_pick_label(const float *hrow, const uint8_t *labrow, uint8_t want, int64_t d, int32_t *ord,
+                              uint64_t seed, uint32_t wid, uint32_t hop) {
+  float M = 0.0f;
+  for (int64_t k = 0; k < d; ++k) {
+    const float x = hrow ? hrow[k] : 1.0f;
+    if (labrow[k] == want && x > M) M = x;
+  }
+  if (!(M > 0.0f)) return -1;
+  uint32_t cnt[5] = {0, 0, 0, 0, 0}, m = 0;
+  for (int c = 0; c < 5; ++c) {
+    for (int64_t k = 0; k < d; ++k) {
+      if (labrow[k] != want) continue;
+      const float x = hrow ? hrow[k] : 1.0f;
+      int ck = 0;
+      float t = 0.5f * M;
+      while (ck < 4 && !(x > t)) {
+        ++ck;
+        t = 0.5f * t;
+      }
+      if (ck == c) {
+        ord[m++] = (int32_t)k;
+        cnt[c]++;
+      }
+    }
+  }
+  uint32_t slots = 0;
+  for (int c = 0; c < 5; ++c) slots += (16u >> c) * cnt[c];
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (uint32_t t = 0;; ++t) {
+    const uint32_t ctr[4] = {wid, hop, 1u, t};
+    uint32_t x[4], sl;
+    or_philox4x32_10(ctr, key, x);
+    if (!lemire_index(x[0], slots, &sl) && !lemire_index(x[1], slots, &sl)) continue;
+    uint32_t base = 0;
+    int c = 0;
+    float bound = M;
+    while (sl >= (16u >> c) * cnt[c]) {
+      sl -= (16u >> c) * cnt[c];
+      base += cnt[c];
+      ++c;
+      bound = 0.5f * bound;
+    }
+    const int64_t k = ord[base + sl / (16u >> c)];
+    const float U = (float)(x[2] >> 8) * 0x1.0p-24f;
+    if (U * bound < (hrow ? hrow[k] : 1.0f)) return k;
+  }
+}
+
 static int64_t walk_impl(const int32_t *offsets, const int32_t *cols, const float *h,
                          const uint8_t *labels, int32_t n, const int32_t *starts, int32_t num_walkers,
                          int32_t len, int32_t algo, float p, float q, float gamma, const uint8_t *schema,
@@ -376,6 +434,9 @@ static int64_t walk_impl(const int32_t *offsets, const int32_t *cols, const floa
         int64_t k;
         if (sampler == 0) {
           k = or_icdf_pick(wt, d, or_exact_uniform(seed, wid, (uint32_t)j));
+        } else if (sampler == 2 && algo == OR_METAPATH) {
+          k = rjs_pick_label(h ? h + offsets[cur] : NULL, labels + offsets[cur], schema[j % schema_len], d, ord, seed,
+                             wid, (uint32_t)j);
         } else {
           float hmax = 0.0f, B;
           for (int64_t e = offsets[cur]; e < offsets[cur + 1]; ++e) {

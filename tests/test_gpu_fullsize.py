@@ -147,6 +147,23 @@ def test_hub_label_distributions_s23(s23, mode, flags, hub_too):
             assert_follows(draw, probs, ("metapath", mode, flags, v, lab), 4_000_000)
 
 
+def test_rjs_full_s23_metapath_sampled_rows(s23):
+    """The metapath bench's launch (2M starts, schema 0-4) with every hop in
+    eRJS inside the label-grouped view (five weight classes per label
+    segment, lognormal weights), no hand-off: sampled 128-row blocks equal
+    the oracle's rejection-sampled walks bit for bit."""
+    g, G = s23
+    starts_h = synth.random_starts(g.n, 2_000_000, seed=43)
+    schema = [0, 1, 2, 3, 4]
+    out = G.walk(torch.from_numpy(starts_h).cuda(), 40, "metapath", schema=schema, mode="rjs", rjs_cap=1 << 30,
+                 seed=42)
+    for b in _blocks(len(starts_h), 4, 128, seed=7):
+        ref, _ = oracle.walk_rjs(g, starts_h[b:b + 128], 40, "metapath", schema=schema, seed=42, walker_base=b,
+                                 envelope="classes")
+        got = out[b:b + 128].cpu().numpy()
+        assert np.array_equal(got, ref), f"block {b}: {(got != ref).any(axis=1).sum()} rows differ"
+
+
 def test_exact_mode_full_s23_metapath_sampled_rows(s23):
     g, G = s23
     starts_h = synth.random_starts(g.n, 2_000_000, seed=43)

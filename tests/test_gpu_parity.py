@@ -97,24 +97,26 @@ def test_plain_rjs_walks_bit_identical_to_oracle_rjs(small, algo, p, q, unweight
     assert np.array_equal(out, ref), f"{(out != ref).any(axis=1).sum()} rows differ"
 
 
-@pytest.mark.parametrize("algo,p,q", [("weighted", 1.0, 1.0), ("node2vec", 1.0, 1.0), ("node2vec", 4.0, 0.25),
-                                      ("node2vec", 2.0, 0.5)])
+@pytest.mark.parametrize("algo,p,q,schema", [("weighted", 1.0, 1.0, None), ("node2vec", 1.0, 1.0, None),
+                                             ("node2vec", 4.0, 0.25, None), ("node2vec", 2.0, 0.5, None),
+                                             ("metapath", 1.0, 1.0, [0, 1, 2, 3, 4]), ("metapath", 1.0, 1.0, [3])])
 @pytest.mark.parametrize("weights", ["uniform01", "lognormal"])
-def test_class_envelope_rjs_walks_bit_identical_to_oracle_rjs(algo, p, q, weights):
-    """eRJS under the weight-class envelope (the default for weighted graphs;
-    these settings use no split proposal), every step kept in eRJS: the
-    class-ordered records, the packed class counts and the slot map give the
-    oracle's proposals trial by trial, so the rows are bit-identical."""
+def test_class_envelope_rjs_walks_bit_identical_to_oracle_rjs(algo, p, q, schema, weights):
+    """eRJS under the weight-class envelopes (the default for weighted graphs;
+    these settings use no split proposal; metapath samples inside the
+    label-grouped view), every step kept in eRJS: the class-ordered records,
+    the packed class counts and the slot map give the oracle's proposals
+    trial by trial, so the rows are bit-identical."""
     g = synth.workload_graph("small")
     if weights == "lognormal":
         g.h = synth.edge_weights(g, "lognormal", 1.5, seed=13)
     G = fw.Graph(g)
     W, L = 4093, 20
     starts = synth.random_starts(g.n, W, seed=23)
-    out = G.walk(_cuda(starts), L, algo, p=p, q=q, mode="rjs", rjs_cap=NO_HANDOFF, seed=42,
+    out = G.walk(_cuda(starts), L, algo, p=p, q=q, schema=schema, mode="rjs", rjs_cap=NO_HANDOFF, seed=42,
                  walker_base=5).cpu().numpy()
     G.close()
-    ref, _ = oracle.walk_rjs(g, starts, L, algo, p, q, seed=42, walker_base=5, envelope="classes")
+    ref, _ = oracle.walk_rjs(g, starts, L, algo, p, q, schema, seed=42, walker_base=5, envelope="classes")
     assert np.array_equal(out, ref), f"{(out != ref).any(axis=1).sum()} rows differ"
 
 

@@ -227,17 +227,17 @@ def test_brute_force_sampler_frequencies(algo, p, q, schema):
 
 
 # --------------------------------------------------------- reductions / invariants
-@pytest.mark.parametrize("algo,p,q", [(a, p, q) for (a, p, q, s) in CASES if a != "metapath"])
+@pytest.mark.parametrize("algo,p,q,schema", CASES)
 @pytest.mark.parametrize("weighted", [True, False])
-def test_rjs_walk_frequencies(algo, p, q, weighted):
+def test_rjs_walk_frequencies(algo, p, q, schema, weighted):
     """Rejection-sampled walks (Sec. 3.3) from one start: path frequencies
     match brute-force path probabilities, as the exact-mode walks' do, with
     and without property weights (also where 1/p or 1/q sets max(w))."""
     g = synth.random_graph(8, 0.45, seed=11, weighted=weighted, nlabels=3)
     L, W, start = 4, 60000, 0
-    bf = _bf_paths(g, start, L, algo, p, q, None)
+    bf = _bf_paths(g, start, L, algo, p, q, schema)
     assert_pvalue_follows(lambda k: merged_chisquare(bf, oracle.walk_rjs(g, np.full(W, start, np.int32), L, algo, p,
-                                                                          q, seed=9 + 7919 * k)[0]),
+                                                                          q, schema, seed=9 + 7919 * k)[0]),
                           ("oracle rjs paths", algo, p, q, weighted))
 
 
@@ -265,18 +265,19 @@ def test_rjs_proposal_is_lemire_index_of_the_trial_words():
             assert out[w, 1] == 1 + k, (d, w)
 
 
-@pytest.mark.parametrize("algo,p,q", [(a, p, q) for (a, p, q, s) in CASES if a != "metapath"])
-def test_rjs_class_envelope_walk_frequencies(algo, p, q):
-    """Rejection sampling under the weight-class envelope (classes of h
-    relative to h_MAX with bounds B, B/2, B/4) on weights spread over three
+@pytest.mark.parametrize("algo,p,q,schema", CASES)
+def test_rjs_class_envelope_walk_frequencies(algo, p, q, schema):
+    """Rejection sampling under the weight-class envelopes (classes of h
+    relative to h_MAX with bounds B, B/2, B/4; for metapath five classes
+    inside the required label's entries) on weights spread over three
     decades, so that every class is populated: path frequencies match
     brute-force path probabilities."""
     g = synth.random_graph(8, 0.45, seed=11, weighted=True, nlabels=3)
     g.h = (g.h ** 3 + np.float32(1e-3)).astype(np.float32)
     L, W, start = 4, 60000, 0
-    bf = _bf_paths(g, start, L, algo, p, q, None)
+    bf = _bf_paths(g, start, L, algo, p, q, schema)
     assert_pvalue_follows(lambda k: merged_chisquare(bf, oracle.walk_rjs(g, np.full(W, start, np.int32), L, algo, p,
-                                                                          q, seed=19 + 7919 * k,
+                                                                          q, schema, seed=19 + 7919 * k,
                                                                           envelope="classes")[0]),
                           ("oracle rjs class envelope paths", algo, p, q))
 
@@ -301,6 +302,30 @@ def test_rjs_class_envelope_slots():
     # the uniform proposal of the single bound spreads over the 5 entries instead
     single, _ = oracle.walk_rjs(g, np.zeros(W, np.int32), 1, "weighted", seed=seed)
     assert not np.array_equal(single, out)
+
+
+def test_rjs_label_class_envelope_slots():
+    """Metapath under the label-segment envelope: the label-1 entries of the
+    star centre carry h = M, M/2, M/4, M/8, M/16 (M = 1), each on its class
+    bound, so every proposal is accepted and hop 0 is the entry named by the
+    first slot.  Row (label, h): (1,1) (0,.7) (1,.125) (1,.5) (2,.3) (1,.0625)
+    (1,.25) (1,1) -> class order 0, 7 | 3 | 6 | 2 | 5 and 16*2 + 8 + 4 + 2 + 1
+    = 47 slots; labels 0 and 2 are never proposed."""
+    labs = [1, 0, 1, 1, 2, 1, 1, 1]
+    hs = [1.0, 0.7, 0.125, 0.5, 0.3, 0.0625, 0.25, 1.0]
+    slot_to_pos = [0] * 16 + [7] * 16 + [3] * 8 + [6] * 4 + [2] * 2 + [5]
+    g = synth.from_edges(9, [(0, i) for i in range(1, 9)], h=hs, labels=labs)
+    W, seed = 4096, 7
+    out, _ = oracle.walk_rjs(g, np.zeros(W, np.int32), 1, "metapath", schema=[1], seed=seed, envelope="classes")
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for w in range(W):
+        x = oracle.philox4x32_10([w, 0, 1, 0], key)
+        t = _lemire(x[0], 47)
+        t = _lemire(x[1], 47) if t is None else t
+        assert out[w, 1] == 1 + slot_to_pos[t], w
+    # a label the row lacks is a dead end
+    dead, _ = oracle.walk_rjs(g, np.zeros(4, np.int32), 2, "metapath", schema=[3], seed=seed, envelope="classes")
+    assert np.all(dead[:, 1:] == -1)
 
 
 def test_node2vec_p1q1_equals_weighted_walk():

@@ -69,7 +69,8 @@ MUTANTS = {
     # 8-bit weights: truncation instead of round-to-nearest
     "quantize_truncate": ("float c = rintf(h[i] / s);", "float c = floorf(h[i] / s);"),
     # RJS (Sec. 3.3): the proposal taken from the word that also gives U
-    "rjs_index_word": ("lemire_index(x[0], slots, &sl)", "lemire_index(x[2], slots, &sl)"),
+    "rjs_index_word": ("lemire_index(x[0], slots, &sl) && !lemire_index(x[1], slots, &sl)) continue;\n    int64_t k",
+                       "lemire_index(x[2], slots, &sl) && !lemire_index(x[1], slots, &sl)) continue;\n    int64_t k"),
     # RJS: the index taken as x mod d instead of Lemire's multiply-shift
     "rjs_index_modulo": ("*k = (uint32_t)(m >> 32);", "*k = x % d;"),
     # RJS: the bound from the row's first weight instead of h_MAX[v]
@@ -78,6 +79,10 @@ MUTANTS = {
     "rjs_class_boundary": ("const int ck = hrow[k] > half ? 0", "const int ck = hrow[k] >= half ? 0"),
     # weight-class envelope: class 1 proposed twice as often as class 2 but bounded by B
     "rjs_class_bound": ("        bound = 0.5f * B;", "        bound = B;"),
+    # label-segment envelope: an entry at exactly M/2^(c+1) moved up a class
+    "rjs_label_class_boundary": ("while (ck < 4 && !(x > t))", "while (ck < 4 && !(x >= t))"),
+    # label-segment envelope: class bounds quartered instead of halved
+    "rjs_label_bound": ("      bound = 0.5f * bound;", "      bound = 0.25f * bound;"),
     # RJS: acceptance test reversed
     "rjs_accept_reversed": ("if (U * bound < wt[k]) return k;", "if (U * bound > wt[k]) return k;"),
 }
