@@ -25,6 +25,14 @@
  *   - An exact inverse-CDF mode (FP32 prefix in neighbour order, one
  *     Philox4x32-10 uniform per hop) reproduces a plain CPU definition bit
  *     for bit; it is the parity mode, not a fast path [Sec. 2.2, ITS].
+ *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed by the
+ *     seed (low word, high word), counter (walker id, hop, stream, draw);
+ *     stream 0 is the exact mode's uniform, stream 1 the eRJS trials (draw =
+ *     trial; the proposal is Lemire's multiply-shift index of word 0, else
+ *     word 1, else none; U from word 2), stream 2 the eRVS keys.  No draw
+ *     depends on the launch, so a walk's rows depend only on the graph, the
+ *     parameters, the seed and the walker ids.  With a trial budget that no
+ *     step reaches, eRJS rows therefore follow from the definition alone.
  *
  * Conventions for every entry point:
  *   - Status codes are returned, never aborts; fw_last_error() gives a
@@ -112,7 +120,10 @@ typedef struct {
   float cost_ratio;      /* r = EdgeCost_RJS / EdgeCost_RVS of Eq. (runtime);
                             <= 0 selects the graph's tuned value (default 4)     */
   int32_t rjs_cap;       /* eRJS trials before a step is handed to eRVS;
-                            <= 0 selects 64                                      */
+                            <= 0: max(64, ceil(m / r)), m the entries that the
+                            eRVS hand-off would scan (d(v); in metapath's
+                            label-grouped view the required label's
+                            entries), r the cost ratio                        */
   uint32_t walker_base;  /* random-stream id of starts[0]; walker i uses
                             walker_base + i                                      */
   float gamma;           /* second-order PageRank parameter in [0, 1]            */
