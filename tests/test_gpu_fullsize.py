@@ -33,6 +33,9 @@ def _blocks(n, nblocks, size, seed):
 
 @pytest.mark.parametrize("p,q", PQ)
 def test_exact_mode_full_s22_sampled_rows(s22, p, q):
+    """All 4,194,304 walkers x 80 hops in exact mode; six contiguous 64-row
+    blocks and a seeded random subset of 65,536 walkers (all 80 hops) equal
+    the oracle's rows, which it computes walker by walker."""
     g, G = s22
     starts = torch.arange(g.n, dtype=torch.int32, device="cuda")
     out = G.walk(starts, 80, "node2vec", p=p, q=q, mode="exact", seed=42)
@@ -41,6 +44,10 @@ def test_exact_mode_full_s22_sampled_rows(s22, p, q):
         ref, _ = oracle.walk(g, sub, 80, "node2vec", p, q, seed=42, walker_base=b)
         got = out[b:b + 64].cpu().numpy()
         assert np.array_equal(got, ref), f"block {b}: {(got != ref).any(axis=1).sum()} rows differ"
+    sub = np.sort(np.random.default_rng(44).choice(g.n, 65_536, replace=False)).astype(np.int32)
+    ref, _ = oracle.walk_ids(g, sub, sub.astype(np.uint32), 80, "node2vec", p, q, seed=42)
+    got = out[torch.from_numpy(sub).cuda().long()].cpu().numpy()
+    assert np.array_equal(got, ref), f"{(got != ref).any(axis=1).sum()} of 65,536 sampled rows differ"
 
 
 @pytest.mark.parametrize("p,q,envelope", [(1.0, 1.0, "single"), (4.0, 0.25, "single"), (0.25, 4.0, "single"),
