@@ -44,6 +44,34 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(L, n)
 
 
+STRUCTS = [("fw_params", fw.fw_params), ("fw_graph_info_t", fw.fw_graph_info_t), ("fw_counters", fw.fw_counters),
+           ("fw_job", fw.fw_job), ("fw_server_config", fw.fw_server_config),
+           ("fw_server_stats_t", fw.fw_server_stats_t)]
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Size, alignment and every field offset of the binding's ctypes
+    structures equal those the C compiler gives the header's structs."""
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "flexiwalk.h"', "int main(void) {"]
+    for cname, py in STRUCTS:
+        lines.append(f'  printf("{cname} size %zu align %zu\\n", sizeof({cname}), _Alignof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()
+    got = dict(line.rsplit(" ", 1) for line in out if " size " not in line)
+    sizes = {w[0]: (int(w[2]), int(w[4])) for w in (line.split() for line in out if " size " in line)}
+    assert len(sizes) == len(STRUCTS) and len(got) == sum(len(py._fields_) for _, py in STRUCTS)
+    for cname, py in STRUCTS:
+        assert sizes[cname] == (ctypes.sizeof(py), ctypes.alignment(py)), cname
+        for fname, _ in py._fields_:
+            assert int(got[f"{cname}.{fname}"]) == getattr(py, fname).offset, (cname, fname)
+
+
 def test_params_default():
     p = fw.make_params()
     assert (p.p, p.q, p.mode, p.flags, p.schema_len, p.rjs_cap, p.walker_base) == (1.0, 1.0, 0, 0, 0, 0, 0)
