@@ -72,6 +72,29 @@ def test_binding_structs_match_the_header(tmp_path):
             assert int(got[f"{cname}.{fname}"]) == getattr(py, fname).offset, (cname, fname)
 
 
+def test_binding_constants_match_the_header(tmp_path):
+    """Status codes, algorithms, modes, pointer kinds and flags of the
+    binding equal the header's enumerators (values printed by a C program
+    compiled against the header)."""
+    want = {f"FW_ALGO_{k.upper()}": v for k, v in fw.ALGO.items()}
+    want.update({f"FW_MODE_{k.upper()}": v for k, v in fw.MODE.items()})
+    want.update({name: code for code, name in fw.STATUS.items()})
+    want.update({"FW_PTR_HOST": fw.PTR_HOST, "FW_PTR_DEVICE": fw.PTR_DEVICE})
+    want.update({f"FW_{k}": getattr(fw, k) for k in dir(fw) if k.startswith("FLAG_")})
+    lines = ["#include <stdio.h>", '#include "flexiwalk.h"', "int main(void) {"]
+    lines += [f'  printf("{k} %d\\n", (int){k});' for k in sorted(want)]
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "consts.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "consts"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    got = {out[i]: int(out[i + 1]) for i in range(0, len(out), 2)}
+    assert got == want
+    header = open(os.path.join(ROOT, "include", "flexiwalk.h")).read()
+    assert set(re.findall(r"\b(FW_FLAG_\w+)\s*=", header)) == {k for k in want if k.startswith("FW_FLAG_")}
+
+
 def test_params_default():
     p = fw.make_params()
     assert (p.p, p.q, p.mode, p.flags, p.schema_len, p.rjs_cap, p.walker_base) == (1.0, 1.0, 0, 0, 0, 0, 0)
