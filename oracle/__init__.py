@@ -90,7 +90,7 @@ def _load():
                                       i32]
             L.or_walk_ids.restype = i64
             L.or_walk_rjs.argtypes = [vp, vp, vp, vp, i32, vp, i32, i32, i32, f32, f32, f32, vp, i32, u64, u32, i32, vp,
-                                      i32]
+                                      i32, vp]
             L.or_walk_rjs.restype = i64
             L.or_node_stats.argtypes = [vp, vp, i32, vp, vp]
             L.or_node_stats.restype = ctypes.c_int
@@ -192,25 +192,28 @@ def walk(g, starts, length, algo, p=1.0, q=1.0, schema=None, seed=42, walker_bas
 
 
 def walk_rjs(g, starts, length, algo, p=1.0, q=1.0, schema=None, seed=42, walker_base=0, threads=0, gamma=0.2,
-             envelope="single"):
+             envelope="single", return_trials=False):
     """Walks whose every hop is drawn by rejection sampling against
     B = max(w) * h_MAX[v] (Sec. 3.3), trial t of hop j of walker i using
     Philox4x32-10 counter (i, j, 1, t): an index by Lemire's method from x0
     (else x1, else no proposal) and U = (x2 >> 8) * 2^-24.  envelope
     "single": the paper's uniform proposal; "classes": the weight-class
     slots of or_walk_rjs (weighted graphs), for metapath the five classes
-    inside the required label's entries.  Returns (out int32[W][L+1], hops)."""
+    inside the required label's entries.  Returns (out int32[W][L+1], hops),
+    and the number of trials of all hops (void ones included) as a third
+    element with return_trials."""
     L = _load()
     offsets, cols, h, labels = _graph_args(g)
     st = np.ascontiguousarray(starts, dtype=np.int32)
     s, slen = _schema_arr(schema)
     out = np.empty((st.shape[0], length + 1), dtype=np.int32)
+    trials = ctypes.c_int64(0)
     hops = L.or_walk_rjs(_ptr(offsets), _ptr(cols), _ptr(h), _ptr(labels), offsets.shape[0] - 1, _ptr(st),
                          st.shape[0], length, ALGOS.get(algo, algo), p, q, gamma, _ptr(s), slen, seed, walker_base,
-                         {"single": 0, "classes": 1}[envelope], _ptr(out), threads)
+                         {"single": 0, "classes": 1}[envelope], _ptr(out), threads, ctypes.byref(trials))
     if hops < 0:
         raise ValueError("or_walk_rjs: bad arguments")
-    return out, int(hops)
+    return (out, int(hops), int(trials.value)) if return_trials else (out, int(hops))
 
 
 def walk_ids(g, starts, ids, length, algo, p=1.0, q=1.0, schema=None, seed=42, threads=0, gamma=0.2):

@@ -224,7 +224,7 @@ static int64_t walk_impl(const int32_t *offsets, const int32_t *cols, const floa
                          const uint8_t *labels, int32_t n, const int32_t *starts, int32_t num_walkers,
                          int32_t len, int32_t algo, float p, float q, float gamma, const uint8_t *schema,
                          int32_t schema_len, uint64_t seed, uint32_t walker_base, const uint32_t *ids,
-                         int32_t sampler, int32_t *out, int32_t nthreads);
+                         int32_t sampler, int32_t *out, int32_t nthreads, int64_t *trials_out);
 
 int64_t or_walk(const int32_t *offsets, const int32_t *cols, const float *h,
                 const uint8_t *labels, int32_t n, const int32_t *starts, int32_t num_walkers,
@@ -232,7 +232,7 @@ int64_t or_walk(const int32_t *offsets, const int32_t *cols, const float *h,
                 int32_t schema_len, uint64_t seed, uint32_t walker_base, int32_t *out,
                 int32_t nthreads) {
   return walk_impl(offsets, cols, h, labels, n, starts, num_walkers, len, algo, p, q, gamma, schema, schema_len,
-                   seed, walker_base, NULL, 0, out, nthreads);
+                   seed, walker_base, NULL, 0, out, nthreads, NULL);
 }
 
 /* Same walks with an explicit random-stream id per walker (ids[i] instead
@@ -244,7 +244,7 @@ int64_t or_walk_ids(const int32_t *offsets, const int32_t *cols, const float *h,
                     int32_t nthreads) {
   if (!ids && num_walkers > 0) return -1;
   return walk_impl(offsets, cols, h, labels, n, starts, num_walkers, len, algo, p, q, gamma, schema, schema_len,
-                   seed, 0, ids, 0, out, nthreads);
+                   seed, 0, ids, 0, out, nthreads, NULL);
 }
 
 /* The same walks with every hop drawn by rejection sampling (RJS, Sec. 3.3)
@@ -268,15 +268,16 @@ int64_t or_walk_ids(const int32_t *offsets, const int32_t *cols, const float *h,
  * class 0, then (t - 4 n0)/2 of class 1, then t - 4 n0 - 2 n1 of class 2;
  * it is accepted iff U * (bound of its class) < w~.  Each entry is proposed
  * in proportion to its class bound, which is at least its w~, so accepted
- * draws follow Eq. (prob) as with the single bound. */
+ * draws follow Eq. (prob) as with the single bound.  trials_out (may be
+ * NULL) receives the number of trials of all hops, void ones included. */
 int64_t or_walk_rjs(const int32_t *offsets, const int32_t *cols, const float *h, const uint8_t *labels, int32_t n,
                     const int32_t *starts, int32_t num_walkers, int32_t len, int32_t algo, float p, float q,
                     float gamma, const uint8_t *schema, int32_t schema_len, uint64_t seed, uint32_t walker_base,
-                    int32_t envelope, int32_t *out, int32_t nthreads) {
+                    int32_t envelope, int32_t *out, int32_t nthreads, int64_t *trials_out) {
   if (envelope != 0 && envelope != 1) return -1;
   if (envelope == 1 && algo != OR_METAPATH && !h) return -1;
   return walk_impl(offsets, cols, h, labels, n, starts, num_walkers, len, algo, p, q, gamma, schema, schema_len,
-                   seed, walker_base, NULL, 1 + envelope, out, nthreads);
+                   seed, walker_base, NULL, 1 + envelope, out, nthreads, trials_out);
 }
 
 /* Lemire's map of a 32-bit word onto [0, d), d >= 1: *k = floor(x * d / 2^32)
@@ -297,7 +298,7 @@ static int lemire_index(uint32_t x, uint32_t d, uint32_t *k) {
  * slots, ord[] receiving the class order.  Returns k, or -1 when no
  * neighbour has weight (the proposal would never be accepted). */
 static int64_t rjs_pick(const float *wt, int64_t d, float B, const float *hrow, float hmax, int32_t *ord,
-                        uint64_t seed, uint32_t wid, uint32_t hop) {
+                        uint64_t seed, uint32_t wid, uint32_t hop, int64_t *trials) {
   int any = 0;
   for (int64_t k = 0; k < d; ++k) any |= wt[k] > 0.0f;
   if (!any) return -1;
@@ -320,6 +321,7 @@ static int64_t rjs_pick(const float *wt, int64_t d, float B, const float *hrow, 
     const uint32_t ctr[4] = {wid, hop, 1u, t};
     uint32_t x[4], sl;
     or_philox4x32_10(ctr, key, x);
+    ++*trials;
     if (!lemire_index(x[0], slots, &sl) && !lemire_index(x[1], slots, &sl)) continue;
     int64_t k = sl;
     float bound = B;
@@ -344,7 +346,7 @@ static int64_t rjs_pick(const float *wt, int64_t d, float B, const float *hrow, 
  * (labrow, hrow; hrow NULL: h = 1).  Returns the row position, or -1 when
  * no entry has the label. */
 static int64_t rjs_pick_label(const float *hrow, const uint8_t *labrow, uint8_t want, int64_t d, int32_t *ord,
-                              uint64_t seed, uint32_t wid, uint32_t hop) {
+                              uint64_t seed, uint32_t wid, uint32_t hop, int64_t *trials) {
   float M = 0.0f;
   for (int64_t k = 0; k < d; ++k) {
     const float x = hrow ? hrow[k] : 1.0f;
@@ -375,6 +377,7 @@ static int64_t rjs_pick_label(const float *hrow, const uint8_t *labrow, uint8_t 
     const uint32_t ctr[4] = {wid, hop, 1u, t};
     uint32_t x[4], sl;
     or_philox4x32_10(ctr, key, x);
+    ++*trials;
     if (!lemire_index(x[0], slots, &sl) && !lemire_index(x[1], slots, &sl)) continue;
     uint32_t base = 0;
     int c = 0;
@@ -395,7 +398,7 @@ static int64_t walk_impl(const int32_t *offsets, const int32_t *cols, const floa
                          const uint8_t *labels, int32_t n, const int32_t *starts, int32_t num_walkers,
                          int32_t len, int32_t algo, float p, float q, float gamma, const uint8_t *schema,
                          int32_t schema_len, uint64_t seed, uint32_t walker_base, const uint32_t *ids,
-                         int32_t sampler, int32_t *out, int32_t nthreads) {
+                         int32_t sampler, int32_t *out, int32_t nthreads, int64_t *trials_out) {
   if (!offsets || !cols || !starts || !out || num_walkers < 0 || len < 0 || n < 0) return -1;
   for (int32_t i = 0; i < num_walkers; ++i)
     if (starts[i] < 0 || starts[i] >= n) return -1;
@@ -410,9 +413,9 @@ static int64_t walk_impl(const int32_t *offsets, const int32_t *cols, const floa
 #else
   (void)nthreads;
 #endif
-  int64_t hops = 0;
+  int64_t hops = 0, trials = 0;
   int failed = 0;
-#pragma omp parallel reduction(+ : hops)
+#pragma omp parallel reduction(+ : hops, trials)
   {
     float *wt = (float *)malloc((size_t)(maxd > 0 ? maxd : 1) * sizeof(float));
     int32_t *ord = (int32_t *)malloc((size_t)(maxd > 0 ? maxd : 1) * sizeof(int32_t));
@@ -436,7 +439,7 @@ static int64_t walk_impl(const int32_t *offsets, const int32_t *cols, const floa
           k = or_icdf_pick(wt, d, or_exact_uniform(seed, wid, (uint32_t)j));
         } else if (sampler == 2 && algo == OR_METAPATH) {
           k = rjs_pick_label(h ? h + offsets[cur] : NULL, labels + offsets[cur], schema[j % schema_len], d, ord, seed,
-                             wid, (uint32_t)j);
+                             wid, (uint32_t)j, &trials);
         } else {
           float hmax = 0.0f, B;
           for (int64_t e = offsets[cur]; e < offsets[cur + 1]; ++e) {
@@ -446,7 +449,7 @@ static int64_t walk_impl(const int32_t *offsets, const int32_t *cols, const floa
           const int32_t dprev = prev >= 0 ? offsets[prev + 1] - offsets[prev] : 0;
           if (d == 0 || or_step_plan(hmax, 0.0f, prev >= 0, (int32_t)d, dprev, algo, p, q, gamma, 1.0f, &B, NULL) < 0)
             break;
-          k = rjs_pick(wt, d, B, sampler == 2 ? h + offsets[cur] : NULL, hmax, ord, seed, wid, (uint32_t)j);
+          k = rjs_pick(wt, d, B, sampler == 2 ? h + offsets[cur] : NULL, hmax, ord, seed, wid, (uint32_t)j, &trials);
         }
         if (k < 0) break;
         int32_t nxt = cols[offsets[cur] + k];
@@ -460,6 +463,7 @@ static int64_t walk_impl(const int32_t *offsets, const int32_t *cols, const floa
     free(wt);
     free(ord);
   }
+  if (trials_out) *trials_out = trials;
   return failed ? -1 : hops;
 }
 

@@ -328,6 +328,44 @@ def test_rjs_label_class_envelope_slots():
     assert np.all(dead[:, 1:] == -1)
 
 
+@pytest.mark.parametrize("envelope", ["single", "classes"])
+@pytest.mark.parametrize("algo,schema", [("weighted", None), ("metapath", [2])])
+def test_rjs_mean_trials_equal_envelope_mass_ratio(envelope, algo, schema):
+    """Sec. 3.3: a trial accepts with probability (sum of w~) / (envelope
+    mass), so the trials per hop are geometric with mean mass / sum w~:
+    single bound d * h_MAX; weight classes (4 n0 + 2 n1 + n2) * h_MAX / 4;
+    metapath label segment (16 n0 + 8 n1 + 4 n2 + 2 n3 + n4) * M / 16 over
+    the required label's entries (single bound: d * h_MAX over the row)."""
+    g = synth.workload_graph("small")
+    g.h = synth.edge_weights(g, "lognormal", 1.5, seed=13)
+    v = int(np.argmax(g.degrees()))
+    h = g.h[g.offsets[v]:g.offsets[v + 1]].astype(np.float64)
+    lab = g.labels[g.offsets[v]:g.offsets[v + 1]]
+    hmax = h.max()
+    if algo == "weighted":
+        total = h.sum()
+        if envelope == "single":
+            mass = len(h) * hmax
+        else:
+            n0, n1 = int((h > hmax / 2).sum()), int(((h > hmax / 4) & (h <= hmax / 2)).sum())
+            mass = (4 * n0 + 2 * n1 + (len(h) - n0 - n1)) * hmax / 4
+    else:
+        hl = h[lab == schema[0]]
+        total = hl.sum()
+        if envelope == "single":
+            mass = len(h) * hmax
+        else:
+            M = hl.max()
+            cls = np.minimum(np.floor(-np.log2(hl / M)).astype(int), 4)  # class c: h in (M/2^(c+1), M/2^c]
+            mass = sum((16 >> c) * int((cls == c).sum()) for c in range(5)) * M / 16
+    W = 200_000
+    _, hops, trials = oracle.walk_rjs(g, np.full(W, v, np.int32), 1, algo, schema=schema, seed=3,
+                                      envelope=envelope, return_trials=True)
+    assert hops == W
+    e = mass / total
+    assert abs(trials / hops - e) < 5 * np.sqrt(e * (e - 1) / W) + 1e-3, (trials / hops, e)
+
+
 def test_node2vec_p1q1_equals_weighted_walk():
     """node2vec with p = q = 1 has w = 1 everywhere, so its walks equal the
     weighted first-order walk bit for bit under the same draws."""
