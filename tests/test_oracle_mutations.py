@@ -15,6 +15,7 @@ GPU parity tests can tell those apart.
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 import pytest
 
@@ -97,27 +98,42 @@ def _build(tmp_path, name, text):
 
 
 def _run_pins(so):
-    env = dict(os.environ, FW_ORACLE_LIB=so, OMP_NUM_THREADS="4")
+    env = dict(os.environ, FW_ORACLE_LIB=so, OMP_NUM_THREADS="2")
     r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(HERE, "test_oracle.py"), "-x", "-q",
                         "-p", "no:cacheprovider", "-m", "not gpu"], cwd=ROOT, env=env, capture_output=True,
-                       text=True, timeout=600)
+                       text=True, timeout=900)
     return r.returncode, r.stdout[-3000:] + r.stderr[-2000:]
 
 
-def test_unmodified_oracle_passes_through_the_harness(tmp_path):
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    """(return code, output tail) of the pins for the unmodified copy and for
+    every mutant; the child runs proceed side by side."""
     with open(SRC) as f:
         text = f.read()
-    rc, out = _run_pins(_build(tmp_path, "unmodified", text))
+    d = tmp_path_factory.mktemp("mutants")
+    sources = {"unmodified": text}
+    for name, (old, new) in MUTANTS.items():
+        if text.count(old) == 1:
+            sources[name] = text.replace(old, new)
+    workers = max(1, min(8, (os.cpu_count() or 2) // 2))
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        futs = {name: ex.submit(lambda nm, src: _run_pins(_build(d, nm, src)), name, src)
+                for name, src in sources.items()}
+        return {name: f.result() for name, f in futs.items()}
+
+
+def test_unmodified_oracle_passes_through_the_harness(outcomes):
+    rc, out = outcomes["unmodified"]
     assert rc == 0, out
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_planted_mistake_fails_a_pin(tmp_path, name):
-    old, new = MUTANTS[name]
+def test_planted_mistake_fails_a_pin(outcomes, name):
+    old, _ = MUTANTS[name]
     with open(SRC) as f:
-        text = f.read()
-    assert text.count(old) == 1, f"{name}: the text to mutate must occur exactly once"
-    rc, out = _run_pins(_build(tmp_path, name, text.replace(old, new)))
+        assert f.read().count(old) == 1, f"{name}: the text to mutate must occur exactly once"
+    rc, out = outcomes[name]
     # 1 = some test failed; anything else (0 = all passed, 2+ = harness or
     # collection error) does not show that a pin caught the mistake
     assert rc == 1, f"{name}: pins returned {rc}\n{out}"
