@@ -67,6 +67,19 @@ MUTANTS = {
                             "return (r * B > S) ? OR_MODE_RJS : OR_MODE_RVS;"),
     # per-label statistics: label sums into the wrong slot
     "label_stats_slot": ("lsum[v * 8 + l] += (double)x;", "lsum[v * 8 + (l + 1) % 8] += (double)x;"),
+    # Eq. (prob): weights returned without normalisation
+    "probs_not_normalised": ("probs[k] = total > 0.0 ? (double)wt[k] / total : 0.0;",
+                             "probs[k] = total > 0.0 ? (double)wt[k] : 0.0;"),
+    # walk: the row after a dead end filled with node 0 instead of -1
+    "walk_suffix_zero": ("for (int32_t r = j + 1; r <= len; ++r) row[r] = -1;",
+                         "for (int32_t r = j + 1; r <= len; ++r) row[r] = 0;"),
+    # walk: the random-stream id ignores walker_base
+    "walk_base_ignored": ("const uint32_t wid = ids ? ids[i] : walker_base + (uint32_t)i;",
+                          "const uint32_t wid = ids ? ids[i] : (uint32_t)i;"),
+    # per-label statistics: the last weight instead of the largest
+    "label_stats_last": ("if (x > lmax[v * 8 + l]) lmax[v * 8 + l] = x;", "lmax[v * 8 + l] = x;"),
+    # 8-bit weights: codes allowed to reach 0 (an edge losing its weight)
+    "quantize_clamp_zero": ("if (c < 1.0f) c = 1.0f;", "if (c < 0.0f) c = 0.0f;"),
     # 8-bit weights: truncation instead of round-to-nearest
     "quantize_truncate": ("float c = rintf(h[i] / s);", "float c = floorf(h[i] / s);"),
     # RJS (Sec. 3.3): the proposal taken from the word that also gives U
