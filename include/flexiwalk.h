@@ -166,7 +166,8 @@ typedef struct {
 typedef struct fw_graph fw_graph;
 
 /* Fill p = q = 1, gamma = 0.2, mode AUTO, cost_ratio = 0 (tuned),
- * rjs_cap = 0 (64), flags 0, walker_base 0, empty schema. */
+ * rjs_cap = 0 (the default trial budget, see fw_params), flags 0,
+ * walker_base 0, empty schema. */
 void fw_params_default(fw_params* params);
 
 /*
