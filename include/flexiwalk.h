@@ -447,7 +447,6 @@ fw_status fw_server_stats(fw_server* server, fw_server_stats_t* out);
 /* Stop accepting queries, finish every submitted one, free the server. */
 fw_status fw_server_destroy(fw_server* server);
 
-/* Number of kernel launches this library has issued (process-wide). */
 /*
  * Measurement hook for the walk kernel's roofline (no counterpart in the
  * paper, whose kernels it does not change).  eRJS trials, node-record
@@ -465,6 +464,7 @@ fw_status fw_server_destroy(fw_server* server);
  */
 fw_status fw_gather_ceiling(void* table, uint64_t table_bytes, double* rate_out, void* stream);
 
+/* Number of kernel launches this library has issued (process-wide). */
 uint64_t fw_launch_count(void);
 
 const char* fw_last_error(void);
