@@ -467,7 +467,11 @@ fw_status fw_gather_ceiling(void* table, uint64_t table_bytes, double* rate_out,
 /* Number of kernel launches this library has issued (process-wide). */
 uint64_t fw_launch_count(void);
 
+/* Message of the last failing call of this thread ("" if none); the
+ * pointer stays valid until this thread's next call into the library. */
 const char* fw_last_error(void);
+/* Name of a status code ("FW_OK", "FW_ERR_ARG", ..., "FW_ERR_UNKNOWN" for
+ * other values); static storage. */
 const char* fw_status_string(fw_status status);
 
 #ifdef __cplusplus
