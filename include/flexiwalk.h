@@ -136,7 +136,7 @@ typedef struct {
   int32_t max_degree;
   int32_t has_weights;
   int32_t has_labels;
-  float cost_ratio;          /* current tuned r                                  */
+  float cost_ratio;          /* current r of node2vec (= cost_ratios[1])         */
   double preprocess_ms;      /* h_MAX / h_SUM reductions, Sec. 4.2 preprocess()  */
   size_t device_bytes;       /* device memory held by the graph                  */
   int32_t symmetric;         /* 1: every edge (v,u) has a mirror (u,v) with the
@@ -196,6 +196,8 @@ fw_status fw_graph_create(const int32_t* offsets, const int32_t* cols, const flo
 /* Release all device memory of the graph (synchronises the device). */
 fw_status fw_graph_destroy(fw_graph* graph);
 
+/* Fill *info (host memory) from the graph's host-side state; no device
+ * work.  FW_ERR_ARG for a NULL argument. */
 fw_status fw_graph_info(const fw_graph* graph, fw_graph_info_t* info);
 
 /* Copy the preprocessed h_MAX[n] and h_SUM[n] (float32) into the device
