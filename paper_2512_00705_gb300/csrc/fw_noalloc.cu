@@ -20,8 +20,11 @@
 // overlap on the GPU if one of them failed after enqueueing work; such
 // overlapping calls race on the shared array.
 //
-// The first call on a device looks up the array's device address
-// (cudaGetSymbolAddress); make that first call before any stream capture.
+// Every call looks up the array's device address on the current device
+// (cudaGetSymbolAddress, under the lock), so a device reset and a reloaded
+// module leave no stale address behind; the first call on a device also
+// loads the module that holds the array, so make it before any stream
+// capture.
 #include <mutex>
 
 #include "fw_internal.h"
@@ -30,24 +33,18 @@ namespace {
 
 constexpr size_t kNoAllocScratchBytes = 16u << 20;   // 16 MiB
 constexpr size_t kHeader = 256;                      // queue counter + padding
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 std::mutex g_noalloc_mu;
-void* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the symbol's host-side name is only a stand-in).
-fw_status scratch_address(int device, unsigned char** out) {
-  if (device < 0 || device >= kMaxDevices) return fw::set_error(FW_ERR_UNSUPPORTED, "device ordinal too large");
-  if (!g_scratch_addr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return fw::cuda_error(e, "cudaGetSymbolAddress(no-alloc scratch)");
-    g_scratch_addr[device] = p;
-  }
-  *out = static_cast<unsigned char*>(g_scratch_addr[device]);
+// Device address of the scratch array on the current device (the symbol's
+// host-side name is only a stand-in).
+fw_status scratch_address(unsigned char** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return fw::cuda_error(e, "cudaGetSymbolAddress(no-alloc scratch)");
+  *out = static_cast<unsigned char*>(p);
   return FW_OK;
 }
 
@@ -60,14 +57,19 @@ extern "C" fw_status fw_walk_host_noalloc(const fw_graph* g, const int32_t* star
   if (!g) return set_error(FW_ERR_ARG, "graph is NULL");
   if (num_walkers < 0 || len < 0) return set_error(FW_ERR_ARG, "negative size");
   if (num_walkers > 0 && (!starts || !out)) return set_error(FW_ERR_ARG, "NULL starts/out");
-  // staged starts, then staged rows starting on a 256-byte boundary
-  const size_t in_bytes = (size_t)num_walkers * sizeof(int32_t);
+  // staged starts, then staged rows starting on a 256-byte boundary; each
+  // term is bounded before it is added, so no product or sum can wrap
+  const size_t limit = kNoAllocScratchBytes - kHeader;
+  const size_t in_bytes = (size_t)num_walkers * sizeof(int32_t);  // < 2^33
   const size_t rows_off = (in_bytes + 255) & ~(size_t)255;
-  const size_t out_bytes = (size_t)num_walkers * ((size_t)len + 1) * sizeof(int32_t);
-  if (rows_off + out_bytes > kNoAllocScratchBytes - kHeader)
-    return set_error(FW_ERR_ARG, "request needs " + std::to_string(rows_off + out_bytes) +
-                                     " bytes of staging; fw_walk_host_noalloc holds at most " +
-                                     std::to_string(kNoAllocScratchBytes - kHeader) + " (use fw_walk_host)");
+  const size_t row_bytes = ((size_t)len + 1) * sizeof(int32_t);    // < 2^34
+  const bool fits = rows_off <= limit && (num_walkers == 0 || row_bytes <= (limit - rows_off) / (size_t)num_walkers);
+  if (!fits)
+    return set_error(FW_ERR_ARG, "request of " + std::to_string(num_walkers) + " walkers x " +
+                                     std::to_string((long long)len + 1) +
+                                     " row entries does not fit the staging array; fw_walk_host_noalloc holds at most " +
+                                     std::to_string(limit) + " bytes (use fw_walk_host)");
+  const size_t out_bytes = (size_t)num_walkers * row_bytes;
   Job J;
   fw_status s = make_job(g, algo, params, seed, &J);
   if (s != FW_OK) return s;
@@ -79,7 +81,7 @@ extern "C" fw_status fw_walk_host_noalloc(const fw_graph* g, const int32_t* star
   if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
   if (dev != g->device) return set_error(FW_ERR_ARG, "the graph lives on another device than the current one");
   unsigned char* base = nullptr;
-  s = scratch_address(dev, &base);
+  s = scratch_address(&base);
   if (s != FW_OK) return s;
   auto* qctr = reinterpret_cast<unsigned long long*>(base);
   auto* d_starts = reinterpret_cast<int32_t*>(base + kHeader);

@@ -343,12 +343,17 @@ extern "C" fw_status fw_server_submit(fw_server* s, const int32_t* starts, int32
   if (params) r->params = *params;
   else fw_params_default(&r->params);
   r->seed = seed;
-  r->rows_off = round256(sizeof(int32_t) * (size_t)num_walkers);
-  r->bytes = r->rows_off + round256(sizeof(int32_t) * (size_t)num_walkers * ((size_t)len + 1));
-  if (r->bytes > s->cfg.mem_budget) {
+  // staged starts and rows must fit the budget; each term is bounded before
+  // it is added or multiplied, so nothing wraps
+  r->rows_off = round256(sizeof(int32_t) * (size_t)num_walkers);  // < 2^34
+  const size_t row_bytes = sizeof(int32_t) * ((size_t)len + 1);    // < 2^34
+  const size_t budget = s->cfg.mem_budget;
+  if (r->rows_off > budget || (num_walkers > 0 && row_bytes > (budget - r->rows_off) / (size_t)num_walkers) ||
+      r->rows_off + round256(row_bytes * (size_t)num_walkers) > budget) {
     delete r;
     return set_error(FW_ERR_OOM, "query needs more device memory than the server's budget");
   }
+  r->bytes = r->rows_off + round256(row_bytes * (size_t)num_walkers);
   r->t_submit = Clock::now();
   {
     std::lock_guard<std::mutex> lk(s->mu);
