@@ -397,6 +397,40 @@ def test_counters(small):
     assert np.array_equal(o, plain), "counting build must not change the walks"
 
 
+@pytest.mark.parametrize("algo,p,q,envelope", [("node2vec", 2.0, 0.5, "single"), ("node2vec", 0.25, 4.0, "single"),
+                                               ("node2vec", 4.0, 0.25, "single"), ("weighted", 1.0, 1.0, "single"),
+                                               ("node2vec", 1.0, 1.0, "classes"), ("node2vec", 4.0, 0.25, "classes"),
+                                               ("node2vec", 2.0, 0.5, "classes"), ("weighted", 1.0, 1.0, "classes")])
+def test_counters_match_oracle_trials_and_byte_model(small, algo, p, q, envelope):
+    """The counting build's trial counter equals the oracle's count of
+    rejection trials (void Lemire draws included) on walks that are
+    bit-identical to the oracle's, and its byte counter equals the byte
+    model recomputed here from those trials: 32 B for each walker's first
+    node record (later ones ride in the accepted trial's edge record), 32 B
+    per trial (one edge record; a trial whose two Lemire draws both fall in
+    the rejection zone reads nothing, about 1e-12 per trial at these
+    degrees), 32 B per membership probe (the GPU's probe count) and 4 B per
+    row entry written."""
+    g, G = small
+    W, L = 4093, 20
+    starts = synth.random_starts(g.n, W, seed=17)
+    flags = fw.FLAG_COUNTERS | (fw.FLAG_PLAIN_RJS if envelope == "single" else 0)
+    G.reset_counters()
+    out = G.walk(_cuda(starts), L, algo, p=p, q=q, mode="rjs", flags=flags, rjs_cap=NO_HANDOFF, seed=42,
+                 walker_base=11).cpu().numpy()
+    c = G.counters()
+    ref, hops, trials = oracle.walk_rjs(g, starts, L, algo, p, q, seed=42, walker_base=11, envelope=envelope,
+                                        return_trials=True)
+    assert np.array_equal(out, ref), f"{(out != ref).any(axis=1).sum()} rows differ"
+    assert c["hops"] == hops
+    assert c["rjs_trials"] == trials, (c["rjs_trials"], trials)
+    assert c["rvs_steps"] == 0 and c["handoffs"] == 0 and c["rjs_steps"] == hops
+    if algo == "weighted" or (p == 1.0 and q == 1.0):
+        assert c["probes"] == 0
+    model = 32 * W + 32 * trials + 32 * c["probes"] + 4 * hops
+    assert c["bytes"] == model, (c["bytes"], model)
+
+
 # ------------------------------------------------------------ whole-walk distributions
 def _asymmetric(g, seed):
     """Same structure, an independent weight on each direction of every edge."""
