@@ -20,7 +20,7 @@ sampling, its own Philox4x32-10), compiled here with gcc and
   step_plan             bound (Sec. 3.3) + sum estimate (Eq. sum_estimation)
                         + cost-model choice (Eq. runtime)
   label_stats           per-node, per-label max / sum of h (labels < 8)
-  quantize_weights      8-bit weight codes with one scale per graph (Sec. 6.2
+  quantize_weights      8-bit weight codes with one scale per node (Sec. 6.2
                         names low-precision weights as an extension)
 
 Graph arguments are any object with ``offsets``, ``cols``, ``h`` (or None)
@@ -98,8 +98,8 @@ def _load():
             L.or_step_plan.restype = ctypes.c_int
             L.or_label_stats.argtypes = [vp, vp, vp, i32, vp, vp]
             L.or_label_stats.restype = ctypes.c_int
-            L.or_quantize_weights.argtypes = [vp, i64, vp, vp]
-            L.or_quantize_weights.restype = f32
+            L.or_quantize_weights.argtypes = [vp, i32, vp, vp, vp, vp]
+            L.or_quantize_weights.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -266,10 +266,15 @@ def label_stats(g):
     return lmax, lsum
 
 
-def quantize_weights(h):
-    """(codes uint8[e], scale float, dequantized float32[e]) of property weights h."""
-    hh = np.ascontiguousarray(h, dtype=np.float32)
-    codes = np.zeros(hh.shape[0], dtype=np.uint8)
-    hq = np.zeros(hh.shape[0], dtype=np.float32)
-    s = _load().or_quantize_weights(_ptr(hh), hh.shape[0], _ptr(codes), _ptr(hq))
-    return codes, float(np.float32(s)), hq
+def quantize_weights(g):
+    """(codes uint8[e], scales float32[n], dequantized float32[e]) of the
+    graph's property weights, one scale per node (its row's maximum / 255)."""
+    offsets, _, h, _ = _graph_args(g)
+    n = offsets.shape[0] - 1
+    e = int(offsets[-1])
+    codes = np.zeros(e, dtype=np.uint8)
+    scales = np.zeros(n, dtype=np.float32)
+    hq = np.zeros(e, dtype=np.float32)
+    if _load().or_quantize_weights(_ptr(offsets), n, _ptr(h), _ptr(codes), _ptr(scales), _ptr(hq)) != 0:
+        raise ValueError("or_quantize_weights: bad arguments")
+    return codes, scales, hq

@@ -570,23 +570,30 @@ int or_label_stats(const int32_t *offsets, const float *h, const uint8_t *labels
 }
 
 /* 8-bit property weights (Sec. 6.2 names low-precision weights as an
- * extension; the format is this reading): one FP32 scale per graph,
- * s = (max over all edges of h) / 255, each weight stored as the nearest
- * integer multiple of s (ties to even), kept within 1..255 so that no edge
- * loses its weight, and read back as code * s.  FP32 throughout, each
- * operation rounded once.  codes / hq may be NULL.  Returns s (0 if e = 0). */
-float or_quantize_weights(const float *h, int64_t e, uint8_t *codes, float *hq) {
-  if (e <= 0) return 0.0f;
-  float hmax = h[0];
-  for (int64_t i = 1; i < e; ++i)
-    if (h[i] > hmax) hmax = h[i];
-  const float s = hmax / 255.0f;
-  for (int64_t i = 0; i < e; ++i) {
-    float c = rintf(h[i] / s);
-    if (c < 1.0f) c = 1.0f;
-    if (c > 255.0f) c = 255.0f;
-    if (codes) codes[i] = (uint8_t)c;
-    if (hq) hq[i] = c * s;
+ * extension; the format is this reading): one FP32 scale per node, from the
+ * node's own row, s_v = (max over the row of v of h) / 255; each weight
+ * h(v,u) is stored as the nearest integer multiple of s_v (ties to even),
+ * kept within 1..255 so that no edge loses its weight, and read back as
+ * code * s_v.  Every row's largest weight gets code 255, so every row keeps
+ * its distribution to within half a code step of its own maximum.  FP32
+ * throughout, each operation rounded once.  codes / scales / hq may be NULL;
+ * rows without entries get scale 0.  Returns 0, or -1 on bad arguments. */
+int or_quantize_weights(const int32_t *offsets, int32_t n, const float *h, uint8_t *codes, float *scales,
+                        float *hq) {
+  if (!offsets || n < 0 || (!h && offsets[n] > 0)) return -1;
+  for (int32_t v = 0; v < n; ++v) {
+    float row_max = 0.0f;
+    for (int64_t i = offsets[v]; i < offsets[v + 1]; ++i)
+      if (h[i] > row_max) row_max = h[i];
+    const float s = row_max / 255.0f;
+    if (scales) scales[v] = s;
+    for (int64_t i = offsets[v]; i < offsets[v + 1]; ++i) {
+      float c = rintf(h[i] / s);
+      if (c < 1.0f) c = 1.0f;
+      if (c > 255.0f) c = 255.0f;
+      if (codes) codes[i] = (uint8_t)c;
+      if (hq) hq[i] = c * s;
+    }
   }
-  return s;
+  return 0;
 }

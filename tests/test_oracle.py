@@ -460,59 +460,106 @@ def test_label_stats_match_library_reductions():
 
 
 # ------------------------------------------------------ 8-bit weights
+def _rows(*rows):
+    """A CSR whose row v holds the weights rows[v] (columns are placeholders:
+    quantization reads only the rows' weights)."""
+    n = max(len(rows), max(len(r) for r in rows) + 1)
+    offsets = np.zeros(n + 1, dtype=np.int32)
+    offsets[1:len(rows) + 1] = np.cumsum([len(r) for r in rows])
+    offsets[len(rows) + 1:] = offsets[len(rows)]
+    cols = np.concatenate([np.arange(1, len(r) + 1) for r in rows]).astype(np.int32)
+    h = np.concatenate([np.asarray(r, np.float32) for r in rows]).astype(np.float32)
+    return synth.Csr(offsets, cols, h)
+
+
 def test_quantize_on_the_integer_grid():
-    """max h = 255 makes the scale exactly 1: codes are h rounded to the
-    nearest integer with ties to even, kept in 1..255, and read back exactly."""
-    h = np.array([255.0, 1.0, 2.0, 0.4, 2.5, 3.5, 254.5, 100.49, 0.5, 1.5, 17.0], np.float32)
-    codes, s, hq = oracle.quantize_weights(h)
-    assert s == 1.0
-    np.testing.assert_array_equal(codes, [255, 1, 2, 1, 2, 4, 254, 100, 1, 2, 17])
-    np.testing.assert_array_equal(hq, codes.astype(np.float32))
-    c0, s0, _ = oracle.quantize_weights(np.zeros(0, np.float32))
-    assert s0 == 0.0 and c0.shape == (0,)
+    """A row whose maximum is 255 gets scale exactly 1: codes are h rounded to
+    the nearest integer with ties to even, kept in 1..255, read back exactly.
+    A row with maximum 127.5 gets scale exactly 1/2 of its own, whatever the
+    other rows hold; rows without entries get scale 0."""
+    g = _rows([255.0, 1.0, 2.0, 0.4, 2.5, 3.5, 254.5, 100.49, 0.5, 1.5, 17.0],
+              [127.5, 0.25, 1.0, 0.75, 1.25, 0.2],
+              [])
+    codes, scales, hq = oracle.quantize_weights(g)
+    assert scales[0] == 1.0 and scales[1] == 0.5 and np.all(scales[2:] == 0.0)
+    np.testing.assert_array_equal(codes[:11], [255, 1, 2, 1, 2, 4, 254, 100, 1, 2, 17])
+    np.testing.assert_array_equal(codes[11:], [255, 1, 2, 2, 2, 1])  # 0.75/0.5 = 1.5 -> 2, 1.25/0.5 = 2.5 -> 2
+    np.testing.assert_array_equal(hq, codes.astype(np.float32) * np.repeat(scales, np.diff(g.offsets)))
 
 
 @pytest.mark.parametrize("kind,param", [("uniform01", 1.0), ("lognormal", 1.0), ("pareto", 1.5)])
 def test_quantize_is_nearest_code_within_half_a_step(kind, param):
-    """Against fp64: s is max(h)/255 rounded once, every unclamped code is the
-    nearest integer to h/s (|code - h/s| <= 1/2, so a floor or a ceiling
-    fails), the largest weight gets 255, and only weights below s/2 clamp."""
+    """Against fp64, row by row: s_v is the row's max h / 255 rounded once,
+    the row's largest weight gets 255, every unclamped code is the nearest
+    integer to h / s_v (|code - h/s_v| <= 1/2, so a floor or a ceiling
+    fails), and only weights below s_v / 2 clamp to 1."""
     g = synth.rmat(12, 16, seed=5)
-    h = synth.edge_weights(g, kind, param, seed=6)
-    codes, s, hq = oracle.quantize_weights(h)
-    hmax = float(h.max())
-    assert s == float(np.float32(hmax / 255.0))
-    assert codes.min() >= 1 and codes[np.argmax(h)] == 255
-    ratio = h.astype(np.float64) / s
-    un = ratio >= 0.5 + 1e-6
-    assert np.all(np.abs(codes[un] - ratio[un]) <= 0.5 + 1e-5)
+    g.h = synth.edge_weights(g, kind, param, seed=6)
+    codes, scales, hq = oracle.quantize_weights(g)
+    deg = np.diff(g.offsets)
+    rows = np.repeat(np.arange(g.n), deg)
+    rmax = np.zeros(g.n, np.float32)
+    np.maximum.at(rmax, rows, g.h)
+    assert np.array_equal(scales, (rmax.astype(np.float64) / 255.0).astype(np.float32))
+    nz = np.nonzero(deg > 0)[0]
+    cmax = np.zeros(g.n, np.int64)
+    np.maximum.at(cmax, rows, codes.astype(np.int64))
+    assert np.all(cmax[nz] == 255) and codes.min() >= 1
+    s = scales[rows].astype(np.float64)
+    ratio = g.h.astype(np.float64) / s
+    slack = ratio * 2.0 ** -22  # the FP32 quotient h / s_v may sit this far from the exact one
+    un = ratio >= 0.5 + slack
+    assert np.all(np.abs(codes[un] - ratio[un]) <= 0.5 + slack[un])
     assert np.all(codes[~un] == 1)
     np.testing.assert_array_equal(hq, (codes.astype(np.float64) * s).astype(np.float32))
-    assert np.all(np.abs(hq[un].astype(np.float64) - h[un]) <= 0.5 * s * (1 + 1e-5))
+    assert np.all(np.abs(hq[un].astype(np.float64) - g.h[un]) <= (0.5 + slack[un]) * s[un] + hq[un] * 2.0 ** -23)
+
+
+def test_quantize_scale_is_per_row():
+    """Multiplying one row's weights by 1000 leaves every other row's codes
+    and scale unchanged, and that row's codes too (its scale grows 1000-fold
+    up to rounding)."""
+    g = synth.rmat(10, 8, seed=2)
+    g.h = synth.edge_weights(g, "lognormal", 1.0, seed=3)
+    c, s, _ = oracle.quantize_weights(g)
+    deg = np.diff(g.offsets)
+    v = int(np.argmax(deg))
+    h2 = g.h.copy()
+    h2[g.offsets[v]:g.offsets[v + 1]] *= np.float32(1024.0)
+    c2, s2, _ = oracle.quantize_weights(synth.Csr(g.offsets, g.cols, h2))
+    np.testing.assert_array_equal(c2, c)
+    other = np.arange(g.n) != v
+    np.testing.assert_array_equal(s2[other], s[other])
+    assert s2[v] == s[v] * 1024.0
 
 
 def test_quantize_commutes_with_power_of_two_scaling():
-    """Scaling every weight by 2^k scales s by 2^k exactly and keeps the codes."""
-    h = synth.edge_weights(synth.rmat(10, 8, seed=2), "lognormal", 1.0, seed=3)
-    c, s, _ = oracle.quantize_weights(h)
+    """Scaling every weight by 2^k scales every s_v by 2^k exactly and keeps the codes."""
+    g = synth.rmat(10, 8, seed=2)
+    g.h = synth.edge_weights(g, "lognormal", 1.0, seed=3)
+    c, s, _ = oracle.quantize_weights(g)
     for k in (-3, 5):
-        ck, sk, _ = oracle.quantize_weights(h * np.float32(2.0 ** k))
-        assert sk == s * 2.0 ** k
+        ck, sk, _ = oracle.quantize_weights(synth.Csr(g.offsets, g.cols, g.h * np.float32(2.0 ** k)))
+        np.testing.assert_array_equal(sk, s * np.float32(2.0 ** k))
         np.testing.assert_array_equal(ck, c)
 
 
 def test_quantized_integer_weights_leave_walks_unchanged():
-    """Integer weights with maximum 255 are their own codes, so exact-mode
-    walks over the dequantized weights equal those over the originals."""
+    """Integer weights whose every row has maximum 255 are their own codes, so
+    exact-mode walks over the dequantized weights equal those over the
+    originals."""
     g = synth.rmat(10, 8, seed=4)
     rng = np.random.default_rng(1)
     w = synth.edge_weights(g, "uniform01", seed=5)
     h = np.ceil(w * 255.0).astype(np.float32)
-    h[np.argmax(h)] = 255.0
-    _, s, hq = oracle.quantize_weights(h)
-    assert s == 1.0 and np.array_equal(hq, h)
+    for v in range(g.n):
+        if g.offsets[v + 1] > g.offsets[v]:
+            h[g.offsets[v] + int(np.argmax(h[g.offsets[v]:g.offsets[v + 1]]))] = 255.0
+    gi = synth.Csr(g.offsets, g.cols, h)
+    _, s, hq = oracle.quantize_weights(gi)
+    assert np.all(s[np.diff(g.offsets) > 0] == 1.0) and np.array_equal(hq, h)
     starts = rng.integers(0, g.n, 500).astype(np.int32)
-    a, _ = oracle.walk(synth.Csr(g.offsets, g.cols, h), starts, 12, "node2vec", 2.0, 0.5, seed=8)
+    a, _ = oracle.walk(gi, starts, 12, "node2vec", 2.0, 0.5, seed=8)
     b, _ = oracle.walk(synth.Csr(g.offsets, g.cols, hq), starts, 12, "node2vec", 2.0, 0.5, seed=8)
     assert np.array_equal(a, b)
 

@@ -82,6 +82,10 @@ MUTANTS = {
     "quantize_clamp_zero": ("if (c < 1.0f) c = 1.0f;", "if (c < 0.0f) c = 0.0f;"),
     # 8-bit weights: truncation instead of round-to-nearest
     "quantize_truncate": ("float c = rintf(h[i] / s);", "float c = floorf(h[i] / s);"),
+    # 8-bit codes: the scale off by one code, or taken from every row instead of the node's own
+    "quantize_scale_256": ("const float s = row_max / 255.0f;", "const float s = row_max / 256.0f;"),
+    "quantize_global_max": ("for (int64_t i = offsets[v]; i < offsets[v + 1]; ++i)\n      if (h[i] > row_max)",
+                            "for (int64_t i = 0; i < offsets[n]; ++i)\n      if (h[i] > row_max)"),
     # RJS (Sec. 3.3): the proposal taken from the word that also gives U
     "rjs_index_word": ("lemire_index(x[0], slots, &sl) && !lemire_index(x[1], slots, &sl)) continue;\n    int64_t k",
                        "lemire_index(x[2], slots, &sl) && !lemire_index(x[1], slots, &sl)) continue;\n    int64_t k"),
