@@ -102,12 +102,17 @@ enum {
   FW_FLAG_PAPER_SUM = 16, /* metapath: plan with the Sec. 4.2 rule (B = h_MAX,
                              sum-hat = h_SUM / 2) even when per-label node
                              statistics exist                                    */
-  FW_FLAG_NO_BLOOM = 32,  /* membership tests in N(v') search the sorted row
-                             only, without the per-row Bloom pre-check (the
-                             answers, and so the walks, are the same)            */
-  FW_FLAG_NO_GROUPS = 64  /* metapath: sample over the whole row of v (label
+  FW_FLAG_NO_BLOOM = 32,  /* with FW_FLAG_NO_TABLE (or no tables): membership
+                             tests search the row without the per-row Bloom
+                             pre-check (same answers, same walks)                */
+  FW_FLAG_NO_GROUPS = 64, /* metapath: sample over the whole row of v (label
                              test per entry) instead of inside the required
                              label's segment of the label-grouped view           */
+  FW_FLAG_NO_TABLE = 128  /* membership tests do not read the row's membership
+                             table (an exact hash set of the row's node ids,
+                             one 32-byte bucket per test in most cases) but
+                             the Bloom filter and a search of the sorted row;
+                             same answers, same walks                          */
 };
 
 /* Parameters of one walk job.  Initialise with fw_params_default(). */
@@ -120,13 +125,22 @@ typedef struct {
   float cost_ratio;      /* r = EdgeCost_RJS / EdgeCost_RVS of Eq. (runtime);
                             <= 0 selects the graph's tuned value (default 4)     */
   int32_t rjs_cap;       /* eRJS trials before a step is handed to eRVS;
-                            <= 0: max(64, ceil(m / r)), m the entries that the
-                            eRVS hand-off would scan (d(v); in metapath's
-                            label-grouped view the required label's
-                            entries), r the cost ratio                        */
+                            <= 0: max(64, ceil(b * m / r)), m the entries
+                            that the eRVS hand-off would scan (d(v); in
+                            metapath's label-grouped view the required
+                            label's entries), r the cost ratio, b the trial
+                            budget scale                                      */
   uint32_t walker_base;  /* random-stream id of starts[0]; walker i uses
                             walker_base + i                                      */
   float gamma;           /* second-order PageRank parameter in [0, 1]            */
+  /* Launch shape of the samplers (none changes a distribution; 0 selects
+   * the graph's tuned value, see fw_autotune method 2): */
+  int32_t lane_max_degree; /* eRVS steps over at most this many entries run on
+                              the walker's own lane, longer ones on the whole
+                              warp; 1..64 (default 8)                          */
+  int32_t rjs_batch;       /* eRJS trials a lane runs between two warp ballots
+                              for hand-offs; 1..16 (default 2)                 */
+  float trial_budget;      /* b of the default rjs_cap, > 0 (default 1)        */
 } fw_params;
 
 /* Filled in by fw_graph_info(). */
@@ -143,7 +157,11 @@ typedef struct {
                                 same weight (found at creation)                   */
   float cost_ratios[4];      /* r per algorithm, indexed by fw_algo             */
   uint64_t fingerprint;      /* hash of sizes and sampled CSR entries (cache key)*/
-  float weight_scale;        /* s after fw_graph_quantize_weights, else 0        */
+  float weight_scale;        /* largest per-node scale s_v after
+                                fw_graph_quantize_weights, else 0                */
+  int32_t lane_max_degrees[4]; /* tuned launch shape per algorithm (fw_params)  */
+  int32_t rjs_batches[4];
+  float trial_budgets[4];
 } fw_graph_info_t;
 
 /* Per-walk counters (FW_FLAG_COUNTERS).  Byte figures follow the
@@ -182,9 +200,11 @@ void fw_params_default(fw_params* params);
  * returns.  Besides the CSR it keeps 32-byte edge records (twice with
  * weights and degrees below 2^24: in CSR order and with each row
  * partitioned by weight class),
- * 32-byte node records, per-row Bloom filters and, with labels all below
- * 8, per-label node statistics and a label-grouped copy of the rows (36
- * bytes per entry) for metapath; if that copy does not fit, metapath
+ * 32-byte node records, per-row Bloom filters, per-row membership tables
+ * (an exact hash set of each row's node ids, about 8 bytes per entry; if
+ * they do not fit, membership tests search the rows) and, with labels all
+ * below 8, per-label node statistics and a label-grouped copy of the rows
+ * (36 bytes per entry) for metapath; if that copy does not fit, metapath
  * samples over whole rows.
  * Synchronous on `stream`.  Errors: FW_ERR_ARG, FW_ERR_CSR, FW_ERR_OOM,
  * FW_ERR_CUDA; *out is NULL on error.
@@ -214,21 +234,31 @@ fw_status fw_graph_label_stats(const fw_graph* graph, float* stats, void* stream
 
 /*
  * Store the property weights as 8-bit codes (a low-precision weight format,
- * named in Sec. 6.2 as an extension of the method): with the per-graph
- * scale s = max_e h_e / 255 (FP32 division), each weight becomes
- *   code_e = clamp(rint(h_e / s), 1, 255)       (round half to even)
+ * named in Sec. 6.2 as an extension of the method): every node v gets the
+ * scale of its own row, s_v = h_MAX[v] / 255 (FP32 division), and each
+ * weight of the row becomes
+ *   code_e = clamp(rint(h_e / s_v), 1, 255)     (round half to even)
  * and from then on the graph samples with the dequantized weights
- *   h'_e = code_e * s                            (FP32 product).
- * Codes never round to 0, so every edge keeps a positive weight.  The
- * preprocessing (h_MAX, h_SUM, edge records, label statistics) and the
- * fingerprint are recomputed from h'; scans in eRVS and exact mode then read
- * one byte per weight.  *scale_out (may be NULL) receives s.  A second call
- * is a no-op.  Synchronous on `stream`; no walk may run on the graph
- * meanwhile.  Errors: FW_ERR_ARG, FW_ERR_UNSUPPORTED (graph without
- * weights), FW_ERR_OOM / FW_ERR_CUDA (the graph is unchanged when the codes
- * cannot be allocated).
+ *   h'_e = code_e * s_v                          (FP32 product).
+ * Codes never round to 0, so every edge keeps a positive weight, and each
+ * row's largest weight keeps code 255, so a row's distribution moves by at
+ * most one code step of its own maximum per weight however skewed the
+ * weights of other rows are.  (Mirrored entries may then differ: h'(u,v)
+ * uses s_u.)  The preprocessing (h_MAX, h_SUM, edge records, label
+ * statistics) and the fingerprint are recomputed from h'; scans in eRVS and
+ * exact mode then read one byte per weight and the row's scale.
+ * *scale_out (may be NULL) receives the largest s_v.  A second call is a
+ * no-op.  Synchronous on `stream`; no walk may run on the graph meanwhile.
+ * Errors: FW_ERR_ARG, FW_ERR_UNSUPPORTED (graph without weights),
+ * FW_ERR_OOM / FW_ERR_CUDA (the graph is unchanged when the codes cannot be
+ * allocated).
  */
 fw_status fw_graph_quantize_weights(fw_graph* graph, float* scale_out, void* stream);
+
+/* Copy the per-node scales s_v of the 8-bit codes into `scales` (device
+ * float32[n]).  Asynchronous on `stream`.  FW_ERR_UNSUPPORTED before
+ * fw_graph_quantize_weights. */
+fw_status fw_graph_weight_scales(const fw_graph* graph, float* scales, void* stream);
 
 /* Set the graph's cost ratio r of Eq. (runtime) for every algorithm (must
  * be finite, > 0). */
@@ -247,11 +277,18 @@ fw_status fw_graph_set_cost_ratio(fw_graph* graph, float ratio);
  *             proportion to their degree, as in a mixed walk) for
  *             r in {0.125, 0.25, 0.5, 1, 2, ..., 64}; of the ratios within
  *             3 % of the fastest time, keep the median
+ *   method 2  method 1's sweep of r with 64-hop sample walks, then the launch
+ *             shape one parameter at a time -- lane_max_degree in
+ *             {1, 4, 8, 16, 32, 64}, rjs_batch in {1, 2, 3, 4, 6},
+ *             trial_budget in {0.25, 0.5, 1, 2, 4} -- each candidate kept
+ *             only if its sample walk (best of three) is at least 2 %
+ *             faster than the incumbent, then r swept again under the
+ *             chosen shape; installs all four for `algo`
  * cache_path (may be NULL): a text file of earlier results keyed by the
  * graph fingerprint, algo, p, q, gamma, flags, schema and method; a hit
  * skips the measurement, a miss appends the new result.  Synchronous on
- * `stream`.  The ratio only changes which sampler runs, never the
- * distribution.
+ * `stream`.  The ratio and the launch shape only change which sampler runs
+ * and how the warp's lanes share the steps, never the distribution.
  */
 fw_status fw_autotune(fw_graph* graph, int32_t algo, const fw_params* params, int32_t method,
                       const char* cache_path, float* ratio_out, void* stream);
@@ -346,9 +383,11 @@ fw_status fw_graph_check(fw_graph* graph, void* stream);
  * (4*num_walkers*(len+1) bytes) must fit in 16 MiB - 256 bytes, else
  * FW_ERR_ARG; larger requests belong to fw_walk_host.  Calls share the
  * array and serialise on a process-wide lock (FW_ERR_BUSY if one is in
- * progress); calls that overlap on the GPU race on it.  The first call on a
- * device looks up the array's device address; make it before any stream
- * capture.  The current device must be the graph's device.
+ * progress); calls that overlap on the GPU race on it.  Every call looks up
+ * the array's device address on the current device, so the call stays valid
+ * after a cudaDeviceReset (with the graph created again); the first call on a
+ * device also loads the module holding the array, so make it before any
+ * stream capture.  The current device must be the graph's device.
  */
 fw_status fw_walk_host_noalloc(const fw_graph* graph, const int32_t* starts, int32_t num_walkers, int32_t len,
                                int32_t algo, const fw_params* params, uint64_t seed, int32_t* out, void* stream);
@@ -416,6 +455,7 @@ typedef struct {
   double p50_ms, p99_ms, mean_ms, max_ms;  /* submit -> rows in host memory, completed   */
   size_t peak_device_bytes;             /* arena high-water mark                        */
   int32_t peak_inflight_waves;
+  uint64_t walker_steps;                /* hops of completed queries (counted on device) */
 } fw_server_stats_t;
 
 typedef struct fw_server fw_server;
@@ -435,10 +475,28 @@ fw_status fw_server_create(const fw_graph* graph, const fw_server_config* config
 fw_status fw_server_submit(fw_server* server, const int32_t* starts, int32_t num_walkers, int32_t len, int32_t algo,
                            const fw_params* params, uint64_t seed, int32_t* out, uint64_t* ticket);
 
+/* Queue `count` queries in one call, each an fw_job whose starts and out
+ * are HOST buffers with the meaning of fw_server_submit's (they must stay
+ * valid until the query is collected); tickets[i] receives query i's
+ * ticket.  All queries are checked first and queued under one lock; on the
+ * first invalid one the call stops, returns that query's error (its index
+ * in the message) and *submitted (may be NULL) tells how many queries before
+ * it were queued. */
+fw_status fw_server_submit_many(fw_server* server, const fw_job* queries, int32_t count, uint64_t* tickets,
+                                int32_t* submitted);
+
 /* Non-blocking: *done = 1 once out is filled (the ticket is then released
  * and the query's status returned; latency_ms, if not NULL, receives the
  * submit-to-completion time). */
 fw_status fw_server_poll(fw_server* server, uint64_t ticket, int32_t* done, double* latency_ms);
+
+/* fw_server_poll for `count` tickets under one lock (host arrays of count
+ * entries): done[i] = 1 once query i has finished, its ticket then released,
+ * status[i] (may be NULL) its fw_status and latency_ms[i] (may be NULL) its
+ * submit-to-completion time.  An unknown ticket gives done[i] = 1 and
+ * status[i] = FW_ERR_ARG.  Returns FW_OK unless the arguments are bad. */
+fw_status fw_server_poll_many(fw_server* server, const uint64_t* tickets, int32_t count, int32_t* done,
+                              double* latency_ms, int32_t* status);
 
 /* Wait up to timeout_s seconds: FW_OK (ticket released), FW_ERR_TIMEOUT
  * (ticket kept; wait again later) or the query's error. */

@@ -31,7 +31,7 @@ DevGraph dev_graph(const fw_graph* g) {
   d.col = g->d_col;
   d.h = g->d_h;
   d.h8 = g->d_h8;
-  d.hscale = g->hscale;
+  d.h8scale = g->d_h8scale;
   d.lab = g->d_lab;
   d.hmax = g->d_hmax;
   d.hsum = g->d_hsum;
@@ -40,6 +40,7 @@ DevGraph dev_graph(const fw_graph* g) {
   d.cerec = g->d_cerec;
   d.lstat = g->d_lstat;
   d.bloom = g->d_bloom;
+  d.mtab = g->d_mtab;
   d.lrec = g->d_lrec;
   d.gerec = g->d_gerec;
   d.gh = g->d_gh;
@@ -66,6 +67,10 @@ fw_status make_job(const fw_graph* g, int32_t algo, const fw_params* params, uin
     if (P.schema_len < 1 || P.schema_len > 16) return set_error(FW_ERR_ARG, "metapath schema_len must be 1..16");
   }
   if (P.cost_ratio > 0.0f && !std::isfinite(P.cost_ratio)) return set_error(FW_ERR_ARG, "cost_ratio not finite");
+  if (P.lane_max_degree < 0 || P.lane_max_degree > 64) return set_error(FW_ERR_ARG, "lane_max_degree must be 0..64");
+  if (P.rjs_batch < 0 || P.rjs_batch > 16) return set_error(FW_ERR_ARG, "rjs_batch must be 0..16");
+  if (!(P.trial_budget >= 0.0f) || !std::isfinite(P.trial_budget))
+    return set_error(FW_ERR_ARG, "trial_budget must be finite and >= 0");
   std::memset(job, 0, sizeof(Job));
   job->algo = algo;
   job->mode = P.mode;
@@ -93,12 +98,16 @@ fw_status make_job(const fw_graph* g, int32_t algo, const fw_params* params, uin
     job->wmean1 = algo == ALGO_METAPATH ? 0.5f : 1.0f;
   }
   job->ratio = P.cost_ratio > 0.0f ? P.cost_ratio : g->ratio_algo[algo];
+  job->lane_max = P.lane_max_degree > 0 ? P.lane_max_degree : g->lane_max_algo[algo];
+  job->rjs_batch = P.rjs_batch > 0 ? P.rjs_batch : g->rjs_batch_algo[algo];
+  job->budget = P.trial_budget > 0.0f ? P.trial_budget : g->budget_algo[algo];
   job->key0 = (uint32_t)seed;
   job->key1 = (uint32_t)(seed >> 32);
   job->walker_base = P.walker_base;
   job->pr_g = P.gamma;
   job->pr_1g = 1.0f - P.gamma;
   job->bloom = (g->d_bloom && !(P.flags & FW_FLAG_NO_BLOOM)) ? 1 : 0;
+  job->table = (g->d_mtab && !(P.flags & FW_FLAG_NO_TABLE)) ? 1 : 0;
   job->label_stats = (algo == ALGO_METAPATH && g->d_lstat && !(P.flags & FW_FLAG_PAPER_SUM) &&
                       (job->weighted || !g->d_h)) ? 1 : 0;
   job->label_group = (job->label_stats && g->d_lrec && !(P.flags & FW_FLAG_NO_GROUPS)) ? 1 : 0;
@@ -114,7 +123,7 @@ fw_status make_job(const fw_graph* g, int32_t algo, const fw_params* params, uin
 // device has no room for it, metapath walks keep the full-row path.
 static fw_status build_label_groups(fw_graph* g, cudaStream_t st) {
   const size_t lrec_bytes = 2 * sizeof(int4) * kLabelStats * ((size_t)g->n + 1);
-  const size_t gerec_bytes = 2 * sizeof(int4) * (size_t)g->e, gh_bytes = sizeof(float) * (size_t)g->e;
+  const size_t gerec_bytes = 2 * sizeof(int4) * (size_t)g->e, gh_bytes = sizeof(float) * ((size_t)g->e + kScanPad);
   if (!g->d_lrec) {
     cudaError_t a = cudaMalloc(&g->d_lrec, lrec_bytes);
     if (a == cudaSuccess) a = cudaMalloc(&g->d_gerec, gerec_bytes);
@@ -130,6 +139,8 @@ static fw_status build_label_groups(fw_graph* g, cudaStream_t st) {
       return FW_OK;
     }
     g->bytes += lrec_bytes + gerec_bytes + gh_bytes;
+    cudaError_t z = cudaMemsetAsync(g->d_gh + g->e, 0, sizeof(float) * kScanPad, st);
+    if (z != cudaSuccess) return cuda_error(z, "cudaMemsetAsync(grouped weights)");
   }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -164,6 +175,14 @@ fw_status rebuild_derived(fw_graph* g, cudaStream_t st) {
       return cuda_error(ae, "cudaMalloc(row filters)");
     }
     g->bytes += bloom_bytes(n, e);
+    // membership tables: without room for them, membership tests search the rows
+    ae = cudaMalloc(&g->d_mtab, table_bytes(n, e));
+    if (ae != cudaSuccess) {
+      g->d_mtab = nullptr;
+      cudaGetLastError();  // an allocation failure is not sticky
+    } else {
+      g->bytes += table_bytes(n, e);
+    }
   }
   if (want_labels && !g->d_lstat) {
     cudaError_t ae = cudaMalloc(&g->d_lstat, sizeof(float2) * kLabelStats * ((size_t)n + 1));
@@ -189,7 +208,8 @@ fw_status rebuild_derived(fw_graph* g, cudaStream_t st) {
   if (le == cudaSuccess && g->d_cerec)
     le = launch_class_group(g->d_off, g->d_h, g->d_nrec, g->d_erec, n, g->d_cerec, g->num_sms, st);
   if (le == cudaSuccess) le = launch_symmetry(g->d_off, g->d_col, g->d_h, n, e, d_asym, g->num_sms, st);
-  if (le == cudaSuccess && build_bloom) le = launch_bloom(g->d_off, g->d_col, n, e, g->d_bloom, g->num_sms, st);
+  if (le == cudaSuccess && build_bloom)
+    le = launch_bloom(g->d_off, g->d_col, n, e, g->d_bloom, g->d_mtab, g->num_sms, st);
   if (le == cudaSuccess && want_labels)
     le = launch_label_stats(g->d_off, g->d_h, g->d_lab, n, g->d_lstat, d_lbad, g->num_sms, st);
   cudaEventRecord(e1, st);
@@ -306,7 +326,9 @@ static void free_graph(fw_graph* g) {
   cudaFree(g->d_cerec);
   cudaFree(g->d_lstat);
   cudaFree(g->d_h8);
+  cudaFree(g->d_h8scale);
   cudaFree(g->d_bloom);
+  cudaFree(g->d_mtab);
   cudaFree(g->d_lrec);
   cudaFree(g->d_gerec);
   cudaFree(g->d_gh);
@@ -352,10 +374,12 @@ extern "C" fw_status fw_graph_create(const int32_t* offsets, const int32_t* cols
   FW_TRY(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device), "cudaDeviceGetAttribute");
   const cudaMemcpyKind kind = ptr_kind == FW_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   const size_t eb = (size_t)(e > 0 ? e : 1);
+  // the arrays the warp scans read in 4-entry chunks carry kScanPad zeroed entries past the end
+  const size_t ep = (size_t)e + kScanPad;
   FW_TRY(cudaMalloc(&g->d_off, sizeof(int32_t) * ((size_t)n + 1)), "cudaMalloc(offsets)");
-  FW_TRY(cudaMalloc(&g->d_col, sizeof(int32_t) * eb), "cudaMalloc(cols)");
-  if (weights) FW_TRY(cudaMalloc(&g->d_h, sizeof(float) * eb), "cudaMalloc(weights)");
-  if (labels) FW_TRY(cudaMalloc(&g->d_lab, eb), "cudaMalloc(labels)");
+  FW_TRY(cudaMalloc(&g->d_col, sizeof(int32_t) * ep), "cudaMalloc(cols)");
+  if (weights) FW_TRY(cudaMalloc(&g->d_h, sizeof(float) * ep), "cudaMalloc(weights)");
+  if (labels) FW_TRY(cudaMalloc(&g->d_lab, ep), "cudaMalloc(labels)");
   FW_TRY(cudaMalloc(&g->d_hmax, sizeof(float) * ((size_t)n + 1)), "cudaMalloc(h_MAX)");
   FW_TRY(cudaMalloc(&g->d_hsum, sizeof(float) * ((size_t)n + 1)), "cudaMalloc(h_SUM)");
   FW_TRY(cudaMalloc(&g->d_nrec, 2 * sizeof(int4) * ((size_t)n + 1)), "cudaMalloc(node records)");
@@ -366,6 +390,9 @@ extern "C" fw_status fw_graph_create(const int32_t* offsets, const int32_t* cols
   g->bytes = sizeof(int32_t) * ((size_t)n + 1) + eb * (4 + (weights ? 4 : 0) + (labels ? 1 : 0)) +
              2 * sizeof(float) * ((size_t)n + 1) + 2 * sizeof(int4) * ((size_t)n + 1) +
              (weights ? 4 : 2) * sizeof(int4) * eb + 64 + sizeof(DevCounters);
+  FW_TRY(cudaMemsetAsync(g->d_col + e, 0, sizeof(int32_t) * kScanPad, st), "cudaMemsetAsync");
+  if (weights) FW_TRY(cudaMemsetAsync(g->d_h + e, 0, sizeof(float) * kScanPad, st), "cudaMemsetAsync");
+  if (labels) FW_TRY(cudaMemsetAsync(g->d_lab + e, 0, kScanPad, st), "cudaMemsetAsync");
   FW_TRY(cudaMemsetAsync(g->d_err, 0, 64, st), "cudaMemsetAsync");
   FW_TRY(cudaMemsetAsync(g->d_cnt, 0, sizeof(DevCounters), st), "cudaMemsetAsync");
   FW_TRY(cudaMemcpyAsync(g->d_off, offsets, sizeof(int32_t) * ((size_t)n + 1), kind, st), "copy offsets");
@@ -428,6 +455,11 @@ extern "C" fw_status fw_graph_info(const fw_graph* g, fw_graph_info_t* info) {
   info->device_bytes = g->bytes;
   info->symmetric = g->sym;
   info->weight_scale = g->d_h8 ? g->hscale : 0.0f;
+  for (int a = 0; a < 4; ++a) {
+    info->lane_max_degrees[a] = g->lane_max_algo[a];
+    info->rjs_batches[a] = g->rjs_batch_algo[a];
+    info->trial_budgets[a] = g->budget_algo[a];
+  }
   return FW_OK;
 }
 
@@ -458,26 +490,40 @@ extern "C" fw_status fw_graph_quantize_weights(fw_graph* g, float* scale_out, vo
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   uint8_t* codes = nullptr;
-  cudaError_t e = cudaMalloc(&codes, (size_t)(g->e > 0 ? g->e : 1));
-  if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(weight codes)");
-  float scale = 0.0f;
-  if (g->e > 0) {
-    e = launch_quantize(g->d_h, g->e, codes, &scale, g->d_err + 14, g->num_sms, st);
-    // the FP32 copy now holds the dequantized weights every derived structure is rebuilt from
-    if (e == cudaSuccess) e = launch_dequantize(codes, g->e, scale, g->d_h, g->num_sms, st);
-  }
+  float* scales = nullptr;
+  cudaError_t e = cudaMalloc(&codes, (size_t)g->e + kScanPad);
+  if (e == cudaSuccess) e = cudaMalloc(&scales, sizeof(float) * ((size_t)g->n + 1));
+  if (e == cudaSuccess) e = cudaMemsetAsync(codes + g->e, 0, kScanPad, st);
   if (e != cudaSuccess) {
     cudaFree(codes);
+    cudaFree(scales);
+    return cuda_error(e, "cudaMalloc(weight codes)");
+  }
+  // the FP32 copy then holds the dequantized weights every derived structure is rebuilt from
+  float max_scale = 0.0f;
+  e = launch_quantize(g->d_off, g->d_h, g->d_hmax, g->n, codes, scales, &max_scale, g->d_err + 14, g->num_sms, st);
+  if (e != cudaSuccess) {
+    cudaFree(codes);
+    cudaFree(scales);
     return cuda_error(e, "weight quantization");
   }
   g->d_h8 = codes;
-  g->hscale = scale;
-  g->bytes += (size_t)g->e;
+  g->d_h8scale = scales;
+  g->hscale = max_scale;
+  g->bytes += (size_t)g->e + sizeof(float) * (size_t)g->n;
   fw_status s = rebuild_derived(g, st);
   if (s == FW_OK) s = graph_fingerprint(g, st, &g->fingerprint);
   if (s != FW_OK) return s;
-  if (scale_out) *scale_out = scale;
+  if (scale_out) *scale_out = max_scale;
   return FW_OK;
+}
+
+extern "C" fw_status fw_graph_weight_scales(const fw_graph* g, float* scales, void* stream) {
+  if (!g || !scales) return set_error(FW_ERR_ARG, "NULL argument");
+  if (!g->d_h8scale) return set_error(FW_ERR_UNSUPPORTED, "the graph's weights are not quantized");
+  cudaError_t e = cudaMemcpyAsync(scales, g->d_h8scale, sizeof(float) * (size_t)g->n, cudaMemcpyDeviceToDevice,
+                                  reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? FW_OK : cuda_error(e, "copy weight scales");
 }
 
 extern "C" fw_status fw_graph_set_cost_ratio(fw_graph* g, float ratio) {

@@ -50,6 +50,7 @@ __device__ __forceinline__ bool profile_ctx(const DevGraph& g, const Job& J, int
     c.ps = c.pe = 0;
   }
   c.wid = (uint32_t)i;
+  c.hsc = g.h8 ? __ldg(g.h8scale + v) : 0.0f;
   c.n0 = -1;  // one weight class: the paper's eRJS
   c.n1 = 0;
   return true;
@@ -124,21 +125,33 @@ struct CacheKey {
   int method;
 };
 
-bool cache_lookup(const char* path, const CacheKey& k, float* r) {
+// A tuned result: r, and (method 2) the launch shape; 0 = not tuned.
+struct Tuned {
+  float r = 0.0f;
+  int lane_max = 0, rjs_batch = 0;
+  float budget = 0.0f;
+};
+
+bool cache_lookup(const char* path, const CacheKey& k, Tuned* t) {
   FILE* f = std::fopen(path, "r");
   if (!f) return false;
-  char line[256];
+  char line[320];
   bool hit = false;
   while (std::fgets(line, sizeof(line), f)) {
     unsigned long long fp;
-    int algo, method, flags;
+    int algo, method, flags, lane = 0, batch = 0;
     unsigned schema;
-    float p, q, gamma, rv;
-    if (std::sscanf(line, "fp=%llx algo=%d p=%g q=%g gamma=%g flags=%d schema=%x method=%d r=%g", &fp, &algo, &p,
-                    &q, &gamma, &flags, &schema, &method, &rv) == 9 &&
-        fp == k.fp && algo == k.algo && p == k.p && q == k.q && gamma == k.gamma && flags == k.flags &&
-        schema == k.schema && method == k.method && rv > 0.0f) {
-      *r = rv;
+    float p, q, gamma, rv, budget = 0.0f;
+    const int got = std::sscanf(line, "fp=%llx algo=%d p=%g q=%g gamma=%g flags=%d schema=%x method=%d r=%g "
+                                      "lane=%d batch=%d budget=%g",
+                                &fp, &algo, &p, &q, &gamma, &flags, &schema, &method, &rv, &lane, &batch, &budget);
+    if ((got == 9 || got == 12) && fp == k.fp && algo == k.algo && p == k.p && q == k.q && gamma == k.gamma &&
+        flags == k.flags && schema == k.schema && method == k.method && rv > 0.0f &&
+        (method != 2 || (got == 12 && lane >= 1 && lane <= 64 && batch >= 1 && batch <= 16 && budget > 0.0f))) {
+      t->r = rv;
+      t->lane_max = got == 12 ? lane : 0;
+      t->rjs_batch = got == 12 ? batch : 0;
+      t->budget = got == 12 ? budget : 0.0f;
       hit = true;  // the last matching line wins
     }
   }
@@ -146,11 +159,13 @@ bool cache_lookup(const char* path, const CacheKey& k, float* r) {
   return hit;
 }
 
-void cache_store(const char* path, const CacheKey& k, float r) {
+void cache_store(const char* path, const CacheKey& k, const Tuned& t) {
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "fp=%016llx algo=%d p=%.9g q=%.9g gamma=%.9g flags=%d schema=%08x method=%d r=%.9g\n", k.fp,
-               k.algo, k.p, k.q, k.gamma, k.flags, k.schema, k.method, r);
+  std::fprintf(f, "fp=%016llx algo=%d p=%.9g q=%.9g gamma=%.9g flags=%d schema=%08x method=%d r=%.9g", k.fp, k.algo,
+               k.p, k.q, k.gamma, k.flags, k.schema, k.method, t.r);
+  if (k.method == 2) std::fprintf(f, " lane=%d batch=%d budget=%.9g", t.lane_max, t.rjs_batch, t.budget);
+  std::fprintf(f, "\n");
   std::fclose(f);
 }
 
@@ -243,71 +258,155 @@ static fw_status profile_ratio(fw_graph* g, const Job& J, cudaStream_t st, float
   return FW_OK;
 }
 
-static fw_status sweep_ratio(fw_graph* g, int32_t algo, const fw_params* params, cudaStream_t st, float* r_out) {
-  // sample walk per candidate r: up to 2^20 walkers from degree-biased starts, 32 hops
-  if (g->e == 0) {
-    *r_out = 4.0f;
-    return FW_OK;
+// Sample walks for the sweeps: up to 2^20 walkers from degree-biased starts.
+struct Sample {
+  int32_t* starts = nullptr;
+  int32_t* out = nullptr;
+  int32_t w = 0, len = 0;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ~Sample() {
+    cudaFree(starts);
+    cudaFree(out);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
   }
-  const int32_t w = (int32_t)(g->e < (1ll << 20) ? g->e : (1ll << 20));
-  const int32_t len = 32;
-  int32_t *d_starts = nullptr, *d_out = nullptr;
-  cudaError_t e = cudaMalloc(&d_starts, sizeof(int32_t) * (size_t)w);
-  if (e == cudaSuccess) e = cudaMalloc(&d_out, sizeof(int32_t) * (size_t)w * (len + 1));
+};
+
+static fw_status make_sample(const fw_graph* g, int32_t len, cudaStream_t st, Sample* sm) {
+  sm->w = (int32_t)(g->e < (1ll << 20) ? g->e : (1ll << 20));
+  sm->len = len;
+  cudaError_t e = cudaMalloc(&sm->starts, sizeof(int32_t) * (size_t)sm->w);
+  if (e == cudaSuccess) e = cudaMalloc(&sm->out, sizeof(int32_t) * (size_t)sm->w * (len + 1));
+  if (e == cudaSuccess) e = cudaEventCreate(&sm->a);
+  if (e == cudaSuccess) e = cudaEventCreate(&sm->b);
   if (e == cudaSuccess) {
-    sweep_starts_kernel<<<(w + 255) / 256, 256, 0, st>>>(g->d_col, (long long)g->e, w, d_starts);
+    sweep_starts_kernel<<<(sm->w + 255) / 256, 256, 0, st>>>(g->d_col, (long long)g->e, sm->w, sm->starts);
     g_launches.fetch_add(1);
     e = cudaGetLastError();
   }
-  if (e != cudaSuccess) {
-    cudaFree(d_starts);
-    cudaFree(d_out);
-    return cuda_error(e, "sweep buffers");
+  return e == cudaSuccess ? FW_OK : cuda_error(e, "sweep buffers");
+}
+
+// Best of `reps` timings of the sample walk under P.
+static fw_status time_sample(const fw_graph* g, int32_t algo, const fw_params& P, Sample& sm, cudaStream_t st,
+                             int reps, float* ms_out) {
+  float t = 1e30f;
+  fw_status s = FW_OK;
+  for (int rep = 0; rep < reps && s == FW_OK; ++rep) {
+    cudaEventRecord(sm.a, st);
+    s = fw_walk(g, sm.starts, sm.w, sm.len, algo, &P, 7, sm.out, st);
+    cudaEventRecord(sm.b, st);
+    cudaEventSynchronize(sm.b);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, sm.a, sm.b);
+    t = std::fmin(t, ms);
   }
+  *ms_out = t;
+  return s;
+}
+
+// r over the ladder {1/8, ..., 64} under P's launch shape.  Where the timing
+// is flat, sample noise alone would decide; take the median (the ladder is
+// geometric: the middle in log r) of the ratios within 3 % of the fastest
+// instead, the smaller one of an even count.
+static fw_status sweep_r(const fw_graph* g, int32_t algo, fw_params P, Sample& sm, cudaStream_t st, int reps,
+                         float* r_out, float* best_ms) {
   const float ladder[] = {0.125f, 0.25f, 0.5f, 1.0f, 2.0f, 4.0f, 8.0f, 16.0f, 32.0f, 64.0f};
-  fw_params P;
-  if (params) P = *params;
-  else fw_params_default(&P);
-  P.mode = FW_MODE_AUTO;
-  P.flags &= ~FW_FLAG_COUNTERS;
-  cudaEvent_t a, b;
-  cudaEventCreate(&a);
-  cudaEventCreate(&b);
   constexpr int kLadder = (int)(sizeof(ladder) / sizeof(ladder[0]));
   float times[kLadder];
-  for (int li = 0; li < kLadder; ++li) times[li] = 1e30f;
   fw_status s = FW_OK;
-  P.cost_ratio = 4.0f;
-  s = fw_walk(g, d_starts, w, len, algo, &P, 7, d_out, st);  // warm-up
   for (int li = 0; li < kLadder && s == FW_OK; ++li) {
     P.cost_ratio = ladder[li];
-    float t = 1e30f;
-    for (int rep = 0; rep < 2 && s == FW_OK; ++rep) {
-      cudaEventRecord(a, st);
-      s = fw_walk(g, d_starts, w, len, algo, &P, 7, d_out, st);
-      cudaEventRecord(b, st);
-      cudaEventSynchronize(b);
-      float ms = 0.0f;
-      cudaEventElapsedTime(&ms, a, b);
-      t = std::fmin(t, ms);
-    }
-    times[li] = t;
+    s = time_sample(g, algo, P, sm, st, reps, &times[li]);
   }
-  // Where the timing is flat, sample noise alone would decide; take the
-  // median (the ladder is geometric: the middle in log r) of the ratios
-  // within 3 % of the fastest instead, the smaller one of an even count.
+  if (s != FW_OK) return s;
   float best = 1e30f;
   for (int li = 0; li < kLadder; ++li) best = std::fmin(best, times[li]);
   int near[kLadder], count = 0;
   for (int li = 0; li < kLadder; ++li)
     if (times[li] <= 1.03f * best) near[count++] = li;
-  const float best_r = count == 0 ? 4.0f : ladder[near[(count - 1) / 2]];
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
-  cudaFree(d_starts);
-  cudaFree(d_out);
+  *r_out = count == 0 ? 4.0f : ladder[near[(count - 1) / 2]];
+  *best_ms = best;
+  return FW_OK;
+}
+
+static fw_params sweep_params(const fw_params* params) {
+  fw_params P;
+  if (params) P = *params;
+  else fw_params_default(&P);
+  P.mode = FW_MODE_AUTO;
+  P.flags &= ~FW_FLAG_COUNTERS;
+  return P;
+}
+
+// Method 1: r from 32-hop sample walks (best of two per candidate).
+static fw_status sweep_ratio(fw_graph* g, int32_t algo, const fw_params* params, cudaStream_t st, Tuned* out) {
+  if (g->e == 0) {
+    out->r = 4.0f;
+    return FW_OK;
+  }
+  Sample sm;
+  fw_status s = make_sample(g, 32, st, &sm);
   if (s != FW_OK) return s;
-  *r_out = best_r;
+  fw_params P = sweep_params(params);
+  P.cost_ratio = 4.0f;
+  s = fw_walk(g, sm.starts, sm.w, sm.len, algo, &P, 7, sm.out, st);  // warm-up
+  float best = 0.0f;
+  if (s == FW_OK) s = sweep_r(g, algo, P, sm, st, 2, &out->r, &best);
+  return s;
+}
+
+// Method 2: r, then the launch shape one parameter at a time, then r again;
+// 64-hop sample walks, best of three per candidate, and a candidate replaces
+// the incumbent only when at least 2 % faster, so timing noise between
+// near-equal settings does not move the result.
+static fw_status sweep_shape(fw_graph* g, int32_t algo, const fw_params* params, cudaStream_t st, Tuned* out) {
+  if (g->e == 0) {
+    out->r = 4.0f;
+    out->lane_max = kLaneMaxDegree;
+    out->rjs_batch = kRjsBatchDefault;
+    out->budget = 1.0f;
+    return FW_OK;
+  }
+  Sample sm;
+  fw_status s = make_sample(g, 64, st, &sm);
+  if (s != FW_OK) return s;
+  fw_params P = sweep_params(params);
+  P.lane_max_degree = kLaneMaxDegree;
+  P.rjs_batch = kRjsBatchDefault;
+  P.trial_budget = 1.0f;
+  P.cost_ratio = 4.0f;
+  s = fw_walk(g, sm.starts, sm.w, sm.len, algo, &P, 7, sm.out, st);  // warm-up
+  float cur = 0.0f;
+  if (s == FW_OK) s = sweep_r(g, algo, P, sm, st, 3, &P.cost_ratio, &cur);
+  if (s == FW_OK) s = time_sample(g, algo, P, sm, st, 3, &cur);
+  auto try_values = [&](auto member, const auto* values, int nv) {
+    for (int i = 0; i < nv && s == FW_OK; ++i) {
+      fw_params Q = P;
+      Q.*member = values[i];
+      if (Q.*member == P.*member) continue;
+      float t = 0.0f;
+      s = time_sample(g, algo, Q, sm, st, 3, &t);
+      if (s == FW_OK && t < 0.98f * cur) {
+        P = Q;
+        cur = t;
+      }
+    }
+  };
+  const int32_t lanes[] = {1, 4, 8, 16, 32, 64};
+  const int32_t batches[] = {1, 2, 3, 4, 6};
+  const float budgets[] = {0.25f, 0.5f, 1.0f, 2.0f, 4.0f};
+  try_values(&fw_params::lane_max_degree, lanes, 6);
+  try_values(&fw_params::rjs_batch, batches, 5);
+  try_values(&fw_params::trial_budget, budgets, 5);
+  float r2 = P.cost_ratio, t2 = 0.0f;
+  if (s == FW_OK) s = sweep_r(g, algo, P, sm, st, 3, &r2, &t2);
+  if (s == FW_OK && t2 < 0.98f * cur) P.cost_ratio = r2;
+  if (s != FW_OK) return s;
+  out->r = P.cost_ratio;
+  out->lane_max = P.lane_max_degree;
+  out->rjs_batch = P.rjs_batch;
+  out->budget = P.trial_budget;
   return FW_OK;
 }
 
@@ -318,7 +417,8 @@ using namespace fw;
 extern "C" fw_status fw_autotune(fw_graph* g, int32_t algo, const fw_params* params, int32_t method,
                                  const char* cache_path, float* ratio_out, void* stream) {
   if (!g) return set_error(FW_ERR_ARG, "graph is NULL");
-  if (method != 0 && method != 1) return set_error(FW_ERR_ARG, "method must be 0 (profiling kernels) or 1 (sweep)");
+  if (method < 0 || method > 2)
+    return set_error(FW_ERR_ARG, "method must be 0 (profiling kernels), 1 (sweep of r) or 2 (r and launch shape)");
   Job J;
   fw_status s = make_job(g, algo, params, 0x5eedull, &J);
   if (s != FW_OK) return s;
@@ -333,15 +433,22 @@ extern "C" fw_status fw_autotune(fw_graph* g, int32_t algo, const fw_params* par
   for (int i = 0; i < J.schema_len; ++i) key.schema = (key.schema ^ J.schema[i]) * 16777619u;
   key.method = method;
   key.fp = g->fingerprint;
-  float r = 0.0f;
-  bool cached = cache_path && cache_path[0] && cache_lookup(cache_path, key, &r);
+  Tuned t;
+  bool cached = cache_path && cache_path[0] && cache_lookup(cache_path, key, &t);
   if (!cached) {
-    s = method == 0 ? profile_ratio(g, J, st, &r) : sweep_ratio(g, algo, params, st, &r);
+    if (method == 0) s = profile_ratio(g, J, st, &t.r);
+    else if (method == 1) s = sweep_ratio(g, algo, params, st, &t);
+    else s = sweep_shape(g, algo, params, st, &t);
     if (s != FW_OK) return s;
-    if (!(r > 0.0f) || !std::isfinite(r)) return set_error(FW_ERR_CUDA, "profiling gave no usable ratio");
-    if (cache_path && cache_path[0]) cache_store(cache_path, key, r);
+    if (!(t.r > 0.0f) || !std::isfinite(t.r)) return set_error(FW_ERR_CUDA, "profiling gave no usable ratio");
+    if (cache_path && cache_path[0]) cache_store(cache_path, key, t);
   }
-  g->ratio_algo[algo] = r;
-  if (ratio_out) *ratio_out = r;
+  g->ratio_algo[algo] = t.r;
+  if (method == 2) {
+    g->lane_max_algo[algo] = t.lane_max;
+    g->rjs_batch_algo[algo] = t.rjs_batch;
+    g->budget_algo[algo] = t.budget;
+  }
+  if (ratio_out) *ratio_out = t.r;
   return FW_OK;
 }

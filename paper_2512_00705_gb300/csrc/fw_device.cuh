@@ -31,7 +31,8 @@ namespace fw {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxJobs = 64;
-constexpr int kThreadRvsMaxDeg = 8;  // eRVS steps with d <= this run on one lane
+constexpr int kLaneMaxDegree = 8;    // default: eRVS steps with d <= this run on one lane
+constexpr int kRjsBatchDefault = 2;  // default: eRJS trials per round before the warp ballot
 constexpr int kLabelStats = 8;       // per-label node statistics for labels 0..7
 constexpr int kWClasses = 5;         // weight classes inside a metapath label segment
 
@@ -47,8 +48,8 @@ struct DevGraph {
   const int32_t* __restrict__ off;
   const int32_t* __restrict__ col;
   const float* __restrict__ h;     // nullptr: h = 1
-  const uint8_t* __restrict__ h8;  // 8-bit weight codes (nullptr: FP32 weights); h = code * hscale
-  float hscale;
+  const uint8_t* __restrict__ h8;  // 8-bit weight codes (nullptr: FP32 weights); h(v,u) = code * h8scale[v]
+  const float* __restrict__ h8scale; // per node: the scale of the codes of its row
   const uint8_t* __restrict__ lab; // nullptr: no labels
   const float* __restrict__ hmax;
   const float* __restrict__ hsum;
@@ -63,6 +64,7 @@ struct DevGraph {
   const float2* __restrict__ lstat; // per node and label l < kLabelStats: {max h, sum h} over the
                                    // edges with that label (nullptr: labels absent or >= kLabelStats)
   const uint32_t* __restrict__ bloom; // blocked Bloom filters of the rows (nullptr: none)
+  const int32_t* __restrict__ mtab;   // per-row membership tables of the node ids (nullptr: none)
   // label-grouped view of the rows (metapath; nullptr: not built): each row
   // reordered stably by (label, weight class).  lrec per node and label
   // l < kLabelStats, 32 bytes: {max h bits, sum h bits, segment start
@@ -92,13 +94,17 @@ struct Job {
   int32_t weighted;        // 1: use h, 0: h = 1
   int32_t second_order;    // node2vec with (1/p, 1/q) != (1, 1): w depends on v'
   int32_t need_member;     // node2vec with 1/q != 1: membership test needed
-  int32_t fixed_cap;       // 1: rjs_cap is a fixed trial cap; 0: cap = max(rjs_cap, ceil(d / ratio))
+  int32_t fixed_cap;       // 1: rjs_cap is a fixed trial cap; 0: cap = max(rjs_cap, ceil(budget * d / ratio))
+  int32_t lane_max;        // eRVS steps over at most this many entries run on the walker's lane
+  int32_t rjs_batch;       // eRJS trials per round before the warp's hand-off ballot
+  float budget;            // trial budget scale of the default cap
   int32_t split_return;    // node2vec with 1/p > max(1, 1/q): eRJS proposes the return edge separately
   int32_t split_common;    // node2vec with 1/q < 1: eRJS may use the two-envelope proposal (d(v') < d(v))
   int32_t label_stats;     // metapath: plan with the per-label h_MAX / h_SUM of the required label
   int32_t label_group;     // metapath: fast modes sample inside the required label's segment
   int32_t classes;         // eRJS proposes from three weight classes (bounds B, B / 2, B / 4)
   int32_t bloom;           // 1: membership tests in N(v') consult the row's Bloom filter first
+  int32_t table;           // 1: membership tests read the row's membership table instead of searching
   float inv_p, inv_q;      // FP32 1/p, 1/q
   float wmax1, wmean1;     // max / mean of w when a previous node exists
   float wlo1, whi1;        // min / max of {1, 1/q}: squeeze bounds of a non-return neighbour
@@ -181,6 +187,7 @@ struct StepCtx {
   float w1, w2;     // second-order PageRank weights of this step: u in N(v') / otherwise
   int32_t n0, n1;   // eRJS weight classes: entries of v in classes 0 and 1 (n0 < 0: one class)
   int4 gcls;        // grouped metapath: entries of weight classes 0..3 in the label segment [ps, pe)
+  float hsc;        // 8-bit weight codes: the scale of v's row (unused with FP32 weights)
 };
 
 // Slots of a label segment's weight-class envelope: class c < kWClasses
@@ -278,37 +285,135 @@ __device__ __forceinline__ long long bloom_word(int32_t x, int32_t rs, int32_t r
   return 8ll * (b0 + (long long)__umulhi((uint32_t)(hk >> 32), nb));
 }
 
-// Position of u in the row [rs, re) of node x, or -1: the filter first (rows
-// of at least kBloomMinDeg entries; a filter test counts as one probe), then
-// the search.  Exact.
+// Membership tables: an exact set of each row's node ids for rows of at least
+// kBloomMinDeg entries.  Node x owns the 32-byte buckets [tb(x), tb(x+1)),
+// tb(x) = floor(off[x]/4) + x -- more than d/4 buckets of 8 slots, so at most
+// half the slots hold an id and the rest are -1.  Id u lives in the first
+// free slot at or after its home bucket umulhi(hash(u), buckets) (linear
+// probing by bucket, wrapping within the row; hash = the high word of the
+// Bloom mix).  Slots fill in order and are never cleared, so every bucket
+// from u's home to the one holding u is full: a lookup reads one bucket,
+// answers "present" on a match and "absent" on a free slot, and moves on
+// only from a full bucket without u (about 5 % of lookups at load 1/2).
+__device__ __forceinline__ long long table_bucket0(int32_t x, int32_t rs) { return (long long)(rs >> 2) + x; }
+__device__ __forceinline__ uint32_t table_buckets(int32_t rs, int32_t re) {
+  return (uint32_t)((re >> 2) - (rs >> 2) + 1);
+}
+
+// One 32-byte bucket in a single load that does not allocate in L1 (as
+// ld_record; a bucket read as two 16-byte loads costs two random accesses).
+// Written as four 64-bit words: the eight-word form of ld_record in this
+// function crashes the assembler of CUDA 13.0.
+__device__ __forceinline__ void ld_bucket(const int32_t* p, int4& a, int4& c) {
+  unsigned long long q0, q1, q2, q3;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.b64 {%0, %1, %2, %3}, [%4];"
+               : "=l"(q0), "=l"(q1), "=l"(q2), "=l"(q3)
+               : "l"(p));
+  a = make_int4((int)q0, (int)(q0 >> 32), (int)q1, (int)(q1 >> 32));
+  c = make_int4((int)q2, (int)(q2 >> 32), (int)q3, (int)(q3 >> 32));
+}
+
+// Buckets after a full home bucket (rare): one 32-byte load each.
+static __device__ __noinline__ bool table_contains_more(const int32_t* __restrict__ tab, long long b0, uint32_t nb,
+                                                        uint32_t b, int32_t u, uint32_t& probes) {
+  for (uint32_t k = 1; k < nb; ++k) {
+    b = (b + 1 == nb) ? 0u : b + 1;
+    int4 a, c;
+    ld_bucket(tab + 8ll * (b0 + b), a, c);
+    ++probes;
+    if (a.x == u || a.y == u || a.z == u || a.w == u || c.x == u || c.y == u || c.z == u || c.w == u) return true;
+    if (c.w == -1) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ bool table_contains(const int32_t* __restrict__ tab, int32_t x, int32_t rs, int32_t re,
+                                               uint32_t hhi, int32_t u, uint32_t& probes) {
+  const long long b0 = table_bucket0(x, rs);
+  const uint32_t nb = table_buckets(rs, re);
+  const uint32_t b = __umulhi(hhi, nb);
+  int4 a, c;  // the home bucket
+  ld_bucket(tab + 8ll * (b0 + b), a, c);
+  ++probes;
+  if (a.x == u || a.y == u || a.z == u || a.w == u || c.x == u || c.y == u || c.z == u || c.w == u) return true;
+  if (c.w == -1) return false;  // slots fill in order: a free last slot means u is not in the row
+  return table_contains_more(tab, b0, nb, b, u, probes);
+}
+
+// Bloom test of u against row x (one probe): false means u is certainly
+// not in the row.
+__device__ __forceinline__ bool bloom_maybe(const DevGraph& g, int32_t x, int32_t rs, int32_t re,
+                                            unsigned long long hk, uint32_t& probes) {
+  const uint32_t* blk = g.bloom + bloom_word(x, rs, re, hk);
+  ++probes;
+  uint32_t hit = 1u;
+#pragma unroll
+  for (int j = 0; j < kBloomBits; ++j) {
+    const uint32_t bit = (uint32_t)(hk >> (8 * j)) & 255u;
+    hit &= __ldg(blk + (bit >> 5)) >> (bit & 31u);
+  }
+  return (hit & 1u) != 0u;
+}
+
+// Is u in the row [rs, re) of node x?  Rows of at least kBloomMinDeg
+// entries: the membership table (one probe per bucket read), or without it
+// the Bloom filter (one probe) and a search of the row where the filter
+// passes; shorter rows: the search.  Exact.
+__device__ __forceinline__ bool row_member(const DevGraph& g, const Job& J, int32_t x, int32_t rs, int32_t re,
+                                           int32_t u, uint32_t& probes) {
+  if (re - rs >= kBloomMinDeg) {
+    if (J.table) return table_contains(g.mtab, x, rs, re, (uint32_t)(bloom_mix((uint32_t)u) >> 32), u, probes);
+    if (J.bloom && !bloom_maybe(g, x, rs, re, bloom_mix((uint32_t)u), probes)) return false;
+  }
+  return row_find(g.col, rs, re, u, g.n, probes) >= 0;
+}
+
+// Position of u in the row [rs, re) of node x, or -1: the table or the
+// filter answers "absent" without a search; otherwise the search gives the
+// position.  Exact.
 __device__ __forceinline__ int32_t row_lookup(const DevGraph& g, const Job& J, int32_t x, int32_t rs, int32_t re,
                                               int32_t u, uint32_t& probes) {
-  if (J.bloom && re - rs >= kBloomMinDeg) {
-    const unsigned long long hk = bloom_mix((uint32_t)u);
-    const uint32_t* blk = g.bloom + bloom_word(x, rs, re, hk);
-    ++probes;
-    uint32_t hit = 1u;
-#pragma unroll
-    for (int j = 0; j < kBloomBits; ++j) {
-      const uint32_t bit = (uint32_t)(hk >> (8 * j)) & 255u;
-      hit &= __ldg(blk + (bit >> 5)) >> (bit & 31u);
+  if (re - rs >= kBloomMinDeg) {
+    if (J.table) {
+      if (!table_contains(g.mtab, x, rs, re, (uint32_t)(bloom_mix((uint32_t)u) >> 32), u, probes)) return -1;
+    } else if (J.bloom && !bloom_maybe(g, x, rs, re, bloom_mix((uint32_t)u), probes)) {
+      return -1;
     }
-    if (!(hit & 1u)) return -1;
   }
   return row_find(g.col, rs, re, u, g.n, probes);
 }
 
-// Is u in N(v') (the row [c.ps, c.pe) of c.vp)?
+// Is u in the sorted array a[0, n) (shared memory)?
+__device__ __forceinline__ bool smem_contains(const int32_t* a, int32_t n, int32_t u) {
+  int32_t lo = 0, len = n;
+  while (len > 0) {
+    const int32_t half = len >> 1;
+    const int32_t v = a[lo + half];
+    if (v == u) return true;
+    if (v < u) {
+      lo += half + 1;
+      len -= half + 1;
+    } else {
+      len = half;
+    }
+  }
+  return false;
+}
+
+// Is u in N(v') (the row [c.ps, c.pe) of c.vp)?  sprev: the row staged in
+// shared memory by the calling warp (nullptr: read it from device memory).
 __device__ __forceinline__ bool prev_contains(const DevGraph& g, const Job& J, const StepCtx& c, int32_t u,
-                                              uint32_t& probes) {
-  return row_lookup(g, J, c.vp, c.ps, c.pe, u, probes) >= 0;
+                                              uint32_t& probes, const int32_t* sprev = nullptr) {
+  if (sprev) return smem_contains(sprev, c.pe - c.ps, u);
+  return row_member(g, J, c.vp, c.ps, c.pe, u, probes);
 }
 
 
-// Property weight of CSR entry i: FP32, or an 8-bit code times the graph's scale.
-__device__ __forceinline__ float load_h(const DevGraph& g, const Job& J, int32_t i) {
+// Property weight of CSR entry i of the row whose code scale is sc: FP32, or
+// an 8-bit code times sc.
+__device__ __forceinline__ float load_h(const DevGraph& g, const Job& J, int32_t i, float sc) {
   if (!J.weighted) return 1.0f;
-  return g.h8 ? __fmul_rn((float)__ldg(g.h8 + i), g.hscale) : __ldg(g.h + i);
+  return g.h8 ? __fmul_rn((float)__ldg(g.h8 + i), sc) : __ldg(g.h + i);
 }
 
 // Second-order PageRank with a short row of v' (Eq. 2ndpr): the common
@@ -321,7 +426,7 @@ static __device__ __noinline__ float common_h_sum(const DevGraph& g, const Job& 
   float sc = 0.0f;
   for (int32_t j = c.ps; j < c.pe; ++j) {
     const int32_t pos = row_lookup(g, J, c.v, c.s, c.s + c.d, __ldg(g.col + j), probes);
-    if (pos >= 0) sc = __fadd_rn(sc, load_h(g, J, pos));
+    if (pos >= 0) sc = __fadd_rn(sc, load_h(g, J, pos, c.hsc));
   }
   return sc;
 }
@@ -334,7 +439,7 @@ static __device__ __noinline__ int32_t common_pick(const DevGraph& g, const Job&
     const int32_t x = __ldg(g.col + j);
     const int32_t pos = row_lookup(g, J, c.v, c.s, c.s + c.d, x, probes);
     if (pos < 0) continue;
-    const float h = load_h(g, J, pos);
+    const float h = load_h(g, J, pos, c.hsc);
     run = __fadd_rn(run, h);
     node = x;
     k = pos - c.s;
@@ -345,28 +450,37 @@ static __device__ __noinline__ int32_t common_pick(const DevGraph& g, const Job&
 }
 
 // Transition weight of the neighbour at CSR index i (= s + k) of step c.
+// Transition weight w~ = w * hk of neighbour u (label lb) of step c.
 template <int ALG = -1>
-__device__ __forceinline__ float item_weight(const DevGraph& g, const Job& J, const StepCtx& c, int32_t i,
-                                             uint32_t& probes) {
-  const float hk = load_h(g, J, i);
+__device__ __forceinline__ float weight_of(const DevGraph& g, const Job& J, const StepCtx& c, float hk, int32_t u,
+                                           uint8_t lb, uint32_t& probes, const int32_t* sprev) {
   if (FW_ALGO(J) == ALGO_NODE2VEC) {
     if (c.vp < 0 || !J.second_order) return hk;
-    const int32_t u = __ldg(g.col + i);
     float w;
     if (u == c.vp) w = J.inv_p;                       // dist(v',u) = 0
     else if (!J.need_member) w = 1.0f;                // 1/q == 1: distances 1 and 2 weigh the same
-    else w = prev_contains(g, J, c, u, probes) ? 1.0f : J.inv_q;
+    else w = prev_contains(g, J, c, u, probes, sprev) ? 1.0f : J.inv_q;
     return __fmul_rn(w, hk);
   }
-  if (FW_ALGO(J) == ALGO_METAPATH) {
-    const uint8_t want = J.schema[c.step % J.schema_len];
-    return (__ldg(g.lab + i) == want) ? hk : 0.0f;    // w in {0, 1}
-  }
-  if (FW_ALGO(J) == ALGO_PAGERANK2 && c.vp >= 0) {
-    const int32_t u = __ldg(g.col + i);
-    return __fmul_rn(prev_contains(g, J, c, u, probes) ? c.w1 : c.w2, hk);
-  }
+  if (FW_ALGO(J) == ALGO_METAPATH) return (lb == J.schema[c.step % J.schema_len]) ? hk : 0.0f;  // w in {0, 1}
+  if (FW_ALGO(J) == ALGO_PAGERANK2 && c.vp >= 0)
+    return __fmul_rn(prev_contains(g, J, c, u, probes, sprev) ? c.w1 : c.w2, hk);
   return hk;
+}
+
+// Does step c's weight read the neighbour's id / its label?
+template <int ALG = -1>
+__device__ __forceinline__ bool weight_needs_col(const Job& J, const StepCtx& c) {
+  return (FW_ALGO(J) == ALGO_NODE2VEC && c.vp >= 0 && J.second_order) || (FW_ALGO(J) == ALGO_PAGERANK2 && c.vp >= 0);
+}
+
+template <int ALG = -1>
+__device__ __forceinline__ float item_weight(const DevGraph& g, const Job& J, const StepCtx& c, int32_t i,
+                                             uint32_t& probes, const int32_t* sprev = nullptr) {
+  const float hk = load_h(g, J, i, c.hsc);
+  const int32_t u = weight_needs_col<ALG>(J, c) ? __ldg(g.col + i) : -1;
+  const uint8_t lb = (FW_ALGO(J) == ALGO_METAPATH) ? __ldg(g.lab + i) : (uint8_t)0;
+  return weight_of<ALG>(g, J, c, hk, u, lb, probes, sprev);
 }
 
 // ---------------------------------------------------------------- plan
@@ -748,18 +862,175 @@ __device__ __forceinline__ int32_t rvs_pick(const DevGraph& g, const Job& J, con
   return (bestK == -CUDART_INF_F) ? -1 : best;
 }
 
+// ---------------------------------------------------------------- warp eRVS over 16-byte chunks
+// The warp's eRVS step (Sec. 3.2, Fig. 4b parallel jumps) with the row read
+// as 16-byte vector loads: with a = the scanned range's start rounded down
+// to a multiple of 4 entries, chunk q holds entries [a + 4q, a + 4q + 4) and
+// lane l owns chunks l, l + 32, ...; entries outside [c.s, c.s + c.d) weigh
+// nothing (the arrays are padded, so the chunk that straddles the end stays
+// inside its allocation).  Phase 1 keys each lane's first entry, the warp
+// maximum K_g is every lane's first reference, each lane then jumps over its
+// remaining entries in order (two chunks in flight), and the final argmax
+// (ties to the larger position) picks the neighbour.  A lane's entries are a
+// fixed subsequence of the row, so the draw follows Alg. 1 exactly as the
+// one-entry-per-lane partition does; draws are indexed by position
+// (counter (wid, hop, 2, k)), and the partition depends only on the row, so
+// the result does not depend on which warp runs the step.
+// GRP: the scanned range is a label segment of the grouped arrays (weights
+// gh); the result is then a grouped position.
+template <int ALG, bool GRP>
+struct Chunk {
+  float h[4];
+  int32_t col[4];
+  uint32_t lab;  // four labels, entry j in byte j
+};
+
+template <int ALG, bool GRP>
+__device__ __forceinline__ void load_chunk(const DevGraph& g, const Job& J, bool need_col, long long i, float sc,
+                                           Chunk<ALG, GRP>& ch) {
+  if (GRP) {
+    if (J.weighted) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(g.gh + i));
+      ch.h[0] = v.x; ch.h[1] = v.y; ch.h[2] = v.z; ch.h[3] = v.w;
+    } else {
+      ch.h[0] = ch.h[1] = ch.h[2] = ch.h[3] = 1.0f;
+    }
+    return;
+  }
+  if (!J.weighted) {
+    ch.h[0] = ch.h[1] = ch.h[2] = ch.h[3] = 1.0f;
+  } else if (g.h8) {
+    const uint32_t q = __ldg(reinterpret_cast<const uint32_t*>(g.h8 + i));
+#pragma unroll
+    for (int j = 0; j < 4; ++j) ch.h[j] = __fmul_rn((float)((q >> (8 * j)) & 255u), sc);
+  } else {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(g.h + i));
+    ch.h[0] = v.x; ch.h[1] = v.y; ch.h[2] = v.z; ch.h[3] = v.w;
+  }
+  if (need_col) {
+    const int4 v = __ldg(reinterpret_cast<const int4*>(g.col + i));
+    ch.col[0] = v.x; ch.col[1] = v.y; ch.col[2] = v.z; ch.col[3] = v.w;
+  } else {
+    ch.col[0] = ch.col[1] = ch.col[2] = ch.col[3] = -1;
+  }
+  ch.lab = (FW_ALGO(J) == ALGO_METAPATH) ? __ldg(reinterpret_cast<const uint32_t*>(g.lab + i)) : 0u;
+}
+
+template <bool COUNT, int ALG, bool GRP>
+__device__ __forceinline__ int32_t rvs_pick_warp(const DevGraph& g, const Job& J, const StepCtx& c, int lane, bool jump,
+                                                 LaneCounters& lc, const int32_t* sprev) {
+  const long long lo = c.s, hi = (long long)c.s + c.d;
+  const long long a = lo & ~3ll;
+  const int32_t nchunks = (int32_t)((hi - a + 3) >> 2);
+  const bool need_col = !GRP && weight_needs_col<ALG>(J, c);
+  uint32_t probes = 0;
+  int32_t scanned = 0, keys = 0;
+  float bestK = -CUDART_INF_F;
+  int32_t best = -1;
+  // phase 1: the first entry of the lane's first chunk
+  Chunk<ALG, GRP> ch0;
+  int32_t j0 = 4;  // first entry of chunk `lane` still to be scanned after phase 1
+  uint32_t xz = 0;
+  if (lane < nchunks) {
+    const long long base = a + 4ll * lane;
+    load_chunk<ALG, GRP>(g, J, need_col, base, c.hsc, ch0);
+    j0 = (base < lo) ? (int32_t)(lo - base) : 0;  // only chunk 0 starts before lo
+    // entry j0 of the chunk, selected without a run-time index into the
+    // chunk's arrays (that would move them to local memory)
+    float h0 = ch0.h[0];
+    int32_t u0 = ch0.col[0];
+#pragma unroll
+    for (int j = 1; j < 4; ++j) {
+      if (j == j0) {
+        h0 = ch0.h[j];
+        u0 = ch0.col[j];
+      }
+    }
+    const float wt = GRP ? h0 : weight_of<ALG>(g, J, c, h0, u0, (uint8_t)(ch0.lab >> (8 * j0)), probes, sprev);
+    const int32_t k = (int32_t)(base + j0 - lo);
+    const uint4 x = philox(make_uint4(c.wid, (uint32_t)c.step, 2u, (uint32_t)k), J.key0, J.key1);
+    xz = x.z;
+    ++scanned;
+    if (wt > 0.0f) {
+      bestK = logf(u01_open(x.x)) / wt;
+      best = k;
+      ++keys;
+    }
+    ++j0;
+  }
+  float ref = warp_max(bestK);
+  // remaining weight before the next crossing; K_ref = -inf: the first positive entry crosses
+  float rem = (ref == -CUDART_INF_F) ? 0.0f : ((ref < 0.0f) ? logf(u01_open(xz)) / ref : CUDART_INF_F);
+  auto visit = [&](const Chunk<ALG, GRP>& ch, long long base, int32_t jfrom) {
+#pragma unroll
+    for (int32_t j = 0; j < 4; ++j) {
+      if (j < jfrom || base + j >= hi) continue;
+      const float wt = GRP ? ch.h[j]
+                           : weight_of<ALG>(g, J, c, ch.h[j], ch.col[j], (uint8_t)(ch.lab >> (8 * j)), probes, sprev);
+      ++scanned;
+      if (!(wt > 0.0f)) continue;
+      const int32_t k = (int32_t)(base + j - lo);
+      if (!jump) {
+        const uint4 x = philox(make_uint4(c.wid, (uint32_t)c.step, 2u, (uint32_t)k), J.key0, J.key1);
+        const float K = logf(u01_open(x.x)) / wt;
+        ++keys;
+        if (K >= bestK) {
+          bestK = K;
+          best = k;
+        }
+      } else {
+        rem -= wt;
+        if (rem <= 0.0f) {
+          const uint4 x = philox(make_uint4(c.wid, (uint32_t)c.step, 2u, (uint32_t)k), J.key0, J.key1);
+          // key conditioned on beating ref: u' ~ U(exp(ref*wt), 1), K = ln(u') / wt
+          const float K = log1pf(expm1f(ref * wt) * u01_open(x.y)) / wt;
+          ++keys;
+          bestK = K;
+          best = k;
+          ref = K;
+          rem = (ref < 0.0f) ? logf(u01_open(x.z)) / ref : CUDART_INF_F;
+        }
+      }
+    }
+  };
+  if (lane < nchunks) visit(ch0, a + 4ll * lane, j0);
+  // the lane's other chunks, two loads in flight per round
+  for (int32_t q = lane + 32; q < nchunks; q += 64) {
+    Chunk<ALG, GRP> c1, c2;
+    const long long b1 = a + 4ll * q, b2 = b1 + 128;
+    load_chunk<ALG, GRP>(g, J, need_col, b1, c.hsc, c1);
+    const bool two = q + 32 < nchunks;
+    if (two) load_chunk<ALG, GRP>(g, J, need_col, b2, c.hsc, c2);
+    visit(c1, b1, 0);
+    if (two) visit(c2, b2, 0);
+  }
+  warp_argmax(bestK, best);
+  if (COUNT) {
+    // per-lane shares; summed over the warp they give the step's totals
+    lc.rvs_items += scanned;
+    lc.rvs_keys += keys;
+    lc.probes += probes;
+    const int per = GRP ? (J.weighted ? 4 : 0)
+                        : ((FW_ALGO(J) == ALGO_NODE2VEC) ? (J.weighted ? 8 : 4)
+                                                         : (FW_ALGO(J) == ALGO_METAPATH ? (J.weighted ? 5 : 1)
+                                                                                        : (J.weighted ? 4 : 0)));
+    lc.bytes += (unsigned long long)scanned * per + 32ull * probes;
+  }
+  return (bestK == -CUDART_INF_F) ? -1 : best;
+}
+
 // ---------------------------------------------------------------- exact
 // Exact inverse CDF with one uniform u: W_k accumulated with FP32 adds in
 // neighbour order (T = 32: the warp loads 32 weights at a time and replays
 // the additions in order through shuffles, so the sum is the serial one).
 template <int T, bool COUNT, int ALG = -1>
 __device__ __forceinline__ int32_t exact_pick(const DevGraph& g, const Job& J, const StepCtx& c, int lane, float u,
-                                              LaneCounters& lc) {
+                                              LaneCounters& lc, const int32_t* sprev = nullptr) {
   uint32_t probes = 0;
   float total = 0.0f;
   for (int32_t base = 0; base < c.d; base += T) {
     const int32_t k = base + lane;
-    const float wt = (k < c.d) ? item_weight<ALG>(g, J, c, c.s + k, probes) : 0.0f;
+    const float wt = (k < c.d) ? item_weight<ALG>(g, J, c, c.s + k, probes, sprev) : 0.0f;
     const int32_t cnt = min(T, c.d - base);
     if (T == 1) {
       total = __fadd_rn(total, wt);
@@ -773,7 +1044,7 @@ __device__ __forceinline__ int32_t exact_pick(const DevGraph& g, const Job& J, c
     float run = 0.0f;
     for (int32_t base = 0; base < c.d && pick < 0; base += T) {
       const int32_t k = base + lane;
-      const float wt = (k < c.d) ? item_weight<ALG>(g, J, c, c.s + k, probes) : 0.0f;
+      const float wt = (k < c.d) ? item_weight<ALG>(g, J, c, c.s + k, probes, sprev) : 0.0f;
       const int32_t cnt = min(T, c.d - base);
       if (T == 1) {
         run = __fadd_rn(run, wt);
@@ -791,7 +1062,7 @@ __device__ __forceinline__ int32_t exact_pick(const DevGraph& g, const Job& J, c
     if (pick < 0) {  // rounding left t >= W_{d-1}: last positive weight
       for (int32_t base = ((c.d - 1) / T) * T; base >= 0 && pick < 0; base -= T) {
         const int32_t k = base + lane;
-        const float wt = (k < c.d) ? item_weight<ALG>(g, J, c, c.s + k, probes) : 0.0f;
+        const float wt = (k < c.d) ? item_weight<ALG>(g, J, c, c.s + k, probes, sprev) : 0.0f;
         if (T == 1) {
           if (wt > 0.0f) pick = k;
         } else {

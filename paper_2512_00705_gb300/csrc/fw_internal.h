@@ -13,6 +13,9 @@
 
 // fw_walk_host splits large requests into at most this many chunks
 constexpr int kHostChunksMax = 16;
+// entries of padding (zeroed) past the end of cols, weights, labels, weight
+// codes and grouped weights: warp scans read rows in aligned 4-entry chunks
+constexpr size_t kScanPad = 4;
 
 struct fw_graph {
   int device = 0;
@@ -32,15 +35,22 @@ struct fw_graph {
   float2* d_lstat = nullptr;  // per-label node statistics (nullptr: not available)
   bool lstat_bad = false;     // a label >= kLabelStats occurs
   uint32_t* d_bloom = nullptr; // blocked Bloom filters of the rows (membership pre-check)
+  int32_t* d_mtab = nullptr;   // membership tables of the rows (exact; nullptr: not built)
   int4* d_lrec = nullptr;      // label-grouped view for metapath (nullptr: not built)
   int4* d_gerec = nullptr;
   float* d_gh = nullptr;
   uint8_t* d_h8 = nullptr;    // 8-bit weight codes after fw_graph_quantize_weights
-  float hscale = 0.0f;
+  float* d_h8scale = nullptr; // per node: the scale of its row's codes
+  float hscale = 0.0f;        // the largest per-node scale (reported by fw_graph_info)
   int32_t sym = 0;
   unsigned* d_err = nullptr;
   fw::DevCounters* d_cnt = nullptr;
   float ratio_algo[4] = {4.0f, 4.0f, 4.0f, 4.0f};  // r of Eq. (runtime) per algorithm (fw_algo order)
+  // launch shape per algorithm (fw_params lane_max_degree, rjs_batch, trial_budget), tuned by method 2
+  int32_t lane_max_algo[4] = {fw::kLaneMaxDegree, fw::kLaneMaxDegree, fw::kLaneMaxDegree, fw::kLaneMaxDegree};
+  int32_t rjs_batch_algo[4] = {fw::kRjsBatchDefault, fw::kRjsBatchDefault, fw::kRjsBatchDefault,
+                               fw::kRjsBatchDefault};
+  float budget_algo[4] = {1.0f, 1.0f, 1.0f, 1.0f};
   unsigned long long fingerprint = 0;
   double preprocess_ms = 0.0;
   size_t bytes = 0;
@@ -101,13 +111,13 @@ cudaError_t launch_label_group(const int32_t* off, const int32_t* col, const flo
                                int num_sms, cudaStream_t stream);
 cudaError_t launch_symmetry(const int32_t* off, const int32_t* col, const float* h, int32_t n, long long e,
                             unsigned* flag, int num_sms, cudaStream_t stream);
-cudaError_t launch_quantize(float* h, long long e, uint8_t* codes, float* scale_out, unsigned* maxbits, int num_sms,
-                            cudaStream_t stream);
-cudaError_t launch_dequantize(const uint8_t* codes, long long e, float scale, float* h, int num_sms, cudaStream_t stream);
+cudaError_t launch_quantize(const int32_t* off, float* h, const float* hmax, int32_t n, uint8_t* codes,
+                            float* scales, float* max_scale, unsigned* maxbits, int num_sms, cudaStream_t stream);
 size_t bloom_bytes(int32_t n, long long e);
+size_t table_bytes(int32_t n, long long e);
 cudaError_t prime_preprocess_kernels();
-cudaError_t launch_bloom(const int32_t* off, const int32_t* col, int32_t n, long long e, uint32_t* bloom, int num_sms,
-                         cudaStream_t stream);
+cudaError_t launch_bloom(const int32_t* off, const int32_t* col, int32_t n, long long e, uint32_t* bloom,
+                         int32_t* mtab, int num_sms, cudaStream_t stream);
 fw_status rebuild_derived(fw_graph* g, cudaStream_t stream);
 cudaError_t launch_check_offsets(const int32_t* off, int32_t n, int64_t e, unsigned* err, int num_sms,
                                  cudaStream_t stream);

@@ -389,37 +389,55 @@ cudaError_t launch_symmetry(const int32_t* off, const int32_t* col, const float*
   return cudaGetLastError();
 }
 
-// Blocked Bloom filters of the rows with at least kBloomMinDeg entries (the
-// layout and hashing are those of prev_contains); one warp per row.
+// Blocked Bloom filters and membership tables of the rows with at least
+// kBloomMinDeg entries (layouts and hashing are those of row_member; the
+// table may be nullptr); one warp per row.  A table entry goes to the first
+// slot at or after its home bucket that an atomicCAS finds free (-1); slots
+// are tried in order, so filled slots stay a prefix of every bucket.
 __global__ void bloom_kernel(const int32_t* __restrict__ off, const int32_t* __restrict__ col, int32_t n,
-                             uint32_t* __restrict__ bloom) {
+                             uint32_t* __restrict__ bloom, int32_t* __restrict__ mtab) {
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long x = warp; x < n; x += nwarps) {
     const int32_t s = off[x], e = off[x + 1];
     if (e - s < kBloomMinDeg) continue;
+    const long long tb0 = table_bucket0((int32_t)x, s);
+    const uint32_t tnb = table_buckets(s, e);
     for (int32_t i = s + lane; i < e; i += 32) {
-      const unsigned long long hk = bloom_mix((uint32_t)col[i]);
+      const int32_t u = col[i];
+      const unsigned long long hk = bloom_mix((uint32_t)u);
       uint32_t* blk = bloom + bloom_word((int32_t)x, s, e, hk);
 #pragma unroll
       for (int j = 0; j < kBloomBits; ++j) {
         const uint32_t bit = (uint32_t)(hk >> (8 * j)) & 255u;
         atomicOr(blk + (bit >> 5), 1u << (bit & 31u));
       }
+      if (mtab) {
+        // at most e - s < 8 * tnb ids share the row's buckets, so a free slot exists
+        uint32_t b = __umulhi((uint32_t)(hk >> 32), tnb);
+        bool placed = false;
+        for (uint32_t k = 0; k < tnb && !placed; ++k) {
+          int32_t* bucket = mtab + 8ll * (tb0 + b);
+          for (int q = 0; q < 8 && !placed; ++q) placed = atomicCAS(bucket + q, -1, u) == -1;
+          b = (b + 1 == tnb) ? 0u : b + 1;
+        }
+      }
     }
   }
 }
 
 size_t bloom_bytes(int32_t n, long long e) { return 32ull * (size_t)((e >> 5) + (long long)n + 1); }
+size_t table_bytes(int32_t n, long long e) { return 32ull * (size_t)((e >> 2) + (long long)n + 1); }
 
-cudaError_t launch_bloom(const int32_t* off, const int32_t* col, int32_t n, long long e, uint32_t* bloom, int num_sms,
-                         cudaStream_t stream) {
+cudaError_t launch_bloom(const int32_t* off, const int32_t* col, int32_t n, long long e, uint32_t* bloom,
+                         int32_t* mtab, int num_sms, cudaStream_t stream) {
   cudaError_t err = cudaMemsetAsync(bloom, 0, bloom_bytes(n, e), stream);
+  if (err == cudaSuccess && mtab) err = cudaMemsetAsync(mtab, 0xff, table_bytes(n, e), stream);
   if (err != cudaSuccess || n == 0) return err;
   const long long want = ((long long)n * 32 + 255) / 256;
   const int grid = (int)(want < (long long)num_sms * 8 ? want : (long long)num_sms * 8);
-  bloom_kernel<<<grid, 256, 0, stream>>>(off, col, n, bloom);
+  bloom_kernel<<<grid, 256, 0, stream>>>(off, col, n, bloom, mtab);
   g_launches.fetch_add(1);
   return cudaGetLastError();
 }
@@ -438,55 +456,47 @@ cudaError_t prime_preprocess_kernels() {
   return e;
 }
 
-// 8-bit weights: scale = max(h) / 255 (FP32 division), code = rint(h / scale)
-// clamped to [1, 255] (h > 0 stays > 0); the walks then use code * scale.
-__global__ void max_bits_kernel(const float* __restrict__ h, long long e, unsigned* __restrict__ maxbits) {
+// 8-bit weights with one scale per node: s_v = h_MAX[v] / 255 (FP32
+// division; h_MAX of the FP32 weights), code = rint(h / s_v) (ties to even)
+// clamped to [1, 255] (h > 0 stays > 0), and the FP32 copy rewritten as
+// code * s_v, from which every derived structure is then rebuilt.  One warp
+// per row; *maxbits receives the largest s_v (as bits: the scales are >= 0).
+__global__ void quantize_rows_kernel(const int32_t* __restrict__ off, float* __restrict__ h,
+                                     const float* __restrict__ hmax, int32_t n, uint8_t* __restrict__ codes,
+                                     float* __restrict__ scales, unsigned* __restrict__ maxbits) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   unsigned m = 0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < e; i += (long long)gridDim.x * blockDim.x)
-    m = max(m, __float_as_uint(h[i]));  // h > 0: the bit patterns order like the values
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
-  if ((threadIdx.x & 31) == 0 && m) atomicMax(maxbits, m);
-}
-
-__global__ void quantize_kernel(const float* __restrict__ h, long long e, const unsigned* __restrict__ maxbits,
-                                uint8_t* __restrict__ codes) {
-  const float scale = __fdiv_rn(__uint_as_float(*maxbits), 255.0f);
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < e; i += (long long)gridDim.x * blockDim.x) {
-    const float c = rintf(__fdiv_rn(h[i], scale));
-    codes[i] = (uint8_t)fminf(255.0f, fmaxf(1.0f, c));
+  for (long long v = warp; v < n; v += nwarps) {
+    const float sv = __fdiv_rn(hmax[v], 255.0f);
+    if (lane == 0) scales[v] = sv;
+    m = max(m, __float_as_uint(sv));
+    for (int32_t i = off[v] + lane; i < off[v + 1]; i += 32) {
+      const float c = fminf(255.0f, fmaxf(1.0f, rintf(__fdiv_rn(h[i], sv))));
+      codes[i] = (uint8_t)c;
+      h[i] = __fmul_rn(c, sv);
+    }
   }
+  if (lane == 0 && m) atomicMax(maxbits, m);
 }
 
-__global__ void dequantize_kernel(const uint8_t* __restrict__ codes, long long e, float scale, float* __restrict__ h) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < e; i += (long long)gridDim.x * blockDim.x)
-    h[i] = __fmul_rn((float)codes[i], scale);
-}
-
-cudaError_t launch_quantize(float* h, long long e, uint8_t* codes, float* scale_out, unsigned* maxbits, int num_sms,
-                            cudaStream_t stream) {
-  const int grid = num_sms * 8;
+cudaError_t launch_quantize(const int32_t* off, float* h, const float* hmax, int32_t n, uint8_t* codes,
+                            float* scales, float* max_scale, unsigned* maxbits, int num_sms, cudaStream_t stream) {
   cudaError_t err = cudaMemsetAsync(maxbits, 0, sizeof(unsigned), stream);
   if (err != cudaSuccess) return err;
-  max_bits_kernel<<<grid, 256, 0, stream>>>(h, e, maxbits);
-  quantize_kernel<<<grid, 256, 0, stream>>>(h, e, maxbits, codes);
-  g_launches.fetch_add(2);
-  err = cudaGetLastError();
-  if (err != cudaSuccess) return err;
+  if (n > 0) {
+    quantize_rows_kernel<<<num_sms * 8, 256, 0, stream>>>(off, h, hmax, n, codes, scales, maxbits);
+    g_launches.fetch_add(1);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+  }
   unsigned bits = 0;
   err = cudaMemcpyAsync(&bits, maxbits, sizeof(unsigned), cudaMemcpyDeviceToHost, stream);
   if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
   if (err != cudaSuccess) return err;
-  float mx;
-  std::memcpy(&mx, &bits, sizeof(float));
-  *scale_out = mx / 255.0f;  // the same FP32 division as the kernel
+  std::memcpy(max_scale, &bits, sizeof(float));
   return cudaSuccess;
-}
-
-cudaError_t launch_dequantize(const uint8_t* codes, long long e, float scale, float* h, int num_sms, cudaStream_t stream) {
-  dequantize_kernel<<<num_sms * 8, 256, 0, stream>>>(codes, e, scale, h);
-  g_launches.fetch_add(1);
-  return cudaGetLastError();
 }
 
 // CSR validation of device-resident input: bit 1 = offsets, bit 2 = column

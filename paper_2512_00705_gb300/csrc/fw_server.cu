@@ -12,9 +12,12 @@
 //   3. launches the admitted queries as one wave on a free stream: upload of
 //      each query's starts, one batched walk (up to 64 queries; one launch
 //      per algorithm present, each algorithm's queries one shared walker
-//      queue), download of each query's rows, an event.  The CUDA calls run
-//      without the server lock, so submitting and polling threads are not
-//      held up by them.
+//      queue), a count of the wave's hops on the device, download of each
+//      query's rows and of the count, an event.  The CUDA calls run without
+//      the server lock, so submitting and polling threads are not held up by
+//      them.
+// Clients may submit and poll many queries per call (one lock each), which
+// keeps a single client thread ahead of tens of thousands of queries/s.
 // Waves on different streams overlap on the device, and queries that arrive
 // while waves run join the next wave: continuous batching.  A query's rows
 // are identical to those of fw_walk_host with the same arguments, alone or
@@ -95,10 +98,37 @@ class Arena {
 struct Wave {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
-  unsigned long long* qctr = nullptr;
+  unsigned long long* qctr = nullptr;       // kQueueCounters queue counters, then the hop count (device)
+  unsigned long long* hops_host = nullptr;  // the wave's hop count, copied back (pinned host)
   std::vector<Request*> reqs;
   bool busy = false;
 };
+
+constexpr int kHopSlot = 8;  // index of the hop count in a wave's 256-byte counter block
+
+// Hops of a wave: row entries after the start column that hold a node (not
+// -1), over the rows of up to kMaxJobs queries; one atomic per warp.
+struct HopRows {
+  const int32_t* rows[fw::kMaxJobs];
+  int32_t walkers[fw::kMaxJobs];
+  int32_t width[fw::kMaxJobs];  // len + 1
+  int32_t n;
+};
+
+__global__ void count_hops_kernel(HopRows t, unsigned long long* __restrict__ hops) {
+  unsigned long long local = 0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (int j = 0; j < t.n; ++j) {
+    const int32_t w = t.width[j];
+    const long long total = (long long)t.walkers[j] * w;
+    const int32_t* r = t.rows[j];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride)
+      local += (i % w != 0 && __ldg(r + i) >= 0) ? 1ull : 0ull;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+  if ((threadIdx.x & 31) == 0 && local) atomicAdd(hops, local);
+}
 
 size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -120,7 +150,8 @@ struct fw_server {
   std::thread worker;
   // statistics
   std::vector<double> latencies_ms;
-  uint64_t completed = 0, failed = 0, waves_launched = 0, queries_in_waves = 0;
+  uint64_t completed = 0, failed = 0, waves_launched = 0, queries_in_waves = 0, walker_steps = 0;
+  unsigned long long* hops_host = nullptr;  // pinned, one slot per wave
   size_t peak_arena = 0;
   int peak_inflight = 0;
 };
@@ -147,6 +178,7 @@ void finish(fw_server* s, Request* r, fw_status st, const std::string& err) {
 // which the worker reserved.  Returns the first failing CUDA call's error.
 cudaError_t enqueue_wave(fw_server* s, Wave& w, const std::vector<Request*>& batch) {
   using namespace fw;
+  *w.hops_host = 0;
   std::vector<Job> tab;
   tab.reserve(batch.size());
   long long total = 0;
@@ -168,8 +200,25 @@ cudaError_t enqueue_wave(fw_server* s, Wave& w, const std::vector<Request*>& bat
       e = cudaMemcpyAsync(d_starts, r->starts, sizeof(int32_t) * (size_t)r->num_walkers, cudaMemcpyHostToDevice,
                           w.stream);
   }
-  if (e == cudaSuccess) e = cudaMemsetAsync(w.qctr, 0, sizeof(unsigned long long) * kQueueCounters, w.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.qctr, 0, sizeof(unsigned long long) * (kHopSlot + 1), w.stream);
   if (e == cudaSuccess && total > 0) e = launch_walk(s->g, tab.data(), (int)tab.size(), total, false, w.qctr, w.stream);
+  if (e == cudaSuccess && total > 0) {
+    HopRows hr;
+    hr.n = (int)tab.size();
+    long long entries = 0;
+    for (int j = 0; j < hr.n; ++j) {
+      hr.rows[j] = tab[j].out;
+      hr.walkers[j] = tab[j].num_walkers;
+      hr.width[j] = tab[j].len + 1;
+      entries += (long long)tab[j].num_walkers * (tab[j].len + 1);
+    }
+    const long long want = (entries + 255) / 256, cap = 4ll * s->g->num_sms;
+    count_hops_kernel<<<(int)(want < cap ? want : cap), 256, 0, w.stream>>>(hr, w.qctr + kHopSlot);
+    g_launches.fetch_add(1);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(w.hops_host, w.qctr + kHopSlot, sizeof(unsigned long long), cudaMemcpyDeviceToHost, w.stream);
   for (Request* r : batch) {
     if (e != cudaSuccess) break;
     e = cudaMemcpyAsync(r->out, s->arena_mem + r->arena_off + r->rows_off,
@@ -222,6 +271,7 @@ void worker_main(fw_server* s) {
       }
       const fw_status st = q == cudaSuccess ? FW_OK : FW_ERR_CUDA;
       const std::string msg = q == cudaSuccess ? std::string() : std::string("wave: ") + cudaGetErrorString(q);
+      if (q == cudaSuccess) s->walker_steps += *w.hops_host;
       for (Request* r : w.reqs) {
         s->arena->release(r->arena_off, r->bytes);
         finish(s, r, st, msg);
@@ -296,11 +346,14 @@ extern "C" fw_status fw_server_create(const fw_graph* g, const fw_server_config*
       if (w.done) cudaEventDestroy(w.done);
     }
     cudaFree(s->arena_mem);
+    cudaFreeHost(s->hops_host);
     delete s;
     return cuda_error(err, what);
   };
   e = cudaMalloc(&s->arena_mem, c.mem_budget);
   if (e != cudaSuccess) return fail(e, "cudaMalloc(server arena)");
+  e = cudaMallocHost(&s->hops_host, sizeof(unsigned long long) * (size_t)c.max_waves);
+  if (e != cudaSuccess) return fail(e, "cudaMallocHost(hop counts)");
   unsigned long long* q = nullptr;
   e = cudaMalloc(&q, 256 * (size_t)c.max_waves);
   if (e != cudaSuccess) return fail(e, "cudaMalloc(wave counters)");
@@ -308,6 +361,7 @@ extern "C" fw_status fw_server_create(const fw_graph* g, const fw_server_config*
   for (int i = 0; i < c.max_waves; ++i) {
     Wave& w = s->waves[i];
     w.qctr = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(q) + 256 * (size_t)i);
+    w.hops_host = s->hops_host + i;
     e = cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -321,20 +375,38 @@ extern "C" fw_status fw_server_create(const fw_graph* g, const fw_server_config*
   return FW_OK;
 }
 
-extern "C" fw_status fw_server_submit(fw_server* s, const int32_t* starts, int32_t num_walkers, int32_t len,
-                                      int32_t algo, const fw_params* params, uint64_t seed, int32_t* out,
-                                      uint64_t* ticket) {
-  if (!s || !ticket) return set_error(FW_ERR_ARG, "NULL argument");
-  if (num_walkers < 0 || len < 0 || (num_walkers > 0 && (!starts || !out)))
-    return set_error(FW_ERR_ARG, "bad sizes or NULL buffers");
+// A validated request for one query (no lock taken); nullptr and the
+// error status on bad arguments.
+static Request* new_request(fw_server* s, const int32_t* starts, int32_t num_walkers, int32_t len, int32_t algo,
+                            const fw_params* params, uint64_t seed, int32_t* out, fw_status* st) {
+  *st = FW_OK;
+  if (num_walkers < 0 || len < 0 || (num_walkers > 0 && (!starts || !out))) {
+    *st = set_error(FW_ERR_ARG, "bad sizes or NULL buffers");
+    return nullptr;
+  }
   Job J;
-  fw_status st = make_job(s->g, algo, params, seed, &J);  // validate parameters now
-  if (st != FW_OK) return st;
+  *st = make_job(s->g, algo, params, seed, &J);  // validate parameters now
+  if (*st != FW_OK) return nullptr;
   for (int32_t i = 0; i < num_walkers; ++i)
-    if (starts[i] < 0 || starts[i] >= s->g->n)
-      return set_error(FW_ERR_ARG, "start " + std::to_string(i) + " outside [0, n)");
+    if (starts[i] < 0 || starts[i] >= s->g->n) {
+      *st = set_error(FW_ERR_ARG, "start " + std::to_string(i) + " outside [0, n)");
+      return nullptr;
+    }
+  // staged starts and rows must fit the budget; each term is bounded before
+  // it is added or multiplied, so nothing wraps
+  const size_t rows_off = round256(sizeof(int32_t) * (size_t)num_walkers);  // < 2^34
+  const size_t row_bytes = sizeof(int32_t) * ((size_t)len + 1);             // < 2^34
+  const size_t budget = s->cfg.mem_budget;
+  if (rows_off > budget || (num_walkers > 0 && row_bytes > (budget - rows_off) / (size_t)num_walkers) ||
+      rows_off + round256(row_bytes * (size_t)num_walkers) > budget) {
+    *st = set_error(FW_ERR_OOM, "query needs more device memory than the server's budget");
+    return nullptr;
+  }
   Request* r = new (std::nothrow) Request();
-  if (!r) return set_error(FW_ERR_OOM, "host allocation");
+  if (!r) {
+    *st = set_error(FW_ERR_OOM, "host allocation");
+    return nullptr;
+  }
   r->starts = starts;
   r->out = out;
   r->num_walkers = num_walkers;
@@ -343,35 +415,70 @@ extern "C" fw_status fw_server_submit(fw_server* s, const int32_t* starts, int32
   if (params) r->params = *params;
   else fw_params_default(&r->params);
   r->seed = seed;
-  // staged starts and rows must fit the budget; each term is bounded before
-  // it is added or multiplied, so nothing wraps
-  r->rows_off = round256(sizeof(int32_t) * (size_t)num_walkers);  // < 2^34
-  const size_t row_bytes = sizeof(int32_t) * ((size_t)len + 1);    // < 2^34
-  const size_t budget = s->cfg.mem_budget;
-  if (r->rows_off > budget || (num_walkers > 0 && row_bytes > (budget - r->rows_off) / (size_t)num_walkers) ||
-      r->rows_off + round256(row_bytes * (size_t)num_walkers) > budget) {
-    delete r;
-    return set_error(FW_ERR_OOM, "query needs more device memory than the server's budget");
-  }
-  r->bytes = r->rows_off + round256(row_bytes * (size_t)num_walkers);
-  r->t_submit = Clock::now();
+  r->rows_off = rows_off;
+  r->bytes = rows_off + round256(row_bytes * (size_t)num_walkers);
+  return r;
+}
+
+// Queue validated requests under one lock; tickets[i] receives request i's.
+static fw_status enqueue(fw_server* s, Request* const* rs, int32_t count, uint64_t* tickets) {
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) {
-      delete r;
+      for (int32_t i = 0; i < count; ++i) delete rs[i];
       return set_error(FW_ERR_BUSY, "server is shutting down");
     }
-    r->id = s->next_id++;
-    if (num_walkers == 0) {
-      finish(s, r, FW_OK, "");
-    } else {
-      s->pending.push_back(r);
+    const auto now = Clock::now();
+    for (int32_t i = 0; i < count; ++i) {
+      Request* r = rs[i];
+      r->t_submit = now;
+      r->id = s->next_id++;
+      if (r->num_walkers == 0) {
+        finish(s, r, FW_OK, "");
+      } else {
+        s->pending.push_back(r);
+      }
+      s->reqs[r->id] = r;
+      tickets[i] = r->id;
     }
-    s->reqs[r->id] = r;
-    *ticket = r->id;
   }
   s->cv_work.notify_one();
   return FW_OK;
+}
+
+extern "C" fw_status fw_server_submit(fw_server* s, const int32_t* starts, int32_t num_walkers, int32_t len,
+                                      int32_t algo, const fw_params* params, uint64_t seed, int32_t* out,
+                                      uint64_t* ticket) {
+  if (!s || !ticket) return set_error(FW_ERR_ARG, "NULL argument");
+  fw_status st;
+  Request* r = new_request(s, starts, num_walkers, len, algo, params, seed, out, &st);
+  if (!r) return st;
+  return enqueue(s, &r, 1, ticket);
+}
+
+extern "C" fw_status fw_server_submit_many(fw_server* s, const fw_job* queries, int32_t count, uint64_t* tickets,
+                                           int32_t* submitted) {
+  if (!s || count < 0 || (count > 0 && (!queries || !tickets))) return set_error(FW_ERR_ARG, "bad arguments");
+  if (submitted) *submitted = 0;
+  std::vector<Request*> rs;
+  rs.reserve((size_t)count);
+  fw_status first_error = FW_OK;
+  for (int32_t i = 0; i < count; ++i) {
+    const fw_job& q = queries[i];
+    fw_status st;
+    Request* r = new_request(s, q.starts, q.num_walkers, q.len, q.algo, &q.params, q.seed, q.out, &st);
+    if (!r) {
+      first_error = set_error(st, "query " + std::to_string(i) + ": " + fw_last_error());
+      break;
+    }
+    rs.push_back(r);
+  }
+  if (!rs.empty()) {
+    const fw_status st = enqueue(s, rs.data(), (int32_t)rs.size(), tickets);
+    if (st != FW_OK) return st;
+    if (submitted) *submitted = (int32_t)rs.size();
+  }
+  return first_error;
 }
 
 static fw_status collect(fw_server* s, std::unordered_map<uint64_t, Request*>::iterator it, double* latency_ms) {
@@ -393,6 +500,29 @@ extern "C" fw_status fw_server_poll(fw_server* s, uint64_t ticket, int32_t* done
   *done = (st == REQ_DONE || st == REQ_FAILED) ? 1 : 0;
   if (!*done) return FW_OK;
   return collect(s, it, latency_ms);
+}
+
+extern "C" fw_status fw_server_poll_many(fw_server* s, const uint64_t* tickets, int32_t count, int32_t* done,
+                                         double* latency_ms, int32_t* status) {
+  if (!s || count < 0 || (count > 0 && (!tickets || !done))) return set_error(FW_ERR_ARG, "bad arguments");
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (int32_t i = 0; i < count; ++i) {
+    auto it = s->reqs.find(tickets[i]);
+    if (it == s->reqs.end()) {
+      done[i] = 1;
+      if (status) status[i] = FW_ERR_ARG;
+      if (latency_ms) latency_ms[i] = 0.0;
+      continue;
+    }
+    Request* r = it->second;
+    done[i] = (r->state == REQ_DONE || r->state == REQ_FAILED) ? 1 : 0;
+    if (!done[i]) continue;
+    if (latency_ms) latency_ms[i] = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+    if (status) status[i] = r->status;
+    s->reqs.erase(it);
+    delete r;
+  }
+  return FW_OK;
 }
 
 extern "C" fw_status fw_server_wait(fw_server* s, uint64_t ticket, double timeout_s, double* latency_ms) {
@@ -422,6 +552,7 @@ extern "C" fw_status fw_server_stats(fw_server* s, fw_server_stats_t* out) {
   out->queries_per_wave = s->waves_launched ? (double)s->queries_in_waves / (double)s->waves_launched : 0.0;
   out->peak_device_bytes = s->peak_arena;
   out->peak_inflight_waves = s->peak_inflight;
+  out->walker_steps = s->walker_steps;
   std::vector<double> l = s->latencies_ms;
   if (!l.empty()) {
     std::sort(l.begin(), l.end());
@@ -452,6 +583,7 @@ extern "C" fw_status fw_server_destroy(fw_server* s) {
   }
   cudaFree(q);
   cudaFree(s->arena_mem);
+  cudaFreeHost(s->hops_host);
   delete s->arena;
   delete s;
   return FW_OK;

@@ -26,8 +26,11 @@ namespace fw {
 
 constexpr int kBlock = 256;
 constexpr int kMinBlocks = 4;  // 4 x 256 threads per SM (64 registers; 3, 5 and 6 blocks measured slower)
-constexpr int kRjsBatch = 2;  // eRJS trials per round before the warp ballot (1, 3 and 4 measured slower)
 constexpr int kThreadExactMaxDeg = 16; // exact steps with d <= this run on one lane
+// Warp-level eRVS / exact steps of node2vec and second-order PageRank stage
+// N(v') in the warp's shared memory when it has at most this many entries:
+// every membership test of the scan is then a shared-memory search.
+constexpr int kStagePrev = 1024;
 
 // Row writes are staged per lane in shared memory, one aligned group of
 // kStageSlots entries at a time, and written out when the group (or the
@@ -96,7 +99,7 @@ struct JobTableN {
 template <bool COUNT, int ALG>
 __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int njobs, long long total,
                                           unsigned long long* __restrict__ qctr, unsigned* __restrict__ err,
-                                          int32_t* obuf, LaneCounters& lc) {
+                                          int32_t* obuf, int32_t* wprev, LaneCounters& lc) {
   static_assert(ALG >= 0 && ALG < kAlgos, "the walk loop is compiled for one algorithm");
   const int lane = threadIdx.x & 31;
   const int tid = threadIdx.x;
@@ -113,6 +116,7 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
   c.w1 = c.w2 = 1.0f;
   c.n0 = -1;
   c.n1 = 0;
+  c.hsc = 0.0f;
   int32_t job = 0, widx = -1;
   int32_t plan = PLAN_NONE, trials = 0, pick = -2, node = -1;
   float B = 0.0f;
@@ -214,6 +218,7 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
       nxt_ok = false;
       c.s = nr.x;
       c.d = nr.y;
+      if (g.h8) c.hsc = __ldg(g.h8scale + c.v);  // scale of the codes of v's row
       // weight classes in eRJS wherever the bound is a multiple of h_MAX[v]
       const bool cls = J.classes && !(FW_ALGO(J) == ALGO_METAPATH && J.label_stats);
       c.n0 = cls ? n0 : -1;
@@ -298,7 +303,7 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
           } else if (m == MODE_DEGREE) {
             m = (c.d < kDegreeRuleThreshold) ? MODE_RVS : MODE_RJS;
           }
-          plan = (m == MODE_RJS) ? PLAN_RJS : (((grp ? c.pe - c.ps : c.d) <= kThreadRvsMaxDeg) ? PLAN_RVS_T : PLAN_RVS_W);
+          plan = (m == MODE_RJS) ? PLAN_RJS : (((grp ? c.pe - c.ps : c.d) <= J.lane_max) ? PLAN_RVS_T : PLAN_RVS_W);
           if (split) {  // second-order PageRank: S_C and the probability of the common-neighbour part
             split = plan == PLAN_RJS;
             if (split) {
@@ -332,7 +337,7 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
                 lc.bytes += 32ull * pb;
               }
               if (pos_ret >= 0) {
-                h_ret = load_h(g, J, pos_ret);
+                h_ret = load_h(g, J, pos_ret, c.hsc);
                 pos_ret -= c.s;
                 have = true;
               }
@@ -355,7 +360,7 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
     // ------------------------------------------------------------ eRJS trials
     if (widx >= 0 && plan == PLAN_RJS && pick == -2) {
       Accept acc;
-      if (rjs_trials<COUNT, ALG>(g, J, c, B, split, beta, pos_ret, h_ret, trials, kRjsBatch, acc, lc, csplit, beta2,
+      if (rjs_trials<COUNT, ALG>(g, J, c, B, split, beta, pos_ret, h_ret, trials, J.rjs_batch, acc, lc, csplit, beta2,
                                  grp)) {
         pick = acc.k;
         node = acc.node;
@@ -366,13 +371,15 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
         nxt_ok = acc.rec_ok;
         if (COUNT) lc.rjs_steps++;
       } else {
-        trials += kRjsBatch;
+        trials += J.rjs_batch;
         // trial budget: the cap, or (default) as many trials as the eRVS scan
-        // they stand in for would cost under the cost model, d / r
+        // they stand in for would cost under the cost model, d / r, times the
+        // budget scale
         const int32_t dd = grp ? c.pe - c.ps : c.d;  // entries the eRVS hand-off would scan
-        const int32_t cap = J.fixed_cap ? J.rjs_cap : max(J.rjs_cap, (int32_t)ceilf((float)dd / J.ratio));
+        const int32_t cap =
+            J.fixed_cap ? J.rjs_cap : max(J.rjs_cap, (int32_t)fminf(ceilf(J.budget * (float)dd / J.ratio), 1.0e9f));
         if (trials >= cap) {
-          plan = (dd <= kThreadRvsMaxDeg) ? PLAN_RVS_T : PLAN_RVS_W;
+          plan = (dd <= J.lane_max) ? PLAN_RVS_T : PLAN_RVS_W;
           if (COUNT) lc.handoffs++;
         }
       }
@@ -427,23 +434,37 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
         w.w1 = __shfl_sync(kFull, c.w1, src);
         w.w2 = __shfl_sync(kFull, c.w2, src);
       }
+      w.hsc = g.h8 ? __shfl_sync(kFull, c.hsc, src) : 0.0f;
       const int jb = __shfl_sync(kFull, job, src);
       const int pl = __shfl_sync(kFull, plan, src);
       bool wg = false;
       if (ALG == ALGO_METAPATH) wg = __shfl_sync(kFull, (int)grp, src) != 0;
       const Job& JW = sj[jb];
+      // N(v') into the warp's shared buffer when the scan's weights test membership in it
+      const int32_t* sp = nullptr;
+      if ((ALG == ALGO_NODE2VEC && w.vp >= 0 && JW.second_order && JW.need_member) ||
+          (ALG == ALGO_PAGERANK2 && w.vp >= 0)) {
+        const int32_t np = w.pe - w.ps;
+        if (np <= kStagePrev) {
+          for (int32_t j = lane; j < np; j += 32) wprev[j] = __ldg(g.col + w.ps + j);
+          __syncwarp();
+          sp = wprev;
+          if (COUNT) lc.bytes += 4ull * (uint32_t)((np - lane + 31) / 32);
+        }
+      }
       int32_t k;
       if (pl == PLAN_EXACT_W) {
         const float u = u01(philox(make_uint4(w.wid, (uint32_t)w.step, 0u, 0u), JW.key0, JW.key1).x);
-        k = exact_pick<32, COUNT, ALG>(g, JW, w, lane, u, lc);
+        k = exact_pick<32, COUNT, ALG>(g, JW, w, lane, u, lc, sp);
       } else if (ALG == ALGO_METAPATH && wg) {
         StepCtx cg = w;
         cg.s = w.ps;
         cg.d = w.pe - w.ps;
-        k = rvs_pick<32, COUNT, ALG, true>(g, JW, cg, lane, !(JW.flags & FW_FLAG_RVS_NOJUMP), lc);
+        k = rvs_pick_warp<COUNT, ALG, true>(g, JW, cg, lane, !(JW.flags & FW_FLAG_RVS_NOJUMP), lc, nullptr);
       } else {
-        k = rvs_pick<32, COUNT, ALG>(g, JW, w, lane, !(JW.flags & FW_FLAG_RVS_NOJUMP), lc);
+        k = rvs_pick_warp<COUNT, ALG, false>(g, JW, w, lane, !(JW.flags & FW_FLAG_RVS_NOJUMP), lc, sp);
       }
+      __syncwarp();  // every lane is done with the staged row before the next hand-off overwrites it
       if (lane == src && ALG == ALGO_METAPATH && wg) {
         pick = -1;
         if (k >= 0) {  // grouped position -> node, position in the row, node record
@@ -531,11 +552,16 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
                                                       unsigned* __restrict__ err, DevCounters* __restrict__ cnt) {
   __shared__ Job sj[NJ];
   __shared__ int32_t obuf[kStageSlots * kBlock];
+  // staged rows of v' for node2vec and second-order PageRank warp steps (one per warp)
+  constexpr int kPrevRows = (ALG == ALGO_NODE2VEC || ALG == ALGO_PAGERANK2) ? kBlock / 32 : 1;
+  constexpr int kPrevLen = (ALG == ALGO_NODE2VEC || ALG == ALGO_PAGERANK2) ? kStagePrev : 1;
+  __shared__ int32_t sprev[kPrevRows][kPrevLen];
   load_jobs(tab.jobs, njobs, sj);
   __syncthreads();
   LaneCounters lc;
   lc.zero();
-  walk_loop<COUNT, ALG>(g, sj, njobs, total, qctr, err, obuf, lc);
+  walk_loop<COUNT, ALG>(g, sj, njobs, total, qctr, err, obuf, sprev[(ALG == ALGO_NODE2VEC || ALG == ALGO_PAGERANK2)
+                                                                       ? (threadIdx.x >> 5) : 0], lc);
   if (COUNT) flush_counters(lc, cnt);
 }
 

@@ -20,7 +20,7 @@ from . import _build
 ALGO = {"weighted": 0, "node2vec": 1, "metapath": 2, "pagerank2": 3}
 MODE = {"auto": 0, "rjs": 1, "rvs": 2, "exact": 3, "random": 4, "degree": 5}
 FLAG_RVS_NOJUMP, FLAG_COUNTERS, FLAG_UNWEIGHTED, FLAG_PLAIN_RJS, FLAG_PAPER_SUM, FLAG_NO_BLOOM = 1, 2, 4, 8, 16, 32
-FLAG_NO_GROUPS = 64
+FLAG_NO_GROUPS, FLAG_NO_TABLE = 64, 128
 PTR_HOST, PTR_DEVICE = 0, 1
 STATUS = {0: "FW_OK", -1: "FW_ERR_ARG", -2: "FW_ERR_CSR", -3: "FW_ERR_OOM", -4: "FW_ERR_CUDA",
           -5: "FW_ERR_TIMEOUT", -6: "FW_ERR_DEVICE_CHECK", -7: "FW_ERR_BUSY", -8: "FW_ERR_UNSUPPORTED"}
@@ -36,7 +36,8 @@ class fw_params(ctypes.Structure):
     _fields_ = [("p", ctypes.c_float), ("q", ctypes.c_float), ("schema", ctypes.c_uint8 * 16),
                 ("schema_len", ctypes.c_int32), ("mode", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("cost_ratio", ctypes.c_float), ("rjs_cap", ctypes.c_int32), ("walker_base", ctypes.c_uint32),
-                ("gamma", ctypes.c_float)]
+                ("gamma", ctypes.c_float), ("lane_max_degree", ctypes.c_int32), ("rjs_batch", ctypes.c_int32),
+                ("trial_budget", ctypes.c_float)]
 
 
 class fw_graph_info_t(ctypes.Structure):
@@ -44,7 +45,8 @@ class fw_graph_info_t(ctypes.Structure):
                 ("has_weights", ctypes.c_int32), ("has_labels", ctypes.c_int32), ("cost_ratio", ctypes.c_float),
                 ("preprocess_ms", ctypes.c_double), ("device_bytes", ctypes.c_size_t), ("symmetric", ctypes.c_int32),
                 ("cost_ratios", ctypes.c_float * 4), ("fingerprint", ctypes.c_uint64),
-                ("weight_scale", ctypes.c_float)]
+                ("weight_scale", ctypes.c_float), ("lane_max_degrees", ctypes.c_int32 * 4),
+                ("rjs_batches", ctypes.c_int32 * 4), ("trial_budgets", ctypes.c_float * 4)]
 
 
 class fw_job(ctypes.Structure):
@@ -60,7 +62,8 @@ class fw_server_stats_t(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64), ("pending", ctypes.c_uint64),
                 ("waves", ctypes.c_uint64), ("queries_per_wave", ctypes.c_double), ("p50_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
-                ("peak_device_bytes", ctypes.c_size_t), ("peak_inflight_waves", ctypes.c_int32)]
+                ("peak_device_bytes", ctypes.c_size_t), ("peak_inflight_waves", ctypes.c_int32),
+                ("walker_steps", ctypes.c_uint64)]
 
 
 COUNTER_FIELDS = ["hops", "rjs_steps", "rvs_steps", "exact_steps", "handoffs", "rjs_trials", "rvs_items",
@@ -100,6 +103,7 @@ def lib() -> ctypes.CDLL:
                 "fw_graph_set_cost_ratio": (ctypes.c_int, [vp, ctypes.c_float]),
                 "fw_graph_label_stats": (ctypes.c_int, [vp, vp, vp]),
                 "fw_graph_quantize_weights": (ctypes.c_int, [vp, P(ctypes.c_float), vp]),
+                "fw_graph_weight_scales": (ctypes.c_int, [vp, vp, vp]),
                 "fw_autotune": (ctypes.c_int, [vp, i32, P(fw_params), i32, ctypes.c_char_p, P(ctypes.c_float), vp]),
                 "fw_walk": (ctypes.c_int, [vp, vp, i32, i32, i32, P(fw_params), u64, vp, vp]),
                 "fw_walk_host": (ctypes.c_int, [vp, vp, i32, i32, i32, P(fw_params), u64, vp, vp]),
@@ -118,6 +122,8 @@ def lib() -> ctypes.CDLL:
                 "fw_server_create": (ctypes.c_int, [vp, P(fw_server_config), P(vp)]),
                 "fw_server_submit": (ctypes.c_int, [vp, vp, i32, i32, i32, P(fw_params), u64, vp,
                                                      P(ctypes.c_uint64)]),
+                "fw_server_submit_many": (ctypes.c_int, [vp, vp, i32, vp, P(i32)]),
+                "fw_server_poll_many": (ctypes.c_int, [vp, vp, i32, vp, vp, vp]),
                 "fw_server_poll": (ctypes.c_int, [vp, ctypes.c_uint64, P(i32), P(ctypes.c_double)]),
                 "fw_server_wait": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_double, P(ctypes.c_double)]),
                 "fw_server_stats": (ctypes.c_int, [vp, P(fw_server_stats_t)]),
@@ -150,7 +156,8 @@ def _stream_ptr(stream) -> Optional[int]:
 
 
 def make_params(p: float = 1.0, q: float = 1.0, schema: Optional[Sequence[int]] = None, mode="auto", flags: int = 0,
-                cost_ratio: float = 0.0, rjs_cap: int = 0, walker_base: int = 0, gamma: float = 0.2) -> fw_params:
+                cost_ratio: float = 0.0, rjs_cap: int = 0, walker_base: int = 0, gamma: float = 0.2,
+                lane_max_degree: int = 0, rjs_batch: int = 0, trial_budget: float = 0.0) -> fw_params:
     prm = fw_params()
     lib().fw_params_default(ctypes.byref(prm))
     prm.p, prm.q = float(p), float(q)
@@ -167,6 +174,9 @@ def make_params(p: float = 1.0, q: float = 1.0, schema: Optional[Sequence[int]] 
     prm.cost_ratio = float(cost_ratio)
     prm.rjs_cap = int(rjs_cap)
     prm.walker_base = int(walker_base)
+    prm.lane_max_degree = int(lane_max_degree)
+    prm.rjs_batch = int(rjs_batch)
+    prm.trial_budget = float(trial_budget)
     return prm
 
 
@@ -206,7 +216,8 @@ def fw_graph_info(handle: int) -> dict:
     info = fw_graph_info_t()
     _check(lib().fw_graph_info(handle, ctypes.byref(info)))
     d = {f: getattr(info, f) for f, _ in fw_graph_info_t._fields_}
-    d["cost_ratios"] = list(d["cost_ratios"])
+    for k in ("cost_ratios", "lane_max_degrees", "rjs_batches", "trial_budgets"):
+        d[k] = list(d[k])
     return d
 
 
@@ -310,38 +321,39 @@ class Graph:
             pass
 
     def walk(self, starts, length: int, algo="node2vec", *, p=1.0, q=1.0, schema=None, mode="auto", seed=42,
-             flags=0, cost_ratio=0.0, rjs_cap=0, walker_base=0, gamma=0.2, out=None, stream=None):
+             flags=0, cost_ratio=0.0, rjs_cap=0, walker_base=0, gamma=0.2, out=None, stream=None, **shape):
+        """shape: lane_max_degree / rjs_batch / trial_budget of fw_params (0: the graph's tuned value)."""
         import torch
         if out is None:
             out = torch.empty((starts.numel(), length + 1), dtype=torch.int32, device=starts.device)
-        prm = make_params(p, q, schema, mode, flags, cost_ratio, rjs_cap, walker_base, gamma)
+        prm = make_params(p, q, schema, mode, flags, cost_ratio, rjs_cap, walker_base, gamma, **shape)
         fw_walk(self.handle, starts, length, algo, prm, seed, out, stream)
         return out
 
     def walk_ids(self, starts, walker_ids, length: int, algo="node2vec", *, p=1.0, q=1.0, schema=None, mode="auto",
-                 seed=42, flags=0, cost_ratio=0.0, rjs_cap=0, gamma=0.2, out=None, stream=None):
+                 seed=42, flags=0, cost_ratio=0.0, rjs_cap=0, gamma=0.2, out=None, stream=None, **shape):
         import torch
         if out is None:
             out = torch.empty((starts.numel(), length + 1), dtype=torch.int32, device=starts.device)
-        prm = make_params(p, q, schema, mode, flags, cost_ratio, rjs_cap, 0, gamma)
+        prm = make_params(p, q, schema, mode, flags, cost_ratio, rjs_cap, 0, gamma, **shape)
         fw_walk_ids(self.handle, starts, walker_ids, length, algo, prm, seed, out, stream)
         return out
 
     def walk_host(self, starts, length: int, algo="node2vec", *, p=1.0, q=1.0, schema=None, mode="auto", seed=42,
-                  flags=0, cost_ratio=0.0, rjs_cap=0, walker_base=0, gamma=0.2, out=None, stream=None):
+                  flags=0, cost_ratio=0.0, rjs_cap=0, walker_base=0, gamma=0.2, out=None, stream=None, **shape):
         if out is None:
             out = np.empty((len(starts), length + 1), dtype=np.int32)
-        prm = make_params(p, q, schema, mode, flags, cost_ratio, rjs_cap, walker_base, gamma)
+        prm = make_params(p, q, schema, mode, flags, cost_ratio, rjs_cap, walker_base, gamma, **shape)
         fw_walk_host(self.handle, starts, length, algo, prm, seed, out, stream)
         return out
 
     def sample_hist(self, v: int, v_prev: int, step: int, algo="node2vec", ndraws: int = 1_000_000, *, p=1.0, q=1.0,
                     schema=None, mode="auto", seed=42, flags=0, cost_ratio=0.0, rjs_cap=0, walker_base=0,
-                    gamma=0.2, stream=None):
+                    gamma=0.2, stream=None, **shape):
         import torch
         d = self.degree(v)
         counts = torch.zeros(max(d, 1), dtype=torch.int64, device="cuda")
-        prm = make_params(p, q, schema, mode, flags, cost_ratio, rjs_cap, walker_base, gamma)
+        prm = make_params(p, q, schema, mode, flags, cost_ratio, rjs_cap, walker_base, gamma, **shape)
         fw_sample_hist(self.handle, v, v_prev, step, algo, prm, seed, ndraws, counts, stream)
         return counts[:d]
 
@@ -391,11 +403,19 @@ class Graph:
         self.info = fw_graph_info(self.handle)
 
     def quantize_weights(self, stream=None) -> float:
-        """Switch the graph to 8-bit weight codes (code * scale); returns the scale."""
+        """Switch the graph to 8-bit weight codes (code * the scale of the
+        row's node); returns the largest per-node scale."""
         s = ctypes.c_float()
         _check(lib().fw_graph_quantize_weights(self.handle, ctypes.byref(s), _stream_ptr(stream)))
         self.info = fw_graph_info(self.handle)
         return float(s.value)
+
+    def weight_scales(self, stream=None):
+        """Per-node scales of the 8-bit codes as a CUDA float32 tensor [n]."""
+        import torch
+        out = torch.empty(max(self.n, 1), dtype=torch.float32, device="cuda")
+        _check(lib().fw_graph_weight_scales(self.handle, _ptr(out), _stream_ptr(stream)))
+        return out[:self.n]
 
     def degree(self, v: int) -> int:
         return int(self._off[v + 1] - self._off[v])
@@ -403,16 +423,31 @@ class Graph:
 
 # ---------------------------------------------------------------- batching
 def make_job(starts, length: int, algo, out, *, p=1.0, q=1.0, schema=None, mode="auto", seed=42, flags=0,
-             cost_ratio=0.0, rjs_cap=0, walker_base=0, gamma=0.2) -> fw_job:
+             cost_ratio=0.0, rjs_cap=0, walker_base=0, gamma=0.2, **shape) -> fw_job:
     """One batch entry; starts / out are CUDA tensors that must outlive the launch."""
     j = fw_job()
     j.starts = _ptr(starts)
     j.num_walkers = starts.numel()
     j.len = length
     j.algo = ALGO.get(algo, algo)
-    j.params = make_params(p, q, schema, mode, flags, cost_ratio, rjs_cap, walker_base, gamma)
+    j.params = make_params(p, q, schema, mode, flags, cost_ratio, rjs_cap, walker_base, gamma, **shape)
     j.seed = seed
     j.out = _ptr(out)
+    return j
+
+
+def make_host_query(starts: np.ndarray, length: int, algo, out: np.ndarray, *, p=1.0, q=1.0, schema=None,
+                    mode="auto", seed=42, flags=0, walker_base=0, gamma=0.2) -> fw_job:
+    """One query for Server.submit_many: starts / out are host numpy arrays
+    (int32[W], int32[W][length+1]) that must outlive the query."""
+    j = fw_job()
+    j.starts = starts.ctypes.data
+    j.num_walkers = starts.shape[0]
+    j.len = length
+    j.algo = ALGO.get(algo, algo)
+    j.params = make_params(p, q, schema, mode, flags, 0.0, 0, walker_base, gamma)
+    j.seed = seed
+    j.out = out.ctypes.data
     return j
 
 
@@ -467,6 +502,28 @@ class Server:
         _check(lib().fw_server_submit(self.handle, _ptr(starts), n, length, ALGO.get(algo, algo), ctypes.byref(prm),
                                       seed, _ptr(out), ctypes.byref(t)))
         return int(t.value)
+
+    def submit_many(self, jobs) -> np.ndarray:
+        """Queue many queries in one call: `jobs` is a ctypes array of fw_job
+        (make_host_query) whose buffers stay alive until collected; returns
+        the tickets (uint64 numpy array)."""
+        n = len(jobs)
+        tickets = np.zeros(n, dtype=np.uint64)
+        done = ctypes.c_int32()
+        _check(lib().fw_server_submit_many(self.handle, ctypes.cast(jobs, ctypes.c_void_p), n,
+                                           tickets.ctypes.data, ctypes.byref(done)))
+        return tickets
+
+    def poll_many(self, tickets: np.ndarray):
+        """(done int32[n], latency_ms float64[n], status int32[n]) for the
+        tickets; finished ones are released."""
+        t = np.ascontiguousarray(tickets, dtype=np.uint64)
+        done = np.zeros(t.shape[0], dtype=np.int32)
+        lat = np.zeros(t.shape[0], dtype=np.float64)
+        st = np.zeros(t.shape[0], dtype=np.int32)
+        _check(lib().fw_server_poll_many(self.handle, t.ctypes.data, t.shape[0], done.ctypes.data, lat.ctypes.data,
+                                         st.ctypes.data))
+        return done, lat, st
 
     def poll(self, ticket: int):
         """None while running, else the latency in ms (the ticket is released)."""
