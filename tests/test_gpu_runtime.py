@@ -1,7 +1,9 @@
 """GPU tests of the runtime around the samplers: the profiled cost ratio
-(Sec. 5.1), its cache, and that no runtime choice changes the walks'
-distribution."""
+(Sec. 5.1), its cache, that no runtime choice changes the walks'
+distribution, batches and the serving loop."""
+import ctypes
 import os
+import time
 
 import numpy as np
 import pytest
@@ -89,13 +91,13 @@ def test_cost_ratio_never_changes_the_distribution(ratio):
 
 
 # ------------------------------------------------------------ batching
-def _mixed_jobs(g, count, seed, max_walkers=3000):
+def _mixed_jobs(g, count, seed, max_walkers=3000, max_length=30):
     rng = np.random.default_rng(seed)
     specs = []
     for i in range(count):
         algo = ["node2vec", "metapath", "weighted", "pagerank2"][i % 4]
         w = int(rng.integers(1, max_walkers))
-        spec = dict(starts=synth.random_starts(g.n, w, seed=seed * 100 + i), length=int(rng.integers(0, 30)),
+        spec = dict(starts=synth.random_starts(g.n, w, seed=seed * 100 + i), length=int(rng.integers(0, max_length)),
                     algo=algo, mode=["auto", "rjs", "rvs", "exact"][int(rng.integers(0, 4))],
                     seed=int(rng.integers(1, 1 << 40)), walker_base=int(rng.integers(0, 1000)))
         if algo == "node2vec":
@@ -185,6 +187,61 @@ def test_server_results_equal_alone_in_a_concurrent_mix(small):
     for sp, out in zip(specs, outs):
         alone = G.walk_host(sp["starts"], sp["length"], sp["algo"], **_kw(sp))
         assert np.array_equal(out, alone)
+
+
+def test_server_burst_merges_queries_into_overlapping_waves(small):
+    """A burst of 400 queries submitted in one call: waves merge several
+    queries (queries_per_wave > 1) and overlap on the device
+    (peak_inflight_waves > 1); every query's rows equal fw_walk_host's
+    alone, the batched poll releases every ticket once, and the device's hop
+    count equals the hops in the rows.  Queries of up to 40,000 walkers x
+    up to 90 hops keep each wave's device work longer than its launch."""
+    g, G = small
+    srv = fw.Server(G, mem_budget=2 << 30, max_waves=6, max_jobs_per_wave=32)
+    specs = _mixed_jobs(g, 400, seed=21, max_walkers=40000, max_length=90)
+    outs = [np.full((len(sp["starts"]), sp["length"] + 1), -7, dtype=np.int32) for sp in specs]
+    qs = (fw.fw_job * len(specs))(*[fw.make_host_query(sp["starts"], sp["length"], sp["algo"], o, **_kw(sp))
+                                     for sp, o in zip(specs, outs)])
+    tickets = srv.submit_many(qs)
+    assert len(set(tickets.tolist())) == len(specs)
+    pending = tickets.copy()
+    deadline = time.time() + 120.0
+    while len(pending) and time.time() < deadline:
+        done, lat, st = srv.poll_many(pending)
+        assert np.all(st[done == 1] == 0)
+        assert np.all(lat[done == 1] >= 0)
+        pending = pending[done == 0]
+    assert len(pending) == 0, "queries did not finish"
+    d2, _, st2 = srv.poll_many(tickets[:3])  # released tickets are unknown now
+    assert np.all(d2 == 1) and np.all(st2 == -1)
+    stats = srv.stats()
+    srv.close()
+    assert stats["completed"] == len(specs) and stats["failed"] == 0
+    assert stats["queries_per_wave"] > 1.0, stats
+    assert stats["peak_inflight_waves"] > 1, stats
+    hops = sum(int((o[:, 1:] >= 0).sum()) for o in outs)
+    assert stats["walker_steps"] == hops
+    for sp, out in zip(specs, outs):
+        assert np.array_equal(out, G.walk_host(sp["starts"], sp["length"], sp["algo"], **_kw(sp)))
+
+
+def test_server_submit_many_stops_at_the_first_bad_query(small):
+    g, G = small
+    srv = fw.Server(G, mem_budget=16 << 20, max_waves=2)
+    good = [np.arange(50, dtype=np.int32) for _ in range(3)]
+    bad = np.array([0, g.n], dtype=np.int32)
+    outs = [np.empty((50, 6), np.int32) for _ in range(3)] + [np.empty((2, 6), np.int32)]
+    qs = (fw.fw_job * 4)(*([fw.make_host_query(st, 5, "weighted", o) for st, o in zip(good[:2], outs[:2])] +
+                            [fw.make_host_query(bad, 5, "weighted", outs[3]),
+                             fw.make_host_query(good[2], 5, "weighted", outs[2])]))
+    tickets = np.zeros(4, dtype=np.uint64)
+    n = ctypes.c_int32()
+    st = fw.lib().fw_server_submit_many(srv.handle, ctypes.cast(qs, ctypes.c_void_p), 4, tickets.ctypes.data,
+                                        ctypes.byref(n))
+    assert st == -1 and n.value == 2 and b"query 2" in fw.lib().fw_last_error()
+    for t in tickets[:2]:
+        srv.wait(int(t), timeout=30.0)
+    srv.close()
 
 
 def test_server_errors_and_timeouts(small):
