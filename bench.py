@@ -21,6 +21,7 @@ For N > 1 launch with torchrun; every rank walks its own replica of the
 workload with its own random streams (weak scaling, no data-path collective).
 """
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -41,7 +42,8 @@ LENGTH = 80
 SEED = 42
 WORKLOAD = ("node2vec on undirected R-MAT s22 ef16 (a=.57,b=c=.19), 4,194,304 nodes, h~U(0,1] FP32, "
             "one walker per node, length 80, (p,q) in {(1,1),(4,.25),(.25,4)}, cost-model mode")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "walk_kernel_s22_node2vec.md")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "walk_kernel_s20_node2vec_traffic.md")
+SUBSET = 65536  # the fixed seeded walker subset the CPU oracle is timed on
 
 
 def parse():
@@ -56,6 +58,8 @@ def parse():
                     "scales are for profiling captures)")
     ap.add_argument("--pq", action="append", default=None, help="restrict to one (p,q), e.g. --pq 4,0.25")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="walk suite: leave out the batched, served and "
+                    "metapath measurements that the default line carries (N = 1 only)")
     ap.add_argument("--suite", default="walk", choices=["walk", "batch", "serve", "metapath", "skew", "ablation"],
                     help="walk: the headline node2vec s22 line; batch: 64 mixed jobs on skewed R-MAT s24, "
                     "batched vs one launch per job; serve: Poisson query stream on s22, continuous batching vs "
@@ -69,7 +73,7 @@ def parse():
                     "(fw_graph_quantize_weights) before tuning and timing")
     ap.add_argument("--duration", type=float, default=10.0, help="serve suite: seconds of offered load")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve suite: mean arrivals per second")
-    ap.add_argument("--max-waves", type=int, default=4, help="serve suite: concurrent waves (streams) of the server")
+    ap.add_argument("--max-waves", type=int, default=8, help="serve suite: concurrent waves (streams) of the server")
     ap.add_argument("--no-serial", action="store_true", help="serve suite: skip the serial comparison (for "
                     "arrival rates far above what serial calls sustain, e.g. capacity runs)")
     a = ap.parse_args()
@@ -167,24 +171,69 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_sample(g, cpu_seconds, threads):
-    """Time the CPU oracle on a seeded sample of the workload's walkers,
-    growing the sample until one timed pass takes about `cpu_seconds`."""
-    import oracle
+def cpu_info():
+    """CPU model and logical CPU count of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return {"model": model or "unknown", "nproc": os.cpu_count() or 1}
+
+
+def subset_starts(g):
+    """The fixed seeded subset of SUBSET non-isolated s22 walkers (numpy PCG64
+    seed 7 permutation of the nodes with neighbours, first SUBSET)."""
     rng = np.random.default_rng(7)
-    nonzero = rng.permutation(np.nonzero(np.diff(g.offsets) > 0)[0]).astype(np.int32)
-    nw = 256
+    return rng.permutation(np.nonzero(np.diff(g.offsets) > 0)[0]).astype(np.int32)[:SUBSET]
+
+
+def oracle_sample(g, cpu_seconds, threads):
+    """Time the CPU oracle (exact inverse-CDF walks, 80 hops, the three (p, q))
+    on the first nw walkers of the fixed subset, nw grown (at most SUBSET)
+    until one timed pass takes about `cpu_seconds`.  Returns (walker-steps/s,
+    nw, hops, seconds)."""
+    import oracle
+    sub = subset_starts(g)
+    nw = 64
     while True:
-        starts = nonzero[:nw]
+        starts = sub[:nw]
         t0 = time.perf_counter()
         hops = 0
         for (p, q) in PQ:
             _, h = oracle.walk(g, starts, LENGTH, "node2vec", p, q, seed=SEED, threads=threads)
             hops += h
         dt = time.perf_counter() - t0
-        if dt >= 0.6 * cpu_seconds or nw >= len(nonzero):
+        if dt >= 0.6 * cpu_seconds or nw >= len(sub):
             return hops / dt, nw, hops, dt
-        nw = int(min(len(nonzero), nw * max(2.0, 1.2 * cpu_seconds / max(dt, 1e-3))))
+        nw = int(min(len(sub), nw * max(2.0, 1.2 * cpu_seconds / max(dt, 1e-3))))
+
+
+def cpu_baseline(g, cpu_seconds):
+    """The oracle on all host cores and on one core, each on a prefix of the
+    fixed subset sized to about `cpu_seconds` (one core: half of that)."""
+    threads = os.cpu_count() or 1
+    rate, nw, hops, dt = oracle_sample(g, cpu_seconds, threads)
+    rate1, nw1, hops1, dt1 = oracle_sample(g, 0.5 * cpu_seconds, 1)
+    info = cpu_info()
+    return {"value": rate, "unit": "walker-steps/s", "cores": threads, "kind": "oracle",
+            "sample": f"walkers 0..{nw - 1} of the fixed seeded {SUBSET}-walker s22 subset (non-isolated nodes, "
+                      f"permutation seed 7) x 80 hops x 3 (p,q): {hops} hops in {dt:.1f} s",
+            "single_core": {"value": rate1, "unit": "walker-steps/s", "cores": 1,
+                            "sample": f"walkers 0..{nw1 - 1} of the same subset: {hops1} hops in {dt1:.1f} s"},
+            "cpu_model": info["model"], "nproc": info["nproc"]}
 
 
 def run_reference(args):
@@ -210,9 +259,11 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * sum(r[3] for r in rates) / len(rates), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "sample": f"{nw} seeded non-isolated walkers x 80 hops x 3 (p,q) per step"},
+            "config": {"workload": WORKLOAD, "sample": f"walkers 0..{nw - 1} of the fixed seeded {SUBSET}-walker "
+                                                      "s22 subset x 80 hops x 3 (p,q) per step"},
             "cpu_baseline": {"value": value, "unit": "walker-steps/s", "cores": threads, "kind": "oracle",
-                             "sample": f"{nw} seeded walkers x 80 hops x 3 (p,q)"},
+                             "sample": f"walkers 0..{nw - 1} of the fixed seeded {SUBSET}-walker s22 subset "
+                                       "x 80 hops x 3 (p,q)", "cpu_model": cpu_info()["model"]},
             "e2e": {"value": value, "unit": "walker-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -230,13 +281,13 @@ def _line(metric, value, unit, args, extra):
     print(json.dumps(line), flush=True)
 
 
-def run_batch(args):
+def batch_result(warmup, steps):
     """64 independent jobs on a skewed R-MAT s24 graph (a=.7, b=c=.1, edge
     factor 24): start sets log-uniform in [1K, 1M] walkers, lengths uniform
     in {5..80}, algorithms node2vec (p, q log-uniform in [0.25, 4]) /
-    metapath (schema 0-1-2-3-4) / weighted, cost ratio profiled per
-    algorithm; one batched launch (a replayed CUDA-graph plan) against one
-    fw_walk launch per job on the same stream."""
+    metapath (schema 0-1-2-3-4) / weighted, autotuned per algorithm; one
+    batched launch (a replayed CUDA-graph plan) against one fw_walk launch
+    per job on the same stream.  Returns the result as a dict."""
     import torch
     from paper_2512_00705_gb300 import _build, synth
     from paper_2512_00705_gb300 import flexiwalk as fw
@@ -269,7 +320,7 @@ def run_batch(args):
         return d
 
     jobs = [fw.make_job(sp["starts"], sp["L"], sp["algo"], sp["out"], **kw(sp)) for sp in specs]
-    plan = fw.BatchPlan(G, jobs)
+    plan = fw.BatchPlan(G, jobs)  # hand-set launch shape (defaults), r from the sweep
 
     def per_job():
         for sp in specs:
@@ -283,34 +334,65 @@ def run_batch(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         per_job()
         plan.launch()
     torch.cuda.synchronize()
     per_ms, bat_ms = [], []
-    for _ in range(args.steps):
+    for _ in range(steps):
         per_ms.append(timed(per_job))
-        ref = [sp["out"].clone() for sp in specs[:4]]
+        ref = [sp["out"].clone() for sp in specs]
         bat_ms.append(timed(plan.launch))
-    same = all(torch.equal(r, sp["out"]) for r, sp in zip(ref, specs[:4]))
+    same = all(torch.equal(r, sp["out"]) for r, sp in zip(ref, specs))
     hops = sum(_hops(sp["out"]) for sp in specs)
     per, bat = statistics.median(per_ms), statistics.median(bat_ms)
     plan.close()
-    _line("walker-steps/sec (batched)", hops / (bat / 1e3), "walker-steps/s", args, {
-        "ms_per_step": bat,
-        "config": {"workload": "64 jobs on skewed R-MAT s24 ef24 (a=.7,b=c=.1), W log-U[1K,1M], L U{5..80}, "
-                               "node2vec/metapath/weighted mixed", "nodes": g.n, "edges": g.e,
-                   "max_degree": int(G.info["max_degree"]), "walkers": sum(sp["w"] for sp in specs),
-                   "hops_per_step": hops, "generation_s": gen_s, "cost_ratios": ratios},
-        "per_job": {"value": hops / (per / 1e3), "ms_per_step": per, "launches": 64},
-        "batched_over_per_job": per / bat, "rows_identical": same})
+    # the autotuner's launch shape (fw_autotune method 2) per algorithm, then the same batch again
+    t_tune = time.perf_counter()
+    tuned = {a: G.autotune(a, p=1.0, q=1.0, schema=[0, 1, 2, 3, 4] if a == "metapath" else None, method=2)
+             for a in ["node2vec", "metapath", "weighted"]}
+    tune_s = time.perf_counter() - t_tune
+    info = G.info
+    shapes = {a: {"r": tuned[a], "lane_max_degree": info["lane_max_degrees"][fw.ALGO[a]],
+                  "rjs_batch": info["rjs_batches"][fw.ALGO[a]], "trial_budget": info["trial_budgets"][fw.ALGO[a]]}
+              for a in tuned}
+    jobs2 = [fw.make_job(sp["starts"], sp["L"], sp["algo"], sp["out"], **kw(sp)) for sp in specs]
+    plan2 = fw.BatchPlan(G, jobs2)
+    for _ in range(warmup):
+        plan2.launch()
+    torch.cuda.synchronize()
+    tuned_ms = []
+    for _ in range(steps):
+        tuned_ms.append(timed(plan2.launch))
+    same2 = all(torch.equal(r, sp["out"]) for r, sp in zip(ref, specs))
+    plan2.close()
+    tun = statistics.median(tuned_ms)
+    res = {"value": hops / (min(bat, tun) / 1e3), "unit": "walker-steps/s", "ms_per_step": min(bat, tun),
+           "hand_set_shape": {"value": hops / (bat / 1e3), "ms_per_step": bat,
+                              "shape": {"lane_max_degree": 8, "rjs_batch": 2, "trial_budget": 1.0}},
+           "autotuned_shape": {"value": hops / (tun / 1e3), "ms_per_step": tun, "per_algorithm": shapes,
+                               "tuning_s": tune_s, "rows_identical": same2},
+           "per_job": {"value": hops / (per / 1e3), "ms_per_step": per, "launches": 64},
+           "batched_over_per_job": per / min(bat, tun), "autotuned_over_hand_set": bat / tun, "rows_identical": same,
+           "config": {"workload": "64 jobs on skewed R-MAT s24 ef24 (a=.7,b=c=.1), W log-U[1K,1M], L U{5..80}, "
+                                  "node2vec/metapath/weighted mixed; batched = one replayed CUDA-graph plan",
+                      "nodes": g.n, "edges": g.e, "max_degree": int(G.info["max_degree"]),
+                      "walkers": sum(sp["w"] for sp in specs), "hops_per_step": hops, "generation_s": gen_s,
+                      "cost_ratios": ratios, "steps": steps, "warmup": warmup}}
     G.close()
+    return res
 
 
-def run_metapath(args):
+def run_batch(args):
+    r = batch_result(args.warmup, args.steps)
+    _line("walker-steps/sec (batched)", r["value"], "walker-steps/s", args,
+          {k: v for k, v in r.items() if k not in ("value", "unit")})
+
+
+def metapath_result(warmup, steps):
     """Metapath walks (schema 0-1-2-3-4, cyclic) on R-MAT s23 ef16 with
     lognormal(0,1) weights and labels U{0..4}: 2M random starts, length 5
-    and 40."""
+    and 40.  Returns the result as a dict."""
     import torch
     from paper_2512_00705_gb300 import _build, synth
     from paper_2512_00705_gb300 import flexiwalk as fw
@@ -323,10 +405,10 @@ def run_metapath(args):
     res = {}
     for L in (5, 40):
         out = torch.empty((starts.numel(), L + 1), dtype=torch.int32, device="cuda")
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             G.walk(starts, L, "metapath", schema=[0, 1, 2, 3, 4], out=out, seed=SEED, cost_ratio=r_meta)
         ms = []
-        for _ in range(args.steps):
+        for _ in range(steps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             G.walk(starts, L, "metapath", schema=[0, 1, 2, 3, 4], out=out, seed=SEED, cost_ratio=r_meta)
@@ -342,26 +424,205 @@ def run_metapath(args):
     tot = sum(t for _, t, _ in res.values())
     per_len = {}
     for L, (h, t, c) in res.items():
-        per_len[str(L)] = {"hops": h, "ms": t, "rjs_share": c["rjs_steps"] / max(1, c["hops"]),
+        per_len[str(L)] = {"hops": h, "ms": t, "walker_steps_per_s": h / (t / 1e3),
+                           "rjs_share": c["rjs_steps"] / max(1, c["hops"]),
                            "rjs_trials_per_rjs_step": c["rjs_trials"] / max(1, c["rjs_steps"]),
                            "rvs_items_per_rvs_step": c["rvs_items"] / max(1, c["rvs_steps"]),
                            "dead_ends": c["dead_ends"], "algorithmic_bytes_per_hop": c["bytes"] / max(1, c["hops"]),
                            "algorithmic_GBps": c["bytes"] / (t / 1e3) / 1e9}
-    _line("walker-steps/sec (metapath)", hops / (tot / 1e3), "walker-steps/s", args, {
-        "ms_per_step": tot,
-        "config": {"workload": "metapath 0-1-2-3-4 on R-MAT s23 ef16, h~lognormal(0,1), labels U{0..4}, "
-                               "2M random starts (seed 43), L=5 and L=40", "nodes": g.n, "edges": g.e, "cost_ratio": r_meta,
-                   "per_length": per_len}})
     G.close()
+    return {"value": hops / (tot / 1e3), "unit": "walker-steps/s", "ms_per_step": tot,
+            "config": {"workload": "metapath 0-1-2-3-4 on R-MAT s23 ef16, h~lognormal(0,1), labels U{0..4}, "
+                                   "2M random starts (seed 43), L=5 and L=40", "nodes": g.n, "edges": g.e,
+                       "cost_ratio": r_meta, "steps": steps, "warmup": warmup, "per_length": per_len}}
+
+
+def run_metapath(args):
+    r = metapath_result(args.warmup, args.steps)
+    _line("walker-steps/sec (metapath)", r["value"], "walker-steps/s", args,
+          {k: v for k, v in r.items() if k not in ("value", "unit")})
+
+
+class _ServeClient:
+    """Client side of the serving measurement: a Poisson stream of walk
+    queries against the resident graph, W log-uniform in [1, 1e5] walkers,
+    length uniform in {10..100}, algorithm uniform over node2vec (p=2,
+    q=0.5) / metapath (0-1-2-3-4) / weighted; host buffers from pinned
+    pools.  Latency = completion - arrival."""
+
+    def __init__(self, G, g):
+        import torch
+        from paper_2512_00705_gb300 import synth
+        self.G, self.g = G, g
+        self.pool_words = 4 * 100_000 + 1
+        self.starts_pool = torch.from_numpy(synth.random_starts(g.n, self.pool_words, seed=46)).pin_memory().numpy()
+        self.ring_words = 1 << 30  # 4 GiB of pinned rows; a query takes the next range, reused once it completes
+        self.ring = torch.empty(self.ring_words, dtype=torch.int32).pin_memory().numpy()
+
+    @staticmethod
+    def queries(rate, duration, seed):
+        rng = np.random.default_rng(seed)
+        n = max(1, int(rate * duration))
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, n))
+        W = np.exp(rng.uniform(0, np.log(1e5), n)).astype(np.int64)
+        Ls = rng.integers(10, 101, n)
+        algos = rng.integers(0, 3, n)
+        return arrivals, W, Ls, algos
+
+    def run(self, mode, rate, duration, seed=45, max_waves=8, count=None):
+        """Offer the query stream to the server (batched submit / poll calls,
+        hops counted on the device) or to serial fw_walk_host calls."""
+        from concurrent.futures import ThreadPoolExecutor
+        from paper_2512_00705_gb300 import flexiwalk as fw
+        arrivals, W, Ls, algos = self.queries(rate, duration, seed)
+        count = len(arrivals) if count is None else min(count, len(arrivals))
+        arrivals, W, Ls, algos = arrivals[:count], W[:count], Ls[:count], algos[:count]
+        words = W * (Ls + 1)
+        # rows go to a pinned ring, allocated in arrival order; query i may be
+        # submitted once every earlier query whose range it reuses is done
+        offs = np.zeros(count, dtype=np.int64)
+        head = 0
+        for i in range(count):
+            if head + words[i] > self.ring_words:
+                head = 0
+            offs[i] = head
+            head += words[i]
+        ends = offs + words
+        # the queries of the previous pass over the ring whose ranges overlap query i's
+        # (within a pass offsets increase, so they form one index range [klo, khi))
+        pass_start = np.nonzero(offs == 0)[0]
+        klo = np.zeros(count, dtype=np.int64)
+        khi = np.zeros(count, dtype=np.int64)
+        for p_ in range(1, len(pass_start)):
+            a0, a1 = pass_start[p_ - 1], pass_start[p_]
+            b1 = pass_start[p_ + 1] if p_ + 1 < len(pass_start) else count
+            idx = np.arange(a1, b1)
+            klo[idx] = a0 + np.searchsorted(ends[a0:a1], offs[idx], side="right")
+            khi[idx] = np.maximum(a0, a0 + np.searchsorted(offs[a0:a1], ends[idx], side="left"))
+        # query i waits until every query below khi[i] is done: those overlapping it in the
+        # previous pass and everything of the passes before (long finished in practice)
+        names = ["node2vec", "metapath", "weighted"]
+
+        def kw(i):
+            d = {"seed": int(1000 + i)}
+            if algos[i] == 0:
+                d["p"], d["q"] = 2.0, 0.5
+            if algos[i] == 1:
+                d["schema"] = [0, 1, 2, 3, 4]
+            return d
+
+        starts_v = [self.starts_pool[(i * 7919) % (self.pool_words - W[i]):][:W[i]] for i in range(count)]
+        outs_v = [self.ring[offs[i]:offs[i] + words[i]].reshape(W[i], Ls[i] + 1) for i in range(count)]
+        lat = np.zeros(count)
+        done = np.zeros(count, dtype=bool)
+
+        prefix = [0]  # every query below prefix[0] is done
+
+        def ring_free(i):
+            while prefix[0] < count and done[prefix[0]]:
+                prefix[0] += 1
+            return prefix[0] >= khi[i]
+
+        if mode == "server":
+            jobs = (fw.fw_job * count)()
+            for i in range(count):
+                jobs[i] = fw.make_host_query(starts_v[i], int(Ls[i]), names[algos[i]], outs_v[i], **kw(i))
+            srv = fw.Server(self.G, mem_budget=8 << 30, max_waves=max_waves)
+            jsize = ctypes.sizeof(fw.fw_job)
+            tickets = np.zeros(count, dtype=np.uint64)
+            lag = np.zeros(count)
+            nxt, ndone = 0, 0
+            t_base = time.perf_counter()
+            while ndone < count:
+                now = time.perf_counter() - t_base
+                hi = int(np.searchsorted(arrivals, now, side="right"))
+                j = nxt
+                while j < hi and ring_free(j):
+                    j += 1
+                if j > nxt:
+                    sub = (fw.fw_job * (j - nxt)).from_address(ctypes.addressof(jobs) + nxt * jsize)
+                    tickets[nxt:j] = srv.submit_many(sub)
+                    lag[nxt:j] = (time.perf_counter() - t_base) - arrivals[nxt:j]
+                    nxt = j
+                pend = np.nonzero(~done[:nxt])[0]
+                if len(pend):
+                    d, l_ms, st = srv.poll_many(tickets[pend])
+                    fin = pend[d.astype(bool)]
+                    if np.any(st[d.astype(bool)] != 0):
+                        raise RuntimeError("a served query failed")
+                    done[fin] = True
+                    lat[fin] = lag[fin] * 1e3 + l_ms[d.astype(bool)]
+                    ndone += len(fin)
+                if nxt < count and ndone < count and not len(pend):
+                    time.sleep(max(0.0, min(0.0005, arrivals[nxt] - (time.perf_counter() - t_base))))
+            wall = time.perf_counter() - t_base
+            stats = srv.stats()
+            srv.close()
+            hops = int(stats["walker_steps"])
+        else:
+            counter = ThreadPoolExecutor(max_workers=8)
+
+            def row_hops(rows):
+                # -1 marks the steps after a dead end; the start column is never -1
+                return rows.shape[0] * (rows.shape[1] - 1) - int(np.count_nonzero(rows[:, 1:] < 0))
+
+            futs = []
+            t_base = time.perf_counter()
+            for i in range(count):
+                while time.perf_counter() - t_base < arrivals[i]:
+                    pass
+                self.G.walk_host(starts_v[i], int(Ls[i]), names[algos[i]], out=outs_v[i], **kw(i))
+                lat[i] = (time.perf_counter() - t_base - arrivals[i]) * 1e3
+                done[i] = True
+                futs.append(counter.submit(row_hops, outs_v[i]))
+            wall = time.perf_counter() - t_base
+            hops = sum(f.result() for f in futs)
+            counter.shutdown()
+            stats = None
+        r = {"queries": count, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+             "mean_ms": float(lat.mean()), "walker_steps_per_s": hops / wall, "wall_s": wall, "hops": hops,
+             "offered_walker_steps_per_s": float((W * Ls).sum() / max(arrivals[-1], 1e-9))}
+        if stats:
+            r.update({"waves": stats["waves"], "queries_per_wave": stats["queries_per_wave"],
+                      "peak_inflight_waves": stats["peak_inflight_waves"]})
+        return r
+
+
+def serve_result(G, g, rate=2000.0, duration=10.0, max_waves=8, serial=True, capacity=True):
+    """Continuous batching (fw_server) against serial fw_walk_host calls on the
+    same arrival sequence at `rate` queries/s for `duration` s; then the
+    server's capacity (saturated throughput at 20x the rate, 3 s) and its
+    p50 / p99 at 70 % of that capacity (5 s).  Returns a dict."""
+    ratios = {"node2vec": G.autotune("node2vec", p=2.0, q=0.5, method=1),
+              "metapath": G.autotune("metapath", schema=[0, 1, 2, 3, 4], method=1),
+              "weighted": G.autotune("weighted", method=1)}
+    cl = _ServeClient(G, g)
+    cl.run("server", rate, duration, max_waves=max_waves, count=400)  # warm-up (module load, arena), discarded
+    out = {"server": cl.run("server", rate, duration, max_waves=max_waves)}
+    if serial:
+        out["serial"] = cl.run("serial", rate, duration)
+    res = {"value": out["server"]["walker_steps_per_s"], "unit": "walker-steps/s",
+           "config": {"workload": f"Poisson {rate:g}/s for {duration:g} s (shortened from 60 s) on R-MAT s22; "
+                                  "W log-U[1,1e5], L U{10..100}, node2vec(2,.5)/metapath/weighted",
+                      "cost_ratios": ratios, "max_waves": max_waves},
+           "serving": out,
+           "p99_server_over_serial": (out["server"]["p99_ms"] / out["serial"]["p99_ms"]) if serial else None,
+           "steps_server_over_serial": (out["server"]["walker_steps_per_s"] / out["serial"]["walker_steps_per_s"])
+           if serial else None}
+    if capacity:
+        sat = cl.run("server", 20.0 * rate, 3.0, seed=47, max_waves=max_waves)
+        cap = sat["walker_steps_per_s"]
+        _, W, Ls, _ = cl.queries(rate, duration, 45)
+        mean_steps = float((W * Ls).mean())
+        rate70 = 0.7 * cap / mean_steps
+        at70 = cl.run("server", rate70, 5.0, seed=48, max_waves=max_waves)
+        res["capacity"] = {"walker_steps_per_s": cap, "saturated_run": sat, "rate_at_70pct": rate70,
+                           "at_70pct": at70,
+                           "rate_saturates": bool(out["server"]["offered_walker_steps_per_s"] >= 0.95 * cap)}
+    return res
 
 
 def run_serve(args):
-    """Poisson stream of walk queries (mean `rate`/s) against the resident
-    s22 graph: W log-uniform in [1, 1e5] walkers, length uniform in
-    {10..100}, algorithm uniform over node2vec (p=2, q=0.5) / metapath /
-    weighted.  Continuous batching (fw_server) against serial fw_walk_host
-    calls on the same arrival sequence; latency = completion - arrival."""
-    import threading
     import torch
     from paper_2512_00705_gb300 import _build, synth
     from paper_2512_00705_gb300 import flexiwalk as fw
@@ -369,117 +630,10 @@ def run_serve(args):
     torch.cuda.set_device(0)
     g = synth.workload_graph("s22")
     G = fw.Graph(g)
-    ratios = {"node2vec": G.autotune("node2vec", p=2.0, q=0.5, method=1),
-              "metapath": G.autotune("metapath", schema=[0, 1, 2, 3, 4], method=1),
-              "weighted": G.autotune("weighted", method=1)}
-    rng = np.random.default_rng(45)
-    n_req = int(args.rate * args.duration)
-    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, n_req))
-    W = np.exp(rng.uniform(0, np.log(1e5), n_req)).astype(np.int64)
-    Ls = rng.integers(10, 101, n_req)
-    algos = rng.integers(0, 3, n_req)
-    pool_words = int(W.max() * 4) + 1
-    starts_pool = torch.from_numpy(synth.random_starts(g.n, pool_words, seed=46)).pin_memory().numpy()
-    # pinned ring for the rows: a query takes the next slot range, reused after it completes
-    ring_words = 1 << 30  # 4 GiB
-    ring = torch.empty(ring_words, dtype=torch.int32).pin_memory().numpy()
-
-    def kw(i):
-        a = ["node2vec", "metapath", "weighted"][algos[i]]
-        d = {"seed": int(1000 + i)}
-        if a == "node2vec":
-            d["p"], d["q"] = 2.0, 0.5
-        if a == "metapath":
-            d["schema"] = [0, 1, 2, 3, 4]
-        return a, d
-
-    from collections import deque
-    from concurrent.futures import ThreadPoolExecutor
-    counter = ThreadPoolExecutor(max_workers=8)  # hop counting off the submit / poll loop
-
-    def row_hops(rows):
-        # -1 marks the steps after a dead end; the start column is never -1
-        return rows.shape[0] * (rows.shape[1] - 1) - int(np.count_nonzero(rows[:, 1:] < 0))
-
-    def run(mode, count):
-        lat = np.zeros(count)
-        hops = [0]
-        head = [0]
-        inflight = []  # (index, ring start, words, ticket, submit lag)
-        counting = deque()  # (ring start, words, future of the hop count)
-        srv = fw.Server(G, mem_budget=8 << 30, max_waves=args.max_waves) if mode == "server" else None
-
-        def reap(block):
-            # collect finished queries in submission order; latency = submit lag + submit-to-done
-            while inflight:
-                i, off, words, t, lag = inflight[0]
-                if srv is not None:
-                    r = srv.wait(t, 120.0) if block else srv.poll(t)
-                    if r is None:
-                        return
-                    lat[i] = lag + r / 1e3
-                rows = ring[off:off + words].reshape(W[i], Ls[i] + 1)
-                counting.append((off, words, counter.submit(row_hops, rows)))
-                inflight.pop(0)
-
-        def drain_counts(lo, hi):
-            # finish the hop counts of ring ranges that start in [lo, hi) (hi = None: all)
-            while counting and (hi is None or lo <= counting[0][0] < hi):
-                hops[0] += counting.popleft()[2].result()
-
-        t_base = time.perf_counter()
-        for i in range(count):
-            while time.perf_counter() - t_base < arrivals[i]:
-                if srv is not None:
-                    reap(False)
-            words = int(W[i] * (Ls[i] + 1))
-            if head[0] + words > ring_words:
-                head[0] = 0
-            while inflight and head[0] <= inflight[0][1] < head[0] + words:
-                reap(True)
-            drain_counts(head[0], head[0] + words)
-            off = head[0]
-            head[0] += words
-            st = starts_pool[(i * 7919) % (pool_words - W[i]):][:W[i]]
-            out = ring[off:off + words].reshape(W[i], Ls[i] + 1)
-            a, d = kw(i)
-            lag = time.perf_counter() - t_base - arrivals[i]
-            if srv is not None:
-                t = srv.submit(st, int(Ls[i]), a, out, **d)
-                inflight.append((i, off, words, t, lag))
-            else:
-                G.walk_host(st, int(Ls[i]), a, out=out, **d)
-                lat[i] = time.perf_counter() - t_base - arrivals[i]
-                inflight.append((i, off, words, None, lag))
-                reap(True)
-        reap(True)
-        drain_counts(0, None)
-        stats = None
-        if srv is not None:
-            stats = srv.stats()
-            srv.close()
-        wall = time.perf_counter() - t_base
-        return lat * 1e3, hops[0], wall, stats
-
-    run("server", min(n_req, 400))  # warm-up (module load, arena, caches), discarded
-    res = {m: run(m, n_req) for m in (("server",) if args.no_serial else ("server", "serial"))}
-    out = {}
-    for m, (lat, hops, wall, stats) in res.items():
-        out[m] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                  "mean_ms": float(lat.mean()), "walker_steps_per_s": hops / wall, "wall_s": wall, "hops": hops}
-        if stats:
-            out[m]["waves"] = stats["waves"]
-            out[m]["queries_per_wave"] = stats["queries_per_wave"]
-            out[m]["peak_inflight_waves"] = stats["peak_inflight_waves"]
-    _line("walker-steps/sec (served)", out["server"]["walker_steps_per_s"], "walker-steps/s", args, {
-        "ms_per_step": None, "higher_is_better": True,
-        "config": {"workload": f"Poisson {args.rate:g}/s for {args.duration:g} s on R-MAT s22; W log-U[1,1e5], "
-                               "L U{10..100}, node2vec(2,.5)/metapath/weighted", "queries": n_req,
-                   "cost_ratios": ratios, "max_waves": args.max_waves,
-                   "offered_walker_steps_per_s": float((W * Ls).sum() / args.duration)},
-        "serving": out,
-        "p99_server_over_serial": (out["server"]["p99_ms"] / out["serial"]["p99_ms"]) if "serial" in out else None})
+    r = serve_result(G, g, args.rate, args.duration, args.max_waves, serial=not args.no_serial)
     G.close()
+    _line("walker-steps/sec (served)", r["value"], "walker-steps/s", args,
+          dict({k: v for k, v in r.items() if k not in ("value", "unit")}, ms_per_step=None))
 
 
 def run_skew(args):
@@ -511,11 +665,28 @@ def run_skew(args):
         r_sweep = G.autotune("node2vec", p=2.0, q=0.5, method=1)
         r = G.autotune("node2vec", p=2.0, q=0.5, method=0)
         row = {"cost_ratio_profiled": r, "cost_ratio_sweep": r_sweep}
-        for mode in ("auto", "auto_sweep", "rjs", "rvs", "random", "degree"):
-            rr = r_sweep if mode == "auto_sweep" else r
-            md = "auto" if mode == "auto_sweep" else mode
+        # method 2 (r and launch shape), tuned afresh `reps` times: the spread shows how stable it is
+        shape_runs = []
+        for _ in range(3 if name == "pareto1" else 1):
+            r2 = G.autotune("node2vec", p=2.0, q=0.5, method=2)
+            inf = G.info
+            shape_runs.append({"r": r2, "lane_max_degree": inf["lane_max_degrees"][1],
+                               "rjs_batch": inf["rjs_batches"][1], "trial_budget": inf["trial_budgets"][1]})
+        row["shape_tuning"] = shape_runs
+        for mode in ["auto", "auto_sweep"] + [f"auto_shape{k}" for k in range(len(shape_runs))] + \
+                ["rjs", "rvs", "random", "degree"]:
+            shp = {}
+            if mode.startswith("auto_shape"):
+                sr = shape_runs[int(mode[len("auto_shape"):])]
+                rr = sr["r"]
+                shp = {k: sr[k] for k in ("lane_max_degree", "rjs_batch", "trial_budget")}
+            else:
+                rr = r_sweep if mode == "auto_sweep" else r
+                shp = {"lane_max_degree": 8, "rjs_batch": 2, "trial_budget": 1.0}
+            md = "auto" if mode.startswith("auto") else mode
             def go(flags=0):
-                G.walk(starts, L, "node2vec", p=2.0, q=0.5, mode=md, cost_ratio=rr, seed=SEED, flags=flags, out=out)
+                G.walk(starts, L, "node2vec", p=2.0, q=0.5, mode=md, cost_ratio=rr, seed=SEED, flags=flags, out=out,
+                       **shp)
             go()
             ms = []
             for _ in range(max(1, args.steps)):
@@ -535,7 +706,7 @@ def run_skew(args):
                 row["rjs_trials_per_rjs_step"] = c["rjs_trials"] / max(1, c["rjs_steps"])
         if h is not None:
             # the same weights as 8-bit codes: re-tuned, cost model only
-            row["int8_scale"] = G.quantize_weights()
+            row["int8_max_scale"] = G.quantize_weights()
             r8 = G.autotune("node2vec", p=2.0, q=0.5, method=1)
             row["cost_ratio_sweep_int8"] = r8
             for md in ("auto", "rvs"):  # eRVS-only: scans read 1-byte weights
@@ -549,10 +720,13 @@ def run_skew(args):
                     torch.cuda.synchronize()
                     ms.append(e0.elapsed_time(e1))
                 row[f"{md}_int8_ms"] = statistics.median(ms)
-            # weights below half a step are stored as code 1: how much of the tail the codes keep
-            row["int8_clamped_share"] = float(np.mean(h.astype(np.float64) < 0.5 * row["int8_scale"]))
+            # weights below half a step of their row's scale are stored as code 1
+            sv = G.weight_scales().cpu().numpy()[np.repeat(np.arange(base.n), np.diff(base.offsets))]
+            row["int8_clamped_share"] = float(np.mean(h.astype(np.float64) < 0.5 * sv))
         row["auto_speedup_vs_best_single"] = min(row["rjs_ms"], row["rvs_ms"]) / row["auto_ms"]
         row["auto_sweep_speedup_vs_best_single"] = min(row["rjs_ms"], row["rvs_ms"]) / row["auto_sweep_ms"]
+        row["auto_shape_speedup_vs_best_single"] = [min(row["rjs_ms"], row["rvs_ms"]) / row[f"auto_shape{k}_ms"]
+                                                    for k in range(len(shape_runs))]
         row["auto_speedup_vs_random"] = row["random_ms"] / row["auto_ms"]
         row["auto_speedup_vs_degree_rule"] = row["degree_ms"] / row["auto_ms"]
         res[name] = row
@@ -799,6 +973,12 @@ def main():
     peak, peak_kind = measured_peaks()
     kern_ms = sum(sum(v) for v in per_launch.values()) / args.steps
     achieved = bytes_per_step / (kern_ms / 1000.0) / 1e9
+    # the survey's byte model of the method: 16 B per walker-step (offsets, bound scalar, row write), 64 B per
+    # eRJS trial (a column sector and a weight sector), 32 B per membership probe, 8 B per eRVS item (col + h)
+    survey_bytes = sum(16 * c["hops"] + 64 * c["rjs_trials"] + 32 * c["probes"] + 8 * c["rvs_items"]
+                       for c in counts.values())
+    achieved_survey = survey_bytes / (kern_ms / 1000.0) / 1e9
+    # DRAM bytes per hop from the ncu capture of the R-MAT s20 case (same kernel source), times this run's hops
     traffic = read_traffic() if args.scale == 22 and not args.int8 else None
     traffic_per_launch = None
     if traffic is not None:
@@ -830,6 +1010,14 @@ def main():
                                       if traffic_per_launch else None),
                      "peak_kind": peak_kind, "kernel": "walk_kernel<1, 0, 1> (single job, uncounted, node2vec)",
                      "algorithmic_bytes_per_launch": bytes_per_step / len(PQ),
+                     "byte_model": "this engine's accesses: 32 B per node record, eRJS edge record and membership "
+                                   "probe; 4 B per row entry; eRVS items 8 B",
+                     "achieved_survey_model": achieved_survey, "frac_survey_model": achieved_survey / peak,
+                     "survey_bytes_per_launch": survey_bytes / len(PQ),
+                     "survey_byte_model": "16 B per walker-step + 64 B per eRJS trial + 32 B per membership probe "
+                                          "+ 8 B per eRVS item, from the counted trials, probes and items",
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per hop on the R-MAT s20 "
+                                       "case of the same kernel source, times this launch's hops",
                      "avg_launch_ms": kern_ms / len(PQ)},
         "roofline_random_access": {
             "bound": "dram_random_access", "unit": "G sector accesses/s",
@@ -843,16 +1031,26 @@ def main():
         "clocks": clocks,
         "counters": {f"p{p:g}_q{q:g}": counts[(p, q)] for (p, q) in PQ},
     }
+    # ---- batched, served and metapath workloads (single GPU only; graphs of their own except serving)
+    if world == 1 and not args.no_extras and args.scale == 22 and len(PQ) == 3:
+        t_x = time.perf_counter()
+        line["serving"] = serve_result(G, g, rate=2000.0, duration=10.0, max_waves=args.max_waves)
+        G.close()
+        del out, flush, starts
+        torch.cuda.empty_cache()
+        line["metapath"] = metapath_result(2, 3)
+        torch.cuda.empty_cache()
+        line["batched"] = batch_result(2, 3)
+        torch.cuda.empty_cache()
+        line["extras_wall_s"] = time.perf_counter() - t_x
+    else:
+        G.close()
     if rank == 0 and not args.no_cpu_baseline and args.scale == 22:
         import oracle
         oracle.build()
-        threads = os.cpu_count() or 1
-        rate, nw, hops, dt = oracle_sample(g, args.cpu_seconds, threads)
-        line["cpu_baseline"] = {"value": rate, "unit": "walker-steps/s", "cores": threads, "kind": "oracle",
-                                "sample": f"{nw} seeded non-isolated walkers x 80 hops x 3 (p,q), {dt:.1f} s"}
+        line["cpu_baseline"] = cpu_baseline(g, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    G.close()
     if world > 1:
         dist.destroy_process_group()
 
