@@ -69,6 +69,9 @@ def parse():
                     "cost model vs eRJS-only / eRVS-only")
     ap.add_argument("--cost-ratio", type=float, default=None, help="walk suite: use this r of Eq. (runtime) for "
                     "every (p,q) instead of tuning it (profiling captures)")
+    ap.add_argument("--mode", default="auto", choices=["auto", "rjs", "rvs", "exact"],
+                    help="walk suite: sampler mode (auto = the cost model; the others force one sampler, for "
+                    "profiling captures)")
     ap.add_argument("--int8", action="store_true", help="walk suite: store the weights as 8-bit codes "
                     "(fw_graph_quantize_weights) before tuning and timing")
     ap.add_argument("--duration", type=float, default=10.0, help="serve suite: seconds of offered load")
@@ -588,6 +591,41 @@ class _ServeClient:
         return r
 
 
+def _device_rate(G, cl, rate, duration, seed, count=2048):
+    """The first `count` queries of a served stream walked straight from
+    device memory as plain batches (fw_walk_batch, 64 queries per launch
+    group, one stream, no host copies, no server): what the GPU does with this
+    mix of queries when nothing but the walks runs."""
+    import torch
+    from paper_2512_00705_gb300 import flexiwalk as fw
+    arrivals, W, Ls, algos = cl.queries(rate, duration, seed)
+    count = min(count, len(arrivals))
+    names = ["node2vec", "metapath", "weighted"]
+    pool = torch.from_numpy(np.ascontiguousarray(cl.starts_pool)).cuda()
+    jobs, outs = [], []
+    for i in range(count):
+        off = (i * 7919) % (cl.pool_words - W[i])
+        st = pool[off:off + W[i]]
+        out = torch.empty((int(W[i]), int(Ls[i]) + 1), dtype=torch.int32, device="cuda")
+        d = {"seed": int(1000 + i)}
+        if algos[i] == 0:
+            d["p"], d["q"] = 2.0, 0.5
+        if algos[i] == 1:
+            d["schema"] = [0, 1, 2, 3, 4]
+        jobs.append(fw.make_job(st, int(Ls[i]), names[algos[i]], out, **d))
+        outs.append(out)
+    fw.fw_walk_batch(G.handle, jobs)  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    fw.fw_walk_batch(G.handle, jobs)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    hops = sum(_hops(o) for o in outs)
+    return {"walker_steps_per_s": hops / (ms / 1e3), "queries": count, "hops": hops, "ms": ms}
+
+
 def serve_result(G, g, rate=2000.0, duration=10.0, max_waves=8, serial=True, capacity=True):
     """Continuous batching (fw_server) against serial fw_walk_host calls on the
     same arrival sequence at `rate` queries/s for `duration` s; then the
@@ -612,11 +650,14 @@ def serve_result(G, g, rate=2000.0, duration=10.0, max_waves=8, serial=True, cap
     if capacity:
         sat = cl.run("server", 20.0 * rate, 3.0, seed=47, max_waves=max_waves)
         cap = sat["walker_steps_per_s"]
+        res["device_rate_same_queries"] = _device_rate(G, cl, 20.0 * rate, 3.0, 47)
         _, W, Ls, _ = cl.queries(rate, duration, 45)
         mean_steps = float((W * Ls).mean())
         rate70 = 0.7 * cap / mean_steps
         at70 = cl.run("server", rate70, 5.0, seed=48, max_waves=max_waves)
-        res["capacity"] = {"walker_steps_per_s": cap, "saturated_run": sat, "rate_at_70pct": rate70,
+        res["capacity"] = {"walker_steps_per_s": cap, "saturated_run": sat,
+                           "over_device_rate": cap / res["device_rate_same_queries"]["walker_steps_per_s"],
+                           "rate_at_70pct": rate70,
                            "at_70pct": at70,
                            "rate_saturates": bool(out["server"]["offered_walker_steps_per_s"] >= 0.95 * cap)}
     return res
@@ -874,10 +915,10 @@ def main():
     def walk(p, q, flags=0):
         r = ratio[(p, q)]
         if wids is None:
-            G.walk(starts, LENGTH, "node2vec", p=p, q=q, mode="auto", seed=SEED, flags=flags, cost_ratio=r, out=out)
+            G.walk(starts, LENGTH, "node2vec", p=p, q=q, mode=args.mode, seed=SEED, flags=flags, cost_ratio=r, out=out)
         else:
-            G.walk_ids(starts, wids, LENGTH, "node2vec", p=p, q=q, mode="auto", seed=SEED, flags=flags, cost_ratio=r,
-                       out=out)
+            G.walk_ids(starts, wids, LENGTH, "node2vec", p=p, q=q, mode=args.mode, seed=SEED, flags=flags,
+                       cost_ratio=r, out=out)
 
     # counted run: hops and algorithmic bytes per launch (untimed)
     counts = {}
@@ -938,7 +979,7 @@ def main():
 
     # ---- e2e through the host-buffer entry point (pinned buffers)
     e2e_line = None
-    if not args.no_e2e:
+    if not args.no_e2e and args.mode == "auto":
         starts_h = starts.cpu().pin_memory()
         out_h = torch.empty((nw, LENGTH + 1), dtype=torch.int32).pin_memory()
         e2e_ms = []
@@ -988,8 +1029,8 @@ def main():
         "metric": "walker-steps/sec", "value": value, "unit": "walker-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": (WORKLOAD if args.scale == 22 and len(PQ) == 3 else
-                                f"node2vec R-MAT s{args.scale} ef16 (profiling case), (p,q)={PQ}")
+        "config": {"workload": (WORKLOAD if args.scale == 22 and len(PQ) == 3 and args.mode == "auto" else
+                                f"node2vec R-MAT s{args.scale} ef16 (profiling case), (p,q)={PQ}, mode {args.mode}")
                    + ("; weights stored as 8-bit codes x FP32 scale" if args.int8 else ""), "walkers": n * world,
                    "walkers_per_gpu": nw, "sharding": "replicas of the workload hashed by start node" if world > 1
                    else "none", "walk_length": LENGTH, "edges": g.e,
@@ -1032,7 +1073,7 @@ def main():
         "counters": {f"p{p:g}_q{q:g}": counts[(p, q)] for (p, q) in PQ},
     }
     # ---- batched, served and metapath workloads (single GPU only; graphs of their own except serving)
-    if world == 1 and not args.no_extras and args.scale == 22 and len(PQ) == 3:
+    if world == 1 and not args.no_extras and args.scale == 22 and len(PQ) == 3 and args.mode == "auto":
         t_x = time.perf_counter()
         line["serving"] = serve_result(G, g, rate=2000.0, duration=10.0, max_waves=args.max_waves)
         G.close()

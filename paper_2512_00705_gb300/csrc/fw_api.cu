@@ -123,7 +123,7 @@ fw_status make_job(const fw_graph* g, int32_t algo, const fw_params* params, uin
 // device has no room for it, metapath walks keep the full-row path.
 static fw_status build_label_groups(fw_graph* g, cudaStream_t st) {
   const size_t lrec_bytes = 2 * sizeof(int4) * kLabelStats * ((size_t)g->n + 1);
-  const size_t gerec_bytes = 2 * sizeof(int4) * (size_t)g->e, gh_bytes = sizeof(float) * ((size_t)g->e + kScanPad);
+  const size_t gerec_bytes = 2 * sizeof(int4) * (size_t)g->e, gh_bytes = sizeof(float) * (size_t)g->e;
   if (!g->d_lrec) {
     cudaError_t a = cudaMalloc(&g->d_lrec, lrec_bytes);
     if (a == cudaSuccess) a = cudaMalloc(&g->d_gerec, gerec_bytes);
@@ -139,8 +139,6 @@ static fw_status build_label_groups(fw_graph* g, cudaStream_t st) {
       return FW_OK;
     }
     g->bytes += lrec_bytes + gerec_bytes + gh_bytes;
-    cudaError_t z = cudaMemsetAsync(g->d_gh + g->e, 0, sizeof(float) * kScanPad, st);
-    if (z != cudaSuccess) return cuda_error(z, "cudaMemsetAsync(grouped weights)");
   }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -374,12 +372,10 @@ extern "C" fw_status fw_graph_create(const int32_t* offsets, const int32_t* cols
   FW_TRY(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device), "cudaDeviceGetAttribute");
   const cudaMemcpyKind kind = ptr_kind == FW_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   const size_t eb = (size_t)(e > 0 ? e : 1);
-  // the arrays the warp scans read in 4-entry chunks carry kScanPad zeroed entries past the end
-  const size_t ep = (size_t)e + kScanPad;
   FW_TRY(cudaMalloc(&g->d_off, sizeof(int32_t) * ((size_t)n + 1)), "cudaMalloc(offsets)");
-  FW_TRY(cudaMalloc(&g->d_col, sizeof(int32_t) * ep), "cudaMalloc(cols)");
-  if (weights) FW_TRY(cudaMalloc(&g->d_h, sizeof(float) * ep), "cudaMalloc(weights)");
-  if (labels) FW_TRY(cudaMalloc(&g->d_lab, ep), "cudaMalloc(labels)");
+  FW_TRY(cudaMalloc(&g->d_col, sizeof(int32_t) * eb), "cudaMalloc(cols)");
+  if (weights) FW_TRY(cudaMalloc(&g->d_h, sizeof(float) * eb), "cudaMalloc(weights)");
+  if (labels) FW_TRY(cudaMalloc(&g->d_lab, eb), "cudaMalloc(labels)");
   FW_TRY(cudaMalloc(&g->d_hmax, sizeof(float) * ((size_t)n + 1)), "cudaMalloc(h_MAX)");
   FW_TRY(cudaMalloc(&g->d_hsum, sizeof(float) * ((size_t)n + 1)), "cudaMalloc(h_SUM)");
   FW_TRY(cudaMalloc(&g->d_nrec, 2 * sizeof(int4) * ((size_t)n + 1)), "cudaMalloc(node records)");
@@ -390,9 +386,6 @@ extern "C" fw_status fw_graph_create(const int32_t* offsets, const int32_t* cols
   g->bytes = sizeof(int32_t) * ((size_t)n + 1) + eb * (4 + (weights ? 4 : 0) + (labels ? 1 : 0)) +
              2 * sizeof(float) * ((size_t)n + 1) + 2 * sizeof(int4) * ((size_t)n + 1) +
              (weights ? 4 : 2) * sizeof(int4) * eb + 64 + sizeof(DevCounters);
-  FW_TRY(cudaMemsetAsync(g->d_col + e, 0, sizeof(int32_t) * kScanPad, st), "cudaMemsetAsync");
-  if (weights) FW_TRY(cudaMemsetAsync(g->d_h + e, 0, sizeof(float) * kScanPad, st), "cudaMemsetAsync");
-  if (labels) FW_TRY(cudaMemsetAsync(g->d_lab + e, 0, kScanPad, st), "cudaMemsetAsync");
   FW_TRY(cudaMemsetAsync(g->d_err, 0, 64, st), "cudaMemsetAsync");
   FW_TRY(cudaMemsetAsync(g->d_cnt, 0, sizeof(DevCounters), st), "cudaMemsetAsync");
   FW_TRY(cudaMemcpyAsync(g->d_off, offsets, sizeof(int32_t) * ((size_t)n + 1), kind, st), "copy offsets");
@@ -491,9 +484,8 @@ extern "C" fw_status fw_graph_quantize_weights(fw_graph* g, float* scale_out, vo
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   uint8_t* codes = nullptr;
   float* scales = nullptr;
-  cudaError_t e = cudaMalloc(&codes, (size_t)g->e + kScanPad);
+  cudaError_t e = cudaMalloc(&codes, (size_t)(g->e > 0 ? g->e : 1));
   if (e == cudaSuccess) e = cudaMalloc(&scales, sizeof(float) * ((size_t)g->n + 1));
-  if (e == cudaSuccess) e = cudaMemsetAsync(codes + g->e, 0, kScanPad, st);
   if (e != cudaSuccess) {
     cudaFree(codes);
     cudaFree(scales);

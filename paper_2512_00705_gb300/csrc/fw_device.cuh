@@ -368,6 +368,20 @@ __device__ __forceinline__ bool row_member(const DevGraph& g, const Job& J, int3
   return row_find(g.col, rs, re, u, g.n, probes) >= 0;
 }
 
+// Membership for the scans of eRVS and exact mode, which test every
+// neighbour of v against the same row of v': the Bloom filter first (its
+// 32-byte blocks, 8 bits per entry, stay cached through the scan), then the
+// table where the filter passes (or, without tables, the search).  Exact.
+__device__ __forceinline__ bool row_member_scan(const DevGraph& g, const Job& J, int32_t x, int32_t rs, int32_t re,
+                                                int32_t u, uint32_t& probes) {
+  if (re - rs >= kBloomMinDeg) {
+    const unsigned long long hk = bloom_mix((uint32_t)u);
+    if (J.bloom && !bloom_maybe(g, x, rs, re, hk, probes)) return false;
+    if (J.table) return table_contains(g.mtab, x, rs, re, (uint32_t)(hk >> 32), u, probes);
+  }
+  return row_find(g.col, rs, re, u, g.n, probes) >= 0;
+}
+
 // Position of u in the row [rs, re) of node x, or -1: the table or the
 // filter answers "absent" without a search; otherwise the search gives the
 // position.  Exact.
@@ -383,29 +397,12 @@ __device__ __forceinline__ int32_t row_lookup(const DevGraph& g, const Job& J, i
   return row_find(g.col, rs, re, u, g.n, probes);
 }
 
-// Is u in the sorted array a[0, n) (shared memory)?
-__device__ __forceinline__ bool smem_contains(const int32_t* a, int32_t n, int32_t u) {
-  int32_t lo = 0, len = n;
-  while (len > 0) {
-    const int32_t half = len >> 1;
-    const int32_t v = a[lo + half];
-    if (v == u) return true;
-    if (v < u) {
-      lo += half + 1;
-      len -= half + 1;
-    } else {
-      len = half;
-    }
-  }
-  return false;
-}
-
-// Is u in N(v') (the row [c.ps, c.pe) of c.vp)?  sprev: the row staged in
-// shared memory by the calling warp (nullptr: read it from device memory).
+// Is u in N(v') (the row [c.ps, c.pe) of c.vp)?  SCAN: the test of a scan
+// over N(v) (eRVS, exact mode) rather than of one eRJS trial.
+template <bool SCAN = false>
 __device__ __forceinline__ bool prev_contains(const DevGraph& g, const Job& J, const StepCtx& c, int32_t u,
-                                              uint32_t& probes, const int32_t* sprev = nullptr) {
-  if (sprev) return smem_contains(sprev, c.pe - c.ps, u);
-  return row_member(g, J, c.vp, c.ps, c.pe, u, probes);
+                                              uint32_t& probes) {
+  return SCAN ? row_member_scan(g, J, c.vp, c.ps, c.pe, u, probes) : row_member(g, J, c.vp, c.ps, c.pe, u, probes);
 }
 
 
@@ -453,18 +450,18 @@ static __device__ __noinline__ int32_t common_pick(const DevGraph& g, const Job&
 // Transition weight w~ = w * hk of neighbour u (label lb) of step c.
 template <int ALG = -1>
 __device__ __forceinline__ float weight_of(const DevGraph& g, const Job& J, const StepCtx& c, float hk, int32_t u,
-                                           uint8_t lb, uint32_t& probes, const int32_t* sprev) {
+                                           uint8_t lb, uint32_t& probes) {
   if (FW_ALGO(J) == ALGO_NODE2VEC) {
     if (c.vp < 0 || !J.second_order) return hk;
     float w;
     if (u == c.vp) w = J.inv_p;                       // dist(v',u) = 0
     else if (!J.need_member) w = 1.0f;                // 1/q == 1: distances 1 and 2 weigh the same
-    else w = prev_contains(g, J, c, u, probes, sprev) ? 1.0f : J.inv_q;
+    else w = prev_contains<true>(g, J, c, u, probes) ? 1.0f : J.inv_q;
     return __fmul_rn(w, hk);
   }
   if (FW_ALGO(J) == ALGO_METAPATH) return (lb == J.schema[c.step % J.schema_len]) ? hk : 0.0f;  // w in {0, 1}
   if (FW_ALGO(J) == ALGO_PAGERANK2 && c.vp >= 0)
-    return __fmul_rn(prev_contains(g, J, c, u, probes, sprev) ? c.w1 : c.w2, hk);
+    return __fmul_rn(prev_contains<true>(g, J, c, u, probes) ? c.w1 : c.w2, hk);
   return hk;
 }
 
@@ -476,11 +473,11 @@ __device__ __forceinline__ bool weight_needs_col(const Job& J, const StepCtx& c)
 
 template <int ALG = -1>
 __device__ __forceinline__ float item_weight(const DevGraph& g, const Job& J, const StepCtx& c, int32_t i,
-                                             uint32_t& probes, const int32_t* sprev = nullptr) {
+                                             uint32_t& probes) {
   const float hk = load_h(g, J, i, c.hsc);
   const int32_t u = weight_needs_col<ALG>(J, c) ? __ldg(g.col + i) : -1;
   const uint8_t lb = (FW_ALGO(J) == ALGO_METAPATH) ? __ldg(g.lab + i) : (uint8_t)0;
-  return weight_of<ALG>(g, J, c, hk, u, lb, probes, sprev);
+  return weight_of<ALG>(g, J, c, hk, u, lb, probes);
 }
 
 // ---------------------------------------------------------------- plan
@@ -862,175 +859,18 @@ __device__ __forceinline__ int32_t rvs_pick(const DevGraph& g, const Job& J, con
   return (bestK == -CUDART_INF_F) ? -1 : best;
 }
 
-// ---------------------------------------------------------------- warp eRVS over 16-byte chunks
-// The warp's eRVS step (Sec. 3.2, Fig. 4b parallel jumps) with the row read
-// as 16-byte vector loads: with a = the scanned range's start rounded down
-// to a multiple of 4 entries, chunk q holds entries [a + 4q, a + 4q + 4) and
-// lane l owns chunks l, l + 32, ...; entries outside [c.s, c.s + c.d) weigh
-// nothing (the arrays are padded, so the chunk that straddles the end stays
-// inside its allocation).  Phase 1 keys each lane's first entry, the warp
-// maximum K_g is every lane's first reference, each lane then jumps over its
-// remaining entries in order (two chunks in flight), and the final argmax
-// (ties to the larger position) picks the neighbour.  A lane's entries are a
-// fixed subsequence of the row, so the draw follows Alg. 1 exactly as the
-// one-entry-per-lane partition does; draws are indexed by position
-// (counter (wid, hop, 2, k)), and the partition depends only on the row, so
-// the result does not depend on which warp runs the step.
-// GRP: the scanned range is a label segment of the grouped arrays (weights
-// gh); the result is then a grouped position.
-template <int ALG, bool GRP>
-struct Chunk {
-  float h[4];
-  int32_t col[4];
-  uint32_t lab;  // four labels, entry j in byte j
-};
-
-template <int ALG, bool GRP>
-__device__ __forceinline__ void load_chunk(const DevGraph& g, const Job& J, bool need_col, long long i, float sc,
-                                           Chunk<ALG, GRP>& ch) {
-  if (GRP) {
-    if (J.weighted) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(g.gh + i));
-      ch.h[0] = v.x; ch.h[1] = v.y; ch.h[2] = v.z; ch.h[3] = v.w;
-    } else {
-      ch.h[0] = ch.h[1] = ch.h[2] = ch.h[3] = 1.0f;
-    }
-    return;
-  }
-  if (!J.weighted) {
-    ch.h[0] = ch.h[1] = ch.h[2] = ch.h[3] = 1.0f;
-  } else if (g.h8) {
-    const uint32_t q = __ldg(reinterpret_cast<const uint32_t*>(g.h8 + i));
-#pragma unroll
-    for (int j = 0; j < 4; ++j) ch.h[j] = __fmul_rn((float)((q >> (8 * j)) & 255u), sc);
-  } else {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(g.h + i));
-    ch.h[0] = v.x; ch.h[1] = v.y; ch.h[2] = v.z; ch.h[3] = v.w;
-  }
-  if (need_col) {
-    const int4 v = __ldg(reinterpret_cast<const int4*>(g.col + i));
-    ch.col[0] = v.x; ch.col[1] = v.y; ch.col[2] = v.z; ch.col[3] = v.w;
-  } else {
-    ch.col[0] = ch.col[1] = ch.col[2] = ch.col[3] = -1;
-  }
-  ch.lab = (FW_ALGO(J) == ALGO_METAPATH) ? __ldg(reinterpret_cast<const uint32_t*>(g.lab + i)) : 0u;
-}
-
-template <bool COUNT, int ALG, bool GRP>
-__device__ __forceinline__ int32_t rvs_pick_warp(const DevGraph& g, const Job& J, const StepCtx& c, int lane, bool jump,
-                                                 LaneCounters& lc, const int32_t* sprev) {
-  const long long lo = c.s, hi = (long long)c.s + c.d;
-  const long long a = lo & ~3ll;
-  const int32_t nchunks = (int32_t)((hi - a + 3) >> 2);
-  const bool need_col = !GRP && weight_needs_col<ALG>(J, c);
-  uint32_t probes = 0;
-  int32_t scanned = 0, keys = 0;
-  float bestK = -CUDART_INF_F;
-  int32_t best = -1;
-  // phase 1: the first entry of the lane's first chunk
-  Chunk<ALG, GRP> ch0;
-  int32_t j0 = 4;  // first entry of chunk `lane` still to be scanned after phase 1
-  uint32_t xz = 0;
-  if (lane < nchunks) {
-    const long long base = a + 4ll * lane;
-    load_chunk<ALG, GRP>(g, J, need_col, base, c.hsc, ch0);
-    j0 = (base < lo) ? (int32_t)(lo - base) : 0;  // only chunk 0 starts before lo
-    // entry j0 of the chunk, selected without a run-time index into the
-    // chunk's arrays (that would move them to local memory)
-    float h0 = ch0.h[0];
-    int32_t u0 = ch0.col[0];
-#pragma unroll
-    for (int j = 1; j < 4; ++j) {
-      if (j == j0) {
-        h0 = ch0.h[j];
-        u0 = ch0.col[j];
-      }
-    }
-    const float wt = GRP ? h0 : weight_of<ALG>(g, J, c, h0, u0, (uint8_t)(ch0.lab >> (8 * j0)), probes, sprev);
-    const int32_t k = (int32_t)(base + j0 - lo);
-    const uint4 x = philox(make_uint4(c.wid, (uint32_t)c.step, 2u, (uint32_t)k), J.key0, J.key1);
-    xz = x.z;
-    ++scanned;
-    if (wt > 0.0f) {
-      bestK = logf(u01_open(x.x)) / wt;
-      best = k;
-      ++keys;
-    }
-    ++j0;
-  }
-  float ref = warp_max(bestK);
-  // remaining weight before the next crossing; K_ref = -inf: the first positive entry crosses
-  float rem = (ref == -CUDART_INF_F) ? 0.0f : ((ref < 0.0f) ? logf(u01_open(xz)) / ref : CUDART_INF_F);
-  auto visit = [&](const Chunk<ALG, GRP>& ch, long long base, int32_t jfrom) {
-#pragma unroll
-    for (int32_t j = 0; j < 4; ++j) {
-      if (j < jfrom || base + j >= hi) continue;
-      const float wt = GRP ? ch.h[j]
-                           : weight_of<ALG>(g, J, c, ch.h[j], ch.col[j], (uint8_t)(ch.lab >> (8 * j)), probes, sprev);
-      ++scanned;
-      if (!(wt > 0.0f)) continue;
-      const int32_t k = (int32_t)(base + j - lo);
-      if (!jump) {
-        const uint4 x = philox(make_uint4(c.wid, (uint32_t)c.step, 2u, (uint32_t)k), J.key0, J.key1);
-        const float K = logf(u01_open(x.x)) / wt;
-        ++keys;
-        if (K >= bestK) {
-          bestK = K;
-          best = k;
-        }
-      } else {
-        rem -= wt;
-        if (rem <= 0.0f) {
-          const uint4 x = philox(make_uint4(c.wid, (uint32_t)c.step, 2u, (uint32_t)k), J.key0, J.key1);
-          // key conditioned on beating ref: u' ~ U(exp(ref*wt), 1), K = ln(u') / wt
-          const float K = log1pf(expm1f(ref * wt) * u01_open(x.y)) / wt;
-          ++keys;
-          bestK = K;
-          best = k;
-          ref = K;
-          rem = (ref < 0.0f) ? logf(u01_open(x.z)) / ref : CUDART_INF_F;
-        }
-      }
-    }
-  };
-  if (lane < nchunks) visit(ch0, a + 4ll * lane, j0);
-  // the lane's other chunks, two loads in flight per round
-  for (int32_t q = lane + 32; q < nchunks; q += 64) {
-    Chunk<ALG, GRP> c1, c2;
-    const long long b1 = a + 4ll * q, b2 = b1 + 128;
-    load_chunk<ALG, GRP>(g, J, need_col, b1, c.hsc, c1);
-    const bool two = q + 32 < nchunks;
-    if (two) load_chunk<ALG, GRP>(g, J, need_col, b2, c.hsc, c2);
-    visit(c1, b1, 0);
-    if (two) visit(c2, b2, 0);
-  }
-  warp_argmax(bestK, best);
-  if (COUNT) {
-    // per-lane shares; summed over the warp they give the step's totals
-    lc.rvs_items += scanned;
-    lc.rvs_keys += keys;
-    lc.probes += probes;
-    const int per = GRP ? (J.weighted ? 4 : 0)
-                        : ((FW_ALGO(J) == ALGO_NODE2VEC) ? (J.weighted ? 8 : 4)
-                                                         : (FW_ALGO(J) == ALGO_METAPATH ? (J.weighted ? 5 : 1)
-                                                                                        : (J.weighted ? 4 : 0)));
-    lc.bytes += (unsigned long long)scanned * per + 32ull * probes;
-  }
-  return (bestK == -CUDART_INF_F) ? -1 : best;
-}
-
 // ---------------------------------------------------------------- exact
 // Exact inverse CDF with one uniform u: W_k accumulated with FP32 adds in
 // neighbour order (T = 32: the warp loads 32 weights at a time and replays
 // the additions in order through shuffles, so the sum is the serial one).
 template <int T, bool COUNT, int ALG = -1>
 __device__ __forceinline__ int32_t exact_pick(const DevGraph& g, const Job& J, const StepCtx& c, int lane, float u,
-                                              LaneCounters& lc, const int32_t* sprev = nullptr) {
+                                              LaneCounters& lc) {
   uint32_t probes = 0;
   float total = 0.0f;
   for (int32_t base = 0; base < c.d; base += T) {
     const int32_t k = base + lane;
-    const float wt = (k < c.d) ? item_weight<ALG>(g, J, c, c.s + k, probes, sprev) : 0.0f;
+    const float wt = (k < c.d) ? item_weight<ALG>(g, J, c, c.s + k, probes) : 0.0f;
     const int32_t cnt = min(T, c.d - base);
     if (T == 1) {
       total = __fadd_rn(total, wt);
@@ -1044,7 +884,7 @@ __device__ __forceinline__ int32_t exact_pick(const DevGraph& g, const Job& J, c
     float run = 0.0f;
     for (int32_t base = 0; base < c.d && pick < 0; base += T) {
       const int32_t k = base + lane;
-      const float wt = (k < c.d) ? item_weight<ALG>(g, J, c, c.s + k, probes, sprev) : 0.0f;
+      const float wt = (k < c.d) ? item_weight<ALG>(g, J, c, c.s + k, probes) : 0.0f;
       const int32_t cnt = min(T, c.d - base);
       if (T == 1) {
         run = __fadd_rn(run, wt);
@@ -1062,7 +902,7 @@ __device__ __forceinline__ int32_t exact_pick(const DevGraph& g, const Job& J, c
     if (pick < 0) {  // rounding left t >= W_{d-1}: last positive weight
       for (int32_t base = ((c.d - 1) / T) * T; base >= 0 && pick < 0; base -= T) {
         const int32_t k = base + lane;
-        const float wt = (k < c.d) ? item_weight<ALG>(g, J, c, c.s + k, probes, sprev) : 0.0f;
+        const float wt = (k < c.d) ? item_weight<ALG>(g, J, c, c.s + k, probes) : 0.0f;
         if (T == 1) {
           if (wt > 0.0f) pick = k;
         } else {

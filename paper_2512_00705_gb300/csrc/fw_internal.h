@@ -13,9 +13,6 @@
 
 // fw_walk_host splits large requests into at most this many chunks
 constexpr int kHostChunksMax = 16;
-// entries of padding (zeroed) past the end of cols, weights, labels, weight
-// codes and grouped weights: warp scans read rows in aligned 4-entry chunks
-constexpr size_t kScanPad = 4;
 
 struct fw_graph {
   int device = 0;

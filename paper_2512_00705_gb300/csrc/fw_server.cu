@@ -18,6 +18,12 @@
 //      them.
 // Clients may submit and poll many queries per call (one lock each), which
 // keeps a single client thread ahead of tens of thousands of queries/s.
+// Copies to or from pageable host memory would block the worker until the
+// wave is done (the driver stages them synchronously), so queries whose
+// buffers are not page-locked go through a page-locked mirror of the arena
+// (allocated on first need): the worker copies their starts into it before
+// the upload and their rows out of it after the wave, and every device copy
+// stays asynchronous, so waves overlap for any caller.
 // Waves on different streams overlap on the device, and queries that arrive
 // while waves run join the next wave: continuous batching.  A query's rows
 // are identical to those of fw_walk_host with the same arguments, alone or
@@ -49,6 +55,7 @@ struct Request {
   fw_params params;
   uint64_t seed = 0;
   size_t bytes = 0, rows_off = 0, arena_off = 0;
+  bool pinned_in = false, pinned_out = false;  // caller buffers page-locked (copied directly)
   Clock::time_point t_submit, t_done;
   int state = REQ_PENDING;
   fw_status status = FW_OK;
@@ -138,6 +145,8 @@ struct fw_server {
   const fw_graph* g = nullptr;
   fw_server_config cfg;
   unsigned char* arena_mem = nullptr;
+  unsigned char* mirror = nullptr;  // page-locked mirror of the arena (pageable callers), or nullptr
+  bool mirror_failed = false;
   Arena* arena = nullptr;
   std::vector<Wave> waves;
   std::mutex mu;
@@ -196,9 +205,13 @@ cudaError_t enqueue_wave(fw_server* s, Wave& w, const std::vector<Request*>& bat
     J.gbase = total;
     total += r->num_walkers;
     tab.push_back(J);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(d_starts, r->starts, sizeof(int32_t) * (size_t)r->num_walkers, cudaMemcpyHostToDevice,
-                          w.stream);
+    const size_t in_bytes = sizeof(int32_t) * (size_t)r->num_walkers;
+    const void* src = r->starts;
+    if (!r->pinned_in && s->mirror) {  // pageable starts: through the page-locked mirror
+      std::memcpy(s->mirror + r->arena_off, r->starts, in_bytes);
+      src = s->mirror + r->arena_off;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_starts, src, in_bytes, cudaMemcpyHostToDevice, w.stream);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(w.qctr, 0, sizeof(unsigned long long) * (kHopSlot + 1), w.stream);
   if (e == cudaSuccess && total > 0) e = launch_walk(s->g, tab.data(), (int)tab.size(), total, false, w.qctr, w.stream);
@@ -221,7 +234,10 @@ cudaError_t enqueue_wave(fw_server* s, Wave& w, const std::vector<Request*>& bat
     e = cudaMemcpyAsync(w.hops_host, w.qctr + kHopSlot, sizeof(unsigned long long), cudaMemcpyDeviceToHost, w.stream);
   for (Request* r : batch) {
     if (e != cudaSuccess) break;
-    e = cudaMemcpyAsync(r->out, s->arena_mem + r->arena_off + r->rows_off,
+    // pageable rows land in the mirror and are copied out when the wave retires
+    void* dst = (!r->pinned_out && s->mirror) ? static_cast<void*>(s->mirror + r->arena_off + r->rows_off)
+                                               : static_cast<void*>(r->out);
+    e = cudaMemcpyAsync(dst, s->arena_mem + r->arena_off + r->rows_off,
                         sizeof(int32_t) * (size_t)r->num_walkers * ((size_t)r->len + 1), cudaMemcpyDeviceToHost,
                         w.stream);
   }
@@ -237,7 +253,18 @@ void launch_wave(fw_server* s, Wave& w, std::unique_lock<std::mutex>& lk) {
   batch.swap(s->admitted);
   for (Request* r : batch) r->state = REQ_LAUNCHED;
   w.busy = true;  // reserved: no other launch takes this wave meanwhile
+  bool need_mirror = false;
+  for (Request* r : batch) need_mirror = need_mirror || !r->pinned_in || !r->pinned_out;
   lk.unlock();
+  if (need_mirror && !s->mirror && !s->mirror_failed) {  // only the worker allocates it
+    unsigned char* m = nullptr;
+    if (cudaMallocHost(reinterpret_cast<void**>(&m), s->cfg.mem_budget) == cudaSuccess) {
+      s->mirror = m;
+    } else {
+      cudaGetLastError();  // not sticky; pageable queries then copy directly (synchronously)
+      s->mirror_failed = true;
+    }
+  }
   const cudaError_t e = enqueue_wave(s, w, batch);
   lk.lock();
   if (e != cudaSuccess) {
@@ -271,7 +298,17 @@ void worker_main(fw_server* s) {
       }
       const fw_status st = q == cudaSuccess ? FW_OK : FW_ERR_CUDA;
       const std::string msg = q == cudaSuccess ? std::string() : std::string("wave: ") + cudaGetErrorString(q);
-      if (q == cudaSuccess) s->walker_steps += *w.hops_host;
+      if (q == cudaSuccess) {
+        s->walker_steps += *w.hops_host;
+        if (s->mirror) {  // rows of pageable callers: out of the mirror, without holding the lock
+          lk.unlock();
+          for (Request* r : w.reqs)
+            if (!r->pinned_out)
+              std::memcpy(r->out, s->mirror + r->arena_off + r->rows_off,
+                          sizeof(int32_t) * (size_t)r->num_walkers * ((size_t)r->len + 1));
+          lk.lock();
+        }
+      }
       for (Request* r : w.reqs) {
         s->arena->release(r->arena_off, r->bytes);
         finish(s, r, st, msg);
@@ -375,6 +412,18 @@ extern "C" fw_status fw_server_create(const fw_graph* g, const fw_server_config*
   return FW_OK;
 }
 
+// Is p in page-locked (or registered) host memory, so that copies to and
+// from it run asynchronously?
+static bool host_pinned(const void* p) {
+  if (!p) return true;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
 // A validated request for one query (no lock taken); nullptr and the
 // error status on bad arguments.
 static Request* new_request(fw_server* s, const int32_t* starts, int32_t num_walkers, int32_t len, int32_t algo,
@@ -417,6 +466,8 @@ static Request* new_request(fw_server* s, const int32_t* starts, int32_t num_wal
   r->seed = seed;
   r->rows_off = rows_off;
   r->bytes = rows_off + round256(row_bytes * (size_t)num_walkers);
+  r->pinned_in = host_pinned(starts);
+  r->pinned_out = host_pinned(out);
   return r;
 }
 
@@ -584,6 +635,7 @@ extern "C" fw_status fw_server_destroy(fw_server* s) {
   cudaFree(q);
   cudaFree(s->arena_mem);
   cudaFreeHost(s->hops_host);
+  if (s->mirror) cudaFreeHost(s->mirror);
   delete s->arena;
   delete s;
   return FW_OK;

@@ -27,10 +27,6 @@ namespace fw {
 constexpr int kBlock = 256;
 constexpr int kMinBlocks = 4;  // 4 x 256 threads per SM (64 registers; 3, 5 and 6 blocks measured slower)
 constexpr int kThreadExactMaxDeg = 16; // exact steps with d <= this run on one lane
-// Warp-level eRVS / exact steps of node2vec and second-order PageRank stage
-// N(v') in the warp's shared memory when it has at most this many entries:
-// every membership test of the scan is then a shared-memory search.
-constexpr int kStagePrev = 1024;
 
 // Row writes are staged per lane in shared memory, one aligned group of
 // kStageSlots entries at a time, and written out when the group (or the
@@ -99,7 +95,7 @@ struct JobTableN {
 template <bool COUNT, int ALG>
 __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int njobs, long long total,
                                           unsigned long long* __restrict__ qctr, unsigned* __restrict__ err,
-                                          int32_t* obuf, int32_t* wprev, LaneCounters& lc) {
+                                          int32_t* obuf, LaneCounters& lc) {
   static_assert(ALG >= 0 && ALG < kAlgos, "the walk loop is compiled for one algorithm");
   const int lane = threadIdx.x & 31;
   const int tid = threadIdx.x;
@@ -440,31 +436,18 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
       bool wg = false;
       if (ALG == ALGO_METAPATH) wg = __shfl_sync(kFull, (int)grp, src) != 0;
       const Job& JW = sj[jb];
-      // N(v') into the warp's shared buffer when the scan's weights test membership in it
-      const int32_t* sp = nullptr;
-      if ((ALG == ALGO_NODE2VEC && w.vp >= 0 && JW.second_order && JW.need_member) ||
-          (ALG == ALGO_PAGERANK2 && w.vp >= 0)) {
-        const int32_t np = w.pe - w.ps;
-        if (np <= kStagePrev) {
-          for (int32_t j = lane; j < np; j += 32) wprev[j] = __ldg(g.col + w.ps + j);
-          __syncwarp();
-          sp = wprev;
-          if (COUNT) lc.bytes += 4ull * (uint32_t)((np - lane + 31) / 32);
-        }
-      }
       int32_t k;
       if (pl == PLAN_EXACT_W) {
         const float u = u01(philox(make_uint4(w.wid, (uint32_t)w.step, 0u, 0u), JW.key0, JW.key1).x);
-        k = exact_pick<32, COUNT, ALG>(g, JW, w, lane, u, lc, sp);
+        k = exact_pick<32, COUNT, ALG>(g, JW, w, lane, u, lc);
       } else if (ALG == ALGO_METAPATH && wg) {
         StepCtx cg = w;
         cg.s = w.ps;
         cg.d = w.pe - w.ps;
-        k = rvs_pick_warp<COUNT, ALG, true>(g, JW, cg, lane, !(JW.flags & FW_FLAG_RVS_NOJUMP), lc, nullptr);
+        k = rvs_pick<32, COUNT, ALG, true>(g, JW, cg, lane, !(JW.flags & FW_FLAG_RVS_NOJUMP), lc);
       } else {
-        k = rvs_pick_warp<COUNT, ALG, false>(g, JW, w, lane, !(JW.flags & FW_FLAG_RVS_NOJUMP), lc, sp);
+        k = rvs_pick<32, COUNT, ALG>(g, JW, w, lane, !(JW.flags & FW_FLAG_RVS_NOJUMP), lc);
       }
-      __syncwarp();  // every lane is done with the staged row before the next hand-off overwrites it
       if (lane == src && ALG == ALGO_METAPATH && wg) {
         pick = -1;
         if (k >= 0) {  // grouped position -> node, position in the row, node record
@@ -552,16 +535,11 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, Jo
                                                       unsigned* __restrict__ err, DevCounters* __restrict__ cnt) {
   __shared__ Job sj[NJ];
   __shared__ int32_t obuf[kStageSlots * kBlock];
-  // staged rows of v' for node2vec and second-order PageRank warp steps (one per warp)
-  constexpr int kPrevRows = (ALG == ALGO_NODE2VEC || ALG == ALGO_PAGERANK2) ? kBlock / 32 : 1;
-  constexpr int kPrevLen = (ALG == ALGO_NODE2VEC || ALG == ALGO_PAGERANK2) ? kStagePrev : 1;
-  __shared__ int32_t sprev[kPrevRows][kPrevLen];
   load_jobs(tab.jobs, njobs, sj);
   __syncthreads();
   LaneCounters lc;
   lc.zero();
-  walk_loop<COUNT, ALG>(g, sj, njobs, total, qctr, err, obuf, sprev[(ALG == ALGO_NODE2VEC || ALG == ALGO_PAGERANK2)
-                                                                       ? (threadIdx.x >> 5) : 0], lc);
+  walk_loop<COUNT, ALG>(g, sj, njobs, total, qctr, err, obuf, lc);
   if (COUNT) flush_counters(lc, cnt);
 }
 
