@@ -777,9 +777,10 @@ __device__ __forceinline__ void warp_argmax(float& key, int32_t& idx) {
 // ---------------------------------------------------------------- eRVS
 // T lanes cooperate on one walker-step (T = 1: a single lane; T = 32: the
 // warp, all lanes converged with identical arguments).  Lane `lane` scans
-// positions lane, lane+T, ...  Phase 1 keys the first T positions; their
-// maximum is the reference K_ref from which every lane jumps over its own
-// subsequence; the final argmax over lanes picks the neighbour.  Counter
+// positions lane, lane+T, ...  Phase 1 keys the first T*m positions (m per
+// lane, see phase1_items); their maximum is the reference K_ref from which
+// every lane jumps over the rest of its own subsequence; the final argmax
+// over lanes picks the neighbour.  Counter
 // draws: (wid, hop, 2, k): x.x = phase-1 key, x.y = key at a crossing,
 // x.z = the lane's next jump threshold.  Returns position k or -1 (all
 // weights zero: dead end).
@@ -792,6 +793,18 @@ __device__ __forceinline__ float scan_weight(const DevGraph& g, const Job& J, co
   return item_weight<ALG>(g, J, c, i, probes);
 }
 
+// Phase 1 keys each lane's first m positions, m growing with the entries per
+// lane (1 .. kPhase1Max): the keys of phase 1 are drawn by all lanes at once,
+// while each jump crossing afterwards runs in the one lane that crosses and
+// stalls the rest of the warp; a larger phase 1 raises the reference K_g and
+// leaves fewer crossings (about ln(1 + n/(T m)) per lane for n entries per
+// lane), so a long row costs fewer divergent crossing blocks.
+constexpr int32_t kPhase1Max = 8;
+__device__ __forceinline__ int32_t phase1_items(int32_t d, int T) {
+  const int32_t per = (d + T - 1) / T;
+  return T == 1 ? 1 : min(kPhase1Max, max(1, per / 8));
+}
+
 template <int T, bool COUNT, int ALG = -1, bool GRP = false>
 __device__ __forceinline__ int32_t rvs_pick(const DevGraph& g, const Job& J, const StepCtx& c, int lane, bool jump,
                                             LaneCounters& lc) {
@@ -800,23 +813,29 @@ __device__ __forceinline__ int32_t rvs_pick(const DevGraph& g, const Job& J, con
   int32_t best = -1;
   uint32_t xz = 0;
   int32_t scanned = 0, keys = 0;
-  if (lane < c.d) {
-    const float wt = scan_weight<ALG, GRP>(g, J, c, c.s + lane, probes);
-    const uint4 x = philox(make_uint4(c.wid, (uint32_t)c.step, 2u, (uint32_t)lane), J.key0, J.key1);
-    xz = x.z;
+  const int32_t m = phase1_items(c.d, T);
+  for (int32_t j = 0; j < m; ++j) {
+    const int32_t k = lane + T * j;
+    if (k >= c.d) break;
+    const float wt = scan_weight<ALG, GRP>(g, J, c, c.s + k, probes);
+    const uint4 x = philox(make_uint4(c.wid, (uint32_t)c.step, 2u, (uint32_t)k), J.key0, J.key1);
+    xz = x.z;  // unused by a phase-1 key: the lane's first jump threshold
     ++scanned;
     if (wt > 0.0f) {
-      bestK = logf(u01_open(x.x)) / wt;
-      best = lane;
+      const float K = logf(u01_open(x.x)) / wt;
       ++keys;
+      if (K >= bestK) {
+        bestK = K;
+        best = k;
+      }
     }
   }
-  if (c.d > T) {
+  if (c.d > T * m) {
     float ref = bestK;
     if (T > 1) ref = warp_max(bestK);
     // remaining weight before the next crossing; K_ref = -inf: first positive item crosses
     float rem = (ref == -CUDART_INF_F) ? 0.0f : ((ref < 0.0f) ? logf(u01_open(xz)) / ref : CUDART_INF_F);
-    for (int32_t k = lane + T; k < c.d; k += T) {
+    for (int32_t k = lane + T * m; k < c.d; k += T) {
       const float wt = scan_weight<ALG, GRP>(g, J, c, c.s + k, probes);
       ++scanned;
       if (!(wt > 0.0f)) continue;
