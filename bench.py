@@ -459,8 +459,10 @@ class _ServeClient:
         self.G, self.g = G, g
         self.pool_words = 4 * 100_000 + 1
         self.starts_pool = torch.from_numpy(synth.random_starts(g.n, self.pool_words, seed=46)).pin_memory().numpy()
-        self.ring_words = 1 << 30  # 4 GiB of pinned rows; a query takes the next range, reused once it completes
-        self.ring = torch.empty(self.ring_words, dtype=torch.int32).pin_memory().numpy()
+        # 16 GiB of pinned rows; a query takes the next range, reused once it completes (at 70 % of
+        # capacity the ring turns over in about 0.2 s, so a slow query does not hold up later ones)
+        self.ring_words = 1 << 32
+        self.ring = torch.empty(self.ring_words, dtype=torch.int32, pin_memory=True).numpy()
 
     @staticmethod
     def queries(rate, duration, seed):
@@ -582,55 +584,85 @@ class _ServeClient:
             hops = sum(f.result() for f in futs)
             counter.shutdown()
             stats = None
+        # offered load: the steps the queries actually took (a dead end ends a walker early) over the
+        # arrival span; the nominal figure counts W x L per query
+        span = max(float(arrivals[-1]), 1e-9)
+        self.last = {"latency_ms": lat, "W": W, "L": Ls, "algo": algos, "arrival_s": arrivals}  # per query
         r = {"queries": count, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
              "mean_ms": float(lat.mean()), "walker_steps_per_s": hops / wall, "wall_s": wall, "hops": hops,
-             "offered_walker_steps_per_s": float((W * Ls).sum() / max(arrivals[-1], 1e-9))}
+             "arrival_span_s": span, "backlog_ms": (wall - span) * 1e3,
+             "offered_walker_steps_per_s": hops / span,
+             "offered_nominal_walker_steps_per_s": float((W * Ls).sum() / span)}
         if stats:
             r.update({"waves": stats["waves"], "queries_per_wave": stats["queries_per_wave"],
-                      "peak_inflight_waves": stats["peak_inflight_waves"]})
+                      "peak_inflight_waves": stats["peak_inflight_waves"],
+                      "submit_lag_p99_ms": float(np.percentile(lag, 99)) * 1e3,
+                      "server_queue_p50_ms": stats["queue_p50_ms"], "server_queue_p99_ms": stats["queue_p99_ms"],
+                      "server_wave_p50_ms": stats["wave_p50_ms"], "server_wave_p99_ms": stats["wave_p99_ms"],
+                      "server_enqueue_ms_per_wave": stats["enqueue_ms_per_wave"],
+                      "copies_per_query": stats["copies"] / max(1, count)})
         return r
 
 
-def _device_rate(G, cl, rate, duration, seed, count=2048):
-    """The first `count` queries of a served stream walked straight from
-    device memory as plain batches (fw_walk_batch, 64 queries per launch
-    group, one stream, no host copies, no server): what the GPU does with this
-    mix of queries when nothing but the walks runs."""
+def _device_rate(G, cl, rate, duration, seed, hops, nstreams=8, per_batch=64):
+    """The queries of a served stream walked straight from device memory, in
+    arrival order, as plain batches of `per_batch` (fw_walk_batch) spread
+    round-robin over `nstreams` streams: no host copies, no server.  What the
+    GPU does with this mix when nothing but the walks runs, batched the way
+    the server's waves are.  Rows of each stream's batches share one device
+    buffer (overwritten); `hops` is the walker-step count of the same queries
+    (their rows are identical to the server's, so the served run's count)."""
     import torch
     from paper_2512_00705_gb300 import flexiwalk as fw
     arrivals, W, Ls, algos = cl.queries(rate, duration, seed)
-    count = min(count, len(arrivals))
+    count = len(arrivals)
     names = ["node2vec", "metapath", "weighted"]
     pool = torch.from_numpy(np.ascontiguousarray(cl.starts_pool)).cuda()
-    jobs, outs = [], []
-    for i in range(count):
-        off = (i * 7919) % (cl.pool_words - W[i])
-        st = pool[off:off + W[i]]
-        out = torch.empty((int(W[i]), int(Ls[i]) + 1), dtype=torch.int32, device="cuda")
-        d = {"seed": int(1000 + i)}
-        if algos[i] == 0:
-            d["p"], d["q"] = 2.0, 0.5
-        if algos[i] == 1:
-            d["schema"] = [0, 1, 2, 3, 4]
-        jobs.append(fw.make_job(st, int(Ls[i]), names[algos[i]], out, **d))
-        outs.append(out)
-    fw.fw_walk_batch(G.handle, jobs)  # warm-up
+    words = (W * (Ls + 1)).astype(np.int64)
+    nb = (count + per_batch - 1) // per_batch
+    most = int(max(words[b * per_batch:(b + 1) * per_batch].sum() for b in range(nb)))
+    streams = [torch.cuda.Stream() for _ in range(nstreams)]
+    bufs = [torch.empty(most, dtype=torch.int32, device="cuda") for _ in range(nstreams)]
+    batches = []
+    for b in range(nb):
+        buf, pos, js = bufs[b % nstreams], 0, []
+        for i in range(b * per_batch, min(count, (b + 1) * per_batch)):
+            off = (i * 7919) % (cl.pool_words - W[i])
+            out = buf[pos:pos + words[i]].view(int(W[i]), int(Ls[i]) + 1)
+            pos += int(words[i])
+            d = {"seed": int(1000 + i)}
+            if algos[i] == 0:
+                d["p"], d["q"] = 2.0, 0.5
+            if algos[i] == 1:
+                d["schema"] = [0, 1, 2, 3, 4]
+            js.append(fw.make_job(pool[off:off + W[i]], int(Ls[i]), names[algos[i]], out, **d))
+        batches.append(js)
+    fw.fw_walk_batch(G.handle, batches[0], stream=streams[0])  # warm-up
     torch.cuda.synchronize()
+    main = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    fw.fw_walk_batch(G.handle, jobs)
-    e1.record()
+    e0.record(main)
+    for st in streams:
+        st.wait_event(e0)
+    for b, js in enumerate(batches):
+        fw.fw_walk_batch(G.handle, js, stream=streams[b % nstreams])
+    for st in streams:
+        main.wait_stream(st)
+    e1.record(main)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    hops = sum(_hops(o) for o in outs)
-    return {"walker_steps_per_s": hops / (ms / 1e3), "queries": count, "hops": hops, "ms": ms}
+    del bufs
+    return {"walker_steps_per_s": hops / (ms / 1e3), "queries": count, "hops": hops, "ms": ms,
+            "batches": nb, "streams": nstreams}
 
 
 def serve_result(G, g, rate=2000.0, duration=10.0, max_waves=8, serial=True, capacity=True):
     """Continuous batching (fw_server) against serial fw_walk_host calls on the
     same arrival sequence at `rate` queries/s for `duration` s; then the
-    server's capacity (saturated throughput at 20x the rate, 3 s) and its
-    p50 / p99 at 70 % of that capacity (5 s).  Returns a dict."""
+    server's capacity (throughput when 60x the rate arrives for 1 s: the
+    same 20x-rate query count, so the queue builds up and the server drains
+    it at its own pace) and its p50 / p99 at 70 % and 50 % of that capacity
+    (5 s each).  Returns a dict."""
     ratios = {"node2vec": G.autotune("node2vec", p=2.0, q=0.5, method=1),
               "metapath": G.autotune("metapath", schema=[0, 1, 2, 3, 4], method=1),
               "weighted": G.autotune("weighted", method=1)}
@@ -648,17 +680,20 @@ def serve_result(G, g, rate=2000.0, duration=10.0, max_waves=8, serial=True, cap
            "steps_server_over_serial": (out["server"]["walker_steps_per_s"] / out["serial"]["walker_steps_per_s"])
            if serial else None}
     if capacity:
-        sat = cl.run("server", 20.0 * rate, 3.0, seed=47, max_waves=max_waves)
+        sat = cl.run("server", 60.0 * rate, 1.0, seed=47, max_waves=max_waves)
         cap = sat["walker_steps_per_s"]
-        res["device_rate_same_queries"] = _device_rate(G, cl, 20.0 * rate, 3.0, 47)
-        _, W, Ls, _ = cl.queries(rate, duration, 45)
-        mean_steps = float((W * Ls).mean())
-        rate70 = 0.7 * cap / mean_steps
+        res["device_rate_same_queries"] = _device_rate(G, cl, 60.0 * rate, 1.0, 47, sat["hops"], max_waves)
+        # queries per second at 70 % of capacity, from the steps a query of this mix actually takes
+        rate70 = 0.7 * cap / (sat["hops"] / sat["queries"])
         at70 = cl.run("server", rate70, 5.0, seed=48, max_waves=max_waves)
+        at50 = cl.run("server", rate70 * 5.0 / 7.0, 5.0, seed=49, max_waves=max_waves)
         res["capacity"] = {"walker_steps_per_s": cap, "saturated_run": sat,
+                           "saturated": bool(sat["offered_walker_steps_per_s"] >= 1.5 * cap),
                            "over_device_rate": cap / res["device_rate_same_queries"]["walker_steps_per_s"],
                            "rate_at_70pct": rate70,
                            "at_70pct": at70,
+                           "at_70pct_load": at70["offered_walker_steps_per_s"] / cap,
+                           "at_50pct": at50,
                            "rate_saturates": bool(out["server"]["offered_walker_steps_per_s"] >= 0.95 * cap)}
     return res
 

@@ -438,12 +438,16 @@ fw_status fw_batch_plan_destroy(fw_batch_plan* plan);
  * max_jobs_per_wave queries) on one of max_waves streams, and retires waves
  * by polling their completion events; queries that arrive while waves run
  * join the next wave, and waves on different streams overlap on the device.
+ * Copies whose host and device ranges both continue the previous query's
+ * merge into one transfer, so clients that take consecutive queries' output
+ * buffers back to back from one pinned pool get few large copies.
  * Results are identical to fw_walk_host with the same arguments, alone or in
  * any mix.  All waits are host-side with caller timeouts; nothing spins on
  * the device.
  */
 typedef struct {
-  size_t mem_budget;          /* device bytes for staged starts + rows (default 1 GiB) */
+  size_t mem_budget;          /* device bytes for staged starts + rows (default 1 GiB;
+                                 rounded down to a multiple of 256)                   */
   int32_t max_waves;          /* concurrent waves / streams, 1..64 (default 4)          */
   int32_t max_jobs_per_wave;  /* queries per launch, 1..64 (default 64)                 */
 } fw_server_config;
@@ -456,6 +460,11 @@ typedef struct {
   size_t peak_device_bytes;             /* arena high-water mark                        */
   int32_t peak_inflight_waves;
   uint64_t walker_steps;                /* hops of completed queries (counted on device) */
+  double queue_p50_ms, queue_p99_ms;    /* submit -> launch of its wave, completed        */
+  double wave_p50_ms, wave_p99_ms;      /* launch of its wave -> rows in host memory      */
+  double enqueue_ms_per_wave;           /* worker's host time to enqueue a wave's copies
+                                           and launches (mean)                            */
+  uint64_t copies;                      /* starts and rows copies issued, after merging   */
 } fw_server_stats_t;
 
 typedef struct fw_server fw_server;

@@ -10,10 +10,13 @@
 //      queue waits for memory rather than being overtaken, so large queries
 //      are not starved;
 //   3. launches the admitted queries as one wave on a free stream: upload of
-//      each query's starts, one batched walk (up to 64 queries; one launch
-//      per algorithm present, each algorithm's queries one shared walker
-//      queue), a count of the wave's hops on the device, download of each
-//      query's rows and of the count, an event.  The CUDA calls run without
+//      the queries' starts, one batched walk (up to 64 queries; one launch
+//      per algorithm present, side by side on the wave's helper streams,
+//      each algorithm's queries one shared walker queue, so the wave ends
+//      with its slowest algorithm rather than after the sum of all), a count
+//      of the wave's hops on the device, download of the
+//      queries' rows and of the count, an event.  Copies of consecutive
+//      queries whose host and device ranges are both contiguous merge.  The CUDA calls run without
 //      the server lock, so submitting and polling threads are not held up by
 //      them.
 // Clients may submit and poll many queries per call (one lock each), which
@@ -54,19 +57,29 @@ struct Request {
   int32_t num_walkers = 0, len = 0, algo = 0;
   fw_params params;
   uint64_t seed = 0;
-  size_t bytes = 0, rows_off = 0, arena_off = 0;
+  size_t in_bytes = 0, row_bytes = 0;  // staged starts, rows (both multiples of 4)
+  size_t starts_off = 0, rows_off = 0;  // their offsets in the arena (and in the mirror)
   bool pinned_in = false, pinned_out = false;  // caller buffers page-locked (copied directly)
-  Clock::time_point t_submit, t_done;
+  Clock::time_point t_submit, t_launch, t_done;
   int state = REQ_PENDING;
   fw_status status = FW_OK;
   std::string error;
 };
 
-// First-fit allocator over [0, size) in 256-byte units.
+// Allocator over [0, size) with byte offsets.  Rows are placed next-fit
+// (right after the previously admitted query's rows when that space is free,
+// else first-fit from the bottom) and staged starts last-fit from the top, so
+// the rows of queries admitted one after another lie back to back and their
+// copies to back-to-back host buffers merge into one.  Zero-byte requests
+// take nothing.
 class Arena {
  public:
   explicit Arena(size_t size) { free_[0] = size; }
   bool alloc(size_t bytes, size_t* off) {
+    if (bytes == 0) {
+      *off = 0;
+      return true;
+    }
     for (auto it = free_.begin(); it != free_.end(); ++it) {
       if (it->second >= bytes) {
         *off = it->first;
@@ -79,7 +92,38 @@ class Arena {
     }
     return false;
   }
+  // [off, off + bytes) if it lies inside one free block
+  bool alloc_at(size_t off, size_t bytes) {
+    if (bytes == 0) return true;
+    auto it = free_.upper_bound(off);
+    if (it == free_.begin()) return false;
+    --it;
+    const size_t start = it->first, end = it->first + it->second;
+    if (off + bytes > end) return false;
+    if (off > start) it->second = off - start;
+    else free_.erase(it);
+    if (off + bytes < end) free_[off + bytes] = end - (off + bytes);
+    used_ += bytes;
+    return true;
+  }
+  bool alloc_top(size_t bytes, size_t* off) {
+    if (bytes == 0) {
+      *off = 0;
+      return true;
+    }
+    for (auto it = free_.rbegin(); it != free_.rend(); ++it) {
+      if (it->second >= bytes) {
+        it->second -= bytes;
+        *off = it->first + it->second;
+        if (it->second == 0) free_.erase(std::next(it).base());
+        used_ += bytes;
+        return true;
+      }
+    }
+    return false;
+  }
   void release(size_t off, size_t bytes) {
+    if (bytes == 0) return;
     auto it = free_.emplace(off, bytes).first;
     auto nx = std::next(it);
     if (nx != free_.end() && it->first + it->second == nx->first) {
@@ -105,11 +149,23 @@ class Arena {
 struct Wave {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
+  cudaStream_t side[fw::kAlgos - 1] = {};  // the other algorithms' launches run beside the first one's
+  cudaEvent_t fork[fw::kAlgos] = {};
   unsigned long long* qctr = nullptr;       // kQueueCounters queue counters, then the hop count (device)
   unsigned long long* hops_host = nullptr;  // the wave's hop count, copied back (pinned host)
   std::vector<Request*> reqs;
+  uint64_t copies = 0;  // starts and rows copies the wave enqueued (after merging)
   bool busy = false;
 };
+
+void destroy_wave(Wave& w) {
+  if (w.stream) cudaStreamDestroy(w.stream);
+  if (w.done) cudaEventDestroy(w.done);
+  for (cudaStream_t& st : w.side)
+    if (st) cudaStreamDestroy(st);
+  for (cudaEvent_t& ev : w.fork)
+    if (ev) cudaEventDestroy(ev);
+}
 
 constexpr int kHopSlot = 8;  // index of the hop count in a wave's 256-byte counter block
 
@@ -137,8 +193,6 @@ __global__ void count_hops_kernel(HopRows t, unsigned long long* __restrict__ ho
   if ((threadIdx.x & 31) == 0 && local) atomicAdd(hops, local);
 }
 
-size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
-
 }  // namespace
 
 struct fw_server {
@@ -158,11 +212,14 @@ struct fw_server {
   bool stop = false;
   std::thread worker;
   // statistics
-  std::vector<double> latencies_ms;
+  std::vector<double> latencies_ms, queue_ms, wave_ms;  // submit -> done, submit -> launch, launch -> done
   uint64_t completed = 0, failed = 0, waves_launched = 0, queries_in_waves = 0, walker_steps = 0;
   unsigned long long* hops_host = nullptr;  // pinned, one slot per wave
   size_t peak_arena = 0;
   int peak_inflight = 0;
+  double enqueue_ms = 0;  // host time spent enqueueing waves
+  uint64_t copies = 0;    // starts and rows copies enqueued
+  size_t rows_cursor = 0; // end of the last admitted query's rows (next-fit placement)
 };
 
 namespace {
@@ -175,10 +232,46 @@ void finish(fw_server* s, Request* r, fw_status st, const std::string& err) {
   if (st == FW_OK) {
     s->completed++;
     s->latencies_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+    s->queue_ms.push_back(std::chrono::duration<double, std::milli>(r->t_launch - r->t_submit).count());
+    s->wave_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_launch).count());
   } else {
     s->failed++;
   }
 }
+
+// Copies of one direction on one stream; a copy whose source and destination
+// both continue the pending one extends it (rows of queries admitted one after
+// another lie back to back in the arena, and clients often take their output
+// buffers back to back from one pool): fewer, larger DMA transfers, which
+// reach a higher share of the host link than many small ones.
+struct CopyRun {
+  cudaMemcpyKind kind;
+  cudaStream_t stream;
+  unsigned char* dst = nullptr;
+  const unsigned char* src = nullptr;
+  size_t n = 0;
+  uint64_t issued = 0;  // copies enqueued
+  CopyRun(cudaMemcpyKind k, cudaStream_t st) : kind(k), stream(st) {}
+  cudaError_t add(unsigned char* d, const unsigned char* sp, size_t bytes) {
+    if (bytes == 0) return cudaSuccess;
+    if (n && d == dst + n && sp == src + n) {
+      n += bytes;
+      return cudaSuccess;
+    }
+    const cudaError_t e = flush();
+    dst = d;
+    src = sp;
+    n = bytes;
+    return e;
+  }
+  cudaError_t flush() {
+    if (!n) return cudaSuccess;
+    const cudaError_t e = cudaMemcpyAsync(dst, src, n, kind, stream);
+    n = 0;
+    ++issued;
+    return e;
+  }
+};
 
 // Enqueue the GPU work of one wave: stage the starts, walk (one launch per
 // algorithm present), copy the rows out, record the wave's event.  Called
@@ -188,6 +281,7 @@ void finish(fw_server* s, Request* r, fw_status st, const std::string& err) {
 cudaError_t enqueue_wave(fw_server* s, Wave& w, const std::vector<Request*>& batch) {
   using namespace fw;
   *w.hops_host = 0;
+  CopyRun up(cudaMemcpyHostToDevice, w.stream), down(cudaMemcpyDeviceToHost, w.stream);
   std::vector<Job> tab;
   tab.reserve(batch.size());
   long long total = 0;
@@ -195,8 +289,8 @@ cudaError_t enqueue_wave(fw_server* s, Wave& w, const std::vector<Request*>& bat
   for (Request* r : batch) {
     Job J;
     if (make_job(s->g, r->algo, &r->params, r->seed, &J) != FW_OK) return cudaErrorInvalidValue;  // checked at submit
-    int32_t* d_starts = reinterpret_cast<int32_t*>(s->arena_mem + r->arena_off);
-    int32_t* d_out = reinterpret_cast<int32_t*>(s->arena_mem + r->arena_off + r->rows_off);
+    int32_t* d_starts = reinterpret_cast<int32_t*>(s->arena_mem + r->starts_off);
+    int32_t* d_out = reinterpret_cast<int32_t*>(s->arena_mem + r->rows_off);
     J.kind = JOB_WALK;
     J.starts = d_starts;
     J.out = d_out;
@@ -205,16 +299,18 @@ cudaError_t enqueue_wave(fw_server* s, Wave& w, const std::vector<Request*>& bat
     J.gbase = total;
     total += r->num_walkers;
     tab.push_back(J);
-    const size_t in_bytes = sizeof(int32_t) * (size_t)r->num_walkers;
-    const void* src = r->starts;
+    const unsigned char* src = reinterpret_cast<const unsigned char*>(r->starts);
     if (!r->pinned_in && s->mirror) {  // pageable starts: through the page-locked mirror
-      std::memcpy(s->mirror + r->arena_off, r->starts, in_bytes);
-      src = s->mirror + r->arena_off;
+      std::memcpy(s->mirror + r->starts_off, r->starts, r->in_bytes);
+      src = s->mirror + r->starts_off;
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_starts, src, in_bytes, cudaMemcpyHostToDevice, w.stream);
+    if (e == cudaSuccess) e = up.add(s->arena_mem + r->starts_off, src, r->in_bytes);
   }
+  if (e == cudaSuccess) e = up.flush();
   if (e == cudaSuccess) e = cudaMemsetAsync(w.qctr, 0, sizeof(unsigned long long) * (kHopSlot + 1), w.stream);
-  if (e == cudaSuccess && total > 0) e = launch_walk(s->g, tab.data(), (int)tab.size(), total, false, w.qctr, w.stream);
+  if (e == cudaSuccess && total > 0)
+    e = tab.size() == 1 ? launch_walk(s->g, tab.data(), 1, total, false, w.qctr, w.stream)
+                        : launch_walk_mixed(s->g, tab.data(), (int)tab.size(), false, w.qctr, w.stream, w.side, w.fork);
   if (e == cudaSuccess && total > 0) {
     HopRows hr;
     hr.n = (int)tab.size();
@@ -235,12 +331,12 @@ cudaError_t enqueue_wave(fw_server* s, Wave& w, const std::vector<Request*>& bat
   for (Request* r : batch) {
     if (e != cudaSuccess) break;
     // pageable rows land in the mirror and are copied out when the wave retires
-    void* dst = (!r->pinned_out && s->mirror) ? static_cast<void*>(s->mirror + r->arena_off + r->rows_off)
-                                               : static_cast<void*>(r->out);
-    e = cudaMemcpyAsync(dst, s->arena_mem + r->arena_off + r->rows_off,
-                        sizeof(int32_t) * (size_t)r->num_walkers * ((size_t)r->len + 1), cudaMemcpyDeviceToHost,
-                        w.stream);
+    unsigned char* dst = (!r->pinned_out && s->mirror) ? s->mirror + r->rows_off
+                                                        : reinterpret_cast<unsigned char*>(r->out);
+    e = down.add(dst, s->arena_mem + r->rows_off, r->row_bytes);
   }
+  if (e == cudaSuccess) e = down.flush();
+  w.copies = up.issued + down.issued;
   if (e == cudaSuccess) e = cudaEventRecord(w.done, w.stream);
   if (e != cudaSuccess) cudaStreamSynchronize(w.stream);  // let what was enqueued finish before its memory is reused
   return e;
@@ -251,7 +347,11 @@ cudaError_t enqueue_wave(fw_server* s, Wave& w, const std::vector<Request*>& bat
 void launch_wave(fw_server* s, Wave& w, std::unique_lock<std::mutex>& lk) {
   std::vector<Request*> batch;
   batch.swap(s->admitted);
-  for (Request* r : batch) r->state = REQ_LAUNCHED;
+  const auto now = Clock::now();
+  for (Request* r : batch) {
+    r->state = REQ_LAUNCHED;
+    r->t_launch = now;
+  }
   w.busy = true;  // reserved: no other launch takes this wave meanwhile
   bool need_mirror = false;
   for (Request* r : batch) need_mirror = need_mirror || !r->pinned_in || !r->pinned_out;
@@ -265,12 +365,17 @@ void launch_wave(fw_server* s, Wave& w, std::unique_lock<std::mutex>& lk) {
       s->mirror_failed = true;
     }
   }
+  const auto t0 = Clock::now();
   const cudaError_t e = enqueue_wave(s, w, batch);
+  const double host_ms = std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
   lk.lock();
+  s->enqueue_ms += host_ms;
+  s->copies += w.copies;
   if (e != cudaSuccess) {
     const std::string msg = std::string("wave launch: ") + cudaGetErrorString(e);
     for (Request* r : batch) {
-      s->arena->release(r->arena_off, r->bytes);
+      s->arena->release(r->rows_off, r->row_bytes);
+      s->arena->release(r->starts_off, r->in_bytes);
       finish(s, r, FW_ERR_CUDA, msg);
     }
     w.busy = false;
@@ -304,13 +409,13 @@ void worker_main(fw_server* s) {
           lk.unlock();
           for (Request* r : w.reqs)
             if (!r->pinned_out)
-              std::memcpy(r->out, s->mirror + r->arena_off + r->rows_off,
-                          sizeof(int32_t) * (size_t)r->num_walkers * ((size_t)r->len + 1));
+              std::memcpy(r->out, s->mirror + r->rows_off, r->row_bytes);
           lk.lock();
         }
       }
       for (Request* r : w.reqs) {
-        s->arena->release(r->arena_off, r->bytes);
+        s->arena->release(r->rows_off, r->row_bytes);
+        s->arena->release(r->starts_off, r->in_bytes);
         finish(s, r, st, msg);
       }
       w.reqs.clear();
@@ -321,9 +426,16 @@ void worker_main(fw_server* s) {
     // 2. admit in arrival order while memory and the job table allow
     while (!s->pending.empty() && (int)s->admitted.size() < s->cfg.max_jobs_per_wave) {
       Request* r = s->pending.front();
-      size_t off = 0;
-      if (!s->arena->alloc(r->bytes, &off)) break;  // the head waits for memory
-      r->arena_off = off;
+      size_t roff = s->rows_cursor, soff = 0;
+      if (!s->arena->alloc_at(roff, r->row_bytes) && !s->arena->alloc(r->row_bytes, &roff))
+        break;  // the head waits for memory
+      if (!s->arena->alloc_top(r->in_bytes, &soff)) {
+        s->arena->release(roff, r->row_bytes);
+        break;
+      }
+      r->rows_off = roff;
+      r->starts_off = soff;
+      s->rows_cursor = roff + r->row_bytes;
       r->state = REQ_ADMITTED;
       s->admitted.push_back(r);
       s->pending.pop_front();
@@ -371,6 +483,7 @@ extern "C" fw_status fw_server_create(const fw_graph* g, const fw_server_config*
   if (c.mem_budget < 4096 || c.max_waves < 1 || c.max_waves > 64 || c.max_jobs_per_wave < 1 ||
       c.max_jobs_per_wave > kMaxJobs)
     return set_error(FW_ERR_ARG, "bad server configuration");
+  c.mem_budget &= ~(size_t)255;  // whole 256-byte units: every arena offset stays 4-byte aligned
   cudaError_t e = prime_walk_occupancy();
   if (e != cudaSuccess) return cuda_error(e, "occupancy query");
   fw_server* s = new (std::nothrow) fw_server();
@@ -378,10 +491,7 @@ extern "C" fw_status fw_server_create(const fw_graph* g, const fw_server_config*
   s->g = g;
   s->cfg = c;
   auto fail = [&](cudaError_t err, const char* what) {
-    for (Wave& w : s->waves) {
-      if (w.stream) cudaStreamDestroy(w.stream);
-      if (w.done) cudaEventDestroy(w.done);
-    }
+    for (Wave& w : s->waves) destroy_wave(w);
     cudaFree(s->arena_mem);
     cudaFreeHost(s->hops_host);
     delete s;
@@ -401,6 +511,10 @@ extern "C" fw_status fw_server_create(const fw_graph* g, const fw_server_config*
     w.hops_host = s->hops_host + i;
     e = cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming);
+    for (int k = 0; k < kAlgos - 1 && e == cudaSuccess; ++k)
+      e = cudaStreamCreateWithFlags(&w.side[k], cudaStreamNonBlocking);
+    for (int k = 0; k < kAlgos && e == cudaSuccess; ++k)
+      e = cudaEventCreateWithFlags(&w.fork[k], cudaEventDisableTiming);
     if (e != cudaSuccess) {
       cudaFree(q);
       return fail(e, "stream / event creation");
@@ -443,11 +557,10 @@ static Request* new_request(fw_server* s, const int32_t* starts, int32_t num_wal
     }
   // staged starts and rows must fit the budget; each term is bounded before
   // it is added or multiplied, so nothing wraps
-  const size_t rows_off = round256(sizeof(int32_t) * (size_t)num_walkers);  // < 2^34
-  const size_t row_bytes = sizeof(int32_t) * ((size_t)len + 1);             // < 2^34
+  const size_t in_bytes = sizeof(int32_t) * (size_t)num_walkers;  // < 2^34
+  const size_t row_bytes = sizeof(int32_t) * ((size_t)len + 1);    // < 2^34
   const size_t budget = s->cfg.mem_budget;
-  if (rows_off > budget || (num_walkers > 0 && row_bytes > (budget - rows_off) / (size_t)num_walkers) ||
-      rows_off + round256(row_bytes * (size_t)num_walkers) > budget) {
+  if (in_bytes > budget || (num_walkers > 0 && row_bytes > (budget - in_bytes) / (size_t)num_walkers)) {
     *st = set_error(FW_ERR_OOM, "query needs more device memory than the server's budget");
     return nullptr;
   }
@@ -464,8 +577,8 @@ static Request* new_request(fw_server* s, const int32_t* starts, int32_t num_wal
   if (params) r->params = *params;
   else fw_params_default(&r->params);
   r->seed = seed;
-  r->rows_off = rows_off;
-  r->bytes = rows_off + round256(row_bytes * (size_t)num_walkers);
+  r->in_bytes = in_bytes;
+  r->row_bytes = row_bytes * (size_t)num_walkers;
   r->pinned_in = host_pinned(starts);
   r->pinned_out = host_pinned(out);
   return r;
@@ -604,16 +717,27 @@ extern "C" fw_status fw_server_stats(fw_server* s, fw_server_stats_t* out) {
   out->peak_device_bytes = s->peak_arena;
   out->peak_inflight_waves = s->peak_inflight;
   out->walker_steps = s->walker_steps;
+  out->enqueue_ms_per_wave = s->waves_launched ? s->enqueue_ms / (double)s->waves_launched : 0.0;
+  out->copies = s->copies;
+  auto pct = [](std::vector<double>& l, double p) {
+    return l[std::min(l.size() - 1, (size_t)(p * (double)(l.size() - 1) + 0.5))];
+  };
   std::vector<double> l = s->latencies_ms;
   if (!l.empty()) {
     std::sort(l.begin(), l.end());
-    auto pct = [&](double p) { return l[std::min(l.size() - 1, (size_t)(p * (double)(l.size() - 1) + 0.5))]; };
-    out->p50_ms = pct(0.50);
-    out->p99_ms = pct(0.99);
+    out->p50_ms = pct(l, 0.50);
+    out->p99_ms = pct(l, 0.99);
     out->max_ms = l.back();
     double sum = 0;
     for (double x : l) sum += x;
     out->mean_ms = sum / (double)l.size();
+    std::vector<double> qw = s->queue_ms, ww = s->wave_ms;
+    std::sort(qw.begin(), qw.end());
+    std::sort(ww.begin(), ww.end());
+    out->queue_p50_ms = pct(qw, 0.50);
+    out->queue_p99_ms = pct(qw, 0.99);
+    out->wave_p50_ms = pct(ww, 0.50);
+    out->wave_p99_ms = pct(ww, 0.99);
   }
   return FW_OK;
 }
@@ -629,8 +753,7 @@ extern "C" fw_status fw_server_destroy(fw_server* s) {
   for (auto& kv : s->reqs) delete kv.second;
   unsigned long long* q = s->waves.empty() ? nullptr : s->waves[0].qctr;
   for (Wave& w : s->waves) {
-    cudaStreamDestroy(w.stream);
-    cudaEventDestroy(w.done);
+    destroy_wave(w);
   }
   cudaFree(q);
   cudaFree(s->arena_mem);

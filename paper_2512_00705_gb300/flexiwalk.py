@@ -63,7 +63,10 @@ class fw_server_stats_t(ctypes.Structure):
                 ("waves", ctypes.c_uint64), ("queries_per_wave", ctypes.c_double), ("p50_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
                 ("peak_device_bytes", ctypes.c_size_t), ("peak_inflight_waves", ctypes.c_int32),
-                ("walker_steps", ctypes.c_uint64)]
+                ("walker_steps", ctypes.c_uint64),
+                ("queue_p50_ms", ctypes.c_double), ("queue_p99_ms", ctypes.c_double),
+                ("wave_p50_ms", ctypes.c_double), ("wave_p99_ms", ctypes.c_double),
+                ("enqueue_ms_per_wave", ctypes.c_double), ("copies", ctypes.c_uint64)]
 
 
 COUNTER_FIELDS = ["hops", "rjs_steps", "rvs_steps", "exact_steps", "handoffs", "rjs_trials", "rvs_items",

@@ -62,6 +62,78 @@ def test_autotune_sweep_picks_from_the_ladder(small):
     G.set_cost_ratio(4.0)
 
 
+def test_autotune_shape_installs_and_caches_the_launch_shape(small, tmp_path):
+    """Method 2 tunes r and the launch shape, installs them for the algorithm
+    alone, and a cache hit restores all four without measuring."""
+    g, G = small
+    cache = str(tmp_path / "shape.txt")
+    r = G.autotune("node2vec", p=0.5, q=2.0, method=2, cache_path=cache)
+    info = G.info
+    a = fw.ALGO["node2vec"]
+    assert r in [0.125, 0.25, 0.5, 1, 2, 4, 8, 16, 32, 64]
+    assert info["lane_max_degrees"][a] in (1, 4, 8, 16, 32, 64)
+    assert info["rjs_batches"][a] in (1, 2, 3, 4, 6)
+    assert info["trial_budgets"][a] in (0.25, 0.5, 1.0, 2.0, 4.0)
+    others = [x for x in range(4) if x != a]
+    assert all(info["lane_max_degrees"][x] == 8 and info["rjs_batches"][x] == 2 for x in others)
+    line = open(cache).read().splitlines()[0]
+    assert "method=2" in line and "lane=" in line and "batch=" in line and "budget=" in line
+    with open(cache, "w") as f:
+        f.write(line.rsplit("r=", 1)[0] + "r=16 lane=32 batch=3 budget=0.5\n")
+    assert G.autotune("node2vec", p=0.5, q=2.0, method=2, cache_path=cache) == pytest.approx(16.0)
+    info = G.info
+    assert (info["lane_max_degrees"][a], info["rjs_batches"][a], info["trial_budgets"][a]) == (32, 3, 0.5)
+    # the shape reaches the walks: an explicit shape in fw_params equals the installed one
+    starts = torch.from_numpy(np.arange(g.n, dtype=np.int32)).cuda()
+    x1 = G.walk(starts, 20, "node2vec", p=0.5, q=2.0, seed=4)
+    x2 = G.walk(starts, 20, "node2vec", p=0.5, q=2.0, seed=4, cost_ratio=16.0, lane_max_degree=32, rjs_batch=3,
+                trial_budget=0.5)
+    assert torch.equal(x1, x2)
+    # back to the defaults for the module's other tests
+    with open(cache, "w") as f:
+        f.write(line.rsplit("r=", 1)[0] + "r=4 lane=8 batch=2 budget=1\n")
+    G.autotune("node2vec", p=0.5, q=2.0, method=2, cache_path=cache)
+    G.set_cost_ratio(4.0)
+
+
+@pytest.mark.parametrize("algo,p,q", [("node2vec", 0.25, 4.0), ("node2vec", 4.0, 0.25), ("weighted", 1.0, 1.0),
+                                      ("pagerank2", 1.0, 1.0)])
+def test_rjs_batch_leaves_rows_unchanged(small, algo, p, q):
+    """Trial t of a step always draws counter t: how many trials a lane runs
+    between two warp ballots changes no row."""
+    g, G = small
+    starts = torch.from_numpy(np.tile(np.arange(g.n, dtype=np.int32), 2)).cuda()
+    ref = G.walk(starts, 25, algo, p=p, q=q, mode="auto", seed=8, rjs_batch=2)
+    for batch in (1, 3, 6, 16):
+        assert torch.equal(G.walk(starts, 25, algo, p=p, q=q, mode="auto", seed=8, rjs_batch=batch), ref), batch
+
+
+@pytest.mark.parametrize("shape", [dict(lane_max_degree=1), dict(lane_max_degree=64), dict(trial_budget=0.25),
+                                   dict(trial_budget=4.0, rjs_batch=6)])
+def test_launch_shape_never_changes_the_distribution(shape):
+    """Where eRVS steps run (lane or warp) and when eRJS hands a step over
+    only change which sampler draws it: whole-path frequencies still match
+    brute-force path probabilities."""
+    g = synth.random_graph(24, 0.85, seed=21, weighted=True, nlabels=3)
+    G = fw.Graph(g)
+    W, L = 300_000, 3
+    starts = torch.zeros(W, dtype=torch.int32, device="cuda")
+    bf = bf_paths(g, 0, L, "node2vec", 0.5, 2.0, None)
+    assert_pvalue_follows(lambda k: merged_chisquare(bf, G.walk(starts, L, "node2vec", p=0.5, q=2.0, mode="auto",
+                                                                 cost_ratio=1.0, seed=13 + 7919 * k,
+                                                                 **shape).cpu().numpy()), ("shape", shape))
+    G.close()
+
+
+def test_launch_shape_out_of_range_is_refused(small):
+    g, G = small
+    starts = torch.zeros(8, dtype=torch.int32, device="cuda")
+    for bad in (dict(lane_max_degree=65), dict(rjs_batch=17), dict(trial_budget=float("inf"))):
+        with pytest.raises(fw.FlexiWalkError) as e:
+            G.walk(starts, 3, "weighted", **bad)
+        assert e.value.status == -1
+
+
 def test_fingerprint_tracks_the_graph(small):
     g, G = small
     G2 = fw.Graph(g)
@@ -221,6 +293,40 @@ def test_server_burst_merges_queries_into_overlapping_waves(small):
     assert stats["peak_inflight_waves"] > 1, stats
     hops = sum(int((o[:, 1:] >= 0).sum()) for o in outs)
     assert stats["walker_steps"] == hops
+    for sp, out in zip(specs, outs):
+        assert np.array_equal(out, G.walk_host(sp["starts"], sp["length"], sp["algo"], **_kw(sp)))
+
+
+def test_server_merges_copies_of_back_to_back_buffers(small):
+    """Queries whose starts and rows are consecutive slices of one pinned
+    pool: their copies merge (fewer copies than two per query) and every
+    query's rows still equal fw_walk_host's alone.  The budget is not a
+    multiple of 256 bytes (it is rounded down, so every staged buffer stays
+    4-byte aligned)."""
+    g, G = small
+    specs = _mixed_jobs(g, 120, seed=33, max_walkers=3000, max_length=40)
+    n_in = sum(len(sp["starts"]) for sp in specs)
+    n_out = sum(len(sp["starts"]) * (sp["length"] + 1) for sp in specs)
+    pool_in = torch.empty(n_in, dtype=torch.int32).pin_memory().numpy()
+    pool_out = torch.empty(n_out, dtype=torch.int32).pin_memory().numpy()
+    pool_out[:] = -7
+    outs, qs, a, b = [], [], 0, 0
+    for sp in specs:
+        w, L = len(sp["starts"]), sp["length"]
+        pool_in[a:a + w] = sp["starts"]
+        o = pool_out[b:b + w * (L + 1)].reshape(w, L + 1)
+        qs.append(fw.make_host_query(pool_in[a:a + w], L, sp["algo"], o, **_kw(sp)))
+        outs.append(o)
+        a += w
+        b += w * (L + 1)
+    srv = fw.Server(G, mem_budget=(256 << 20) + 37, max_waves=4, max_jobs_per_wave=32)
+    tickets = srv.submit_many((fw.fw_job * len(qs))(*qs))
+    for t in tickets:
+        srv.wait(int(t), timeout=60.0)
+    stats = srv.stats()
+    srv.close()
+    assert stats["completed"] == len(specs) and stats["failed"] == 0
+    assert stats["copies"] < 2 * len(specs), stats
     for sp, out in zip(specs, outs):
         assert np.array_equal(out, G.walk_host(sp["starts"], sp["length"], sp["algo"], **_kw(sp)))
 
