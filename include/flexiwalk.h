@@ -108,11 +108,18 @@ enum {
   FW_FLAG_NO_GROUPS = 64, /* metapath: sample over the whole row of v (label
                              test per entry) instead of inside the required
                              label's segment of the label-grouped view           */
-  FW_FLAG_NO_TABLE = 128  /* membership tests do not read the row's membership
+  FW_FLAG_NO_TABLE = 128, /* membership tests do not read the row's membership
                              table (an exact hash set of the row's node ids,
                              one 32-byte bucket per test in most cases) but
                              the Bloom filter and a search of the sorted row;
                              same answers, same walks                          */
+  FW_FLAG_NO_HUB_SHARE = 256 /* eRVS steps over rows of 16,384 entries or more
+                             are scanned in fixed chunks from a phase-1
+                             reference; in launches of at most 1/8 of the
+                             resident lanes with forced eRVS, idle warps of a
+                             block help scan them (CTA-level sharing).  This
+                             flag keeps every such step on its own warp: same
+                             walks, no sharing                                  */
 };
 
 /* Parameters of one walk job.  Initialise with fw_params_default(). */

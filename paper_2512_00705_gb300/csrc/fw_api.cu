@@ -716,7 +716,9 @@ extern "C" fw_status fw_graph_check(fw_graph* g, void* stream) {
   if (e == cudaSuccess) e = cudaMemcpy(&bits, g->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemset(g->d_err, 0, sizeof(unsigned));
   if (e != cudaSuccess) return cuda_error(e, "check");
-  if (bits) return set_error(FW_ERR_DEVICE_CHECK, (bits & DEVERR_START) ? "a start node was outside [0, n)"
-                                                                       : "device check failed");
+  if (bits)
+    return set_error(FW_ERR_DEVICE_CHECK, (bits & DEVERR_START) ? "a start node was outside [0, n)"
+                                          : (bits & DEVERR_HUB) ? "a shared hub step did not complete in time"
+                                                                : "device check failed");
   return FW_OK;
 }

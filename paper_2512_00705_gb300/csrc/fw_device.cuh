@@ -42,7 +42,7 @@ enum : int32_t { MODE_AUTO = 0, MODE_RJS = 1, MODE_RVS = 2, MODE_EXACT = 3, MODE
 constexpr int32_t kDegreeRuleThreshold = 1000;  // Sec. 5.4 degree-based selection
 enum : int32_t { JOB_WALK = 0, JOB_HIST = 1 };
 enum : int32_t { PLAN_NONE = 0, PLAN_RJS = 1, PLAN_RVS_T = 2, PLAN_RVS_W = 3, PLAN_EXACT_T = 4, PLAN_EXACT_W = 5 };
-enum : uint32_t { DEVERR_START = 1u };
+enum : uint32_t { DEVERR_START = 1u, DEVERR_HUB = 2u };
 
 struct DevGraph {
   const int32_t* __restrict__ off;
@@ -805,18 +805,40 @@ __device__ __forceinline__ int32_t phase1_items(int32_t d, int T) {
   return T == 1 ? 1 : min(kPhase1Max, max(1, per / 8));
 }
 
+// Counting build: a lane's share of an eRVS scan (summed over the lanes
+// they give the step's totals).
+template <int ALG, bool GRP>
+__device__ __forceinline__ void rvs_count(const Job& J, int32_t scanned, int32_t keys, uint32_t probes,
+                                          LaneCounters& lc) {
+  lc.rvs_items += scanned;
+  lc.rvs_keys += keys;
+  lc.probes += probes;
+  const int per = GRP ? (J.weighted ? 4 : 0)
+                      : ((FW_ALGO(J) == ALGO_NODE2VEC) ? (J.weighted ? 8 : 4)
+                                                       : (FW_ALGO(J) == ALGO_METAPATH ? (J.weighted ? 5 : 1)
+                                                                                      : (J.weighted ? 4 : 0)));
+  lc.bytes += (unsigned long long)scanned * per + 32ull * probes;
+}
+
+// The scan of positions [lo, hi) of the row: lane `lane` of T takes
+// lo + lane, lo + lane + T, ...; phase 1 and the jumps as described above,
+// with the reference taken over these T lanes.  Leaves the lane's best key
+// and position in bestK / best (before any argmax over lanes).  Draws are
+// keyed by the absolute position, so a range's result does not depend on
+// which lanes or warps scan the other ranges.
 template <int T, bool COUNT, int ALG = -1, bool GRP = false>
-__device__ __forceinline__ int32_t rvs_pick(const DevGraph& g, const Job& J, const StepCtx& c, int lane, bool jump,
-                                            LaneCounters& lc) {
+__device__ __forceinline__ void rvs_scan(const DevGraph& g, const Job& J, const StepCtx& c, int32_t lo, int32_t hi,
+                                         int lane, bool jump, LaneCounters& lc, float& bestK, int32_t& best) {
   uint32_t probes = 0;
-  float bestK = -CUDART_INF_F;
-  int32_t best = -1;
+  bestK = -CUDART_INF_F;
+  best = -1;
   uint32_t xz = 0;
   int32_t scanned = 0, keys = 0;
-  const int32_t m = phase1_items(c.d, T);
+  const int32_t n = hi - lo;
+  const int32_t m = phase1_items(n, T);
   for (int32_t j = 0; j < m; ++j) {
-    const int32_t k = lane + T * j;
-    if (k >= c.d) break;
+    const int32_t k = lo + lane + T * j;
+    if (k >= hi) break;
     const float wt = scan_weight<ALG, GRP>(g, J, c, c.s + k, probes);
     const uint4 x = philox(make_uint4(c.wid, (uint32_t)c.step, 2u, (uint32_t)k), J.key0, J.key1);
     xz = x.z;  // unused by a phase-1 key: the lane's first jump threshold
@@ -830,12 +852,12 @@ __device__ __forceinline__ int32_t rvs_pick(const DevGraph& g, const Job& J, con
       }
     }
   }
-  if (c.d > T * m) {
+  if (n > T * m) {
     float ref = bestK;
     if (T > 1) ref = warp_max(bestK);
     // remaining weight before the next crossing; K_ref = -inf: first positive item crosses
     float rem = (ref == -CUDART_INF_F) ? 0.0f : ((ref < 0.0f) ? logf(u01_open(xz)) / ref : CUDART_INF_F);
-    for (int32_t k = lane + T * m; k < c.d; k += T) {
+    for (int32_t k = lo + lane + T * m; k < hi; k += T) {
       const float wt = scan_weight<ALG, GRP>(g, J, c, c.s + k, probes);
       ++scanned;
       if (!(wt > 0.0f)) continue;
@@ -863,18 +885,16 @@ __device__ __forceinline__ int32_t rvs_pick(const DevGraph& g, const Job& J, con
       }
     }
   }
+  if (COUNT) rvs_count<ALG, GRP>(J, scanned, keys, probes, lc);
+}
+
+template <int T, bool COUNT, int ALG = -1, bool GRP = false>
+__device__ __forceinline__ int32_t rvs_pick(const DevGraph& g, const Job& J, const StepCtx& c, int lane, bool jump,
+                                            LaneCounters& lc) {
+  float bestK;
+  int32_t best;
+  rvs_scan<T, COUNT, ALG, GRP>(g, J, c, 0, c.d, lane, jump, lc, bestK, best);
   if (T > 1) warp_argmax(bestK, best);
-  if (COUNT) {
-    // per-lane shares; summed over the T lanes they give the step's totals
-    lc.rvs_items += scanned;
-    lc.rvs_keys += keys;
-    lc.probes += probes;
-    const int per = GRP ? (J.weighted ? 4 : 0)
-                        : ((FW_ALGO(J) == ALGO_NODE2VEC) ? (J.weighted ? 8 : 4)
-                                                         : (FW_ALGO(J) == ALGO_METAPATH ? (J.weighted ? 5 : 1)
-                                                                                        : (J.weighted ? 4 : 0)));
-    lc.bytes += (unsigned long long)scanned * per + 32ull * probes;
-  }
   return (bestK == -CUDART_INF_F) ? -1 : best;
 }
 

@@ -12,12 +12,12 @@
 namespace fw {
 
 
-template <bool COUNT>
+template <bool COUNT, bool SHARE = false>
 static cudaError_t prime_single(int* b) {
-  cudaError_t e = walk_blocks_per_sm<1, COUNT, ALGO_WEIGHTED>(b);
-  if (e == cudaSuccess) e = walk_blocks_per_sm<1, COUNT, ALGO_NODE2VEC>(b);
-  if (e == cudaSuccess) e = walk_blocks_per_sm<1, COUNT, ALGO_METAPATH>(b);
-  if (e == cudaSuccess) e = walk_blocks_per_sm<1, COUNT, ALGO_PAGERANK2>(b);
+  cudaError_t e = walk_blocks_per_sm<1, COUNT, ALGO_WEIGHTED, SHARE>(b);
+  if (e == cudaSuccess) e = walk_blocks_per_sm<1, COUNT, ALGO_NODE2VEC, SHARE>(b);
+  if (e == cudaSuccess) e = walk_blocks_per_sm<1, COUNT, ALGO_METAPATH, SHARE>(b);
+  if (e == cudaSuccess) e = walk_blocks_per_sm<1, COUNT, ALGO_PAGERANK2, SHARE>(b);
   return e;
 }
 
@@ -25,6 +25,7 @@ cudaError_t prime_walk_occupancy() {
   int b;
   cudaError_t e = prime_single<false>(&b);
   if (e == cudaSuccess) e = prime_single<true>(&b);
+  if (e == cudaSuccess) e = prime_single<false, true>(&b);
   if (e == cudaSuccess) e = prime_walk_mixed_occupancy();
   return e;
 }

@@ -15,9 +15,12 @@
 //   * eRVS / exact  [Sec. 3.2, Sec. 5.2]: steps of degree <= a small threshold
 //                   run on their own lane; larger ones are handed to the whole
 //                   warp one at a time (shuffle of the walker's state), and
-//                   the result goes back to the owning lane.
+//                   the result goes back to the owning lane; hub rows
+//                   (d >= kHubMinDeg) are cut into chunks that every warp of
+//                   the block scans (CTA-level parallel jumps, see hub steps).
 //   * update        [Sec. 4.2, update()]: prev <- cur, cur <- next, row write.
-// All loops are bounded (trial cap, degree, walk length); there are no waits.
+// All loops are bounded (trial cap, degree, walk length, hub wait limit); no
+// warp waits on another.
 #pragma once
 
 #include "fw_internal.h"
@@ -87,15 +90,325 @@ struct JobTableN {
   Job jobs[NJ];
 };
 
+// ---------------------------------------------------------------- hub steps
+// An eRVS step of degree >= kHubMinDeg is shared by the warps of the block
+// (the parallel jump process of Sec. 3.2 at CTA level).  The warp that owns
+// the step keys the row's first kHubPhase1 positions (phase 1, the draws of
+// the warp scan), and their maximum key K_g becomes the reference from which
+// every other position is reached by jumps.  Those positions are cut into
+// chunks of kHubChunk; inside a chunk, lane l scans lo + l, lo + l + 32, ...
+// and starts with its own jump threshold, drawn from counter (walker, hop,
+// 5, lo + l); crossings draw as in the warp scan.  A chunk's keys therefore
+// depend on its positions and K_g alone, so the result is the same whether
+// the owning warp scans every chunk itself or the block shares them, and
+// whatever warp scans which chunk when.
+//
+// Sharing: the owning warp posts the step to a free slot of the block's task
+// table in shared memory (else it scans the chunks alone).  A warp that
+// looks (see the walk loop: warps with a waiting lane, and warps whose queue
+// ran dry) claims the next chunk of an open task, scans it and enters the
+// chunk's best (key, position) by one 64-bit atomicMax on the pair packed in
+// key order (equal keys: the larger position, as in warp_argmax), then
+// counts the chunk done.  The owning lane takes the result once every chunk
+// is done; its warp keeps walking its other lanes and claims chunks itself,
+// so no warp waits on another and a task completes even when no other warp
+// helps.  Busy warps do not look: with every lane walking, sharing would
+// move work between warps without shortening the launch, and the check
+// itself costs time on every iteration.
+constexpr int32_t kHubMinDeg = 16384;            // eRVS steps of at least this degree are shared
+constexpr int32_t kHubPhase1 = 32 * kPhase1Max;  // positions keyed in phase 1 (the warp scan's)
+constexpr int32_t kHubChunk = 2048;              // positions per chunk (64 per lane)
+constexpr int kHubTasks = 4;                     // open hub steps per block
+constexpr int32_t kHubMaxChunks = 1 << 19;       // the 20-bit chunk counter never wraps
+constexpr uint32_t kHubWaitLimit = 1u << 24;     // loop iterations a lane waits for its step at most
+// slot word: state (2 bits) | generation (10 bits) | next unclaimed chunk (20 bits)
+constexpr uint32_t kHubFree = 0u, kHubReserved = 1u, kHubOpen = 2u;
+constexpr uint32_t kHubGenMask = 0x3ff00000u, kHubNextMask = 0x000fffffu;
+
+struct HubTask {
+  uint32_t word;
+  int32_t nchunks;
+  int32_t done;              // chunks scanned
+  int32_t job;
+  unsigned long long best;   // packed (ordered key, position) of the best key so far; 0: none
+  float ref;                 // K_g: the phase-1 maximum key
+  int32_t grp;               // grouped metapath: c.s, c.d are the label segment
+  StepCtx c;
+};
+
+struct HubBlock {  // shared memory, per block
+  HubTask task[kHubTasks];
+  int32_t open;    // tasks with chunks left to claim
+  int32_t live;    // warps of the block still walking (the others linger to help)
+};
+constexpr uint32_t kLingerLimit = 1u << 22;  // idle checks of a lingering warp at most
+
+// float key -> unsigned in the same order (no NaN keys arise)
+__device__ __forceinline__ uint32_t key_order(float k) {
+  const uint32_t u = __float_as_uint(k);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ unsigned long long key_pack(float k, int32_t pos) {
+  return (k == -CUDART_INF_F) ? 0ull : (((unsigned long long)key_order(k) << 32) | (uint32_t)pos);
+}
+
+__device__ __forceinline__ int32_t hub_chunks(int32_t d) { return (d - kHubPhase1 + kHubChunk - 1) / kHubChunk; }
+
+// Phase 1 of a hub step (the whole warp): keys of positions lane + 32 j,
+// j < kPhase1Max.  Leaves the lane's best in bestK / best.
+template <bool COUNT, int ALG, bool GRP>
+__device__ __forceinline__ void hub_phase1(const DevGraph& g, const Job& J, const StepCtx& c, int lane,
+                                           LaneCounters& lc, float& bestK, int32_t& best) {
+  uint32_t probes = 0;
+  bestK = -CUDART_INF_F;
+  best = -1;
+  int32_t keys = 0;
+#pragma unroll 1
+  for (int32_t j = 0; j < kPhase1Max; ++j) {
+    const int32_t k = lane + 32 * j;
+    const float wt = scan_weight<ALG, GRP>(g, J, c, c.s + k, probes);
+    if (wt > 0.0f) {
+      const uint4 x = philox(make_uint4(c.wid, (uint32_t)c.step, 2u, (uint32_t)k), J.key0, J.key1);
+      const float K = logf(u01_open(x.x)) / wt;
+      ++keys;
+      if (K >= bestK) {
+        bestK = K;
+        best = k;
+      }
+    }
+  }
+  if (COUNT) rvs_count<ALG, GRP>(J, kPhase1Max, keys, probes, lc);
+}
+
+// Chunk [lo, hi) of a hub step (the whole warp): jumps from K_g = ref with
+// per-lane thresholds from counter stream 5 (without jumps: every key, as in
+// the warp scan).  Leaves the lane's best in bestK / best.
+template <bool COUNT, int ALG, bool GRP>
+__device__ __forceinline__ void hub_chunk_scan(const DevGraph& g, const Job& J, const StepCtx& c, int32_t lo,
+                                               int32_t hi, float ref, bool jump, int lane, LaneCounters& lc,
+                                               float& bestK, int32_t& best) {
+  uint32_t probes = 0;
+  int32_t scanned = 0, keys = 0;
+  bestK = -CUDART_INF_F;
+  best = -1;
+  float r = ref, rem = 0.0f;  // K_g = -inf: the first positive item crosses
+  if (jump && r != -CUDART_INF_F) {
+    const uint4 x0 = philox(make_uint4(c.wid, (uint32_t)c.step, 5u, (uint32_t)(lo + lane)), J.key0, J.key1);
+    rem = (r < 0.0f) ? logf(u01_open(x0.x)) / r : CUDART_INF_F;
+  }
+  for (int32_t k = lo + lane; k < hi; k += 32) {
+    const float wt = scan_weight<ALG, GRP>(g, J, c, c.s + k, probes);
+    ++scanned;
+    if (!(wt > 0.0f)) continue;
+    if (!jump) {
+      const uint4 x = philox(make_uint4(c.wid, (uint32_t)c.step, 2u, (uint32_t)k), J.key0, J.key1);
+      const float K = logf(u01_open(x.x)) / wt;
+      ++keys;
+      if (K >= bestK) {
+        bestK = K;
+        best = k;
+      }
+    } else {
+      rem -= wt;
+      if (rem <= 0.0f) {
+        const uint4 x = philox(make_uint4(c.wid, (uint32_t)c.step, 2u, (uint32_t)k), J.key0, J.key1);
+        // key conditioned on beating r: u' ~ U(exp(r*wt), 1), K = ln(u') / wt
+        const float K = log1pf(expm1f(r * wt) * u01_open(x.y)) / wt;
+        ++keys;
+        bestK = K;
+        best = k;
+        r = K;
+        rem = (r < 0.0f) ? logf(u01_open(x.z)) / r : CUDART_INF_F;
+      }
+    }
+  }
+  if (COUNT) rvs_count<ALG, GRP>(J, scanned, keys, probes, lc);
+}
+
+// Post a hub step (one lane); -1: every slot taken.
+__device__ __forceinline__ int hub_post(HubBlock* hb, const StepCtx& c, int32_t job, bool grp, float ref,
+                                        unsigned long long best) {
+  for (int i = 0; i < kHubTasks; ++i) {
+    HubTask& t = hb->task[i];
+    const uint32_t w = *reinterpret_cast<volatile uint32_t*>(&t.word);
+    if ((w >> 30) != kHubFree) continue;
+    if (atomicCAS(&t.word, w, (kHubReserved << 30) | (w & kHubGenMask)) != w) continue;
+    t.c = c;
+    t.job = job;
+    t.grp = grp ? 1 : 0;
+    t.ref = ref;
+    t.nchunks = hub_chunks(c.d);
+    t.done = 0;
+    t.best = best;
+    __threadfence_block();  // the fields before the slot opens
+    const uint32_t gen = ((w >> 20) + 1u) & 0x3ffu;
+    atomicExch(&t.word, (kHubOpen << 30) | (gen << 20));
+    atomicAdd(&hb->open, 1);
+    return i;
+  }
+  return -1;
+}
+
+// Claim the next unclaimed chunk of the open task in `slot` (one lane);
+// false: none left.  The compare-and-swap against the word read fails if
+// the slot was claimed, closed or reopened meanwhile, so a successful claim
+// also vouches for the chunk count read before it.  Taking a task's last
+// chunk closes it for the lingering warps' check.
+__device__ __forceinline__ bool hub_claim_slot(HubBlock* hb, int slot, int32_t& chunk) {
+  HubTask& t = hb->task[slot];
+  uint32_t w = *reinterpret_cast<volatile uint32_t*>(&t.word);
+  for (int tries = 0; tries < 64 && (w >> 30) == kHubOpen; ++tries) {
+    const int32_t nc = *reinterpret_cast<volatile int32_t*>(&t.nchunks);
+    const int32_t nx = (int32_t)(w & kHubNextMask);
+    if (nx >= nc) return false;
+    const uint32_t old = atomicCAS(&t.word, w, w + 1u);
+    if (old == w) {
+      if (nx + 1 == nc) atomicSub(&hb->open, 1);
+      chunk = nx;
+      return true;
+    }
+    w = old;
+  }
+  return false;
+}
+
+// Scan claimed chunk `chunk` of the task in `slot` (the whole warp,
+// converged), enter its best and count it done.
+template <bool COUNT, int ALG>
+__device__ __forceinline__ void hub_scan_claimed(const DevGraph& g, const Job* sj, HubBlock* hb, int slot,
+                                                 int32_t chunk, LaneCounters& lc) {
+  const int lane = threadIdx.x & 31;
+  HubTask& t = hb->task[slot];  // fixed until this chunk is counted done
+  StepCtx hc;
+  const volatile int32_t* src = reinterpret_cast<const volatile int32_t*>(&t.c);
+  int32_t* dst = reinterpret_cast<int32_t*>(&hc);
+#pragma unroll
+  for (int q = 0; q < (int)(sizeof(StepCtx) / 4); ++q) dst[q] = src[q];
+  const Job& J = sj[*reinterpret_cast<volatile int32_t*>(&t.job)];
+  const float ref = *reinterpret_cast<volatile float*>(&t.ref);
+  const int32_t lo = kHubPhase1 + chunk * kHubChunk, hi = min(hc.d, lo + kHubChunk);
+  const bool jump = !(J.flags & FW_FLAG_RVS_NOJUMP);
+  float bk;
+  int32_t bi;
+  if (ALG == ALGO_METAPATH && *reinterpret_cast<volatile int32_t*>(&t.grp) != 0)
+    hub_chunk_scan<COUNT, ALG, true>(g, J, hc, lo, hi, ref, jump, lane, lc, bk, bi);
+  else
+    hub_chunk_scan<COUNT, ALG, false>(g, J, hc, lo, hi, ref, jump, lane, lc, bk, bi);
+  warp_argmax(bk, bi);
+  if (lane == 0) {
+    if (bk != -CUDART_INF_F) atomicMax(&t.best, key_pack(bk, bi));
+    __threadfence_block();  // the result before the chunk counts as done
+    atomicAdd(&t.done, 1);
+  }
+  __syncwarp();
+}
+
+// A lingering warp (converged, no walker left): claim and scan one chunk of
+// any open task of the block.  Returns whether a chunk was scanned.
+template <bool COUNT, int ALG>
+__device__ __forceinline__ bool hub_help(const DevGraph& g, const Job* sj, HubBlock* hb, LaneCounters& lc) {
+  const int lane = threadIdx.x & 31;
+  if (__shfl_sync(kFull, *reinterpret_cast<volatile int32_t*>(&hb->open), 0) <= 0) return false;
+  int32_t chunk = 0;
+  int slot = -1;
+  if (lane == 0) {
+    for (int i = 0; i < kHubTasks && slot < 0; ++i)
+      if (hub_claim_slot(hb, i, chunk)) slot = i;
+  }
+  slot = __shfl_sync(kFull, slot, 0);
+  if (slot < 0) return false;
+  chunk = __shfl_sync(kFull, chunk, 0);
+  __syncwarp();
+  hub_scan_claimed<COUNT, ALG>(g, sj, hb, slot, chunk, lc);
+  return true;
+}
+
+// A hub step (the whole warp, converged; cw, JW: the step and its job, jb
+// its index, grp: grouped metapath).  Phase 1; then, when a warp of the
+// block lingers to help, the step is posted and this warp claims and scans
+// chunks alongside the helpers until none is left, waits for the chunks the
+// helpers hold (they wait on nothing) and frees the slot; otherwise it scans
+// every chunk alone (always, without SHARE).  Returns the position (-1: all
+// weights zero, or the join wait ran out, which also sets DEVERR_HUB).
+template <bool COUNT, int ALG, bool SHARE>
+__device__ __forceinline__ int32_t hub_step(const DevGraph& g, const Job* sj, const Job& JW, const StepCtx& cw,
+                                            int32_t jb, bool grp, HubBlock* hb, unsigned* err, LaneCounters& lc) {
+  const int lane = threadIdx.x & 31;
+  float bk;
+  int32_t bi;
+  if (ALG == ALGO_METAPATH && grp) hub_phase1<COUNT, ALG, true>(g, JW, cw, lane, lc, bk, bi);
+  else hub_phase1<COUNT, ALG, false>(g, JW, cw, lane, lc, bk, bi);
+  const float ref = warp_max(bk);
+  warp_argmax(bk, bi);
+  int slot = -1;
+  if (SHARE && lane == 0 && *reinterpret_cast<volatile int32_t*>(&hb->live) < (int32_t)(blockDim.x >> 5))
+    slot = hub_post(hb, cw, jb, grp, ref, key_pack(bk, bi));
+  if (SHARE) slot = __shfl_sync(kFull, slot, 0);
+  if (SHARE && slot >= 0) {
+    HubTask& t = hb->task[slot];
+    while (true) {
+      int32_t chunk = 0;
+      bool got = false;
+      if (lane == 0) got = hub_claim_slot(hb, slot, chunk);
+      if (!__shfl_sync(kFull, (int)got, 0)) break;
+      chunk = __shfl_sync(kFull, chunk, 0);
+      __syncwarp();
+      hub_scan_claimed<COUNT, ALG>(g, sj, hb, slot, chunk, lc);
+    }
+    // join: the helpers finish the chunks they claimed
+    bool ok = false;
+    if (lane == 0) {
+      const int32_t nc = t.nchunks;
+      for (uint32_t it = 0; it < kHubWaitLimit; ++it) {
+        if (*reinterpret_cast<volatile int32_t*>(&t.done) >= nc) {
+          ok = true;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    ok = __shfl_sync(kFull, (int)ok, 0) != 0;
+    if (!ok) {
+      if (lane == 0) atomicOr(err, DEVERR_HUB);  // the slot stays taken
+      return -1;
+    }
+    __threadfence_block();
+    const unsigned long long r = *reinterpret_cast<volatile unsigned long long*>(&t.best);
+    __syncwarp();
+    if (lane == 0) {
+      const uint32_t wd = *reinterpret_cast<volatile uint32_t*>(&t.word);
+      atomicExch(&t.word, wd & kHubGenMask);  // free, keeping the generation
+    }
+    return r ? (int32_t)(uint32_t)r : -1;
+  }
+  const bool jump = !(JW.flags & FW_FLAG_RVS_NOJUMP);
+  const int32_t nch = hub_chunks(cw.d);
+  for (int32_t q = 0; q < nch; ++q) {
+    const int32_t lo = kHubPhase1 + q * kHubChunk, hi = min(cw.d, lo + kHubChunk);
+    float ck;
+    int32_t ci;
+    if (ALG == ALGO_METAPATH && grp) hub_chunk_scan<COUNT, ALG, true>(g, JW, cw, lo, hi, ref, jump, lane, lc, ck, ci);
+    else hub_chunk_scan<COUNT, ALG, false>(g, JW, cw, lo, hi, ref, jump, lane, lc, ck, ci);
+    warp_argmax(ck, ci);
+    if (ck > bk || (ck == bk && ci > bi)) {
+      bk = ck;
+      bi = ci;
+    }
+  }
+  return (bk == -CUDART_INF_F) ? -1 : bi;
+}
+
 // The walk loop of one warp over one queue: take walkers, plan, sample and
 // write rows until the queue is exhausted and the warp holds no walker.
 // `sj` (shared memory) is the queue's job table: its jobs' walkers form the
 // index space [0, total), job j owning [sj[j].gbase, sj[j].gbase + W_j).
-// ALG fixes the algorithm of every job at compile time.
-template <bool COUNT, int ALG>
+// ALG fixes the algorithm of every job at compile time; SHARE: hub steps
+// may be shared with the block's idle warps (see hub steps).
+template <bool COUNT, int ALG, bool SHARE>
 __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int njobs, long long total,
                                           unsigned long long* __restrict__ qctr, unsigned* __restrict__ err,
-                                          int32_t* obuf, LaneCounters& lc) {
+                                          int32_t* obuf, HubBlock* hb, LaneCounters& lc) {
   static_assert(ALG >= 0 && ALG < kAlgos, "the walk loop is compiled for one algorithm");
   const int lane = threadIdx.x & 31;
   const int tid = threadIdx.x;
@@ -437,9 +750,17 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
       if (ALG == ALGO_METAPATH) wg = __shfl_sync(kFull, (int)grp, src) != 0;
       const Job& JW = sj[jb];
       int32_t k;
+      const int32_t hd = (ALG == ALGO_METAPATH && wg) ? w.pe - w.ps : w.d;
       if (pl == PLAN_EXACT_W) {
         const float u = u01(philox(make_uint4(w.wid, (uint32_t)w.step, 0u, 0u), JW.key0, JW.key1).x);
         k = exact_pick<32, COUNT, ALG>(g, JW, w, lane, u, lc);
+      } else if (hd >= kHubMinDeg && hub_chunks(hd) <= kHubMaxChunks) {
+        StepCtx cw = w;
+        if (ALG == ALGO_METAPATH && wg) {
+          cw.s = w.ps;
+          cw.d = hd;
+        }
+        k = hub_step<COUNT, ALG, SHARE>(g, sj, JW, cw, jb, wg, hb, err, lc);
       } else if (ALG == ALGO_METAPATH && wg) {
         StepCtx cg = w;
         cg.s = w.ps;
@@ -503,6 +824,20 @@ __device__ __forceinline__ void walk_loop(const DevGraph& g, const Job* sj, int 
   }
 }
 
+// A warp with no walker left stops counting among the block's walking warps
+// and, while any still walk, scans chunks of their hub steps (sleeping
+// between checks).  Lingering is optional help: nothing waits for it, and the
+// bound only caps how long a warp stays.
+template <bool COUNT, int ALG>
+__device__ __forceinline__ void hub_linger(const DevGraph& g, const Job* sj, HubBlock* hb, LaneCounters& lc) {
+  if ((threadIdx.x & 31) == 0) atomicSub(&hb->live, 1);
+  for (uint32_t it = 0; it < kLingerLimit; ++it) {
+    if (hub_help<COUNT, ALG>(g, sj, hb, lc)) continue;
+    if (__shfl_sync(kFull, *reinterpret_cast<volatile int32_t*>(&hb->live), 0) <= 0) break;
+    __nanosleep(256);
+  }
+}
+
 // Per-warp sums of the lane counters, added once to the device counters.
 __device__ __forceinline__ void flush_counters(const LaneCounters& lc, DevCounters* cnt) {
   const int lane = threadIdx.x & 31;
@@ -528,33 +863,57 @@ __device__ __forceinline__ void load_jobs(const Job* src_jobs, int njobs, Job* s
 }
 
 // Single-job (or one-algorithm) launch: the job table in shared memory, one
-// walk loop per warp over the launch's queue.
-template <int NJ, bool COUNT, int ALG>
+// walk loop per warp over the launch's queue.  SHARE: idle warps linger to
+// help the block's hub steps.
+template <int NJ, bool COUNT, int ALG, bool SHARE = false>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) walk_kernel(DevGraph g, JobTableN<NJ> tab, int njobs, long long total,
                                                       unsigned long long* __restrict__ qctr,
                                                       unsigned* __restrict__ err, DevCounters* __restrict__ cnt) {
   __shared__ Job sj[NJ];
   __shared__ int32_t obuf[kStageSlots * kBlock];
+  __shared__ HubBlock hb;
   load_jobs(tab.jobs, njobs, sj);
+  if (SHARE && threadIdx.x < kHubTasks) hb.task[threadIdx.x].word = 0u;
+  if (SHARE && threadIdx.x == 0) {
+    hb.open = 0;
+    hb.live = (int32_t)(blockDim.x >> 5);
+  }
   __syncthreads();
   LaneCounters lc;
   lc.zero();
-  walk_loop<COUNT, ALG>(g, sj, njobs, total, qctr, err, obuf, lc);
+  walk_loop<COUNT, ALG, SHARE>(g, sj, njobs, total, qctr, err, obuf, &hb, lc);
+  if (SHARE) hub_linger<COUNT, ALG>(g, sj, &hb, lc);
   if (COUNT) flush_counters(lc, cnt);
 }
 
-template <int NJ, bool COUNT, int ALG>
+template <int NJ, bool COUNT, int ALG, bool SHARE = false>
 inline cudaError_t walk_blocks_per_sm(int* out) {
   static std::atomic<int> cached{0};
   int b = cached.load();
   if (b == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, walk_kernel<NJ, COUNT, ALG>, kBlock, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, walk_kernel<NJ, COUNT, ALG, SHARE>, kBlock, 0);
     if (e != cudaSuccess) return e;
     b = b > 0 ? b : 1;
     cached.store(b);
   }
   *out = b;
   return cudaSuccess;
+}
+
+// Hub sharing pays where warps would idle: launches that fill at most 1/8
+// of the resident lanes, with eRVS forced (in the cost model's choice hub
+// rows go to eRJS almost always) on a graph with hub rows.  The lingering
+// code costs the loop about 13 % per step (measured on R-MAT s22), so big
+// launches and the cost model's walks use the kernel without it; the rows
+// are the same either way.
+inline bool hub_share_pays(const fw_graph* g, const Job* jobs, int njobs, long long total, long long lanes) {
+  if (g->max_degree < kHubMinDeg || total * 8 > lanes) return false;
+  bool rvs = false;
+  for (int i = 0; i < njobs; ++i) {
+    if (jobs[i].flags & FW_FLAG_NO_HUB_SHARE) return false;
+    rvs = rvs || jobs[i].mode == MODE_RVS;
+  }
+  return rvs;
 }
 
 template <int NJ, bool COUNT, int ALG>
@@ -565,10 +924,22 @@ inline cudaError_t launch_walk_t(const fw_graph* g, const Job* jobs, int njobs, 
   if (oe != cudaSuccess) return oe;
   JobTableN<NJ> tab;
   for (int i = 0; i < njobs; ++i) tab.jobs[i] = jobs[i];
-  const long long want = (total + kBlock - 1) / kBlock;
   const long long cap = (long long)g->num_sms * blocks_per_sm;
-  const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
-  walk_kernel<NJ, COUNT, ALG><<<grid, kBlock, 0, stream>>>(dev_graph(g), tab, njobs, total, qctr, g->d_err, g->d_cnt);
+  if (!COUNT && hub_share_pays(g, jobs, njobs, total, cap * kBlock)) {
+    int bs = 1;
+    oe = walk_blocks_per_sm<NJ, false, ALG, true>(&bs);
+    if (oe != cudaSuccess) return oe;
+    // one warp's worth of walkers per block: the other warps of each block are free to help
+    const long long want = (total + 31) / 32, cs = (long long)g->num_sms * bs;
+    const int grid = (int)(want < cs ? (want > 0 ? want : 1) : cs);
+    walk_kernel<NJ, false, ALG, true><<<grid, kBlock, 0, stream>>>(dev_graph(g), tab, njobs, total, qctr, g->d_err,
+                                                                   g->d_cnt);
+  } else {
+    const long long want = (total + kBlock - 1) / kBlock;
+    const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
+    walk_kernel<NJ, COUNT, ALG><<<grid, kBlock, 0, stream>>>(dev_graph(g), tab, njobs, total, qctr, g->d_err,
+                                                             g->d_cnt);
+  }
   g_launches.fetch_add(1);
   return cudaGetLastError();
 }

@@ -28,12 +28,12 @@ cudaError_t launch_group(int a, const fw_graph* g, const Job* jobs, int njobs, l
   }
 }
 
-template <bool COUNT>
+template <bool COUNT, bool SHARE = false>
 cudaError_t prime_groups(int* b) {
-  cudaError_t e = walk_blocks_per_sm<kMaxJobs, COUNT, ALGO_WEIGHTED>(b);
-  if (e == cudaSuccess) e = walk_blocks_per_sm<kMaxJobs, COUNT, ALGO_NODE2VEC>(b);
-  if (e == cudaSuccess) e = walk_blocks_per_sm<kMaxJobs, COUNT, ALGO_METAPATH>(b);
-  if (e == cudaSuccess) e = walk_blocks_per_sm<kMaxJobs, COUNT, ALGO_PAGERANK2>(b);
+  cudaError_t e = walk_blocks_per_sm<kMaxJobs, COUNT, ALGO_WEIGHTED, SHARE>(b);
+  if (e == cudaSuccess) e = walk_blocks_per_sm<kMaxJobs, COUNT, ALGO_NODE2VEC, SHARE>(b);
+  if (e == cudaSuccess) e = walk_blocks_per_sm<kMaxJobs, COUNT, ALGO_METAPATH, SHARE>(b);
+  if (e == cudaSuccess) e = walk_blocks_per_sm<kMaxJobs, COUNT, ALGO_PAGERANK2, SHARE>(b);
   return e;
 }
 
@@ -43,6 +43,7 @@ cudaError_t prime_walk_mixed_occupancy() {
   int b;
   cudaError_t e = prime_groups<false>(&b);
   if (e == cudaSuccess) e = prime_groups<true>(&b);
+  if (e == cudaSuccess) e = prime_groups<false, true>(&b);
   return e;
 }
 

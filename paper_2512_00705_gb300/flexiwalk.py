@@ -20,7 +20,7 @@ from . import _build
 ALGO = {"weighted": 0, "node2vec": 1, "metapath": 2, "pagerank2": 3}
 MODE = {"auto": 0, "rjs": 1, "rvs": 2, "exact": 3, "random": 4, "degree": 5}
 FLAG_RVS_NOJUMP, FLAG_COUNTERS, FLAG_UNWEIGHTED, FLAG_PLAIN_RJS, FLAG_PAPER_SUM, FLAG_NO_BLOOM = 1, 2, 4, 8, 16, 32
-FLAG_NO_GROUPS, FLAG_NO_TABLE = 64, 128
+FLAG_NO_GROUPS, FLAG_NO_TABLE, FLAG_NO_HUB_SHARE = 64, 128, 256
 PTR_HOST, PTR_DEVICE = 0, 1
 STATUS = {0: "FW_OK", -1: "FW_ERR_ARG", -2: "FW_ERR_CSR", -3: "FW_ERR_OOM", -4: "FW_ERR_CUDA",
           -5: "FW_ERR_TIMEOUT", -6: "FW_ERR_DEVICE_CHECK", -7: "FW_ERR_BUSY", -8: "FW_ERR_UNSUPPORTED"}

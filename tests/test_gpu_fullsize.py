@@ -126,6 +126,57 @@ def test_hub_distributions_s22(s22, mode, flags):
         assert_follows(draw, probs, (mode, flags, v, vp, algo, p, q), ndraws)
 
 
+@pytest.mark.parametrize("algo,p,q,flags", [("weighted", 1.0, 1.0, 0), ("node2vec", 2.0, 0.5, 0),
+                                             ("node2vec", 0.25, 4.0, fw.FLAG_RVS_NOJUMP)])
+def test_hub_steps_same_rows_shared_or_alone(s22, algo, p, q, flags):
+    """eRVS steps at the largest hub (d = 162,957 >= the sharing threshold)
+    are scanned in fixed chunks from a phase-1 reference.  In a small launch
+    with forced eRVS, idle warps of a block help scan them (or the owning
+    warp scans alone when the block's task slots are taken); with
+    FW_FLAG_NO_HUB_SHARE every step stays on its warp, as in big launches.
+    4,096 walkers starting at the hub give the same rows either way, and the
+    first 16 walked one per launch give the same rows again."""
+    g, G = s22
+    hub = int(np.argmax(g.degrees()))
+    W, L = 4096, 3
+    starts = torch.full((W,), hub, dtype=torch.int32, device="cuda")
+    kw = dict(p=p, q=q, mode="rvs", seed=91)
+    shared = G.walk(starts, L, algo, flags=flags, **kw).cpu().numpy()
+    alone = G.walk(starts, L, algo, flags=flags | fw.FLAG_NO_HUB_SHARE, **kw).cpu().numpy()
+    assert np.all(shared[:, 1] >= 0)
+    assert np.array_equal(shared, alone), f"{(shared != alone).any(axis=1).sum()} rows differ"
+    for i in range(16):
+        one = G.walk(starts[i:i + 1], L, algo, walker_base=i, flags=flags, **kw).cpu().numpy()
+        assert np.array_equal(one[0], shared[i]), i
+    G.check()
+
+
+def test_hub_sharing_shortens_small_hub_walks(s22):
+    """32 walkers from the largest hub, 10 hops of forced eRVS: with the
+    block's idle warps helping, the launch takes well under the time of
+    every hub step on its own warp (same rows)."""
+    g, G = s22
+    hub = int(np.argmax(g.degrees()))
+    starts = torch.full((32,), hub, dtype=torch.int32, device="cuda")
+
+    def timed(flags):
+        out = G.walk(starts, 10, "node2vec", mode="rvs", seed=5, flags=flags)
+        ts = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            G.walk(starts, 10, "node2vec", mode="rvs", seed=5, flags=flags, out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return min(ts), out.cpu().numpy()
+
+    t_shared, rows_shared = timed(0)
+    t_alone, rows_alone = timed(fw.FLAG_NO_HUB_SHARE)
+    assert np.array_equal(rows_shared, rows_alone)
+    assert t_shared < 0.6 * t_alone, (t_shared, t_alone)
+
+
 @pytest.fixture(scope="module")
 def s23():
     g = synth.workload_graph("s23_meta")
