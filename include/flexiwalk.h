@@ -113,7 +113,7 @@ enum {
                              one 32-byte bucket per test in most cases) but
                              the Bloom filter and a search of the sorted row;
                              same answers, same walks                          */
-  FW_FLAG_NO_HUB_SHARE = 256 /* eRVS steps over rows of 16,384 entries or more
+  FW_FLAG_NO_HUB_SHARE = 256 /* eRVS steps over rows of 32,768 entries or more
                              are scanned in fixed chunks from a phase-1
                              reference; in launches of at most 1/8 of the
                              resident lanes with forced eRVS, idle warps of a

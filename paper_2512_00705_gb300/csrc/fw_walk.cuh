@@ -115,9 +115,10 @@ struct JobTableN {
 // helps.  Busy warps do not look: with every lane walking, sharing would
 // move work between warps without shortening the launch, and the check
 // itself costs time on every iteration.
-constexpr int32_t kHubMinDeg = 16384;            // eRVS steps of at least this degree are shared
-constexpr int32_t kHubPhase1 = 32 * kPhase1Max;  // positions keyed in phase 1 (the warp scan's)
-constexpr int32_t kHubChunk = 2048;              // positions per chunk (64 per lane)
+constexpr int32_t kHubMinDeg = 32768;            // eRVS steps of at least this degree are shared
+constexpr int32_t kHubPhase1Keys = 32;           // phase-1 keys per lane
+constexpr int32_t kHubPhase1 = 32 * kHubPhase1Keys;  // positions keyed in phase 1
+constexpr int32_t kHubChunk = 8192;              // positions per chunk (256 per lane)
 constexpr int kHubTasks = 4;                     // open hub steps per block
 constexpr int32_t kHubMaxChunks = 1 << 19;       // the 20-bit chunk counter never wraps
 constexpr uint32_t kHubWaitLimit = 1u << 24;     // loop iterations a lane waits for its step at most
@@ -156,7 +157,10 @@ __device__ __forceinline__ unsigned long long key_pack(float k, int32_t pos) {
 __device__ __forceinline__ int32_t hub_chunks(int32_t d) { return (d - kHubPhase1 + kHubChunk - 1) / kHubChunk; }
 
 // Phase 1 of a hub step (the whole warp): keys of positions lane + 32 j,
-// j < kPhase1Max.  Leaves the lane's best in bestK / best.
+// j < kHubPhase1Keys.  A chunk lane crosses K_g about ln(1 + n / kHubPhase1)
+// times over its n positions, every crossing a divergent key draw, so the
+// reference is taken over more positions than a warp scan's phase 1.
+// Leaves the lane's best in bestK / best.
 template <bool COUNT, int ALG, bool GRP>
 __device__ __forceinline__ void hub_phase1(const DevGraph& g, const Job& J, const StepCtx& c, int lane,
                                            LaneCounters& lc, float& bestK, int32_t& best) {
@@ -165,7 +169,7 @@ __device__ __forceinline__ void hub_phase1(const DevGraph& g, const Job& J, cons
   best = -1;
   int32_t keys = 0;
 #pragma unroll 1
-  for (int32_t j = 0; j < kPhase1Max; ++j) {
+  for (int32_t j = 0; j < kHubPhase1Keys; ++j) {
     const int32_t k = lane + 32 * j;
     const float wt = scan_weight<ALG, GRP>(g, J, c, c.s + k, probes);
     if (wt > 0.0f) {
@@ -178,7 +182,7 @@ __device__ __forceinline__ void hub_phase1(const DevGraph& g, const Job& J, cons
       }
     }
   }
-  if (COUNT) rvs_count<ALG, GRP>(J, kPhase1Max, keys, probes, lc);
+  if (COUNT) rvs_count<ALG, GRP>(J, kHubPhase1Keys, keys, probes, lc);
 }
 
 // Chunk [lo, hi) of a hub step (the whole warp): jumps from K_g = ref with

@@ -129,7 +129,7 @@ def test_hub_distributions_s22(s22, mode, flags):
 @pytest.mark.parametrize("algo,p,q,flags", [("weighted", 1.0, 1.0, 0), ("node2vec", 2.0, 0.5, 0),
                                              ("node2vec", 0.25, 4.0, fw.FLAG_RVS_NOJUMP)])
 def test_hub_steps_same_rows_shared_or_alone(s22, algo, p, q, flags):
-    """eRVS steps at the largest hub (d = 162,957 >= the sharing threshold)
+    """eRVS steps at the largest hub (d = 162,957, above the 32,768-entry threshold)
     are scanned in fixed chunks from a phase-1 reference.  In a small launch
     with forced eRVS, idle warps of a block help scan them (or the owning
     warp scans alone when the block's task slots are taken); with
