@@ -1084,7 +1084,7 @@ def main():
                                       if traffic_per_launch else None),
                      "traffic_frac": (traffic_per_launch / (kern_ms / len(PQ) / 1000.0) / 1e9 / peak
                                       if traffic_per_launch else None),
-                     "peak_kind": peak_kind, "kernel": "walk_kernel<1, 0, 1> (single job, uncounted, node2vec)",
+                     "peak_kind": peak_kind, "kernel": "walk_kernel<1, 0, 1, 0> (single job, uncounted, node2vec, no hub sharing)",
                      "algorithmic_bytes_per_launch": bytes_per_step / len(PQ),
                      "byte_model": "this engine's accesses: 32 B per node record, eRJS edge record and membership "
                                    "probe; 4 B per row entry; eRVS items 8 B",
