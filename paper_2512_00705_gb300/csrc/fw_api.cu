@@ -334,7 +334,8 @@ static void free_graph(fw_graph* g) {
   cudaFree(g->d_cnt);
   cudaFree(g->d_stage_starts);
   cudaFree(g->d_stage_out);
-  if (g->host_walk2) cudaStreamDestroy(g->host_walk2);
+  for (cudaStream_t w : g->host_walk)
+    if (w) cudaStreamDestroy(w);
   if (g->host_copy) cudaStreamDestroy(g->host_copy);
   for (cudaEvent_t ev : g->host_ev)
     if (ev) cudaEventDestroy(ev);
@@ -599,16 +600,19 @@ extern "C" fw_status fw_walk_host(fw_graph* g, const int32_t* starts, int32_t nu
     g->stage_out_cap = nout;
   }
   if (!g->host_copy) {
-    cudaError_t e = cudaStreamCreateWithFlags(&g->host_walk2, cudaStreamNonBlocking);
+    cudaError_t e = cudaSuccess;
+    for (cudaStream_t& w : g->host_walk)
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->host_copy, cudaStreamNonBlocking);
     for (int i = 0; i <= kHostChunksMax && e == cudaSuccess; ++i)
       e = cudaEventCreateWithFlags(&g->host_ev[i], cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_error(e, "create fw_walk_host streams");
   }
-  // Chunk c holds walkers [c*W/K, (c+1)*W/K).  Chunks are walked alternately
-  // on `stream` and a second stream (a chunk's last blocks share the GPU with
-  // the next chunk's first ones) and each chunk's rows are copied out on a
-  // third stream as soon as its walk ends.  Chunk c's walkers keep their
+  // Chunk c holds walkers [c*W/K, (c+1)*W/K).  Chunks are walked in turn on
+  // `stream` and kHostWalkStreams - 1 more streams, so that a chunk's tail
+  // (its last walkers, a few blocks busy for many hops) shares the GPU with
+  // the next chunks' bulk, and each chunk's rows are copied out on another
+  // stream as soon as its walk ends.  Chunk c's walkers keep their
   // random-stream ids walker_base + index, so the rows equal one fw_walk.
   const size_t bytes_out = nout * sizeof(int32_t);
   const int K = (int)std::min<size_t>((size_t)kHostChunksMax, std::max<size_t>(1, bytes_out / kHostChunkBytes));
@@ -616,14 +620,15 @@ extern "C" fw_status fw_walk_host(fw_graph* g, const int32_t* starts, int32_t nu
   cudaEvent_t* ev = g->host_ev;
   cudaError_t e = cudaMemcpyAsync(g->d_stage_starts, starts, nin * sizeof(int32_t), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaEventRecord(ev[kHostChunksMax], st);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(g->host_walk2, ev[kHostChunksMax], 0);
+  for (cudaStream_t w : g->host_walk)
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(w, ev[kHostChunksMax], 0);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(g->host_copy, ev[kHostChunksMax], 0);
   if (e != cudaSuccess) return cuda_error(e, "copy starts");
   s = FW_OK;
   for (int c = 0; c < K && s == FW_OK; ++c) {
     const size_t lo = nin * (size_t)c / (size_t)K, hi = nin * (size_t)(c + 1) / (size_t)K;
     if (hi == lo) continue;
-    cudaStream_t ws = (c & 1) ? g->host_walk2 : st;
+    cudaStream_t ws = (c % kHostWalkStreams) ? g->host_walk[c % kHostWalkStreams - 1] : st;
     Job Jc = J;
     Jc.kind = JOB_WALK;
     Jc.starts = g->d_stage_starts + lo;
@@ -645,7 +650,11 @@ extern "C" fw_status fw_walk_host(fw_graph* g, const int32_t* starts, int32_t nu
   cudaError_t e1 = cudaEventRecord(ev[kHostChunksMax], g->host_copy);
   if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(st, ev[kHostChunksMax], 0);
   cudaError_t e2 = cudaStreamSynchronize(g->host_copy);
-  cudaError_t e3 = cudaStreamSynchronize(g->host_walk2);
+  cudaError_t e3 = cudaSuccess;
+  for (cudaStream_t w : g->host_walk) {
+    const cudaError_t x = cudaStreamSynchronize(w);
+    if (e3 == cudaSuccess) e3 = x;
+  }
   cudaError_t e4 = cudaStreamSynchronize(st);
   if (s != FW_OK) return s;
   for (cudaError_t x : {e1, e2, e3, e4})

@@ -19,8 +19,9 @@
 //            first k with t < W_k (fallback: last k with w~_k > 0).
 // Random numbers come from Philox4x32-10 (Salmon et al., SC'11) keyed by the
 // walk seed with counter (walker id, hop, stream, draw); stream 0 is the exact
-// mode, 1 eRJS (draw = trial), 2 eRVS (draw = neighbour position).  No draw
-// depends on the lane, block or co-running walkers.
+// mode, 1 eRJS (draw = trial), 2 eRVS crossings (draw = neighbour position),
+// 5-7 eRVS jump thresholds and phase-1 keys (see rvs_scan and the hub
+// steps).  No draw depends on the lane, block or co-running walkers.
 #pragma once
 
 #include <cstdint>
@@ -781,8 +782,12 @@ __device__ __forceinline__ void warp_argmax(float& key, int32_t& idx) {
 // lane, see phase1_items); their maximum is the reference K_ref from which
 // every lane jumps over the rest of its own subsequence; the final argmax
 // over lanes picks the neighbour.  Counter
-// draws: (wid, hop, 2, k): x.x = phase-1 key, x.y = key at a crossing,
-// x.z = the lane's next jump threshold.  Returns position k or -1 (all
+// draws: phase 1 keys the lane's positions k, k+T, k+2T, k+3T from one block
+// (wid, hop, 6, k) (x.x .. x.w; a Philox block costs more than the key it
+// feeds, so one per four keys); the lane's first jump threshold is the
+// block's unused x.w when phase 1 ends inside a block, else x.x of
+// (wid, hop, 7, first position of the lane); a crossing at k draws
+// (wid, hop, 2, k): x.y = its key, x.z = the lane's next threshold.  Returns position k or -1 (all
 // weights zero: dead end).
 // GRP: scan the label-grouped h (c.s, c.d are a segment of the grouped
 // arrays, every entry of weight h); the result is a grouped position.
@@ -836,15 +841,16 @@ __device__ __forceinline__ void rvs_scan(const DevGraph& g, const Job& J, const 
   int32_t scanned = 0, keys = 0;
   const int32_t n = hi - lo;
   const int32_t m = phase1_items(n, T);
+  uint4 x4 = make_uint4(0u, 0u, 0u, 0u);
   for (int32_t j = 0; j < m; ++j) {
     const int32_t k = lo + lane + T * j;
     if (k >= hi) break;
     const float wt = scan_weight<ALG, GRP>(g, J, c, c.s + k, probes);
-    const uint4 x = philox(make_uint4(c.wid, (uint32_t)c.step, 2u, (uint32_t)k), J.key0, J.key1);
-    xz = x.z;  // unused by a phase-1 key: the lane's first jump threshold
+    if ((j & 3) == 0) x4 = philox(make_uint4(c.wid, (uint32_t)c.step, 6u, (uint32_t)k), J.key0, J.key1);
+    const uint32_t r = (j & 3) == 0 ? x4.x : ((j & 3) == 1 ? x4.y : ((j & 3) == 2 ? x4.z : x4.w));
     ++scanned;
     if (wt > 0.0f) {
-      const float K = logf(u01_open(x.x)) / wt;
+      const float K = logf(u01_open(r)) / wt;
       ++keys;
       if (K >= bestK) {
         bestK = K;
@@ -853,6 +859,9 @@ __device__ __forceinline__ void rvs_scan(const DevGraph& g, const Job& J, const 
     }
   }
   if (n > T * m) {
+    // the lane's first jump threshold: x.w of its last phase-1 block when that block fed fewer than four keys
+    if (jump)
+      xz = (m & 3) ? x4.w : philox(make_uint4(c.wid, (uint32_t)c.step, 7u, (uint32_t)(lo + lane)), J.key0, J.key1).x;
     float ref = bestK;
     if (T > 1) ref = warp_max(bestK);
     // remaining weight before the next crossing; K_ref = -inf: first positive item crosses

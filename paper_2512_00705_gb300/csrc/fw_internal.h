@@ -13,6 +13,7 @@
 
 // fw_walk_host splits large requests into at most this many chunks
 constexpr int kHostChunksMax = 16;
+constexpr int kHostWalkStreams = 4;  // fw_walk_host: chunks in flight (the caller's stream and 3 more)
 
 struct fw_graph {
   int device = 0;
@@ -58,7 +59,7 @@ struct fw_graph {
   int32_t* d_stage_out = nullptr;
   size_t stage_out_cap = 0;
   // pipelined fw_walk_host: a second walk stream, a copy stream and one event per chunk
-  cudaStream_t host_walk2 = nullptr;
+  cudaStream_t host_walk[kHostWalkStreams - 1] = {};  // fw_walk_host: walk streams beside the caller's
   cudaStream_t host_copy = nullptr;
   cudaEvent_t host_ev[kHostChunksMax + 1] = {};
 };

@@ -157,7 +157,7 @@ __device__ __forceinline__ unsigned long long key_pack(float k, int32_t pos) {
 __device__ __forceinline__ int32_t hub_chunks(int32_t d) { return (d - kHubPhase1 + kHubChunk - 1) / kHubChunk; }
 
 // Phase 1 of a hub step (the whole warp): keys of positions lane + 32 j,
-// j < kHubPhase1Keys.  A chunk lane crosses K_g about ln(1 + n / kHubPhase1)
+// j < kHubPhase1Keys, four per Philox block as in rvs_scan.  A chunk lane crosses K_g about ln(1 + n / kHubPhase1)
 // times over its n positions, every crossing a divergent key draw, so the
 // reference is taken over more positions than a warp scan's phase 1.
 // Leaves the lane's best in bestK / best.
@@ -168,13 +168,15 @@ __device__ __forceinline__ void hub_phase1(const DevGraph& g, const Job& J, cons
   bestK = -CUDART_INF_F;
   best = -1;
   int32_t keys = 0;
+  uint4 x4 = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll 1
   for (int32_t j = 0; j < kHubPhase1Keys; ++j) {
     const int32_t k = lane + 32 * j;
     const float wt = scan_weight<ALG, GRP>(g, J, c, c.s + k, probes);
+    if ((j & 3) == 0) x4 = philox(make_uint4(c.wid, (uint32_t)c.step, 6u, (uint32_t)k), J.key0, J.key1);
+    const uint32_t r = (j & 3) == 0 ? x4.x : ((j & 3) == 1 ? x4.y : ((j & 3) == 2 ? x4.z : x4.w));
     if (wt > 0.0f) {
-      const uint4 x = philox(make_uint4(c.wid, (uint32_t)c.step, 2u, (uint32_t)k), J.key0, J.key1);
-      const float K = logf(u01_open(x.x)) / wt;
+      const float K = logf(u01_open(r)) / wt;
       ++keys;
       if (K >= bestK) {
         bestK = K;
