@@ -474,7 +474,7 @@ class _ServeClient:
         algos = rng.integers(0, 3, n)
         return arrivals, W, Ls, algos
 
-    def run(self, mode, rate, duration, seed=45, max_waves=8, count=None):
+    def run(self, mode, rate, duration, seed=45, max_waves=8, count=None, large_query_steps=None):
         """Offer the query stream to the server (batched submit / poll calls,
         hops counted on the device) or to serial fw_walk_host calls."""
         from concurrent.futures import ThreadPoolExecutor
@@ -532,7 +532,7 @@ class _ServeClient:
             jobs = (fw.fw_job * count)()
             for i in range(count):
                 jobs[i] = fw.make_host_query(starts_v[i], int(Ls[i]), names[algos[i]], outs_v[i], **kw(i))
-            srv = fw.Server(self.G, mem_budget=8 << 30, max_waves=max_waves)
+            srv = fw.Server(self.G, mem_budget=8 << 30, max_waves=max_waves, large_query_steps=large_query_steps)
             jsize = ctypes.sizeof(fw.fw_job)
             tickets = np.zeros(count, dtype=np.uint64)
             lag = np.zeros(count)

@@ -441,8 +441,9 @@ fw_status fw_batch_plan_destroy(fw_batch_plan* plan);
  * Serving: continuous batching of walk queries against a resident graph.
  * A worker thread admits queued queries in arrival order while a fixed
  * device arena of mem_budget bytes has room for their staged starts and
- * rows, launches the admitted queries as one batched walk ("wave", up to
- * max_jobs_per_wave queries) on one of max_waves streams, and retires waves
+ * rows (small queries before large ones, see large_query_steps), launches
+ * the admitted queries as one batched walk ("wave", up to max_jobs_per_wave
+ * queries of one size class) on one of max_waves streams, and retires waves
  * by polling their completion events; queries that arrive while waves run
  * join the next wave, and waves on different streams overlap on the device.
  * Copies whose host and device ranges both continue the previous query's
@@ -457,6 +458,12 @@ typedef struct {
                                  rounded down to a multiple of 256)                   */
   int32_t max_waves;          /* concurrent waves / streams, 1..64 (default 4)          */
   int32_t max_jobs_per_wave;  /* queries per launch, 1..64 (default 64)                 */
+  int64_t large_query_steps;  /* queries with W x L at least this are "large": they get
+                                 waves of their own, small queries are admitted first
+                                 (a large one after waiting 100 ms goes first), and
+                                 large waves leave max(1, max_waves / 8) streams to
+                                 small ones; 0: one class, plain arrival order
+                                 (default)                                             */
 } fw_server_config;
 
 typedef struct {

@@ -5,11 +5,15 @@
 //   1. retires finished waves: polls each in-flight wave's completion event
 //      (cudaEventQuery, never a blocking wait), marks its queries done and
 //      returns their device memory to the arena;
-//   2. admits queries in arrival order while the device arena (the memory
-//      budget) has room for their staged starts and rows -- the head of the
-//      queue waits for memory rather than being overtaken, so large queries
-//      are not starved;
-//   3. launches the admitted queries as one wave on a free stream: upload of
+//   2. admits queries in arrival order within two size classes (small, and
+//      large: W x L at least large_query_steps) while the device arena (the
+//      memory budget) has room for their staged starts and rows; small
+//      queries go first, so a burst of large ones does not hold them up, and a
+//      large query that has waited kLargeAging goes first and, while it waits
+//      for memory, stops small admissions, so large queries are not starved;
+//   3. launches each class's admitted queries as one wave on a free stream
+//      (large waves leave an eighth of the streams, at least one, to small
+//      ones): upload of
 //      the queries' starts, one batched walk (up to 64 queries; one launch
 //      per algorithm present, side by side on the wave's helper streams,
 //      each algorithm's queries one shared walker queue, so the wave ends
@@ -62,6 +66,7 @@ struct Request {
   bool pinned_in = false, pinned_out = false;  // caller buffers page-locked (copied directly)
   Clock::time_point t_submit, t_launch, t_done;
   int state = REQ_PENDING;
+  int cls = 0;  // size class: 0 small, 1 large
   fw_status status = FW_OK;
   std::string error;
 };
@@ -155,6 +160,7 @@ struct Wave {
   unsigned long long* hops_host = nullptr;  // the wave's hop count, copied back (pinned host)
   std::vector<Request*> reqs;
   uint64_t copies = 0;  // starts and rows copies the wave enqueued (after merging)
+  int cls = 0;          // size class of the wave's queries
   bool busy = false;
 };
 
@@ -168,6 +174,8 @@ void destroy_wave(Wave& w) {
 }
 
 constexpr int kHopSlot = 8;  // index of the hop count in a wave's 256-byte counter block
+// A large query waiting longer than this is admitted before small ones.
+constexpr std::chrono::milliseconds kLargeAging{100};
 
 // Hops of a wave: row entries after the start column that hold a node (not
 // -1), over the rows of up to kMaxJobs queries; one atomic per warp.
@@ -205,8 +213,8 @@ struct fw_server {
   std::vector<Wave> waves;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
-  std::deque<Request*> pending;
-  std::vector<Request*> admitted;
+  std::deque<Request*> pending[2];     // per size class: 0 small, 1 large (W x L >= large_query_steps)
+  std::vector<Request*> admitted[2];   // the next wave of each class
   std::unordered_map<uint64_t, Request*> reqs;
   uint64_t next_id = 1;
   bool stop = false;
@@ -344,9 +352,10 @@ cudaError_t enqueue_wave(fw_server* s, Wave& w, const std::vector<Request*>& bat
 
 // Launch the admitted queries as one wave on the free wave w.  Called and
 // returns with the lock held; drops it around the CUDA calls.
-void launch_wave(fw_server* s, Wave& w, std::unique_lock<std::mutex>& lk) {
+void launch_wave(fw_server* s, Wave& w, int cls, std::unique_lock<std::mutex>& lk) {
   std::vector<Request*> batch;
-  batch.swap(s->admitted);
+  batch.swap(s->admitted[cls]);
+  w.cls = cls;
   const auto now = Clock::now();
   for (Request* r : batch) {
     r->state = REQ_LAUNCHED;
@@ -423,37 +432,57 @@ void worker_main(fw_server* s) {
       progress = true;
     }
     if (progress) s->cv_done.notify_all();
-    // 2. admit in arrival order while memory and the job table allow
-    while (!s->pending.empty() && (int)s->admitted.size() < s->cfg.max_jobs_per_wave) {
-      Request* r = s->pending.front();
-      size_t roff = s->rows_cursor, soff = 0;
-      if (!s->arena->alloc_at(roff, r->row_bytes) && !s->arena->alloc(r->row_bytes, &roff))
-        break;  // the head waits for memory
-      if (!s->arena->alloc_top(r->in_bytes, &soff)) {
-        s->arena->release(roff, r->row_bytes);
-        break;
+    // 2. admit in arrival order within each size class while memory and the
+    //    job table allow: small queries first, unless the oldest large query
+    //    has waited kLargeAging; then it goes first, and while it waits for
+    //    memory no small query is admitted (so large queries are not starved)
+    const bool large_first =
+        !s->pending[1].empty() && Clock::now() - s->pending[1].front()->t_submit > kLargeAging;
+    for (int pass = 0; pass < 2; ++pass) {
+      const int c = large_first ? 1 - pass : pass;
+      bool blocked = false;
+      while (!s->pending[c].empty() && (int)s->admitted[c].size() < s->cfg.max_jobs_per_wave) {
+        Request* r = s->pending[c].front();
+        size_t roff = s->rows_cursor, soff = 0;
+        if (!s->arena->alloc_at(roff, r->row_bytes) && !s->arena->alloc(r->row_bytes, &roff)) {
+          blocked = true;  // the head waits for memory
+          break;
+        }
+        if (!s->arena->alloc_top(r->in_bytes, &soff)) {
+          s->arena->release(roff, r->row_bytes);
+          blocked = true;
+          break;
+        }
+        r->rows_off = roff;
+        r->starts_off = soff;
+        s->rows_cursor = roff + r->row_bytes;
+        r->state = REQ_ADMITTED;
+        s->admitted[c].push_back(r);
+        s->pending[c].pop_front();
+        s->peak_arena = std::max(s->peak_arena, s->arena->used());
+        progress = true;
       }
-      r->rows_off = roff;
-      r->starts_off = soff;
-      s->rows_cursor = roff + r->row_bytes;
-      r->state = REQ_ADMITTED;
-      s->admitted.push_back(r);
-      s->pending.pop_front();
-      s->peak_arena = std::max(s->peak_arena, s->arena->used());
-      progress = true;
+      if (large_first && c == 1 && blocked) break;
     }
-    // 3. launch the admitted queries on a free stream
-    if (!s->admitted.empty()) {
+    // 3. launch each class's admitted queries on a free stream, small ones
+    //    first; large waves leave kSmallSlots of the streams to small ones
+    int large_busy = 0;
+    for (const Wave& w : s->waves) large_busy += (w.busy && w.cls == 1) ? 1 : 0;
+    const int small_slots = s->cfg.max_waves > 1 ? std::max(1, s->cfg.max_waves / 8) : 0;
+    for (int c = 0; c < 2; ++c) {
+      if (s->admitted[c].empty()) continue;
+      if (c == 1 && large_busy >= s->cfg.max_waves - small_slots) continue;
       for (Wave& w : s->waves) {
         if (w.busy) continue;
-        launch_wave(s, w, lk);
+        launch_wave(s, w, c, lk);
         if (w.busy) ++inflight;
         progress = true;
         break;
       }
     }
     s->peak_inflight = std::max(s->peak_inflight, inflight);
-    const bool idle = s->pending.empty() && s->admitted.empty() && inflight == 0;
+    const bool idle = s->pending[0].empty() && s->pending[1].empty() && s->admitted[0].empty() &&
+                      s->admitted[1].empty() && inflight == 0;
     if (s->stop && idle) break;
     if (!progress) {
       if (idle) s->cv_work.wait_for(lk, std::chrono::milliseconds(20));
@@ -471,6 +500,7 @@ extern "C" void fw_server_config_default(fw_server_config* c) {
   c->mem_budget = (size_t)1 << 30;
   c->max_waves = 4;
   c->max_jobs_per_wave = 64;
+  c->large_query_steps = 0;
 }
 
 extern "C" fw_status fw_server_create(const fw_graph* g, const fw_server_config* cfg, fw_server** out) {
@@ -481,7 +511,7 @@ extern "C" fw_status fw_server_create(const fw_graph* g, const fw_server_config*
   if (cfg) c = *cfg;
   else fw_server_config_default(&c);
   if (c.mem_budget < 4096 || c.max_waves < 1 || c.max_waves > 64 || c.max_jobs_per_wave < 1 ||
-      c.max_jobs_per_wave > kMaxJobs)
+      c.max_jobs_per_wave > kMaxJobs || c.large_query_steps < 0)
     return set_error(FW_ERR_ARG, "bad server configuration");
   c.mem_budget &= ~(size_t)255;  // whole 256-byte units: every arena offset stays 4-byte aligned
   cudaError_t e = prime_walk_occupancy();
@@ -577,6 +607,9 @@ static Request* new_request(fw_server* s, const int32_t* starts, int32_t num_wal
   if (params) r->params = *params;
   else fw_params_default(&r->params);
   r->seed = seed;
+  // size class: large queries (W x L >= large_query_steps; 0: none) get waves of their own
+  r->cls = (s->cfg.large_query_steps > 0 &&
+            (long long)num_walkers * (long long)len >= s->cfg.large_query_steps) ? 1 : 0;
   r->in_bytes = in_bytes;
   r->row_bytes = row_bytes * (size_t)num_walkers;
   r->pinned_in = host_pinned(starts);
@@ -600,7 +633,7 @@ static fw_status enqueue(fw_server* s, Request* const* rs, int32_t count, uint64
       if (r->num_walkers == 0) {
         finish(s, r, FW_OK, "");
       } else {
-        s->pending.push_back(r);
+        s->pending[r->cls].push_back(r);
       }
       s->reqs[r->id] = r;
       tickets[i] = r->id;
@@ -711,7 +744,7 @@ extern "C" fw_status fw_server_stats(fw_server* s, fw_server_stats_t* out) {
   std::memset(out, 0, sizeof(*out));
   out->completed = s->completed;
   out->failed = s->failed;
-  out->pending = s->pending.size() + s->admitted.size();
+  out->pending = s->pending[0].size() + s->pending[1].size() + s->admitted[0].size() + s->admitted[1].size();
   out->waves = s->waves_launched;
   out->queries_per_wave = s->waves_launched ? (double)s->queries_in_waves / (double)s->waves_launched : 0.0;
   out->peak_device_bytes = s->peak_arena;

@@ -55,7 +55,8 @@ class fw_job(ctypes.Structure):
 
 
 class fw_server_config(ctypes.Structure):
-    _fields_ = [("mem_budget", ctypes.c_size_t), ("max_waves", ctypes.c_int32), ("max_jobs_per_wave", ctypes.c_int32)]
+    _fields_ = [("mem_budget", ctypes.c_size_t), ("max_waves", ctypes.c_int32), ("max_jobs_per_wave", ctypes.c_int32),
+                ("large_query_steps", ctypes.c_int64)]
 
 
 class fw_server_stats_t(ctypes.Structure):
@@ -487,10 +488,13 @@ class BatchPlan:
 class Server:
     """Continuous-batching walk server over a resident Graph (C ABI fw_server_*)."""
 
-    def __init__(self, graph: "Graph", mem_budget: int = 1 << 30, max_waves: int = 4, max_jobs_per_wave: int = 64):
+    def __init__(self, graph: "Graph", mem_budget: int = 1 << 30, max_waves: int = 4, max_jobs_per_wave: int = 64,
+                 large_query_steps: Optional[int] = None):
         cfg = fw_server_config()
         lib().fw_server_config_default(ctypes.byref(cfg))
         cfg.mem_budget, cfg.max_waves, cfg.max_jobs_per_wave = mem_budget, max_waves, max_jobs_per_wave
+        if large_query_steps is not None:
+            cfg.large_query_steps = large_query_steps
         h = ctypes.c_void_p()
         _check(lib().fw_server_create(graph.handle, ctypes.byref(cfg), ctypes.byref(h)))
         self.handle = h.value

@@ -232,12 +232,15 @@ def test_batch_plan_replays(small):
 
 
 # ------------------------------------------------------------ serving
-def test_server_results_equal_alone_in_a_concurrent_mix(small):
+@pytest.mark.parametrize("large_query_steps", [None, 0, 5000])
+def test_server_results_equal_alone_in_a_concurrent_mix(small, large_query_steps):
     """Queries submitted from several threads while others run on the GPU
-    give exactly the rows of fw_walk_host alone (0 differing entries)."""
+    give exactly the rows of fw_walk_host alone (0 differing entries), with
+    the default size classes, with one class, and with most queries large
+    (their own waves, admitted after the small ones)."""
     import threading
     g, G = small
-    srv = fw.Server(G, mem_budget=64 << 20, max_waves=3, max_jobs_per_wave=16)
+    srv = fw.Server(G, mem_budget=64 << 20, max_waves=3, max_jobs_per_wave=16, large_query_steps=large_query_steps)
     specs = _mixed_jobs(g, 160, seed=9, max_walkers=5000)
     outs = [np.full((len(sp["starts"]), sp["length"] + 1), -7, dtype=np.int32) for sp in specs]
     tickets = [None] * len(specs)
@@ -352,6 +355,9 @@ def test_server_submit_many_stops_at_the_first_bad_query(small):
 
 def test_server_errors_and_timeouts(small):
     g, G = small
+    with pytest.raises(fw.FlexiWalkError) as e:
+        fw.Server(G, mem_budget=1 << 20, max_waves=2, large_query_steps=-1)
+    assert e.value.status == -1
     srv = fw.Server(G, mem_budget=1 << 20, max_waves=2)
     big = np.zeros(1 << 17, dtype=np.int32)                 # 2^17 walkers x 11 entries > 1 MiB
     with pytest.raises(fw.FlexiWalkError) as e:
