@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--duration", type=float, default=10.0, help="serve suite: seconds of offered load")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve suite: mean arrivals per second")
     ap.add_argument("--max-waves", type=int, default=8, help="serve suite: concurrent waves (streams) of the server")
+    ap.add_argument("--large-query-steps", type=int, default=0,
+                    help="serve suite: the server's size-class threshold on W x L (0: one class, arrival order)")
     ap.add_argument("--no-serial", action="store_true", help="serve suite: skip the serial comparison (for "
                     "arrival rates far above what serial calls sustain, e.g. capacity runs)")
     a = ap.parse_args()
@@ -656,7 +658,7 @@ def _device_rate(G, cl, rate, duration, seed, hops, nstreams=8, per_batch=64):
             "batches": nb, "streams": nstreams}
 
 
-def serve_result(G, g, rate=2000.0, duration=10.0, max_waves=8, serial=True, capacity=True):
+def serve_result(G, g, rate=2000.0, duration=10.0, max_waves=8, serial=True, capacity=True, large_query_steps=0):
     """Continuous batching (fw_server) against serial fw_walk_host calls on the
     same arrival sequence at `rate` queries/s for `duration` s; then the
     server's capacity (throughput when 60x the rate arrives for 1 s: the
@@ -667,26 +669,27 @@ def serve_result(G, g, rate=2000.0, duration=10.0, max_waves=8, serial=True, cap
               "metapath": G.autotune("metapath", schema=[0, 1, 2, 3, 4], method=1),
               "weighted": G.autotune("weighted", method=1)}
     cl = _ServeClient(G, g)
-    cl.run("server", rate, duration, max_waves=max_waves, count=400)  # warm-up (module load, arena), discarded
-    out = {"server": cl.run("server", rate, duration, max_waves=max_waves)}
+    lqs = large_query_steps
+    cl.run("server", rate, duration, max_waves=max_waves, count=400, large_query_steps=lqs)  # warm-up, discarded
+    out = {"server": cl.run("server", rate, duration, max_waves=max_waves, large_query_steps=lqs)}
     if serial:
         out["serial"] = cl.run("serial", rate, duration)
     res = {"value": out["server"]["walker_steps_per_s"], "unit": "walker-steps/s",
            "config": {"workload": f"Poisson {rate:g}/s for {duration:g} s (shortened from 60 s) on R-MAT s22; "
                                   "W log-U[1,1e5], L U{10..100}, node2vec(2,.5)/metapath/weighted",
-                      "cost_ratios": ratios, "max_waves": max_waves},
+                      "cost_ratios": ratios, "max_waves": max_waves, "large_query_steps": large_query_steps},
            "serving": out,
            "p99_server_over_serial": (out["server"]["p99_ms"] / out["serial"]["p99_ms"]) if serial else None,
            "steps_server_over_serial": (out["server"]["walker_steps_per_s"] / out["serial"]["walker_steps_per_s"])
            if serial else None}
     if capacity:
-        sat = cl.run("server", 60.0 * rate, 1.0, seed=47, max_waves=max_waves)
+        sat = cl.run("server", 60.0 * rate, 1.0, seed=47, max_waves=max_waves, large_query_steps=lqs)
         cap = sat["walker_steps_per_s"]
         res["device_rate_same_queries"] = _device_rate(G, cl, 60.0 * rate, 1.0, 47, sat["hops"], max_waves)
         # queries per second at 70 % of capacity, from the steps a query of this mix actually takes
         rate70 = 0.7 * cap / (sat["hops"] / sat["queries"])
-        at70 = cl.run("server", rate70, 5.0, seed=48, max_waves=max_waves)
-        at50 = cl.run("server", rate70 * 5.0 / 7.0, 5.0, seed=49, max_waves=max_waves)
+        at70 = cl.run("server", rate70, 5.0, seed=48, max_waves=max_waves, large_query_steps=lqs)
+        at50 = cl.run("server", rate70 * 5.0 / 7.0, 5.0, seed=49, max_waves=max_waves, large_query_steps=lqs)
         res["capacity"] = {"walker_steps_per_s": cap, "saturated_run": sat,
                            "saturated": bool(sat["offered_walker_steps_per_s"] >= 1.5 * cap),
                            "over_device_rate": cap / res["device_rate_same_queries"]["walker_steps_per_s"],
@@ -706,7 +709,8 @@ def run_serve(args):
     torch.cuda.set_device(0)
     g = synth.workload_graph("s22")
     G = fw.Graph(g)
-    r = serve_result(G, g, args.rate, args.duration, args.max_waves, serial=not args.no_serial)
+    r = serve_result(G, g, args.rate, args.duration, args.max_waves, serial=not args.no_serial,
+                     large_query_steps=args.large_query_steps)
     G.close()
     _line("walker-steps/sec (served)", r["value"], "walker-steps/s", args,
           dict({k: v for k, v in r.items() if k not in ("value", "unit")}, ms_per_step=None))
